@@ -1,0 +1,248 @@
+"""Seeded synthetic SRTM workloads (linear kinetics) shared by the oracle tests,
+the CUDA parity tests and the benchmark.
+
+This module only builds models and simulates data from them: it draws rate
+constants, forms the fast transition ``F = expm(K dt)``, and simulates the
+fast-rate linear Gaussian system with slow-rate integrated measurements
+
+    x_{t+1} = F x_t + w_t,            w_t ~ N(0, Q)
+    y_k     = H sum_{i=1..l} x_{k,i} + v_k,   v_k ~ N(0, R)
+
+(the dual-rate model of Sec. III, with the measurement matrix ``H`` applied
+to the *sum* of the ``l`` fast states of interval ``k``; the paper's ``C``
+applies to their average, so ``C = l H``).  It contains no filtering or
+smoothing arithmetic.
+
+The paper's own benchmark (a CSTR case study whose parameters live in a cited
+paper) is not available; these five synthetic families stand in for it:
+
+1. 2-state A->B kinetics, l=10, N=100 (small reference case).
+2. 4-species first-order chain, rates log-U[0.05,1], dt=0.05, l=20, ny=2.
+3. 8-state random stable network K=-(D+S), l=50, ny=3, dense random H.
+4. 4096 ragged chains (nx=4, ny=1), l in {5,10,20}, N ~ U[100,20000].
+5. Stiff 6-species chain, rates log-U[1e-3,1e2], dt=0.01, l=100, ny=2.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+import scipy.linalg
+
+
+@dataclass
+class Problem:
+    """One SRTM sequence: model, prior and slow-rate measurements (all float64).
+
+    F: (nx,nx) fast transition.  Q: (nx,nx) fast process-noise covariance.
+    H: (ny,nx) applied to the sum of the ``ratio`` fast states of a slow interval.
+    R: (ny,ny) measurement-noise covariance.  m0, P0: prior of x_0.
+    y: (n_slow, ny) measurements; row k is y_{k+1} in the paper's 1-based index.
+    x: optional (n_slow*ratio+1, nx) simulated fast states x_0, x_{1,1}, ..., x_{N,l}.
+    """
+
+    F: np.ndarray
+    Q: np.ndarray
+    H: np.ndarray
+    R: np.ndarray
+    m0: np.ndarray
+    P0: np.ndarray
+    y: np.ndarray
+    ratio: int
+    x: np.ndarray | None = None
+    name: str = ""
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def nx(self) -> int:
+        return self.F.shape[0]
+
+    @property
+    def ny(self) -> int:
+        return self.H.shape[0]
+
+    @property
+    def n_slow(self) -> int:
+        return self.y.shape[0]
+
+
+def chain_rates_matrix(rates: np.ndarray) -> np.ndarray:
+    """Lower-bidiagonal first-order chain X1 -> X2 -> ... -> Xn -> (out)."""
+    n = len(rates)
+    K = np.zeros((n, n))
+    for j in range(n):
+        K[j, j] = -rates[j]
+        if j + 1 < n:
+            K[j + 1, j] = rates[j]
+    return K
+
+
+def log_uniform(rng: np.random.Generator, lo: float, hi: float, size) -> np.ndarray:
+    return np.exp(rng.uniform(np.log(lo), np.log(hi), size=size))
+
+
+def simulate(rng: np.random.Generator, F, Q, H, R, m0, P0, ratio: int, n_slow: int,
+             keep_states: bool = True):
+    """Draw x_0 ~ N(m0,P0), run x_{t+1} = F x_t + w_t for n_slow*ratio fast steps
+    and form y_k = H sum_{i=1..ratio} x_{k,i} + v_k.
+
+    The fast recursion is evaluated interval by interval, vectorised over the
+    intervals: the within-interval noise response e_{k,i} = F e_{k,i-1} + w
+    for all k at once, the interval end states by repeated doubling with
+    F^ratio, then x_{k,i} = F^i x_{k-1,l} + e_{k,i}.  This is the same sample
+    path as the step-by-step loop driven by the same noise draws.
+    """
+    nx = F.shape[0]
+    ny = H.shape[0]
+    l, N = ratio, n_slow
+    Lq = np.linalg.cholesky(Q)
+    Lr = np.linalg.cholesky(R)
+    x0 = m0 + np.linalg.cholesky(P0) @ rng.standard_normal(nx)
+    w = rng.standard_normal((N, l, nx)) @ Lq.T          # w[k, i-1]: noise into x_{k,i}
+    v = rng.standard_normal((N, ny)) @ Lr.T
+    # e[k, i-1] = sum_{r<=i} F^{i-r} w[k, r-1]
+    e = np.empty_like(w)
+    acc = np.zeros((N, nx))
+    for i in range(l):
+        acc = acc @ F.T + w[:, i]
+        e[:, i] = acc
+    # interval end states: z_k = F^l z_{k-1} + e[k, l-1], z_0 = x0  (doubling scan)
+    Fl = np.linalg.matrix_power(F, l)
+    z = np.concatenate([x0[None], e[:, l - 1]], axis=0)   # z[0]=x0, z[k]=e_k
+    Fd = Fl.copy()
+    d = 1
+    while d < N + 1:
+        z[d:] = z[d:] + z[:-d] @ Fd.T
+        Fd = Fd @ Fd
+        d *= 2
+    # fast states x_{k,i} = F^i z_{k-1} + e[k, i-1]
+    Fpow = np.empty((l, nx, nx))
+    P = np.eye(nx)
+    for i in range(l):
+        P = F @ P
+        Fpow[i] = P
+    xs = np.einsum("inm,km->kin", Fpow, z[:-1]) + e      # (N, l, nx)
+    y = xs.sum(axis=1) @ H.T + v
+    x = None
+    if keep_states:
+        x = np.concatenate([x0[None], xs.reshape(N * l, nx)], axis=0)
+    return y, x
+
+
+def config1(seed: int = 0, n_slow: int = 100, keep_states: bool = True) -> Problem:
+    """2-state A->B kinetics: K=[[-k1,0],[k1,-k2]], k1=.5, k2=.2, dt=.1, l=10,
+    Q=.01 I, m0=[1,0], P0=.1 I, y = [0,1] * sum of 10 fast states + N(0, 0.1)."""
+    rng = np.random.default_rng(seed)
+    k1, k2, dt = 0.5, 0.2, 0.1
+    K = np.array([[-k1, 0.0], [k1, -k2]])
+    F = scipy.linalg.expm(K * dt)
+    Q = 0.01 * np.eye(2)
+    H = np.array([[0.0, 1.0]])
+    R = np.array([[0.1]])
+    m0 = np.array([1.0, 0.0])
+    P0 = 0.1 * np.eye(2)
+    y, x = simulate(rng, F, Q, H, R, m0, P0, 10, n_slow, keep_states)
+    return Problem(F, Q, H, R, m0, P0, y, 10, x, "cfg1", {"K": K, "dt": dt})
+
+
+def config2(seed: int = 0, n_slow: int = 10_000, keep_states: bool = True) -> Problem:
+    """4-species chain, rates log-U[0.05,1], dt=.05, l=20, H=[e3;e4], Q=1e-3 I,
+    R=.05 I, m0=e1, P0=.1 I."""
+    rng = np.random.default_rng(seed)
+    rates = log_uniform(rng, 0.05, 1.0, 4)
+    K = chain_rates_matrix(rates)
+    dt = 0.05
+    F = scipy.linalg.expm(K * dt)
+    Q = 1e-3 * np.eye(4)
+    H = np.zeros((2, 4)); H[0, 2] = 1.0; H[1, 3] = 1.0
+    R = 0.05 * np.eye(2)
+    m0 = np.eye(4)[0]
+    P0 = 0.1 * np.eye(4)
+    y, x = simulate(rng, F, Q, H, R, m0, P0, 20, n_slow, keep_states)
+    return Problem(F, Q, H, R, m0, P0, y, 20, x, "cfg2", {"K": K, "dt": dt, "rates": rates})
+
+
+def config3(seed: int = 0, n_slow: int = 100_000, keep_states: bool = False) -> Problem:
+    """8-state stable network K = -(D+S): D diag log-U[.01,2], S 20%-dense N(0,1)
+    scaled so ||S||_2 <= 0.5 min(D) (then K+K^T < 0).  l=50, H (3x8) iid N(0,1),
+    Q=1e-4 I, R=.01 I, dt=.05, m0=e1, P0=.1 I."""
+    rng = np.random.default_rng(seed)
+    n = 8
+    D = np.diag(log_uniform(rng, 0.01, 2.0, n))
+    S = rng.standard_normal((n, n)) * (rng.uniform(size=(n, n)) < 0.2)
+    np.fill_diagonal(S, 0.0)
+    s2 = np.linalg.norm(S, 2)
+    if s2 > 0:
+        S *= 0.5 * np.min(np.diag(D)) / s2
+    K = -(D + S)
+    dt = 0.05
+    F = scipy.linalg.expm(K * dt)
+    Q = 1e-4 * np.eye(n)
+    H = rng.standard_normal((3, n))
+    R = 0.01 * np.eye(3)
+    m0 = np.eye(n)[0]
+    P0 = 0.1 * np.eye(n)
+    y, x = simulate(rng, F, Q, H, R, m0, P0, 50, n_slow, keep_states)
+    return Problem(F, Q, H, R, m0, P0, y, 50, x, "cfg3", {"K": K, "dt": dt})
+
+
+def config4(seed: int = 0, n_seq: int = 4096, n_min: int = 100, n_max: int = 20_000,
+            ratios=(5, 10, 20), keep_states: bool = False) -> list[Problem]:
+    """Ragged batch: per sequence a 4-species chain as in config 2 (dt=.05),
+    ratio drawn from {5,10,20}, n_slow ~ U[n_min, n_max], ny=1 observing
+    species 4, Q=1e-3 I, R=.05, m0=e1, P0=.1 I."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for s in range(n_seq):
+        rates = log_uniform(rng, 0.05, 1.0, 4)
+        K = chain_rates_matrix(rates)
+        F = scipy.linalg.expm(K * 0.05)
+        Q = 1e-3 * np.eye(4)
+        H = np.zeros((1, 4)); H[0, 3] = 1.0
+        R = np.array([[0.05]])
+        m0 = np.eye(4)[0]
+        P0 = 0.1 * np.eye(4)
+        l = int(rng.choice(ratios))
+        N = int(rng.integers(n_min, n_max + 1))
+        y, x = simulate(rng, F, Q, H, R, m0, P0, l, N, keep_states)
+        out.append(Problem(F, Q, H, R, m0, P0, y, l, x, f"cfg4[{s}]", {"K": K}))
+    return out
+
+
+def config5(seed: int = 0, n_slow: int = 10_000, keep_states: bool = False) -> Problem:
+    """Stiff 6-species chain, rates log-U[1e-3,1e2], dt=.01, l=100, observing the
+    last two species, Q=1e-6 I, R=1e-3 I, m0=e1, P0=.1 I."""
+    rng = np.random.default_rng(seed)
+    rates = log_uniform(rng, 1e-3, 1e2, 6)
+    K = chain_rates_matrix(rates)
+    dt = 0.01
+    F = scipy.linalg.expm(K * dt)
+    Q = 1e-6 * np.eye(6)
+    H = np.zeros((2, 6)); H[0, 4] = 1.0; H[1, 5] = 1.0
+    R = 1e-3 * np.eye(2)
+    m0 = np.eye(6)[0]
+    P0 = 0.1 * np.eye(6)
+    y, x = simulate(rng, F, Q, H, R, m0, P0, 100, n_slow, keep_states)
+    return Problem(F, Q, H, R, m0, P0, y, 100, x, "cfg5", {"K": K, "dt": dt, "rates": rates})
+
+
+def random_model(seed: int, nx: int, ny: int, ratio: int, n_slow: int,
+                 q_scale: float = 0.05, r_scale: float = 0.1) -> Problem:
+    """Small generic model with dense (non-diagonal) Q, R and P0, a random
+    stable F and random H; used for pins and edge cases at tiny sizes."""
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((nx, nx))
+    A *= 0.9 / max(1e-12, np.max(np.abs(np.linalg.eigvals(A))))
+    G = rng.standard_normal((nx, nx))
+    Q = q_scale * (G @ G.T / nx + 0.2 * np.eye(nx))
+    Gr = rng.standard_normal((ny, ny))
+    R = r_scale * (Gr @ Gr.T / ny + 0.5 * np.eye(ny))
+    H = rng.standard_normal((ny, nx))
+    m0 = rng.standard_normal(nx)
+    Gp = rng.standard_normal((nx, nx))
+    P0 = 0.2 * (Gp @ Gp.T / nx + 0.3 * np.eye(nx))
+    y, x = simulate(rng, A, Q, H, R, m0, P0, ratio, n_slow, True)
+    return Problem(A, Q, H, R, m0, P0, y, ratio, x, f"rand{nx}x{ny}l{ratio}N{n_slow}")
+
+
+CONFIGS = {1: config1, 2: config2, 3: config3, 4: config4, 5: config5}

@@ -1,0 +1,244 @@
+"""Pins of the FP64 CPU oracle against things other than itself.
+
+Each pin is chosen so that a plausible slip in the oracle (a dropped term, a
+wrong sign or index, a transposed operand) fails at least one of them:
+
+* brute-force dense joint-Gaussian posteriors over all stacked fast states
+  (tests/brute.py) for the filter (Eq. 17), the slow IMKF (Eq. 12), the
+  sequential smoother (Eq. 21, 22) and the parallel form (Eq. 25-30);
+* the textbook Kalman filter + RTS smoother when the ratio l is 1 (Sec. III-C
+  notes that l=1 is the standard RTS case);
+* the lifted slow-rate constants (Eq. 7-11) read off the joint prior;
+* the discrete algebraic Riccati equation with cross term (scipy) as the
+  steady state of the slow filter covariance;
+* associativity and the identity of both operators (Eq. 27, 30);
+* invariants: symmetry, PSD, smoothed == filtered on the last interval
+  (E_N = 0, Eq. 29), smoothed covariance <= filtered covariance;
+* a planted mistake (the printed S_k without the transpose) must fail the
+  brute-force pin.
+"""
+import numpy as np
+import pytest
+import scipy.linalg
+
+from paper_2410_00627_gb300 import synth
+from tests import brute
+
+
+def rel_mean(a, b):
+    return np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)
+
+
+def rel_cov(a, b):
+    return np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)
+
+
+TINY = [
+    dict(seed=1, nx=1, ny=1, ratio=3, n_slow=4),
+    dict(seed=2, nx=2, ny=1, ratio=1, n_slow=5),
+    dict(seed=3, nx=3, ny=2, ratio=4, n_slow=5),
+    dict(seed=4, nx=2, ny=2, ratio=2, n_slow=1),
+    dict(seed=5, nx=3, ny=1, ratio=5, n_slow=3),
+    dict(seed=6, nx=4, ny=3, ratio=2, n_slow=4),
+]
+
+
+@pytest.mark.parametrize("kw", TINY, ids=lambda k: "n{nx}m{ny}l{ratio}N{n_slow}".format(**k))
+def test_sequential_matches_brute_force(oracle_mod, kw):
+    prob = synth.random_model(kw["seed"], kw["nx"], kw["ny"], kw["ratio"], kw["n_slow"])
+    ref = brute.posteriors(prob)
+    out = oracle_mod.sequential(prob)
+    l, n = prob.ratio, prob.nx
+    for key in ["fast_filt_mean", "fast_smooth_mean"]:
+        assert rel_mean(out[key], ref[key]) < 1e-11, key
+    for key in ["fast_filt_cov", "fast_smooth_cov"]:
+        assert rel_cov(out[key], ref[key]) < 1e-11, key
+    # slow IMKF (Eq. 12) = x_{k,l} | y_{1:k};  first smoothed state (Eq. 22) = x_{k,1} | y_{1:N}
+    last = np.arange(prob.n_slow) * l + (l - 1)
+    first = np.arange(prob.n_slow) * l
+    assert rel_mean(out["slow_filt_mean"], ref["fast_filt_mean"][last]) < 1e-11
+    assert rel_cov(out["slow_filt_cov"], ref["fast_filt_cov"][last]) < 1e-11
+    assert rel_mean(out["first_smooth_mean"], ref["fast_smooth_mean"][first]) < 1e-11
+    assert rel_cov(out["first_smooth_cov"], ref["fast_smooth_cov"][first]) < 1e-11
+    assert out["fast_filt_cov"].shape == (prob.n_slow * l, n, n)
+
+
+@pytest.mark.parametrize("kw", TINY, ids=lambda k: "n{nx}m{ny}l{ratio}N{n_slow}".format(**k))
+@pytest.mark.parametrize("order", [0, 1])
+def test_parallel_form_matches_brute_force(oracle_mod, kw, order):
+    prob = synth.random_model(kw["seed"], kw["nx"], kw["ny"], kw["ratio"], kw["n_slow"])
+    ref = brute.posteriors(prob)
+    out = oracle_mod.parallel(prob, order=order)
+    l = prob.ratio
+    last = np.arange(prob.n_slow) * l + (l - 1)
+    first = np.arange(prob.n_slow) * l
+    assert rel_mean(out["slow_filt_mean"], ref["fast_filt_mean"][last]) < 1e-10
+    assert rel_cov(out["slow_filt_cov"], ref["fast_filt_cov"][last]) < 1e-10
+    assert rel_mean(out["first_smooth_mean"], ref["fast_smooth_mean"][first]) < 1e-10
+    assert rel_cov(out["first_smooth_cov"], ref["fast_smooth_cov"][first]) < 1e-10
+
+
+def test_printed_sk_without_transpose_fails_brute_force(oracle_mod):
+    """Plants the printed S_k = P^f_{k,1} - E_k A P^f_{k,1,l} (no transpose) in the
+    oracle's parallel smoother and shows the brute-force pin rejects it, while
+    the transposed reading passes (the reading this build takes, Eq. 29)."""
+    prob = synth.random_model(3, 3, 2, 4, 5)
+    ref = brute.posteriors(prob)
+    first = np.arange(prob.n_slow) * prob.ratio
+    good = oracle_mod.parallel(prob, order=0, flags=0)
+    bad = oracle_mod.parallel(prob, order=0, flags=1)
+    assert rel_cov(good["first_smooth_cov"], ref["fast_smooth_cov"][first]) < 1e-10
+    assert rel_cov(bad["first_smooth_cov"], ref["fast_smooth_cov"][first]) > 1e-4
+
+
+def textbook_kf_rts(F, Q, H, R, m0, P0, y):
+    """Standard Kalman filter + RTS smoother (x_k = F x_{k-1} + w, y_k = H x_k + v)."""
+    N, n = y.shape[0], F.shape[0]
+    mf = np.zeros((N, n)); Pf = np.zeros((N, n, n))
+    mp = np.zeros((N, n)); Pp = np.zeros((N, n, n))
+    m, P = m0, P0
+    for k in range(N):
+        m, P = F @ m, F @ P @ F.T + Q
+        mp[k], Pp[k] = m, P
+        S = H @ P @ H.T + R
+        K = np.linalg.solve(S, H @ P).T
+        m = m + K @ (y[k] - H @ m)
+        P = P - K @ S @ K.T
+        mf[k], Pf[k] = m, P
+    ms = mf.copy(); Ps = Pf.copy()
+    for k in range(N - 2, -1, -1):
+        G = np.linalg.solve(Pp[k + 1], F @ Pf[k]).T
+        ms[k] = mf[k] + G @ (ms[k + 1] - mp[k + 1])
+        Ps[k] = Pf[k] + G @ (Ps[k + 1] - Pp[k + 1]) @ G.T
+    return mf, Pf, ms, Ps
+
+
+@pytest.mark.parametrize("seed,nx,ny", [(11, 2, 1), (12, 3, 2), (13, 4, 4)])
+def test_ratio_one_is_textbook_kalman_rts(oracle_mod, seed, nx, ny):
+    prob = synth.random_model(seed, nx, ny, 1, 60)
+    mf, Pf, ms, Ps = textbook_kf_rts(prob.F, prob.Q, prob.H, prob.R, prob.m0, prob.P0, prob.y)
+    out = oracle_mod.sequential(prob)
+    assert rel_mean(out["fast_filt_mean"], mf) < 1e-11
+    assert rel_cov(out["fast_filt_cov"], Pf) < 1e-11
+    assert rel_mean(out["slow_filt_mean"], mf) < 1e-11
+    assert rel_mean(out["fast_smooth_mean"], ms) < 1e-10
+    assert rel_cov(out["fast_smooth_cov"], Ps) < 1e-10
+    par = oracle_mod.parallel(prob, order=1)
+    assert rel_mean(par["first_smooth_mean"], ms) < 1e-10
+    assert rel_cov(par["first_smooth_cov"], Ps) < 1e-10
+
+
+@pytest.mark.parametrize("seed,nx,ny,l", [(21, 2, 1, 3), (22, 3, 2, 5), (23, 4, 2, 20)])
+def test_lifted_constants_from_joint_prior(oracle_mod, seed, nx, ny, l):
+    """With x_{k-1,l} known, (x_{k,l}, y_k) has covariance [[Qbar, GQM],[GQM^T, MQM+R]]
+    and means (Abar x, Cbar x): read them off the joint prior of one interval."""
+    prob = synth.random_model(seed, nx, ny, l, 1)
+    lift = oracle_mod.lifted(prob.F, prob.Q, prob.H, l)
+    n = nx
+    mu, S = brute.joint_prior(prob.F, prob.Q, np.zeros(n), np.zeros((n, n)), l)
+    Hz = brute.meas_matrix(prob.H, n, l, 1)
+    xl = slice(l * n, (l + 1) * n)
+    assert np.allclose(lift["Qbar"], S[xl, xl], rtol=0, atol=1e-13 * np.abs(S).max())
+    assert np.allclose(lift["MQM"], Hz @ S @ Hz.T, rtol=0, atol=1e-13 * np.abs(Hz @ S @ Hz.T).max())
+    assert np.allclose(lift["GQM"], S[xl] @ Hz.T, rtol=0, atol=1e-13 * np.abs(S[xl] @ Hz.T).max())
+    # means are linear in x_0: use the transition maps of the unrolled prior
+    e = np.eye(n)
+    Ab = np.stack([brute.joint_prior(prob.F, prob.Q, e[j], np.zeros((n, n)), l)[0][xl] for j in range(n)], 1)
+    Cb = np.stack([Hz @ brute.joint_prior(prob.F, prob.Q, e[j], np.zeros((n, n)), l)[0] for j in range(n)], 1)
+    assert np.allclose(lift["Abar"], Ab, atol=1e-13)
+    assert np.allclose(lift["Cbar"], Cb, atol=1e-12 * max(1, np.abs(Cb).max()))
+
+
+@pytest.mark.parametrize("cfg", [1, 2])
+def test_slow_filter_reaches_dare(oracle_mod, cfg):
+    """The IMKF covariance converges to the DARE solution with cross term
+    S = G Q~ M^T:  X = A X A^T + Qbar - (A X C^T + S)(C X C^T + R_x)^{-1}(.)^T."""
+    prob = synth.CONFIGS[cfg](seed=0, n_slow=400, keep_states=False)
+    lift = oracle_mod.lifted(prob.F, prob.Q, prob.H, prob.ratio)
+    X = scipy.linalg.solve_discrete_are(lift["Abar"].T, lift["Cbar"].T, lift["Qbar"],
+                                        lift["MQM"] + prob.R, s=lift["GQM"])
+    out = oracle_mod.sequential(prob, fast=False, smooth=False)
+    assert rel_cov(out["slow_filt_cov"][-1], X) < 1e-9
+
+
+def _random_filter_element(rng, n):
+    G1, G2 = rng.standard_normal((n, n)), rng.standard_normal((n, n))
+    return {"F": rng.standard_normal((n, n)) * 0.7, "d": rng.standard_normal(n),
+            "D": G1 @ G1.T / n, "eta": rng.standard_normal(n), "J": G2 @ G2.T / n}
+
+
+@pytest.mark.parametrize("n", [1, 2, 4, 6])
+def test_filter_operator_associative_with_identity(oracle_mod, n):
+    rng = np.random.default_rng(n)
+    a, b, c = (_random_filter_element(rng, n) for _ in range(3))
+    left = oracle_mod.filter_op(oracle_mod.filter_op(a, b), c)
+    right = oracle_mod.filter_op(a, oracle_mod.filter_op(b, c))
+    for k in left:
+        assert np.allclose(left[k], right[k], rtol=1e-10, atol=1e-10), k
+    ident = {"F": np.eye(n), "d": np.zeros(n), "D": np.zeros((n, n)), "eta": np.zeros(n), "J": np.zeros((n, n))}
+    for x in (oracle_mod.filter_op(ident, a), oracle_mod.filter_op(a, ident)):
+        for k in x:
+            assert np.allclose(x[k], a[k], rtol=1e-13, atol=1e-13), k
+
+
+@pytest.mark.parametrize("n", [1, 3, 8])
+def test_smoother_operator_associative_with_identity(oracle_mod, n):
+    rng = np.random.default_rng(100 + n)
+
+    def el():
+        G = rng.standard_normal((n, n))
+        return {"E": rng.standard_normal((n, n)) * 0.5, "g": rng.standard_normal(n), "S": G @ G.T}
+
+    a, b, c = el(), el(), el()
+    left = oracle_mod.smoother_op(oracle_mod.smoother_op(a, b), c)
+    right = oracle_mod.smoother_op(a, oracle_mod.smoother_op(b, c))
+    for k in left:
+        assert np.allclose(left[k], right[k], rtol=1e-12, atol=1e-12), k
+    ident = {"E": np.eye(n), "g": np.zeros(n), "S": np.zeros((n, n))}
+    for x in (oracle_mod.smoother_op(ident, a), oracle_mod.smoother_op(a, ident)):
+        for k in x:
+            assert np.allclose(x[k], a[k], atol=1e-14), k
+
+
+@pytest.mark.parametrize("cfg,n_slow", [(1, 100), (2, 150)])
+def test_parallel_equals_sequential_midsize(oracle_mod, cfg, n_slow):
+    """The paper states the parallel and sequential forms give identical results."""
+    prob = synth.CONFIGS[cfg](seed=3, n_slow=n_slow, keep_states=False)
+    seq = oracle_mod.sequential(prob, fast=False)
+    for order in (0, 1):
+        par = oracle_mod.parallel(prob, order=order)
+        for k in ["slow_filt_mean", "first_smooth_mean"]:
+            assert rel_mean(par[k], seq[k]) < 1e-10, (k, order)
+        for k in ["slow_filt_cov", "first_smooth_cov"]:
+            assert rel_cov(par[k], seq[k]) < 1e-10, (k, order)
+
+
+@pytest.mark.parametrize("cfg", [1, 2])
+def test_invariants(oracle_mod, cfg):
+    prob = synth.CONFIGS[cfg](seed=5, n_slow=60, keep_states=False)
+    out = oracle_mod.sequential(prob)
+    l = prob.ratio
+    for key in ["fast_filt_cov", "fast_smooth_cov", "slow_filt_cov", "first_smooth_cov"]:
+        P = out[key]
+        assert np.max(np.abs(P - np.swapaxes(P, 1, 2))) <= 1e-12 * np.abs(P).max(), key
+        ev = np.linalg.eigvalsh(0.5 * (P + np.swapaxes(P, 1, 2)))
+        assert ev.min() >= -1e-12 * np.abs(P).max(), key
+    # last interval: smoothed == filtered (E_N = 0)
+    assert np.array_equal(out["fast_smooth_mean"][-l:], out["fast_filt_mean"][-l:])
+    assert np.array_equal(out["fast_smooth_cov"][-l:], out["fast_filt_cov"][-l:])
+    # smoothing never increases uncertainty
+    d = out["fast_filt_cov"] - out["fast_smooth_cov"]
+    ev = np.linalg.eigvalsh(0.5 * (d + np.swapaxes(d, 1, 2)))
+    assert ev.min() >= -1e-10 * np.abs(out["fast_filt_cov"]).max()
+    # slow IMKF == last block of the fast filter (two derivations of the same quantity)
+    assert rel_mean(out["slow_filt_mean"], out["fast_filt_mean"][l - 1::l]) < 1e-12
+    assert rel_cov(out["slow_filt_cov"], out["fast_filt_cov"][l - 1::l]) < 1e-11
+
+
+def test_sampled_fast_range_matches_full(oracle_mod):
+    prob = synth.config2(seed=7, n_slow=30, keep_states=False)
+    full = oracle_mod.sequential(prob)
+    part = oracle_mod.sequential(prob, k_lo=10, k_hi=13)
+    l = prob.ratio
+    for k in ["fast_filt_mean", "fast_filt_cov", "fast_smooth_mean", "fast_smooth_cov"]:
+        assert np.array_equal(part[k], full[k][10 * l:13 * l]), k
