@@ -1,0 +1,319 @@
+"""Benchmark of the GB300 SRTM filter + smoother (fast-rate smoothed states/s).
+
+One step = one srtm_smoother call over one synthetic sequence: per-model
+constants, forward filter scan, interval setup + smoother elements, reverse
+smoother scan and fast-rate recovery (fast and slow smoothed means and
+covariances written to HBM).  Workload (default): config 2, the 4-species
+chain with nx=4, ny=2, ratio L=20, T=10^4 slow measurements (2*10^5 fast
+steps), synthetic data from the seeded generator.  Inputs and outputs are
+resident in HBM; L2 (129 MB) is flushed by writing a 256 MB buffer before
+every timed step, outside the timed events.
+
+Headline `value`: mixed precision (float32 scans with float64 solves,
+symmetrisation and recovery).  The same line carries the plain-FP64 number.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Multi-GPU (torchrun): every rank runs its own independent sequence (weak
+scaling, no collective on the data path); rank 0 prints.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "fast-rate smoothed states/sec (filter+smoother) on 1 GB300, mixed vs FP64, at oracle tol"
+UNIT = "fast states/s"
+FP64_PEAK_GFLOPS = 1250.0   # GB300 FP64 nominal (recipe table); no FP64 entry in MEASURED_PEAKS.json
+HBM_FALLBACK_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["mixed", "fp64", "fp32"], default="mixed")
+    ap.add_argument("--n-slow", type=int, default=10_000)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-extras", action="store_true", help="skip the fp64, e2e and cpu legs")
+    return ap.parse_args()
+
+
+def workload(args, rank=0):
+    from paper_2410_00627_gb300 import synth
+    return synth.config2(seed=args.seed + rank, n_slow=args.n_slow, keep_states=False)
+
+
+def config_dict(args, prob, precision):
+    return {"workload": f"config 2: 4-species chain nx=4 ny=2 L={prob.ratio} T={prob.n_slow} slow "
+                        f"({prob.n_slow * prob.ratio} fast steps)",
+            "precision": precision, "nx": prob.nx, "ny": prob.ny, "ratio": prob.ratio,
+            "n_slow": prob.n_slow, "l2": "flushed (256 MB write) before every timed step",
+            "seed": args.seed}
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.hw_slowdown",
+              "clocks_event_reasons.hw_thermal_slowdown", "clocks_event_reasons.sw_thermal_slowdown",
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index, self.rows, self.proc = index, [], None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={','.join(self.FIELDS)}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == len(self.FIELDS):
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for r in self.rows for j in range(4) if r[3 + j].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# --------------------------------------------------------------------------- our arm
+def run_ours(args, rank, world, dist):
+    import torch
+
+    from paper_2410_00627_gb300 import api, build
+    build.build()
+    api.load()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    prob = workload(args, rank)
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)  # noqa: E731
+    ins = [t(getattr(prob, k)) for k in ("F", "Q", "H", "R", "m0", "P0", "y")]
+    n_fast = prob.n_slow * prob.ratio
+    outs = {"fast_mean": torch.empty(n_fast, prob.nx, dtype=torch.float64, device=dev),
+            "fast_cov": torch.empty(n_fast, prob.nx, prob.nx, dtype=torch.float64, device=dev),
+            "slow_mean": torch.empty(prob.n_slow, prob.nx, dtype=torch.float64, device=dev),
+            "slow_cov": torch.empty(prob.n_slow, prob.nx, prob.nx, dtype=torch.float64, device=dev)}
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(precision):
+        api.smoother(*ins, prob.ratio, precision=precision, out=outs)
+
+    def timed(precision, steps, warmup, stage=False):
+        for _ in range(warmup):
+            step(precision)
+        api.status()
+        ms, rec_ms = [], []
+        api.set_stage_timing(stage)
+        try:
+            torch.cuda.synchronize()
+            if dist:
+                dist.barrier()
+            for _ in range(steps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                step(precision)
+                e1.record(stream)
+                if stage:
+                    rec_ms.append(api.stage_times())
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            torch.cuda.synchronize()
+            if dist:
+                dist.barrier()
+        finally:
+            api.set_stage_timing(False)
+        api.status()
+        return ms, rec_ms
+
+    clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if clocks:
+        clocks.start()
+    ms, stages = timed(args.precision, args.steps, args.warmup, stage=True)
+    clock_info = clocks.stop() if clocks else None
+    mean_ms = float(np.mean(ms))
+    if dist:
+        tt = torch.tensor([mean_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        mean_ms = float(tt.item())
+    value = world * n_fast / (mean_ms * 1e-3)
+    if rank != 0:
+        return None
+    stage_mean = {k: float(np.mean([s[k] for s in stages])) for k in stages[0]}
+    # roofline of the dominant kernel (fast-rate recovery): FP64 ALU bound.
+    n, m = prob.nx, prob.ny
+    fma_per_fast = 7 * n ** 3 + 3 * n * n * m + n * m * m
+    rec_s = stage_mean["recovery"] * 1e-3
+    achieved = 2.0 * fma_per_fast * n_fast / rec_s / 1e9
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "recover_kernel_traffic.json")
+    if os.path.exists(prof):
+        try:
+            tr = json.load(open(prof))
+            if tr.get("n_fast") and tr.get("precision") == args.precision:
+                traffic = tr["dram_bytes_per_fast_step"] * n_fast
+        except (ValueError, KeyError):
+            traffic = None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"mixed": "f32+f64", "fp64": "f64", "fp32": "f32"}[args.precision],
+        "data": "synthetic (seeded generator, config 2 linear kinetics)",
+        "config": config_dict(args, prob, args.precision),
+        "stage_ms": stage_mean,
+        "roofline": {"bound": "alu", "kernel": "recover_kernel", "achieved": achieved,
+                     "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": achieved / FP64_PEAK_GFLOPS,
+                     "peak_source": "GB300 FP64 nominal 1.25 TFLOP/s (recipe table)",
+                     "flops_per_fast_step": 2 * fma_per_fast, "traffic": traffic},
+        "gpu_launches": args.steps * api.launches_per_call(True),
+        "clocks": clock_info,
+    }
+    if not args.no_extras:
+        other = "fp64" if args.precision != "fp64" else "mixed"
+        ms2, _ = timed(other, max(5, args.steps // 2), 3)
+        line[other] = {"value": n_fast / (float(np.mean(ms2)) * 1e-3), "ms_per_step": float(np.mean(ms2))}
+        line["e2e"] = run_e2e(args, prob, api, torch, flush)
+        line["cpu_baseline"] = run_cpu_baseline(args, prob)
+    return line
+
+
+def run_e2e(args, prob, api, torch, flush):
+    """Same metric through the host-buffer C-ABI entry point: pinned host
+    inputs/outputs, H2D copies, the device path and D2H copies in the timed region."""
+    def pinned(a):
+        t = torch.empty(a.shape, dtype=torch.float64, pin_memory=True)
+        t.numpy()[...] = a
+        return t
+    ins = {k: pinned(np.ascontiguousarray(getattr(prob, k))) for k in ("F", "Q", "H", "R", "m0", "P0", "y")}
+    n_fast = prob.n_slow * prob.ratio
+    nx = prob.nx
+    outs = {"fast_mean": torch.empty((n_fast, nx), dtype=torch.float64, pin_memory=True),
+            "fast_cov": torch.empty((n_fast, nx, nx), dtype=torch.float64, pin_memory=True),
+            "slow_mean": torch.empty((prob.n_slow, nx), dtype=torch.float64, pin_memory=True),
+            "slow_cov": torch.empty((prob.n_slow, nx, nx), dtype=torch.float64, pin_memory=True)}
+    on = {k: v.numpy() for k, v in outs.items()}
+    stream = torch.cuda.current_stream()
+    args_np = [ins[k].numpy() for k in ("F", "Q", "H", "R", "m0", "P0", "y")]
+    for _ in range(3):
+        api.smoother_host(*args_np, prob.ratio, precision=args.precision, out=on, stream=stream)
+    ms = []
+    steps = max(5, args.steps // 2)
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        api.smoother_host(*args_np, prob.ratio, precision=args.precision, out=on, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    h2d = sum(a.nbytes for a in args_np)
+    d2h = sum(a.nbytes for a in on.values())
+    return {"value": n_fast / (float(np.mean(ms)) * 1e-3), "unit": UNIT, "ms_per_step": float(np.mean(ms)),
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "api": "srtm_smoother_host (C-ABI, pinned host buffers)"}
+
+
+def oracle_time(prob, seconds):
+    """The FP64 CPU oracle as it stands (sequential IMKF + fast filter + the
+    paper's sequential smoother, every fast output), single thread, timed on
+    repeated passes over the whole workload for about `seconds`."""
+    import oracle
+    oracle.build()
+    n_fast = prob.n_slow * prob.ratio
+    oracle.sequential(prob)  # warm
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        oracle.sequential(prob)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return reps * n_fast / el, reps, el
+
+
+def run_cpu_baseline(args, prob):
+    v, reps, el = oracle_time(prob, args.cpu_seconds)
+    return {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{reps} full passes over the config-2 workload ({prob.n_slow} slow / "
+                      f"{prob.n_slow * prob.ratio} fast steps) in {el:.1f} s, 1 thread, FP64 C (-O2)"}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle on the host cores, same workload."""
+    from paper_2410_00627_gb300 import synth  # noqa: F401
+    prob = workload(args)
+    n_fast = prob.n_slow * prob.ratio
+    import oracle
+    oracle.build()
+    for _ in range(args.warmup):
+        oracle.sequential(prob)
+    ts = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.sequential(prob)
+        ts.append(time.perf_counter() - t0)
+    mean = float(np.mean(ts))
+    value = n_fast / mean
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded generator)",
+            "config": config_dict(args, prob, "fp64 (CPU oracle)"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"the whole workload per step, {args.steps} steps, 1 thread"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)), flush=True)
+        return
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        local = int(os.environ.get("LOCAL_RANK", "0"))
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", init_method="env://")
+    line = run_ours(args, rank, world, dist)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,170 @@
+/*
+ * srtm.h -- C-ABI of the GB300 (sm_103a) parallel-in-time filter and smoother
+ * for linear Gaussian systems with slow-rate integrated measurements (SRTM),
+ * after Yaghoobi & Sarkka, "Parallel state estimation for systems with
+ * integrated measurements" (arXiv 2410.00627).
+ *
+ * Model (Sec. III, Eq. (5)-(6)), one sequence:
+ *     x_{k,i} = F x_{k,i-1} + w,          w ~ N(0, Q),   x_{k,0} = x_{k-1,l}
+ *     y_k     = H sum_{i=1..l} x_{k,i} + v_k,  v_k ~ N(0, R),  x_{0,l} ~ N(m0, P0)
+ * for slow steps k = 1..N and fast steps i = 1..l (l = ratio).  H multiplies
+ * the SUM of the l fast states; the paper's C (which multiplies their average)
+ * is l*H.
+ *
+ * Every entry point runs the whole method on the GPU: per-model constants
+ * (Eq. 7-12, 25-26), the forward filter scan with the (F,d,D,eta,J) operator
+ * (Eq. 27), the per-interval smoother elements (Eq. 29), the reverse smoother
+ * scan with the (E,g,S) operator (Eq. 30), and the fast-rate recovery inside
+ * each slow interval (Eq. 17 and 21, Remarks 1 and 3).  No CPU fallback exists.
+ *
+ * Conventions for all entry points
+ *   - Matrices are row-major IEEE float64.  Device entry points take DEVICE
+ *     pointers (cudaMalloc'd or managed); passing a host pointer returns
+ *     SRTM_ERR_ARG.  The caller owns every input and output buffer.
+ *   - Calls are asynchronous on `stream` (NULL = legacy default stream).
+ *     Errors found on the device (a look-back wait that exceeded its bound, a
+ *     singular solve, inconsistent batch metadata) are latched on the device
+ *     and returned by srtm_status(), which synchronizes the stream.
+ *   - The library owns one cached device workspace per GPU.  A call whose
+ *     problem needs more workspace than any earlier call allocates it (a
+ *     synchronizing cudaMalloc); make one such call before capturing calls
+ *     into a CUDA graph.  srtm_release() frees it.  Calls that share a GPU
+ *     must be issued on one stream (or be otherwise serialized): they share
+ *     the workspace.
+ *   - Limits: 1 <= nx <= 8, 1 <= ny <= 4, ratio >= 1, n_slow >= 1.
+ *   - Output index convention: the fast state x_{k,i} (paper index, 1-based k
+ *     and i) is row (k-1)*ratio + (i-1) of the fast outputs; the slow outputs
+ *     hold x_{k,l} (the last fast state of interval k) in row k-1.  Each
+ *     covariance row is a full nx*nx row-major matrix (exactly symmetric).
+ */
+#ifndef SRTM_H
+#define SRTM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t. */
+typedef struct CUstream_st *srtm_stream_t;
+
+typedef enum {
+  SRTM_FP64 = 0,  /* everything in float64                                       */
+  SRTM_MIXED = 1, /* scans and filter elements in float32; the (I + D_i J_j)
+                     solves of Eq. 27, the per-interval smoother elements and
+                     solves (Eq. 17, 29), covariance symmetrisation and the
+                     fast-rate recovery in float64                                */
+  SRTM_FP32 = 2   /* everything after the per-model constants in float32          */
+} srtm_precision;
+
+enum {
+  SRTM_OK = 0,
+  SRTM_ERR_ARG = -1,         /* bad size, NULL required pointer, host pointer   */
+  SRTM_ERR_SINGULAR = -3,    /* a solve met a zero or non-finite pivot          */
+  SRTM_ERR_TIMEOUT = -4,     /* a scan look-back wait exceeded its bound        */
+  SRTM_ERR_CUDA = -5,        /* a CUDA runtime call failed                      */
+  SRTM_ERR_UNSUPPORTED = -6, /* nx or ny outside the compiled range             */
+  SRTM_ERR_META = -7         /* batch metadata inconsistent with declared sizes */
+};
+
+/* One sequence.  All pointers are device pointers to float64.
+ *   F  nx*nx   fast transition (the paper's A)
+ *   Q  nx*nx   fast process-noise covariance
+ *   H  ny*nx   integrated-measurement matrix (applies to the sum of l states)
+ *   R  ny*ny   measurement-noise covariance
+ *   m0 nx, P0 nx*nx   prior of x_0
+ *   y  n_slow*ny      y_k in row k-1                                          */
+typedef struct {
+  int nx, ny, ratio, n_slow;
+  const double *F, *Q, *H, *R, *m0, *P0;
+  const double *y;
+} srtm_problem;
+
+/* Caller-allocated outputs; any pointer may be NULL (that output is skipped).
+ *   fast_mean n_slow*ratio*nx,  fast_cov n_slow*ratio*nx*nx
+ *   slow_mean n_slow*nx,        slow_cov n_slow*nx*nx                          */
+typedef struct {
+  double *fast_mean, *fast_cov, *slow_mean, *slow_cov;
+} srtm_output;
+
+/* A ragged batch of independent sequences with common nx and ny.
+ *   ratio[s], n_slow[s]   DEVICE int arrays of length n_seq
+ *   F,Q,R,P0 ... packed per sequence: sequence s uses F + s*nx*nx, Q + s*nx*nx,
+ *              H + s*ny*nx, R + s*ny*ny, m0 + s*nx, P0 + s*nx*nx
+ *   y          rows of all sequences concatenated in order (total_slow rows)
+ *   max_ratio  host-side upper bound of ratio[]
+ *   total_slow host-side sum of n_slow[]; total_fast = sum of n_slow[s]*ratio[s]
+ * Outputs are concatenated the same way (fast rows in sequence order, then
+ * slow rows in sequence order).  Metadata that disagrees with total_slow,
+ * total_fast or max_ratio is detected on the device: nothing is computed and
+ * srtm_status() returns SRTM_ERR_META.                                         */
+typedef struct {
+  int n_seq, nx, ny, max_ratio;
+  long long total_slow, total_fast;
+  const int *ratio, *n_slow;
+  const double *F, *Q, *H, *R, *m0, *P0;
+  const double *y;
+} srtm_batch;
+
+/* Filtering p(x_{k,i} | y_{1:k}): slow IMKF by the parallel scan (Eq. 25-27)
+ * and fast-rate filtering per interval (Eq. 17, Remark 1).                     */
+int srtm_filter(const srtm_problem *p, srtm_precision prec, const srtm_output *filt,
+                srtm_stream_t stream);
+
+/* Smoothing p(x_{k,i} | y_{1:N}) (Eq. 21, 29-30).  `filt` (may be NULL)
+ * additionally receives the filtering results computed on the way.            */
+int srtm_smoother(const srtm_problem *p, srtm_precision prec, const srtm_output *smooth,
+                  const srtm_output *filt, srtm_stream_t stream);
+
+/* Ragged-batch forms: every sequence of the batch in the same launches.       */
+int srtm_filter_batch(const srtm_batch *b, srtm_precision prec, const srtm_output *filt,
+                      srtm_stream_t stream);
+int srtm_smoother_batch(const srtm_batch *b, srtm_precision prec, const srtm_output *smooth,
+                        const srtm_output *filt, srtm_stream_t stream);
+
+/* srtm_smoother with HOST buffers (pageable or pinned) for every input and
+ * output.  Copies the inputs to a library-owned device staging area, runs the
+ * device path, copies the results back and synchronizes the stream; returns
+ * the final status (as srtm_status).                                          */
+int srtm_smoother_host(const srtm_problem *host_p, srtm_precision prec,
+                       const srtm_output *host_smooth, srtm_stream_t stream);
+
+/* Synchronizes `stream`, then returns and clears the device-side error latch of
+ * the current GPU: SRTM_OK, SRTM_ERR_TIMEOUT, SRTM_ERR_SINGULAR or SRTM_ERR_META. */
+int srtm_status(srtm_stream_t stream);
+
+/* Copies a NUL-terminated description of the last host-side error of this
+ * thread into buf (at most len bytes).  Returns the length of the message.    */
+int srtm_last_error_detail(char *buf, int len);
+
+/* Frees the cached device workspace and staging buffers of every GPU.        */
+int srtm_release(void);
+
+/* Tuning of the launch shapes (elements per lane group, groups per block,
+ * fast steps per recovery chunk) for one (nx, precision).  Zero values keep
+ * the built-in choice.  Returns SRTM_ERR_ARG for out-of-range values.        */
+typedef struct {
+  int scan_groups;      /* lane groups per scan block: a power of two such that
+                           groups x lanes-per-group (1, 4, 16 or 32 by nx) is
+                           32..256                                              */
+  int scan_elems;       /* elements per lane group per tile (1..64)            */
+  int recover_threads;  /* recovery block size (32..1024, multiple of 32)      */
+  int recover_chunk;    /* target fast steps per recovery chunk (32..65536)    */
+} srtm_tuning;
+int srtm_set_tuning(int nx, srtm_precision prec, const srtm_tuning *t);
+int srtm_get_tuning(int nx, srtm_precision prec, srtm_tuning *t);
+
+/* Launch count of the device path for one call (for reporting). */
+int srtm_launches_per_call(int smoothing);
+
+/* Stage timing.  While enabled, every call records CUDA events on its stream
+ * around each of its launches.  srtm_stage_times() waits for the last timed
+ * call of the current GPU and writes up to n durations in milliseconds, in
+ * launch order: metadata, model constants, filter scan, interval setup,
+ * smoother scan (0 for a filter call), fast-rate recovery.                   */
+int srtm_set_stage_timing(int enable);
+int srtm_stage_times(float *ms, int n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SRTM_H */

@@ -1,0 +1,270 @@
+"""ctypes binding of ``libsrtm.so`` (see include/srtm.h).
+
+Argument marshalling only: every step of the filter/smoother runs in the
+library's CUDA kernels.  Tensors are torch CUDA float64 tensors (row-major,
+contiguous); PyTorch provides device memory and streams.  There is no CPU
+fallback: if the library is missing, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import c_int, c_longlong, c_void_p
+
+from . import build as _build
+
+PRECISION = {"fp64": 0, "mixed": 1, "fp32": 2}
+ERRORS = {0: "SRTM_OK", -1: "SRTM_ERR_ARG", -3: "SRTM_ERR_SINGULAR", -4: "SRTM_ERR_TIMEOUT",
+          -5: "SRTM_ERR_CUDA", -6: "SRTM_ERR_UNSUPPORTED", -7: "SRTM_ERR_META"}
+OUTPUT_KEYS = ("fast_mean", "fast_cov", "slow_mean", "slow_cov")
+
+# every entry point declared in include/srtm.h
+SYMBOLS = ("srtm_filter", "srtm_smoother", "srtm_filter_batch", "srtm_smoother_batch",
+           "srtm_smoother_host", "srtm_status", "srtm_last_error_detail", "srtm_release",
+           "srtm_set_tuning", "srtm_get_tuning", "srtm_launches_per_call", "srtm_set_stage_timing",
+           "srtm_stage_times")
+STAGES = ("metadata", "constants", "filter_scan", "interval_setup", "smoother_scan", "recovery")
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("nx", c_int), ("ny", c_int), ("ratio", c_int), ("n_slow", c_int),
+                ("F", c_void_p), ("Q", c_void_p), ("H", c_void_p), ("R", c_void_p),
+                ("m0", c_void_p), ("P0", c_void_p), ("y", c_void_p)]
+
+
+class Output(ctypes.Structure):
+    _fields_ = [(k, c_void_p) for k in OUTPUT_KEYS]
+
+
+class Batch(ctypes.Structure):
+    _fields_ = [("n_seq", c_int), ("nx", c_int), ("ny", c_int), ("max_ratio", c_int),
+                ("total_slow", c_longlong), ("total_fast", c_longlong),
+                ("ratio", c_void_p), ("n_slow", c_void_p),
+                ("F", c_void_p), ("Q", c_void_p), ("H", c_void_p), ("R", c_void_p),
+                ("m0", c_void_p), ("P0", c_void_p), ("y", c_void_p)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("scan_groups", c_int), ("scan_elems", c_int), ("recover_threads", c_int),
+                ("recover_chunk", c_int)]
+
+
+class SRTMError(RuntimeError):
+    def __init__(self, code: int, detail: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {detail}")
+        self.code = code
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libsrtm.so (built by ``paper_2410_00627_gb300.build.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = lib_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_2410_00627_gb300.build.build() "
+                           "(there is no CPU fallback)")
+    lib = ctypes.CDLL(path)
+    P, O, B, T = ctypes.POINTER(Problem), ctypes.POINTER(Output), ctypes.POINTER(Batch), ctypes.POINTER(Tuning)
+    sig = {
+        "srtm_filter": [P, c_int, O, c_void_p],
+        "srtm_smoother": [P, c_int, O, O, c_void_p],
+        "srtm_filter_batch": [B, c_int, O, c_void_p],
+        "srtm_smoother_batch": [B, c_int, O, O, c_void_p],
+        "srtm_smoother_host": [P, c_int, O, c_void_p],
+        "srtm_status": [c_void_p],
+        "srtm_last_error_detail": [ctypes.c_char_p, c_int],
+        "srtm_release": [],
+        "srtm_set_tuning": [c_int, c_int, T],
+        "srtm_get_tuning": [c_int, c_int, T],
+        "srtm_launches_per_call": [c_int],
+        "srtm_set_stage_timing": [c_int],
+        "srtm_stage_times": [ctypes.POINTER(ctypes.c_float), c_int],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = c_int
+    _lib = lib
+    return lib
+
+
+def last_error_detail() -> str:
+    buf = ctypes.create_string_buffer(512)
+    load().srtm_last_error_detail(buf, 512)
+    return buf.value.decode(errors="replace")
+
+
+def _check(rc: int) -> None:
+    if rc != 0:
+        raise SRTMError(rc, last_error_detail())
+
+
+def _stream_handle(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return c_void_p(s.cuda_stream)
+
+
+def _dev_tensor(t, name, shape):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError(f"{name} must be a contiguous CUDA float64 tensor")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return c_void_p(t.data_ptr())
+
+
+def _alloc_outputs(keys, device, rows_fast, rows_slow, nx, out=None):
+    import torch
+    res = {}
+    shapes = {"fast_mean": (rows_fast, nx), "fast_cov": (rows_fast, nx, nx),
+              "slow_mean": (rows_slow, nx), "slow_cov": (rows_slow, nx, nx)}
+    for k in keys:
+        if k not in shapes:
+            raise ValueError(f"unknown output {k}")
+        t = None if out is None else out.get(k)
+        if t is None:
+            t = torch.empty(shapes[k], dtype=torch.float64, device=device)
+        _dev_tensor(t, k, shapes[k])
+        res[k] = t
+    o = Output(*[c_void_p(res[k].data_ptr()) if k in res else None for k in OUTPUT_KEYS])
+    return res, o
+
+
+def _problem(F, Q, H, R, m0, P0, y, ratio):
+    nx, ny = F.shape[0], H.shape[0]
+    n_slow = y.shape[0]
+    return Problem(nx, ny, int(ratio), n_slow, _dev_tensor(F, "F", (nx, nx)), _dev_tensor(Q, "Q", (nx, nx)),
+                   _dev_tensor(H, "H", (ny, nx)), _dev_tensor(R, "R", (ny, ny)), _dev_tensor(m0, "m0", (nx,)),
+                   _dev_tensor(P0, "P0", (nx, nx)), _dev_tensor(y, "y", (n_slow, ny)))
+
+
+def smoother(F, Q, H, R, m0, P0, y, ratio, precision="fp64", outputs=OUTPUT_KEYS, filtered=(),
+             stream=None, out=None, out_filtered=None):
+    """p(x_{k,i} | y_{1:N}) for one sequence.  Returns (smoothed, filtered) dicts
+    of CUDA tensors keyed by fast_mean / fast_cov / slow_mean / slow_cov."""
+    prob = _problem(F, Q, H, R, m0, P0, y, ratio)
+    rows_fast, rows_slow = prob.n_slow * prob.ratio, prob.n_slow
+    sm, so = _alloc_outputs(outputs, y.device, rows_fast, rows_slow, prob.nx, out)
+    fi, fo = _alloc_outputs(filtered, y.device, rows_fast, rows_slow, prob.nx, out_filtered)
+    rc = load().srtm_smoother(ctypes.byref(prob), PRECISION[precision], ctypes.byref(so),
+                              ctypes.byref(fo) if filtered else None, _stream_handle(stream))
+    _check(rc)
+    return sm, fi
+
+
+def filter(F, Q, H, R, m0, P0, y, ratio, precision="fp64", outputs=OUTPUT_KEYS, stream=None, out=None):  # noqa: A001
+    """p(x_{k,i} | y_{1:k}) for one sequence."""
+    prob = _problem(F, Q, H, R, m0, P0, y, ratio)
+    res, o = _alloc_outputs(outputs, y.device, prob.n_slow * prob.ratio, prob.n_slow, prob.nx, out)
+    _check(load().srtm_filter(ctypes.byref(prob), PRECISION[precision], ctypes.byref(o), _stream_handle(stream)))
+    return res
+
+
+def make_batch(F, Q, H, R, m0, P0, y, ratio, n_slow, max_ratio, total_slow, total_fast):
+    """Batch descriptor over packed CUDA tensors: F (S,nx,nx), Q, H (S,ny,nx), R, m0 (S,nx),
+    P0, y (total_slow, ny) and CUDA int32 tensors ratio (S,), n_slow (S,)."""
+    import torch
+    S, nx, ny = F.shape[0], F.shape[1], H.shape[1]
+    for t, nm in ((ratio, "ratio"), (n_slow, "n_slow")):
+        if not (t.is_cuda and t.dtype == torch.int32 and t.is_contiguous() and tuple(t.shape) == (S,)):
+            raise TypeError(f"{nm} must be a contiguous CUDA int32 tensor of shape ({S},)")
+    return Batch(S, nx, ny, int(max_ratio), int(total_slow), int(total_fast),
+                 c_void_p(ratio.data_ptr()), c_void_p(n_slow.data_ptr()),
+                 _dev_tensor(F, "F", (S, nx, nx)), _dev_tensor(Q, "Q", (S, nx, nx)),
+                 _dev_tensor(H, "H", (S, ny, nx)), _dev_tensor(R, "R", (S, ny, ny)),
+                 _dev_tensor(m0, "m0", (S, nx)), _dev_tensor(P0, "P0", (S, nx, nx)),
+                 _dev_tensor(y, "y", (int(total_slow), ny)))
+
+
+def smoother_batch(batch: Batch, precision="fp64", outputs=OUTPUT_KEYS, filtered=(), stream=None,
+                   device=None, out=None, out_filtered=None):
+    """Ragged batch: every sequence of ``batch`` in one set of launches."""
+    import torch
+    device = device or torch.device("cuda", torch.cuda.current_device())
+    sm, so = _alloc_outputs(outputs, device, batch.total_fast, batch.total_slow, batch.nx, out)
+    fi, fo = _alloc_outputs(filtered, device, batch.total_fast, batch.total_slow, batch.nx, out_filtered)
+    _check(load().srtm_smoother_batch(ctypes.byref(batch), PRECISION[precision], ctypes.byref(so),
+                                      ctypes.byref(fo) if filtered else None, _stream_handle(stream)))
+    return sm, fi
+
+
+def filter_batch(batch: Batch, precision="fp64", outputs=OUTPUT_KEYS, stream=None, device=None, out=None):
+    import torch
+    device = device or torch.device("cuda", torch.cuda.current_device())
+    res, o = _alloc_outputs(outputs, device, batch.total_fast, batch.total_slow, batch.nx, out)
+    _check(load().srtm_filter_batch(ctypes.byref(batch), PRECISION[precision], ctypes.byref(o),
+                                    _stream_handle(stream)))
+    return res
+
+
+def smoother_host(F, Q, H, R, m0, P0, y, ratio, precision="fp64", out=None, stream=None):
+    """Host-buffer entry point: numpy float64 inputs/outputs (pinned or pageable
+    memory); the library copies to the GPU, runs the smoother, copies back and
+    synchronizes.  ``out`` may hold preallocated (e.g. pinned) output arrays."""
+    import numpy as np
+
+    def host(a, name, shape):
+        if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous):
+            raise TypeError(f"{name} must be a C-contiguous float64 numpy array")
+        if tuple(a.shape) != tuple(shape):
+            raise ValueError(f"{name} has shape {a.shape}, expected {shape}")
+        return c_void_p(a.ctypes.data)
+
+    nx, ny, N = F.shape[0], H.shape[0], y.shape[0]
+    prob = Problem(nx, ny, int(ratio), N, host(F, "F", (nx, nx)), host(Q, "Q", (nx, nx)), host(H, "H", (ny, nx)),
+                   host(R, "R", (ny, ny)), host(m0, "m0", (nx,)), host(P0, "P0", (nx, nx)), host(y, "y", (N, ny)))
+    shapes = {"fast_mean": (N * ratio, nx), "fast_cov": (N * ratio, nx, nx), "slow_mean": (N, nx),
+              "slow_cov": (N, nx, nx)}
+    res = {}
+    for k, s in shapes.items():
+        a = None if out is None else out.get(k)
+        res[k] = np.empty(s) if a is None else a
+        host(res[k], k, s)
+    o = Output(*[c_void_p(res[k].ctypes.data) for k in OUTPUT_KEYS])
+    s = c_void_p(0) if stream is None else c_void_p(stream.cuda_stream)
+    _check(load().srtm_smoother_host(ctypes.byref(prob), PRECISION[precision], ctypes.byref(o), s))
+    return res
+
+
+def status(stream=None) -> None:
+    """Synchronize the stream and raise if the device latched an error."""
+    _check(load().srtm_status(_stream_handle(stream)))
+
+
+def set_tuning(nx: int, precision: str, scan_groups=0, scan_elems=0, recover_threads=0, recover_chunk=0):
+    _check(load().srtm_set_tuning(nx, PRECISION[precision],
+                                  ctypes.byref(Tuning(scan_groups, scan_elems, recover_threads, recover_chunk))))
+
+
+def get_tuning(nx: int, precision: str) -> dict:
+    t = Tuning()
+    _check(load().srtm_get_tuning(nx, PRECISION[precision], ctypes.byref(t)))
+    return {k: getattr(t, k) for k, _ in Tuning._fields_}
+
+
+def launches_per_call(smoothing: bool = True) -> int:
+    return load().srtm_launches_per_call(1 if smoothing else 0)
+
+
+def set_stage_timing(enable: bool) -> None:
+    _check(load().srtm_set_stage_timing(1 if enable else 0))
+
+
+def stage_times() -> dict:
+    """Durations (ms) of each launch of the last timed call on this GPU."""
+    buf = (ctypes.c_float * len(STAGES))()
+    _check(load().srtm_stage_times(buf, len(STAGES)))
+    return dict(zip(STAGES, list(buf)))
+
+
+def release() -> None:
+    load().srtm_release()

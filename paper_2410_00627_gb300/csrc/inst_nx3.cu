@@ -1,0 +1,4 @@
+// Instantiates the device path for nx = 3 (one translation unit per state
+// size so that the units compile in parallel).
+#include "kernels.cuh"
+SRTM_INSTANTIATE(3)

@@ -1,0 +1,1100 @@
+// kernels.cuh -- templated device path of the SRTM filter/smoother for one
+// state size NX: the two associative scans (Eq. 27 and Eq. 30), the
+// per-interval setup (fast-filter blocks and smoother elements, Eq. 17, 29)
+// and the fast-rate recovery (Eq. 17, 21).  Instantiated per NX in
+// inst_nx*.cu so that the translation units compile in parallel.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "grp.cuh"
+#include "srtm_internal.cuh"
+
+namespace srtm {
+
+__host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) / 16 * 16; }
+
+// ===========================================================================
+// scan operators
+// ===========================================================================
+
+// Forward scan of the parallel IMKF (Sec. IV): elements a_k of Eq. (25)-(26),
+// operator Eq. (27).  Scan position p is the slow step k (0-based).
+template <int NX, class T_, class TS_>
+struct FilterOp {
+  using T = T_;
+  using TS = TS_;
+  using L = FL<NX>;
+  static constexpr int G = GroupSize<NX>::value;
+  static constexpr int ES = L::SIZE;
+  static constexpr int SCR = 4 * NX * NX + 2 * NX;
+  static constexpr int SCRS = 2 * NX * NX;
+  static constexpr int TICKET = 0;
+
+  __device__ static bool combine(const Grp<G>& g, T* o, const T* left, const T* right, T* sc, TS* scs,
+                                 bool prefix) {
+    return g_filter_combine<NX, G, T, TS>(g, o, left, right, sc, scs, prefix);
+  }
+  __device__ static void identity(const Grp<G>& g, T* x) {  // (I, 0, 0, 0, 0)
+    for (int e = g.lane; e < ES; e += G) x[e] = (e < NX * NX && e / NX == e % NX) ? T(1) : T(0);
+  }
+  // a_1 = (0, m^f_{1,l}, P^f_{1,l}, 0, 0);  a_k = (F, K y_k, D, C_bar^T R_x^-1 y_k, J), k > 1
+  __device__ static void load(const Grp<G>& g, T* x, const Ctx& c, int s, long long p, int /*N*/) {
+    constexpr int NN = NX * NX;
+    const double* md = c.model + (long long)s * c.ml.stride;
+    if (p == 0) {
+      for (int e = g.lane; e < ES; e += G) {
+        double v = 0.0;
+        if (e >= L::d && e < L::d + NX) v = md[c.ml.m1 + (e - L::d)];
+        else if (e >= L::D && e < L::D + NN) v = md[c.ml.P1 + (e - L::D)];
+        x[e] = (T)v;
+      }
+      return;
+    }
+    for (int e = g.lane; e < NN; e += G) {
+      x[L::F + e] = (T)md[c.ml.Fc + e];
+      x[L::D + e] = (T)md[c.ml.Dc + e];
+      x[L::J + e] = (T)md[c.ml.Jc + e];
+    }
+    const int m = c.ny;
+    const double* yk = c.y + (c.meta.off_slow[s] + p) * m;
+    for (int r = g.lane; r < NX; r += G) {
+      double dv = 0.0, ev = 0.0;
+      for (int j = 0; j < m; ++j) {
+        const double yj = yk[j];
+        dv = fma(md[c.ml.K + r * m + j], yj, dv);
+        ev = fma(md[c.ml.Cr + r * m + j], yj, ev);
+      }
+      x[L::d + r] = (T)dv;
+      x[L::e + r] = (T)ev;
+    }
+  }
+  // filter result at k: d_k = m^f_{k,l}, D_k = P^f_{k,l}
+  __device__ static void store(const Grp<G>& g, const T* x, const Ctx& c, int s, long long p, int /*N*/) {
+    constexpr int NN = NX * NX;
+    T* out = (T*)c.fout + (c.meta.off_slow[s] + p) * (NX + NN);
+    for (int e = g.lane; e < NX + NN; e += G) out[e] = x[L::d + e];  // d then D are contiguous
+  }
+  __device__ static unsigned char* tile_state(const Ctx& c, long long t) { return c.ftile + t * c.ftile_stride; }
+  __device__ static const long long* tile_off(const Ctx& c) { return c.meta.tile_off_f; }
+  __device__ static long long total_tiles(const Ctx& c) { return c.ctr->total_tiles_f; }
+  __device__ static int tile_elems(const Ctx& c) { return c.tile_f; }
+};
+
+// Reverse scan of the parallel IMS (Sec. IV): elements of Eq. (29) built by
+// the interval-setup kernel, operator Eq. (30).  Scan position p is slow step
+// k = N-1-p, so the scan-order combine left (x) right is right (x) left in
+// the paper's order.
+template <int NX, class T_>
+struct SmootherOp {
+  using T = T_;
+  using TS = T_;
+  using L = SL<NX>;
+  static constexpr int G = GroupSize<NX>::value;
+  static constexpr int ES = L::SIZE;
+  static constexpr int SCR = NX * NX;
+  static constexpr int SCRS = 0;
+  static constexpr int TICKET = 1;
+
+  __device__ static bool combine(const Grp<G>& g, T* o, const T* left, const T* right, T* sc, TS*, bool prefix) {
+    g_smoother_combine<NX, G, T>(g, o, right, left, sc, prefix);
+    return true;
+  }
+  __device__ static void identity(const Grp<G>& g, T* x) {  // (I, 0, 0)
+    for (int e = g.lane; e < ES; e += G) x[e] = (e < NX * NX && e / NX == e % NX) ? T(1) : T(0);
+  }
+  __device__ static void load(const Grp<G>& g, T* x, const Ctx& c, int s, long long p, int N) {
+    const T* src = (const T*)c.selem + (c.meta.off_slow[s] + (N - 1 - p)) * ES;
+    for (int e = g.lane; e < ES; e += G) x[e] = src[e];
+  }
+  // smoothed first state of interval k: g = m^s_{k,1}, S = P^s_{k,1}
+  __device__ static void store(const Grp<G>& g, const T* x, const Ctx& c, int s, long long p, int N) {
+    constexpr int NN = NX * NX;
+    T* out = (T*)c.sout + (c.meta.off_slow[s] + (N - 1 - p)) * (NX + NN);
+    for (int e = g.lane; e < NX + NN; e += G) out[e] = x[L::g + e];  // g then S are contiguous
+  }
+  __device__ static unsigned char* tile_state(const Ctx& c, long long t) { return c.stile + t * c.stile_stride; }
+  __device__ static const long long* tile_off(const Ctx& c) { return c.meta.tile_off_s; }
+  __device__ static long long total_tiles(const Ctx& c) { return c.ctr->total_tiles_s; }
+  __device__ static int tile_elems(const Ctx& c) { return c.tile_s; }
+};
+
+// ===========================================================================
+// scan skeleton: persistent blocks take tiles in ticket order; per tile
+//   1. each lane group folds E consecutive elements,
+//   2. Kogge-Stone scan of the group aggregates in shared memory,
+//   3. group 0 resolves the tile prefix by decoupled look-back over the
+//      preceding tiles of the same sequence (aggregate / inclusive-prefix
+//      flags tagged with the call's epoch),
+//   4. each group re-walks its elements from its exclusive prefix and writes
+//      the scan results.
+// Tickets are taken in increasing order, so every tile waited on belongs to a
+// block that is already running and never waits on a later tile: the
+// look-back cannot deadlock.  Its waits are still bounded (SPIN_LIMIT).
+// ===========================================================================
+template <class Op>
+struct ScanSmem {
+  using T = typename Op::T;
+  using TS = typename Op::TS;
+  __host__ __device__ static size_t group_bytes() {
+    return align16((3 * Op::ES + Op::SCR) * sizeof(T)) + align16((Op::SCRS > 0 ? Op::SCRS : 1) * sizeof(TS));
+  }
+  __host__ __device__ static size_t bytes(int NG) {
+    return NG * group_bytes() + 2 * align16((size_t)NG * Op::ES * sizeof(T)) + align16(Op::ES * sizeof(T)) + 16;
+  }
+  __host__ __device__ static size_t payload_bytes() { return align16(Op::ES * sizeof(T)); }
+  __host__ __device__ static size_t tile_state_bytes() { return 16 + 2 * payload_bytes(); }
+};
+
+template <class Op>
+__device__ __forceinline__ void publish(const Grp<Op::G>& g, unsigned char* ts, const typename Op::T* x, int slot,
+                                        unsigned status, unsigned long long epoch) {
+  using T = typename Op::T;
+  T* dst = (T*)(ts + 16 + slot * ScanSmem<Op>::payload_bytes());
+  for (int e = g.lane; e < Op::ES; e += Op::G) __stcg(dst + e, x[e]);
+  __threadfence();
+  g.sync();
+  if (g.lane == 0) st_release_u64((unsigned long long*)ts, ((epoch & 0xffffffffull) << 32) | status);
+}
+
+// status of tile state ts in this call: 1 aggregate, 2 inclusive prefix, 0 = wait bound hit
+template <int G>
+__device__ __forceinline__ unsigned wait_status(const Grp<G>& g, const unsigned char* ts, unsigned long long epoch) {
+  unsigned st = 0;
+  if (g.lane == 0) {
+    unsigned ns = 32;
+    for (long long it = 0; it < SPIN_LIMIT; ++it) {
+      const unsigned long long v = ld_acquire_u64((const unsigned long long*)ts);
+      if ((v >> 32) == (epoch & 0xffffffffull) && (v & 3ull)) { st = (unsigned)(v & 3ull); break; }
+      __nanosleep(ns);
+      if (ns < 2048) ns <<= 1;
+    }
+  }
+  st = __shfl_sync(g.mask, st, (threadIdx.x & 31) & ~(G - 1));
+  g.sync();
+  return st;
+}
+
+template <class Op>
+__device__ void lookback(const Grp<Op::G>& g, const Ctx& c, unsigned long long epoch, long long tile_id,
+                         long long t_in_seq, const typename Op::T* agg, typename Op::T* excl, typename Op::T* b0,
+                         typename Op::T* b1, typename Op::T* b2, typename Op::T* sc, typename Op::TS* scs) {
+  using T = typename Op::T;
+  unsigned char* ts = Op::tile_state(c, tile_id);
+  if (t_in_seq == 0) {
+    Op::identity(g, excl);
+    publish<Op>(g, ts, agg, 1, 2u, epoch);
+    g.sync();
+    return;
+  }
+  publish<Op>(g, ts, agg, 0, 1u, epoch);
+  T* acc = b0;
+  T* pay = b1;
+  T* tmp = b2;
+  Op::identity(g, acc);
+  g.sync();
+  bool ok = true;
+  for (long long j = tile_id - 1;; --j) {
+    const unsigned char* tj = Op::tile_state(c, j);
+    const unsigned st = wait_status<Op::G>(g, tj, epoch);
+    if (st == 0) {
+      if (g.lane == 0) raise_err(c.ctr, DEVERR_TIMEOUT);
+      break;
+    }
+    const T* src = (const T*)(tj + 16 + (st == 2u ? 1 : 0) * ScanSmem<Op>::payload_bytes());
+    for (int e = g.lane; e < Op::ES; e += Op::G) pay[e] = __ldcg(src + e);
+    g.sync();
+    ok &= Op::combine(g, tmp, pay, acc, sc, scs, false);
+    T* t = acc; acc = tmp; tmp = t;
+    if (st == 2u) break;
+  }
+  for (int e = g.lane; e < Op::ES; e += Op::G) excl[e] = acc[e];
+  g.sync();
+  ok &= Op::combine(g, tmp, excl, agg, sc, scs, false);
+  publish<Op>(g, ts, tmp, 1, 2u, epoch);
+  if (!ok && g.lane == 0) raise_err(c.ctr, DEVERR_SINGULAR);
+}
+
+template <class Op>
+__global__ void __launch_bounds__(256) scan_kernel(Ctx c, int NG, int E) {
+  using T = typename Op::T;
+  using TS = typename Op::TS;
+  constexpr int G = Op::G, ES = Op::ES;
+  extern __shared__ __align__(16) unsigned char smem[];
+  if (!c.ctr->call_ok) return;  // metadata rejected for this call
+  const int gid = threadIdx.x / G;
+  const Grp<G> g;
+  const size_t gb = ScanSmem<Op>::group_bytes();
+  unsigned char* gbase = smem + gid * gb;
+  T* b0 = (T*)gbase;
+  T* b1 = b0 + ES;
+  T* b2 = b1 + ES;
+  T* sc = b2 + ES;
+  TS* scs = (TS*)(gbase + align16((3 * ES + Op::SCR) * sizeof(T)));
+  T* ksA = (T*)(smem + NG * gb);
+  T* ksB = (T*)((unsigned char*)ksA + align16((size_t)NG * ES * sizeof(T)));
+  T* excl = (T*)((unsigned char*)ksB + align16((size_t)NG * ES * sizeof(T)));
+  long long* s_tile = (long long*)((unsigned char*)excl + align16(ES * sizeof(T)));
+
+  const unsigned long long epoch = c.ctr->epoch;
+  const long long total = Op::total_tiles(c);
+  const long long* toff = Op::tile_off(c);
+  const int tile_elems = Op::tile_elems(c);
+  bool ok = true;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) *s_tile = (long long)atomicAdd(&c.ctr->ticket[Op::TICKET], 1u);
+    __syncthreads();
+    const long long tile_id = *s_tile;
+    if (tile_id >= total) break;
+    const int s = find_segment(toff, c.n_seq, tile_id);
+    const long long t = tile_id - toff[s];
+    const int N = c.meta.nslow[s];
+    const long long p0 = t * tile_elems + (long long)gid * E;
+    const int cnt = (int)max(0LL, min((long long)E, (long long)N - p0));
+
+    // 1. fold the group's elements
+    T* cur = b0;
+    T* el = b1;
+    T* tmp = b2;
+    if (cnt == 0) {
+      Op::identity(g, cur);
+    } else {
+      Op::load(g, cur, c, s, p0, N);
+      for (int e = 1; e < cnt; ++e) {
+        g.sync();
+        Op::load(g, el, c, s, p0 + e, N);
+        g.sync();
+        ok &= Op::combine(g, tmp, cur, el, sc, scs, false);
+        T* x = cur; cur = tmp; tmp = x;
+      }
+    }
+    g.sync();
+    for (int e = g.lane; e < ES; e += G) ksA[gid * ES + e] = cur[e];
+    __syncthreads();
+    // 2. inclusive scan over the groups of the tile
+    T* src = ksA;
+    T* dst = ksB;
+    for (int d = 1; d < NG; d <<= 1) {
+      if (gid >= d) {
+        ok &= Op::combine(g, dst + gid * ES, src + (gid - d) * ES, src + gid * ES, sc, scs, false);
+      } else {
+        for (int e = g.lane; e < ES; e += G) dst[gid * ES + e] = src[gid * ES + e];
+      }
+      __syncthreads();
+      T* x = src; src = dst; dst = x;
+    }
+    // 3. tile prefix
+    if (gid == 0) lookback<Op>(g, c, epoch, tile_id, t, src + (NG - 1) * ES, excl, b0, b1, b2, sc, scs);
+    __syncthreads();
+    // 4. results from the exclusive prefixes
+    if (cnt > 0) {
+      T* st = b0;
+      T* nx = b2;
+      if (gid == 0) {
+        for (int e = g.lane; e < ES; e += G) st[e] = excl[e];
+      } else {
+        ok &= Op::combine(g, st, excl, src + (gid - 1) * ES, sc, scs, true);
+      }
+      g.sync();
+      for (int e = 0; e < cnt; ++e) {
+        Op::load(g, b1, c, s, p0 + e, N);
+        g.sync();
+        ok &= Op::combine(g, nx, st, b1, sc, scs, true);
+        T* x = st; st = nx; nx = x;
+        Op::store(g, st, c, s, p0 + e, N);
+        g.sync();
+      }
+    }
+  }
+  if (!ok && g.lane == 0) raise_err(c.ctr, DEVERR_SINGULAR);
+}
+
+// ===========================================================================
+// thread-local small-matrix helpers (interval setup, recovery)
+// ===========================================================================
+
+// inverse of a symmetric positive definite N x N matrix by Cholesky
+// (a = L L^T, a^-1 = L^-T L^-1).  Returns false if a pivot is not positive.
+template <int N, class T>
+__device__ __forceinline__ bool spd_inverse(const T (&a)[N][N], T (&inv)[N][N]) {
+  T Lm[N][N];
+  bool ok = true;
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    T d = a[j][j];
+#pragma unroll
+    for (int k = 0; k < j; ++k) d = fma(-Lm[j][k], Lm[j][k], d);
+    if (!(d > T(0)) || !isfinite(d)) { ok = false; d = T(1); }
+    const T ljj = sqrt(d), rinv = T(1) / ljj;
+    Lm[j][j] = ljj;
+#pragma unroll
+    for (int i = j + 1; i < N; ++i) {
+      T s = a[i][j];
+#pragma unroll
+      for (int k = 0; k < j; ++k) s = fma(-Lm[i][k], Lm[j][k], s);
+      Lm[i][j] = s * rinv;
+    }
+#pragma unroll
+    for (int i = 0; i < j; ++i) Lm[i][j] = T(0);
+  }
+  T Li[N][N];  // L^-1, lower triangular
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    Li[i][i] = T(1) / Lm[i][i];
+#pragma unroll
+    for (int j = 0; j < i; ++j) {
+      T s = T(0);
+#pragma unroll
+      for (int k = j; k < i; ++k) s = fma(Lm[i][k], Li[k][j], s);
+      Li[i][j] = -s * Li[i][i];
+    }
+#pragma unroll
+    for (int j = i + 1; j < N; ++j) Li[i][j] = T(0);
+  }
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+#pragma unroll
+    for (int j = i; j < N; ++j) {
+      T s = T(0);
+#pragma unroll
+      for (int k = j; k < N; ++k) s = fma(Li[k][i], Li[k][j], s);
+      inv[i][j] = s;
+      inv[j][i] = s;
+    }
+  return ok;
+}
+
+// ===========================================================================
+// interval setup: one thread per slow interval k (paper index k+1) computes,
+// from p(x_{k-1,l}|y_{1:k-1}) and y_k, the fast-filter blocks it needs
+// (Eq. 17 on the blocks of Remark 2) and the parallel IMS element (Eq. 29):
+//   X = P C_bar^T, S_y = C_bar X + R_x, kap = S_y^-1 (y - C_bar m),
+//   U_i = A^i X + V_i H^T   (U_i = sum_j P^-_{ij} H^T),
+//   m^f_i = A^i m + U_i kap,  P^f_{ij} = A^i P A^{jT} + Cov(e_i,e_j) - U_i S_y^-1 U_j^T,
+//   P^-_{k+1,1} = A P^f_{ll} A^T + Q,  Z = A^T (P^-_{k+1,1})^-1,
+//   E_k = P^f_{1l} Z,  g_k = m^f_1 - E_k A m^f_l,  S_k = P^f_{11} - E_k A (P^f_{1l})^T
+// (last interval: E = 0, g = m^f_1, S = P^f_{11}).  The record keeps what the
+// recovery reuses.  Runs in TR (float64 except in the float32 mode).
+// ===========================================================================
+template <int NX, class T, class TR>
+__global__ void __launch_bounds__(128) interval_setup_kernel(Ctx c) {
+  constexpr int NN = NX * NX;
+  using RL = Rec<NX>;
+  using SLy = SL<NX>;
+  const long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (!c.ctr->call_ok || gi >= c.total_slow) return;
+  const int s = find_segment(c.meta.off_slow, c.n_seq, gi);
+  const long long k = gi - c.meta.off_slow[s];
+  const int N = c.meta.nslow[s], l = c.meta.ratio[s], m = c.ny;
+  const double* md = c.model + (long long)s * c.ml.stride;
+  const double* Apow = md + c.ml.Apow;
+  const double* Al = Apow + (long long)l * NN;
+  const double* A1 = Apow + NN;
+  const double* Cb = md + c.ml.Cb;
+  const double* Rx = md + c.ml.Rx;
+
+  TR P[NX][NX], mv[NX];
+  if (k == 0) {
+#pragma unroll
+    for (int r = 0; r < NX; ++r) {
+      mv[r] = (TR)c.m0[(long long)s * NX + r];
+#pragma unroll
+      for (int q = 0; q < NX; ++q) P[r][q] = (TR)c.P0[(long long)s * NN + r * NX + q];
+    }
+  } else {
+    const T* f = (const T*)c.fout + (gi - 1) * (NX + NN);
+#pragma unroll
+    for (int r = 0; r < NX; ++r) {
+      mv[r] = (TR)f[r];
+#pragma unroll
+      for (int q = 0; q < NX; ++q) P[r][q] = (TR)f[NX + r * NX + q];
+    }
+  }
+  // X = P C_bar^T (columns >= m are zero)
+  TR X[NX][MY];
+#pragma unroll
+  for (int r = 0; r < NX; ++r)
+#pragma unroll
+    for (int j = 0; j < MY; ++j) {
+      TR s2 = TR(0);
+      if (j < m) {
+#pragma unroll
+        for (int q = 0; q < NX; ++q) s2 = fma(P[r][q], (TR)Cb[j * NX + q], s2);
+      }
+      X[r][j] = s2;
+    }
+  // S_y = C_bar X + R_x, padded with the identity
+  TR Sy[MY][MY], Si[MY][MY];
+#pragma unroll
+  for (int i = 0; i < MY; ++i)
+#pragma unroll
+    for (int j = 0; j < MY; ++j) {
+      TR v = (i == j) ? TR(1) : TR(0);
+      if (i < m && j < m) {
+        v = (TR)Rx[i * m + j];
+#pragma unroll
+        for (int q = 0; q < NX; ++q) v = fma((TR)Cb[i * NX + q], X[q][j], v);
+      }
+      Sy[i][j] = v;
+    }
+#pragma unroll
+  for (int i = 0; i < MY; ++i)
+#pragma unroll
+    for (int j = i + 1; j < MY; ++j) { const TR v = TR(0.5) * (Sy[i][j] + Sy[j][i]); Sy[i][j] = v; Sy[j][i] = v; }
+  bool ok = spd_inverse<MY, TR>(Sy, Si);
+  TR kap[MY];
+  {
+    TR e[MY];
+    const double* yk = c.y + gi * m;
+#pragma unroll
+    for (int j = 0; j < MY; ++j) {
+      TR v = TR(0);
+      if (j < m) {
+        v = (TR)yk[j];
+#pragma unroll
+        for (int q = 0; q < NX; ++q) v = fma(-(TR)Cb[j * NX + q], mv[q], v);
+      }
+      e[j] = v;
+    }
+#pragma unroll
+    for (int i = 0; i < MY; ++i) {
+      TR v = TR(0);
+#pragma unroll
+      for (int j = 0; j < MY; ++j) v = fma(Si[i][j], e[j], v);
+      kap[i] = v;
+    }
+  }
+  // U_l = A^l X + V_l H^T ; SUl = S_y^-1 U_l^T ; m^f_l
+  TR Ul[NX][MY], SUl[MY][NX], ml[NX];
+  {
+    const double* VHl = md + c.ml.VH + (long long)(l - 1) * NX * m;
+#pragma unroll
+    for (int r = 0; r < NX; ++r)
+#pragma unroll
+      for (int j = 0; j < MY; ++j) {
+        TR v = TR(0);
+        if (j < m) {
+          v = (TR)VHl[r * m + j];
+#pragma unroll
+          for (int q = 0; q < NX; ++q) v = fma((TR)Al[r * NX + q], X[q][j], v);
+        }
+        Ul[r][j] = v;
+      }
+#pragma unroll
+    for (int i = 0; i < MY; ++i)
+#pragma unroll
+      for (int r = 0; r < NX; ++r) {
+        TR v = TR(0);
+#pragma unroll
+        for (int j = 0; j < MY; ++j) v = fma(Si[i][j], Ul[r][j], v);
+        SUl[i][r] = v;
+      }
+#pragma unroll
+    for (int r = 0; r < NX; ++r) {
+      TR v = TR(0);
+#pragma unroll
+      for (int q = 0; q < NX; ++q) v = fma((TR)Al[r * NX + q], mv[q], v);
+#pragma unroll
+      for (int j = 0; j < MY; ++j) v = fma(Ul[r][j], kap[j], v);
+      ml[r] = v;
+    }
+  }
+  // Pl = P A^{lT};  P^f_{ll} = A^l Pl + Qc_l - U_l SUl
+  TR Pl[NX][NX], Pm[NX][NX];
+#pragma unroll
+  for (int r = 0; r < NX; ++r)
+#pragma unroll
+    for (int q = 0; q < NX; ++q) {
+      TR v = TR(0);
+#pragma unroll
+      for (int t = 0; t < NX; ++t) v = fma(P[r][t], (TR)Al[q * NX + t], v);
+      Pl[r][q] = v;
+    }
+  {
+    TR Pll[NX][NX];
+    const double* Qcl = md + c.ml.Qc + (long long)(l - 1) * NN;
+#pragma unroll
+    for (int r = 0; r < NX; ++r)
+#pragma unroll
+      for (int q = r; q < NX; ++q) {
+        TR v = (TR)Qcl[r * NX + q];
+#pragma unroll
+        for (int t = 0; t < NX; ++t) v = fma((TR)Al[r * NX + t], Pl[t][q], v);
+#pragma unroll
+        for (int j = 0; j < MY; ++j) v = fma(-Ul[r][j], SUl[j][q], v);
+        Pll[r][q] = v;
+        Pll[q][r] = v;
+      }
+    // P^-_{k+1,1} = A P^f_{ll} A^T + Q
+    TR AP[NX][NX];
+#pragma unroll
+    for (int r = 0; r < NX; ++r)
+#pragma unroll
+      for (int q = 0; q < NX; ++q) {
+        TR v = TR(0);
+#pragma unroll
+        for (int t = 0; t < NX; ++t) v = fma((TR)A1[r * NX + t], Pll[t][q], v);
+        AP[r][q] = v;
+      }
+    const double* Qm = md + c.ml.Q;
+#pragma unroll
+    for (int r = 0; r < NX; ++r)
+#pragma unroll
+      for (int q = r; q < NX; ++q) {
+        TR v = (TR)(0.5 * (Qm[r * NX + q] + Qm[q * NX + r]));
+#pragma unroll
+        for (int t = 0; t < NX; ++t) v = fma(AP[r][t], (TR)A1[q * NX + t], v);
+        Pm[r][q] = v;
+        Pm[q][r] = v;
+      }
+  }
+  TR Z[NX][NX];
+  {
+    TR Pmi[NX][NX];
+    ok &= spd_inverse<NX, TR>(Pm, Pmi);
+#pragma unroll
+    for (int r = 0; r < NX; ++r)
+#pragma unroll
+      for (int q = 0; q < NX; ++q) {
+        TR v = TR(0);
+#pragma unroll
+        for (int t = 0; t < NX; ++t) v = fma((TR)A1[t * NX + r], Pmi[t][q], v);
+        Z[r][q] = v;
+      }
+  }
+  // record
+  {
+    TR* rc = (TR*)c.rec + gi * RL::SIZE;
+#pragma unroll
+    for (int r = 0; r < NX; ++r) {
+      rc[RL::mv + r] = mv[r];
+      rc[RL::ml + r] = ml[r];
+#pragma unroll
+      for (int q = 0; q < NX; ++q) {
+        rc[RL::P + r * NX + q] = P[r][q];
+        rc[RL::Pl + r * NX + q] = Pl[r][q];
+        rc[RL::Z + r * NX + q] = Z[r][q];
+        rc[RL::Pm + r * NX + q] = Pm[r][q];
+      }
+#pragma unroll
+      for (int j = 0; j < MY; ++j) {
+        rc[RL::X + r * MY + j] = X[r][j];
+        rc[RL::SUl + j * NX + r] = SUl[j][r];
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < MY; ++i) {
+      rc[RL::kap + i] = kap[i];
+#pragma unroll
+      for (int j = 0; j < MY; ++j) rc[RL::Si + i * MY + j] = Si[i][j];
+    }
+  }
+  if (c.smoothing) {
+    // first fast state of the interval: U_1, m^f_1, P^f_{11}, P^f_{1l}
+    const double* VH1 = md + c.ml.VH;
+    const double* Qc1 = md + c.ml.Qc;
+    const double* Ql1 = md + c.ml.Ql;
+    TR U1[NX][MY], m1[NX];
+#pragma unroll
+    for (int r = 0; r < NX; ++r)
+#pragma unroll
+      for (int j = 0; j < MY; ++j) {
+        TR v = TR(0);
+        if (j < m) {
+          v = (TR)VH1[r * m + j];
+#pragma unroll
+          for (int q = 0; q < NX; ++q) v = fma((TR)A1[r * NX + q], X[q][j], v);
+        }
+        U1[r][j] = v;
+      }
+#pragma unroll
+    for (int r = 0; r < NX; ++r) {
+      TR v = TR(0);
+#pragma unroll
+      for (int q = 0; q < NX; ++q) v = fma((TR)A1[r * NX + q], mv[q], v);
+#pragma unroll
+      for (int j = 0; j < MY; ++j) v = fma(U1[r][j], kap[j], v);
+      m1[r] = v;
+    }
+    TR P11[NX][NX], P1l[NX][NX];
+    {
+      TR US[NX][MY], AP[NX][NX];
+#pragma unroll
+      for (int r = 0; r < NX; ++r)
+#pragma unroll
+        for (int j = 0; j < MY; ++j) {
+          TR v = TR(0);
+#pragma unroll
+          for (int jj = 0; jj < MY; ++jj) v = fma(U1[r][jj], Si[jj][j], v);
+          US[r][j] = v;
+        }
+#pragma unroll
+      for (int r = 0; r < NX; ++r)
+#pragma unroll
+        for (int q = 0; q < NX; ++q) {
+          TR v = TR(0);
+#pragma unroll
+          for (int t = 0; t < NX; ++t) v = fma((TR)A1[r * NX + t], P[t][q], v);
+          AP[r][q] = v;
+        }
+#pragma unroll
+      for (int r = 0; r < NX; ++r)
+#pragma unroll
+        for (int q = r; q < NX; ++q) {
+          TR v = (TR)(0.5 * (Qc1[r * NX + q] + Qc1[q * NX + r]));
+#pragma unroll
+          for (int t = 0; t < NX; ++t) v = fma(AP[r][t], (TR)A1[q * NX + t], v);
+#pragma unroll
+          for (int j = 0; j < MY; ++j) v = fma(-US[r][j], U1[q][j], v);
+          P11[r][q] = v;
+          P11[q][r] = v;
+        }
+#pragma unroll
+      for (int r = 0; r < NX; ++r)
+#pragma unroll
+        for (int q = 0; q < NX; ++q) {
+          TR v = (TR)Ql1[r * NX + q];
+#pragma unroll
+          for (int t = 0; t < NX; ++t) v = fma((TR)A1[r * NX + t], Pl[t][q], v);
+#pragma unroll
+          for (int j = 0; j < MY; ++j) v = fma(-U1[r][j], SUl[j][q], v);
+          P1l[r][q] = v;
+        }
+    }
+    T* se = (T*)c.selem + gi * SLy::SIZE;
+    if (k < N - 1) {
+      TR E[NX][NX], Aml[NX], AP1[NX][NX];
+#pragma unroll
+      for (int r = 0; r < NX; ++r)
+#pragma unroll
+        for (int q = 0; q < NX; ++q) {
+          TR v = TR(0);
+#pragma unroll
+          for (int t = 0; t < NX; ++t) v = fma(P1l[r][t], Z[t][q], v);
+          E[r][q] = v;
+        }
+#pragma unroll
+      for (int r = 0; r < NX; ++r) {
+        TR v = TR(0);
+#pragma unroll
+        for (int q = 0; q < NX; ++q) v = fma((TR)A1[r * NX + q], ml[q], v);
+        Aml[r] = v;
+      }
+      // A (P^f_{1l})^T
+#pragma unroll
+      for (int r = 0; r < NX; ++r)
+#pragma unroll
+        for (int q = 0; q < NX; ++q) {
+          TR v = TR(0);
+#pragma unroll
+          for (int t = 0; t < NX; ++t) v = fma((TR)A1[r * NX + t], P1l[q][t], v);
+          AP1[r][q] = v;
+        }
+#pragma unroll
+      for (int r = 0; r < NX; ++r) {
+        TR v = m1[r];
+#pragma unroll
+        for (int q = 0; q < NX; ++q) v = fma(-E[r][q], Aml[q], v);
+        se[SLy::g + r] = (T)v;
+#pragma unroll
+        for (int q = 0; q < NX; ++q) se[SLy::E + r * NX + q] = (T)E[r][q];
+      }
+      // S_k = P^f_{11} - E_k A (P^f_{1l})^T, symmetrised in TR
+      TR S[NX][NX];
+#pragma unroll
+      for (int r = 0; r < NX; ++r)
+#pragma unroll
+        for (int q = 0; q < NX; ++q) {
+          TR v = P11[r][q];
+#pragma unroll
+          for (int t = 0; t < NX; ++t) v = fma(-E[r][t], AP1[t][q], v);
+          S[r][q] = v;
+        }
+#pragma unroll
+      for (int r = 0; r < NX; ++r)
+#pragma unroll
+        for (int q = r; q < NX; ++q) {
+          const T v = (T)(TR(0.5) * (S[r][q] + S[q][r]));
+          se[SLy::S + r * NX + q] = v;
+          se[SLy::S + q * NX + r] = v;
+        }
+    } else {
+#pragma unroll
+      for (int r = 0; r < NX; ++r) {
+        se[SLy::g + r] = (T)m1[r];
+#pragma unroll
+        for (int q = 0; q < NX; ++q) {
+          se[SLy::E + r * NX + q] = T(0);
+          se[SLy::S + r * NX + q] = (T)P11[r][q];
+        }
+      }
+    }
+  }
+  if (!ok) raise_err(c.ctr, DEVERR_SINGULAR);
+}
+
+// ===========================================================================
+// fast-rate recovery (Remarks 1 and 3): one thread per fast step (k, i).
+// Per slow interval (shared by its l fast steps, computed once per block):
+//   dm = m^s_{k+1,1} - A m^f_{k,l},  dP = P^s_{k+1,1} - P^-_{k+1,1},
+//   om = Z dm,  Om = Z dP Z^T          (so that G_i dm = P^f_{il} om and
+//                                       G_i dP G_i^T = P^f_{il} Om P^f_{il}^T)
+// Per fast step, with the record of the interval:
+//   U_i   = A^i X + V_i H^T
+//   m^f_i = A^i m + U_i kap
+//   P^f_ii = A^i P A^{iT} + Qc_i - (U_i S_y^-1) U_i^T
+//   P^f_il = A^i (P A^{lT}) + Cov(e_i,e_l) - U_i (S_y^-1 U_l^T)
+//   m^s_i = m^f_i + P^f_il om,   P^s_ii = P^f_ii + (P^f_il Om) P^f_il^T
+// which is Eq. (17) and Eq. (21) with G_{k,i} = P^f_{k,i,l} A^T (P^-_{k+1,1})^-1
+// grouped so that no n x n product is repeated per fast step.  The last
+// interval is smoothed = filtered (E_N = 0).  Covariances are formed on the
+// upper triangle and mirrored (exactly symmetric).
+// ===========================================================================
+template <int NX, class T, class TR>
+__global__ void __launch_bounds__(256) recover_kernel(Ctx c) {
+  constexpr int NN = NX * NX, NT = NX * (NX + 1) / 2;
+  using RL = Rec<NX>;
+  extern __shared__ __align__(16) unsigned char rsm[];
+  __shared__ long long s_chunk;
+  if (!c.ctr->call_ok) return;
+  const long long total = c.ctr->total_chunks;
+  const int m = c.ny;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_chunk = (long long)atomicAdd(&c.ctr->ticket[2], 1u);
+    __syncthreads();
+    const long long ch = s_chunk;
+    if (ch >= total) break;
+    const int s = find_segment(c.meta.chunk_off, c.n_seq, ch);
+    const int C = c.meta.chunk_C[s], l = c.meta.ratio[s], N = c.meta.nslow[s];
+    const long long k0 = (ch - c.meta.chunk_off[s]) * C;
+    const int nk = (int)min((long long)C, (long long)N - k0);
+    const long long off_slow = c.meta.off_slow[s], off_fast = c.meta.off_fast[s];
+    const double* md = c.model + (long long)s * c.ml.stride;
+    const double* A1 = md + c.ml.Apow + NN;
+    TR* Om = (TR*)rsm;                   // [C][NN]
+    TR* om = Om + (size_t)C * NN;        // [C][NX]
+    const bool smooth = c.smoothing != 0;
+    if (smooth) {
+      for (int j = threadIdx.x; j < nk; j += blockDim.x) {
+        const long long k = k0 + j;
+        if (k >= N - 1) continue;
+        const TR* rc = (const TR*)c.rec + (off_slow + k) * RL::SIZE;
+        const T* so = (const T*)c.sout + (off_slow + k + 1) * (NX + NN);
+        TR Z[NX][NX], dm[NX], ZdP[NX][NX];
+#pragma unroll
+        for (int r = 0; r < NX; ++r)
+#pragma unroll
+          for (int q = 0; q < NX; ++q) Z[r][q] = rc[RL::Z + r * NX + q];
+#pragma unroll
+        for (int r = 0; r < NX; ++r) {
+          TR v = (TR)so[r];
+#pragma unroll
+          for (int q = 0; q < NX; ++q) v = fma(-(TR)A1[r * NX + q], rc[RL::ml + q], v);
+          dm[r] = v;
+        }
+#pragma unroll
+        for (int r = 0; r < NX; ++r) {
+          TR v = TR(0);
+#pragma unroll
+          for (int q = 0; q < NX; ++q) v = fma(Z[r][q], dm[q], v);
+          om[j * NX + r] = v;
+        }
+#pragma unroll
+        for (int r = 0; r < NX; ++r)
+#pragma unroll
+          for (int q = 0; q < NX; ++q) {
+            TR v = TR(0);
+#pragma unroll
+            for (int t = 0; t < NX; ++t) v = fma(Z[r][t], (TR)so[NX + t * NX + q] - rc[RL::Pm + t * NX + q], v);
+            ZdP[r][q] = v;
+          }
+#pragma unroll
+        for (int r = 0; r < NX; ++r)
+#pragma unroll
+          for (int q = r; q < NX; ++q) {
+            TR v = TR(0);
+#pragma unroll
+            for (int t = 0; t < NX; ++t) v = fma(ZdP[r][t], Z[q][t], v);
+            Om[j * NN + r * NX + q] = v;
+            Om[j * NN + q * NX + r] = v;
+          }
+      }
+    }
+    __syncthreads();
+    const int nf = nk * l;
+    for (int f = threadIdx.x; f < nf; f += blockDim.x) {
+      const int j = f / l;
+      const int i = f - j * l + 1;
+      const long long k = k0 + j;
+      const TR* rc = (const TR*)c.rec + (off_slow + k) * RL::SIZE;
+      const double* Ai = md + c.ml.Apow + (long long)i * NN;
+      const double* VHi = md + c.ml.VH + (long long)(i - 1) * NX * m;
+      const double* Qci = md + c.ml.Qc + (long long)(i - 1) * NN;
+      const double* Qli = md + c.ml.Ql + (long long)(i - 1) * NN;
+      TR a[NX][NX];
+#pragma unroll
+      for (int r = 0; r < NX; ++r)
+#pragma unroll
+        for (int q = 0; q < NX; ++q) a[r][q] = (TR)Ai[r * NX + q];
+      // U_i = A^i X + V_i H^T
+      TR U[NX][MY];
+#pragma unroll
+      for (int r = 0; r < NX; ++r)
+#pragma unroll
+        for (int jj = 0; jj < MY; ++jj) {
+          TR v = TR(0);
+          if (jj < m) {
+            v = (TR)VHi[r * m + jj];
+#pragma unroll
+            for (int q = 0; q < NX; ++q) v = fma(a[r][q], rc[RL::X + q * MY + jj], v);
+          }
+          U[r][jj] = v;
+        }
+      // m^f_i = A^i m + U_i kap
+      TR mf[NX];
+#pragma unroll
+      for (int r = 0; r < NX; ++r) {
+        TR v = TR(0);
+#pragma unroll
+        for (int q = 0; q < NX; ++q) v = fma(a[r][q], rc[RL::mv + q], v);
+#pragma unroll
+        for (int jj = 0; jj < MY; ++jj)
+          if (jj < m) v = fma(U[r][jj], rc[RL::kap + jj], v);
+        mf[r] = v;
+      }
+      const bool smooth_k = smooth && (k < N - 1);
+      // P^f_il = A^i Pl + Cov(e_i,e_l) - U_i SUl
+      TR Pfl[NX][NX];
+      if (smooth_k) {
+#pragma unroll
+        for (int r = 0; r < NX; ++r)
+#pragma unroll
+          for (int q = 0; q < NX; ++q) {
+            TR v = (TR)Qli[r * NX + q];
+#pragma unroll
+            for (int t = 0; t < NX; ++t) v = fma(a[r][t], rc[RL::Pl + t * NX + q], v);
+#pragma unroll
+            for (int jj = 0; jj < MY; ++jj)
+              if (jj < m) v = fma(-U[r][jj], rc[RL::SUl + jj * NX + q], v);
+            Pfl[r][q] = v;
+          }
+      }
+      // P^f_ii (upper triangle)
+      TR Pf[NT];
+      {
+        TR US[NX][MY], AP[NX][NX];
+#pragma unroll
+        for (int r = 0; r < NX; ++r)
+#pragma unroll
+          for (int jj = 0; jj < MY; ++jj) {
+            TR v = TR(0);
+            if (jj < m) {
+#pragma unroll
+              for (int j2 = 0; j2 < MY; ++j2)
+                if (j2 < m) v = fma(U[r][j2], rc[RL::Si + j2 * MY + jj], v);
+            }
+            US[r][jj] = v;
+          }
+#pragma unroll
+        for (int r = 0; r < NX; ++r)
+#pragma unroll
+          for (int q = 0; q < NX; ++q) {
+            TR v = TR(0);
+#pragma unroll
+            for (int t = 0; t < NX; ++t) v = fma(a[r][t], rc[RL::P + t * NX + q], v);
+            AP[r][q] = v;
+          }
+        int u = 0;
+#pragma unroll
+        for (int r = 0; r < NX; ++r)
+#pragma unroll
+          for (int q = r; q < NX; ++q) {
+            TR v = (TR)Qci[r * NX + q];
+#pragma unroll
+            for (int t = 0; t < NX; ++t) v = fma(AP[r][t], a[q][t], v);
+#pragma unroll
+            for (int jj = 0; jj < MY; ++jj)
+              if (jj < m) v = fma(-US[r][jj], U[q][jj], v);
+            Pf[u++] = v;
+          }
+      }
+      const long long fi = off_fast + k * l + (i - 1);
+      double* fm_out = smooth ? c.ffast_mean : c.fast_mean;
+      double* fc_out = smooth ? c.ffast_cov : c.fast_cov;
+      double* sm_out = smooth ? c.fslow_mean : c.slow_mean;
+      double* sc_out = smooth ? c.fslow_cov : c.slow_cov;
+      auto store_state = [&](double* mo, double* co, double* smo, double* sco, const TR* mvv, const TR* Pu) {
+        if (mo) {
+#pragma unroll
+          for (int r = 0; r < NX; ++r) mo[fi * NX + r] = (double)mvv[r];
+        }
+        if (co) {
+          double* dst = co + fi * NN;
+          int uu = 0;
+#pragma unroll
+          for (int r = 0; r < NX; ++r)
+#pragma unroll
+            for (int q = r; q < NX; ++q) {
+              const double v = (double)Pu[uu++];
+              dst[r * NX + q] = v;
+              dst[q * NX + r] = v;
+            }
+        }
+        if (i == l) {
+          const long long si = off_slow + k;
+          if (smo) {
+#pragma unroll
+            for (int r = 0; r < NX; ++r) smo[si * NX + r] = (double)mvv[r];
+          }
+          if (sco) {
+            double* dst = sco + si * NN;
+            int uu = 0;
+#pragma unroll
+            for (int r = 0; r < NX; ++r)
+#pragma unroll
+              for (int q = r; q < NX; ++q) {
+                const double v = (double)Pu[uu++];
+                dst[r * NX + q] = v;
+                dst[q * NX + r] = v;
+              }
+          }
+        }
+      };
+      // filtered outputs (the call's outputs for a filter, the optional extras for a smoother)
+      store_state(fm_out, fc_out, sm_out, sc_out, mf, Pf);
+      if (!smooth) continue;
+      if (smooth_k) {
+        const TR* Omj = Om + (size_t)j * NN;
+        const TR* omj = om + (size_t)j * NX;
+        TR T1[NX][NX];
+#pragma unroll
+        for (int r = 0; r < NX; ++r)
+#pragma unroll
+          for (int q = 0; q < NX; ++q) {
+            TR v = TR(0);
+#pragma unroll
+            for (int t = 0; t < NX; ++t) v = fma(Pfl[r][t], Omj[t * NX + q], v);
+            T1[r][q] = v;
+          }
+        int u = 0;
+#pragma unroll
+        for (int r = 0; r < NX; ++r)
+#pragma unroll
+          for (int q = r; q < NX; ++q) {
+            TR v = Pf[u];
+#pragma unroll
+            for (int t = 0; t < NX; ++t) v = fma(T1[r][t], Pfl[q][t], v);
+            Pf[u++] = v;
+          }
+#pragma unroll
+        for (int r = 0; r < NX; ++r) {
+          TR v = mf[r];
+#pragma unroll
+          for (int t = 0; t < NX; ++t) v = fma(Pfl[r][t], omj[t], v);
+          mf[r] = v;
+        }
+      }
+      store_state(c.fast_mean, c.fast_cov, c.slow_mean, c.slow_cov, mf, Pf);
+    }
+  }
+}
+
+// ===========================================================================
+// host-side launch of the templated stages
+// ===========================================================================
+template <class Op>
+inline void set_smem_attr(const void* fn, size_t bytes) {
+  if (bytes > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <int NX, class T, class TS, class TR>
+int query_shapes_t(int scan_groups, int scan_elems, int recover_threads, int recover_chunk, int sm_count,
+                   long long total_slow, int n_seq, Shapes* sh) {
+  using FOp = FilterOp<NX, T, TS>;
+  using SOp = SmootherOp<NX, T>;
+  constexpr int G = FOp::G;
+  const int NG = scan_groups;
+  const int threads = NG * G;
+  if (threads < 32 || threads > 256) return SRTM_ERR_ARG;
+  sh->scan_groups_f = sh->scan_groups_s = NG;
+  sh->scan_elems_f = sh->scan_elems_s = scan_elems;
+  sh->smem_f = ScanSmem<FOp>::bytes(NG);
+  sh->smem_s = ScanSmem<SOp>::bytes(NG);
+  set_smem_attr<FOp>((const void*)scan_kernel<FOp>, sh->smem_f);
+  set_smem_attr<SOp>((const void*)scan_kernel<SOp>, sh->smem_s);
+  int nb = 0;
+  const long long tiles = total_slow / ((long long)NG * scan_elems) + n_seq;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, scan_kernel<FOp>, threads, sh->smem_f);
+  sh->grid_f = (int)std::max(1LL, std::min((long long)std::max(nb, 1) * sm_count, tiles));
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, scan_kernel<SOp>, threads, sh->smem_s);
+  sh->grid_s = (int)std::max(1LL, std::min((long long)std::max(nb, 1) * sm_count, tiles));
+  sh->grid_setup = (int)((total_slow + 127) / 128);
+  sh->recover_threads = recover_threads;
+  sh->recover_chunk = recover_chunk;
+  // shared memory per recovery block: C_max intervals of (Om, om)
+  const size_t per_int = (size_t)(NX * NX + NX) * sizeof(TR);
+  int cmax = (int)std::min<size_t>(32768 / per_int, 4096);
+  if (cmax < 1) cmax = 1;
+  sh->smem_r = (size_t)cmax * per_int;
+  set_smem_attr<void>((const void*)recover_kernel<NX, T, TR>, sh->smem_r);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, recover_kernel<NX, T, TR>, recover_threads, sh->smem_r);
+  sh->grid_r = std::max(1, std::max(nb, 1) * sm_count);
+  if (cudaGetLastError() != cudaSuccess) return SRTM_ERR_CUDA;
+  return SRTM_OK;
+}
+
+template <int NX>
+int query_shapes(srtm_precision prec, int scan_groups, int scan_elems, int recover_threads, int recover_chunk,
+                 int sm_count, long long total_slow, int n_seq, Shapes* sh) {
+  switch (prec) {
+    case SRTM_FP64:
+      return query_shapes_t<NX, double, double, double>(scan_groups, scan_elems, recover_threads, recover_chunk,
+                                                         sm_count, total_slow, n_seq, sh);
+    case SRTM_MIXED:
+      return query_shapes_t<NX, float, double, double>(scan_groups, scan_elems, recover_threads, recover_chunk,
+                                                        sm_count, total_slow, n_seq, sh);
+    case SRTM_FP32:
+      return query_shapes_t<NX, float, float, float>(scan_groups, scan_elems, recover_threads, recover_chunk,
+                                                      sm_count, total_slow, n_seq, sh);
+  }
+  return SRTM_ERR_ARG;
+}
+
+// ev (optional): four events recorded after the filter scan, the interval
+// setup, the smoother scan and the recovery.
+template <int NX, class T, class TS, class TR>
+int launch_t(const Ctx& c, const Shapes& sh, cudaStream_t st, cudaEvent_t* ev) {
+  using FOp = FilterOp<NX, T, TS>;
+  using SOp = SmootherOp<NX, T>;
+  constexpr int G = FOp::G;
+  scan_kernel<FOp><<<sh.grid_f, sh.scan_groups_f * G, sh.smem_f, st>>>(c, sh.scan_groups_f, sh.scan_elems_f);
+  if (ev) cudaEventRecord(ev[0], st);
+  interval_setup_kernel<NX, T, TR><<<sh.grid_setup, 128, 0, st>>>(c);
+  if (ev) cudaEventRecord(ev[1], st);
+  if (c.smoothing)
+    scan_kernel<SOp><<<sh.grid_s, sh.scan_groups_s * G, sh.smem_s, st>>>(c, sh.scan_groups_s, sh.scan_elems_s);
+  if (ev) cudaEventRecord(ev[2], st);
+  recover_kernel<NX, T, TR><<<sh.grid_r, sh.recover_threads, sh.smem_r, st>>>(c);
+  if (ev) cudaEventRecord(ev[3], st);
+  return cudaGetLastError() == cudaSuccess ? SRTM_OK : SRTM_ERR_CUDA;
+}
+
+template <int NX>
+int launch_device_path(const Ctx& c, srtm_precision prec, const Shapes& sh, cudaStream_t st, cudaEvent_t* ev) {
+  switch (prec) {
+    case SRTM_FP64: return launch_t<NX, double, double, double>(c, sh, st, ev);
+    case SRTM_MIXED: return launch_t<NX, float, double, double>(c, sh, st, ev);
+    case SRTM_FP32: return launch_t<NX, float, float, float>(c, sh, st, ev);
+  }
+  return SRTM_ERR_ARG;
+}
+
+}  // namespace srtm
+
+#define SRTM_INSTANTIATE(NXV)                                                                                \
+  template int srtm::launch_device_path<NXV>(const srtm::Ctx&, srtm_precision, const srtm::Shapes&,          \
+                                             cudaStream_t, cudaEvent_t*);                                    \
+  template int srtm::query_shapes<NXV>(srtm_precision, int, int, int, int, int, long long, int, srtm::Shapes*);

@@ -1,0 +1,483 @@
+// srtm_api.cu -- the C-ABI entry points declared in include/srtm.h: argument
+// validation, the cached per-GPU workspace, launch of the device path, the
+// host-buffer entry point and the device error latch.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "srtm_internal.cuh"
+
+namespace srtm {
+int launch_meta_and_precompute(const Ctx& c, cudaStream_t st, cudaEvent_t* ev);
+}
+using namespace srtm;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+constexpr int NSTAGE = 6;  // metadata, constants, filter scan, interval setup, smoother scan, recovery
+struct DevState {
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  void* stage = nullptr;
+  size_t stage_bytes = 0;
+  int sms = 0;
+  cudaEvent_t ev[NSTAGE + 1] = {};  // stage-timing events (created on first use)
+  cudaStream_t ev_stream = nullptr;
+  bool ev_valid = false;
+  // placement of the scan tile-state regions used by the previous call
+  size_t last_ftile = 0, last_ftile_bytes = 0, last_stile = 0, last_stile_bytes = 0;
+  long long last_fstride = 0, last_sstride = 0;
+};
+constexpr int MAXDEV = 64;
+std::mutex g_mu;
+DevState g_dev[MAXDEV];
+srtm_tuning g_tune[MAXNX + 1][3];  // zero fields = built-in choice
+bool g_timing = false;
+
+int group_size(int nx) { return nx == 1 ? 1 : (nx <= 2 ? 4 : (nx <= 4 ? 16 : 32)); }
+
+srtm_tuning effective_tuning(int nx, srtm_precision prec) {
+  srtm_tuning t;
+  const int G = group_size(nx);
+  t.scan_groups = std::max(1, 128 / G);
+  t.scan_elems = 4;
+  t.recover_threads = 128;
+  t.recover_chunk = 512;
+  const srtm_tuning& u = g_tune[nx][prec];
+  if (u.scan_groups) t.scan_groups = u.scan_groups;
+  if (u.scan_elems) t.scan_elems = u.scan_elems;
+  if (u.recover_threads) t.recover_threads = u.recover_threads;
+  if (u.recover_chunk) t.recover_chunk = u.recover_chunk;
+  return t;
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+size_t a256(size_t x) { return (x + 255) / 256 * 256; }
+size_t a16(size_t x) { return (x + 15) / 16 * 16; }
+
+struct Layout {
+  size_t ctr, ratio, nslow, chunkC, off_slow, off_fast, tile_f, tile_s, chunk_off, model, ftile, stile, fout, rec,
+      selem, sout, total;
+  long long ftile_stride, stile_stride;
+  ModelLayout ml;
+};
+
+Layout make_layout(int nx, int ny, int max_ratio, int n_seq, long long total_slow, srtm_precision prec, int tile_f,
+                   int tile_s) {
+  Layout L;
+  const size_t sT = prec == SRTM_FP64 ? 8 : 4, sR = prec == SRTM_FP32 ? 4 : 8;
+  const long long nn = (long long)nx * nx;
+  const long long FE = 3 * nn + 2 * nx, SE = 2 * nn + nx;
+  const long long REC = 4 * nn + 2 * nx + 2LL * nx * MY + MY * MY + MY;
+  L.ml = make_model_layout(nx, ny, max_ratio);
+  L.ftile_stride = 16 + 2 * (long long)a16(FE * sT);
+  L.stile_stride = 16 + 2 * (long long)a16(SE * sT);
+  const long long tiles_f = total_slow / tile_f + n_seq, tiles_s = total_slow / tile_s + n_seq;
+  size_t o = 0;
+  auto take = [&](size_t bytes) { const size_t at = a256(o); o = at + bytes; return at; };
+  L.ctr = take(sizeof(Counters));
+  L.ratio = take(sizeof(int) * n_seq);
+  L.nslow = take(sizeof(int) * n_seq);
+  L.chunkC = take(sizeof(int) * n_seq);
+  L.off_slow = take(sizeof(long long) * (n_seq + 1));
+  L.off_fast = take(sizeof(long long) * (n_seq + 1));
+  L.tile_f = take(sizeof(long long) * (n_seq + 1));
+  L.tile_s = take(sizeof(long long) * (n_seq + 1));
+  L.chunk_off = take(sizeof(long long) * (n_seq + 1));
+  L.model = take(sizeof(double) * (size_t)L.ml.stride * n_seq);
+  L.ftile = take((size_t)L.ftile_stride * tiles_f);
+  L.stile = take((size_t)L.stile_stride * tiles_s);
+  L.fout = take(sT * (size_t)(nx + nn) * total_slow);
+  L.rec = take(sR * (size_t)REC * total_slow);
+  L.selem = take(sT * (size_t)SE * total_slow);
+  L.sout = take(sT * (size_t)(nx + nn) * total_slow);
+  L.total = a256(o);
+  return L;
+}
+
+int shapes_for(int nx, srtm_precision prec, const srtm_tuning& t, int sms, long long total_slow, int n_seq,
+               Shapes* sh) {
+#define SRTM_Q(N) \
+  case N: return query_shapes<N>(prec, t.scan_groups, t.scan_elems, t.recover_threads, t.recover_chunk, sms, total_slow, n_seq, sh);
+  switch (nx) {
+    SRTM_Q(1) SRTM_Q(2) SRTM_Q(3) SRTM_Q(4) SRTM_Q(5) SRTM_Q(6) SRTM_Q(7) SRTM_Q(8)
+  }
+#undef SRTM_Q
+  return SRTM_ERR_UNSUPPORTED;
+}
+
+int launch_for(int nx, const Ctx& c, srtm_precision prec, const Shapes& sh, cudaStream_t st, cudaEvent_t* ev) {
+#define SRTM_L(N) \
+  case N: return launch_device_path<N>(c, prec, sh, st, ev);
+  switch (nx) {
+    SRTM_L(1) SRTM_L(2) SRTM_L(3) SRTM_L(4) SRTM_L(5) SRTM_L(6) SRTM_L(7) SRTM_L(8)
+  }
+#undef SRTM_L
+  return SRTM_ERR_UNSUPPORTED;
+}
+
+// Runs the device path for a fully validated context (sizes in `c` set).
+int run(Ctx c, srtm_precision prec, cudaStream_t st) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAXDEV)
+    return fail(SRTM_ERR_CUDA, "no usable CUDA device");
+  std::lock_guard<std::mutex> lk(g_mu);
+  DevState& d = g_dev[dev];
+  if (!d.sms && cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return fail(SRTM_ERR_CUDA, "cudaDeviceGetAttribute failed");
+  const srtm_tuning t = effective_tuning(c.nx, prec);
+  Shapes sh;
+  int rc = shapes_for(c.nx, prec, t, d.sms, c.total_slow, c.n_seq, &sh);
+  if (rc) return fail(rc, "launch shape query failed (%d)", rc);
+  const int tile_f = sh.scan_groups_f * sh.scan_elems_f, tile_s = sh.scan_groups_s * sh.scan_elems_s;
+  const Layout L = make_layout(c.nx, c.ny, c.max_ratio, c.n_seq, c.total_slow, prec, tile_f, tile_s);
+  if (d.ws_bytes < L.total) {
+    if (d.ws) {
+      cudaDeviceSynchronize();
+      cudaFree(d.ws);
+      d.ws = nullptr;
+      d.ws_bytes = 0;
+    }
+    if (cudaMalloc(&d.ws, L.total) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(SRTM_ERR_CUDA, "workspace cudaMalloc of %zu bytes failed", L.total);
+    }
+    if (cudaMemset(d.ws, 0, L.total) != cudaSuccess) return fail(SRTM_ERR_CUDA, "workspace memset failed");
+    d.ws_bytes = L.total;
+    d.last_ftile = d.last_ftile_bytes = d.last_stile = d.last_stile_bytes = 0;
+    d.last_fstride = d.last_sstride = 0;
+  }
+  unsigned char* w = (unsigned char*)d.ws;
+  // The look-back flags carry the call epoch, so flags left by earlier calls
+  // never match.  When the tile-state regions move or change stride, other
+  // data may now sit where flags are read: clear the regions first.
+  const size_t fbytes = L.stile - L.ftile, sbytes = L.fout - L.stile;
+  if (L.ftile != d.last_ftile || fbytes != d.last_ftile_bytes || L.stile != d.last_stile ||
+      sbytes != d.last_stile_bytes || L.ftile_stride != d.last_fstride || L.stile_stride != d.last_sstride) {
+    if (cudaMemsetAsync(w + L.ftile, 0, fbytes + sbytes, st) != cudaSuccess)
+      return fail(SRTM_ERR_CUDA, "tile-state clear failed");
+    d.last_ftile = L.ftile; d.last_ftile_bytes = fbytes; d.last_stile = L.stile; d.last_stile_bytes = sbytes;
+    d.last_fstride = L.ftile_stride; d.last_sstride = L.stile_stride;
+  }
+  c.ctr = (Counters*)(w + L.ctr);
+  c.meta.ratio = (int*)(w + L.ratio);
+  c.meta.nslow = (int*)(w + L.nslow);
+  c.meta.chunk_C = (int*)(w + L.chunkC);
+  c.meta.off_slow = (long long*)(w + L.off_slow);
+  c.meta.off_fast = (long long*)(w + L.off_fast);
+  c.meta.tile_off_f = (long long*)(w + L.tile_f);
+  c.meta.tile_off_s = (long long*)(w + L.tile_s);
+  c.meta.chunk_off = (long long*)(w + L.chunk_off);
+  c.model = (double*)(w + L.model);
+  c.ml = L.ml;
+  c.ftile = w + L.ftile;
+  c.ftile_stride = L.ftile_stride;
+  c.stile = w + L.stile;
+  c.stile_stride = L.stile_stride;
+  c.fout = w + L.fout;
+  c.rec = w + L.rec;
+  c.selem = w + L.selem;
+  c.sout = w + L.sout;
+  c.tile_f = tile_f;
+  c.tile_s = tile_s;
+  c.chunk_fast = sh.recover_chunk;
+  const size_t per_int = (size_t)(c.nx * c.nx + c.nx) * (prec == SRTM_FP32 ? 4 : 8);
+  c.chunk_cmax = (int)std::max<size_t>(1, sh.smem_r / per_int);
+  cudaEvent_t* ev = nullptr;
+  if (g_timing) {
+    if (!d.ev[0])
+      for (int i = 0; i <= NSTAGE; ++i) cudaEventCreate(&d.ev[i]);
+    ev = d.ev;
+    d.ev_stream = st;
+    d.ev_valid = true;
+  }
+  rc = launch_meta_and_precompute(c, st, ev);
+  if (rc) return fail(rc, "launch of the metadata/constants kernels failed: %s", cudaGetErrorString(cudaGetLastError()));
+  rc = launch_for(c.nx, c, prec, sh, st, ev ? ev + 3 : nullptr);
+  if (rc) return fail(rc, "launch of the scan/recovery kernels failed: %s", cudaGetErrorString(cudaGetLastError()));
+  return SRTM_OK;
+}
+
+int check_dims(int nx, int ny) {
+  if (nx < 1 || nx > MAXNX) return fail(SRTM_ERR_UNSUPPORTED, "nx=%d outside 1..%d", nx, MAXNX);
+  if (ny < 1 || ny > MY) return fail(SRTM_ERR_UNSUPPORTED, "ny=%d outside 1..%d", ny, MY);
+  return SRTM_OK;
+}
+
+int check_outputs(const srtm_output* o, const char* what) {
+  if (!o) return SRTM_OK;
+  const double* ps[4] = {o->fast_mean, o->fast_cov, o->slow_mean, o->slow_cov};
+  const char* nm[4] = {"fast_mean", "fast_cov", "slow_mean", "slow_cov"};
+  for (int i = 0; i < 4; ++i)
+    if (ps[i] && !is_device_ptr(ps[i])) return fail(SRTM_ERR_ARG, "%s.%s is not a device pointer", what, nm[i]);
+  return SRTM_OK;
+}
+
+int check_inputs(const double* F, const double* Q, const double* H, const double* R, const double* m0,
+                 const double* P0, const double* y) {
+  const double* ps[7] = {F, Q, H, R, m0, P0, y};
+  const char* nm[7] = {"F", "Q", "H", "R", "m0", "P0", "y"};
+  for (int i = 0; i < 7; ++i) {
+    if (!ps[i]) return fail(SRTM_ERR_ARG, "%s is NULL", nm[i]);
+    if (!is_device_ptr(ps[i])) return fail(SRTM_ERR_ARG, "%s is not a device pointer", nm[i]);
+  }
+  return SRTM_OK;
+}
+
+void set_outputs(Ctx& c, const srtm_output* main, const srtm_output* extra) {
+  c.fast_mean = main ? main->fast_mean : nullptr;
+  c.fast_cov = main ? main->fast_cov : nullptr;
+  c.slow_mean = main ? main->slow_mean : nullptr;
+  c.slow_cov = main ? main->slow_cov : nullptr;
+  c.ffast_mean = extra ? extra->fast_mean : nullptr;
+  c.ffast_cov = extra ? extra->fast_cov : nullptr;
+  c.fslow_mean = extra ? extra->slow_mean : nullptr;
+  c.fslow_cov = extra ? extra->slow_cov : nullptr;
+}
+
+int single(const srtm_problem* p, srtm_precision prec, const srtm_output* out, const srtm_output* extra,
+           int smoothing, srtm_stream_t stream) {
+  if (!p) return fail(SRTM_ERR_ARG, "problem is NULL");
+  if (prec < SRTM_FP64 || prec > SRTM_FP32) return fail(SRTM_ERR_ARG, "unknown precision %d", (int)prec);
+  int rc = check_dims(p->nx, p->ny);
+  if (rc) return rc;
+  if (p->ratio < 1) return fail(SRTM_ERR_ARG, "ratio=%d < 1", p->ratio);
+  if (p->n_slow < 1) return fail(SRTM_ERR_ARG, "n_slow=%d < 1", p->n_slow);
+  if ((rc = check_inputs(p->F, p->Q, p->H, p->R, p->m0, p->P0, p->y))) return rc;
+  if ((rc = check_outputs(out, "output")) || (rc = check_outputs(extra, "filtered output"))) return rc;
+  Ctx c;
+  memset(&c, 0, sizeof c);
+  c.n_seq = 1;
+  c.nx = p->nx;
+  c.ny = p->ny;
+  c.max_ratio = p->ratio;
+  c.smoothing = smoothing;
+  c.uniform_ratio = p->ratio;
+  c.uniform_nslow = p->n_slow;
+  c.total_slow = p->n_slow;
+  c.total_fast = (long long)p->n_slow * p->ratio;
+  c.F = p->F; c.Q = p->Q; c.H = p->H; c.R = p->R; c.m0 = p->m0; c.P0 = p->P0; c.y = p->y;
+  set_outputs(c, out, extra);
+  return run(c, prec, (cudaStream_t)stream);
+}
+
+int batch(const srtm_batch* b, srtm_precision prec, const srtm_output* out, const srtm_output* extra, int smoothing,
+          srtm_stream_t stream) {
+  if (!b) return fail(SRTM_ERR_ARG, "batch is NULL");
+  if (prec < SRTM_FP64 || prec > SRTM_FP32) return fail(SRTM_ERR_ARG, "unknown precision %d", (int)prec);
+  int rc = check_dims(b->nx, b->ny);
+  if (rc) return rc;
+  if (b->n_seq < 1) return fail(SRTM_ERR_ARG, "n_seq=%d < 1", b->n_seq);
+  if (b->max_ratio < 1) return fail(SRTM_ERR_ARG, "max_ratio=%d < 1", b->max_ratio);
+  if (b->total_slow < b->n_seq || b->total_fast < b->total_slow)
+    return fail(SRTM_ERR_ARG, "total_slow=%lld / total_fast=%lld inconsistent with n_seq=%d", b->total_slow,
+                b->total_fast, b->n_seq);
+  if (!is_device_ptr(b->ratio) || !is_device_ptr(b->n_slow))
+    return fail(SRTM_ERR_ARG, "ratio and n_slow must be device int arrays");
+  if ((rc = check_inputs(b->F, b->Q, b->H, b->R, b->m0, b->P0, b->y))) return rc;
+  if ((rc = check_outputs(out, "output")) || (rc = check_outputs(extra, "filtered output"))) return rc;
+  Ctx c;
+  memset(&c, 0, sizeof c);
+  c.n_seq = b->n_seq;
+  c.nx = b->nx;
+  c.ny = b->ny;
+  c.max_ratio = b->max_ratio;
+  c.smoothing = smoothing;
+  c.total_slow = b->total_slow;
+  c.total_fast = b->total_fast;
+  c.in_ratio = b->ratio;
+  c.in_nslow = b->n_slow;
+  c.F = b->F; c.Q = b->Q; c.H = b->H; c.R = b->R; c.m0 = b->m0; c.P0 = b->P0; c.y = b->y;
+  set_outputs(c, out, extra);
+  return run(c, prec, (cudaStream_t)stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+int srtm_filter(const srtm_problem* p, srtm_precision prec, const srtm_output* filt, srtm_stream_t stream) {
+  return single(p, prec, filt, nullptr, 0, stream);
+}
+
+int srtm_smoother(const srtm_problem* p, srtm_precision prec, const srtm_output* smooth, const srtm_output* filt,
+                  srtm_stream_t stream) {
+  return single(p, prec, smooth, filt, 1, stream);
+}
+
+int srtm_filter_batch(const srtm_batch* b, srtm_precision prec, const srtm_output* filt, srtm_stream_t stream) {
+  return batch(b, prec, filt, nullptr, 0, stream);
+}
+
+int srtm_smoother_batch(const srtm_batch* b, srtm_precision prec, const srtm_output* smooth,
+                        const srtm_output* filt, srtm_stream_t stream) {
+  return batch(b, prec, smooth, filt, 1, stream);
+}
+
+int srtm_status(srtm_stream_t stream) {
+  if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess)
+    return fail(SRTM_ERR_CUDA, "stream synchronize failed: %s", cudaGetErrorString(cudaGetLastError()));
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAXDEV) return fail(SRTM_ERR_CUDA, "no device");
+  std::lock_guard<std::mutex> lk(g_mu);
+  DevState& d = g_dev[dev];
+  if (!d.ws) return SRTM_OK;
+  unsigned err = 0;
+  unsigned* perr = (unsigned*)((unsigned char*)d.ws + offsetof(Counters, err));
+  if (cudaMemcpy(&err, perr, sizeof err, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return fail(SRTM_ERR_CUDA, "reading the device error latch failed");
+  if (!err) return SRTM_OK;
+  cudaMemset(perr, 0, sizeof err);
+  if (err & DEVERR_META) return fail(SRTM_ERR_META, "batch metadata disagrees with the declared sizes");
+  if (err & DEVERR_TIMEOUT) return fail(SRTM_ERR_TIMEOUT, "a scan look-back wait exceeded its bound");
+  return fail(SRTM_ERR_SINGULAR, "a solve met a zero, negative or non-finite pivot");
+}
+
+int srtm_smoother_host(const srtm_problem* hp, srtm_precision prec, const srtm_output* hout, srtm_stream_t stream) {
+  if (!hp || !hout) return fail(SRTM_ERR_ARG, "problem and output must not be NULL");
+  int rc = check_dims(hp->nx, hp->ny);
+  if (rc) return rc;
+  if (hp->ratio < 1 || hp->n_slow < 1) return fail(SRTM_ERR_ARG, "ratio and n_slow must be >= 1");
+  const double* in[7] = {hp->F, hp->Q, hp->H, hp->R, hp->m0, hp->P0, hp->y};
+  for (int i = 0; i < 7; ++i)
+    if (!in[i]) return fail(SRTM_ERR_ARG, "input %d is NULL", i);
+  const long long nx = hp->nx, ny = hp->ny, N = hp->n_slow, l = hp->ratio;
+  const size_t in_cnt[7] = {(size_t)(nx * nx), (size_t)(nx * nx), (size_t)(ny * nx), (size_t)(ny * ny),
+                            (size_t)nx, (size_t)(nx * nx), (size_t)(N * ny)};
+  const size_t out_cnt[4] = {(size_t)(N * l * nx), (size_t)(N * l * nx * nx), (size_t)(N * nx), (size_t)(N * nx * nx)};
+  double* hout_p[4] = {hout->fast_mean, hout->fast_cov, hout->slow_mean, hout->slow_cov};
+  size_t off[11], o = 0;
+  for (int i = 0; i < 7; ++i) { off[i] = o; o += a256(in_cnt[i] * sizeof(double)); }
+  for (int i = 0; i < 4; ++i) { off[7 + i] = o; o += hout_p[i] ? a256(out_cnt[i] * sizeof(double)) : 0; }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAXDEV) return fail(SRTM_ERR_CUDA, "no device");
+  unsigned char* stg = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    DevState& d = g_dev[dev];
+    if (d.stage_bytes < o) {
+      if (d.stage) { cudaDeviceSynchronize(); cudaFree(d.stage); d.stage = nullptr; d.stage_bytes = 0; }
+      if (cudaMalloc(&d.stage, o) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SRTM_ERR_CUDA, "staging cudaMalloc of %zu bytes failed", o);
+      }
+      d.stage_bytes = o;
+    }
+    stg = (unsigned char*)d.stage;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  for (int i = 0; i < 7; ++i)
+    if (cudaMemcpyAsync(stg + off[i], in[i], in_cnt[i] * sizeof(double), cudaMemcpyDefault, st) != cudaSuccess)
+      return fail(SRTM_ERR_CUDA, "input copy %d failed", i);
+  srtm_problem dp = *hp;
+  dp.F = (const double*)(stg + off[0]); dp.Q = (const double*)(stg + off[1]);
+  dp.H = (const double*)(stg + off[2]); dp.R = (const double*)(stg + off[3]);
+  dp.m0 = (const double*)(stg + off[4]); dp.P0 = (const double*)(stg + off[5]);
+  dp.y = (const double*)(stg + off[6]);
+  srtm_output dout;
+  double** dsl[4] = {&dout.fast_mean, &dout.fast_cov, &dout.slow_mean, &dout.slow_cov};
+  for (int i = 0; i < 4; ++i) *dsl[i] = hout_p[i] ? (double*)(stg + off[7 + i]) : nullptr;
+  rc = srtm_smoother(&dp, prec, &dout, nullptr, stream);
+  if (rc) return rc;
+  for (int i = 0; i < 4; ++i)
+    if (hout_p[i] &&
+        cudaMemcpyAsync(hout_p[i], *dsl[i], out_cnt[i] * sizeof(double), cudaMemcpyDefault, st) != cudaSuccess)
+      return fail(SRTM_ERR_CUDA, "output copy %d failed", i);
+  return srtm_status(stream);
+}
+
+int srtm_last_error_detail(char* buf, int len) {
+  const int n = (int)strlen(g_err);
+  if (buf && len > 0) {
+    strncpy(buf, g_err, (size_t)len - 1);
+    buf[len - 1] = '\0';
+  }
+  return n;
+}
+
+int srtm_release(void) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  int cur = 0;
+  cudaGetDevice(&cur);
+  for (int d = 0; d < MAXDEV; ++d) {
+    if (!g_dev[d].ws && !g_dev[d].stage) continue;
+    cudaSetDevice(d);
+    cudaDeviceSynchronize();
+    if (g_dev[d].ws) cudaFree(g_dev[d].ws);
+    if (g_dev[d].stage) cudaFree(g_dev[d].stage);
+    for (int i = 0; i <= NSTAGE; ++i)
+      if (g_dev[d].ev[i]) cudaEventDestroy(g_dev[d].ev[i]);
+    g_dev[d] = DevState();
+  }
+  cudaSetDevice(cur);
+  return SRTM_OK;
+}
+
+int srtm_set_tuning(int nx, srtm_precision prec, const srtm_tuning* t) {
+  if (nx < 1 || nx > MAXNX || prec < SRTM_FP64 || prec > SRTM_FP32 || !t) return fail(SRTM_ERR_ARG, "bad tuning key");
+  const int G = group_size(nx);
+  if (t->scan_groups && (t->scan_groups < 1 || t->scan_groups > 256 || (t->scan_groups & (t->scan_groups - 1)) ||
+                         t->scan_groups * G < 32 || t->scan_groups * G > 256))
+    return fail(SRTM_ERR_ARG, "scan_groups=%d invalid for nx=%d", t->scan_groups, nx);
+  if (t->scan_elems && (t->scan_elems < 1 || t->scan_elems > 64)) return fail(SRTM_ERR_ARG, "scan_elems out of range");
+  if (t->recover_threads && (t->recover_threads < 32 || t->recover_threads > 256 || t->recover_threads % 32))
+    return fail(SRTM_ERR_ARG, "recover_threads out of range");
+  if (t->recover_chunk && (t->recover_chunk < 32 || t->recover_chunk > 65536))
+    return fail(SRTM_ERR_ARG, "recover_chunk out of range");
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_tune[nx][prec] = *t;
+  return SRTM_OK;
+}
+
+int srtm_get_tuning(int nx, srtm_precision prec, srtm_tuning* t) {
+  if (nx < 1 || nx > MAXNX || prec < SRTM_FP64 || prec > SRTM_FP32 || !t) return fail(SRTM_ERR_ARG, "bad tuning key");
+  std::lock_guard<std::mutex> lk(g_mu);
+  *t = effective_tuning(nx, prec);
+  return SRTM_OK;
+}
+
+int srtm_launches_per_call(int smoothing) { return smoothing ? 6 : 5; }
+
+int srtm_set_stage_timing(int enable) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_timing = enable != 0;
+  return SRTM_OK;
+}
+
+int srtm_stage_times(float* ms, int n) {
+  int dev = 0;
+  if (!ms || n < 1) return fail(SRTM_ERR_ARG, "ms must hold at least one value");
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAXDEV) return fail(SRTM_ERR_CUDA, "no device");
+  std::lock_guard<std::mutex> lk(g_mu);
+  DevState& d = g_dev[dev];
+  if (!d.ev_valid) return fail(SRTM_ERR_ARG, "no call was timed on this device (srtm_set_stage_timing(1) first)");
+  if (cudaEventSynchronize(d.ev[NSTAGE]) != cudaSuccess) return fail(SRTM_ERR_CUDA, "event synchronize failed");
+  for (int i = 0; i < n && i < NSTAGE; ++i)
+    if (cudaEventElapsedTime(&ms[i], d.ev[i], d.ev[i + 1]) != cudaSuccess) return fail(SRTM_ERR_CUDA, "event timing failed");
+  return SRTM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,189 @@
+// srtm_internal.cuh -- shared definitions of the sm_103a SRTM library:
+// the launch context, device-workspace layouts and memory-ordering helpers.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "srtm.h"
+
+namespace srtm {
+
+constexpr int MAXNX = 8;  // compiled state sizes 1..8
+constexpr int MY = 4;     // measurement sizes 1..4 (padded to 4 in per-interval records)
+
+enum DevErr : unsigned { DEVERR_TIMEOUT = 1u, DEVERR_SINGULAR = 2u, DEVERR_META = 4u };
+
+// Look-back wait bound: polls with exponential __nanosleep back-off capped at
+// 2 us, so the bound is a few seconds of wall time.
+constexpr long long SPIN_LIMIT = 2000000;
+
+// Device-side control block at offset 0 of the workspace.
+struct Counters {
+  unsigned long long epoch;   // bumped once per call by the metadata kernel
+  unsigned int ticket[4];     // tile / chunk tickets: 0 filter scan, 1 smoother scan, 2 recovery
+  unsigned int err;           // DevErr bits, sticky until srtm_status()
+  unsigned int call_ok;       // 1 when this call's metadata passed validation
+  long long total_tiles_f, total_tiles_s, total_chunks;
+};
+
+// Per-sequence metadata (SoA, written by the metadata kernel).
+struct SeqMeta {
+  int* ratio;
+  int* nslow;
+  int* chunk_C;               // slow intervals per recovery chunk
+  long long* off_slow;        // [n_seq+1] row offsets of y / slow outputs
+  long long* off_fast;        // [n_seq+1] row offsets of fast outputs
+  long long* tile_off_f;      // [n_seq+1] filter-scan tile offsets
+  long long* tile_off_s;      // [n_seq+1] smoother-scan tile offsets
+  long long* chunk_off;       // [n_seq+1] recovery chunk offsets
+};
+
+// Per-model constant table (float64), offsets in doubles.  L is the largest
+// ratio of the call; sequence s uses its own l <= L.
+struct ModelLayout {
+  long long Apow;  // (L+1) n^2   A^0..A^L
+  long long VH;    // L n m       V_i H^T,  V_i = Cov(e_i, sum_j e_j)
+  long long Qc;    // L n^2       Qc_i = Cov(e_i) = sum_{r<i} A^r Q A^rT
+  long long Ql;    // L n^2       Cov(e_i, e_l) = Qc_i A^{(l-i)T}
+  long long Ssc;   // L n^2       scratch: S_q = sum_{j<=q} A^j
+  long long Vsc;   // L n^2       scratch: V_i
+  long long Cb;    // m n         C_bar = H sum_{i=1..l} A^i
+  long long Rx;    // m m         M Q~ M^T + R
+  long long Fc;    // n^2         A^l - K C_bar
+  long long Dc;    // n^2         Q_bar - K (G Q~ M^T)^T
+  long long Jc;    // n^2         C_bar^T R_x^-1 C_bar
+  long long K;     // n m         G Q~ M^T R_x^-1
+  long long Cr;    // n m         C_bar^T R_x^-1
+  long long m1;    // n           m^f_{1,l}
+  long long P1;    // n^2         P^f_{1,l}
+  long long Q;     // n^2         copy of Q
+  long long stride;
+};
+
+__host__ __device__ inline ModelLayout make_model_layout(int n, int m, int L) {
+  ModelLayout ml;
+  long long o = 0, nn = (long long)n * n;
+  ml.Apow = o; o += (L + 1) * nn;
+  ml.VH = o;   o += (long long)L * n * m;
+  ml.Qc = o;   o += L * nn;
+  ml.Ql = o;   o += L * nn;
+  ml.Ssc = o;  o += L * nn;
+  ml.Vsc = o;  o += L * nn;
+  ml.Cb = o;   o += (long long)m * n;
+  ml.Rx = o;   o += (long long)m * m;
+  ml.Fc = o;   o += nn;
+  ml.Dc = o;   o += nn;
+  ml.Jc = o;   o += nn;
+  ml.K = o;    o += (long long)n * m;
+  ml.Cr = o;   o += (long long)n * m;
+  ml.m1 = o;   o += n;
+  ml.P1 = o;   o += nn;
+  ml.Q = o;    o += nn;
+  ml.stride = (o + 31) / 32 * 32;
+  return ml;
+}
+
+// Per-interval record written by the interval-setup kernel, read by the
+// recovery (units of TR).  Sizes use the padded measurement dimension MY.
+template <int NX>
+struct Rec {
+  static constexpr int NN = NX * NX;
+  static constexpr int P = 0;                 // P^f_{k-1,l}          NN
+  static constexpr int mv = P + NN;           // m^f_{k-1,l}          NX
+  static constexpr int X = mv + NX;           // P C_bar^T            NX*MY
+  static constexpr int Si = X + NX * MY;      // S_y^-1               MY*MY
+  static constexpr int kap = Si + MY * MY;    // S_y^-1 (y - C_bar m) MY
+  static constexpr int Pl = kap + MY;         // P A^{lT}             NN
+  static constexpr int SUl = Pl + NN;         // S_y^-1 U_l^T         MY*NX
+  static constexpr int Z = SUl + MY * NX;     // A^T (P^-_{k+1,1})^-1 NN
+  static constexpr int ml = Z + NN;           // m^f_{k,l}            NX
+  static constexpr int Pm = ml + NX;          // P^-_{k+1,1}          NN
+  static constexpr int SIZE = Pm + NN;
+};
+
+// Filter element (F, d, D, eta, J) and smoother element (E, g, S) layouts.
+template <int NX>
+struct FL {
+  static constexpr int NN = NX * NX;
+  static constexpr int F = 0, d = NN, D = NN + NX, e = 2 * NN + NX, J = 2 * NN + 2 * NX;
+  static constexpr int SIZE = 3 * NN + 2 * NX;
+};
+template <int NX>
+struct SL {
+  static constexpr int NN = NX * NX;
+  static constexpr int E = 0, g = NN, S = NN + NX;
+  static constexpr int SIZE = 2 * NN + NX;
+};
+
+// Everything a kernel needs; passed by value.
+struct Ctx {
+  int n_seq, nx, ny, max_ratio;
+  int smoothing;                      // 1: smoother call, 0: filter only
+  int uniform_ratio, uniform_nslow;   // used when in_ratio/in_nslow are NULL
+  long long total_slow, total_fast;   // declared totals (validated on the device)
+  const int* in_ratio;
+  const int* in_nslow;
+  const double *F, *Q, *H, *R, *m0, *P0, *y;
+  // outputs of the call (smoothed, or filtered for a filter-only call)
+  double *fast_mean, *fast_cov, *slow_mean, *slow_cov;
+  // filtered outputs requested alongside a smoother call
+  double *ffast_mean, *ffast_cov, *fslow_mean, *fslow_cov;
+  // workspace
+  Counters* ctr;
+  SeqMeta meta;
+  double* model;
+  ModelLayout ml;
+  unsigned char* ftile;  long long ftile_stride;  // filter scan tile states
+  unsigned char* stile;  long long stile_stride;  // smoother scan tile states
+  void* fout;   // [total_slow][NX + NN] filter results m^f_{k,l}, P^f_{k,l}   (scan type)
+  void* rec;    // [total_slow][Rec::SIZE] per-interval records              (recovery type)
+  void* selem;  // [total_slow][SL::SIZE]  smoother elements                  (scan type)
+  void* sout;   // [total_slow][NX + NN]   smoothed first states m^s_{k,1}, P^s_{k,1}
+  // launch shapes
+  int tile_f, tile_s;    // elements per scan tile
+  int chunk_fast;        // target fast steps per recovery chunk
+  int chunk_cmax;        // max intervals per recovery chunk (shared-memory bound)
+};
+
+// ---------------------------------------------------------------------------
+// memory-ordering helpers (look-back protocol)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// index s with off[s] <= x < off[s+1]; off has n+1 nondecreasing entries.
+__device__ __forceinline__ int find_segment(const long long* off, int n, long long x) {
+  int lo = 0, hi = n;  // invariant off[lo] <= x < off[hi]
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (__ldg(off + mid) <= x) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ void raise_err(Counters* c, unsigned bits) { atomicOr(&c->err, bits); }
+
+// ---------------------------------------------------------------------------
+// host-side launch entry points (defined per nx in inst_nx*.cu)
+// ---------------------------------------------------------------------------
+struct Shapes {  // resolved launch shapes for one call
+  int scan_groups_f, scan_elems_f, scan_groups_s, scan_elems_s;
+  int recover_threads, recover_chunk;
+  int grid_f, grid_s, grid_r, grid_setup;
+  size_t smem_f, smem_s, smem_r;
+};
+
+template <int NX>
+int launch_device_path(const Ctx& c, srtm_precision prec, const Shapes& sh, cudaStream_t st, cudaEvent_t* ev);
+
+template <int NX>
+int query_shapes(srtm_precision prec, int scan_groups, int scan_elems, int recover_threads,
+                 int recover_chunk, int sm_count, long long total_slow, int n_seq, Shapes* sh);
+
+}  // namespace srtm

@@ -1,0 +1,61 @@
+"""Helpers for the GPU parity tests: run a problem through the C-ABI
+(via the ctypes binding) and compare with the FP64 oracle."""
+from __future__ import annotations
+
+import numpy as np
+
+TOL = {  # (means, covariances) relative tolerances of the paper-method outputs vs the FP64 oracle
+    "fp64": (1e-9, 1e-8),
+    "mixed": (1e-4, 1e-3),
+}
+
+
+def to_dev(a):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device="cuda")
+
+
+def run_smoother(prob, precision="fp64", filtered=True):
+    import torch
+
+    from paper_2410_00627_gb300 import api
+    args = [to_dev(getattr(prob, k)) for k in ("F", "Q", "H", "R", "m0", "P0", "y")]
+    sm, fi = api.smoother(*args, prob.ratio, precision=precision,
+                          filtered=api.OUTPUT_KEYS if filtered else ())
+    api.status()
+    torch.cuda.synchronize()
+    return ({k: v.cpu().numpy() for k, v in sm.items()}, {k: v.cpu().numpy() for k, v in fi.items()})
+
+
+def run_filter(prob, precision="fp64"):
+    from paper_2410_00627_gb300 import api
+    args = [to_dev(getattr(prob, k)) for k in ("F", "Q", "H", "R", "m0", "P0", "y")]
+    out = api.filter(*args, prob.ratio, precision=precision)
+    api.status()
+    return {k: v.cpu().numpy() for k, v in out.items()}
+
+
+def rel_err(a, b):
+    return float(np.max(np.abs(a - b)) / max(float(np.max(np.abs(b))), 1e-300))
+
+
+def compare(gpu, ref, tol_m, tol_c, label=""):
+    """gpu / ref: dicts of arrays with *_mean / *_cov keys; returns the errors."""
+    errs = {}
+    for k in ref:
+        if k not in gpu:
+            continue
+        e = rel_err(gpu[k], ref[k])
+        errs[k] = e
+        tol = tol_m if k.endswith("mean") else tol_c
+        assert e <= tol, f"{label} {k}: rel err {e:.3e} > {tol:.1e}"
+    return errs
+
+
+def oracle_views(o, l):
+    """Oracle outputs in the library's layout (smoothed, filtered)."""
+    sm = {"fast_mean": o["fast_smooth_mean"], "fast_cov": o["fast_smooth_cov"],
+          "slow_mean": o["fast_smooth_mean"][l - 1::l], "slow_cov": o["fast_smooth_cov"][l - 1::l]}
+    fi = {"fast_mean": o["fast_filt_mean"], "fast_cov": o["fast_filt_cov"],
+          "slow_mean": o["slow_filt_mean"], "slow_cov": o["slow_filt_cov"]}
+    return sm, fi

@@ -1,0 +1,74 @@
+"""Host-side checks of the C-ABI library that need no GPU: it loads, exports
+every entry point declared in include/srtm.h, and rejects bad arguments
+before touching the device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2410_00627_gb300 import api, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return api.load()
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "srtm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*int\s+(srtm_\w+)\s*\(", src, flags=re.M)))
+
+
+def test_header_declares_binding_symbols():
+    assert header_functions() == sorted(api.SYMBOLS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in header_functions():
+        assert hasattr(lib, name), name
+
+
+def test_struct_layouts_match_header():
+    # two 4-int headers then pointers on LP64
+    assert ctypes.sizeof(api.Problem) == 16 + 7 * 8
+    assert ctypes.sizeof(api.Output) == 4 * 8
+    assert ctypes.sizeof(api.Batch) == 16 + 16 + 9 * 8
+    assert ctypes.sizeof(api.Tuning) == 16
+
+
+def test_rejects_bad_arguments_without_gpu(lib):
+    assert lib.srtm_smoother(None, 0, None, None, None) == -1
+    bad = api.Problem(9, 1, 2, 3)  # nx out of range: rejected before any pointer is inspected
+    assert lib.srtm_smoother(ctypes.byref(bad), 0, None, None, None) == -6
+    assert "nx=9" in api.last_error_detail()
+    bad = api.Problem(2, 5, 2, 3)
+    assert lib.srtm_filter(ctypes.byref(bad), 0, None, None) == -6
+    bad = api.Problem(2, 1, 0, 3)
+    assert lib.srtm_smoother(ctypes.byref(bad), 0, None, None, None) == -1
+    bad = api.Problem(2, 1, 2, 3)
+    assert lib.srtm_smoother(ctypes.byref(bad), 7, None, None, None) == -1
+
+
+def test_tuning_validation_and_roundtrip(lib):
+    t = api.Tuning(0, 0, 0, 0)
+    assert lib.srtm_get_tuning(4, 1, ctypes.byref(t)) == 0
+    assert t.scan_groups * 16 == 128 and t.scan_elems >= 1 and t.recover_threads % 32 == 0
+    assert lib.srtm_set_tuning(4, 1, ctypes.byref(api.Tuning(3, 0, 0, 0))) == -1   # not a power of two
+    assert lib.srtm_set_tuning(4, 1, ctypes.byref(api.Tuning(32, 0, 0, 0))) == -1  # 32*16 lanes > 256
+    assert lib.srtm_set_tuning(4, 1, ctypes.byref(api.Tuning(0, 0, 48, 0))) == -1  # not a multiple of 32
+    assert lib.srtm_set_tuning(4, 1, ctypes.byref(api.Tuning(4, 8, 256, 1024))) == 0
+    assert lib.srtm_get_tuning(4, 1, ctypes.byref(t)) == 0
+    assert (t.scan_groups, t.scan_elems, t.recover_threads, t.recover_chunk) == (4, 8, 256, 1024)
+    assert lib.srtm_set_tuning(4, 1, ctypes.byref(api.Tuning(0, 0, 0, 0))) == 0
+    assert lib.srtm_set_tuning(1, 0, ctypes.byref(api.Tuning(128, 0, 0, 0))) == 0
+    assert lib.srtm_set_tuning(1, 0, ctypes.byref(api.Tuning(0, 0, 0, 0))) == 0
+
+
+def test_launch_counts(lib):
+    assert lib.srtm_launches_per_call(1) == 6
+    assert lib.srtm_launches_per_call(0) == 5

@@ -1,0 +1,227 @@
+"""GPU parity: the CUDA path (through the C-ABI) against the FP64 oracle.
+
+Small cases compare every output element by element; they span several scan
+tiles with a ragged tail (scan tiles hold 16-128 slow steps depending on nx).
+Full-size cases (config 2 at 10^4 slow steps, the benchmark's workload and
+launch configuration) compare sampled windows of fast outputs plus every
+slow output against the oracle.  Tolerances: FP64 1e-9 (means) / 1e-8
+(covariances, relative to max |P|); mixed 1e-4 / 1e-3.
+"""
+import numpy as np
+import pytest
+
+from paper_2410_00627_gb300 import synth
+from tests.gpu_util import TOL, compare, oracle_views, run_filter, run_smoother
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2410_00627_gb300 import api, build
+    build.build()
+    api.load()
+
+
+CASES = [  # (seed, nx, ny, ratio, n_slow)
+    (1, 1, 1, 3, 70),
+    (2, 2, 1, 1, 300),
+    (3, 3, 2, 4, 97),
+    (4, 4, 2, 20, 161),
+    (5, 4, 4, 7, 65),
+    (6, 5, 3, 6, 50),
+    (7, 6, 2, 5, 49),
+    (8, 7, 1, 3, 33),
+    (9, 8, 3, 4, 67),
+    (10, 2, 2, 2, 1),
+    (11, 4, 1, 5, 2),
+    (12, 3, 3, 1, 17),
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: "n{1}m{2}l{3}N{4}".format(*c))
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_smoother_matches_oracle(oracle_mod, case, precision):
+    seed, nx, ny, l, N = case
+    prob = synth.random_model(seed, nx, ny, l, N)
+    ref_sm, ref_fi = oracle_views(oracle_mod.sequential(prob), l)
+    sm, fi = run_smoother(prob, precision)
+    tm, tc = TOL[precision]
+    compare(sm, ref_sm, tm, tc, f"smoothed {precision}")
+    compare(fi, ref_fi, tm, tc, f"filtered {precision}")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("cfg,n_slow", [(1, 100), (2, 257), (5, 40)])
+def test_configs_small_match_oracle(oracle_mod, cfg, n_slow, precision):
+    prob = synth.CONFIGS[cfg](seed=11, n_slow=n_slow, keep_states=False)
+    ref_sm, ref_fi = oracle_views(oracle_mod.sequential(prob), prob.ratio)
+    sm, fi = run_smoother(prob, precision)
+    tm, tc = TOL[precision]
+    compare(sm, ref_sm, tm, tc, f"cfg{cfg} smoothed {precision}")
+    compare(fi, ref_fi, tm, tc, f"cfg{cfg} filtered {precision}")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_filter_call_matches_oracle(oracle_mod, precision):
+    prob = synth.random_model(21, 4, 2, 6, 131)
+    o = oracle_mod.sequential(prob, smooth=False)
+    out = run_filter(prob, precision)
+    l = prob.ratio
+    ref = {"fast_mean": o["fast_filt_mean"], "fast_cov": o["fast_filt_cov"],
+           "slow_mean": o["slow_filt_mean"], "slow_cov": o["slow_filt_cov"]}
+    compare(out, ref, *TOL[precision], label=f"filter {precision}")
+    assert np.array_equal(out["slow_mean"], out["fast_mean"][l - 1::l])
+
+
+def test_fp32_mode_runs_and_is_close(oracle_mod):
+    prob = synth.config2(seed=2, n_slow=120, keep_states=False)
+    ref_sm, _ = oracle_views(oracle_mod.sequential(prob), prob.ratio)
+    sm, _ = run_smoother(prob, "fp32", filtered=False)
+    errs = compare(sm, ref_sm, 1e-2, 1e-1, "fp32")
+    assert all(np.isfinite(v) for v in errs.values())
+
+
+def test_outputs_exactly_symmetric_and_last_interval(oracle_mod):
+    prob = synth.config2(seed=3, n_slow=50, keep_states=False)
+    sm, fi = run_smoother(prob, "fp64")
+    P = sm["fast_cov"]
+    assert np.array_equal(P, np.swapaxes(P, 1, 2))
+    l = prob.ratio
+    assert np.array_equal(sm["fast_mean"][-l:], fi["fast_mean"][-l:])
+    assert np.array_equal(sm["fast_cov"][-l:], fi["fast_cov"][-l:])
+
+
+def test_repeated_calls_are_bitwise_identical():
+    prob = synth.config2(seed=4, n_slow=300, keep_states=False)
+    a, _ = run_smoother(prob, "fp64", filtered=False)
+    b, _ = run_smoother(prob, "fp64", filtered=False)
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_full_size_config2_sampled(oracle_mod, precision):
+    """Config 2 at its full size (10^4 slow steps, 2*10^5 fast steps) in the
+    benchmark's launch configuration: every slow output, and fast outputs of
+    sampled windows (start, two interior windows, end)."""
+    prob = synth.config2(seed=0, n_slow=10_000, keep_states=False)
+    l, N = prob.ratio, prob.n_slow
+    sm, fi = run_smoother(prob, precision)
+    seq = oracle_mod.sequential(prob, fast=False)
+    tm, tc = TOL[precision]
+    windows = [(0, 3), (4093, 4099), (7770, 7772), (N - 3, N)]
+    for k0, k1 in windows:
+        o = oracle_mod.sequential(prob, k_lo=k0, k_hi=k1, slow=False)
+        sl = slice(k0 * l, k1 * l)
+        compare({"fast_mean": sm["fast_mean"][sl], "fast_cov": sm["fast_cov"][sl]},
+                {"fast_mean": o["fast_smooth_mean"], "fast_cov": o["fast_smooth_cov"]}, tm, tc, f"window {k0}")
+        compare({"fast_mean": fi["fast_mean"][sl], "fast_cov": fi["fast_cov"][sl]},
+                {"fast_mean": o["fast_filt_mean"], "fast_cov": o["fast_filt_cov"]}, tm, tc, f"window {k0}")
+    compare({"slow_mean": fi["slow_mean"], "slow_cov": fi["slow_cov"]},
+            {"slow_mean": seq["slow_filt_mean"], "slow_cov": seq["slow_filt_cov"]}, tm, tc, "slow filtered")
+    compare({"m": sm["fast_mean"][0::l], "P": sm["fast_cov"][0::l]},
+            {"m": seq["first_smooth_mean"], "P": seq["first_smooth_cov"]}, tm, tc, "first smoothed")
+
+
+def test_ragged_batch_matches_per_sequence_oracle(oracle_mod):
+    import torch
+
+    from paper_2410_00627_gb300 import api
+    from tests.gpu_util import to_dev
+    probs = synth.config4(seed=5, n_seq=9, n_min=1, n_max=120)
+    probs[3] = synth.config4(seed=6, n_seq=1, n_min=1, n_max=1)[0]   # a length-1 sequence
+    S = len(probs)
+    stack = lambda k: to_dev(np.stack([getattr(p, k) for p in probs]))  # noqa: E731
+    y = to_dev(np.concatenate([p.y for p in probs]))
+    ratio = torch.tensor([p.ratio for p in probs], dtype=torch.int32, device="cuda")
+    n_slow = torch.tensor([p.n_slow for p in probs], dtype=torch.int32, device="cuda")
+    tot_s = sum(p.n_slow for p in probs)
+    tot_f = sum(p.n_slow * p.ratio for p in probs)
+    for precision in ("fp64", "mixed"):
+        b = api.make_batch(stack("F"), stack("Q"), stack("H"), stack("R"), stack("m0"), stack("P0"), y,
+                           ratio, n_slow, max(p.ratio for p in probs), tot_s, tot_f)
+        sm, fi = api.smoother_batch(b, precision=precision, filtered=api.OUTPUT_KEYS)
+        api.status()
+        sm = {k: v.cpu().numpy() for k, v in sm.items()}
+        fi = {k: v.cpu().numpy() for k, v in fi.items()}
+        fo = so = 0
+        for p in probs:
+            l, N = p.ratio, p.n_slow
+            ref_sm, ref_fi = oracle_views(oracle_mod.sequential(p), l)
+            got_sm = {"fast_mean": sm["fast_mean"][fo:fo + N * l], "fast_cov": sm["fast_cov"][fo:fo + N * l],
+                      "slow_mean": sm["slow_mean"][so:so + N], "slow_cov": sm["slow_cov"][so:so + N]}
+            got_fi = {"fast_mean": fi["fast_mean"][fo:fo + N * l], "fast_cov": fi["fast_cov"][fo:fo + N * l],
+                      "slow_mean": fi["slow_mean"][so:so + N], "slow_cov": fi["slow_cov"][so:so + N]}
+            compare(got_sm, ref_sm, *TOL[precision], label=f"batch {p.name} {precision}")
+            compare(got_fi, ref_fi, *TOL[precision], label=f"batch {p.name} {precision}")
+            fo += N * l
+            so += N
+
+
+def test_batch_metadata_mismatch_is_reported_not_computed():
+    import torch
+
+    from paper_2410_00627_gb300 import api
+    from tests.gpu_util import to_dev
+    probs = synth.config4(seed=7, n_seq=3, n_min=5, n_max=9)
+    stack = lambda k: to_dev(np.stack([getattr(p, k) for p in probs]))  # noqa: E731
+    y = to_dev(np.concatenate([p.y for p in probs]))
+    ratio = torch.tensor([p.ratio for p in probs], dtype=torch.int32, device="cuda")
+    n_slow = torch.tensor([p.n_slow for p in probs], dtype=torch.int32, device="cuda")
+    tot_s = sum(p.n_slow for p in probs)
+    tot_f = sum(p.n_slow * p.ratio for p in probs)
+    # declared total_fast one row short of the metadata: rejected on the device
+    b = api.make_batch(stack("F"), stack("Q"), stack("H"), stack("R"), stack("m0"), stack("P0"), y,
+                       ratio, n_slow, 20, tot_s, tot_f - 1)
+    api.smoother_batch(b, precision="fp64")
+    with pytest.raises(api.SRTMError) as ei:
+        api.status()
+    assert ei.value.code == -7
+    # a ratio above the declared max_ratio is rejected the same way
+    b = api.make_batch(stack("F"), stack("Q"), stack("H"), stack("R"), stack("m0"), stack("P0"), y,
+                       ratio, n_slow, 4, tot_s, tot_f)
+    api.smoother_batch(b, precision="fp64")
+    with pytest.raises(api.SRTMError):
+        api.status()
+    api.status()  # latch cleared
+
+
+def test_host_pointer_rejected():
+    import ctypes
+
+    from paper_2410_00627_gb300 import api
+    prob = synth.random_model(1, 2, 1, 2, 3)
+    F = np.ascontiguousarray(prob.F)
+    p = api.Problem(2, 1, 2, 3, *[ctypes.c_void_p(np.ascontiguousarray(getattr(prob, k)).ctypes.data)
+                                  for k in ("F", "Q", "H", "R", "m0", "P0", "y")])
+    assert F.size == 4
+    out = api.Output(None, None, None, None)
+    assert api.load().srtm_smoother(ctypes.byref(p), 0, ctypes.byref(out), None, None) == -1
+    assert "not a device pointer" in api.last_error_detail()
+
+
+def test_host_entry_point_matches_device_entry_point():
+    from paper_2410_00627_gb300 import api
+    prob = synth.config2(seed=8, n_slow=200, keep_states=False)
+    dev, _ = run_smoother(prob, "mixed", filtered=False)
+    host = api.smoother_host(*[np.ascontiguousarray(getattr(prob, k)) for k in ("F", "Q", "H", "R", "m0", "P0", "y")],
+                             prob.ratio, precision="mixed")
+    for k in dev:
+        assert np.array_equal(dev[k], host[k]), k
+
+
+def test_stage_timing_reports_every_stage():
+    from paper_2410_00627_gb300 import api
+    prob = synth.config2(seed=9, n_slow=500, keep_states=False)
+    api.set_stage_timing(True)
+    try:
+        run_smoother(prob, "fp64", filtered=False)
+        t = api.stage_times()
+    finally:
+        api.set_stage_timing(False)
+    assert set(t) == set(api.STAGES)
+    assert all(v > 0 for v in t.values())
