@@ -164,6 +164,26 @@ int srtm_launches_per_call(int smoothing);
 int srtm_set_stage_timing(int enable);
 int srtm_stage_times(float *ms, int n);
 
+/* srtm_smoother for callers that must not allocate device memory (the paper
+ * has no counterpart; this is a deployment variant).  Such callers include a
+ * process whose GPU memory is already reserved by another allocator, where a
+ * new cudaMalloc could fail or fragment that pool, and latency-bound loops
+ * that cannot absorb the device-wide synchronisation of cudaMalloc/cudaFree.
+ * This entry point calls no cudaMalloc, cudaFree or other allocating routine:
+ * its scratch is a 32 MiB static device array that every GPU loading this
+ * library reserves until the library is unloaded.  Inputs and outputs are the
+ * caller's device buffers, as for srtm_smoother (filtered extras are not
+ * offered).  A problem whose scratch would exceed 32 MiB (for nx=4 in float64
+ * about 2*10^4 slow steps) returns SRTM_ERR_ARG with the needed size in
+ * srtm_last_error_detail().  The first call on a GPU looks up the array's
+ * device address on that GPU (make it before any stream capture).  All calls
+ * share the array: calls whose work overlaps on the GPU (other streams or
+ * threads) race and must be serialized by the caller.  The call waits for its
+ * own work and returns the device-side status directly (SRTM_OK,
+ * SRTM_ERR_TIMEOUT or SRTM_ERR_SINGULAR).                                       */
+int srtm_smoother_noalloc(const srtm_problem *p, srtm_precision prec, const srtm_output *smooth,
+                          srtm_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

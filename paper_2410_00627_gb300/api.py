@@ -22,7 +22,7 @@ OUTPUT_KEYS = ("fast_mean", "fast_cov", "slow_mean", "slow_cov")
 SYMBOLS = ("srtm_filter", "srtm_smoother", "srtm_filter_batch", "srtm_smoother_batch",
            "srtm_smoother_host", "srtm_status", "srtm_last_error_detail", "srtm_release",
            "srtm_set_tuning", "srtm_get_tuning", "srtm_launches_per_call", "srtm_set_stage_timing",
-           "srtm_stage_times")
+           "srtm_stage_times", "srtm_smoother_noalloc")
 STAGES = ("metadata", "constants", "filter_scan", "interval_setup", "smoother_scan", "recovery")
 
 
@@ -87,6 +87,7 @@ def load():
         "srtm_launches_per_call": [c_int],
         "srtm_set_stage_timing": [c_int],
         "srtm_stage_times": [ctypes.POINTER(ctypes.c_float), c_int],
+        "srtm_smoother_noalloc": [P, c_int, O, c_void_p],
     }
     for name, args in sig.items():
         f = getattr(lib, name)

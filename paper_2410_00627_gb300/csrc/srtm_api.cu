@@ -481,3 +481,123 @@ int srtm_stage_times(float* ms, int n) {
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// Allocation-free smoother.
+//
+// Some callers must not allocate device memory at all: a process whose HBM
+// is already reserved by another allocator (a new cudaMalloc could fail or
+// fragment that pool), or a latency-bound loop that cannot absorb the
+// device-wide synchronisation that cudaMalloc/cudaFree imply.  For them,
+// srtm_smoother_noalloc runs the same device path as srtm_smoother with its
+// scratch (metadata, model tables, look-back tile states, per-interval
+// records) in the file-scope array below instead of the cached workspace.
+// The array is reserved on every GPU that loads this library, for as long as
+// the library stays loaded.
+// ===========================================================================
+namespace {
+constexpr size_t NOALLOC_SCRATCH_BYTES = 32ull << 20;  // 32 MiB
+}
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+namespace {
+// Device address of g_noalloc_scratch per GPU.  In host code the symbol is
+// only a host-side stand-in, so the address is fetched once per device.
+void* g_noalloc_addr[MAXDEV] = {};
+}
+
+extern "C" int srtm_smoother_noalloc(const srtm_problem* p, srtm_precision prec, const srtm_output* smooth,
+                                     srtm_stream_t stream) {
+  if (!p) return fail(SRTM_ERR_ARG, "problem is NULL");
+  if (prec < SRTM_FP64 || prec > SRTM_FP32) return fail(SRTM_ERR_ARG, "unknown precision %d", (int)prec);
+  int rc = check_dims(p->nx, p->ny);
+  if (rc) return rc;
+  if (p->ratio < 1) return fail(SRTM_ERR_ARG, "ratio=%d < 1", p->ratio);
+  if (p->n_slow < 1) return fail(SRTM_ERR_ARG, "n_slow=%d < 1", p->n_slow);
+  if ((rc = check_inputs(p->F, p->Q, p->H, p->R, p->m0, p->P0, p->y))) return rc;
+  if ((rc = check_outputs(smooth, "output"))) return rc;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAXDEV)
+    return fail(SRTM_ERR_CUDA, "no usable CUDA device");
+  cudaStream_t st = (cudaStream_t)stream;
+  Ctx c;
+  memset(&c, 0, sizeof c);
+  c.n_seq = 1;
+  c.nx = p->nx;
+  c.ny = p->ny;
+  c.max_ratio = p->ratio;
+  c.smoothing = 1;
+  c.uniform_ratio = p->ratio;
+  c.uniform_nslow = p->n_slow;
+  c.total_slow = p->n_slow;
+  c.total_fast = (long long)p->n_slow * p->ratio;
+  c.F = p->F; c.Q = p->Q; c.H = p->H; c.R = p->R; c.m0 = p->m0; c.P0 = p->P0; c.y = p->y;
+  set_outputs(c, smooth, nullptr);
+  unsigned char* w = nullptr;
+  Layout L;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_noalloc_addr[dev]) {
+      void* addr = nullptr;
+      const cudaError_t e = cudaGetSymbolAddress(&addr, g_noalloc_scratch);
+      if (e != cudaSuccess || !addr)
+        return fail(SRTM_ERR_CUDA, "cudaGetSymbolAddress of the static scratch failed: %s", cudaGetErrorString(e));
+      g_noalloc_addr[dev] = addr;
+    }
+    w = (unsigned char*)g_noalloc_addr[dev];
+    DevState& d = g_dev[dev];
+    if (!d.sms && cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return fail(SRTM_ERR_CUDA, "cudaDeviceGetAttribute failed");
+    const srtm_tuning t = effective_tuning(c.nx, prec);
+    Shapes sh;
+    rc = shapes_for(c.nx, prec, t, d.sms, c.total_slow, c.n_seq, &sh);
+    if (rc) return fail(rc, "launch shape query failed (%d)", rc);
+    const int tile_f = sh.scan_groups_f * sh.scan_elems_f, tile_s = sh.scan_groups_s * sh.scan_elems_s;
+    L = make_layout(c.nx, c.ny, c.max_ratio, c.n_seq, c.total_slow, prec, tile_f, tile_s);
+    if (L.total > NOALLOC_SCRATCH_BYTES)
+      return fail(SRTM_ERR_ARG, "this problem needs %zu bytes of scratch; the static scratch holds %zu bytes",
+                  L.total, NOALLOC_SCRATCH_BYTES);
+    // The array keeps the previous call's contents: the control block and
+    // the look-back flags must start at zero.
+    if (cudaMemsetAsync(w + L.ctr, 0, sizeof(Counters), st) != cudaSuccess ||
+        cudaMemsetAsync(w + L.ftile, 0, L.fout - L.ftile, st) != cudaSuccess)
+      return fail(SRTM_ERR_CUDA, "clearing the static scratch failed");
+    c.ctr = (Counters*)(w + L.ctr);
+    c.meta.ratio = (int*)(w + L.ratio);
+    c.meta.nslow = (int*)(w + L.nslow);
+    c.meta.chunk_C = (int*)(w + L.chunkC);
+    c.meta.off_slow = (long long*)(w + L.off_slow);
+    c.meta.off_fast = (long long*)(w + L.off_fast);
+    c.meta.tile_off_f = (long long*)(w + L.tile_f);
+    c.meta.tile_off_s = (long long*)(w + L.tile_s);
+    c.meta.chunk_off = (long long*)(w + L.chunk_off);
+    c.model = (double*)(w + L.model);
+    c.ml = L.ml;
+    c.ftile = w + L.ftile;
+    c.ftile_stride = L.ftile_stride;
+    c.stile = w + L.stile;
+    c.stile_stride = L.stile_stride;
+    c.fout = w + L.fout;
+    c.rec = w + L.rec;
+    c.selem = w + L.selem;
+    c.sout = w + L.sout;
+    c.tile_f = tile_f;
+    c.tile_s = tile_s;
+    c.chunk_fast = sh.recover_chunk;
+    const size_t per_int = (size_t)(c.nx * c.nx + c.nx) * (prec == SRTM_FP32 ? 4 : 8);
+    c.chunk_cmax = (int)std::max<size_t>(1, sh.smem_r / per_int);
+    rc = launch_meta_and_precompute(c, st, nullptr);
+    if (rc) return fail(rc, "launch of the metadata/constants kernels failed");
+    rc = launch_for(c.nx, c, prec, sh, st, nullptr);
+    if (rc) return fail(rc, "launch of the scan/recovery kernels failed");
+  }
+  // Device-side errors of this call live in the static scratch: wait for the
+  // call and read them here.
+  if (cudaStreamSynchronize(st) != cudaSuccess)
+    return fail(SRTM_ERR_CUDA, "stream synchronize failed: %s", cudaGetErrorString(cudaGetLastError()));
+  unsigned err = 0;
+  if (cudaMemcpy(&err, w + L.ctr + offsetof(Counters, err), sizeof err, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return fail(SRTM_ERR_CUDA, "reading the device error latch failed");
+  if (err & DEVERR_TIMEOUT) return fail(SRTM_ERR_TIMEOUT, "a scan look-back wait exceeded its bound");
+  if (err & DEVERR_SINGULAR) return fail(SRTM_ERR_SINGULAR, "a solve met a zero, negative or non-finite pivot");
+  return SRTM_OK;
+}
