@@ -139,16 +139,15 @@ int srtm_last_error_detail(char *buf, int len);
 /* Frees the cached device workspace and staging buffers of every GPU.        */
 int srtm_release(void);
 
-/* Tuning of the launch shapes (elements per lane group, groups per block,
- * fast steps per recovery chunk) for one (nx, precision).  Zero values keep
- * the built-in choice.  Returns SRTM_ERR_ARG for out-of-range values.        */
+/* Tuning of the launch shapes (lane groups per scan block, elements per lane
+ * group, recovery block size) for one (nx, precision).  Zero values keep the
+ * built-in choice.  Returns SRTM_ERR_ARG for out-of-range values.           */
 typedef struct {
   int scan_groups;      /* lane groups per scan block: a power of two such that
                            groups x lanes-per-group (1, 4, 16 or 32 by nx) is
                            32..256                                              */
   int scan_elems;       /* elements per lane group per tile (1..64)            */
-  int recover_threads;  /* recovery block size (32..1024, multiple of 32)      */
-  int recover_chunk;    /* target fast steps per recovery chunk (32..65536)    */
+  int recover_threads;  /* recovery block size (32..128, multiple of 32)       */
 } srtm_tuning;
 int srtm_set_tuning(int nx, srtm_precision prec, const srtm_tuning *t);
 int srtm_get_tuning(int nx, srtm_precision prec, srtm_tuning *t);

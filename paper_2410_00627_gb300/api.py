@@ -45,8 +45,7 @@ class Batch(ctypes.Structure):
 
 
 class Tuning(ctypes.Structure):
-    _fields_ = [("scan_groups", c_int), ("scan_elems", c_int), ("recover_threads", c_int),
-                ("recover_chunk", c_int)]
+    _fields_ = [("scan_groups", c_int), ("scan_elems", c_int), ("recover_threads", c_int)]
 
 
 class SRTMError(RuntimeError):
@@ -241,9 +240,9 @@ def status(stream=None) -> None:
     _check(load().srtm_status(_stream_handle(stream)))
 
 
-def set_tuning(nx: int, precision: str, scan_groups=0, scan_elems=0, recover_threads=0, recover_chunk=0):
+def set_tuning(nx: int, precision: str, scan_groups=0, scan_elems=0, recover_threads=0):
     _check(load().srtm_set_tuning(nx, PRECISION[precision],
-                                  ctypes.byref(Tuning(scan_groups, scan_elems, recover_threads, recover_chunk))))
+                                  ctypes.byref(Tuning(scan_groups, scan_elems, recover_threads))))
 
 
 def get_tuning(nx: int, precision: str) -> dict:

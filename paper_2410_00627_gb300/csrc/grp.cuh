@@ -108,58 +108,180 @@ __device__ __forceinline__ void g_copy(const Grp<G>& g, T* dst, const TS* src, i
   for (int e = g.lane; e < count; e += G) dst[e] = (T)src[e];
 }
 
-// Gauss-Jordan elimination with partial pivoting on the augmented NX x 2NX
-// matrix Ma = [M | I] (row-major, leading dimension 2NX): on return the right
-// half holds M^{-1}.  Every lane of the group reads the pivot column itself,
-// so the pivot choice needs no exchange.  Returns false on a zero or
-// non-finite pivot (the step then divides by one to stay finite).
+// |x| as an order-preserving integer (IEEE magnitudes compare like their bit
+// patterns), so pivot selection uses the integer pipe, not the FP64 pipe.
+__device__ __forceinline__ unsigned long long mag_key(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+}
+__device__ __forceinline__ unsigned long long mag_key(float x) {
+  return (unsigned long long)((unsigned)__float_as_int(x) & 0x7fffffffu);
+}
+// zero, infinite or NaN pivot, tested on the bit pattern
+__device__ __forceinline__ bool bad_pivot(double x) {
+  const unsigned long long m = mag_key(x);
+  return m == 0ull || m >= 0x7ff0000000000000ull;
+}
+__device__ __forceinline__ bool bad_pivot(float x) {
+  const unsigned long long m = mag_key(x);
+  return m == 0ull || m >= 0x7f800000ull;
+}
+
+// In-place Gauss-Jordan inversion with partial (row) pivoting of the NX x NX
+// matrix a (row-major, shared memory).  Step s swaps the pivot row into place
+// and applies
+//   a_ss <- 1/p,  a_sc <- a_sc/p,  a_rs <- -a_rs/p,  a_rc <- a_rc - a_rs a_sc/p,
+// which leaves (P M)^{-1} after NX steps; undoing the row interchanges on the
+// columns (last step first) gives M^{-1}.  Every lane scans the pivot column
+// itself, so the choice needs no exchange.  Returns false on a zero or
+// non-finite pivot (the step then uses 1 to stay finite).
 template <int NX, int G, class TS>
-__device__ __forceinline__ bool g_gauss_jordan(const Grp<G>& g, TS* Ma) {
-  constexpr int W = 2 * NX, NE = NX * W, EPL = (NE + G - 1) / G;
+__device__ __forceinline__ bool g_gauss_jordan(const Grp<G>& g, TS* a) {
+  constexpr int NN = NX * NX, EPL = (NN + G - 1) / G;
   bool ok = true;
-#pragma unroll 1
+  int pv[NX];
+#pragma unroll
   for (int s = 0; s < NX; ++s) {
     int p = s;
-    TS best = fabs(Ma[s * W + s]);
+    unsigned long long best = mag_key(a[s * NX + s]);
+#pragma unroll
     for (int r = s + 1; r < NX; ++r) {
-      const TS v = fabs(Ma[r * W + s]);
+      const unsigned long long v = mag_key(a[r * NX + s]);
       if (v > best) { best = v; p = r; }
     }
+    pv[s] = p;
     g.sync();
     if (p != s) {
-      for (int c = g.lane; c < W; c += G) {
-        const TS t = Ma[s * W + c];
-        Ma[s * W + c] = Ma[p * W + c];
-        Ma[p * W + c] = t;
+      for (int c = g.lane; c < NX; c += G) {
+        const TS t = a[s * NX + c];
+        a[s * NX + c] = a[p * NX + c];
+        a[p * NX + c] = t;
       }
     }
     g.sync();
-    TS piv = Ma[s * W + s];
-    if (!(fabs(piv) > TS(0)) || !isfinite(piv)) { ok = false; piv = TS(1); }
+    TS piv = a[s * NX + s];
+    if (bad_pivot(piv)) { ok = false; piv = TS(1); }
     const TS inv = TS(1) / piv;
-    TS v[EPL], f[EPL], rs[EPL];
+    TS v[EPL], ars[EPL], asc[EPL];
 #pragma unroll
     for (int j = 0; j < EPL; ++j) {
       const int e = j * G + g.lane;
-      if (e < NE) {
-        const int r = e / W, c = e - (e / W) * W;
-        v[j] = Ma[e];
-        f[j] = Ma[r * W + s] * inv;
-        rs[j] = Ma[s * W + c];
+      if (e < NN) {
+        const int r = e / NX, c = e - (e / NX) * NX;
+        v[j] = a[e];
+        ars[j] = a[r * NX + s];
+        asc[j] = a[s * NX + c];
       }
     }
     g.sync();
 #pragma unroll
     for (int j = 0; j < EPL; ++j) {
       const int e = j * G + g.lane;
-      if (e < NE) {
-        const int r = e / W;
-        Ma[e] = (r == s) ? v[j] * inv : fma(-f[j], rs[j], v[j]);
+      if (e < NN) {
+        const int r = e / NX, c = e - (e / NX) * NX;
+        TS out;
+        if (r == s) out = (c == s) ? inv : v[j] * inv;
+        else if (c == s) out = -ars[j] * inv;
+        else out = fma(-ars[j] * inv, asc[j], v[j]);
+        a[e] = out;
       }
     }
     g.sync();
   }
+#pragma unroll
+  for (int s = NX - 1; s >= 0; --s) {
+    if (pv[s] != s) {
+      for (int r = g.lane; r < NX; r += G) {
+        const TS t = a[r * NX + s];
+        a[r * NX + s] = a[r * NX + pv[s]];
+        a[r * NX + pv[s]] = t;
+      }
+      g.sync();
+    }
+  }
   return ok;
+}
+
+// Inverse of an NX x NX matrix, NX <= 4, by the adjugate: entries are
+// cofactors over the determinant, so a single division is needed (a pivoted
+// elimination needs one per pivot, and a float64 division costs about six
+// FMAs on this part).  For NX = 4 the cofactors come from the Laplace
+// expansion by complementary 2x2 minors of rows (0,1) and (2,3):
+//   s_u = a_0p a_1q - a_1p a_0q,  c_u = a_2p a_3q - a_3p a_2q,
+//   (p,q) in (0,1),(0,2),(0,3),(1,2),(1,3),(2,3) for u = 0..5,
+//   det = s0 c5 - s1 c4 + s2 c3 + s3 c2 - s4 c1 + s5 c0.
+// In place on a (shared memory); mn holds the 12 minors.  Returns false on
+// a zero or non-finite determinant (then divides by one to stay finite).
+template <int NX, int G, class TS>
+__device__ __forceinline__ bool g_small_inverse(const Grp<G>& g, TS* a, TS* mn) {
+  static_assert(NX >= 1 && NX <= 4, "adjugate inverse is for NX <= 4");
+  constexpr int NN = NX * NX, EPL = (NN + G - 1) / G;
+  bool ok = true;
+  TS det;
+  if (NX == 4) {
+    for (int u = g.lane; u < 12; u += G) {
+      const int r0 = u < 6 ? 0 : 2, v = u < 6 ? u : u - 6;
+      const int p = v < 3 ? 0 : (v < 5 ? 1 : 2);
+      const int q = v < 3 ? v + 1 : (v < 5 ? v - 1 : 3);
+      mn[u] = fma(a[r0 * 4 + p], a[(r0 + 1) * 4 + q], -a[(r0 + 1) * 4 + p] * a[r0 * 4 + q]);
+    }
+    g.sync();
+    const TS* sm = mn;
+    const TS* cm = mn + 6;
+    det = sm[0] * cm[5] - sm[1] * cm[4] + sm[2] * cm[3] + sm[3] * cm[2] - sm[4] * cm[1] + sm[5] * cm[0];
+  } else if (NX == 3) {
+    det = a[0] * (a[4] * a[8] - a[5] * a[7]) - a[1] * (a[3] * a[8] - a[5] * a[6]) + a[2] * (a[3] * a[7] - a[4] * a[6]);
+  } else if (NX == 2) {
+    det = a[0] * a[3] - a[1] * a[2];
+  } else {
+    det = a[0];
+  }
+  if (bad_pivot(det)) { ok = false; det = TS(1); }
+  const TS id = TS(1) / det;
+  TS out[EPL];
+#pragma unroll
+  for (int j = 0; j < EPL; ++j) {
+    const int e = j * G + g.lane;
+    if (e < NN) {
+      const int r = e / NX, col = e - (e / NX) * NX;
+      TS v;
+      if (NX == 1) {
+        v = TS(1);
+      } else if (NX == 2) {
+        v = (r == col) ? a[(1 - r) * 3] : -a[r * 2 + col];
+      } else if (NX == 3) {
+        // inv[r][col] = cofactor(col, r): minor without row col and column r
+        const int i0 = col == 0 ? 1 : 0, i1 = col == 2 ? 1 : 2;
+        const int j0 = r == 0 ? 1 : 0, j1 = r == 2 ? 1 : 2;
+        v = a[i0 * 3 + j0] * a[i1 * 3 + j1] - a[i0 * 3 + j1] * a[i1 * 3 + j0];
+        if ((r + col) & 1) v = -v;
+      } else {
+        const int arow = col ^ 1;
+        const TS* mins = col < 2 ? mn + 6 : mn;
+        const int code = r == 0 ? 0x543 : (r == 1 ? 0x521 : (r == 2 ? 0x420 : 0x310));
+        const int k0 = r > 0 ? 0 : 1, k1 = r > 1 ? 1 : 2, k2 = r > 2 ? 2 : 3;
+        v = a[arow * 4 + k0] * mins[(code >> 8) & 15];
+        v = fma(-a[arow * 4 + k1], mins[(code >> 4) & 15], v);
+        v = fma(a[arow * 4 + k2], mins[code & 15], v);
+        if (((col & 1) != 0) != ((r & 1) != 0)) v = -v;
+      }
+      out[j] = v * id;
+    }
+  }
+  g.sync();
+#pragma unroll
+  for (int j = 0; j < EPL; ++j) {
+    const int e = j * G + g.lane;
+    if (e < NN) a[e] = out[j];
+  }
+  g.sync();
+  return ok;
+}
+
+// M^{-1} in place: adjugate for NX <= 4, pivoted Gauss-Jordan above.
+template <int NX, int G, class TS>
+__device__ __forceinline__ bool g_inverse(const Grp<G>& g, TS* a, TS* mn) {
+  if constexpr (NX <= 4) return g_small_inverse<NX, G, TS>(g, a, mn);
+  else return g_gauss_jordan<NX, G, TS>(g, a);
 }
 
 // ---------------------------------------------------------------------------
@@ -169,58 +291,46 @@ __device__ __forceinline__ bool g_gauss_jordan(const Grp<G>& g, TS* Ma) {
 //   F_ij = W F_i,                 d_ij = W (d_i + D_i eta_j) + d_j,
 //   D_ij = W D_i F_j^T + D_j,     eta_ij = V^T (eta_j - J_j d_i) + eta_i,
 //   J_ij = V^T J_j F_i + J_i.
-// M, its inverse, W and V are formed in TS (float64 in the mixed mode); the
-// rest in T.  D_ij and J_ij are written exactly symmetric.
+// M is inverted in TS (float64 in the mixed mode) by pivoted Gauss-Jordan;
+// everything else is in T.  D_ij and J_ij are written exactly symmetric.
 // prefix=true: a is a prefix that contains the first element (F = 0, eta = 0,
 // J = 0 exactly, Eq. 25 with k = 1), so only d_ij, D_ij are formed and F_ij,
 // eta_ij, J_ij are zero.
-// Scratch: sc (T) 4NN + 2NX, sm (TS) 2NN.
+// Scratch: sc (T) 5NN + 2NX, sm (TS) NN + 12.
 // ---------------------------------------------------------------------------
 template <int NX, int G, class T, class TS>
 __device__ __forceinline__ bool g_filter_combine(const Grp<G>& g, T* o, const T* a, const T* b, T* sc, TS* Ma,
                                                  bool prefix) {
   using L = FL<NX>;
-  constexpr int NN = NX * NX, W2 = 2 * NX, NE = NX * W2;
+  constexpr int NN = NX * NX;
   T *W = sc, *V = sc + NN, *WD = sc + 2 * NN, *JF = sc + 3 * NN, *t1 = sc + 4 * NN, *t2 = sc + 4 * NN + NX;
-  // [I + D_i J_j | I]
+  T* Mi = sc + 4 * NN + 2 * NX;
+  // M = I + D_i J_j, formed in T and held in TS for the solve
 #pragma unroll
-  for (int e0 = 0; e0 < NE; e0 += G) {
+  for (int e0 = 0; e0 < NN; e0 += G) {
     const int e = e0 + g.lane;
-    if (e < NE) {
-      const int r = e / W2, c = e - (e / W2) * W2;
-      if (c < NX) {
-        TS s = (r == c) ? TS(1) : TS(0);
+    if (e < NN) {
+      const int r = e / NX, c = e - (e / NX) * NX;
+      T s = (r == c) ? T(1) : T(0);
 #pragma unroll
-        for (int k = 0; k < NX; ++k) s = fma((TS)a[L::D + r * NX + k], (TS)b[L::J + k * NX + c], s);
-        Ma[e] = s;
-      } else {
-        Ma[e] = (r == c - NX) ? TS(1) : TS(0);
-      }
+      for (int k = 0; k < NX; ++k) s = fma(a[L::D + r * NX + k], b[L::J + k * NX + c], s);
+      Ma[e] = (TS)s;
     }
   }
   // t1 = d_i + D_i eta_j ;  t2 = eta_j - J_j d_i
   g_mv<NX, G, false, T>(g, t1, a + L::D, b + L::e, a + L::d);
   if (!prefix) g_mv<NX, G, false, T>(g, t2, b + L::J, a + L::d, b + L::e, T(-1));
   g.sync();
-  const bool ok = g_gauss_jordan<NX, G, TS>(g, Ma);
-  // W = F_j M^{-1} ; V = M^{-1} F_i
-#pragma unroll
-  for (int e0 = 0; e0 < NN; e0 += G) {
-    const int e = e0 + g.lane;
-    if (e < NN) {
-      const int r = e / NX, c = e - (e / NX) * NX;
-      TS s = TS(0);
-#pragma unroll
-      for (int k = 0; k < NX; ++k) s = fma((TS)b[L::F + r * NX + k], Ma[k * W2 + NX + c], s);
-      W[e] = (T)s;
-      if (!prefix) {
-        TS v = TS(0);
-#pragma unroll
-        for (int k = 0; k < NX; ++k) v = fma(Ma[r * W2 + NX + k], (TS)a[L::F + k * NX + c], v);
-        V[e] = (T)v;
-      }
-    }
+  const bool ok = g_inverse<NX, G, TS>(g, Ma, Ma + NN);
+  const T* Minv = (const T*)Ma;
+  if (sizeof(T) != sizeof(TS)) {  // one rounding of M^{-1} to T
+    for (int e = g.lane; e < NN; e += G) Mi[e] = (T)Ma[e];
+    g.sync();
+    Minv = Mi;
   }
+  // W = F_j M^{-1} ; V = M^{-1} F_i
+  g_mm<NX, G, false, false, T>(g, W, b + L::F, Minv, (const T*)nullptr);
+  if (!prefix) g_mm<NX, G, false, false, T>(g, V, Minv, a + L::F, (const T*)nullptr);
   g.sync();
   g_mm<NX, G, false, false, T>(g, WD, W, a + L::D, (const T*)nullptr);
   if (!prefix) {

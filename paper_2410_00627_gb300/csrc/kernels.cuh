@@ -28,8 +28,8 @@ struct FilterOp {
   using L = FL<NX>;
   static constexpr int G = GroupSize<NX>::value;
   static constexpr int ES = L::SIZE;
-  static constexpr int SCR = 4 * NX * NX + 2 * NX;
-  static constexpr int SCRS = 2 * NX * NX;
+  static constexpr int SCR = 5 * NX * NX + 2 * NX;
+  static constexpr int SCRS = NX * NX + 12;
   static constexpr int TICKET = 0;
 
   __device__ static bool combine(const Grp<G>& g, T* o, const T* left, const T* right, T* sc, TS* scs,
@@ -70,11 +70,12 @@ struct FilterOp {
       x[L::e + r] = (T)ev;
     }
   }
-  // filter result at k: d_k = m^f_{k,l}, D_k = P^f_{k,l}
-  __device__ static void store(const Grp<G>& g, const T* x, const Ctx& c, int s, long long p, int /*N*/) {
+  // filter result at k: d_k = m^f_{k,l}, D_k = P^f_{k,l}, kept in TS (float64
+  // in the mixed mode) for the float64 interval setup
+  __device__ static void store(const Grp<G>& g, const T* x, const Ctx& c, int s, long long p, int /*N*/, T*, TS*) {
     constexpr int NN = NX * NX;
-    T* out = (T*)c.fout + (c.meta.off_slow[s] + p) * (NX + NN);
-    for (int e = g.lane; e < NX + NN; e += G) out[e] = x[L::d + e];  // d then D are contiguous
+    TS* out = (TS*)c.fout + (c.meta.off_slow[s] + p) * (NX + NN);
+    for (int e = g.lane; e < NX + NN; e += G) out[e] = (TS)x[L::d + e];  // d then D are contiguous
   }
   __device__ static unsigned char* tile_state(const Ctx& c, long long t) { return c.ftile + t * c.ftile_stride; }
   __device__ static const long long* tile_off(const Ctx& c) { return c.meta.tile_off_f; }
@@ -85,16 +86,21 @@ struct FilterOp {
 // Reverse scan of the parallel IMS (Sec. IV): elements of Eq. (29) built by
 // the interval-setup kernel, operator Eq. (30).  Scan position p is slow step
 // k = N-1-p, so the scan-order combine left (x) right is right (x) left in
-// the paper's order.
-template <int NX, class T_>
+// the paper's order.  Its result at k is p(x_{k,1} | y_{1:N}) = N(g, S); the
+// store step turns it at once into the smoothing terms that the recovery of
+// interval k-1 needs (Eq. 21 with G_{k-1,i} = P^f_{k-1,i,l} Z_{k-1}):
+//   dm = m^s_{k,1} - A m^f_{k-1,l},  dP = P^s_{k,1} - P^-_{k,1},
+//   om_{k-1} = Z dm,  Om_{k-1} = Z dP Z^T,   Z = A^T (P^-_{k,1})^{-1},
+// formed by the lane group in TR (float64 except in the float32 mode).
+template <int NX, class T_, class TR_>
 struct SmootherOp {
   using T = T_;
-  using TS = T_;
+  using TS = TR_;
   using L = SL<NX>;
   static constexpr int G = GroupSize<NX>::value;
   static constexpr int ES = L::SIZE;
   static constexpr int SCR = NX * NX;
-  static constexpr int SCRS = 0;
+  static constexpr int SCRS = 2 * NX * NX + NX;
   static constexpr int TICKET = 1;
 
   __device__ static bool combine(const Grp<G>& g, T* o, const T* left, const T* right, T* sc, TS*, bool prefix) {
@@ -108,11 +114,27 @@ struct SmootherOp {
     const T* src = (const T*)c.selem + (c.meta.off_slow[s] + (N - 1 - p)) * ES;
     for (int e = g.lane; e < ES; e += G) x[e] = src[e];
   }
-  // smoothed first state of interval k: g = m^s_{k,1}, S = P^s_{k,1}
-  __device__ static void store(const Grp<G>& g, const T* x, const Ctx& c, int s, long long p, int N) {
+  __device__ static void store(const Grp<G>& g, const T* x, const Ctx& c, int s, long long p, int N, T*, TS* scs) {
     constexpr int NN = NX * NX;
-    T* out = (T*)c.sout + (c.meta.off_slow[s] + (N - 1 - p)) * (NX + NN);
-    for (int e = g.lane; e < NX + NN; e += G) out[e] = x[L::g + e];  // g then S are contiguous
+    using RL = Rec<NX>;
+    using TR = TS;
+    const long long k = N - 1 - p;
+    if (k == 0) return;
+    const long long row = c.meta.off_slow[s] + k - 1;
+    const TR* rc = (const TR*)c.rec + row * RL::SIZE;
+    const double* A1 = c.model + (long long)s * c.ml.stride + c.ml.Apow + NN;
+    TR* dP = scs;
+    TR* ZdP = scs + NN;
+    TR* dm = scs + 2 * NN;
+    TR* out = (TR*)c.sfin + row * (NN + NX);
+    for (int e = g.lane; e < NN; e += G) dP[e] = (TR)x[L::S + e] - rc[RL::Pm + e];
+    g_mv<NX, G, false, TR>(g, dm, A1, rc + RL::ml, x + L::g, TR(-1));
+    g.sync();
+    g_mm<NX, G, false, false, TR>(g, ZdP, rc + RL::Z, dP, (const TR*)nullptr);
+    g_mv<NX, G, false, TR>(g, out + NN, rc + RL::Z, dm, (const TR*)nullptr);
+    g.sync();
+    g_mm_sym<NX, G, false, true, TR>(g, out, ZdP, rc + RL::Z, (const TR*)nullptr);
+    g.sync();
   }
   __device__ static unsigned char* tile_state(const Ctx& c, long long t) { return c.stile + t * c.stile_stride; }
   __device__ static const long long* tile_off(const Ctx& c) { return c.meta.tile_off_s; }
@@ -140,8 +162,11 @@ struct ScanSmem {
   __host__ __device__ static size_t group_bytes() {
     return align16((3 * Op::ES + Op::SCR) * sizeof(T)) + align16((Op::SCRS > 0 ? Op::SCRS : 1) * sizeof(TS));
   }
+  static constexpr int WIN = 16;  // look-back window (predecessor tiles per round)
+  __host__ __device__ static size_t window_bytes() { return align16((size_t)(WIN + WIN / 2) * Op::ES * sizeof(T)); }
   __host__ __device__ static size_t bytes(int NG) {
-    return NG * group_bytes() + 2 * align16((size_t)NG * Op::ES * sizeof(T)) + align16(Op::ES * sizeof(T)) + 16;
+    return NG * group_bytes() + 2 * align16((size_t)NG * Op::ES * sizeof(T)) + align16(Op::ES * sizeof(T)) +
+           window_bytes() + 32;
   }
   __host__ __device__ static size_t payload_bytes() { return align16(Op::ES * sizeof(T)); }
   __host__ __device__ static size_t tile_state_bytes() { return 16 + 2 * payload_bytes(); }
@@ -158,62 +183,116 @@ __device__ __forceinline__ void publish(const Grp<Op::G>& g, unsigned char* ts, 
   if (g.lane == 0) st_release_u64((unsigned long long*)ts, ((epoch & 0xffffffffull) << 32) | status);
 }
 
-// status of tile state ts in this call: 1 aggregate, 2 inclusive prefix, 0 = wait bound hit
-template <int G>
-__device__ __forceinline__ unsigned wait_status(const Grp<G>& g, const unsigned char* ts, unsigned long long epoch) {
-  unsigned st = 0;
-  if (g.lane == 0) {
-    unsigned ns = 32;
-    for (long long it = 0; it < SPIN_LIMIT; ++it) {
-      const unsigned long long v = ld_acquire_u64((const unsigned long long*)ts);
-      if ((v >> 32) == (epoch & 0xffffffffull) && (v & 3ull)) { st = (unsigned)(v & 3ull); break; }
-      __nanosleep(ns);
-      if (ns < 2048) ns <<= 1;
-    }
-  }
-  st = __shfl_sync(g.mask, st, (threadIdx.x & 31) & ~(G - 1));
-  g.sync();
-  return st;
-}
-
+// Decoupled look-back of one tile, done by the whole block, a window of up to
+// WIN predecessor tiles per round.  Lane group 0 polls the flags (tile
+// j_hi - q for q < w); the round needs the tiles down to the nearest one that
+// already holds its inclusive prefix (or the whole window).  All threads fetch
+// those payloads together, and all lane groups fold them pairwise in a tree
+// of log2(WIN) levels (scan order: the older tile is the left operand) before
+// group 0 folds the result into the running exclusive prefix.  Every wait is
+// bounded: past SPIN_LIMIT polls the block records DEVERR_TIMEOUT and goes on
+// with what it has, so the kernel always terminates.
 template <class Op>
-__device__ void lookback(const Grp<Op::G>& g, const Ctx& c, unsigned long long epoch, long long tile_id,
-                         long long t_in_seq, const typename Op::T* agg, typename Op::T* excl, typename Op::T* b0,
-                         typename Op::T* b1, typename Op::T* b2, typename Op::T* sc, typename Op::TS* scs) {
+__device__ bool lookback(const Grp<Op::G>& g, int gid, int NG, const Ctx& c, unsigned long long epoch,
+                         long long tile_id, long long t_in_seq, const typename Op::T* agg, typename Op::T* excl,
+                         typename Op::T* tmp, typename Op::T* win, int* ctl, typename Op::T* sc,
+                         typename Op::TS* scs) {
   using T = typename Op::T;
+  constexpr int G = Op::G, ES = Op::ES, WIN = ScanSmem<Op>::WIN;
+  T* win2 = win + WIN * ES;
   unsigned char* ts = Op::tile_state(c, tile_id);
-  if (t_in_seq == 0) {
-    Op::identity(g, excl);
-    publish<Op>(g, ts, agg, 1, 2u, epoch);
-    g.sync();
-    return;
-  }
-  publish<Op>(g, ts, agg, 0, 1u, epoch);
-  T* acc = b0;
-  T* pay = b1;
-  T* tmp = b2;
-  Op::identity(g, acc);
-  g.sync();
   bool ok = true;
-  for (long long j = tile_id - 1;; --j) {
-    const unsigned char* tj = Op::tile_state(c, j);
-    const unsigned st = wait_status<Op::G>(g, tj, epoch);
-    if (st == 0) {
-      if (g.lane == 0) raise_err(c.ctr, DEVERR_TIMEOUT);
-      break;
+  if (t_in_seq == 0) {
+    if (gid == 0) {
+      Op::identity(g, excl);
+      publish<Op>(g, ts, agg, 1, 2u, epoch);
+      g.sync();
     }
-    const T* src = (const T*)(tj + 16 + (st == 2u ? 1 : 0) * ScanSmem<Op>::payload_bytes());
-    for (int e = g.lane; e < Op::ES; e += Op::G) pay[e] = __ldcg(src + e);
-    g.sync();
-    ok &= Op::combine(g, tmp, pay, acc, sc, scs, false);
-    T* t = acc; acc = tmp; tmp = t;
-    if (st == 2u) break;
+    __syncthreads();
+    return ok;
   }
-  for (int e = g.lane; e < Op::ES; e += Op::G) excl[e] = acc[e];
-  g.sync();
-  ok &= Op::combine(g, tmp, excl, agg, sc, scs, false);
-  publish<Op>(g, ts, tmp, 1, 2u, epoch);
-  if (!ok && g.lane == 0) raise_err(c.ctr, DEVERR_SINGULAR);
+  if (gid == 0) {
+    publish<Op>(g, ts, agg, 0, 1u, epoch);
+    Op::identity(g, excl);
+    g.sync();
+  }
+  __syncthreads();
+  const long long j_lo = tile_id - t_in_seq;  // first tile of this sequence
+  long long j_hi = tile_id - 1;
+  for (;;) {
+    const int w = (int)min((long long)WIN, j_hi - j_lo + 1);
+    if (gid == 0) {
+      unsigned ready = 0, pref = 0;
+      bool timed_out = true;
+      int need = w;
+      unsigned ns = 32;
+      for (long long it = 0; it < SPIN_LIMIT; ++it) {
+        for (int q = g.lane; q < w; q += G) {
+          if (!((ready >> q) & 1u)) {
+            const unsigned long long v = ld_acquire_u64((const unsigned long long*)Op::tile_state(c, j_hi - q));
+            if ((v >> 32) == (epoch & 0xffffffffull) && (v & 3ull)) {
+              ready |= 1u << q;
+              if ((v & 3ull) == 2ull) pref |= 1u << q;
+            }
+          }
+        }
+        ready = __reduce_or_sync(g.mask, ready);
+        pref = __reduce_or_sync(g.mask, pref);
+        need = pref ? __ffs(pref) : w;  // tiles q < need
+        const unsigned want = (need >= 32) ? 0xffffffffu : ((1u << need) - 1u);
+        if ((ready & want) == want) { timed_out = false; break; }
+        __nanosleep(ns);
+        if (ns < 1024) ns <<= 1;
+      }
+      if (g.lane == 0) {
+        ctl[0] = need;
+        ctl[1] = pref ? 1 : 0;
+        ctl[2] = timed_out ? 1 : 0;
+        if (timed_out) raise_err(c.ctr, DEVERR_TIMEOUT);
+      }
+    }
+    __syncthreads();
+    const int need = ctl[0];
+    const bool found = ctl[1] != 0;
+    if (ctl[2]) break;
+    // payloads: aggregates, except the last one when it holds a prefix
+    for (int idx = threadIdx.x; idx < need * ES; idx += blockDim.x) {
+      const int q = idx / ES, e = idx - (idx / ES) * ES;
+      const int slot = (found && q == need - 1) ? 1 : 0;
+      const T* srcp = (const T*)(Op::tile_state(c, j_hi - q) + 16 + slot * ScanSmem<Op>::payload_bytes());
+      win[idx] = __ldcg(srcp + e);
+    }
+    __syncthreads();
+    // tree: x_q = tile j_hi - q; product in scan order x_{k-1} (x) ... (x) x_0
+    T* cur = win;
+    T* nxt = win2;
+    int k = need;
+    while (k > 1) {
+      const int pairs = k >> 1;
+      for (int pi = gid; pi < pairs; pi += NG)
+        ok &= Op::combine(g, nxt + pi * ES, cur + (2 * pi + 1) * ES, cur + 2 * pi * ES, sc, scs, false);
+      if ((k & 1) && gid == pairs % NG)
+        for (int e = g.lane; e < ES; e += G) nxt[pairs * ES + e] = cur[(k - 1) * ES + e];
+      __syncthreads();
+      T* x = cur; cur = nxt; nxt = x;
+      k = pairs + (k & 1);
+    }
+    if (gid == 0) {
+      ok &= Op::combine(g, tmp, cur, excl, sc, scs, false);
+      for (int e = g.lane; e < ES; e += G) excl[e] = tmp[e];
+      g.sync();
+    }
+    __syncthreads();
+    if (found || j_hi - need < j_lo) break;
+    j_hi -= need;
+  }
+  if (gid == 0) {
+    ok &= Op::combine(g, tmp, excl, agg, sc, scs, false);
+    publish<Op>(g, ts, tmp, 1, 2u, epoch);
+    g.sync();
+  }
+  __syncthreads();
+  return ok;
 }
 
 template <class Op>
@@ -235,7 +314,9 @@ __global__ void __launch_bounds__(256) scan_kernel(Ctx c, int NG, int E) {
   T* ksA = (T*)(smem + NG * gb);
   T* ksB = (T*)((unsigned char*)ksA + align16((size_t)NG * ES * sizeof(T)));
   T* excl = (T*)((unsigned char*)ksB + align16((size_t)NG * ES * sizeof(T)));
-  long long* s_tile = (long long*)((unsigned char*)excl + align16(ES * sizeof(T)));
+  T* win = (T*)((unsigned char*)excl + align16(ES * sizeof(T)));
+  long long* s_tile = (long long*)((unsigned char*)win + ScanSmem<Op>::window_bytes());
+  int* ctl = (int*)(s_tile + 1);
 
   const unsigned long long epoch = c.ctr->epoch;
   const long long total = Op::total_tiles(c);
@@ -286,8 +367,7 @@ __global__ void __launch_bounds__(256) scan_kernel(Ctx c, int NG, int E) {
       T* x = src; src = dst; dst = x;
     }
     // 3. tile prefix
-    if (gid == 0) lookback<Op>(g, c, epoch, tile_id, t, src + (NG - 1) * ES, excl, b0, b1, b2, sc, scs);
-    __syncthreads();
+    ok &= lookback<Op>(g, gid, NG, c, epoch, tile_id, t, src + (NG - 1) * ES, excl, b2, win, ctl, sc, scs);
     // 4. results from the exclusive prefixes
     if (cnt > 0) {
       T* st = b0;
@@ -303,7 +383,7 @@ __global__ void __launch_bounds__(256) scan_kernel(Ctx c, int NG, int E) {
         g.sync();
         ok &= Op::combine(g, nx, st, b1, sc, scs, true);
         T* x = st; st = nx; nx = x;
-        Op::store(g, st, c, s, p0 + e, N);
+        Op::store(g, st, c, s, p0 + e, N, sc, scs);
         g.sync();
       }
     }
@@ -379,7 +459,7 @@ __device__ __forceinline__ bool spd_inverse(const T (&a)[N][N], T (&inv)[N][N]) 
 // recovery reuses.  Runs in TR (float64 except in the float32 mode).
 // ===========================================================================
 template <int NX, class T, class TR>
-__global__ void __launch_bounds__(128) interval_setup_kernel(Ctx c) {
+__global__ void __launch_bounds__(64) interval_setup_kernel(Ctx c) {
   constexpr int NN = NX * NX;
   using RL = Rec<NX>;
   using SLy = SL<NX>;
@@ -404,7 +484,7 @@ __global__ void __launch_bounds__(128) interval_setup_kernel(Ctx c) {
       for (int q = 0; q < NX; ++q) P[r][q] = (TR)c.P0[(long long)s * NN + r * NX + q];
     }
   } else {
-    const T* f = (const T*)c.fout + (gi - 1) * (NX + NN);
+    const TR* f = (const TR*)c.fout + (gi - 1) * (NX + NN);
 #pragma unroll
     for (int r = 0; r < NX; ++r) {
       mv[r] = (TR)f[r];
@@ -736,270 +816,203 @@ __global__ void __launch_bounds__(128) interval_setup_kernel(Ctx c) {
 }
 
 // ===========================================================================
-// fast-rate recovery (Remarks 1 and 3): one thread per fast step (k, i).
-// Per slow interval (shared by its l fast steps, computed once per block):
-//   dm = m^s_{k+1,1} - A m^f_{k,l},  dP = P^s_{k+1,1} - P^-_{k+1,1},
-//   om = Z dm,  Om = Z dP Z^T          (so that G_i dm = P^f_{il} om and
-//                                       G_i dP G_i^T = P^f_{il} Om P^f_{il}^T)
-// Per fast step, with the record of the interval:
-//   U_i   = A^i X + V_i H^T
-//   m^f_i = A^i m + U_i kap
+// fast-rate recovery (Remarks 1 and 3): one thread per fast step (k, i), a
+// flat grid over every fast step of the call.  With the record of interval k
+// and the smoothing terms (Om_k, om_k) formed by the smoother scan:
+//   U_i    = A^i X + V_i H^T
+//   m^f_i  = A^i m + U_i kap
 //   P^f_ii = A^i P A^{iT} + Qc_i - (U_i S_y^-1) U_i^T
 //   P^f_il = A^i (P A^{lT}) + Cov(e_i,e_l) - U_i (S_y^-1 U_l^T)
-//   m^s_i = m^f_i + P^f_il om,   P^s_ii = P^f_ii + (P^f_il Om) P^f_il^T
-// which is Eq. (17) and Eq. (21) with G_{k,i} = P^f_{k,i,l} A^T (P^-_{k+1,1})^-1
+//   m^s_i  = m^f_i + P^f_il om,   P^s_ii = P^f_ii + (P^f_il Om) P^f_il^T
+// which is Eq. (17) and Eq. (21) with G_{k,i} = P^f_{k,i,l} A^T (P^-_{k+1,1})^-1,
 // grouped so that no n x n product is repeated per fast step.  The last
 // interval is smoothed = filtered (E_N = 0).  Covariances are formed on the
 // upper triangle and mirrored (exactly symmetric).
 // ===========================================================================
-template <int NX, class T, class TR>
-__global__ void __launch_bounds__(256) recover_kernel(Ctx c) {
+template <int NX, class TR>
+__global__ void __launch_bounds__(128) recover_kernel(Ctx c) {
   constexpr int NN = NX * NX, NT = NX * (NX + 1) / 2;
   using RL = Rec<NX>;
-  extern __shared__ __align__(16) unsigned char rsm[];
-  __shared__ long long s_chunk;
   if (!c.ctr->call_ok) return;
-  const long long total = c.ctr->total_chunks;
+  const long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (f >= c.total_fast) return;
   const int m = c.ny;
-  for (;;) {
-    __syncthreads();
-    if (threadIdx.x == 0) s_chunk = (long long)atomicAdd(&c.ctr->ticket[2], 1u);
-    __syncthreads();
-    const long long ch = s_chunk;
-    if (ch >= total) break;
-    const int s = find_segment(c.meta.chunk_off, c.n_seq, ch);
-    const int C = c.meta.chunk_C[s], l = c.meta.ratio[s], N = c.meta.nslow[s];
-    const long long k0 = (ch - c.meta.chunk_off[s]) * C;
-    const int nk = (int)min((long long)C, (long long)N - k0);
-    const long long off_slow = c.meta.off_slow[s], off_fast = c.meta.off_fast[s];
-    const double* md = c.model + (long long)s * c.ml.stride;
-    const double* A1 = md + c.ml.Apow + NN;
-    TR* Om = (TR*)rsm;                   // [C][NN]
-    TR* om = Om + (size_t)C * NN;        // [C][NX]
-    const bool smooth = c.smoothing != 0;
-    if (smooth) {
-      for (int j = threadIdx.x; j < nk; j += blockDim.x) {
-        const long long k = k0 + j;
-        if (k >= N - 1) continue;
-        const TR* rc = (const TR*)c.rec + (off_slow + k) * RL::SIZE;
-        const T* so = (const T*)c.sout + (off_slow + k + 1) * (NX + NN);
-        TR Z[NX][NX], dm[NX], ZdP[NX][NX];
+  const int s = find_segment(c.meta.off_fast, c.n_seq, f);
+  const int l = c.meta.ratio[s], N = c.meta.nslow[s];
+  const long long loc = f - c.meta.off_fast[s];
+  const long long k = loc / l;
+  const int i = (int)(loc - k * l) + 1;
+  const long long row = c.meta.off_slow[s] + k;
+  const double* md = c.model + (long long)s * c.ml.stride;
+  const TR* rc = (const TR*)c.rec + row * RL::SIZE;
+  const double* Ai = md + c.ml.Apow + (long long)i * NN;
+  const double* VHi = md + c.ml.VH + (long long)(i - 1) * NX * m;
+  const double* Qci = md + c.ml.Qc + (long long)(i - 1) * NN;
+  const double* Qli = md + c.ml.Ql + (long long)(i - 1) * NN;
+  const bool smooth = c.smoothing != 0;
+  TR a[NX][NX];
 #pragma unroll
-        for (int r = 0; r < NX; ++r)
+  for (int r = 0; r < NX; ++r)
 #pragma unroll
-          for (int q = 0; q < NX; ++q) Z[r][q] = rc[RL::Z + r * NX + q];
+    for (int q = 0; q < NX; ++q) a[r][q] = (TR)__ldg(Ai + r * NX + q);
+  // U_i = A^i X + V_i H^T
+  TR U[NX][MY];
 #pragma unroll
-        for (int r = 0; r < NX; ++r) {
-          TR v = (TR)so[r];
+  for (int r = 0; r < NX; ++r)
 #pragma unroll
-          for (int q = 0; q < NX; ++q) v = fma(-(TR)A1[r * NX + q], rc[RL::ml + q], v);
-          dm[r] = v;
-        }
+    for (int jj = 0; jj < MY; ++jj) {
+      TR v = TR(0);
+      if (jj < m) {
+        v = (TR)__ldg(VHi + r * m + jj);
 #pragma unroll
-        for (int r = 0; r < NX; ++r) {
-          TR v = TR(0);
-#pragma unroll
-          for (int q = 0; q < NX; ++q) v = fma(Z[r][q], dm[q], v);
-          om[j * NX + r] = v;
-        }
-#pragma unroll
-        for (int r = 0; r < NX; ++r)
-#pragma unroll
-          for (int q = 0; q < NX; ++q) {
-            TR v = TR(0);
-#pragma unroll
-            for (int t = 0; t < NX; ++t) v = fma(Z[r][t], (TR)so[NX + t * NX + q] - rc[RL::Pm + t * NX + q], v);
-            ZdP[r][q] = v;
-          }
-#pragma unroll
-        for (int r = 0; r < NX; ++r)
-#pragma unroll
-          for (int q = r; q < NX; ++q) {
-            TR v = TR(0);
-#pragma unroll
-            for (int t = 0; t < NX; ++t) v = fma(ZdP[r][t], Z[q][t], v);
-            Om[j * NN + r * NX + q] = v;
-            Om[j * NN + q * NX + r] = v;
-          }
+        for (int q = 0; q < NX; ++q) v = fma(a[r][q], rc[RL::X + q * MY + jj], v);
       }
+      U[r][jj] = v;
     }
-    __syncthreads();
-    const int nf = nk * l;
-    for (int f = threadIdx.x; f < nf; f += blockDim.x) {
-      const int j = f / l;
-      const int i = f - j * l + 1;
-      const long long k = k0 + j;
-      const TR* rc = (const TR*)c.rec + (off_slow + k) * RL::SIZE;
-      const double* Ai = md + c.ml.Apow + (long long)i * NN;
-      const double* VHi = md + c.ml.VH + (long long)(i - 1) * NX * m;
-      const double* Qci = md + c.ml.Qc + (long long)(i - 1) * NN;
-      const double* Qli = md + c.ml.Ql + (long long)(i - 1) * NN;
-      TR a[NX][NX];
+  // m^f_i = A^i m + U_i kap
+  TR mf[NX];
 #pragma unroll
-      for (int r = 0; r < NX; ++r)
+  for (int r = 0; r < NX; ++r) {
+    TR v = TR(0);
 #pragma unroll
-        for (int q = 0; q < NX; ++q) a[r][q] = (TR)Ai[r * NX + q];
-      // U_i = A^i X + V_i H^T
-      TR U[NX][MY];
+    for (int q = 0; q < NX; ++q) v = fma(a[r][q], rc[RL::mv + q], v);
 #pragma unroll
-      for (int r = 0; r < NX; ++r)
+    for (int jj = 0; jj < MY; ++jj)
+      if (jj < m) v = fma(U[r][jj], rc[RL::kap + jj], v);
+    mf[r] = v;
+  }
+  const bool smooth_k = smooth && (k < N - 1);
+  // P^f_il = A^i Pl + Cov(e_i,e_l) - U_i SUl
+  TR Pfl[NX][NX];
+  if (smooth_k) {
 #pragma unroll
-        for (int jj = 0; jj < MY; ++jj) {
-          TR v = TR(0);
-          if (jj < m) {
-            v = (TR)VHi[r * m + jj];
+    for (int r = 0; r < NX; ++r)
 #pragma unroll
-            for (int q = 0; q < NX; ++q) v = fma(a[r][q], rc[RL::X + q * MY + jj], v);
-          }
-          U[r][jj] = v;
-        }
-      // m^f_i = A^i m + U_i kap
-      TR mf[NX];
+      for (int q = 0; q < NX; ++q) {
+        TR v = (TR)__ldg(Qli + r * NX + q);
 #pragma unroll
-      for (int r = 0; r < NX; ++r) {
-        TR v = TR(0);
-#pragma unroll
-        for (int q = 0; q < NX; ++q) v = fma(a[r][q], rc[RL::mv + q], v);
+        for (int t = 0; t < NX; ++t) v = fma(a[r][t], rc[RL::Pl + t * NX + q], v);
 #pragma unroll
         for (int jj = 0; jj < MY; ++jj)
-          if (jj < m) v = fma(U[r][jj], rc[RL::kap + jj], v);
-        mf[r] = v;
+          if (jj < m) v = fma(-U[r][jj], rc[RL::SUl + jj * NX + q], v);
+        Pfl[r][q] = v;
       }
-      const bool smooth_k = smooth && (k < N - 1);
-      // P^f_il = A^i Pl + Cov(e_i,e_l) - U_i SUl
-      TR Pfl[NX][NX];
-      if (smooth_k) {
+  }
+  // P^f_ii (upper triangle)
+  TR Pf[NT];
+  {
+    TR US[NX][MY], AP[NX][NX];
 #pragma unroll
-        for (int r = 0; r < NX; ++r)
+    for (int r = 0; r < NX; ++r)
 #pragma unroll
-          for (int q = 0; q < NX; ++q) {
-            TR v = (TR)Qli[r * NX + q];
+      for (int jj = 0; jj < MY; ++jj) {
+        TR v = TR(0);
+        if (jj < m) {
 #pragma unroll
-            for (int t = 0; t < NX; ++t) v = fma(a[r][t], rc[RL::Pl + t * NX + q], v);
-#pragma unroll
-            for (int jj = 0; jj < MY; ++jj)
-              if (jj < m) v = fma(-U[r][jj], rc[RL::SUl + jj * NX + q], v);
-            Pfl[r][q] = v;
-          }
+          for (int j2 = 0; j2 < MY; ++j2)
+            if (j2 < m) v = fma(U[r][j2], rc[RL::Si + j2 * MY + jj], v);
+        }
+        US[r][jj] = v;
       }
-      // P^f_ii (upper triangle)
-      TR Pf[NT];
-      {
-        TR US[NX][MY], AP[NX][NX];
 #pragma unroll
-        for (int r = 0; r < NX; ++r)
+    for (int r = 0; r < NX; ++r)
 #pragma unroll
-          for (int jj = 0; jj < MY; ++jj) {
-            TR v = TR(0);
-            if (jj < m) {
+      for (int q = 0; q < NX; ++q) {
+        TR v = TR(0);
 #pragma unroll
-              for (int j2 = 0; j2 < MY; ++j2)
-                if (j2 < m) v = fma(U[r][j2], rc[RL::Si + j2 * MY + jj], v);
-            }
-            US[r][jj] = v;
-          }
+        for (int t = 0; t < NX; ++t) v = fma(a[r][t], rc[RL::P + t * NX + q], v);
+        AP[r][q] = v;
+      }
+    int u = 0;
 #pragma unroll
-        for (int r = 0; r < NX; ++r)
+    for (int r = 0; r < NX; ++r)
 #pragma unroll
-          for (int q = 0; q < NX; ++q) {
-            TR v = TR(0);
+      for (int q = r; q < NX; ++q) {
+        TR v = (TR)__ldg(Qci + r * NX + q);
 #pragma unroll
-            for (int t = 0; t < NX; ++t) v = fma(a[r][t], rc[RL::P + t * NX + q], v);
-            AP[r][q] = v;
-          }
-        int u = 0;
+        for (int t = 0; t < NX; ++t) v = fma(AP[r][t], a[q][t], v);
+#pragma unroll
+        for (int jj = 0; jj < MY; ++jj)
+          if (jj < m) v = fma(-US[r][jj], U[q][jj], v);
+        Pf[u++] = v;
+      }
+  }
+  const long long fi = f;
+  const long long si = row;
+  auto store_state = [&](double* mo, double* co, double* smo, double* sco, const TR* mvv, const TR* Pu) {
+    if (mo) {
+#pragma unroll
+      for (int r = 0; r < NX; ++r) mo[fi * NX + r] = (double)mvv[r];
+    }
+    if (co) {
+      double* dst = co + fi * NN;
+      int uu = 0;
+#pragma unroll
+      for (int r = 0; r < NX; ++r)
+#pragma unroll
+        for (int q = r; q < NX; ++q) {
+          const double v = (double)Pu[uu++];
+          dst[r * NX + q] = v;
+          dst[q * NX + r] = v;
+        }
+    }
+    if (i == l) {
+      if (smo) {
+#pragma unroll
+        for (int r = 0; r < NX; ++r) smo[si * NX + r] = (double)mvv[r];
+      }
+      if (sco) {
+        double* dst = sco + si * NN;
+        int uu = 0;
 #pragma unroll
         for (int r = 0; r < NX; ++r)
 #pragma unroll
           for (int q = r; q < NX; ++q) {
-            TR v = (TR)Qci[r * NX + q];
-#pragma unroll
-            for (int t = 0; t < NX; ++t) v = fma(AP[r][t], a[q][t], v);
-#pragma unroll
-            for (int jj = 0; jj < MY; ++jj)
-              if (jj < m) v = fma(-US[r][jj], U[q][jj], v);
-            Pf[u++] = v;
+            const double v = (double)Pu[uu++];
+            dst[r * NX + q] = v;
+            dst[q * NX + r] = v;
           }
       }
-      const long long fi = off_fast + k * l + (i - 1);
-      double* fm_out = smooth ? c.ffast_mean : c.fast_mean;
-      double* fc_out = smooth ? c.ffast_cov : c.fast_cov;
-      double* sm_out = smooth ? c.fslow_mean : c.slow_mean;
-      double* sc_out = smooth ? c.fslow_cov : c.slow_cov;
-      auto store_state = [&](double* mo, double* co, double* smo, double* sco, const TR* mvv, const TR* Pu) {
-        if (mo) {
+    }
+  };
+  // filtered outputs (the call's outputs for a filter, the optional extras for a smoother)
+  if (!smooth) {
+    store_state(c.fast_mean, c.fast_cov, c.slow_mean, c.slow_cov, mf, Pf);
+    return;
+  }
+  store_state(c.ffast_mean, c.ffast_cov, c.fslow_mean, c.fslow_cov, mf, Pf);
+  if (smooth_k) {
+    const TR* Om = (const TR*)c.sfin + row * (NN + NX);
+    const TR* om = Om + NN;
+    TR T1[NX][NX];
 #pragma unroll
-          for (int r = 0; r < NX; ++r) mo[fi * NX + r] = (double)mvv[r];
-        }
-        if (co) {
-          double* dst = co + fi * NN;
-          int uu = 0;
+    for (int r = 0; r < NX; ++r)
 #pragma unroll
-          for (int r = 0; r < NX; ++r)
+      for (int q = 0; q < NX; ++q) {
+        TR v = TR(0);
 #pragma unroll
-            for (int q = r; q < NX; ++q) {
-              const double v = (double)Pu[uu++];
-              dst[r * NX + q] = v;
-              dst[q * NX + r] = v;
-            }
-        }
-        if (i == l) {
-          const long long si = off_slow + k;
-          if (smo) {
-#pragma unroll
-            for (int r = 0; r < NX; ++r) smo[si * NX + r] = (double)mvv[r];
-          }
-          if (sco) {
-            double* dst = sco + si * NN;
-            int uu = 0;
-#pragma unroll
-            for (int r = 0; r < NX; ++r)
-#pragma unroll
-              for (int q = r; q < NX; ++q) {
-                const double v = (double)Pu[uu++];
-                dst[r * NX + q] = v;
-                dst[q * NX + r] = v;
-              }
-          }
-        }
-      };
-      // filtered outputs (the call's outputs for a filter, the optional extras for a smoother)
-      store_state(fm_out, fc_out, sm_out, sc_out, mf, Pf);
-      if (!smooth) continue;
-      if (smooth_k) {
-        const TR* Omj = Om + (size_t)j * NN;
-        const TR* omj = om + (size_t)j * NX;
-        TR T1[NX][NX];
-#pragma unroll
-        for (int r = 0; r < NX; ++r)
-#pragma unroll
-          for (int q = 0; q < NX; ++q) {
-            TR v = TR(0);
-#pragma unroll
-            for (int t = 0; t < NX; ++t) v = fma(Pfl[r][t], Omj[t * NX + q], v);
-            T1[r][q] = v;
-          }
-        int u = 0;
-#pragma unroll
-        for (int r = 0; r < NX; ++r)
-#pragma unroll
-          for (int q = r; q < NX; ++q) {
-            TR v = Pf[u];
-#pragma unroll
-            for (int t = 0; t < NX; ++t) v = fma(T1[r][t], Pfl[q][t], v);
-            Pf[u++] = v;
-          }
-#pragma unroll
-        for (int r = 0; r < NX; ++r) {
-          TR v = mf[r];
-#pragma unroll
-          for (int t = 0; t < NX; ++t) v = fma(Pfl[r][t], omj[t], v);
-          mf[r] = v;
-        }
+        for (int t = 0; t < NX; ++t) v = fma(Pfl[r][t], Om[t * NX + q], v);
+        T1[r][q] = v;
       }
-      store_state(c.fast_mean, c.fast_cov, c.slow_mean, c.slow_cov, mf, Pf);
+    int u = 0;
+#pragma unroll
+    for (int r = 0; r < NX; ++r)
+#pragma unroll
+      for (int q = r; q < NX; ++q) {
+        TR v = Pf[u];
+#pragma unroll
+        for (int t = 0; t < NX; ++t) v = fma(T1[r][t], Pfl[q][t], v);
+        Pf[u++] = v;
+      }
+#pragma unroll
+    for (int r = 0; r < NX; ++r) {
+      TR v = mf[r];
+#pragma unroll
+      for (int t = 0; t < NX; ++t) v = fma(Pfl[r][t], om[t], v);
+      mf[r] = v;
     }
   }
+  store_state(c.fast_mean, c.fast_cov, c.slow_mean, c.slow_cov, mf, Pf);
 }
 
 // ===========================================================================
@@ -1011,10 +1024,10 @@ inline void set_smem_attr(const void* fn, size_t bytes) {
 }
 
 template <int NX, class T, class TS, class TR>
-int query_shapes_t(int scan_groups, int scan_elems, int recover_threads, int recover_chunk, int sm_count,
-                   long long total_slow, int n_seq, Shapes* sh) {
+int query_shapes_t(int scan_groups, int scan_elems, int recover_threads, int sm_count, long long total_slow,
+                   int n_seq, Shapes* sh) {
   using FOp = FilterOp<NX, T, TS>;
-  using SOp = SmootherOp<NX, T>;
+  using SOp = SmootherOp<NX, T, TR>;
   constexpr int G = FOp::G;
   const int NG = scan_groups;
   const int threads = NG * G;
@@ -1031,34 +1044,25 @@ int query_shapes_t(int scan_groups, int scan_elems, int recover_threads, int rec
   sh->grid_f = (int)std::max(1LL, std::min((long long)std::max(nb, 1) * sm_count, tiles));
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, scan_kernel<SOp>, threads, sh->smem_s);
   sh->grid_s = (int)std::max(1LL, std::min((long long)std::max(nb, 1) * sm_count, tiles));
-  sh->grid_setup = (int)((total_slow + 127) / 128);
+  sh->grid_setup = (int)((total_slow + 63) / 64);
   sh->recover_threads = recover_threads;
-  sh->recover_chunk = recover_chunk;
-  // shared memory per recovery block: C_max intervals of (Om, om)
-  const size_t per_int = (size_t)(NX * NX + NX) * sizeof(TR);
-  int cmax = (int)std::min<size_t>(32768 / per_int, 4096);
-  if (cmax < 1) cmax = 1;
-  sh->smem_r = (size_t)cmax * per_int;
-  set_smem_attr<void>((const void*)recover_kernel<NX, T, TR>, sh->smem_r);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, recover_kernel<NX, T, TR>, recover_threads, sh->smem_r);
-  sh->grid_r = std::max(1, std::max(nb, 1) * sm_count);
   if (cudaGetLastError() != cudaSuccess) return SRTM_ERR_CUDA;
   return SRTM_OK;
 }
 
 template <int NX>
-int query_shapes(srtm_precision prec, int scan_groups, int scan_elems, int recover_threads, int recover_chunk,
-                 int sm_count, long long total_slow, int n_seq, Shapes* sh) {
+int query_shapes(srtm_precision prec, int scan_groups, int scan_elems, int recover_threads, int sm_count,
+                 long long total_slow, int n_seq, Shapes* sh) {
   switch (prec) {
     case SRTM_FP64:
-      return query_shapes_t<NX, double, double, double>(scan_groups, scan_elems, recover_threads, recover_chunk,
-                                                         sm_count, total_slow, n_seq, sh);
+      return query_shapes_t<NX, double, double, double>(scan_groups, scan_elems, recover_threads, sm_count,
+                                                         total_slow, n_seq, sh);
     case SRTM_MIXED:
-      return query_shapes_t<NX, float, double, double>(scan_groups, scan_elems, recover_threads, recover_chunk,
-                                                        sm_count, total_slow, n_seq, sh);
+      return query_shapes_t<NX, float, double, double>(scan_groups, scan_elems, recover_threads, sm_count,
+                                                        total_slow, n_seq, sh);
     case SRTM_FP32:
-      return query_shapes_t<NX, float, float, float>(scan_groups, scan_elems, recover_threads, recover_chunk,
-                                                      sm_count, total_slow, n_seq, sh);
+      return query_shapes_t<NX, float, float, float>(scan_groups, scan_elems, recover_threads, sm_count,
+                                                      total_slow, n_seq, sh);
   }
   return SRTM_ERR_ARG;
 }
@@ -1068,16 +1072,17 @@ int query_shapes(srtm_precision prec, int scan_groups, int scan_elems, int recov
 template <int NX, class T, class TS, class TR>
 int launch_t(const Ctx& c, const Shapes& sh, cudaStream_t st, cudaEvent_t* ev) {
   using FOp = FilterOp<NX, T, TS>;
-  using SOp = SmootherOp<NX, T>;
+  using SOp = SmootherOp<NX, T, TR>;
   constexpr int G = FOp::G;
   scan_kernel<FOp><<<sh.grid_f, sh.scan_groups_f * G, sh.smem_f, st>>>(c, sh.scan_groups_f, sh.scan_elems_f);
   if (ev) cudaEventRecord(ev[0], st);
-  interval_setup_kernel<NX, T, TR><<<sh.grid_setup, 128, 0, st>>>(c);
+  interval_setup_kernel<NX, T, TR><<<sh.grid_setup, 64, 0, st>>>(c);
   if (ev) cudaEventRecord(ev[1], st);
   if (c.smoothing)
     scan_kernel<SOp><<<sh.grid_s, sh.scan_groups_s * G, sh.smem_s, st>>>(c, sh.scan_groups_s, sh.scan_elems_s);
   if (ev) cudaEventRecord(ev[2], st);
-  recover_kernel<NX, T, TR><<<sh.grid_r, sh.recover_threads, sh.smem_r, st>>>(c);
+  const long long blocks = (c.total_fast + sh.recover_threads - 1) / sh.recover_threads;
+  recover_kernel<NX, TR><<<(unsigned)blocks, sh.recover_threads, 0, st>>>(c);
   if (ev) cudaEventRecord(ev[3], st);
   return cudaGetLastError() == cudaSuccess ? SRTM_OK : SRTM_ERR_CUDA;
 }
@@ -1097,4 +1102,4 @@ int launch_device_path(const Ctx& c, srtm_precision prec, const Shapes& sh, cuda
 #define SRTM_INSTANTIATE(NXV)                                                                                \
   template int srtm::launch_device_path<NXV>(const srtm::Ctx&, srtm_precision, const srtm::Shapes&,          \
                                              cudaStream_t, cudaEvent_t*);                                    \
-  template int srtm::query_shapes<NXV>(srtm_precision, int, int, int, int, int, long long, int, srtm::Shapes*);
+  template int srtm::query_shapes<NXV>(srtm_precision, int, int, int, int, long long, int, srtm::Shapes*);

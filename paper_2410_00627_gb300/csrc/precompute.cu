@@ -1,7 +1,7 @@
 // precompute.cu -- per-call metadata and per-model constants (float64).
 //
-// meta_kernel (one block): validates the batch metadata, forms the row,
-// tile and chunk offsets of every sequence, resets the tickets and bumps the
+// meta_kernel (one block): validates the batch metadata, forms the row and
+// tile offsets of every sequence, resets the tickets and bumps the
 // call epoch that tags the scans' look-back flags.
 //
 // precompute_kernel (one block per sequence): the constants of the lifted
@@ -24,7 +24,7 @@ namespace srtm {
 
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024) meta_kernel(Ctx c) {
-  __shared__ long long sc[5][1024];
+  __shared__ long long sc[4][1024];
   __shared__ int s_bad;
   const int tid = threadIdx.x, nt = blockDim.x;
   if (tid == 0) {
@@ -35,52 +35,44 @@ __global__ void __launch_bounds__(1024) meta_kernel(Ctx c) {
   __syncthreads();
   const int per = (c.n_seq + nt - 1) / nt;
   const int s0 = min(c.n_seq, tid * per), s1 = min(c.n_seq, s0 + per);
-  long long acc[5] = {0, 0, 0, 0, 0};
+  long long acc[4] = {0, 0, 0, 0};
   int bad = 0;
   for (int s = s0; s < s1; ++s) {
     const int r = c.in_ratio ? c.in_ratio[s] : c.uniform_ratio;
     const int n = c.in_nslow ? c.in_nslow[s] : c.uniform_nslow;
     if (r < 1 || r > c.max_ratio || n < 1) { bad = 1; continue; }
-    int C = (c.chunk_fast + r - 1) / r;
-    C = max(1, min(C, c.chunk_cmax));
     acc[0] += n;
     acc[1] += (long long)n * r;
     acc[2] += (n + c.tile_f - 1) / c.tile_f;
     acc[3] += (n + c.tile_s - 1) / c.tile_s;
-    acc[4] += (n + C - 1) / C;
   }
   if (bad) atomicOr(&s_bad, 1);
-  for (int q = 0; q < 5; ++q) sc[q][tid] = acc[q];
+  for (int q = 0; q < 4; ++q) sc[q][tid] = acc[q];
   __syncthreads();
   // inclusive Hillis-Steele scan of the per-thread sums
   for (int d = 1; d < nt; d <<= 1) {
-    long long v[5];
-    for (int q = 0; q < 5; ++q) v[q] = (tid >= d) ? sc[q][tid - d] : 0;
+    long long v[4];
+    for (int q = 0; q < 4; ++q) v[q] = (tid >= d) ? sc[q][tid - d] : 0;
     __syncthreads();
-    for (int q = 0; q < 5; ++q) sc[q][tid] += v[q];
+    for (int q = 0; q < 4; ++q) sc[q][tid] += v[q];
     __syncthreads();
   }
-  long long run[5];
-  for (int q = 0; q < 5; ++q) run[q] = (tid > 0) ? sc[q][tid - 1] : 0;
+  long long run[4];
+  for (int q = 0; q < 4; ++q) run[q] = (tid > 0) ? sc[q][tid - 1] : 0;
   for (int s = s0; s < s1; ++s) {
     const int r = c.in_ratio ? c.in_ratio[s] : c.uniform_ratio;
     const int n = c.in_nslow ? c.in_nslow[s] : c.uniform_nslow;
     const int rr = max(r, 1), nn = max(n, 1);
-    int C = (c.chunk_fast + rr - 1) / rr;
-    C = max(1, min(C, c.chunk_cmax));
     c.meta.ratio[s] = r;
     c.meta.nslow[s] = n;
-    c.meta.chunk_C[s] = C;
     c.meta.off_slow[s] = run[0];
     c.meta.off_fast[s] = run[1];
     c.meta.tile_off_f[s] = run[2];
     c.meta.tile_off_s[s] = run[3];
-    c.meta.chunk_off[s] = run[4];
     run[0] += nn;
     run[1] += (long long)nn * rr;
     run[2] += (nn + c.tile_f - 1) / c.tile_f;
     run[3] += (nn + c.tile_s - 1) / c.tile_s;
-    run[4] += (nn + C - 1) / C;
   }
   __syncthreads();
   if (tid == nt - 1) {
@@ -89,10 +81,8 @@ __global__ void __launch_bounds__(1024) meta_kernel(Ctx c) {
     c.meta.off_fast[c.n_seq] = sc[1][nt - 1];
     c.meta.tile_off_f[c.n_seq] = sc[2][nt - 1];
     c.meta.tile_off_s[c.n_seq] = sc[3][nt - 1];
-    c.meta.chunk_off[c.n_seq] = sc[4][nt - 1];
     c.ctr->total_tiles_f = ok ? sc[2][nt - 1] : 0;
     c.ctr->total_tiles_s = ok ? sc[3][nt - 1] : 0;
-    c.ctr->total_chunks = ok ? sc[4][nt - 1] : 0;
     c.ctr->call_ok = ok ? 1u : 0u;
     if (!ok) atomicOr(&c.ctr->err, DEVERR_META);
   }
@@ -160,120 +150,152 @@ __device__ bool small_inverse(int n, double* a, double* inv) {
   return ok;
 }
 
-__global__ void __launch_bounds__(128) precompute_kernel(Ctx c) {
+// Shared-memory footprint of precompute_kernel: inputs and per-warp scratch,
+// plus the A^i, S_q, Qc_i and V_i tables when they fit.
+constexpr int PRE_BASE = 64 + 64 + 32 + 16 + 64 + 8 + 8 + 64 + 4 * 6 * 64;  // doubles
+constexpr size_t PRE_SMEM_CAP = 200 * 1024;
+inline size_t precompute_table_doubles(int n, int L) { return (size_t)(4 * L + 1) * n * n; }
+
+__global__ void __launch_bounds__(128) precompute_kernel(Ctx c, int tables_in_smem) {
+  extern __shared__ __align__(16) double dsm[];
   if (!c.ctr->call_ok) return;
   const int s = blockIdx.x;
   const int n = c.nx, m = c.ny, nn = n * n, l = c.meta.ratio[s];
   const ModelLayout L = c.ml;
   double* md = c.model + (long long)s * L.stride;
-  const double* A = c.F + (long long)s * nn;
-  const double* Q = c.Q + (long long)s * nn;
-  const double* H = c.H + (long long)s * m * n;
-  const double* R = c.R + (long long)s * m * m;
-  const double* m0 = c.m0 + (long long)s * n;
-  const double* P0 = c.P0 + (long long)s * nn;
-  const double* y0 = c.y + c.meta.off_slow[s] * m;
-  double* Apow = md + L.Apow;
-  double* Ssc = md + L.Ssc;
-  double* Qc = md + L.Qc;
-  double* Ql = md + L.Ql;
-  double* Vsc = md + L.Vsc;
-  double* VH = md + L.VH;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  __shared__ double sb[4][6][64];  // per warp six n x n scratch matrices (n <= 8)
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x, nt = blockDim.x;
+  double* sA = dsm;
+  double* sQ = sA + 64;
+  double* sH = sQ + 64;
+  double* sR = sH + 32;
+  double* sP0 = sR + 16;
+  double* sm0 = sP0 + 64;
+  double* sy0 = sm0 + 8;
+  double* sT = sy0 + 8;          // sum_{i=1..l} A^i
+  double* scr = sT + 64;         // per-warp scratch: 6 matrices of 64
+  double* wb = scr + warp * 6 * 64;
+  double *Ap, *Sp, *Qp, *Vp;
+  if (tables_in_smem) {
+    Ap = dsm + PRE_BASE;
+    Sp = Ap + (size_t)(l + 1) * nn;
+    Qp = Sp + (size_t)l * nn;
+    Vp = Qp + (size_t)l * nn;
+  } else {
+    Ap = md + L.Apow;
+    Sp = md + L.Ssc;
+    Qp = md + L.Qc;
+    Vp = md + L.Vsc;
+  }
   __shared__ int s_ok;
-  if (threadIdx.x == 0) s_ok = 1;
-
-  // --- phase A: powers and the running sums S_q (warp 0); Qc chain (warp 1)
-  if (warp == 0) {
-    double* cur = sb[0][0];
-    double* nxt = sb[0][1];
-    double* ssum = sb[0][2];
-    for (int e = lane; e < nn; e += 32) {
-      const double v = (e / n == e % n) ? 1.0 : 0.0;
-      cur[e] = v; ssum[e] = v; Apow[e] = v; Ssc[e] = v;
+  {
+    const double* F = c.F + (long long)s * nn;
+    const double* Q = c.Q + (long long)s * nn;
+    const double* H = c.H + (long long)s * m * n;
+    const double* R = c.R + (long long)s * m * m;
+    const double* P0 = c.P0 + (long long)s * nn;
+    const double* m0 = c.m0 + (long long)s * n;
+    const double* y0 = c.y + c.meta.off_slow[s] * m;
+    for (int e = tid; e < nn; e += nt) {
+      const int r = e / n, q = e - (e / n) * n;
+      sA[e] = F[e];
+      sQ[e] = 0.5 * (Q[e] + Q[q * n + r]);
+      md[L.Q + e] = sQ[e];
+      sP0[e] = P0[e];
+      Ap[e] = (r == q) ? 1.0 : 0.0;
+      Ap[nn + e] = F[e];
     }
+    for (int e = tid; e < m * n; e += nt) sH[e] = H[e];
+    for (int e = tid; e < m * m; e += nt) sR[e] = R[e];
+    for (int e = tid; e < n; e += nt) sm0[e] = m0[e];
+    for (int e = tid; e < m; e += nt) sy0[e] = y0[e];
+    if (tid == 0) s_ok = 1;
+  }
+  __syncthreads();
+  // --- A^i for i = 1..l by doubling: A^{h+t} = A^h A^t, t = 1..h, per round
+  for (int h = 1; h < l; h *= 2) {
+    const int cnt = min(h, l - h);
+    for (int t = warp; t < cnt; t += 4)
+      w_mm(n, n, n, Ap + (size_t)(h + 1 + t) * nn, Ap + (size_t)h * nn, false, Ap + (size_t)(1 + t) * nn, false,
+           nullptr, 1.0, lane);
+    __syncthreads();
+  }
+  // --- terms A^r Q A^{rT} (r = 0..l-1) into the Qc table, all warps
+  for (int r = warp; r < l; r += 4) {
+    double* t = wb;
+    w_mm(n, n, n, t, Ap + (size_t)r * nn, false, sQ, false, nullptr, 1.0, lane);
     __syncwarp();
-    for (int i = 1; i <= l; ++i) {
-      w_mm(n, n, n, nxt, cur, false, A, false, nullptr, 1.0, lane);
-      __syncwarp();
-      for (int e = lane; e < nn; e += 32) {
-        Apow[(long long)i * nn + e] = nxt[e];
-        ssum[e] += nxt[e];
-        if (i < l) Ssc[(long long)i * nn + e] = ssum[e];
-      }
-      double* t = cur; cur = nxt; nxt = t;
-      __syncwarp();
+    w_mm(n, n, n, Qp + (size_t)r * nn, t, false, Ap + (size_t)r * nn, true, nullptr, 1.0, lane);
+    __syncwarp();
+  }
+  __syncthreads();
+  // --- running sums: S_q = sum_{j<=q} A^j (q < l), sum_{i=1..l} A^i, and
+  //     Qc_i = sum_{r<i} A^r Q A^rT (symmetric: one thread per upper-triangle pair)
+  for (int e = tid; e < nn; e += nt) {
+    const int r = e / n, q = e - (e / n) * n;
+    double acc = (r == q) ? 1.0 : 0.0;
+    Sp[e] = acc;
+    for (int j = 1; j < l; ++j) {
+      acc += Ap[(size_t)j * nn + e];
+      Sp[(size_t)j * nn + e] = acc;
     }
-    // ssum = sum_{i=0..l} A^i  ->  C_bar = H (ssum - I)
-    for (int e = lane; e < nn; e += 32) ssum[e] -= (e / n == e % n) ? 1.0 : 0.0;
-    __syncwarp();
-    w_mm(m, n, n, md + L.Cb, H, false, ssum, false, nullptr, 1.0, lane);
-  } else if (warp == 1) {
-    double* cur = sb[1][0];
-    double* t = sb[1][1];
-    double* nxt = sb[1][2];
-    for (int e = lane; e < nn; e += 32) {
-      const double q = 0.5 * (Q[e] + Q[(e % n) * n + e / n]);
-      cur[e] = q; Qc[e] = q; md[L.Q + e] = q;
-    }
-    __syncwarp();
-    for (int i = 2; i <= l; ++i) {
-      w_mm(n, n, n, t, A, false, cur, false, nullptr, 1.0, lane);
-      __syncwarp();
-      w_mm(n, n, n, nxt, t, false, A, true, md + L.Q, 1.0, lane);
-      w_sym(n, nxt, lane);
-      for (int e = lane; e < nn; e += 32) Qc[(long long)(i - 1) * nn + e] = nxt[e];
-      double* x = cur; cur = nxt; nxt = x;
-      __syncwarp();
+    sT[e] = acc + Ap[(size_t)l * nn + e] - ((r == q) ? 1.0 : 0.0);
+  }
+  for (int e = tid; e < nn; e += nt) {
+    const int r = e / n, q = e - (e / n) * n;
+    if (r > q) continue;
+    double acc = 0.0;
+    for (int j = 0; j < l; ++j) {
+      acc += 0.5 * (Qp[(size_t)j * nn + r * n + q] + Qp[(size_t)j * nn + q * n + r]);
+      Qp[(size_t)j * nn + r * n + q] = acc;
+      Qp[(size_t)j * nn + q * n + r] = acc;
     }
   }
   __syncthreads();
-  // --- phase B: V chain (warp 0); Cov(e_i, e_l) = Qc_i A^{(l-i)T} (warps 1..3)
+  // --- V chain (warp 0):  V_1 = Q S_{l-1}^T,  V_i = A V_{i-1} + Q S_{l-i}^T
+  //     Cov(e_i, e_l) = Qc_i A^{(l-i)T} (warps 1..3);  C_bar = H sum A^i (warp 1)
   if (warp == 0) {
-    double* cur = sb[0][0];
-    double* t = sb[0][1];
-    double* nxt = sb[0][2];
-    const double* Qs = md + L.Q;
-    w_mm(n, n, n, cur, Qs, false, Ssc + (long long)(l - 1) * nn, true, nullptr, 1.0, lane);
+    double* t = wb;
+    w_mm(n, n, n, Vp, sQ, false, Sp + (size_t)(l - 1) * nn, true, nullptr, 1.0, lane);
     __syncwarp();
-    for (int e = lane; e < nn; e += 32) Vsc[e] = cur[e];
     for (int i = 2; i <= l; ++i) {
-      w_mm(n, n, n, t, A, false, cur, false, nullptr, 1.0, lane);
+      w_mm(n, n, n, t, sA, false, Vp + (size_t)(i - 2) * nn, false, nullptr, 1.0, lane);
       __syncwarp();
-      w_mm(n, n, n, nxt, Qs, false, Ssc + (long long)(l - i) * nn, true, t, 1.0, lane);
-      __syncwarp();
-      for (int e = lane; e < nn; e += 32) Vsc[(long long)(i - 1) * nn + e] = nxt[e];
-      double* x = cur; cur = nxt; nxt = x;
+      w_mm(n, n, n, Vp + (size_t)(i - 1) * nn, sQ, false, Sp + (size_t)(l - i) * nn, true, t, 1.0, lane);
       __syncwarp();
     }
   } else {
+    if (warp == 1) w_mm(m, n, n, md + L.Cb, sH, false, sT, false, nullptr, 1.0, lane);
     for (int i = warp; i <= l; i += 3)
-      w_mm(n, n, n, Ql + (long long)(i - 1) * nn, Qc + (long long)(i - 1) * nn, false, Apow + (long long)(l - i) * nn,
+      w_mm(n, n, n, md + L.Ql + (size_t)(i - 1) * nn, Qp + (size_t)(i - 1) * nn, false, Ap + (size_t)(l - i) * nn,
            true, nullptr, 1.0, lane);
   }
   __syncthreads();
-  // --- phase C: V_i H^T for every i (all warps)
+  // --- V_i H^T (all warps); tables to global when they were in shared memory
   for (int i = warp + 1; i <= l; i += 4)
-    w_mm(n, n, m, VH + (long long)(i - 1) * n * m, Vsc + (long long)(i - 1) * nn, false, H, true, nullptr, 1.0, lane);
+    w_mm(n, n, m, md + L.VH + (size_t)(i - 1) * n * m, Vp + (size_t)(i - 1) * nn, false, sH, true, nullptr, 1.0,
+         lane);
+  if (tables_in_smem) {
+    for (size_t e = tid; e < (size_t)(l + 1) * nn; e += nt) md[L.Apow + e] = Ap[e];
+    for (size_t e = tid; e < (size_t)l * nn; e += nt) md[L.Qc + e] = Qp[e];
+  }
   __syncthreads();
-  // --- phase D: slow-model constants and the first filter element (warp 0)
+  // --- slow-model constants and the first filter element (warp 0)
   if (warp == 0) {
-    double* Vs = sb[0][0];   // sum_i V_i = Var(sum e)
-    double* t = sb[0][1];
-    double* MQM = sb[0][2];  // m x m
-    double* Rxi = sb[0][3];
-    double* wk = sb[0][4];
-    double* wk2 = sb[0][5];
+    double* Vs = wb;          // sum_i V_i = Var(sum e)
+    double* t = wb + 64;
+    double* MQM = wb + 128;   // m x m
+    double* Rxi = wb + 192;
+    double* wk = wb + 256;
+    double* wk2 = wb + 320;
     for (int e = lane; e < nn; e += 32) {
       double v = 0.0;
-      for (int i = 0; i < l; ++i) v += Vsc[(long long)i * nn + e];
+      for (int i = 0; i < l; ++i) v += Vp[(size_t)i * nn + e];
       Vs[e] = v;
     }
     w_sym(n, Vs, lane);
-    w_mm(m, n, n, t, H, false, Vs, false, nullptr, 1.0, lane);  // H Vs (m x n)
+    w_mm(m, n, n, t, sH, false, Vs, false, nullptr, 1.0, lane);  // H Vs (m x n)
     __syncwarp();
-    w_mm(m, n, m, MQM, t, false, H, true, R, 1.0, lane);          // R_x = H Vs H^T + R
+    w_mm(m, n, m, MQM, t, false, sH, true, sR, 1.0, lane);        // R_x = H Vs H^T + R
     w_sym(m, MQM, lane);
     for (int e = lane; e < m * m; e += 32) md[L.Rx + e] = MQM[e];
     __syncwarp();
@@ -283,14 +305,15 @@ __global__ void __launch_bounds__(128) precompute_kernel(Ctx c) {
     }
     __syncwarp();
     w_sym(m, Rxi, lane);
-    const double* GQM = VH + (long long)(l - 1) * n * m;  // G Q~ M^T = V_l H^T
-    const double* Al = Apow + (long long)l * nn;
+    const double* GQM = md + L.VH + (size_t)(l - 1) * n * m;  // G Q~ M^T = V_l H^T
+    const double* Al = Ap + (size_t)l * nn;
     const double* Cb = md + L.Cb;
+    const double* Qcl = Qp + (size_t)(l - 1) * nn;
     w_mm(n, m, m, md + L.K, GQM, false, Rxi, false, nullptr, 1.0, lane);   // K
     w_mm(n, m, m, md + L.Cr, Cb, true, Rxi, false, nullptr, 1.0, lane);    // C_bar^T R_x^-1
     __syncwarp();
     w_mm(n, m, n, md + L.Fc, md + L.K, false, Cb, false, Al, -1.0, lane);  // A^l - K C_bar
-    w_mm(n, m, n, t, md + L.K, false, GQM, true, Qc + (long long)(l - 1) * nn, -1.0, lane);
+    w_mm(n, m, n, t, md + L.K, false, GQM, true, Qcl, -1.0, lane);
     w_sym(n, t, lane);
     for (int e = lane; e < nn; e += 32) md[L.Dc + e] = t[e];              // Q_bar - K GQM^T
     __syncwarp();
@@ -299,45 +322,46 @@ __global__ void __launch_bounds__(128) precompute_kernel(Ctx c) {
     for (int e = lane; e < nn; e += 32) md[L.Jc + e] = t[e];              // C_bar^T R_x^-1 C_bar
     __syncwarp();
     // first element: one IMKF step from (m0, P0) with y_1 (Eq. 9, 12)
-    double* AP = sb[0][1];   // A^l P0
-    double* cross = wk2;     // A^l P0 C_bar^T + G Q~ M^T   (n x m)
-    double* S1 = sb[0][2];   // C_bar P0 C_bar^T + R_x      (m x m)
-    double* S1i = sb[0][3];
-    double* CP = sb[0][4];   // C_bar P0 (m x n)
-    w_mm(n, n, n, AP, Al, false, P0, false, nullptr, 1.0, lane);
-    w_mm(m, n, n, CP, Cb, false, P0, false, nullptr, 1.0, lane);
+    double* AP = t;           // A^l P0
+    double* cross = wk2;      // A^l P0 C_bar^T + G Q~ M^T   (n x m)
+    double* S1 = MQM;         // C_bar P0 C_bar^T + R_x      (m x m)
+    double* S1i = Rxi;
+    double* CP = wk;          // C_bar P0 (m x n)
+    w_mm(n, n, n, AP, Al, false, sP0, false, nullptr, 1.0, lane);
+    w_mm(m, n, n, CP, Cb, false, sP0, false, nullptr, 1.0, lane);
     __syncwarp();
     w_mm(n, n, m, cross, AP, false, Cb, true, GQM, 1.0, lane);
     w_mm(m, n, m, S1, CP, false, Cb, true, md + L.Rx, 1.0, lane);
     w_sym(m, S1, lane);
-    double* Lg = sb[1][0];   // n x m gain (warp 1 scratch is free now)
-    double* tmp = sb[1][1];
+    double* w1 = scr + 1 * 6 * 64;  // warp 1 scratch is free now
+    double* Lg = w1;                // n x m gain
+    double* tmp = w1 + 64;
+    double* innov = w1 + 128;
+    double* P1 = w1 + 192;
+    double* P1o = w1 + 256;
     if (lane == 0) {
       for (int e = 0; e < m * m; ++e) tmp[e] = S1[e];
       if (!small_inverse(m, tmp, S1i)) s_ok = 0;
     }
     __syncwarp();
     w_mm(n, m, m, Lg, cross, false, S1i, false, nullptr, 1.0, lane);
-    // innovation y_1 - C_bar m0 (lanes < m)
-    double* innov = sb[1][2];
     for (int j = lane; j < m; j += 32) {
-      double v = y0[j];
-      for (int q = 0; q < n; ++q) v = fma(-Cb[j * n + q], m0[q], v);
+      double v = sy0[j];
+      for (int q = 0; q < n; ++q) v = fma(-Cb[j * n + q], sm0[q], v);
       innov[j] = v;
     }
     __syncwarp();
     for (int r = lane; r < n; r += 32) {
       double v = 0.0;
-      for (int q = 0; q < n; ++q) v = fma(Al[r * n + q], m0[q], v);
+      for (int q = 0; q < n; ++q) v = fma(Al[r * n + q], sm0[q], v);
       for (int j = 0; j < m; ++j) v = fma(Lg[r * m + j], innov[j], v);
       md[L.m1 + r] = v;
     }
-    double* P1 = sb[1][3];
-    w_mm(n, n, n, P1, AP, false, Al, true, Qc + (long long)(l - 1) * nn, 1.0, lane);
+    w_mm(n, n, n, P1, AP, false, Al, true, Qcl, 1.0, lane);
     __syncwarp();
-    w_mm(n, m, n, sb[1][4], Lg, false, cross, true, P1, -1.0, lane);
-    w_sym(n, sb[1][4], lane);
-    for (int e = lane; e < nn; e += 32) md[L.P1 + e] = sb[1][4][e];
+    w_mm(n, m, n, P1o, Lg, false, cross, true, P1, -1.0, lane);
+    w_sym(n, P1o, lane);
+    for (int e = lane; e < nn; e += 32) md[L.P1 + e] = P1o[e];
     __syncwarp();
     if (lane == 0 && !s_ok) atomicOr(&c.ctr->err, DEVERR_SINGULAR);
   }
@@ -349,7 +373,12 @@ int launch_meta_and_precompute(const Ctx& c, cudaStream_t st, cudaEvent_t* ev) {
   if (ev) cudaEventRecord(ev[0], st);
   meta_kernel<<<1, 1024, 0, st>>>(c);
   if (ev) cudaEventRecord(ev[1], st);
-  precompute_kernel<<<c.n_seq, 128, 0, st>>>(c);
+  const size_t tab = precompute_table_doubles(c.nx, c.max_ratio) * sizeof(double);
+  const size_t base = PRE_BASE * sizeof(double);
+  const int in_smem = base + tab <= PRE_SMEM_CAP ? 1 : 0;
+  const size_t smem = base + (in_smem ? tab : 0);
+  if (smem > 48 * 1024) cudaFuncSetAttribute(precompute_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  precompute_kernel<<<c.n_seq, 128, smem, st>>>(c, in_smem);
   if (ev) cudaEventRecord(ev[2], st);
   return cudaGetLastError() == cudaSuccess ? SRTM_OK : SRTM_ERR_CUDA;
 }

@@ -56,12 +56,10 @@ srtm_tuning effective_tuning(int nx, srtm_precision prec) {
   t.scan_groups = std::max(1, 128 / G);
   t.scan_elems = 4;
   t.recover_threads = 128;
-  t.recover_chunk = 512;
   const srtm_tuning& u = g_tune[nx][prec];
   if (u.scan_groups) t.scan_groups = u.scan_groups;
   if (u.scan_elems) t.scan_elems = u.scan_elems;
   if (u.recover_threads) t.recover_threads = u.recover_threads;
-  if (u.recover_chunk) t.recover_chunk = u.recover_chunk;
   return t;
 }
 
@@ -79,8 +77,8 @@ size_t a256(size_t x) { return (x + 255) / 256 * 256; }
 size_t a16(size_t x) { return (x + 15) / 16 * 16; }
 
 struct Layout {
-  size_t ctr, ratio, nslow, chunkC, off_slow, off_fast, tile_f, tile_s, chunk_off, model, ftile, stile, fout, rec,
-      selem, sout, total;
+  size_t ctr, ratio, nslow, off_slow, off_fast, tile_f, tile_s, model, ftile, stile, fout, rec, selem, sfin,
+      total;
   long long ftile_stride, stile_stride;
   ModelLayout ml;
 };
@@ -101,19 +99,17 @@ Layout make_layout(int nx, int ny, int max_ratio, int n_seq, long long total_slo
   L.ctr = take(sizeof(Counters));
   L.ratio = take(sizeof(int) * n_seq);
   L.nslow = take(sizeof(int) * n_seq);
-  L.chunkC = take(sizeof(int) * n_seq);
   L.off_slow = take(sizeof(long long) * (n_seq + 1));
   L.off_fast = take(sizeof(long long) * (n_seq + 1));
   L.tile_f = take(sizeof(long long) * (n_seq + 1));
   L.tile_s = take(sizeof(long long) * (n_seq + 1));
-  L.chunk_off = take(sizeof(long long) * (n_seq + 1));
   L.model = take(sizeof(double) * (size_t)L.ml.stride * n_seq);
   L.ftile = take((size_t)L.ftile_stride * tiles_f);
   L.stile = take((size_t)L.stile_stride * tiles_s);
-  L.fout = take(sT * (size_t)(nx + nn) * total_slow);
+  L.fout = take(sR * (size_t)(nx + nn) * total_slow);
   L.rec = take(sR * (size_t)REC * total_slow);
   L.selem = take(sT * (size_t)SE * total_slow);
-  L.sout = take(sT * (size_t)(nx + nn) * total_slow);
+  L.sfin = take(sR * (size_t)(nx + nn) * total_slow);
   L.total = a256(o);
   return L;
 }
@@ -121,7 +117,7 @@ Layout make_layout(int nx, int ny, int max_ratio, int n_seq, long long total_slo
 int shapes_for(int nx, srtm_precision prec, const srtm_tuning& t, int sms, long long total_slow, int n_seq,
                Shapes* sh) {
 #define SRTM_Q(N) \
-  case N: return query_shapes<N>(prec, t.scan_groups, t.scan_elems, t.recover_threads, t.recover_chunk, sms, total_slow, n_seq, sh);
+  case N: return query_shapes<N>(prec, t.scan_groups, t.scan_elems, t.recover_threads, sms, total_slow, n_seq, sh);
   switch (nx) {
     SRTM_Q(1) SRTM_Q(2) SRTM_Q(3) SRTM_Q(4) SRTM_Q(5) SRTM_Q(6) SRTM_Q(7) SRTM_Q(8)
   }
@@ -185,12 +181,10 @@ int run(Ctx c, srtm_precision prec, cudaStream_t st) {
   c.ctr = (Counters*)(w + L.ctr);
   c.meta.ratio = (int*)(w + L.ratio);
   c.meta.nslow = (int*)(w + L.nslow);
-  c.meta.chunk_C = (int*)(w + L.chunkC);
   c.meta.off_slow = (long long*)(w + L.off_slow);
   c.meta.off_fast = (long long*)(w + L.off_fast);
   c.meta.tile_off_f = (long long*)(w + L.tile_f);
   c.meta.tile_off_s = (long long*)(w + L.tile_s);
-  c.meta.chunk_off = (long long*)(w + L.chunk_off);
   c.model = (double*)(w + L.model);
   c.ml = L.ml;
   c.ftile = w + L.ftile;
@@ -200,12 +194,9 @@ int run(Ctx c, srtm_precision prec, cudaStream_t st) {
   c.fout = w + L.fout;
   c.rec = w + L.rec;
   c.selem = w + L.selem;
-  c.sout = w + L.sout;
+  c.sfin = w + L.sfin;
   c.tile_f = tile_f;
   c.tile_s = tile_s;
-  c.chunk_fast = sh.recover_chunk;
-  const size_t per_int = (size_t)(c.nx * c.nx + c.nx) * (prec == SRTM_FP32 ? 4 : 8);
-  c.chunk_cmax = (int)std::max<size_t>(1, sh.smem_r / per_int);
   cudaEvent_t* ev = nullptr;
   if (g_timing) {
     if (!d.ev[0])
@@ -443,10 +434,8 @@ int srtm_set_tuning(int nx, srtm_precision prec, const srtm_tuning* t) {
                          t->scan_groups * G < 32 || t->scan_groups * G > 256))
     return fail(SRTM_ERR_ARG, "scan_groups=%d invalid for nx=%d", t->scan_groups, nx);
   if (t->scan_elems && (t->scan_elems < 1 || t->scan_elems > 64)) return fail(SRTM_ERR_ARG, "scan_elems out of range");
-  if (t->recover_threads && (t->recover_threads < 32 || t->recover_threads > 256 || t->recover_threads % 32))
+  if (t->recover_threads && (t->recover_threads < 32 || t->recover_threads > 128 || t->recover_threads % 32))
     return fail(SRTM_ERR_ARG, "recover_threads out of range");
-  if (t->recover_chunk && (t->recover_chunk < 32 || t->recover_chunk > 65536))
-    return fail(SRTM_ERR_ARG, "recover_chunk out of range");
   std::lock_guard<std::mutex> lk(g_mu);
   g_tune[nx][prec] = *t;
   return SRTM_OK;
@@ -564,12 +553,10 @@ extern "C" int srtm_smoother_noalloc(const srtm_problem* p, srtm_precision prec,
     c.ctr = (Counters*)(w + L.ctr);
     c.meta.ratio = (int*)(w + L.ratio);
     c.meta.nslow = (int*)(w + L.nslow);
-    c.meta.chunk_C = (int*)(w + L.chunkC);
     c.meta.off_slow = (long long*)(w + L.off_slow);
     c.meta.off_fast = (long long*)(w + L.off_fast);
     c.meta.tile_off_f = (long long*)(w + L.tile_f);
     c.meta.tile_off_s = (long long*)(w + L.tile_s);
-    c.meta.chunk_off = (long long*)(w + L.chunk_off);
     c.model = (double*)(w + L.model);
     c.ml = L.ml;
     c.ftile = w + L.ftile;
@@ -579,12 +566,9 @@ extern "C" int srtm_smoother_noalloc(const srtm_problem* p, srtm_precision prec,
     c.fout = w + L.fout;
     c.rec = w + L.rec;
     c.selem = w + L.selem;
-    c.sout = w + L.sout;
+    c.sfin = w + L.sfin;
     c.tile_f = tile_f;
     c.tile_s = tile_s;
-    c.chunk_fast = sh.recover_chunk;
-    const size_t per_int = (size_t)(c.nx * c.nx + c.nx) * (prec == SRTM_FP32 ? 4 : 8);
-    c.chunk_cmax = (int)std::max<size_t>(1, sh.smem_r / per_int);
     rc = launch_meta_and_precompute(c, st, nullptr);
     if (rc) return fail(rc, "launch of the metadata/constants kernels failed");
     rc = launch_for(c.nx, c, prec, sh, st, nullptr);

@@ -20,22 +20,20 @@ constexpr long long SPIN_LIMIT = 2000000;
 // Device-side control block at offset 0 of the workspace.
 struct Counters {
   unsigned long long epoch;   // bumped once per call by the metadata kernel
-  unsigned int ticket[4];     // tile / chunk tickets: 0 filter scan, 1 smoother scan, 2 recovery
+  unsigned int ticket[4];     // tile tickets: 0 filter scan, 1 smoother scan
   unsigned int err;           // DevErr bits, sticky until srtm_status()
   unsigned int call_ok;       // 1 when this call's metadata passed validation
-  long long total_tiles_f, total_tiles_s, total_chunks;
+  long long total_tiles_f, total_tiles_s;
 };
 
 // Per-sequence metadata (SoA, written by the metadata kernel).
 struct SeqMeta {
   int* ratio;
   int* nslow;
-  int* chunk_C;               // slow intervals per recovery chunk
   long long* off_slow;        // [n_seq+1] row offsets of y / slow outputs
   long long* off_fast;        // [n_seq+1] row offsets of fast outputs
   long long* tile_off_f;      // [n_seq+1] filter-scan tile offsets
   long long* tile_off_s;      // [n_seq+1] smoother-scan tile offsets
-  long long* chunk_off;       // [n_seq+1] recovery chunk offsets
 };
 
 // Per-model constant table (float64), offsets in doubles.  L is the largest
@@ -135,14 +133,12 @@ struct Ctx {
   ModelLayout ml;
   unsigned char* ftile;  long long ftile_stride;  // filter scan tile states
   unsigned char* stile;  long long stile_stride;  // smoother scan tile states
-  void* fout;   // [total_slow][NX + NN] filter results m^f_{k,l}, P^f_{k,l}   (scan type)
+  void* fout;   // [total_slow][NX + NN] filter results m^f_{k,l}, P^f_{k,l}   (solve type)
   void* rec;    // [total_slow][Rec::SIZE] per-interval records              (recovery type)
   void* selem;  // [total_slow][SL::SIZE]  smoother elements                  (scan type)
-  void* sout;   // [total_slow][NX + NN]   smoothed first states m^s_{k,1}, P^s_{k,1}
+  void* sfin;   // [total_slow][NN + NX]   per-interval smoothing terms Om_k, om_k (recovery type)
   // launch shapes
   int tile_f, tile_s;    // elements per scan tile
-  int chunk_fast;        // target fast steps per recovery chunk
-  int chunk_cmax;        // max intervals per recovery chunk (shared-memory bound)
 };
 
 // ---------------------------------------------------------------------------
@@ -174,16 +170,16 @@ __device__ __forceinline__ void raise_err(Counters* c, unsigned bits) { atomicOr
 // ---------------------------------------------------------------------------
 struct Shapes {  // resolved launch shapes for one call
   int scan_groups_f, scan_elems_f, scan_groups_s, scan_elems_s;
-  int recover_threads, recover_chunk;
-  int grid_f, grid_s, grid_r, grid_setup;
-  size_t smem_f, smem_s, smem_r;
+  int recover_threads;
+  int grid_f, grid_s, grid_setup;
+  size_t smem_f, smem_s;
 };
 
 template <int NX>
 int launch_device_path(const Ctx& c, srtm_precision prec, const Shapes& sh, cudaStream_t st, cudaEvent_t* ev);
 
 template <int NX>
-int query_shapes(srtm_precision prec, int scan_groups, int scan_elems, int recover_threads,
-                 int recover_chunk, int sm_count, long long total_slow, int n_seq, Shapes* sh);
+int query_shapes(srtm_precision prec, int scan_groups, int scan_elems, int recover_threads, int sm_count,
+                 long long total_slow, int n_seq, Shapes* sh);
 
 }  // namespace srtm
