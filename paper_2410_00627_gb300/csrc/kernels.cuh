@@ -8,6 +8,7 @@
 
 #include <algorithm>
 
+#include "constants.cuh"
 #include "grp.cuh"
 #include "srtm_internal.cuh"
 
@@ -395,53 +396,65 @@ __global__ void __launch_bounds__(256) scan_kernel(Ctx c, int NG, int E) {
 // thread-local small-matrix helpers (interval setup, recovery)
 // ===========================================================================
 
-// inverse of a symmetric positive definite N x N matrix by Cholesky
-// (a = L L^T, a^-1 = L^-T L^-1).  Returns false if a pivot is not positive.
+// inverse of a symmetric positive definite matrix by Cholesky (a = L L^T,
+// a^-1 = L^-T L^-1).  Only the leading nact x nact block is inverted; the
+// rest of inv is set to the identity.  Returns false if a pivot is not
+// positive.
 template <int N, class T>
-__device__ __forceinline__ bool spd_inverse(const T (&a)[N][N], T (&inv)[N][N]) {
+__device__ __forceinline__ bool spd_inverse(const T (&a)[N][N], T (&inv)[N][N], int nact = N) {
   T Lm[N][N];
   bool ok = true;
 #pragma unroll
   for (int j = 0; j < N; ++j) {
-    T d = a[j][j];
 #pragma unroll
-    for (int k = 0; k < j; ++k) d = fma(-Lm[j][k], Lm[j][k], d);
-    if (!(d > T(0)) || !isfinite(d)) { ok = false; d = T(1); }
-    const T ljj = sqrt(d), rinv = T(1) / ljj;
-    Lm[j][j] = ljj;
+    for (int i = 0; i < N; ++i) Lm[i][j] = (i == j) ? T(1) : T(0);
+    if (j < nact) {
+      T d = a[j][j];
 #pragma unroll
-    for (int i = j + 1; i < N; ++i) {
-      T s = a[i][j];
+      for (int k = 0; k < j; ++k) d = fma(-Lm[j][k], Lm[j][k], d);
+      if (!(d > T(0)) || !isfinite(d)) { ok = false; d = T(1); }
+      const T ljj = sqrt(d), rinv = T(1) / ljj;
+      Lm[j][j] = ljj;
 #pragma unroll
-      for (int k = 0; k < j; ++k) s = fma(-Lm[i][k], Lm[j][k], s);
-      Lm[i][j] = s * rinv;
+      for (int i = j + 1; i < N; ++i) {
+        if (i < nact) {
+          T s2 = a[i][j];
+#pragma unroll
+          for (int k = 0; k < j; ++k) s2 = fma(-Lm[i][k], Lm[j][k], s2);
+          Lm[i][j] = s2 * rinv;
+        }
+      }
     }
-#pragma unroll
-    for (int i = 0; i < j; ++i) Lm[i][j] = T(0);
   }
   T Li[N][N];  // L^-1, lower triangular
 #pragma unroll
   for (int i = 0; i < N; ++i) {
-    Li[i][i] = T(1) / Lm[i][i];
 #pragma unroll
-    for (int j = 0; j < i; ++j) {
-      T s = T(0);
+    for (int j = 0; j < N; ++j) Li[i][j] = (i == j) ? T(1) : T(0);
+    if (i < nact) {
+      Li[i][i] = T(1) / Lm[i][i];
 #pragma unroll
-      for (int k = j; k < i; ++k) s = fma(Lm[i][k], Li[k][j], s);
-      Li[i][j] = -s * Li[i][i];
+      for (int j = 0; j < i; ++j) {
+        T s2 = T(0);
+#pragma unroll
+        for (int k = j; k < i; ++k) s2 = fma(Lm[i][k], Li[k][j], s2);
+        Li[i][j] = -s2 * Li[i][i];
+      }
     }
-#pragma unroll
-    for (int j = i + 1; j < N; ++j) Li[i][j] = T(0);
   }
 #pragma unroll
   for (int i = 0; i < N; ++i)
 #pragma unroll
     for (int j = i; j < N; ++j) {
-      T s = T(0);
+      T s2 = (i == j) ? T(1) : T(0);
+      if (j < nact) {
+        s2 = T(0);
 #pragma unroll
-      for (int k = j; k < N; ++k) s = fma(Li[k][i], Li[k][j], s);
-      inv[i][j] = s;
-      inv[j][i] = s;
+        for (int k = j; k < N; ++k)
+          if (k < nact) s2 = fma(Li[k][i], Li[k][j], s2);
+      }
+      inv[i][j] = s2;
+      inv[j][i] = s2;
     }
   return ok;
 }
@@ -523,7 +536,7 @@ __global__ void __launch_bounds__(64) interval_setup_kernel(Ctx c) {
   for (int i = 0; i < MY; ++i)
 #pragma unroll
     for (int j = i + 1; j < MY; ++j) { const TR v = TR(0.5) * (Sy[i][j] + Sy[j][i]); Sy[i][j] = v; Sy[j][i] = v; }
-  bool ok = spd_inverse<MY, TR>(Sy, Si);
+  bool ok = spd_inverse<MY, TR>(Sy, Si, m);
   TR kap[MY];
   {
     TR e[MY];
@@ -542,7 +555,8 @@ __global__ void __launch_bounds__(64) interval_setup_kernel(Ctx c) {
     for (int i = 0; i < MY; ++i) {
       TR v = TR(0);
 #pragma unroll
-      for (int j = 0; j < MY; ++j) v = fma(Si[i][j], e[j], v);
+      for (int j = 0; j < MY; ++j)
+        if (i < m && j < m) v = fma(Si[i][j], e[j], v);
       kap[i] = v;
     }
   }
@@ -568,7 +582,8 @@ __global__ void __launch_bounds__(64) interval_setup_kernel(Ctx c) {
       for (int r = 0; r < NX; ++r) {
         TR v = TR(0);
 #pragma unroll
-        for (int j = 0; j < MY; ++j) v = fma(Si[i][j], Ul[r][j], v);
+        for (int j = 0; j < MY; ++j)
+          if (i < m && j < m) v = fma(Si[i][j], Ul[r][j], v);
         SUl[i][r] = v;
       }
 #pragma unroll
@@ -577,7 +592,8 @@ __global__ void __launch_bounds__(64) interval_setup_kernel(Ctx c) {
 #pragma unroll
       for (int q = 0; q < NX; ++q) v = fma((TR)Al[r * NX + q], mv[q], v);
 #pragma unroll
-      for (int j = 0; j < MY; ++j) v = fma(Ul[r][j], kap[j], v);
+      for (int j = 0; j < MY; ++j)
+        if (j < m) v = fma(Ul[r][j], kap[j], v);
       ml[r] = v;
     }
   }
@@ -603,7 +619,8 @@ __global__ void __launch_bounds__(64) interval_setup_kernel(Ctx c) {
 #pragma unroll
         for (int t = 0; t < NX; ++t) v = fma((TR)Al[r * NX + t], Pl[t][q], v);
 #pragma unroll
-        for (int j = 0; j < MY; ++j) v = fma(-Ul[r][j], SUl[j][q], v);
+        for (int j = 0; j < MY; ++j)
+          if (j < m) v = fma(-Ul[r][j], SUl[j][q], v);
         Pll[r][q] = v;
         Pll[q][r] = v;
       }
@@ -695,7 +712,8 @@ __global__ void __launch_bounds__(64) interval_setup_kernel(Ctx c) {
 #pragma unroll
       for (int q = 0; q < NX; ++q) v = fma((TR)A1[r * NX + q], mv[q], v);
 #pragma unroll
-      for (int j = 0; j < MY; ++j) v = fma(U1[r][j], kap[j], v);
+      for (int j = 0; j < MY; ++j)
+        if (j < m) v = fma(U1[r][j], kap[j], v);
       m1[r] = v;
     }
     TR P11[NX][NX], P1l[NX][NX];
@@ -707,7 +725,8 @@ __global__ void __launch_bounds__(64) interval_setup_kernel(Ctx c) {
         for (int j = 0; j < MY; ++j) {
           TR v = TR(0);
 #pragma unroll
-          for (int jj = 0; jj < MY; ++jj) v = fma(U1[r][jj], Si[jj][j], v);
+          for (int jj = 0; jj < MY; ++jj)
+            if (jj < m && j < m) v = fma(U1[r][jj], Si[jj][j], v);
           US[r][j] = v;
         }
 #pragma unroll
@@ -727,7 +746,8 @@ __global__ void __launch_bounds__(64) interval_setup_kernel(Ctx c) {
 #pragma unroll
           for (int t = 0; t < NX; ++t) v = fma(AP[r][t], (TR)A1[q * NX + t], v);
 #pragma unroll
-          for (int j = 0; j < MY; ++j) v = fma(-US[r][j], U1[q][j], v);
+          for (int j = 0; j < MY; ++j)
+            if (j < m) v = fma(-US[r][j], U1[q][j], v);
           P11[r][q] = v;
           P11[q][r] = v;
         }
@@ -739,7 +759,8 @@ __global__ void __launch_bounds__(64) interval_setup_kernel(Ctx c) {
 #pragma unroll
           for (int t = 0; t < NX; ++t) v = fma((TR)A1[r * NX + t], Pl[t][q], v);
 #pragma unroll
-          for (int j = 0; j < MY; ++j) v = fma(-U1[r][j], SUl[j][q], v);
+          for (int j = 0; j < MY; ++j)
+            if (j < m) v = fma(-U1[r][j], SUl[j][q], v);
           P1l[r][q] = v;
         }
     }
@@ -1067,23 +1088,25 @@ int query_shapes(srtm_precision prec, int scan_groups, int scan_elems, int recov
   return SRTM_ERR_ARG;
 }
 
-// ev (optional): four events recorded after the filter scan, the interval
-// setup, the smoother scan and the recovery.
+// ev (optional): five events recorded after the constants, the filter scan,
+// the interval setup, the smoother scan and the recovery.
 template <int NX, class T, class TS, class TR>
 int launch_t(const Ctx& c, const Shapes& sh, cudaStream_t st, cudaEvent_t* ev) {
   using FOp = FilterOp<NX, T, TS>;
   using SOp = SmootherOp<NX, T, TR>;
   constexpr int G = FOp::G;
-  scan_kernel<FOp><<<sh.grid_f, sh.scan_groups_f * G, sh.smem_f, st>>>(c, sh.scan_groups_f, sh.scan_elems_f);
+  launch_precompute<NX>(c, st);
   if (ev) cudaEventRecord(ev[0], st);
-  interval_setup_kernel<NX, T, TR><<<sh.grid_setup, 64, 0, st>>>(c);
+  scan_kernel<FOp><<<sh.grid_f, sh.scan_groups_f * G, sh.smem_f, st>>>(c, sh.scan_groups_f, sh.scan_elems_f);
   if (ev) cudaEventRecord(ev[1], st);
+  interval_setup_kernel<NX, T, TR><<<sh.grid_setup, 64, 0, st>>>(c);
+  if (ev) cudaEventRecord(ev[2], st);
   if (c.smoothing)
     scan_kernel<SOp><<<sh.grid_s, sh.scan_groups_s * G, sh.smem_s, st>>>(c, sh.scan_groups_s, sh.scan_elems_s);
-  if (ev) cudaEventRecord(ev[2], st);
+  if (ev) cudaEventRecord(ev[3], st);
   const long long blocks = (c.total_fast + sh.recover_threads - 1) / sh.recover_threads;
   recover_kernel<NX, TR><<<(unsigned)blocks, sh.recover_threads, 0, st>>>(c);
-  if (ev) cudaEventRecord(ev[3], st);
+  if (ev) cudaEventRecord(ev[4], st);
   return cudaGetLastError() == cudaSuccess ? SRTM_OK : SRTM_ERR_CUDA;
 }
 

@@ -1,0 +1,84 @@
+// meta.cu -- per-call metadata: meta_kernel (one block) validates the batch
+// metadata, forms the row and tile offsets of every sequence, resets the scan
+// tickets and bumps the call epoch that tags the scans' look-back flags.
+#include <cuda_runtime.h>
+
+#include "srtm_internal.cuh"
+
+namespace srtm {
+
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) meta_kernel(Ctx c) {
+  __shared__ long long sc[4][1024];
+  __shared__ int s_bad;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (tid == 0) {
+    s_bad = 0;
+    c.ctr->epoch = c.ctr->epoch + 1;
+    for (int i = 0; i < 4; ++i) c.ctr->ticket[i] = 0;
+  }
+  __syncthreads();
+  const int per = (c.n_seq + nt - 1) / nt;
+  const int s0 = min(c.n_seq, tid * per), s1 = min(c.n_seq, s0 + per);
+  long long acc[4] = {0, 0, 0, 0};
+  int bad = 0;
+  for (int s = s0; s < s1; ++s) {
+    const int r = c.in_ratio ? c.in_ratio[s] : c.uniform_ratio;
+    const int n = c.in_nslow ? c.in_nslow[s] : c.uniform_nslow;
+    if (r < 1 || r > c.max_ratio || n < 1) { bad = 1; continue; }
+    acc[0] += n;
+    acc[1] += (long long)n * r;
+    acc[2] += (n + c.tile_f - 1) / c.tile_f;
+    acc[3] += (n + c.tile_s - 1) / c.tile_s;
+  }
+  if (bad) atomicOr(&s_bad, 1);
+  for (int q = 0; q < 4; ++q) sc[q][tid] = acc[q];
+  __syncthreads();
+  // inclusive Hillis-Steele scan of the per-thread sums
+  for (int d = 1; d < nt; d <<= 1) {
+    long long v[4];
+    for (int q = 0; q < 4; ++q) v[q] = (tid >= d) ? sc[q][tid - d] : 0;
+    __syncthreads();
+    for (int q = 0; q < 4; ++q) sc[q][tid] += v[q];
+    __syncthreads();
+  }
+  long long run[4];
+  for (int q = 0; q < 4; ++q) run[q] = (tid > 0) ? sc[q][tid - 1] : 0;
+  for (int s = s0; s < s1; ++s) {
+    const int r = c.in_ratio ? c.in_ratio[s] : c.uniform_ratio;
+    const int n = c.in_nslow ? c.in_nslow[s] : c.uniform_nslow;
+    const int rr = max(r, 1), nn = max(n, 1);
+    c.meta.ratio[s] = r;
+    c.meta.nslow[s] = n;
+    c.meta.off_slow[s] = run[0];
+    c.meta.off_fast[s] = run[1];
+    c.meta.tile_off_f[s] = run[2];
+    c.meta.tile_off_s[s] = run[3];
+    run[0] += nn;
+    run[1] += (long long)nn * rr;
+    run[2] += (nn + c.tile_f - 1) / c.tile_f;
+    run[3] += (nn + c.tile_s - 1) / c.tile_s;
+  }
+  __syncthreads();
+  if (tid == nt - 1) {
+    const bool ok = !s_bad && sc[0][nt - 1] == c.total_slow && sc[1][nt - 1] == c.total_fast;
+    c.meta.off_slow[c.n_seq] = sc[0][nt - 1];
+    c.meta.off_fast[c.n_seq] = sc[1][nt - 1];
+    c.meta.tile_off_f[c.n_seq] = sc[2][nt - 1];
+    c.meta.tile_off_s[c.n_seq] = sc[3][nt - 1];
+    c.ctr->total_tiles_f = ok ? sc[2][nt - 1] : 0;
+    c.ctr->total_tiles_s = ok ? sc[3][nt - 1] : 0;
+    c.ctr->call_ok = ok ? 1u : 0u;
+    if (!ok) atomicOr(&c.ctr->err, DEVERR_META);
+  }
+}
+
+// ev (optional): two events recorded before and after the metadata kernel.
+int launch_meta(const Ctx& c, cudaStream_t st, cudaEvent_t* ev) {
+  if (ev) cudaEventRecord(ev[0], st);
+  meta_kernel<<<1, 1024, 0, st>>>(c);
+  if (ev) cudaEventRecord(ev[1], st);
+  return cudaGetLastError() == cudaSuccess ? SRTM_OK : SRTM_ERR_CUDA;
+}
+
+}  // namespace srtm

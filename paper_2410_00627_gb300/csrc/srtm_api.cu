@@ -12,7 +12,7 @@
 #include "srtm_internal.cuh"
 
 namespace srtm {
-int launch_meta_and_precompute(const Ctx& c, cudaStream_t st, cudaEvent_t* ev);
+int launch_meta(const Ctx& c, cudaStream_t st, cudaEvent_t* ev);
 }
 using namespace srtm;
 
@@ -205,9 +205,9 @@ int run(Ctx c, srtm_precision prec, cudaStream_t st) {
     d.ev_stream = st;
     d.ev_valid = true;
   }
-  rc = launch_meta_and_precompute(c, st, ev);
-  if (rc) return fail(rc, "launch of the metadata/constants kernels failed: %s", cudaGetErrorString(cudaGetLastError()));
-  rc = launch_for(c.nx, c, prec, sh, st, ev ? ev + 3 : nullptr);
+  rc = launch_meta(c, st, ev);
+  if (rc) return fail(rc, "launch of the metadata kernel failed: %s", cudaGetErrorString(cudaGetLastError()));
+  rc = launch_for(c.nx, c, prec, sh, st, ev ? ev + 2 : nullptr);
   if (rc) return fail(rc, "launch of the scan/recovery kernels failed: %s", cudaGetErrorString(cudaGetLastError()));
   return SRTM_OK;
 }
@@ -569,8 +569,8 @@ extern "C" int srtm_smoother_noalloc(const srtm_problem* p, srtm_precision prec,
     c.sfin = w + L.sfin;
     c.tile_f = tile_f;
     c.tile_s = tile_s;
-    rc = launch_meta_and_precompute(c, st, nullptr);
-    if (rc) return fail(rc, "launch of the metadata/constants kernels failed");
+    rc = launch_meta(c, st, nullptr);
+    if (rc) return fail(rc, "launch of the metadata kernel failed");
     rc = launch_for(c.nx, c, prec, sh, st, nullptr);
     if (rc) return fail(rc, "launch of the scan/recovery kernels failed");
   }
