@@ -174,15 +174,7 @@ def run_ours(args, rank, world, dist):
     fma_per_fast = 7 * n ** 3 + 3 * n * n * m + n * m * m
     rec_s = stage_mean["recovery"] * 1e-3
     achieved = 2.0 * fma_per_fast * n_fast / rec_s / 1e9
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "recover_kernel_traffic.json")
-    if os.path.exists(prof):
-        try:
-            tr = json.load(open(prof))
-            if tr.get("n_fast") and tr.get("precision") == args.precision:
-                traffic = tr["dram_bytes_per_fast_step"] * n_fast
-        except (ValueError, KeyError):
-            traffic = None
+    traffic = recorded_traffic(args.precision, n_fast)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak",
@@ -204,6 +196,25 @@ def run_ours(args, rank, world, dist):
         line["e2e"] = run_e2e(args, prob, api, torch, flush)
         line["cpu_baseline"] = run_cpu_baseline(args, prob)
     return line
+
+
+def recorded_traffic(precision, n_fast):
+    """DRAM bytes per recovery launch from the committed ncu summary, if it was
+    taken on this workload and the recovery kernel's source is unchanged since."""
+    import hashlib
+    prof = os.path.join(ROOT, "profiles", f"recover_kernel_config2_T1e4_{precision}.json")
+    if not os.path.exists(prof):
+        return None
+    try:
+        tr = json.load(open(prof))
+        src = open(os.path.join(ROOT, "paper_2410_00627_gb300", "csrc", "kernels.cuh")).read()
+        a = src.index("// fast-rate recovery (Remarks 1 and 3)")
+        b = src.index("// host-side launch of the templated stages")
+        if tr.get("n_fast") != n_fast or tr.get("source_sha1") != hashlib.sha1(src[a:b].encode()).hexdigest():
+            return None
+        return float(tr["dram_bytes_per_launch"])
+    except (ValueError, KeyError, OSError):
+        return None
 
 
 def run_e2e(args, prob, api, torch, flush):
