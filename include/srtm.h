@@ -152,8 +152,10 @@ typedef struct {
 int srtm_set_tuning(int nx, srtm_precision prec, const srtm_tuning *t);
 int srtm_get_tuning(int nx, srtm_precision prec, srtm_tuning *t);
 
-/* Launch count of the device path for one call (for reporting). */
-int srtm_launches_per_call(int smoothing);
+/* Kernel launches of one call (for reporting): constants, filter scan (which
+ * also forms the per-interval smoother elements), smoother scan (smoother
+ * calls only) and fast-rate recovery, plus the metadata kernel for batches. */
+int srtm_launches_per_call(int smoothing, int batched);
 
 /* Stage timing.  While enabled, every call records CUDA events on its stream
  * around each of its launches.  srtm_stage_times() waits for the last timed

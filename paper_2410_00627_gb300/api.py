@@ -83,7 +83,7 @@ def load():
         "srtm_release": [],
         "srtm_set_tuning": [c_int, c_int, T],
         "srtm_get_tuning": [c_int, c_int, T],
-        "srtm_launches_per_call": [c_int],
+        "srtm_launches_per_call": [c_int, c_int],
         "srtm_set_stage_timing": [c_int],
         "srtm_stage_times": [ctypes.POINTER(ctypes.c_float), c_int],
         "srtm_smoother_noalloc": [P, c_int, O, c_void_p],
@@ -251,8 +251,8 @@ def get_tuning(nx: int, precision: str) -> dict:
     return {k: getattr(t, k) for k, _ in Tuning._fields_}
 
 
-def launches_per_call(smoothing: bool = True) -> int:
-    return load().srtm_launches_per_call(1 if smoothing else 0)
+def launches_per_call(smoothing: bool = True, batched: bool = False) -> int:
+    return load().srtm_launches_per_call(1 if smoothing else 0, 1 if batched else 0)
 
 
 def set_stage_timing(enable: bool) -> None:

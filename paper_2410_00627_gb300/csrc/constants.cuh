@@ -110,7 +110,30 @@ __global__ void __launch_bounds__(32 * PRE_WARPS) precompute_kernel(Ctx c, int t
   using S = PreSmem<NX>;
   extern __shared__ __align__(16) double dsm[];
   __shared__ int s_ok;
-  if (!c.ctr->call_ok) return;
+  if (c.fold_meta) {
+    // single sequence (host-validated): this block writes the call metadata
+    if (threadIdx.x == 0) {
+      const int r = c.uniform_ratio, n = c.uniform_nslow;
+      c.ctr->epoch = c.ctr->epoch + 1;
+      for (int i = 0; i < 4; ++i) c.ctr->ticket[i] = 0;
+      c.meta.ratio[0] = r;
+      c.meta.nslow[0] = n;
+      c.meta.off_slow[0] = 0;
+      c.meta.off_slow[1] = n;
+      c.meta.off_fast[0] = 0;
+      c.meta.off_fast[1] = (long long)n * r;
+      c.meta.tile_off_f[0] = 0;
+      c.meta.tile_off_f[1] = (n + c.tile_f - 1) / c.tile_f;
+      c.meta.tile_off_s[0] = 0;
+      c.meta.tile_off_s[1] = (n + c.tile_s - 1) / c.tile_s;
+      c.ctr->total_tiles_f = (n + c.tile_f - 1) / c.tile_f;
+      c.ctr->total_tiles_s = (n + c.tile_s - 1) / c.tile_s;
+      c.ctr->call_ok = 1u;
+    }
+    __syncthreads();
+  } else if (!c.ctr->call_ok) {
+    return;
+  }
   const int s = blockIdx.x;
   const int m = c.ny, l = c.meta.ratio[s];
   const ModelLayout L = c.ml;

@@ -17,6 +17,440 @@ namespace srtm {
 __host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) / 16 * 16; }
 
 // ===========================================================================
+// thread-local small-matrix helpers (interval setup, recovery)
+// ===========================================================================
+
+// inverse of a symmetric positive definite matrix by Cholesky (a = L L^T,
+// a^-1 = L^-T L^-1).  Only the leading nact x nact block is inverted; the
+// rest of inv is set to the identity.  Returns false if a pivot is not
+// positive.
+template <int N, class T>
+__device__ __forceinline__ bool spd_inverse(const T (&a)[N][N], T (&inv)[N][N], int nact = N) {
+  T Lm[N][N];
+  bool ok = true;
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) Lm[i][j] = (i == j) ? T(1) : T(0);
+    if (j < nact) {
+      T d = a[j][j];
+#pragma unroll
+      for (int k = 0; k < j; ++k) d = fma(-Lm[j][k], Lm[j][k], d);
+      if (!(d > T(0)) || !isfinite(d)) { ok = false; d = T(1); }
+      const T ljj = sqrt(d), rinv = T(1) / ljj;
+      Lm[j][j] = ljj;
+#pragma unroll
+      for (int i = j + 1; i < N; ++i) {
+        if (i < nact) {
+          T s2 = a[i][j];
+#pragma unroll
+          for (int k = 0; k < j; ++k) s2 = fma(-Lm[i][k], Lm[j][k], s2);
+          Lm[i][j] = s2 * rinv;
+        }
+      }
+    }
+  }
+  T Li[N][N];  // L^-1, lower triangular
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+#pragma unroll
+    for (int j = 0; j < N; ++j) Li[i][j] = (i == j) ? T(1) : T(0);
+    if (i < nact) {
+      Li[i][i] = T(1) / Lm[i][i];
+#pragma unroll
+      for (int j = 0; j < i; ++j) {
+        T s2 = T(0);
+#pragma unroll
+        for (int k = j; k < i; ++k) s2 = fma(Lm[i][k], Li[k][j], s2);
+        Li[i][j] = -s2 * Li[i][i];
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+#pragma unroll
+    for (int j = i; j < N; ++j) {
+      T s2 = (i == j) ? T(1) : T(0);
+      if (j < nact) {
+        s2 = T(0);
+#pragma unroll
+        for (int k = j; k < N; ++k)
+          if (k < nact) s2 = fma(Li[k][i], Li[k][j], s2);
+      }
+      inv[i][j] = s2;
+      inv[j][i] = s2;
+    }
+  return ok;
+}
+
+// ===========================================================================
+// interval setup: for every slow interval k (paper index k+1), from
+// p(x_{k-1,l}|y_{1:k-1}) and y_k, the fast-filter blocks it needs (Eq. 17 on
+// the blocks of Remark 2) and the parallel IMS element (Eq. 29):
+//   X = P C_bar^T, S_y = C_bar X + R_x, kap = S_y^-1 (y - C_bar m),
+//   U_i = A^i X + V_i H^T   (U_i = sum_j P^-_{ij} H^T),
+//   m^f_i = A^i m + U_i kap,  P^f_{ij} = A^i P A^{jT} + Cov(e_i,e_j) - U_i S_y^-1 U_j^T,
+//   P^-_{k+1,1} = A P^f_{ll} A^T + Q,  Z = A^T (P^-_{k+1,1})^-1,
+//   E_k = P^f_{1l} Z,  g_k = m^f_1 - E_k A m^f_l,  S_k = P^f_{11} - E_k A (P^f_{1l})^T
+// (last interval: E = 0, g = m^f_1, S = P^f_{11}).  The record keeps what the
+// recovery reuses.  Runs in TR (float64 except in the float32 mode).
+//
+// Row split: SG lanes per interval (SG = nx rounded up to a power of two),
+// lane r owns row r of every n x n product; the interval's matrices live in
+// a shared-memory slot.  The small SPD inverses are formed by every lane of
+// the interval from the slot (a warp FP64 instruction costs the same whatever
+// its active lanes, so the repetition is free).
+// ===========================================================================
+template <int NX>
+struct SetupGeom {
+  static constexpr int SG = NX == 1 ? 1 : (NX == 2 ? 2 : (NX <= 4 ? 4 : 8));
+  static constexpr int NN = NX * NX, NM = NX * MY;
+  // slot layout (units of TR); S, AP1 and P11 reuse Pll, AP and Pm, whose
+  // last reads precede them
+  static constexpr int P = 0, mv = P + NN, X = mv + NX, SUl = X + NM, ml = SUl + NM, Pl = ml + NX, Pll = Pl + NN,
+                       AP = Pll + NN, Pm = AP + NN, Z = Pm + NN, U1 = Z + NN, P1l = U1 + NM, SLOT = P1l + NN;
+  static constexpr int S = Pll, AP1 = AP, P11 = Pm;
+};
+
+// One interval by its SG lanes (lane = row), slot sb in shared memory.
+// prev (optional): p(x_{k-1,l}|y_{1:k-1}) as (m, P) when it is not yet in
+// the filter results (the first interval of a scan tile reads it from the
+// tile's exclusive prefix).
+template <int NX, class T, class TR>
+__device__ void setup_interval(const Ctx& c, long long gi, int lane, unsigned mask, TR* sb, const TR* prev) {
+  using Gm = SetupGeom<NX>;
+  constexpr int NN = NX * NX;
+  using RL = Rec<NX>;
+  using SLy = SL<NX>;
+  const int r = lane;
+  const bool row = r < NX;
+  const int s = find_segment(c.meta.off_slow, c.n_seq, gi);
+  const long long k = gi - c.meta.off_slow[s];
+  const int N = c.meta.nslow[s], l = c.meta.ratio[s], m = c.ny;
+  const double* md = c.model + (long long)s * c.ml.stride;
+  const double* Apow = md + c.ml.Apow;
+  const double* Al = Apow + (long long)l * NN;
+  const double* A1 = Apow + NN;
+  const double* Cb = md + c.ml.Cb;
+  const double* Rx = md + c.ml.Rx;
+  bool ok = true;
+  // P^f_{k-1,l}, m^f_{k-1,l}
+  if (row) {
+    if (k == 0) {
+      sb[Gm::mv + r] = (TR)c.m0[(long long)s * NX + r];
+#pragma unroll
+      for (int q = 0; q < NX; ++q) sb[Gm::P + r * NX + q] = (TR)c.P0[(long long)s * NN + r * NX + q];
+    } else {
+      const TR* f = prev ? prev : (const TR*)c.fout + (gi - 1) * (NX + NN);
+      sb[Gm::mv + r] = f[r];
+#pragma unroll
+      for (int q = 0; q < NX; ++q) sb[Gm::P + r * NX + q] = f[NX + r * NX + q];
+    }
+  }
+  __syncwarp(mask);
+  // X = P C_bar^T (row r; columns >= m are zero)
+  if (row) {
+#pragma unroll
+    for (int j = 0; j < MY; ++j) {
+      TR v = TR(0);
+      if (j < m) {
+#pragma unroll
+        for (int q = 0; q < NX; ++q) v = fma(sb[Gm::P + r * NX + q], (TR)Cb[j * NX + q], v);
+      }
+      sb[Gm::X + r * MY + j] = v;
+    }
+  }
+  __syncwarp(mask);
+  // S_y = C_bar X + R_x (every lane), its inverse, kap
+  TR Si[MY][MY], kap[MY];
+  {
+    TR Sy[MY][MY];
+#pragma unroll
+    for (int i = 0; i < MY; ++i)
+#pragma unroll
+      for (int j = 0; j < MY; ++j) {
+        TR v = (i == j) ? TR(1) : TR(0);
+        if (i < m && j < m) {
+          v = (TR)Rx[i * m + j];
+#pragma unroll
+          for (int q = 0; q < NX; ++q) v = fma((TR)Cb[i * NX + q], sb[Gm::X + q * MY + j], v);
+        }
+        Sy[i][j] = v;
+      }
+#pragma unroll
+    for (int i = 0; i < MY; ++i)
+#pragma unroll
+      for (int j = i + 1; j < MY; ++j) {
+        const TR v = TR(0.5) * (Sy[i][j] + Sy[j][i]);
+        Sy[i][j] = v;
+        Sy[j][i] = v;
+      }
+    ok &= spd_inverse<MY, TR>(Sy, Si, m);
+    TR e[MY];
+    const double* yk = c.y + gi * m;
+#pragma unroll
+    for (int j = 0; j < MY; ++j) {
+      TR v = TR(0);
+      if (j < m) {
+        v = (TR)yk[j];
+#pragma unroll
+        for (int q = 0; q < NX; ++q) v = fma(-(TR)Cb[j * NX + q], sb[Gm::mv + q], v);
+      }
+      e[j] = v;
+    }
+#pragma unroll
+    for (int i = 0; i < MY; ++i) {
+      TR v = TR(0);
+#pragma unroll
+      for (int j = 0; j < MY; ++j)
+        if (i < m && j < m) v = fma(Si[i][j], e[j], v);
+      kap[i] = v;
+    }
+  }
+  // row r: U_l, S_y^-1 U_l^T (column r), m^f_l, P A^{lT}
+  TR Ul[MY];
+  if (row) {
+    const double* VHl = md + c.ml.VH + (long long)(l - 1) * NX * m;
+#pragma unroll
+    for (int j = 0; j < MY; ++j) {
+      TR v = TR(0);
+      if (j < m) {
+        v = (TR)VHl[r * m + j];
+#pragma unroll
+        for (int q = 0; q < NX; ++q) v = fma((TR)Al[r * NX + q], sb[Gm::X + q * MY + j], v);
+      }
+      Ul[j] = v;
+    }
+#pragma unroll
+    for (int i = 0; i < MY; ++i) {
+      TR v = TR(0);
+#pragma unroll
+      for (int j = 0; j < MY; ++j)
+        if (i < m && j < m) v = fma(Si[i][j], Ul[j], v);
+      sb[Gm::SUl + i * NX + r] = v;
+    }
+    TR v = TR(0);
+#pragma unroll
+    for (int q = 0; q < NX; ++q) v = fma((TR)Al[r * NX + q], sb[Gm::mv + q], v);
+#pragma unroll
+    for (int j = 0; j < MY; ++j)
+      if (j < m) v = fma(Ul[j], kap[j], v);
+    sb[Gm::ml + r] = v;
+#pragma unroll
+    for (int q = 0; q < NX; ++q) {
+      TR w = TR(0);
+#pragma unroll
+      for (int t = 0; t < NX; ++t) w = fma(sb[Gm::P + r * NX + t], (TR)Al[q * NX + t], w);
+      sb[Gm::Pl + r * NX + q] = w;
+    }
+  }
+  __syncwarp(mask);
+  // P^f_{ll} = A^l Pl + Qc_l - U_l SUl (row r)
+  if (row) {
+    const double* Qcl = md + c.ml.Qc + (long long)(l - 1) * NN;
+#pragma unroll
+    for (int q = 0; q < NX; ++q) {
+      TR v = (TR)Qcl[r * NX + q];
+#pragma unroll
+      for (int t = 0; t < NX; ++t) v = fma((TR)Al[r * NX + t], sb[Gm::Pl + t * NX + q], v);
+#pragma unroll
+      for (int j = 0; j < MY; ++j)
+        if (j < m) v = fma(-Ul[j], sb[Gm::SUl + j * NX + q], v);
+      sb[Gm::Pll + r * NX + q] = v;
+    }
+  }
+  __syncwarp(mask);
+  // A P^f_{ll} (row r)
+  if (row) {
+#pragma unroll
+    for (int q = 0; q < NX; ++q) {
+      TR v = TR(0);
+#pragma unroll
+      for (int t = 0; t < NX; ++t) v = fma((TR)A1[r * NX + t], sb[Gm::Pll + t * NX + q], v);
+      sb[Gm::AP + r * NX + q] = v;
+    }
+  }
+  __syncwarp(mask);
+  // P^-_{k+1,1} = (A P^f_{ll}) A^T + Q (row r)
+  if (row) {
+    const double* Qm = md + c.ml.Q;
+#pragma unroll
+    for (int q = 0; q < NX; ++q) {
+      TR v = (TR)Qm[r * NX + q];
+#pragma unroll
+      for (int t = 0; t < NX; ++t) v = fma(sb[Gm::AP + r * NX + t], (TR)A1[q * NX + t], v);
+      sb[Gm::Pm + r * NX + q] = v;
+    }
+  }
+  __syncwarp(mask);
+  // (P^-)^{-1} (every lane, symmetrised), Z = A^T (P^-)^{-1} (row r)
+  {
+    TR Pmv[NX][NX], Pmi[NX][NX];
+#pragma unroll
+    for (int i = 0; i < NX; ++i)
+#pragma unroll
+      for (int j = 0; j < NX; ++j) Pmv[i][j] = TR(0.5) * (sb[Gm::Pm + i * NX + j] + sb[Gm::Pm + j * NX + i]);
+    ok &= spd_inverse<NX, TR>(Pmv, Pmi);
+    if (row) {
+#pragma unroll
+      for (int q = 0; q < NX; ++q) {
+        TR v = TR(0);
+#pragma unroll
+        for (int t = 0; t < NX; ++t) v = fma((TR)A1[t * NX + r], Pmi[t][q], v);
+        sb[Gm::Z + r * NX + q] = v;
+      }
+    }
+  }
+  __syncwarp(mask);
+  // record (row r; lane 0 the m-sized parts)
+  {
+    TR* rc = (TR*)c.rec + gi * RL::SIZE;
+    if (row) {
+      rc[RL::mv + r] = sb[Gm::mv + r];
+      rc[RL::ml + r] = sb[Gm::ml + r];
+#pragma unroll
+      for (int q = 0; q < NX; ++q) {
+        rc[RL::P + r * NX + q] = sb[Gm::P + r * NX + q];
+        rc[RL::Pl + r * NX + q] = sb[Gm::Pl + r * NX + q];
+        rc[RL::Z + r * NX + q] = sb[Gm::Z + r * NX + q];
+        rc[RL::Pm + r * NX + q] = TR(0.5) * (sb[Gm::Pm + r * NX + q] + sb[Gm::Pm + q * NX + r]);
+      }
+#pragma unroll
+      for (int j = 0; j < MY; ++j) {
+        rc[RL::X + r * MY + j] = sb[Gm::X + r * MY + j];
+        rc[RL::SUl + j * NX + r] = sb[Gm::SUl + j * NX + r];
+      }
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int i = 0; i < MY; ++i) {
+        rc[RL::kap + i] = kap[i];
+#pragma unroll
+        for (int j = 0; j < MY; ++j) rc[RL::Si + i * MY + j] = Si[i][j];
+      }
+    }
+  }
+  if (c.smoothing) {
+    // first fast state of the interval: U_1, m^f_1, P^f_{11}, P^f_{1l} (row r)
+    const double* VH1 = md + c.ml.VH;
+    const double* Qc1 = md + c.ml.Qc;
+    const double* Ql1 = md + c.ml.Ql;
+    TR U1[MY], m1 = TR(0);
+    if (row) {
+#pragma unroll
+      for (int j = 0; j < MY; ++j) {
+        TR v = TR(0);
+        if (j < m) {
+          v = (TR)VH1[r * m + j];
+#pragma unroll
+          for (int q = 0; q < NX; ++q) v = fma((TR)A1[r * NX + q], sb[Gm::X + q * MY + j], v);
+        }
+        U1[j] = v;
+        sb[Gm::U1 + r * MY + j] = v;
+      }
+#pragma unroll
+      for (int q = 0; q < NX; ++q) m1 = fma((TR)A1[r * NX + q], sb[Gm::mv + q], m1);
+#pragma unroll
+      for (int j = 0; j < MY; ++j)
+        if (j < m) m1 = fma(U1[j], kap[j], m1);
+    }
+    __syncwarp(mask);
+    if (row) {
+      TR US[MY], APr[NX];
+#pragma unroll
+      for (int j = 0; j < MY; ++j) {
+        TR v = TR(0);
+#pragma unroll
+        for (int jj = 0; jj < MY; ++jj)
+          if (jj < m && j < m) v = fma(U1[jj], Si[jj][j], v);
+        US[j] = v;
+      }
+#pragma unroll
+      for (int q = 0; q < NX; ++q) {
+        TR v = TR(0);
+#pragma unroll
+        for (int t = 0; t < NX; ++t) v = fma((TR)A1[r * NX + t], sb[Gm::P + t * NX + q], v);
+        APr[q] = v;
+      }
+#pragma unroll
+      for (int q = 0; q < NX; ++q) {
+        TR v = (TR)(0.5 * (Qc1[r * NX + q] + Qc1[q * NX + r]));
+#pragma unroll
+        for (int t = 0; t < NX; ++t) v = fma(APr[t], (TR)A1[q * NX + t], v);
+#pragma unroll
+        for (int j = 0; j < MY; ++j)
+          if (j < m) v = fma(-US[j], sb[Gm::U1 + q * MY + j], v);
+        sb[Gm::P11 + r * NX + q] = v;
+        TR w = (TR)Ql1[r * NX + q];
+#pragma unroll
+        for (int t = 0; t < NX; ++t) w = fma((TR)A1[r * NX + t], sb[Gm::Pl + t * NX + q], w);
+#pragma unroll
+        for (int j = 0; j < MY; ++j)
+          if (j < m) w = fma(-U1[j], sb[Gm::SUl + j * NX + q], w);
+        sb[Gm::P1l + r * NX + q] = w;
+      }
+    }
+    __syncwarp(mask);
+    T* se = (T*)c.selem + gi * SLy::SIZE;
+    if (k < N - 1) {
+      // E = P^f_{1l} Z ; g = m^f_1 - E A m^f_l ; A (P^f_{1l})^T (rows)
+      TR Er[NX];
+      if (row) {
+#pragma unroll
+        for (int q = 0; q < NX; ++q) {
+          TR v = TR(0);
+#pragma unroll
+          for (int t = 0; t < NX; ++t) v = fma(sb[Gm::P1l + r * NX + t], sb[Gm::Z + t * NX + q], v);
+          Er[q] = v;
+          se[SLy::E + r * NX + q] = (T)v;
+        }
+        TR g = m1;
+#pragma unroll
+        for (int q = 0; q < NX; ++q) {
+          TR aml = TR(0);
+#pragma unroll
+          for (int t = 0; t < NX; ++t) aml = fma((TR)A1[q * NX + t], sb[Gm::ml + t], aml);
+          g = fma(-Er[q], aml, g);
+        }
+        se[SLy::g + r] = (T)g;
+#pragma unroll
+        for (int q = 0; q < NX; ++q) {
+          TR v = TR(0);
+#pragma unroll
+          for (int t = 0; t < NX; ++t) v = fma((TR)A1[r * NX + t], sb[Gm::P1l + q * NX + t], v);
+          sb[Gm::AP1 + r * NX + q] = v;
+        }
+      }
+      __syncwarp(mask);
+      // S = P^f_{11} - E A (P^f_{1l})^T (row r), then symmetrised
+      if (row) {
+#pragma unroll
+        for (int q = 0; q < NX; ++q) {
+          TR v = sb[Gm::P11 + r * NX + q];
+#pragma unroll
+          for (int t = 0; t < NX; ++t) v = fma(-Er[t], sb[Gm::AP1 + t * NX + q], v);
+          sb[Gm::S + r * NX + q] = v;
+        }
+      }
+      __syncwarp(mask);
+      if (row) {
+#pragma unroll
+        for (int q = 0; q < NX; ++q)
+          se[SLy::S + r * NX + q] = (T)(TR(0.5) * (sb[Gm::S + r * NX + q] + sb[Gm::S + q * NX + r]));
+      }
+    } else if (row) {
+      se[SLy::g + r] = (T)m1;
+#pragma unroll
+      for (int q = 0; q < NX; ++q) {
+        se[SLy::E + r * NX + q] = T(0);
+        se[SLy::S + r * NX + q] = (T)(TR(0.5) * (sb[Gm::P11 + r * NX + q] + sb[Gm::P11 + q * NX + r]));
+      }
+    }
+  }
+  if (!ok && lane == 0) raise_err(c.ctr, DEVERR_SINGULAR);
+}
+
+// ===========================================================================
 // scan operators
 // ===========================================================================
 
@@ -82,6 +516,35 @@ struct FilterOp {
   __device__ static const long long* tile_off(const Ctx& c) { return c.meta.tile_off_f; }
   __device__ static long long total_tiles(const Ctx& c) { return c.ctr->total_tiles_f; }
   __device__ static int tile_elems(const Ctx& c) { return c.tile_f; }
+
+  // After a tile's results are written: the interval setup (fast-filter
+  // blocks, smoother elements and recovery records) of the tile's intervals,
+  // by the whole block in rounds of blockDim/SG intervals.  The first
+  // interval's predecessor result is the tile's exclusive prefix.
+  static constexpr bool HAS_EPILOGUE = true;
+  __host__ __device__ static size_t epilogue_bytes(int threads) {
+    using Gm = SetupGeom<NX>;
+    return align16((NX + NX * NX) * sizeof(TS)) + (size_t)(threads / Gm::SG) * Gm::SLOT * sizeof(TS);
+  }
+  __device__ static void epilogue(const Ctx& c, int s, long long p0, int count, const T* excl, unsigned char* esm) {
+    using Gm = SetupGeom<NX>;
+    constexpr int SG = Gm::SG;
+    TS* prevb = (TS*)esm;
+    TS* slots = (TS*)(esm + align16((NX + NX * NX) * sizeof(TS)));
+    __syncthreads();
+    for (int e = threadIdx.x; e < NX + NX * NX; e += blockDim.x) prevb[e] = (TS)excl[L::d + e];
+    __syncthreads();
+    const int lane = threadIdx.x % SG, slot = threadIdx.x / SG, per_round = blockDim.x / SG;
+    const unsigned mask = (SG == 32) ? 0xffffffffu : (((1u << SG) - 1u) << ((threadIdx.x & 31) & ~(SG - 1)));
+    const long long base_row = c.meta.off_slow[s];
+    for (int j0 = 0; j0 < count; j0 += per_round) {
+      const int j = j0 + slot;
+      if (j < count)
+        setup_interval<NX, T, TS>(c, base_row + p0 + j, lane, mask, slots + (size_t)slot * Gm::SLOT,
+                                  j == 0 ? prevb : nullptr);
+    }
+    __syncthreads();
+  }
 };
 
 // Reverse scan of the parallel IMS (Sec. IV): elements of Eq. (29) built by
@@ -141,6 +604,9 @@ struct SmootherOp {
   __device__ static const long long* tile_off(const Ctx& c) { return c.meta.tile_off_s; }
   __device__ static long long total_tiles(const Ctx& c) { return c.ctr->total_tiles_s; }
   __device__ static int tile_elems(const Ctx& c) { return c.tile_s; }
+  static constexpr bool HAS_EPILOGUE = false;
+  __host__ __device__ static size_t epilogue_bytes(int) { return 0; }
+  __device__ static void epilogue(const Ctx&, int, long long, int, const T*, unsigned char*) {}
 };
 
 // ===========================================================================
@@ -165,9 +631,14 @@ struct ScanSmem {
   }
   static constexpr int WIN = 16;  // look-back window (predecessor tiles per round)
   __host__ __device__ static size_t window_bytes() { return align16((size_t)(WIN + WIN / 2) * Op::ES * sizeof(T)); }
+  // layout: [excl | tile id, control | union{ lane-group buffers, group
+  // aggregates x2, look-back window ; tile epilogue }]
+  __host__ __device__ static size_t scan_part(int NG) {
+    return NG * group_bytes() + 2 * align16((size_t)NG * Op::ES * sizeof(T)) + window_bytes();
+  }
   __host__ __device__ static size_t bytes(int NG) {
-    return NG * group_bytes() + 2 * align16((size_t)NG * Op::ES * sizeof(T)) + align16(Op::ES * sizeof(T)) +
-           window_bytes() + 32;
+    const size_t sp = scan_part(NG), ep = Op::epilogue_bytes(NG * Op::G);
+    return align16(Op::ES * sizeof(T)) + 32 + (sp > ep ? sp : ep);
   }
   __host__ __device__ static size_t payload_bytes() { return align16(Op::ES * sizeof(T)); }
   __host__ __device__ static size_t tile_state_bytes() { return 16 + 2 * payload_bytes(); }
@@ -306,18 +777,20 @@ __global__ void __launch_bounds__(256) scan_kernel(Ctx c, int NG, int E) {
   const int gid = threadIdx.x / G;
   const Grp<G> g;
   const size_t gb = ScanSmem<Op>::group_bytes();
-  unsigned char* gbase = smem + gid * gb;
+  T* excl = (T*)smem;
+  long long* s_tile = (long long*)(smem + align16(ES * sizeof(T)));
+  int* ctl = (int*)(s_tile + 1);
+  unsigned char* uni = (unsigned char*)s_tile + 32;
+  unsigned char* gbase = uni + gid * gb;
   T* b0 = (T*)gbase;
   T* b1 = b0 + ES;
   T* b2 = b1 + ES;
   T* sc = b2 + ES;
   TS* scs = (TS*)(gbase + align16((3 * ES + Op::SCR) * sizeof(T)));
-  T* ksA = (T*)(smem + NG * gb);
+  T* ksA = (T*)(uni + NG * gb);
   T* ksB = (T*)((unsigned char*)ksA + align16((size_t)NG * ES * sizeof(T)));
-  T* excl = (T*)((unsigned char*)ksB + align16((size_t)NG * ES * sizeof(T)));
-  T* win = (T*)((unsigned char*)excl + align16(ES * sizeof(T)));
-  long long* s_tile = (long long*)((unsigned char*)win + ScanSmem<Op>::window_bytes());
-  int* ctl = (int*)(s_tile + 1);
+  T* win = (T*)((unsigned char*)ksB + align16((size_t)NG * ES * sizeof(T)));
+  unsigned char* esm = uni;  // the tile epilogue reuses the scan buffers
 
   const unsigned long long epoch = c.ctr->epoch;
   const long long total = Op::total_tiles(c);
@@ -388,452 +861,12 @@ __global__ void __launch_bounds__(256) scan_kernel(Ctx c, int NG, int E) {
         g.sync();
       }
     }
+    if (Op::HAS_EPILOGUE) {
+      const long long tp0 = t * tile_elems;
+      Op::epilogue(c, s, tp0, (int)min((long long)tile_elems, (long long)N - tp0), excl, esm);
+    }
   }
   if (!ok && g.lane == 0) raise_err(c.ctr, DEVERR_SINGULAR);
-}
-
-// ===========================================================================
-// thread-local small-matrix helpers (interval setup, recovery)
-// ===========================================================================
-
-// inverse of a symmetric positive definite matrix by Cholesky (a = L L^T,
-// a^-1 = L^-T L^-1).  Only the leading nact x nact block is inverted; the
-// rest of inv is set to the identity.  Returns false if a pivot is not
-// positive.
-template <int N, class T>
-__device__ __forceinline__ bool spd_inverse(const T (&a)[N][N], T (&inv)[N][N], int nact = N) {
-  T Lm[N][N];
-  bool ok = true;
-#pragma unroll
-  for (int j = 0; j < N; ++j) {
-#pragma unroll
-    for (int i = 0; i < N; ++i) Lm[i][j] = (i == j) ? T(1) : T(0);
-    if (j < nact) {
-      T d = a[j][j];
-#pragma unroll
-      for (int k = 0; k < j; ++k) d = fma(-Lm[j][k], Lm[j][k], d);
-      if (!(d > T(0)) || !isfinite(d)) { ok = false; d = T(1); }
-      const T ljj = sqrt(d), rinv = T(1) / ljj;
-      Lm[j][j] = ljj;
-#pragma unroll
-      for (int i = j + 1; i < N; ++i) {
-        if (i < nact) {
-          T s2 = a[i][j];
-#pragma unroll
-          for (int k = 0; k < j; ++k) s2 = fma(-Lm[i][k], Lm[j][k], s2);
-          Lm[i][j] = s2 * rinv;
-        }
-      }
-    }
-  }
-  T Li[N][N];  // L^-1, lower triangular
-#pragma unroll
-  for (int i = 0; i < N; ++i) {
-#pragma unroll
-    for (int j = 0; j < N; ++j) Li[i][j] = (i == j) ? T(1) : T(0);
-    if (i < nact) {
-      Li[i][i] = T(1) / Lm[i][i];
-#pragma unroll
-      for (int j = 0; j < i; ++j) {
-        T s2 = T(0);
-#pragma unroll
-        for (int k = j; k < i; ++k) s2 = fma(Lm[i][k], Li[k][j], s2);
-        Li[i][j] = -s2 * Li[i][i];
-      }
-    }
-  }
-#pragma unroll
-  for (int i = 0; i < N; ++i)
-#pragma unroll
-    for (int j = i; j < N; ++j) {
-      T s2 = (i == j) ? T(1) : T(0);
-      if (j < nact) {
-        s2 = T(0);
-#pragma unroll
-        for (int k = j; k < N; ++k)
-          if (k < nact) s2 = fma(Li[k][i], Li[k][j], s2);
-      }
-      inv[i][j] = s2;
-      inv[j][i] = s2;
-    }
-  return ok;
-}
-
-// ===========================================================================
-// interval setup: one thread per slow interval k (paper index k+1) computes,
-// from p(x_{k-1,l}|y_{1:k-1}) and y_k, the fast-filter blocks it needs
-// (Eq. 17 on the blocks of Remark 2) and the parallel IMS element (Eq. 29):
-//   X = P C_bar^T, S_y = C_bar X + R_x, kap = S_y^-1 (y - C_bar m),
-//   U_i = A^i X + V_i H^T   (U_i = sum_j P^-_{ij} H^T),
-//   m^f_i = A^i m + U_i kap,  P^f_{ij} = A^i P A^{jT} + Cov(e_i,e_j) - U_i S_y^-1 U_j^T,
-//   P^-_{k+1,1} = A P^f_{ll} A^T + Q,  Z = A^T (P^-_{k+1,1})^-1,
-//   E_k = P^f_{1l} Z,  g_k = m^f_1 - E_k A m^f_l,  S_k = P^f_{11} - E_k A (P^f_{1l})^T
-// (last interval: E = 0, g = m^f_1, S = P^f_{11}).  The record keeps what the
-// recovery reuses.  Runs in TR (float64 except in the float32 mode).
-// ===========================================================================
-template <int NX, class T, class TR>
-__global__ void __launch_bounds__(64) interval_setup_kernel(Ctx c) {
-  constexpr int NN = NX * NX;
-  using RL = Rec<NX>;
-  using SLy = SL<NX>;
-  const long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (!c.ctr->call_ok || gi >= c.total_slow) return;
-  const int s = find_segment(c.meta.off_slow, c.n_seq, gi);
-  const long long k = gi - c.meta.off_slow[s];
-  const int N = c.meta.nslow[s], l = c.meta.ratio[s], m = c.ny;
-  const double* md = c.model + (long long)s * c.ml.stride;
-  const double* Apow = md + c.ml.Apow;
-  const double* Al = Apow + (long long)l * NN;
-  const double* A1 = Apow + NN;
-  const double* Cb = md + c.ml.Cb;
-  const double* Rx = md + c.ml.Rx;
-
-  TR P[NX][NX], mv[NX];
-  if (k == 0) {
-#pragma unroll
-    for (int r = 0; r < NX; ++r) {
-      mv[r] = (TR)c.m0[(long long)s * NX + r];
-#pragma unroll
-      for (int q = 0; q < NX; ++q) P[r][q] = (TR)c.P0[(long long)s * NN + r * NX + q];
-    }
-  } else {
-    const TR* f = (const TR*)c.fout + (gi - 1) * (NX + NN);
-#pragma unroll
-    for (int r = 0; r < NX; ++r) {
-      mv[r] = (TR)f[r];
-#pragma unroll
-      for (int q = 0; q < NX; ++q) P[r][q] = (TR)f[NX + r * NX + q];
-    }
-  }
-  // X = P C_bar^T (columns >= m are zero)
-  TR X[NX][MY];
-#pragma unroll
-  for (int r = 0; r < NX; ++r)
-#pragma unroll
-    for (int j = 0; j < MY; ++j) {
-      TR s2 = TR(0);
-      if (j < m) {
-#pragma unroll
-        for (int q = 0; q < NX; ++q) s2 = fma(P[r][q], (TR)Cb[j * NX + q], s2);
-      }
-      X[r][j] = s2;
-    }
-  // S_y = C_bar X + R_x, padded with the identity
-  TR Sy[MY][MY], Si[MY][MY];
-#pragma unroll
-  for (int i = 0; i < MY; ++i)
-#pragma unroll
-    for (int j = 0; j < MY; ++j) {
-      TR v = (i == j) ? TR(1) : TR(0);
-      if (i < m && j < m) {
-        v = (TR)Rx[i * m + j];
-#pragma unroll
-        for (int q = 0; q < NX; ++q) v = fma((TR)Cb[i * NX + q], X[q][j], v);
-      }
-      Sy[i][j] = v;
-    }
-#pragma unroll
-  for (int i = 0; i < MY; ++i)
-#pragma unroll
-    for (int j = i + 1; j < MY; ++j) { const TR v = TR(0.5) * (Sy[i][j] + Sy[j][i]); Sy[i][j] = v; Sy[j][i] = v; }
-  bool ok = spd_inverse<MY, TR>(Sy, Si, m);
-  TR kap[MY];
-  {
-    TR e[MY];
-    const double* yk = c.y + gi * m;
-#pragma unroll
-    for (int j = 0; j < MY; ++j) {
-      TR v = TR(0);
-      if (j < m) {
-        v = (TR)yk[j];
-#pragma unroll
-        for (int q = 0; q < NX; ++q) v = fma(-(TR)Cb[j * NX + q], mv[q], v);
-      }
-      e[j] = v;
-    }
-#pragma unroll
-    for (int i = 0; i < MY; ++i) {
-      TR v = TR(0);
-#pragma unroll
-      for (int j = 0; j < MY; ++j)
-        if (i < m && j < m) v = fma(Si[i][j], e[j], v);
-      kap[i] = v;
-    }
-  }
-  // U_l = A^l X + V_l H^T ; SUl = S_y^-1 U_l^T ; m^f_l
-  TR Ul[NX][MY], SUl[MY][NX], ml[NX];
-  {
-    const double* VHl = md + c.ml.VH + (long long)(l - 1) * NX * m;
-#pragma unroll
-    for (int r = 0; r < NX; ++r)
-#pragma unroll
-      for (int j = 0; j < MY; ++j) {
-        TR v = TR(0);
-        if (j < m) {
-          v = (TR)VHl[r * m + j];
-#pragma unroll
-          for (int q = 0; q < NX; ++q) v = fma((TR)Al[r * NX + q], X[q][j], v);
-        }
-        Ul[r][j] = v;
-      }
-#pragma unroll
-    for (int i = 0; i < MY; ++i)
-#pragma unroll
-      for (int r = 0; r < NX; ++r) {
-        TR v = TR(0);
-#pragma unroll
-        for (int j = 0; j < MY; ++j)
-          if (i < m && j < m) v = fma(Si[i][j], Ul[r][j], v);
-        SUl[i][r] = v;
-      }
-#pragma unroll
-    for (int r = 0; r < NX; ++r) {
-      TR v = TR(0);
-#pragma unroll
-      for (int q = 0; q < NX; ++q) v = fma((TR)Al[r * NX + q], mv[q], v);
-#pragma unroll
-      for (int j = 0; j < MY; ++j)
-        if (j < m) v = fma(Ul[r][j], kap[j], v);
-      ml[r] = v;
-    }
-  }
-  // Pl = P A^{lT};  P^f_{ll} = A^l Pl + Qc_l - U_l SUl
-  TR Pl[NX][NX], Pm[NX][NX];
-#pragma unroll
-  for (int r = 0; r < NX; ++r)
-#pragma unroll
-    for (int q = 0; q < NX; ++q) {
-      TR v = TR(0);
-#pragma unroll
-      for (int t = 0; t < NX; ++t) v = fma(P[r][t], (TR)Al[q * NX + t], v);
-      Pl[r][q] = v;
-    }
-  {
-    TR Pll[NX][NX];
-    const double* Qcl = md + c.ml.Qc + (long long)(l - 1) * NN;
-#pragma unroll
-    for (int r = 0; r < NX; ++r)
-#pragma unroll
-      for (int q = r; q < NX; ++q) {
-        TR v = (TR)Qcl[r * NX + q];
-#pragma unroll
-        for (int t = 0; t < NX; ++t) v = fma((TR)Al[r * NX + t], Pl[t][q], v);
-#pragma unroll
-        for (int j = 0; j < MY; ++j)
-          if (j < m) v = fma(-Ul[r][j], SUl[j][q], v);
-        Pll[r][q] = v;
-        Pll[q][r] = v;
-      }
-    // P^-_{k+1,1} = A P^f_{ll} A^T + Q
-    TR AP[NX][NX];
-#pragma unroll
-    for (int r = 0; r < NX; ++r)
-#pragma unroll
-      for (int q = 0; q < NX; ++q) {
-        TR v = TR(0);
-#pragma unroll
-        for (int t = 0; t < NX; ++t) v = fma((TR)A1[r * NX + t], Pll[t][q], v);
-        AP[r][q] = v;
-      }
-    const double* Qm = md + c.ml.Q;
-#pragma unroll
-    for (int r = 0; r < NX; ++r)
-#pragma unroll
-      for (int q = r; q < NX; ++q) {
-        TR v = (TR)(0.5 * (Qm[r * NX + q] + Qm[q * NX + r]));
-#pragma unroll
-        for (int t = 0; t < NX; ++t) v = fma(AP[r][t], (TR)A1[q * NX + t], v);
-        Pm[r][q] = v;
-        Pm[q][r] = v;
-      }
-  }
-  TR Z[NX][NX];
-  {
-    TR Pmi[NX][NX];
-    ok &= spd_inverse<NX, TR>(Pm, Pmi);
-#pragma unroll
-    for (int r = 0; r < NX; ++r)
-#pragma unroll
-      for (int q = 0; q < NX; ++q) {
-        TR v = TR(0);
-#pragma unroll
-        for (int t = 0; t < NX; ++t) v = fma((TR)A1[t * NX + r], Pmi[t][q], v);
-        Z[r][q] = v;
-      }
-  }
-  // record
-  {
-    TR* rc = (TR*)c.rec + gi * RL::SIZE;
-#pragma unroll
-    for (int r = 0; r < NX; ++r) {
-      rc[RL::mv + r] = mv[r];
-      rc[RL::ml + r] = ml[r];
-#pragma unroll
-      for (int q = 0; q < NX; ++q) {
-        rc[RL::P + r * NX + q] = P[r][q];
-        rc[RL::Pl + r * NX + q] = Pl[r][q];
-        rc[RL::Z + r * NX + q] = Z[r][q];
-        rc[RL::Pm + r * NX + q] = Pm[r][q];
-      }
-#pragma unroll
-      for (int j = 0; j < MY; ++j) {
-        rc[RL::X + r * MY + j] = X[r][j];
-        rc[RL::SUl + j * NX + r] = SUl[j][r];
-      }
-    }
-#pragma unroll
-    for (int i = 0; i < MY; ++i) {
-      rc[RL::kap + i] = kap[i];
-#pragma unroll
-      for (int j = 0; j < MY; ++j) rc[RL::Si + i * MY + j] = Si[i][j];
-    }
-  }
-  if (c.smoothing) {
-    // first fast state of the interval: U_1, m^f_1, P^f_{11}, P^f_{1l}
-    const double* VH1 = md + c.ml.VH;
-    const double* Qc1 = md + c.ml.Qc;
-    const double* Ql1 = md + c.ml.Ql;
-    TR U1[NX][MY], m1[NX];
-#pragma unroll
-    for (int r = 0; r < NX; ++r)
-#pragma unroll
-      for (int j = 0; j < MY; ++j) {
-        TR v = TR(0);
-        if (j < m) {
-          v = (TR)VH1[r * m + j];
-#pragma unroll
-          for (int q = 0; q < NX; ++q) v = fma((TR)A1[r * NX + q], X[q][j], v);
-        }
-        U1[r][j] = v;
-      }
-#pragma unroll
-    for (int r = 0; r < NX; ++r) {
-      TR v = TR(0);
-#pragma unroll
-      for (int q = 0; q < NX; ++q) v = fma((TR)A1[r * NX + q], mv[q], v);
-#pragma unroll
-      for (int j = 0; j < MY; ++j)
-        if (j < m) v = fma(U1[r][j], kap[j], v);
-      m1[r] = v;
-    }
-    TR P11[NX][NX], P1l[NX][NX];
-    {
-      TR US[NX][MY], AP[NX][NX];
-#pragma unroll
-      for (int r = 0; r < NX; ++r)
-#pragma unroll
-        for (int j = 0; j < MY; ++j) {
-          TR v = TR(0);
-#pragma unroll
-          for (int jj = 0; jj < MY; ++jj)
-            if (jj < m && j < m) v = fma(U1[r][jj], Si[jj][j], v);
-          US[r][j] = v;
-        }
-#pragma unroll
-      for (int r = 0; r < NX; ++r)
-#pragma unroll
-        for (int q = 0; q < NX; ++q) {
-          TR v = TR(0);
-#pragma unroll
-          for (int t = 0; t < NX; ++t) v = fma((TR)A1[r * NX + t], P[t][q], v);
-          AP[r][q] = v;
-        }
-#pragma unroll
-      for (int r = 0; r < NX; ++r)
-#pragma unroll
-        for (int q = r; q < NX; ++q) {
-          TR v = (TR)(0.5 * (Qc1[r * NX + q] + Qc1[q * NX + r]));
-#pragma unroll
-          for (int t = 0; t < NX; ++t) v = fma(AP[r][t], (TR)A1[q * NX + t], v);
-#pragma unroll
-          for (int j = 0; j < MY; ++j)
-            if (j < m) v = fma(-US[r][j], U1[q][j], v);
-          P11[r][q] = v;
-          P11[q][r] = v;
-        }
-#pragma unroll
-      for (int r = 0; r < NX; ++r)
-#pragma unroll
-        for (int q = 0; q < NX; ++q) {
-          TR v = (TR)Ql1[r * NX + q];
-#pragma unroll
-          for (int t = 0; t < NX; ++t) v = fma((TR)A1[r * NX + t], Pl[t][q], v);
-#pragma unroll
-          for (int j = 0; j < MY; ++j)
-            if (j < m) v = fma(-U1[r][j], SUl[j][q], v);
-          P1l[r][q] = v;
-        }
-    }
-    T* se = (T*)c.selem + gi * SLy::SIZE;
-    if (k < N - 1) {
-      TR E[NX][NX], Aml[NX], AP1[NX][NX];
-#pragma unroll
-      for (int r = 0; r < NX; ++r)
-#pragma unroll
-        for (int q = 0; q < NX; ++q) {
-          TR v = TR(0);
-#pragma unroll
-          for (int t = 0; t < NX; ++t) v = fma(P1l[r][t], Z[t][q], v);
-          E[r][q] = v;
-        }
-#pragma unroll
-      for (int r = 0; r < NX; ++r) {
-        TR v = TR(0);
-#pragma unroll
-        for (int q = 0; q < NX; ++q) v = fma((TR)A1[r * NX + q], ml[q], v);
-        Aml[r] = v;
-      }
-      // A (P^f_{1l})^T
-#pragma unroll
-      for (int r = 0; r < NX; ++r)
-#pragma unroll
-        for (int q = 0; q < NX; ++q) {
-          TR v = TR(0);
-#pragma unroll
-          for (int t = 0; t < NX; ++t) v = fma((TR)A1[r * NX + t], P1l[q][t], v);
-          AP1[r][q] = v;
-        }
-#pragma unroll
-      for (int r = 0; r < NX; ++r) {
-        TR v = m1[r];
-#pragma unroll
-        for (int q = 0; q < NX; ++q) v = fma(-E[r][q], Aml[q], v);
-        se[SLy::g + r] = (T)v;
-#pragma unroll
-        for (int q = 0; q < NX; ++q) se[SLy::E + r * NX + q] = (T)E[r][q];
-      }
-      // S_k = P^f_{11} - E_k A (P^f_{1l})^T, symmetrised in TR
-      TR S[NX][NX];
-#pragma unroll
-      for (int r = 0; r < NX; ++r)
-#pragma unroll
-        for (int q = 0; q < NX; ++q) {
-          TR v = P11[r][q];
-#pragma unroll
-          for (int t = 0; t < NX; ++t) v = fma(-E[r][t], AP1[t][q], v);
-          S[r][q] = v;
-        }
-#pragma unroll
-      for (int r = 0; r < NX; ++r)
-#pragma unroll
-        for (int q = r; q < NX; ++q) {
-          const T v = (T)(TR(0.5) * (S[r][q] + S[q][r]));
-          se[SLy::S + r * NX + q] = v;
-          se[SLy::S + q * NX + r] = v;
-        }
-    } else {
-#pragma unroll
-      for (int r = 0; r < NX; ++r) {
-        se[SLy::g + r] = (T)m1[r];
-#pragma unroll
-        for (int q = 0; q < NX; ++q) {
-          se[SLy::E + r * NX + q] = T(0);
-          se[SLy::S + r * NX + q] = (T)P11[r][q];
-        }
-      }
-    }
-  }
-  if (!ok) raise_err(c.ctr, DEVERR_SINGULAR);
 }
 
 // ===========================================================================
@@ -1065,7 +1098,8 @@ int query_shapes_t(int scan_groups, int scan_elems, int recover_threads, int sm_
   sh->grid_f = (int)std::max(1LL, std::min((long long)std::max(nb, 1) * sm_count, tiles));
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, scan_kernel<SOp>, threads, sh->smem_s);
   sh->grid_s = (int)std::max(1LL, std::min((long long)std::max(nb, 1) * sm_count, tiles));
-  sh->grid_setup = (int)((total_slow + 63) / 64);
+  sh->grid_setup = 0;
+  sh->smem_setup = 0;
   sh->recover_threads = recover_threads;
   if (cudaGetLastError() != cudaSuccess) return SRTM_ERR_CUDA;
   return SRTM_OK;
@@ -1099,8 +1133,7 @@ int launch_t(const Ctx& c, const Shapes& sh, cudaStream_t st, cudaEvent_t* ev) {
   if (ev) cudaEventRecord(ev[0], st);
   scan_kernel<FOp><<<sh.grid_f, sh.scan_groups_f * G, sh.smem_f, st>>>(c, sh.scan_groups_f, sh.scan_elems_f);
   if (ev) cudaEventRecord(ev[1], st);
-  interval_setup_kernel<NX, T, TR><<<sh.grid_setup, 64, 0, st>>>(c);
-  if (ev) cudaEventRecord(ev[2], st);
+  if (ev) cudaEventRecord(ev[2], st);  // the interval setup runs inside the filter scan
   if (c.smoothing)
     scan_kernel<SOp><<<sh.grid_s, sh.scan_groups_s * G, sh.smem_s, st>>>(c, sh.scan_groups_s, sh.scan_elems_s);
   if (ev) cudaEventRecord(ev[3], st);

@@ -74,9 +74,11 @@ __global__ void __launch_bounds__(1024) meta_kernel(Ctx c) {
 }
 
 // ev (optional): two events recorded before and after the metadata kernel.
+// A single sequence needs no scan over sequences: its metadata is written by
+// the constants kernel instead (c.fold_meta), saving this launch.
 int launch_meta(const Ctx& c, cudaStream_t st, cudaEvent_t* ev) {
   if (ev) cudaEventRecord(ev[0], st);
-  meta_kernel<<<1, 1024, 0, st>>>(c);
+  if (!c.fold_meta) meta_kernel<<<1, 1024, 0, st>>>(c);
   if (ev) cudaEventRecord(ev[1], st);
   return cudaGetLastError() == cudaSuccess ? SRTM_OK : SRTM_ERR_CUDA;
 }

@@ -262,6 +262,7 @@ int single(const srtm_problem* p, srtm_precision prec, const srtm_output* out, c
   Ctx c;
   memset(&c, 0, sizeof c);
   c.n_seq = 1;
+  c.fold_meta = 1;
   c.nx = p->nx;
   c.ny = p->ny;
   c.max_ratio = p->ratio;
@@ -448,7 +449,7 @@ int srtm_get_tuning(int nx, srtm_precision prec, srtm_tuning* t) {
   return SRTM_OK;
 }
 
-int srtm_launches_per_call(int smoothing) { return smoothing ? 6 : 5; }
+int srtm_launches_per_call(int smoothing, int batched) { return (smoothing ? 4 : 3) + (batched ? 1 : 0); }
 
 int srtm_set_stage_timing(int enable) {
   std::lock_guard<std::mutex> lk(g_mu);
@@ -511,6 +512,7 @@ extern "C" int srtm_smoother_noalloc(const srtm_problem* p, srtm_precision prec,
   Ctx c;
   memset(&c, 0, sizeof c);
   c.n_seq = 1;
+  c.fold_meta = 1;
   c.nx = p->nx;
   c.ny = p->ny;
   c.max_ratio = p->ratio;

@@ -117,6 +117,7 @@ struct SL {
 struct Ctx {
   int n_seq, nx, ny, max_ratio;
   int smoothing;                      // 1: smoother call, 0: filter only
+  int fold_meta;                      // 1: single sequence, metadata written by the constants kernel
   int uniform_ratio, uniform_nslow;   // used when in_ratio/in_nslow are NULL
   long long total_slow, total_fast;   // declared totals (validated on the device)
   const int* in_ratio;
@@ -172,7 +173,7 @@ struct Shapes {  // resolved launch shapes for one call
   int scan_groups_f, scan_elems_f, scan_groups_s, scan_elems_s;
   int recover_threads;
   int grid_f, grid_s, grid_setup;
-  size_t smem_f, smem_s;
+  size_t smem_f, smem_s, smem_setup;
 };
 
 template <int NX>

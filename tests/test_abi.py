@@ -71,5 +71,6 @@ def test_tuning_validation_and_roundtrip(lib):
 
 
 def test_launch_counts(lib):
-    assert lib.srtm_launches_per_call(1) == 6
-    assert lib.srtm_launches_per_call(0) == 5
+    assert lib.srtm_launches_per_call(1, 0) == 4
+    assert lib.srtm_launches_per_call(0, 0) == 3
+    assert lib.srtm_launches_per_call(1, 1) == 5
