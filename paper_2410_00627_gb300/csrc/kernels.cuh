@@ -101,15 +101,119 @@ __device__ __forceinline__ bool spd_inverse(const T (&a)[N][N], T (&inv)[N][N], 
 // the interval from the slot (a warp FP64 instruction costs the same whatever
 // its active lanes, so the repetition is free).
 // ===========================================================================
+// zero, infinite or NaN test on the bit pattern
+__device__ __forceinline__ bool bad_value(double x) { return bad_pivot(x); }
+__device__ __forceinline__ bool bad_value(float x) { return bad_pivot(x); }
+
+// Inverse of a small symmetric m x m matrix (m <= MY, runtime) held in the
+// leading block of a: adjugate for m <= 3 (one division), Cholesky for m = 4.
+// The rest of inv is the identity.  Returns false on a singular matrix.
+template <class TR>
+__device__ __forceinline__ bool small_sym_inverse(const TR (&a)[MY][MY], TR (&inv)[MY][MY], int m) {
+#pragma unroll
+  for (int i = 0; i < MY; ++i)
+#pragma unroll
+    for (int j = 0; j < MY; ++j) inv[i][j] = (i == j) ? TR(1) : TR(0);
+  if (m == 4) return spd_inverse<MY, TR>(a, inv, 4);
+  TR det;
+  if (m == 1) {
+    det = a[0][0];
+  } else if (m == 2) {
+    det = a[0][0] * a[1][1] - a[0][1] * a[1][0];
+  } else {
+    det = a[0][0] * (a[1][1] * a[2][2] - a[1][2] * a[2][1]) - a[0][1] * (a[1][0] * a[2][2] - a[1][2] * a[2][0]) +
+          a[0][2] * (a[1][0] * a[2][1] - a[1][1] * a[2][0]);
+  }
+  bool ok = !bad_value(det);
+  if (!ok) det = TR(1);
+  const TR id = TR(1) / det;
+  if (m == 1) {
+    inv[0][0] = id;
+  } else if (m == 2) {
+    inv[0][0] = a[1][1] * id;
+    inv[1][1] = a[0][0] * id;
+    inv[0][1] = -a[0][1] * id;
+    inv[1][0] = -a[1][0] * id;
+  } else {
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const int i0 = c == 0 ? 1 : 0, i1 = c == 2 ? 1 : 2, j0 = r == 0 ? 1 : 0, j1 = r == 2 ? 1 : 2;
+        TR v = a[i0][j0] * a[i1][j1] - a[i0][j1] * a[i1][j0];
+        inv[r][c] = (((r + c) & 1) ? -v : v) * id;
+      }
+  }
+  return ok;
+}
+
+// Row r of the inverse of an NX x NX matrix a (row-major), NX <= 4, by the
+// adjugate (for NX = 4 the cofactors come from the 2x2 complementary minors
+// of rows (0,1) and (2,3)).  Returns false on a zero or non-finite determinant.
+template <int NX, class TR>
+__device__ __forceinline__ bool inverse_row_small(const TR* a, int r, TR* out) {
+  TR det;
+  if (NX == 1) {
+    det = a[0];
+  } else if (NX == 2) {
+    det = a[0] * a[3] - a[1] * a[2];
+  } else if (NX == 3) {
+    det = a[0] * (a[4] * a[8] - a[5] * a[7]) - a[1] * (a[3] * a[8] - a[5] * a[6]) + a[2] * (a[3] * a[7] - a[4] * a[6]);
+  } else {
+    TR sm[6], cm[6];
+#pragma unroll
+    for (int v = 0; v < 6; ++v) {
+      const int p = v < 3 ? 0 : (v < 5 ? 1 : 2), q = v < 3 ? v + 1 : (v < 5 ? v - 1 : 3);
+      sm[v] = a[0 * 4 + p] * a[1 * 4 + q] - a[1 * 4 + p] * a[0 * 4 + q];
+      cm[v] = a[2 * 4 + p] * a[3 * 4 + q] - a[3 * 4 + p] * a[2 * 4 + q];
+    }
+    det = sm[0] * cm[5] - sm[1] * cm[4] + sm[2] * cm[3] + sm[3] * cm[2] - sm[4] * cm[1] + sm[5] * cm[0];
+    bool ok = !bad_value(det);
+    if (!ok) det = TR(1);
+    const TR id = TR(1) / det;
+    const int code = r == 0 ? 0x543 : (r == 1 ? 0x521 : (r == 2 ? 0x420 : 0x310));
+    const int k0 = r > 0 ? 0 : 1, k1 = r > 1 ? 1 : 2, k2 = r > 2 ? 2 : 3;
+#pragma unroll
+    for (int col = 0; col < 4; ++col) {
+      const int arow = col ^ 1;
+      const TR* mins = col < 2 ? cm : sm;
+      TR v = a[arow * 4 + k0] * mins[(code >> 8) & 15];
+      v = fma(-a[arow * 4 + k1], mins[(code >> 4) & 15], v);
+      v = fma(a[arow * 4 + k2], mins[code & 15], v);
+      if (((col & 1) != 0) != ((r & 1) != 0)) v = -v;
+      out[col] = v * id;
+    }
+    return ok;
+  }
+  bool ok = !bad_value(det);
+  if (!ok) det = TR(1);
+  const TR id = TR(1) / det;
+#pragma unroll
+  for (int col = 0; col < NX; ++col) {
+    TR v;
+    if (NX == 1) {
+      v = TR(1);
+    } else if (NX == 2) {
+      v = (r == col) ? a[(1 - r) * 3] : -a[r * 2 + col];
+    } else {
+      const int i0 = col == 0 ? 1 : 0, i1 = col == 2 ? 1 : 2, j0 = r == 0 ? 1 : 0, j1 = r == 2 ? 1 : 2;
+      v = a[i0 * 3 + j0] * a[i1 * 3 + j1] - a[i0 * 3 + j1] * a[i1 * 3 + j0];
+      if ((r + col) & 1) v = -v;
+    }
+    out[col] = v * id;
+  }
+  return ok;
+}
+
 template <int NX>
 struct SetupGeom {
   static constexpr int SG = NX == 1 ? 1 : (NX == 2 ? 2 : (NX <= 4 ? 4 : 8));
   static constexpr int NN = NX * NX, NM = NX * MY;
-  // slot layout (units of TR); S, AP1 and P11 reuse Pll, AP and Pm, whose
-  // last reads precede them
+  // slot layout (units of TR); Aml, AP1 and P11 reuse Pll, AP and Pm, whose
+  // last reads precede them (AP also holds the rows of (P^-)^{-1} for NX <= 4)
   static constexpr int P = 0, mv = P + NN, X = mv + NX, SUl = X + NM, ml = SUl + NM, Pl = ml + NX, Pll = Pl + NN,
                        AP = Pll + NN, Pm = AP + NN, Z = Pm + NN, U1 = Z + NN, P1l = U1 + NM, SLOT = P1l + NN;
-  static constexpr int S = Pll, AP1 = AP, P11 = Pm;
+  static constexpr int Aml = Pll, AP1 = AP, P11 = Pm;
 };
 
 // One interval by its SG lanes (lane = row), slot sb in shared memory.
@@ -185,7 +289,7 @@ __device__ void setup_interval(const Ctx& c, long long gi, int lane, unsigned ma
         Sy[i][j] = v;
         Sy[j][i] = v;
       }
-    ok &= spd_inverse<MY, TR>(Sy, Si, m);
+    ok &= small_sym_inverse<TR>(Sy, Si, m);
     TR e[MY];
     const double* yk = c.y + gi * m;
 #pragma unroll
@@ -271,25 +375,46 @@ __device__ void setup_interval(const Ctx& c, long long gi, int lane, unsigned ma
     }
   }
   __syncwarp(mask);
-  // P^-_{k+1,1} = (A P^f_{ll}) A^T + Q (row r)
+  // P^-_{k+1,1} = (A P^f_{ll}) A^T + Q (row r, upper triangle, mirrored)
   if (row) {
     const double* Qm = md + c.ml.Q;
 #pragma unroll
     for (int q = 0; q < NX; ++q) {
-      TR v = (TR)Qm[r * NX + q];
+      if (q >= r) {
+        TR v = (TR)Qm[r * NX + q];
 #pragma unroll
-      for (int t = 0; t < NX; ++t) v = fma(sb[Gm::AP + r * NX + t], (TR)A1[q * NX + t], v);
-      sb[Gm::Pm + r * NX + q] = v;
+        for (int t = 0; t < NX; ++t) v = fma(sb[Gm::AP + r * NX + t], (TR)A1[q * NX + t], v);
+        sb[Gm::Pm + r * NX + q] = v;
+        sb[Gm::Pm + q * NX + r] = v;
+      }
     }
   }
   __syncwarp(mask);
-  // (P^-)^{-1} (every lane, symmetrised), Z = A^T (P^-)^{-1} (row r)
-  {
+  // (P^-)^{-1}: row r by the adjugate (NX <= 4) into the AP slot; above,
+  // every lane forms the whole inverse by Cholesky.  Z = A^T (P^-)^{-1} (row r).
+  if constexpr (NX <= 4) {
+    if (row) {
+      TR rowv[NX];
+      ok &= inverse_row_small<NX, TR>(sb + Gm::Pm, r, rowv);
+#pragma unroll
+      for (int q = 0; q < NX; ++q) sb[Gm::AP + r * NX + q] = rowv[q];
+    }
+    __syncwarp(mask);
+    if (row) {
+#pragma unroll
+      for (int q = 0; q < NX; ++q) {
+        TR v = TR(0);
+#pragma unroll
+        for (int t = 0; t < NX; ++t) v = fma((TR)A1[t * NX + r], sb[Gm::AP + t * NX + q], v);
+        sb[Gm::Z + r * NX + q] = v;
+      }
+    }
+  } else {
     TR Pmv[NX][NX], Pmi[NX][NX];
 #pragma unroll
     for (int i = 0; i < NX; ++i)
 #pragma unroll
-      for (int j = 0; j < NX; ++j) Pmv[i][j] = TR(0.5) * (sb[Gm::Pm + i * NX + j] + sb[Gm::Pm + j * NX + i]);
+      for (int j = 0; j < NX; ++j) Pmv[i][j] = sb[Gm::Pm + i * NX + j];
     ok &= spd_inverse<NX, TR>(Pmv, Pmi);
     if (row) {
 #pragma unroll
@@ -313,7 +438,7 @@ __device__ void setup_interval(const Ctx& c, long long gi, int lane, unsigned ma
         rc[RL::P + r * NX + q] = sb[Gm::P + r * NX + q];
         rc[RL::Pl + r * NX + q] = sb[Gm::Pl + r * NX + q];
         rc[RL::Z + r * NX + q] = sb[Gm::Z + r * NX + q];
-        rc[RL::Pm + r * NX + q] = TR(0.5) * (sb[Gm::Pm + r * NX + q] + sb[Gm::Pm + q * NX + r]);
+        rc[RL::Pm + r * NX + q] = sb[Gm::Pm + r * NX + q];
       }
 #pragma unroll
       for (int j = 0; j < MY; ++j) {
@@ -353,6 +478,10 @@ __device__ void setup_interval(const Ctx& c, long long gi, int lane, unsigned ma
 #pragma unroll
       for (int j = 0; j < MY; ++j)
         if (j < m) m1 = fma(U1[j], kap[j], m1);
+      TR aml = TR(0);
+#pragma unroll
+      for (int t = 0; t < NX; ++t) aml = fma((TR)A1[r * NX + t], sb[Gm::ml + t], aml);
+      sb[Gm::Aml + r] = aml;
     }
     __syncwarp(mask);
     if (row) {
@@ -374,13 +503,16 @@ __device__ void setup_interval(const Ctx& c, long long gi, int lane, unsigned ma
       }
 #pragma unroll
       for (int q = 0; q < NX; ++q) {
-        TR v = (TR)(0.5 * (Qc1[r * NX + q] + Qc1[q * NX + r]));
+        if (q >= r) {
+          TR v = (TR)Qc1[r * NX + q];
 #pragma unroll
-        for (int t = 0; t < NX; ++t) v = fma(APr[t], (TR)A1[q * NX + t], v);
+          for (int t = 0; t < NX; ++t) v = fma(APr[t], (TR)A1[q * NX + t], v);
 #pragma unroll
-        for (int j = 0; j < MY; ++j)
-          if (j < m) v = fma(-US[j], sb[Gm::U1 + q * MY + j], v);
-        sb[Gm::P11 + r * NX + q] = v;
+          for (int j = 0; j < MY; ++j)
+            if (j < m) v = fma(-US[j], sb[Gm::U1 + q * MY + j], v);
+          sb[Gm::P11 + r * NX + q] = v;
+          sb[Gm::P11 + q * NX + r] = v;
+        }
         TR w = (TR)Ql1[r * NX + q];
 #pragma unroll
         for (int t = 0; t < NX; ++t) w = fma((TR)A1[r * NX + t], sb[Gm::Pl + t * NX + q], w);
@@ -406,12 +538,7 @@ __device__ void setup_interval(const Ctx& c, long long gi, int lane, unsigned ma
         }
         TR g = m1;
 #pragma unroll
-        for (int q = 0; q < NX; ++q) {
-          TR aml = TR(0);
-#pragma unroll
-          for (int t = 0; t < NX; ++t) aml = fma((TR)A1[q * NX + t], sb[Gm::ml + t], aml);
-          g = fma(-Er[q], aml, g);
-        }
+        for (int q = 0; q < NX; ++q) g = fma(-Er[q], sb[Gm::Aml + q], g);
         se[SLy::g + r] = (T)g;
 #pragma unroll
         for (int q = 0; q < NX; ++q) {
@@ -422,28 +549,25 @@ __device__ void setup_interval(const Ctx& c, long long gi, int lane, unsigned ma
         }
       }
       __syncwarp(mask);
-      // S = P^f_{11} - E A (P^f_{1l})^T (row r), then symmetrised
+      // S = P^f_{11} - E A (P^f_{1l})^T (row r, upper triangle, mirrored)
       if (row) {
 #pragma unroll
         for (int q = 0; q < NX; ++q) {
-          TR v = sb[Gm::P11 + r * NX + q];
+          if (q >= r) {
+            TR v = sb[Gm::P11 + r * NX + q];
 #pragma unroll
-          for (int t = 0; t < NX; ++t) v = fma(-Er[t], sb[Gm::AP1 + t * NX + q], v);
-          sb[Gm::S + r * NX + q] = v;
+            for (int t = 0; t < NX; ++t) v = fma(-Er[t], sb[Gm::AP1 + t * NX + q], v);
+            se[SLy::S + r * NX + q] = (T)v;
+            se[SLy::S + q * NX + r] = (T)v;
+          }
         }
-      }
-      __syncwarp(mask);
-      if (row) {
-#pragma unroll
-        for (int q = 0; q < NX; ++q)
-          se[SLy::S + r * NX + q] = (T)(TR(0.5) * (sb[Gm::S + r * NX + q] + sb[Gm::S + q * NX + r]));
       }
     } else if (row) {
       se[SLy::g + r] = (T)m1;
 #pragma unroll
       for (int q = 0; q < NX; ++q) {
         se[SLy::E + r * NX + q] = T(0);
-        se[SLy::S + r * NX + q] = (T)(TR(0.5) * (sb[Gm::P11 + r * NX + q] + sb[Gm::P11 + q * NX + r]));
+        se[SLy::S + r * NX + q] = (T)sb[Gm::P11 + r * NX + q];
       }
     }
   }
