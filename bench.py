@@ -11,9 +11,19 @@ every timed step, outside the timed events.
 
 Headline `value`: mixed precision (float32 scans with float64 solves,
 symmetrisation and recovery).  The same line carries the plain-FP64 number.
+Before timing, the library's autotuner (srtm_autotune) picks the launch shapes
+for the workload; the chosen shapes are reported in `config.tuning`.
+
+`--workload config4`: the ragged batch of config 4 (4096 sequences, nx=4,
+ny=1, ratio in {5,10,20}, 100..20000 slow steps each) as one
+srtm_smoother_batch call captured in a CUDA graph and replayed; outputs (about
+77 GB per step) are far larger than L2, so no flush.  The line adds the plain
+FP64 batched number and the plain FP64 single-sequence path looped over the
+4096 sequences.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-Multi-GPU (torchrun): every rank runs its own independent sequence (weak
+                  [--workload config2|config4]
+Multi-GPU (torchrun): every rank runs its own independent workload (weak
 scaling, no collective on the data path); rank 0 prints.
 """
 from __future__ import annotations
@@ -38,7 +48,7 @@ FP64_PEAK_GFLOPS = 1250.0   # GB300 FP64 nominal (recipe table); no FP64 entry i
 HBM_FALLBACK_GBS = 6800.0
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
@@ -49,7 +59,11 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-extras", action="store_true", help="skip the fp64, e2e and cpu legs")
-    return ap.parse_args()
+    ap.add_argument("--workload", choices=["config2", "config4"], default="config2")
+    ap.add_argument("--n-seq", type=int, default=4096, help="config4: sequences in the batch")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the built-in launch shapes")
+    ap.add_argument("--tune-reps", type=int, default=2)
+    return ap.parse_args(argv)
 
 
 def workload(args, rank=0):
@@ -105,6 +119,20 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
+def reduce_over_ranks(mean_ms, units, dist, device):
+    """Whole-job figures over the ranks: the slowest rank's mean step time and
+    the units (fast states) all ranks processed per step.  Without a process
+    group: this rank's own figures."""
+    if dist is None:
+        return float(mean_ms), float(units)
+    import torch
+    t = torch.tensor([float(mean_ms)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 # --------------------------------------------------------------------------- our arm
 def run_ours(args, rank, world, dist):
     import torch
@@ -155,17 +183,18 @@ def run_ours(args, rank, world, dist):
         api.status()
         return ms, rec_ms
 
+    tuning = {}
+    if not args.no_autotune:
+        precs = [args.precision] + ([] if args.no_extras else ["fp64" if args.precision != "fp64" else "mixed"])
+        for p in precs:
+            tuning[p], _ = api.autotune(*ins, prob.ratio, precision=p, reps=args.tune_reps, out=outs)
     clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
     if clocks:
         clocks.start()
     ms, stages = timed(args.precision, args.steps, args.warmup, stage=True)
     clock_info = clocks.stop() if clocks else None
-    mean_ms = float(np.mean(ms))
-    if dist:
-        tt = torch.tensor([mean_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        mean_ms = float(tt.item())
-    value = world * n_fast / (mean_ms * 1e-3)
+    mean_ms, units = reduce_over_ranks(float(np.mean(ms)), n_fast, dist, dev)
+    value = units / (mean_ms * 1e-3)
     if rank != 0:
         return None
     stage_mean = {k: float(np.mean([s[k] for s in stages])) for k in stages[0]}
@@ -180,7 +209,8 @@ def run_ours(args, rank, world, dist):
         "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"mixed": "f32+f64", "fp64": "f64", "fp32": "f32"}[args.precision],
         "data": "synthetic (seeded generator, config 2 linear kinetics)",
-        "config": config_dict(args, prob, args.precision),
+        "config": dict(config_dict(args, prob, args.precision),
+                       tuning=tuning.get(args.precision, api.get_tuning(prob.nx, args.precision))),
         "stage_ms": stage_mean,
         "roofline": {"bound": "alu", "kernel": "recover_kernel", "achieved": achieved,
                      "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": achieved / FP64_PEAK_GFLOPS,
@@ -192,10 +222,238 @@ def run_ours(args, rank, world, dist):
     if not args.no_extras:
         other = "fp64" if args.precision != "fp64" else "mixed"
         ms2, _ = timed(other, max(5, args.steps // 2), 3)
-        line[other] = {"value": n_fast / (float(np.mean(ms2)) * 1e-3), "ms_per_step": float(np.mean(ms2))}
+        line[other] = {"value": n_fast / (float(np.mean(ms2)) * 1e-3), "ms_per_step": float(np.mean(ms2)),
+                       "tuning": tuning.get(other, api.get_tuning(prob.nx, other))}
         line["e2e"] = run_e2e(args, prob, api, torch, flush)
         line["cpu_baseline"] = run_cpu_baseline(args, prob)
     return line
+
+
+# --------------------------------------------------------------------------- config 4 (batched)
+def batched_workload(args, rank=0):
+    from paper_2410_00627_gb300 import synth
+    workers = max(1, min(16, (os.cpu_count() or 1)))
+    return synth.config4(seed=args.seed + rank, n_seq=args.n_seq, workers=workers)
+
+
+def batched_config(args, pk, precision, tuning):
+    return {"workload": f"config 4: {len(pk['ratio'])} ragged 4-species chains nx=4 ny=1 L in {{5,10,20}} "
+                        f"N in [100,20000] ({pk['total_slow']} slow / {pk['total_fast']} fast steps)",
+            "precision": precision, "n_seq": int(len(pk["ratio"])), "total_slow": pk["total_slow"],
+            "total_fast": pk["total_fast"], "call": "srtm_smoother_batch captured in a CUDA graph, replayed",
+            "l2": "not flushed: each step writes ~160 B per fast step (far above the 129 MB L2)",
+            "seed": args.seed, "tuning": tuning}
+
+
+def upload_batch(pk, api, torch, dev):
+    t = lambda a: torch.as_tensor(a, device=dev)  # noqa: E731
+    ten = {k: t(pk[k]) for k in ("F", "Q", "H", "R", "m0", "P0", "y", "ratio", "n_slow")}
+    b = api.make_batch(ten["F"], ten["Q"], ten["H"], ten["R"], ten["m0"], ten["P0"], ten["y"], ten["ratio"],
+                       ten["n_slow"], pk["max_ratio"], pk["total_slow"], pk["total_fast"])
+    return b, ten
+
+
+def batch_outputs(torch, dev, n_fast, n_slow, nx):
+    return {"fast_mean": torch.empty(n_fast, nx, dtype=torch.float64, device=dev),
+            "fast_cov": torch.empty(n_fast, nx, nx, dtype=torch.float64, device=dev),
+            "slow_mean": torch.empty(n_slow, nx, dtype=torch.float64, device=dev),
+            "slow_cov": torch.empty(n_slow, nx, nx, dtype=torch.float64, device=dev)}
+
+
+def run_batched(args, rank, world, dist):
+    import torch
+
+    from paper_2410_00627_gb300 import api, build, synth
+    build.build()
+    api.load()
+    probs = batched_workload(args, rank)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    pk = synth.pack(probs)
+    batch, ten = upload_batch(pk, api, torch, dev)
+    nx = pk["F"].shape[1]
+    n_fast, n_slow = pk["total_fast"], pk["total_slow"]
+    outs = batch_outputs(torch, dev, n_fast, n_slow, nx)
+    precs = [args.precision] + ([] if args.no_extras else ["fp64" if args.precision != "fp64" else "mixed"])
+    tuning = {}
+    if not args.no_autotune:   # on the first 512 sequences (same distribution, ~1/8 of the work)
+        sub = synth.pack(probs[:min(512, len(probs))])
+        sb, sten = upload_batch(sub, api, torch, dev)
+        so = batch_outputs(torch, dev, sub["total_fast"], sub["total_slow"], nx)
+        for p in precs:
+            tuning[p], _ = api.autotune_batch(sb, precision=p, reps=1, out=so)
+        del sb, sten, so
+    stream = torch.cuda.Stream()
+
+    def graph_for(precision):
+        with torch.cuda.stream(stream):
+            for _ in range(max(1, args.warmup)):
+                api.smoother_batch(batch, precision=precision, out=outs, stream=stream)
+            api.status(stream)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream, capture_error_mode="relaxed"):
+            api.smoother_batch(batch, precision=precision, out=outs, stream=stream)
+        with torch.cuda.stream(stream):
+            g.replay()
+        stream.synchronize()
+        api.status(stream)
+        return g
+
+    def timed_graph(g, steps):
+        ms = []
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        with torch.cuda.stream(stream):   # replay() launches on the current stream
+            for _ in range(steps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                g.replay()
+                e1.record(stream)
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        api.status(stream)
+        return ms
+
+    g = graph_for(args.precision)
+    clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if clocks:
+        clocks.start()
+    ms = timed_graph(g, args.steps)
+    clock_info = clocks.stop() if clocks else None
+    del g
+    mean_ms, units = reduce_over_ranks(float(np.mean(ms)), n_fast, dist, dev)
+    value = units / (mean_ms * 1e-3)
+    # per-launch durations of one ungraphed call (library stage events)
+    api.set_stage_timing(True)
+    try:
+        with torch.cuda.stream(stream):
+            api.smoother_batch(batch, precision=args.precision, out=outs, stream=stream)
+            stage = api.stage_times()
+    finally:
+        api.set_stage_timing(False)
+    api.status(stream)
+    if rank != 0:
+        return None
+    n, m = nx, pk["H"].shape[1]
+    fma_per_fast = 7 * n ** 3 + 3 * n * n * m + n * m * m
+    achieved = 2.0 * fma_per_fast * n_fast / (stage["recovery"] * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"mixed": "f32+f64", "fp64": "f64", "fp32": "f32"}[args.precision],
+        "data": "synthetic (seeded generator, config 4 ragged linear-kinetics batch)",
+        "config": batched_config(args, pk, args.precision, tuning.get(args.precision,
+                                                                       api.get_tuning(nx, args.precision))),
+        "stage_ms": stage,
+        "roofline": {"bound": "alu", "kernel": "recover_kernel", "achieved": achieved,
+                     "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": achieved / FP64_PEAK_GFLOPS,
+                     "peak_source": "GB300 FP64 nominal 1.25 TFLOP/s (recipe table)",
+                     "flops_per_fast_step": 2 * fma_per_fast, "traffic": None},
+        "gpu_launches": args.steps * api.launches_per_call(True, True),
+        "clocks": clock_info,
+    }
+    if not args.no_extras:
+        other = precs[1]
+        g2 = graph_for(other)
+        ms2 = timed_graph(g2, max(2, args.steps // 2))
+        del g2
+        line[other + "_batched"] = {"value": n_fast / (float(np.mean(ms2)) * 1e-3),
+                                    "ms_per_step": float(np.mean(ms2)),
+                                    "tuning": tuning.get(other, api.get_tuning(nx, other))}
+        line["fp64_single_sequence_loop"] = run_single_loop(probs, pk, ten, outs, api, torch, stream)
+        line["e2e"] = run_batched_e2e(args, pk, batch, ten, outs, api, torch, stream)
+        line["cpu_baseline"] = run_cpu_baseline_batched(args, probs)
+    return line
+
+
+def run_single_loop(probs, pk, ten, outs, api, torch, stream):
+    """The plain FP64 single-sequence path (srtm_smoother) called once per
+    sequence of the batch, into the same output buffers, timed as one loop."""
+    off_s = np.concatenate([[0], np.cumsum(pk["n_slow"].astype(np.int64))])
+    off_f = np.concatenate([[0], np.cumsum(pk["n_slow"].astype(np.int64) * pk["ratio"])])
+
+    def one(s):
+        sl_s, sl_f = slice(int(off_s[s]), int(off_s[s + 1])), slice(int(off_f[s]), int(off_f[s + 1]))
+        o = {"fast_mean": outs["fast_mean"][sl_f], "fast_cov": outs["fast_cov"][sl_f],
+             "slow_mean": outs["slow_mean"][sl_s], "slow_cov": outs["slow_cov"][sl_s]}
+        api.smoother(ten["F"][s], ten["Q"][s], ten["H"][s], ten["R"][s], ten["m0"][s], ten["P0"][s],
+                     ten["y"][sl_s], int(pk["ratio"][s]), precision="fp64", out=o, stream=stream)
+
+    with torch.cuda.stream(stream):
+        for s in range(min(32, len(probs))):
+            one(s)
+        api.status(stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for s in range(len(probs)):
+            one(s)
+        e1.record(stream)
+        e1.synchronize()
+        api.status(stream)
+    ms = e0.elapsed_time(e1)
+    return {"value": pk["total_fast"] / (ms * 1e-3), "ms_per_step": ms, "calls": len(probs),
+            "api": "srtm_smoother (FP64) once per sequence, same stream"}
+
+
+def run_batched_e2e(args, pk, batch, ten, outs, api, torch, stream):
+    """Batched step with its host traffic: the inputs copied from pinned host
+    memory into the batch's device buffers, the captured call, and the
+    slow-rate outputs (means and covariances) read back to pinned host memory.
+    The fast-rate outputs stay in HBM."""
+    keys = ("F", "Q", "H", "R", "m0", "P0", "y", "ratio", "n_slow")
+    host_in = {}
+    for k in keys:
+        h = torch.empty(pk[k].shape, dtype=ten[k].dtype, pin_memory=True)
+        h.numpy()[...] = pk[k]
+        host_in[k] = h
+    host_out = {k: torch.empty(outs[k].shape, dtype=torch.float64, pin_memory=True) for k in ("slow_mean", "slow_cov")}
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(stream):
+        api.smoother_batch(batch, precision=args.precision, out=outs, stream=stream)
+        api.status(stream)
+    with torch.cuda.graph(g, stream=stream, capture_error_mode="relaxed"):
+        api.smoother_batch(batch, precision=args.precision, out=outs, stream=stream)
+    ms = []
+    steps = max(2, args.steps // 2)
+    with torch.cuda.stream(stream):
+        for _ in range(steps + 1):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for k in keys:
+                ten[k].copy_(host_in[k], non_blocking=True)
+            g.replay()
+            for k, h in host_out.items():
+                h.copy_(outs[k], non_blocking=True)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        api.status(stream)
+    ms = ms[1:]
+    h2d = sum(h.numel() * h.element_size() for h in host_in.values())
+    d2h = sum(h.numel() * h.element_size() for h in host_out.values())
+    return {"value": pk["total_fast"] / (float(np.mean(ms)) * 1e-3), "unit": UNIT, "ms_per_step": float(np.mean(ms)),
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "api": "pinned host inputs -> device batch, srtm_smoother_batch (graph), slow-rate outputs -> pinned host"}
+
+
+def run_cpu_baseline_batched(args, probs, seconds=None):
+    import oracle
+    oracle.build()
+    seconds = args.cpu_seconds if seconds is None else seconds
+    n, t0 = 0, time.perf_counter()
+    used = 0
+    for p in probs:
+        oracle.sequential(p)
+        n += p.n_slow * p.ratio
+        used += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    el = time.perf_counter() - t0
+    return {"value": n / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"the first {used} sequences of the batch ({n} fast steps) in {el:.1f} s, 1 thread, FP64 C"}
 
 
 def recorded_traffic(precision, n_fast):
@@ -279,7 +537,25 @@ def run_cpu_baseline(args, prob):
 
 
 def run_reference(args):
-    """Reference arm: the FP64 CPU oracle on the host cores, same workload."""
+    """Reference arm: the FP64 CPU oracle on the host cores, same workload
+    (config 4: the first sequences of the batch, about --cpu-seconds of work
+    per step)."""
+    if args.workload == "config4":
+        probs = batched_workload(args)
+        import oracle
+        oracle.build()
+        from paper_2410_00627_gb300 import synth
+        pk = synth.pack(probs)
+        vals = [run_cpu_baseline_batched(args, probs, seconds=args.cpu_seconds / 4) for _ in range(args.warmup)]
+        vals = [run_cpu_baseline_batched(args, probs, seconds=args.cpu_seconds / 2) for _ in range(args.steps)]
+        value = float(np.mean([v["value"] for v in vals]))
+        return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded generator)",
+                "config": batched_config(args, pk, "fp64 (CPU oracle)", None),
+                "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                 "sample": vals[-1]["sample"]},
+                "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     from paper_2410_00627_gb300 import synth  # noqa: F401
     prob = workload(args)
     n_fast = prob.n_slow * prob.ratio
@@ -318,7 +594,7 @@ def main():
         local = int(os.environ.get("LOCAL_RANK", "0"))
         torch.cuda.set_device(local)
         dist.init_process_group("nccl", init_method="env://")
-    line = run_ours(args, rank, world, dist)
+    line = (run_batched if args.workload == "config4" else run_ours)(args, rank, world, dist)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

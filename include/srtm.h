@@ -140,17 +140,41 @@ int srtm_last_error_detail(char *buf, int len);
 int srtm_release(void);
 
 /* Tuning of the launch shapes (lane groups per scan block, elements per lane
- * group, recovery block size) for one (nx, precision).  Zero values keep the
- * built-in choice.  Returns SRTM_ERR_ARG for out-of-range values.           */
+ * group, recovery block size, look-back depth) for one (nx, precision).  Zero
+ * values keep the built-in choice (128/lanes-per-group groups, 4 elements,
+ * 128 threads, window 16).  Returns SRTM_ERR_ARG for out-of-range values.
+ * The setting is process-wide and applies to the calls issued after it.     */
 typedef struct {
   int scan_groups;      /* lane groups per scan block: a power of two such that
                            groups x lanes-per-group (1, 4, 16 or 32 by nx) is
                            32..256                                              */
   int scan_elems;       /* elements per lane group per tile (1..64)            */
   int recover_threads;  /* recovery block size (32..128, multiple of 32)       */
+  int lookback_window;  /* scan look-back depth: preceding tiles examined per
+                           round of the decoupled look-back (1..32)            */
 } srtm_tuning;
 int srtm_set_tuning(int nx, srtm_precision prec, const srtm_tuning *t);
 int srtm_get_tuning(int nx, srtm_precision prec, srtm_tuning *t);
+
+/* Autotuner (the paper has no counterpart; launch shapes are a property of
+ * this implementation).  Runs srtm_smoother on the caller's problem with a
+ * sequence of candidate tunings and keeps the fastest for (p->nx, prec) as if
+ * by srtm_set_tuning: first the grid of scan_groups (every valid power of
+ * two) x scan_elems (1, 2, 4, 8, 16, 32), then lookback_window (4, 8, 16, 32)
+ * and recover_threads (32, 64, 96, 128) one at a time from the best so far.
+ * Each candidate is run once untimed and then `reps` times (reps >= 1), timed
+ * by CUDA events on `stream` around the call; its score is the fastest of
+ * the reps.  Inputs and `smooth` are as for srtm_smoother (device buffers
+ * owned by the caller); `smooth` is overwritten by every run.  The stream is
+ * synchronized after each run.  On success *best (if not NULL) receives the
+ * chosen tuning and *best_ms (if not NULL) its time in milliseconds.  Errors:
+ * those of srtm_smoother and srtm_status (the first failing candidate stops
+ * the search and the previous tuning is restored).                          */
+int srtm_autotune(const srtm_problem *p, srtm_precision prec, const srtm_output *smooth, int reps,
+                  srtm_tuning *best, float *best_ms, srtm_stream_t stream);
+/* The same for a batch (srtm_smoother_batch; tuning key (b->nx, prec)).      */
+int srtm_autotune_batch(const srtm_batch *b, srtm_precision prec, const srtm_output *smooth, int reps,
+                        srtm_tuning *best, float *best_ms, srtm_stream_t stream);
 
 /* Kernel launches of one call (for reporting): constants, filter scan (which
  * also forms the per-interval smoother elements), smoother scan (smoother

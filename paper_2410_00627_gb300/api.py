@@ -22,7 +22,7 @@ OUTPUT_KEYS = ("fast_mean", "fast_cov", "slow_mean", "slow_cov")
 SYMBOLS = ("srtm_filter", "srtm_smoother", "srtm_filter_batch", "srtm_smoother_batch",
            "srtm_smoother_host", "srtm_status", "srtm_last_error_detail", "srtm_release",
            "srtm_set_tuning", "srtm_get_tuning", "srtm_launches_per_call", "srtm_set_stage_timing",
-           "srtm_stage_times", "srtm_smoother_noalloc")
+           "srtm_stage_times", "srtm_smoother_noalloc", "srtm_autotune", "srtm_autotune_batch")
 STAGES = ("metadata", "constants", "filter_scan", "interval_setup", "smoother_scan", "recovery")
 
 
@@ -45,7 +45,8 @@ class Batch(ctypes.Structure):
 
 
 class Tuning(ctypes.Structure):
-    _fields_ = [("scan_groups", c_int), ("scan_elems", c_int), ("recover_threads", c_int)]
+    _fields_ = [("scan_groups", c_int), ("scan_elems", c_int), ("recover_threads", c_int),
+                ("lookback_window", c_int)]
 
 
 class SRTMError(RuntimeError):
@@ -87,6 +88,8 @@ def load():
         "srtm_set_stage_timing": [c_int],
         "srtm_stage_times": [ctypes.POINTER(ctypes.c_float), c_int],
         "srtm_smoother_noalloc": [P, c_int, O, c_void_p],
+        "srtm_autotune": [P, c_int, O, c_int, T, ctypes.POINTER(ctypes.c_float), c_void_p],
+        "srtm_autotune_batch": [B, c_int, O, c_int, T, ctypes.POINTER(ctypes.c_float), c_void_p],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -240,15 +243,37 @@ def status(stream=None) -> None:
     _check(load().srtm_status(_stream_handle(stream)))
 
 
-def set_tuning(nx: int, precision: str, scan_groups=0, scan_elems=0, recover_threads=0):
+def set_tuning(nx: int, precision: str, scan_groups=0, scan_elems=0, recover_threads=0, lookback_window=0):
     _check(load().srtm_set_tuning(nx, PRECISION[precision],
-                                  ctypes.byref(Tuning(scan_groups, scan_elems, recover_threads))))
+                                  ctypes.byref(Tuning(scan_groups, scan_elems, recover_threads, lookback_window))))
 
 
 def get_tuning(nx: int, precision: str) -> dict:
     t = Tuning()
     _check(load().srtm_get_tuning(nx, PRECISION[precision], ctypes.byref(t)))
     return {k: getattr(t, k) for k, _ in Tuning._fields_}
+
+
+def autotune(F, Q, H, R, m0, P0, y, ratio, precision="mixed", reps=2, stream=None, out=None):
+    """Search the launch shapes for this problem (srtm_autotune) and keep the
+    fastest for (nx, precision).  Returns (tuning dict, milliseconds per call)."""
+    prob = _problem(F, Q, H, R, m0, P0, y, ratio)
+    _, so = _alloc_outputs(OUTPUT_KEYS, y.device, prob.n_slow * prob.ratio, prob.n_slow, prob.nx, out)
+    t, ms = Tuning(), ctypes.c_float()
+    _check(load().srtm_autotune(ctypes.byref(prob), PRECISION[precision], ctypes.byref(so), int(reps),
+                                ctypes.byref(t), ctypes.byref(ms), _stream_handle(stream)))
+    return {k: getattr(t, k) for k, _ in Tuning._fields_}, float(ms.value)
+
+
+def autotune_batch(batch: Batch, precision="mixed", reps=2, stream=None, device=None, out=None):
+    """srtm_autotune_batch: the same search for a ragged batch."""
+    import torch
+    device = device or torch.device("cuda", torch.cuda.current_device())
+    _, so = _alloc_outputs(OUTPUT_KEYS, device, batch.total_fast, batch.total_slow, batch.nx, out)
+    t, ms = Tuning(), ctypes.c_float()
+    _check(load().srtm_autotune_batch(ctypes.byref(batch), PRECISION[precision], ctypes.byref(so), int(reps),
+                                      ctypes.byref(t), ctypes.byref(ms), _stream_handle(stream)))
+    return {k: getattr(t, k) for k, _ in Tuning._fields_}, float(ms.value)
 
 
 def launches_per_call(smoothing: bool = True, batched: bool = False) -> int:

@@ -753,15 +753,19 @@ struct ScanSmem {
   __host__ __device__ static size_t group_bytes() {
     return align16((3 * Op::ES + Op::SCR) * sizeof(T)) + align16((Op::SCRS > 0 ? Op::SCRS : 1) * sizeof(TS));
   }
-  static constexpr int WIN = 16;  // look-back window (predecessor tiles per round)
-  __host__ __device__ static size_t window_bytes() { return align16((size_t)(WIN + WIN / 2) * Op::ES * sizeof(T)); }
+  // look-back window W: predecessor tiles examined per round (1..MAXWIN)
+  static constexpr int MAXWIN = 32;
+  // W payloads plus ceil(W/2) for the second buffer of the pairwise fold
+  __host__ __device__ static size_t window_bytes(int W) {
+    return align16((size_t)(W + (W + 1) / 2) * Op::ES * sizeof(T));
+  }
   // layout: [excl | tile id, control | union{ lane-group buffers, group
   // aggregates x2, look-back window ; tile epilogue }]
-  __host__ __device__ static size_t scan_part(int NG) {
-    return NG * group_bytes() + 2 * align16((size_t)NG * Op::ES * sizeof(T)) + window_bytes();
+  __host__ __device__ static size_t scan_part(int NG, int W) {
+    return NG * group_bytes() + 2 * align16((size_t)NG * Op::ES * sizeof(T)) + window_bytes(W);
   }
-  __host__ __device__ static size_t bytes(int NG) {
-    const size_t sp = scan_part(NG), ep = Op::epilogue_bytes(NG * Op::G);
+  __host__ __device__ static size_t bytes(int NG, int W) {
+    const size_t sp = scan_part(NG, W), ep = Op::epilogue_bytes(NG * Op::G);
     return align16(Op::ES * sizeof(T)) + 32 + (sp > ep ? sp : ep);
   }
   __host__ __device__ static size_t payload_bytes() { return align16(Op::ES * sizeof(T)); }
@@ -780,22 +784,22 @@ __device__ __forceinline__ void publish(const Grp<Op::G>& g, unsigned char* ts, 
 }
 
 // Decoupled look-back of one tile, done by the whole block, a window of up to
-// WIN predecessor tiles per round.  Lane group 0 polls the flags (tile
+// W predecessor tiles per round.  Lane group 0 polls the flags (tile
 // j_hi - q for q < w); the round needs the tiles down to the nearest one that
 // already holds its inclusive prefix (or the whole window).  All threads fetch
 // those payloads together, and all lane groups fold them pairwise in a tree
-// of log2(WIN) levels (scan order: the older tile is the left operand) before
+// of log2(W) levels (scan order: the older tile is the left operand) before
 // group 0 folds the result into the running exclusive prefix.  Every wait is
 // bounded: past SPIN_LIMIT polls the block records DEVERR_TIMEOUT and goes on
 // with what it has, so the kernel always terminates.
 template <class Op>
-__device__ bool lookback(const Grp<Op::G>& g, int gid, int NG, const Ctx& c, unsigned long long epoch,
+__device__ bool lookback(const Grp<Op::G>& g, int gid, int NG, int W, const Ctx& c, unsigned long long epoch,
                          long long tile_id, long long t_in_seq, const typename Op::T* agg, typename Op::T* excl,
                          typename Op::T* tmp, typename Op::T* win, int* ctl, typename Op::T* sc,
                          typename Op::TS* scs) {
   using T = typename Op::T;
-  constexpr int G = Op::G, ES = Op::ES, WIN = ScanSmem<Op>::WIN;
-  T* win2 = win + WIN * ES;
+  constexpr int G = Op::G, ES = Op::ES;
+  T* win2 = win + W * ES;
   unsigned char* ts = Op::tile_state(c, tile_id);
   bool ok = true;
   if (t_in_seq == 0) {
@@ -816,7 +820,7 @@ __device__ bool lookback(const Grp<Op::G>& g, int gid, int NG, const Ctx& c, uns
   const long long j_lo = tile_id - t_in_seq;  // first tile of this sequence
   long long j_hi = tile_id - 1;
   for (;;) {
-    const int w = (int)min((long long)WIN, j_hi - j_lo + 1);
+    const int w = (int)min((long long)W, j_hi - j_lo + 1);
     if (gid == 0) {
       unsigned ready = 0, pref = 0;
       bool timed_out = true;
@@ -892,7 +896,7 @@ __device__ bool lookback(const Grp<Op::G>& g, int gid, int NG, const Ctx& c, uns
 }
 
 template <class Op>
-__global__ void __launch_bounds__(256) scan_kernel(Ctx c, int NG, int E) {
+__global__ void __launch_bounds__(256) scan_kernel(Ctx c, int NG, int E, int W) {
   using T = typename Op::T;
   using TS = typename Op::TS;
   constexpr int G = Op::G, ES = Op::ES;
@@ -965,7 +969,7 @@ __global__ void __launch_bounds__(256) scan_kernel(Ctx c, int NG, int E) {
       T* x = src; src = dst; dst = x;
     }
     // 3. tile prefix
-    ok &= lookback<Op>(g, gid, NG, c, epoch, tile_id, t, src + (NG - 1) * ES, excl, b2, win, ctl, sc, scs);
+    ok &= lookback<Op>(g, gid, NG, W, c, epoch, tile_id, t, src + (NG - 1) * ES, excl, b2, win, ctl, sc, scs);
     // 4. results from the exclusive prefixes
     if (cnt > 0) {
       T* st = b0;
@@ -1202,18 +1206,19 @@ inline void set_smem_attr(const void* fn, size_t bytes) {
 }
 
 template <int NX, class T, class TS, class TR>
-int query_shapes_t(int scan_groups, int scan_elems, int recover_threads, int sm_count, long long total_slow,
-                   int n_seq, Shapes* sh) {
+int query_shapes_t(int scan_groups, int scan_elems, int window, int recover_threads, int sm_count,
+                   long long total_slow, int n_seq, Shapes* sh) {
   using FOp = FilterOp<NX, T, TS>;
   using SOp = SmootherOp<NX, T, TR>;
   constexpr int G = FOp::G;
   const int NG = scan_groups;
   const int threads = NG * G;
-  if (threads < 32 || threads > 256) return SRTM_ERR_ARG;
+  if (threads < 32 || threads > 256 || window < 1 || window > ScanSmem<FOp>::MAXWIN) return SRTM_ERR_ARG;
   sh->scan_groups_f = sh->scan_groups_s = NG;
   sh->scan_elems_f = sh->scan_elems_s = scan_elems;
-  sh->smem_f = ScanSmem<FOp>::bytes(NG);
-  sh->smem_s = ScanSmem<SOp>::bytes(NG);
+  sh->window_f = sh->window_s = window;
+  sh->smem_f = ScanSmem<FOp>::bytes(NG, window);
+  sh->smem_s = ScanSmem<SOp>::bytes(NG, window);
   set_smem_attr<FOp>((const void*)scan_kernel<FOp>, sh->smem_f);
   set_smem_attr<SOp>((const void*)scan_kernel<SOp>, sh->smem_s);
   int nb = 0;
@@ -1230,18 +1235,18 @@ int query_shapes_t(int scan_groups, int scan_elems, int recover_threads, int sm_
 }
 
 template <int NX>
-int query_shapes(srtm_precision prec, int scan_groups, int scan_elems, int recover_threads, int sm_count,
-                 long long total_slow, int n_seq, Shapes* sh) {
+int query_shapes(srtm_precision prec, int scan_groups, int scan_elems, int window, int recover_threads,
+                 int sm_count, long long total_slow, int n_seq, Shapes* sh) {
   switch (prec) {
     case SRTM_FP64:
-      return query_shapes_t<NX, double, double, double>(scan_groups, scan_elems, recover_threads, sm_count,
-                                                         total_slow, n_seq, sh);
+      return query_shapes_t<NX, double, double, double>(scan_groups, scan_elems, window, recover_threads,
+                                                         sm_count, total_slow, n_seq, sh);
     case SRTM_MIXED:
-      return query_shapes_t<NX, float, double, double>(scan_groups, scan_elems, recover_threads, sm_count,
-                                                        total_slow, n_seq, sh);
+      return query_shapes_t<NX, float, double, double>(scan_groups, scan_elems, window, recover_threads,
+                                                        sm_count, total_slow, n_seq, sh);
     case SRTM_FP32:
-      return query_shapes_t<NX, float, float, float>(scan_groups, scan_elems, recover_threads, sm_count,
-                                                      total_slow, n_seq, sh);
+      return query_shapes_t<NX, float, float, float>(scan_groups, scan_elems, window, recover_threads,
+                                                      sm_count, total_slow, n_seq, sh);
   }
   return SRTM_ERR_ARG;
 }
@@ -1255,11 +1260,11 @@ int launch_t(const Ctx& c, const Shapes& sh, cudaStream_t st, cudaEvent_t* ev) {
   constexpr int G = FOp::G;
   launch_precompute<NX>(c, st);
   if (ev) cudaEventRecord(ev[0], st);
-  scan_kernel<FOp><<<sh.grid_f, sh.scan_groups_f * G, sh.smem_f, st>>>(c, sh.scan_groups_f, sh.scan_elems_f);
+  scan_kernel<FOp><<<sh.grid_f, sh.scan_groups_f * G, sh.smem_f, st>>>(c, sh.scan_groups_f, sh.scan_elems_f, sh.window_f);
   if (ev) cudaEventRecord(ev[1], st);
   if (ev) cudaEventRecord(ev[2], st);  // the interval setup runs inside the filter scan
   if (c.smoothing)
-    scan_kernel<SOp><<<sh.grid_s, sh.scan_groups_s * G, sh.smem_s, st>>>(c, sh.scan_groups_s, sh.scan_elems_s);
+    scan_kernel<SOp><<<sh.grid_s, sh.scan_groups_s * G, sh.smem_s, st>>>(c, sh.scan_groups_s, sh.scan_elems_s, sh.window_s);
   if (ev) cudaEventRecord(ev[3], st);
   const long long blocks = (c.total_fast + sh.recover_threads - 1) / sh.recover_threads;
   recover_kernel<NX, TR><<<(unsigned)blocks, sh.recover_threads, 0, st>>>(c);
@@ -1282,4 +1287,4 @@ int launch_device_path(const Ctx& c, srtm_precision prec, const Shapes& sh, cuda
 #define SRTM_INSTANTIATE(NXV)                                                                                \
   template int srtm::launch_device_path<NXV>(const srtm::Ctx&, srtm_precision, const srtm::Shapes&,          \
                                              cudaStream_t, cudaEvent_t*);                                    \
-  template int srtm::query_shapes<NXV>(srtm_precision, int, int, int, int, long long, int, srtm::Shapes*);
+  template int srtm::query_shapes<NXV>(srtm_precision, int, int, int, int, int, long long, int, srtm::Shapes*);

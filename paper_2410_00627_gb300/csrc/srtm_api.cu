@@ -56,10 +56,12 @@ srtm_tuning effective_tuning(int nx, srtm_precision prec) {
   t.scan_groups = std::max(1, 128 / G);
   t.scan_elems = 4;
   t.recover_threads = 128;
+  t.lookback_window = 16;
   const srtm_tuning& u = g_tune[nx][prec];
   if (u.scan_groups) t.scan_groups = u.scan_groups;
   if (u.scan_elems) t.scan_elems = u.scan_elems;
   if (u.recover_threads) t.recover_threads = u.recover_threads;
+  if (u.lookback_window) t.lookback_window = u.lookback_window;
   return t;
 }
 
@@ -117,7 +119,9 @@ Layout make_layout(int nx, int ny, int max_ratio, int n_seq, long long total_slo
 int shapes_for(int nx, srtm_precision prec, const srtm_tuning& t, int sms, long long total_slow, int n_seq,
                Shapes* sh) {
 #define SRTM_Q(N) \
-  case N: return query_shapes<N>(prec, t.scan_groups, t.scan_elems, t.recover_threads, sms, total_slow, n_seq, sh);
+  case N:                                                                                               \
+    return query_shapes<N>(prec, t.scan_groups, t.scan_elems, t.lookback_window, t.recover_threads, sms, total_slow, \
+                           n_seq, sh);
   switch (nx) {
     SRTM_Q(1) SRTM_Q(2) SRTM_Q(3) SRTM_Q(4) SRTM_Q(5) SRTM_Q(6) SRTM_Q(7) SRTM_Q(8)
   }
@@ -437,6 +441,8 @@ int srtm_set_tuning(int nx, srtm_precision prec, const srtm_tuning* t) {
   if (t->scan_elems && (t->scan_elems < 1 || t->scan_elems > 64)) return fail(SRTM_ERR_ARG, "scan_elems out of range");
   if (t->recover_threads && (t->recover_threads < 32 || t->recover_threads > 128 || t->recover_threads % 32))
     return fail(SRTM_ERR_ARG, "recover_threads out of range");
+  if (t->lookback_window && (t->lookback_window < 1 || t->lookback_window > 32))
+    return fail(SRTM_ERR_ARG, "lookback_window out of range");
   std::lock_guard<std::mutex> lk(g_mu);
   g_tune[nx][prec] = *t;
   return SRTM_OK;
@@ -447,6 +453,121 @@ int srtm_get_tuning(int nx, srtm_precision prec, srtm_tuning* t) {
   std::lock_guard<std::mutex> lk(g_mu);
   *t = effective_tuning(nx, prec);
   return SRTM_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Times `call` under each candidate tuning of (nx, prec); see srtm_autotune.
+template <class Call>
+int autotune_impl(int nx, srtm_precision prec, int reps, Call call, srtm_tuning* best, float* best_ms,
+                  cudaStream_t st) {
+  if (reps < 1) return fail(SRTM_ERR_ARG, "reps=%d < 1", reps);
+  srtm_tuning saved;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    saved = g_tune[nx][prec];
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return fail(SRTM_ERR_CUDA, "event creation failed");
+  }
+  auto restore = [&](int rc) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_tune[nx][prec] = saved;
+    return rc;
+  };
+  auto score = [&](const srtm_tuning& t, float* ms) -> int {
+    {
+      std::lock_guard<std::mutex> lk(g_mu);
+      g_tune[nx][prec] = t;
+    }
+    int rc = call();
+    if (!rc) rc = srtm_status(st);
+    float bestr = 0.f;
+    for (int r = 0; r < reps && !rc; ++r) {
+      cudaEventRecord(e0, st);
+      rc = call();
+      cudaEventRecord(e1, st);
+      if (!rc) rc = srtm_status(st);
+      float v = 0.f;
+      if (!rc && cudaEventElapsedTime(&v, e0, e1) != cudaSuccess) rc = fail(SRTM_ERR_CUDA, "event timing failed");
+      if (!rc && (r == 0 || v < bestr)) bestr = v;
+    }
+    *ms = bestr;
+    return rc;
+  };
+  const int G = group_size(nx);
+  srtm_tuning cur = effective_tuning(nx, prec);
+  float cur_ms = 0.f;
+  bool have = false;
+  int rc = SRTM_OK;
+  auto consider = [&](const srtm_tuning& t) {
+    float ms = 0.f;
+    rc = score(t, &ms);
+    if (!rc && (!have || ms < cur_ms)) { cur = t; cur_ms = ms; have = true; }
+    return rc;
+  };
+  const int elems[] = {1, 2, 4, 8, 16, 32};
+  for (int sg = 1; sg * G <= 256 && !rc; sg *= 2) {
+    if (sg * G < 32) continue;
+    for (int e : elems) {
+      srtm_tuning t = cur;
+      t.scan_groups = sg;
+      t.scan_elems = e;
+      if (consider(t)) break;
+    }
+  }
+  const int windows[] = {4, 8, 16, 32};
+  for (int w : windows) {
+    if (rc || w == cur.lookback_window) continue;
+    srtm_tuning t = cur;
+    t.lookback_window = w;
+    consider(t);
+  }
+  const int threads[] = {32, 64, 96, 128};
+  for (int th : threads) {
+    if (rc || th == cur.recover_threads) continue;
+    srtm_tuning t = cur;
+    t.recover_threads = th;
+    consider(t);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return restore(rc);
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_tune[nx][prec] = cur;
+  }
+  if (best) *best = cur;
+  if (best_ms) *best_ms = cur_ms;
+  return SRTM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int srtm_autotune(const srtm_problem* p, srtm_precision prec, const srtm_output* smooth, int reps,
+                  srtm_tuning* best, float* best_ms, srtm_stream_t stream) {
+  if (!p) return fail(SRTM_ERR_ARG, "problem is NULL");
+  int rc = check_dims(p->nx, p->ny);
+  if (rc) return rc;
+  if (prec < SRTM_FP64 || prec > SRTM_FP32) return fail(SRTM_ERR_ARG, "unknown precision %d", (int)prec);
+  return autotune_impl(p->nx, prec, reps, [&]() { return srtm_smoother(p, prec, smooth, nullptr, stream); }, best,
+                       best_ms, (cudaStream_t)stream);
+}
+
+int srtm_autotune_batch(const srtm_batch* b, srtm_precision prec, const srtm_output* smooth, int reps,
+                        srtm_tuning* best, float* best_ms, srtm_stream_t stream) {
+  if (!b) return fail(SRTM_ERR_ARG, "batch is NULL");
+  int rc = check_dims(b->nx, b->ny);
+  if (rc) return rc;
+  if (prec < SRTM_FP64 || prec > SRTM_FP32) return fail(SRTM_ERR_ARG, "unknown precision %d", (int)prec);
+  return autotune_impl(b->nx, prec, reps, [&]() { return srtm_smoother_batch(b, prec, smooth, nullptr, stream); },
+                       best, best_ms, (cudaStream_t)stream);
 }
 
 int srtm_launches_per_call(int smoothing, int batched) { return (smoothing ? 4 : 3) + (batched ? 1 : 0); }

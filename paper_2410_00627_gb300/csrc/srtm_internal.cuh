@@ -171,6 +171,7 @@ __device__ __forceinline__ void raise_err(Counters* c, unsigned bits) { atomicOr
 // ---------------------------------------------------------------------------
 struct Shapes {  // resolved launch shapes for one call
   int scan_groups_f, scan_elems_f, scan_groups_s, scan_elems_s;
+  int window_f, window_s;  // look-back window (tiles per round)
   int recover_threads;
   int grid_f, grid_s, grid_setup;
   size_t smem_f, smem_s, smem_setup;
@@ -180,7 +181,7 @@ template <int NX>
 int launch_device_path(const Ctx& c, srtm_precision prec, const Shapes& sh, cudaStream_t st, cudaEvent_t* ev);
 
 template <int NX>
-int query_shapes(srtm_precision prec, int scan_groups, int scan_elems, int recover_threads, int sm_count,
-                 long long total_slow, int n_seq, Shapes* sh);
+int query_shapes(srtm_precision prec, int scan_groups, int scan_elems, int window, int recover_threads,
+                 int sm_count, long long total_slow, int n_seq, Shapes* sh);
 
 }  // namespace srtm

@@ -98,7 +98,7 @@ def simulate(rng: np.random.Generator, F, Q, H, R, m0, P0, ratio: int, n_slow: i
     Lq = np.linalg.cholesky(Q)
     Lr = np.linalg.cholesky(R)
     x0 = m0 + np.linalg.cholesky(P0) @ rng.standard_normal(nx)
-    w = rng.standard_normal((N, l, nx)) @ Lq.T          # w[k, i-1]: noise into x_{k,i}
+    w = (rng.standard_normal((N * l, nx)) @ Lq.T).reshape(N, l, nx)   # w[k, i-1]: noise into x_{k,i}
     v = rng.standard_normal((N, ny)) @ Lr.T
     # e[k, i-1] = sum_{r<=i} F^{i-r} w[k, r-1]
     e = np.empty_like(w)
@@ -121,7 +121,7 @@ def simulate(rng: np.random.Generator, F, Q, H, R, m0, P0, ratio: int, n_slow: i
     for i in range(l):
         P = F @ P
         Fpow[i] = P
-    xs = np.einsum("inm,km->kin", Fpow, z[:-1]) + e      # (N, l, nx)
+    xs = (z[:-1] @ Fpow.reshape(l * nx, nx).T).reshape(N, l, nx) + e   # (N, l, nx)
     y = xs.sum(axis=1) @ H.T + v
     x = None
     if keep_states:
@@ -186,26 +186,59 @@ def config3(seed: int = 0, n_slow: int = 100_000, keep_states: bool = False) -> 
     return Problem(F, Q, H, R, m0, P0, y, 50, x, "cfg3", {"K": K, "dt": dt})
 
 
+def _config4_one(seed: int, s: int, n_min: int, n_max: int, ratios, keep_states: bool) -> Problem:
+    rng = np.random.default_rng([seed, s])
+    rates = log_uniform(rng, 0.05, 1.0, 4)
+    K = chain_rates_matrix(rates)
+    F = scipy.linalg.expm(K * 0.05)
+    Q = 1e-3 * np.eye(4)
+    H = np.zeros((1, 4)); H[0, 3] = 1.0
+    R = np.array([[0.05]])
+    m0 = np.eye(4)[0]
+    P0 = 0.1 * np.eye(4)
+    l = int(rng.choice(ratios))
+    N = int(rng.integers(n_min, n_max + 1))
+    y, x = simulate(rng, F, Q, H, R, m0, P0, l, N, keep_states)
+    return Problem(F, Q, H, R, m0, P0, y, l, x, f"cfg4[{s}]", {"K": K})
+
+
+def _config4_chunk(args):
+    seed, lo, hi, n_min, n_max, ratios, keep_states = args
+    return [_config4_one(seed, s, n_min, n_max, ratios, keep_states) for s in range(lo, hi)]
+
+
 def config4(seed: int = 0, n_seq: int = 4096, n_min: int = 100, n_max: int = 20_000,
-            ratios=(5, 10, 20), keep_states: bool = False) -> list[Problem]:
+            ratios=(5, 10, 20), keep_states: bool = False, workers: int = 1) -> list[Problem]:
     """Ragged batch: per sequence a 4-species chain as in config 2 (dt=.05),
     ratio drawn from {5,10,20}, n_slow ~ U[n_min, n_max], ny=1 observing
-    species 4, Q=1e-3 I, R=.05, m0=e1, P0=.1 I."""
-    rng = np.random.default_rng(seed)
-    out = []
-    for s in range(n_seq):
-        rates = log_uniform(rng, 0.05, 1.0, 4)
-        K = chain_rates_matrix(rates)
-        F = scipy.linalg.expm(K * 0.05)
-        Q = 1e-3 * np.eye(4)
-        H = np.zeros((1, 4)); H[0, 3] = 1.0
-        R = np.array([[0.05]])
-        m0 = np.eye(4)[0]
-        P0 = 0.1 * np.eye(4)
-        l = int(rng.choice(ratios))
-        N = int(rng.integers(n_min, n_max + 1))
-        y, x = simulate(rng, F, Q, H, R, m0, P0, l, N, keep_states)
-        out.append(Problem(F, Q, H, R, m0, P0, y, l, x, f"cfg4[{s}]", {"K": K}))
+    species 4, Q=1e-3 I, R=.05, m0=e1, P0=.1 I.
+
+    Sequence s draws from its own generator seeded with (seed, s), so the
+    batch is the same whether it is built serially or by ``workers`` processes
+    (a pool started with the ``spawn`` method, safe after CUDA has been used).
+    """
+    ratios = tuple(int(r) for r in ratios)
+    if workers <= 1 or n_seq < 2 * workers:
+        return _config4_chunk((seed, 0, n_seq, n_min, n_max, ratios, keep_states))
+    import multiprocessing as mp
+    bounds = np.linspace(0, n_seq, 4 * workers + 1).astype(int)
+    jobs = [(seed, int(a), int(b), n_min, n_max, ratios, keep_states) for a, b in zip(bounds[:-1], bounds[1:]) if b > a]
+    with mp.get_context("spawn").Pool(workers) as pool:
+        parts = pool.map(_config4_chunk, jobs)
+    return [p for part in parts for p in part]
+
+
+def pack(probs: list[Problem]) -> dict:
+    """A list of same-size sequences as the batch layout of the C-ABI: stacked
+    F, Q, H, R, m0, P0, the measurements concatenated in sequence order, and
+    per-sequence ratio / n_slow (int32) with the batch totals."""
+    out = {k: np.ascontiguousarray(np.stack([getattr(p, k) for p in probs])) for k in ("F", "Q", "H", "R", "m0", "P0")}
+    out["y"] = np.ascontiguousarray(np.concatenate([p.y for p in probs]))
+    out["ratio"] = np.array([p.ratio for p in probs], dtype=np.int32)
+    out["n_slow"] = np.array([p.n_slow for p in probs], dtype=np.int32)
+    out["max_ratio"] = int(out["ratio"].max())
+    out["total_slow"] = int(out["n_slow"].sum(dtype=np.int64))
+    out["total_fast"] = int((out["n_slow"].astype(np.int64) * out["ratio"]).sum())
     return out
 
 

@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 from paper_2410_00627_gb300 import synth
-from tests.gpu_util import TOL, compare, oracle_views, run_filter, run_smoother
+from tests.gpu_util import TOL, compare, oracle_views, run_filter, run_smoother, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -106,11 +106,18 @@ def test_repeated_calls_are_bitwise_identical():
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_full_size_config2_sampled(oracle_mod, precision):
     """Config 2 at its full size (10^4 slow steps, 2*10^5 fast steps) in the
-    benchmark's launch configuration: every slow output, and fast outputs of
-    sampled windows (start, two interior windows, end)."""
+    benchmark's launch configuration (shapes chosen by the autotuner): every
+    slow output, and fast outputs of sampled windows (start, two interior
+    windows, end)."""
+    from paper_2410_00627_gb300 import api
     prob = synth.config2(seed=0, n_slow=10_000, keep_states=False)
     l, N = prob.ratio, prob.n_slow
-    sm, fi = run_smoother(prob, precision)
+    args = [to_dev(getattr(prob, k)) for k in ("F", "Q", "H", "R", "m0", "P0", "y")]
+    try:
+        api.autotune(*args, l, precision=precision, reps=1)   # the benchmark's shapes
+        sm, fi = run_smoother(prob, precision)
+    finally:
+        api.set_tuning(4, precision)
     seq = oracle_mod.sequential(prob, fast=False)
     tm, tc = TOL[precision]
     windows = [(0, 3), (4093, 4099), (7770, 7772), (N - 3, N)]
@@ -225,3 +232,47 @@ def test_stage_timing_reports_every_stage():
         api.set_stage_timing(False)
     assert set(t) == set(api.STAGES)
     assert all(v > 0 for v in t.values())
+
+
+SHAPES = [  # (scan_groups, scan_elems, recover_threads, lookback_window) for nx=4 (16 lanes per group)
+    (2, 1, 32, 1),     # smallest tiles, serial look-back
+    (16, 32, 128, 32),  # largest tiles and window
+    (8, 4, 64, 4),
+    (4, 2, 96, 2),
+]
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "g{}e{}t{}w{}".format(*s))
+def test_launch_shapes_do_not_change_results(oracle_mod, shape):
+    from paper_2410_00627_gb300 import api
+    prob = synth.config2(seed=5, n_slow=613, keep_states=False)
+    ref_sm, ref_fi = oracle_views(oracle_mod.sequential(prob), prob.ratio)
+    try:
+        for precision in ("fp64", "mixed"):
+            api.set_tuning(4, precision, *shape)
+            sm, fi = run_smoother(prob, precision)
+            tm, tc = TOL[precision]
+            compare(sm, ref_sm, tm, tc, f"smoothed {precision} {shape}")
+            compare(fi, ref_fi, tm, tc, f"filtered {precision} {shape}")
+    finally:
+        api.set_tuning(4, "fp64")
+        api.set_tuning(4, "mixed")
+
+
+def test_autotune_keeps_a_valid_tuning_and_results_still_match(oracle_mod):
+    from paper_2410_00627_gb300 import api
+    prob = synth.config2(seed=6, n_slow=900, keep_states=False)
+    args = [to_dev(getattr(prob, k)) for k in ("F", "Q", "H", "R", "m0", "P0", "y")]
+    try:
+        tuned, ms = api.autotune(*args, prob.ratio, precision="mixed", reps=1)
+        assert ms > 0
+        assert tuned == api.get_tuning(4, "mixed")
+        assert tuned["scan_groups"] in (2, 4, 8, 16) and 1 <= tuned["scan_elems"] <= 32
+        assert tuned["recover_threads"] in (32, 64, 96, 128) and tuned["lookback_window"] in (4, 8, 16, 32)
+        ref_sm, ref_fi = oracle_views(oracle_mod.sequential(prob), prob.ratio)
+        sm, fi = run_smoother(prob, "mixed")
+        tm, tc = TOL["mixed"]
+        compare(sm, ref_sm, tm, tc, "smoothed after autotune")
+        compare(fi, ref_fi, tm, tc, "filtered after autotune")
+    finally:
+        api.set_tuning(4, "mixed")

@@ -53,3 +53,18 @@ def test_config_shapes_and_structure():
     b = synth.config4(seed=0, n_seq=8, n_min=10, n_max=30)
     assert len(b) == 8 and all(q.ratio in (5, 10, 20) for q in b)
     assert all(10 <= q.n_slow <= 30 for q in b) and all(q.H.shape == (1, 4) for q in b)
+
+
+def test_config4_parallel_build_equals_serial_and_packs():
+    a = synth.config4(seed=3, n_seq=12, n_min=5, n_max=40)
+    b = synth.config4(seed=3, n_seq=12, n_min=5, n_max=40, workers=2)
+    assert len(a) == len(b) == 12
+    for p, q in zip(a, b):
+        assert p.ratio == q.ratio and np.array_equal(p.y, q.y) and np.array_equal(p.F, q.F)
+    pk = synth.pack(a)
+    assert pk["F"].shape == (12, 4, 4) and pk["H"].shape == (12, 1, 4) and pk["m0"].shape == (12, 4)
+    assert pk["y"].shape == (pk["total_slow"], 1) and pk["ratio"].dtype == np.int32
+    assert pk["total_fast"] == sum(p.n_slow * p.ratio for p in a)
+    off = np.concatenate([[0], np.cumsum(pk["n_slow"])])
+    for s, p in enumerate(a):
+        assert np.array_equal(pk["y"][off[s]:off[s + 1]], p.y)
