@@ -207,16 +207,21 @@ __device__ __forceinline__ bool g_gauss_jordan(const Grp<G>& g, TS* a) {
 // FMAs on this part).  For NX = 4 the cofactors come from the Laplace
 // expansion by complementary 2x2 minors of rows (0,1) and (2,3):
 //   s_u = a_0p a_1q - a_1p a_0q,  c_u = a_2p a_3q - a_3p a_2q,
-//   (p,q) in (0,1),(0,2),(0,3),(1,2),(1,3),(2,3) for u = 0..5,
-//   det = s0 c5 - s1 c4 + s2 c3 + s3 c2 - s4 c1 + s5 c0.
+//   (p,q) in (0,1),(0,2),(0,3),(1,2),(1,3),(2,3) for u = 0..5.
+// When every lane of the group holds one entry (G >= NX*NX), the
+// determinant is the expansion along column 0, det = sum_c a_c0 C_c0, whose
+// cofactors C_c0 are the unscaled entries (0, c) of the inverse that lanes
+// 0..NX-1 have just formed: one product per lane and a two-level shuffle sum
+// instead of a full determinant on every lane (on this part a float64
+// instruction costs the same whatever its active lanes).
 // In place on a (shared memory); mn holds the 12 minors.  Returns false on
 // a zero or non-finite determinant (then divides by one to stay finite).
 template <int NX, int G, class TS>
 __device__ __forceinline__ bool g_small_inverse(const Grp<G>& g, TS* a, TS* mn) {
   static_assert(NX >= 1 && NX <= 4, "adjugate inverse is for NX <= 4");
   constexpr int NN = NX * NX, EPL = (NN + G - 1) / G;
+  constexpr bool SPLIT_DET = (NX >= 3) && (G >= NN) && (G >= 4);
   bool ok = true;
-  TS det;
   if (NX == 4) {
     for (int u = g.lane; u < 12; u += G) {
       const int r0 = u < 6 ? 0 : 2, v = u < 6 ? u : u - 6;
@@ -225,25 +230,15 @@ __device__ __forceinline__ bool g_small_inverse(const Grp<G>& g, TS* a, TS* mn) 
       mn[u] = fma(a[r0 * 4 + p], a[(r0 + 1) * 4 + q], -a[(r0 + 1) * 4 + p] * a[r0 * 4 + q]);
     }
     g.sync();
-    const TS* sm = mn;
-    const TS* cm = mn + 6;
-    det = sm[0] * cm[5] - sm[1] * cm[4] + sm[2] * cm[3] + sm[3] * cm[2] - sm[4] * cm[1] + sm[5] * cm[0];
-  } else if (NX == 3) {
-    det = a[0] * (a[4] * a[8] - a[5] * a[7]) - a[1] * (a[3] * a[8] - a[5] * a[6]) + a[2] * (a[3] * a[7] - a[4] * a[6]);
-  } else if (NX == 2) {
-    det = a[0] * a[3] - a[1] * a[2];
-  } else {
-    det = a[0];
   }
-  if (bad_pivot(det)) { ok = false; det = TS(1); }
-  const TS id = TS(1) / det;
+  // unscaled inverse entries (cofactors of the transposed positions)
   TS out[EPL];
 #pragma unroll
   for (int j = 0; j < EPL; ++j) {
     const int e = j * G + g.lane;
+    TS v = TS(0);
     if (e < NN) {
       const int r = e / NX, col = e - (e / NX) * NX;
-      TS v;
       if (NX == 1) {
         v = TS(1);
       } else if (NX == 2) {
@@ -264,14 +259,34 @@ __device__ __forceinline__ bool g_small_inverse(const Grp<G>& g, TS* a, TS* mn) 
         v = fma(a[arow * 4 + k2], mins[code & 15], v);
         if (((col & 1) != 0) != ((r & 1) != 0)) v = -v;
       }
-      out[j] = v * id;
     }
+    out[j] = v;
   }
+  TS det;
+  if constexpr (SPLIT_DET) {
+    // lanes 0..NX-1 hold C_c0 (row 0 of the unscaled inverse, c = lane)
+    TS t = (g.lane < NX) ? a[g.lane * NX] * out[0] : TS(0);
+    t += __shfl_xor_sync(g.mask, t, 1);
+    t += __shfl_xor_sync(g.mask, t, 2);
+    det = __shfl_sync(g.mask, t, (int)(threadIdx.x & 31) & ~(G - 1));
+  } else if (NX == 4) {
+    const TS* sm = mn;
+    const TS* cm = mn + 6;
+    det = sm[0] * cm[5] - sm[1] * cm[4] + sm[2] * cm[3] + sm[3] * cm[2] - sm[4] * cm[1] + sm[5] * cm[0];
+  } else if (NX == 3) {
+    det = a[0] * (a[4] * a[8] - a[5] * a[7]) - a[1] * (a[3] * a[8] - a[5] * a[6]) + a[2] * (a[3] * a[7] - a[4] * a[6]);
+  } else if (NX == 2) {
+    det = a[0] * a[3] - a[1] * a[2];
+  } else {
+    det = a[0];
+  }
+  if (bad_pivot(det)) { ok = false; det = TS(1); }
+  const TS id = TS(1) / det;
   g.sync();
 #pragma unroll
   for (int j = 0; j < EPL; ++j) {
     const int e = j * G + g.lane;
-    if (e < NN) a[e] = out[j];
+    if (e < NN) a[e] = out[j] * id;
   }
   g.sync();
   return ok;

@@ -208,24 +208,165 @@ __device__ __forceinline__ bool inverse_row_small(const TR* a, int r, TR* out) {
 template <int NX>
 struct SetupGeom {
   static constexpr int SG = NX == 1 ? 1 : (NX == 2 ? 2 : (NX <= 4 ? 4 : 8));
-  static constexpr int NN = NX * NX, NM = NX * MY;
-  // slot layout (units of TR); Aml, AP1 and P11 reuse Pll, AP and Pm, whose
-  // last reads precede them (AP also holds the rows of (P^-)^{-1} for NX <= 4)
+  static constexpr int NN = NX * NX, NM = NX * MY, UA = NM > NN ? NM : NN;
+  // slot layout in TR; Aml, AP1 and P11 reuse Pll, AP and Pm, whose last
+  // reads precede them, and AP also holds the 2x2 minors of P^- (NX = 4)
   static constexpr int P = 0, mv = P + NN, X = mv + NX, SUl = X + NM, ml = SUl + NM, Pl = ml + NX, Pll = Pl + NN,
-                       AP = Pll + NN, Pm = AP + NN, Z = Pm + NN, U1 = Z + NN, P1l = U1 + NM, SLOT = P1l + NN;
+                       AP = Pll + NN, Pm = AP + NN, Z = Pm + NN, U1 = Z + NN, P1l = U1 + NM, Sy = P1l + NN,
+                       ev = Sy + MY * MY, SLOT = ev + MY;
   static constexpr int Aml = Pll, AP1 = AP, P11 = Pm;
+  // float region of a slot (mixed mode: the smoother elements in float32):
+  // float copies of P, Pl, X, SUl, Z, m^f_l, m, then U1 (later A P1l^T, so
+  // max(NM, NN) entries), P1l, P11, A m^f_l
+  static constexpr int fP = 0, fPl = fP + NN, fX = fPl + NN, fSUl = fX + NM, fZ = fSUl + NM, fml = fZ + NN,
+                       fmv = fml + NX, fU1 = fmv + NX, fP1l = fU1 + UA, fP11 = fP1l + NN, fAml = fP11 + NN,
+                       SLOTF = fAml + NX;
+  // per-tile constants staged as float: A, Qc_1, Cov(e_1, e_l), V_1 H^T
+  static constexpr int cA = 0, cQc = NN, cQl = 2 * NN, cVH = 3 * NN, CONSTF = 3 * NN + NM;
+  template <class T, class TR>
+  __host__ __device__ static constexpr size_t slot_bytes() {
+    return ((SLOT * sizeof(TR) + 15) / 16) * 16 + (sizeof(T) != sizeof(TR) ? ((SLOTF * sizeof(T) + 15) / 16) * 16 : 0);
+  }
 };
 
-// One interval by its SG lanes (lane = row), slot sb in shared memory.
+// Smoother element of one interval (Eq. 29 with the fast-filter blocks of
+// Eq. 17 for i = 1 and i = l), row r by lane r, in the arithmetic type TE:
+//   U_1 = A X + V_1 H^T,  m^f_1 = A m + U_1 kap,
+//   P^f_11 = A P A^T + Qc_1 - U_1 S_y^-1 U_1^T,
+//   P^f_1l = A (P A^{lT}) + Cov(e_1,e_l) - U_1 (S_y^-1 U_l^T),
+//   E = P^f_1l Z,  g = m^f_1 - E A m^f_l,  S = P^f_11 - E A (P^f_1l)^T
+// (reading A7 for S).  Inputs: P, Pl, X, SUl, Z, ml, mv (slot arrays) and
+// the model's A, Qc_1, Cov(e_1,e_l), V_1 H^T (cA, cQc, cQl, cVH; row-major,
+// V_1 H^T with row stride m).  Work arrays: U1 (NX x MY), P1l, P11, Aml and
+// AP1 (NX x NX, A P1l^T; may alias U1 when that holds NX x NX entries).
+template <int NX, class TE, class TC, class T>
+__device__ __forceinline__ void setup_elements(int r, bool row, unsigned mask, int m, bool last, const TE* P,
+                                               const TE* Pl, const TE* X, const TE* SUl, const TE* Z, const TE* ml,
+                                               const TE* mv, const TC* cA, const TC* cQc, const TC* cQl,
+                                               const TC* cVH, const TE (&Si)[MY][MY], const TE (&kap)[MY], TE* U1,
+                                               TE* P1l, TE* P11, TE* Aml, TE* AP1, T* se) {
+  using SLy = SL<NX>;
+  TE U1r[MY], m1 = TE(0);
+  if (row) {
+#pragma unroll
+    for (int j = 0; j < MY; ++j) {
+      TE v = TE(0);
+      if (j < m) {
+        v = (TE)cVH[r * m + j];
+#pragma unroll
+        for (int q = 0; q < NX; ++q) v = fma((TE)cA[r * NX + q], X[q * MY + j], v);
+      }
+      U1r[j] = v;
+      U1[r * MY + j] = v;
+    }
+#pragma unroll
+    for (int q = 0; q < NX; ++q) m1 = fma((TE)cA[r * NX + q], mv[q], m1);
+#pragma unroll
+    for (int j = 0; j < MY; ++j)
+      if (j < m) m1 = fma(U1r[j], kap[j], m1);
+    TE aml = TE(0);
+#pragma unroll
+    for (int t = 0; t < NX; ++t) aml = fma((TE)cA[r * NX + t], ml[t], aml);
+    Aml[r] = aml;
+  }
+  __syncwarp(mask);
+  if (row) {
+    TE US[MY], APr[NX];
+#pragma unroll
+    for (int j = 0; j < MY; ++j) {
+      TE v = TE(0);
+#pragma unroll
+      for (int jj = 0; jj < MY; ++jj)
+        if (jj < m && j < m) v = fma(U1r[jj], Si[jj][j], v);
+      US[j] = v;
+    }
+#pragma unroll
+    for (int q = 0; q < NX; ++q) {
+      TE v = TE(0);
+#pragma unroll
+      for (int t = 0; t < NX; ++t) v = fma((TE)cA[r * NX + t], P[t * NX + q], v);
+      APr[q] = v;
+    }
+#pragma unroll
+    for (int q = 0; q < NX; ++q) {
+      if (q >= r) {
+        TE v = (TE)cQc[r * NX + q];
+#pragma unroll
+        for (int t = 0; t < NX; ++t) v = fma(APr[t], (TE)cA[q * NX + t], v);
+#pragma unroll
+        for (int j = 0; j < MY; ++j)
+          if (j < m) v = fma(-US[j], U1[q * MY + j], v);
+        P11[r * NX + q] = v;
+        P11[q * NX + r] = v;
+      }
+      TE w = (TE)cQl[r * NX + q];
+#pragma unroll
+      for (int t = 0; t < NX; ++t) w = fma((TE)cA[r * NX + t], Pl[t * NX + q], w);
+#pragma unroll
+      for (int j = 0; j < MY; ++j)
+        if (j < m) w = fma(-U1r[j], SUl[j * NX + q], w);
+      P1l[r * NX + q] = w;
+    }
+  }
+  __syncwarp(mask);
+  if (!last) {
+    TE Er[NX];
+    if (row) {
+#pragma unroll
+      for (int q = 0; q < NX; ++q) {
+        TE v = TE(0);
+#pragma unroll
+        for (int t = 0; t < NX; ++t) v = fma(P1l[r * NX + t], Z[t * NX + q], v);
+        Er[q] = v;
+        se[SLy::E + r * NX + q] = (T)v;
+      }
+      TE g = m1;
+#pragma unroll
+      for (int q = 0; q < NX; ++q) g = fma(-Er[q], Aml[q], g);
+      se[SLy::g + r] = (T)g;
+#pragma unroll
+      for (int q = 0; q < NX; ++q) {
+        TE v = TE(0);
+#pragma unroll
+        for (int t = 0; t < NX; ++t) v = fma((TE)cA[r * NX + t], P1l[q * NX + t], v);
+        AP1[r * NX + q] = v;
+      }
+    }
+    __syncwarp(mask);
+    if (row) {
+#pragma unroll
+      for (int q = 0; q < NX; ++q) {
+        if (q >= r) {
+          TE v = P11[r * NX + q];
+#pragma unroll
+          for (int t = 0; t < NX; ++t) v = fma(-Er[t], AP1[t * NX + q], v);
+          se[SLy::S + r * NX + q] = (T)v;
+          se[SLy::S + q * NX + r] = (T)v;
+        }
+      }
+    }
+  } else if (row) {  // last interval: E_N = 0, g = m^f_{N,1}, S = P^f_{N,1}
+    se[SLy::g + r] = (T)m1;
+#pragma unroll
+    for (int q = 0; q < NX; ++q) {
+      se[SLy::E + r * NX + q] = T(0);
+      se[SLy::S + r * NX + q] = (T)P11[r * NX + q];
+    }
+  }
+}
+
+// One interval by its SG lanes (lane = row), slot sb in shared memory (with
+// its float region sf when the smoother elements are formed in float32).
 // prev (optional): p(x_{k-1,l}|y_{1:k-1}) as (m, P) when it is not yet in
 // the filter results (the first interval of a scan tile reads it from the
-// tile's exclusive prefix).
+// tile's exclusive prefix).  cf: the tile's model constants as float (used
+// when T is narrower than TR).
 template <int NX, class T, class TR>
-__device__ void setup_interval(const Ctx& c, long long gi, int lane, unsigned mask, TR* sb, const TR* prev) {
+__device__ void setup_interval(const Ctx& c, long long gi, int lane, unsigned mask, TR* sb, T* sf, const TR* prev,
+                               const T* cf) {
   using Gm = SetupGeom<NX>;
   constexpr int NN = NX * NX;
   using RL = Rec<NX>;
-  using SLy = SL<NX>;
   const int r = lane;
   const bool row = r < NX;
   const int s = find_segment(c.meta.off_slow, c.n_seq, gi);
@@ -265,49 +406,41 @@ __device__ void setup_interval(const Ctx& c, long long gi, int lane, unsigned ma
     }
   }
   __syncwarp(mask);
-  // S_y = C_bar X + R_x (every lane), its inverse, kap
+  // S_y = C_bar X + R_x (upper entries spread over the lanes, mirrored) and
+  // the innovation e = y_k - C_bar m (lane j < m)
+  for (int u = lane; u < MY * MY; u += Gm::SG) {
+    const int i = u / MY, j = u - (u / MY) * MY;
+    if (i <= j && j < m) {
+      TR v = (TR)Rx[i * m + j];
+#pragma unroll
+      for (int q = 0; q < NX; ++q) v = fma((TR)Cb[i * NX + q], sb[Gm::X + q * MY + j], v);
+      sb[Gm::Sy + i * MY + j] = v;
+      sb[Gm::Sy + j * MY + i] = v;
+    }
+  }
+  if (lane < m) {
+    const double* yk = c.y + gi * m;
+    TR v = (TR)yk[lane];
+#pragma unroll
+    for (int q = 0; q < NX; ++q) v = fma(-(TR)Cb[lane * NX + q], sb[Gm::mv + q], v);
+    sb[Gm::ev + lane] = v;
+  }
+  __syncwarp(mask);
+  // S_y^-1 and kap = S_y^-1 e (every lane)
   TR Si[MY][MY], kap[MY];
   {
     TR Sy[MY][MY];
 #pragma unroll
     for (int i = 0; i < MY; ++i)
 #pragma unroll
-      for (int j = 0; j < MY; ++j) {
-        TR v = (i == j) ? TR(1) : TR(0);
-        if (i < m && j < m) {
-          v = (TR)Rx[i * m + j];
-#pragma unroll
-          for (int q = 0; q < NX; ++q) v = fma((TR)Cb[i * NX + q], sb[Gm::X + q * MY + j], v);
-        }
-        Sy[i][j] = v;
-      }
-#pragma unroll
-    for (int i = 0; i < MY; ++i)
-#pragma unroll
-      for (int j = i + 1; j < MY; ++j) {
-        const TR v = TR(0.5) * (Sy[i][j] + Sy[j][i]);
-        Sy[i][j] = v;
-        Sy[j][i] = v;
-      }
+      for (int j = 0; j < MY; ++j) Sy[i][j] = (i < m && j < m) ? sb[Gm::Sy + i * MY + j] : ((i == j) ? TR(1) : TR(0));
     ok &= small_sym_inverse<TR>(Sy, Si, m);
-    TR e[MY];
-    const double* yk = c.y + gi * m;
-#pragma unroll
-    for (int j = 0; j < MY; ++j) {
-      TR v = TR(0);
-      if (j < m) {
-        v = (TR)yk[j];
-#pragma unroll
-        for (int q = 0; q < NX; ++q) v = fma(-(TR)Cb[j * NX + q], sb[Gm::mv + q], v);
-      }
-      e[j] = v;
-    }
 #pragma unroll
     for (int i = 0; i < MY; ++i) {
       TR v = TR(0);
 #pragma unroll
       for (int j = 0; j < MY; ++j)
-        if (i < m && j < m) v = fma(Si[i][j], e[j], v);
+        if (i < m && j < m) v = fma(Si[i][j], sb[Gm::ev + j], v);
       kap[i] = v;
     }
   }
@@ -390,14 +523,57 @@ __device__ void setup_interval(const Ctx& c, long long gi, int lane, unsigned ma
     }
   }
   __syncwarp(mask);
-  // (P^-)^{-1}: row r by the adjugate (NX <= 4) into the AP slot; above,
-  // every lane forms the whole inverse by Cholesky.  Z = A^T (P^-)^{-1} (row r).
+  // (P^-)^{-1} by the adjugate for NX <= 4: lane r forms row r of the inverse,
+  // the cofactors C_{c,r} of column r, so that det = sum_c P^-_{c,r} C_{c,r}
+  // needs no other lane; for NX = 4 the twelve 2x2 minors are shared (three
+  // per lane, in the AP slot).  Above NX = 4 every lane forms the whole
+  // inverse by Cholesky.  Then Z = A^T (P^-)^{-1} (row r).
   if constexpr (NX <= 4) {
+    const TR* Pm = sb + Gm::Pm;
+    TR* mn = sb + Gm::AP;
+    if constexpr (NX == 4) {
+      for (int u = lane; u < 12; u += Gm::SG) {
+        const int r0 = u < 6 ? 0 : 2, v = u < 6 ? u : u - 6;
+        const int p = v < 3 ? 0 : (v < 5 ? 1 : 2);
+        const int q = v < 3 ? v + 1 : (v < 5 ? v - 1 : 3);
+        mn[u] = fma(Pm[r0 * 4 + p], Pm[(r0 + 1) * 4 + q], -Pm[(r0 + 1) * 4 + p] * Pm[r0 * 4 + q]);
+      }
+      __syncwarp(mask);
+    }
+    TR cof[NX];
+    TR det = TR(0);
     if (row) {
-      TR rowv[NX];
-      ok &= inverse_row_small<NX, TR>(sb + Gm::Pm, r, rowv);
 #pragma unroll
-      for (int q = 0; q < NX; ++q) sb[Gm::AP + r * NX + q] = rowv[q];
+      for (int col = 0; col < NX; ++col) {
+        TR v;
+        if (NX == 1) {
+          v = TR(1);
+        } else if (NX == 2) {
+          v = (r == col) ? Pm[(1 - r) * 3] : -Pm[r * 2 + col];
+        } else if (NX == 3) {
+          const int i0 = col == 0 ? 1 : 0, i1 = col == 2 ? 1 : 2, j0 = r == 0 ? 1 : 0, j1 = r == 2 ? 1 : 2;
+          v = Pm[i0 * 3 + j0] * Pm[i1 * 3 + j1] - Pm[i0 * 3 + j1] * Pm[i1 * 3 + j0];
+          if ((r + col) & 1) v = -v;
+        } else {
+          const int arow = col ^ 1;
+          const TR* mins = col < 2 ? mn + 6 : mn;
+          const int code = r == 0 ? 0x543 : (r == 1 ? 0x521 : (r == 2 ? 0x420 : 0x310));
+          const int k0 = r > 0 ? 0 : 1, k1 = r > 1 ? 1 : 2, k2 = r > 2 ? 2 : 3;
+          v = Pm[arow * 4 + k0] * mins[(code >> 8) & 15];
+          v = fma(-Pm[arow * 4 + k1], mins[(code >> 4) & 15], v);
+          v = fma(Pm[arow * 4 + k2], mins[code & 15], v);
+          if (((col & 1) != 0) != ((r & 1) != 0)) v = -v;
+        }
+        cof[col] = v;
+        det = fma(Pm[col * NX + r], v, det);
+      }
+      if (bad_value(det)) { ok = false; det = TR(1); }
+    }
+    __syncwarp(mask);  // the minors' last reads
+    if (row) {
+      const TR id = TR(1) / det;
+#pragma unroll
+      for (int q = 0; q < NX; ++q) sb[Gm::AP + r * NX + q] = cof[q] * id;
     }
     __syncwarp(mask);
     if (row) {
@@ -456,119 +632,43 @@ __device__ void setup_interval(const Ctx& c, long long gi, int lane, unsigned ma
     }
   }
   if (c.smoothing) {
-    // first fast state of the interval: U_1, m^f_1, P^f_{11}, P^f_{1l} (row r)
-    const double* VH1 = md + c.ml.VH;
-    const double* Qc1 = md + c.ml.Qc;
-    const double* Ql1 = md + c.ml.Ql;
-    TR U1[MY], m1 = TR(0);
-    if (row) {
-#pragma unroll
-      for (int j = 0; j < MY; ++j) {
-        TR v = TR(0);
-        if (j < m) {
-          v = (TR)VH1[r * m + j];
-#pragma unroll
-          for (int q = 0; q < NX; ++q) v = fma((TR)A1[r * NX + q], sb[Gm::X + q * MY + j], v);
-        }
-        U1[j] = v;
-        sb[Gm::U1 + r * MY + j] = v;
-      }
-#pragma unroll
-      for (int q = 0; q < NX; ++q) m1 = fma((TR)A1[r * NX + q], sb[Gm::mv + q], m1);
-#pragma unroll
-      for (int j = 0; j < MY; ++j)
-        if (j < m) m1 = fma(U1[j], kap[j], m1);
-      TR aml = TR(0);
-#pragma unroll
-      for (int t = 0; t < NX; ++t) aml = fma((TR)A1[r * NX + t], sb[Gm::ml + t], aml);
-      sb[Gm::Aml + r] = aml;
-    }
-    __syncwarp(mask);
-    if (row) {
-      TR US[MY], APr[NX];
-#pragma unroll
-      for (int j = 0; j < MY; ++j) {
-        TR v = TR(0);
-#pragma unroll
-        for (int jj = 0; jj < MY; ++jj)
-          if (jj < m && j < m) v = fma(U1[jj], Si[jj][j], v);
-        US[j] = v;
-      }
-#pragma unroll
-      for (int q = 0; q < NX; ++q) {
-        TR v = TR(0);
-#pragma unroll
-        for (int t = 0; t < NX; ++t) v = fma((TR)A1[r * NX + t], sb[Gm::P + t * NX + q], v);
-        APr[q] = v;
-      }
-#pragma unroll
-      for (int q = 0; q < NX; ++q) {
-        if (q >= r) {
-          TR v = (TR)Qc1[r * NX + q];
-#pragma unroll
-          for (int t = 0; t < NX; ++t) v = fma(APr[t], (TR)A1[q * NX + t], v);
-#pragma unroll
-          for (int j = 0; j < MY; ++j)
-            if (j < m) v = fma(-US[j], sb[Gm::U1 + q * MY + j], v);
-          sb[Gm::P11 + r * NX + q] = v;
-          sb[Gm::P11 + q * NX + r] = v;
-        }
-        TR w = (TR)Ql1[r * NX + q];
-#pragma unroll
-        for (int t = 0; t < NX; ++t) w = fma((TR)A1[r * NX + t], sb[Gm::Pl + t * NX + q], w);
-#pragma unroll
-        for (int j = 0; j < MY; ++j)
-          if (j < m) w = fma(-U1[j], sb[Gm::SUl + j * NX + q], w);
-        sb[Gm::P1l + r * NX + q] = w;
-      }
-    }
-    __syncwarp(mask);
-    T* se = (T*)c.selem + gi * SLy::SIZE;
-    if (k < N - 1) {
-      // E = P^f_{1l} Z ; g = m^f_1 - E A m^f_l ; A (P^f_{1l})^T (rows)
-      TR Er[NX];
+    T* se = (T*)c.selem + gi * SL<NX>::SIZE;
+    const bool last = k >= N - 1;
+    if constexpr (sizeof(T) == sizeof(TR)) {
+      __syncwarp(mask);  // the record's reads of Pm (P11 reuses it)
+      setup_elements<NX, TR, double, T>(r, row, mask, m, last, sb + Gm::P, sb + Gm::Pl, sb + Gm::X, sb + Gm::SUl,
+                                        sb + Gm::Z, sb + Gm::ml, sb + Gm::mv, A1, md + c.ml.Qc, md + c.ml.Ql,
+                                        md + c.ml.VH, Si, kap, sb + Gm::U1, sb + Gm::P1l, sb + Gm::P11,
+                                        sb + Gm::Aml, sb + Gm::AP1, se);
+    } else {
+      // float copies of this lane's rows, then the elements in float32
       if (row) {
 #pragma unroll
         for (int q = 0; q < NX; ++q) {
-          TR v = TR(0);
-#pragma unroll
-          for (int t = 0; t < NX; ++t) v = fma(sb[Gm::P1l + r * NX + t], sb[Gm::Z + t * NX + q], v);
-          Er[q] = v;
-          se[SLy::E + r * NX + q] = (T)v;
+          sf[Gm::fP + r * NX + q] = (T)sb[Gm::P + r * NX + q];
+          sf[Gm::fPl + r * NX + q] = (T)sb[Gm::Pl + r * NX + q];
+          sf[Gm::fZ + r * NX + q] = (T)sb[Gm::Z + r * NX + q];
         }
-        TR g = m1;
 #pragma unroll
-        for (int q = 0; q < NX; ++q) g = fma(-Er[q], sb[Gm::Aml + q], g);
-        se[SLy::g + r] = (T)g;
-#pragma unroll
-        for (int q = 0; q < NX; ++q) {
-          TR v = TR(0);
-#pragma unroll
-          for (int t = 0; t < NX; ++t) v = fma((TR)A1[r * NX + t], sb[Gm::P1l + q * NX + t], v);
-          sb[Gm::AP1 + r * NX + q] = v;
+        for (int j = 0; j < MY; ++j) {
+          sf[Gm::fX + r * MY + j] = (T)sb[Gm::X + r * MY + j];
+          sf[Gm::fSUl + j * NX + r] = (T)sb[Gm::SUl + j * NX + r];
         }
+        sf[Gm::fml + r] = (T)sb[Gm::ml + r];
+        sf[Gm::fmv + r] = (T)sb[Gm::mv + r];
+      }
+      T Sif[MY][MY], kapf[MY];
+#pragma unroll
+      for (int i = 0; i < MY; ++i) {
+        kapf[i] = (T)kap[i];
+#pragma unroll
+        for (int j = 0; j < MY; ++j) Sif[i][j] = (T)Si[i][j];
       }
       __syncwarp(mask);
-      // S = P^f_{11} - E A (P^f_{1l})^T (row r, upper triangle, mirrored)
-      if (row) {
-#pragma unroll
-        for (int q = 0; q < NX; ++q) {
-          if (q >= r) {
-            TR v = sb[Gm::P11 + r * NX + q];
-#pragma unroll
-            for (int t = 0; t < NX; ++t) v = fma(-Er[t], sb[Gm::AP1 + t * NX + q], v);
-            se[SLy::S + r * NX + q] = (T)v;
-            se[SLy::S + q * NX + r] = (T)v;
-          }
-        }
-      }
-    } else if (row) {
-      se[SLy::g + r] = (T)m1;
-#pragma unroll
-      for (int q = 0; q < NX; ++q) {
-        se[SLy::E + r * NX + q] = T(0);
-        se[SLy::S + r * NX + q] = (T)sb[Gm::P11 + r * NX + q];
-      }
+      setup_elements<NX, T, T, T>(r, row, mask, m, last, sf + Gm::fP, sf + Gm::fPl, sf + Gm::fX, sf + Gm::fSUl,
+                                  sf + Gm::fZ, sf + Gm::fml, sf + Gm::fmv, cf + Gm::cA, cf + Gm::cQc, cf + Gm::cQl,
+                                  cf + Gm::cVH, Sif, kapf, sf + Gm::fU1, sf + Gm::fP1l, sf + Gm::fP11,
+                                  sf + Gm::fAml, sf + Gm::fU1, se);
     }
   }
   if (!ok && lane == 0) raise_err(c.ctr, DEVERR_SINGULAR);
@@ -646,26 +746,46 @@ struct FilterOp {
   // by the whole block in rounds of blockDim/SG intervals.  The first
   // interval's predecessor result is the tile's exclusive prefix.
   static constexpr bool HAS_EPILOGUE = true;
-  __host__ __device__ static size_t epilogue_bytes(int threads) {
+  // Slots: one per interval of the tile, at most one per SG threads.
+  __host__ __device__ static int epilogue_slots(int threads, int tile) {
+    const int per = threads / SetupGeom<NX>::SG;
+    return per < tile ? per : tile;
+  }
+  static constexpr bool FLOAT_ELEMENTS = sizeof(T) != sizeof(TS);
+  __host__ __device__ static size_t epilogue_bytes(int threads, int tile) {
     using Gm = SetupGeom<NX>;
-    return align16((NX + NX * NX) * sizeof(TS)) + (size_t)(threads / Gm::SG) * Gm::SLOT * sizeof(TS);
+    const size_t head = align16((NX + NX * NX) * sizeof(TS)) + (FLOAT_ELEMENTS ? align16(Gm::CONSTF * sizeof(T)) : 0);
+    return head + (size_t)epilogue_slots(threads, tile) * Gm::template slot_bytes<T, TS>();
   }
   __device__ static void epilogue(const Ctx& c, int s, long long p0, int count, const T* excl, unsigned char* esm) {
     using Gm = SetupGeom<NX>;
-    constexpr int SG = Gm::SG;
+    constexpr int SG = Gm::SG, NN = NX * NX;
     TS* prevb = (TS*)esm;
-    TS* slots = (TS*)(esm + align16((NX + NX * NX) * sizeof(TS)));
+    T* cf = (T*)(esm + align16((NX + NN) * sizeof(TS)));
+    unsigned char* slots =
+        esm + align16((NX + NN) * sizeof(TS)) + (FLOAT_ELEMENTS ? align16(Gm::CONSTF * sizeof(T)) : 0);
     __syncthreads();
-    for (int e = threadIdx.x; e < NX + NX * NX; e += blockDim.x) prevb[e] = (TS)excl[L::d + e];
+    for (int e = threadIdx.x; e < NX + NN; e += blockDim.x) prevb[e] = (TS)excl[L::d + e];
+    if (FLOAT_ELEMENTS) {  // the sequence's A, Qc_1, Cov(e_1,e_l), V_1 H^T as float, once per tile
+      const double* md = c.model + (long long)s * c.ml.stride;
+      for (int e = threadIdx.x; e < NN; e += blockDim.x) {
+        cf[Gm::cA + e] = (T)md[c.ml.Apow + NN + e];
+        cf[Gm::cQc + e] = (T)md[c.ml.Qc + e];
+        cf[Gm::cQl + e] = (T)md[c.ml.Ql + e];
+      }
+      for (int e = threadIdx.x; e < NX * c.ny; e += blockDim.x) cf[Gm::cVH + e] = (T)md[c.ml.VH + e];
+    }
     __syncthreads();
-    const int lane = threadIdx.x % SG, slot = threadIdx.x / SG, per_round = blockDim.x / SG;
+    const int lane = threadIdx.x % SG, slot = threadIdx.x / SG;
+    const int per_round = epilogue_slots(blockDim.x, tile_elems(c));
     const unsigned mask = (SG == 32) ? 0xffffffffu : (((1u << SG) - 1u) << ((threadIdx.x & 31) & ~(SG - 1)));
     const long long base_row = c.meta.off_slow[s];
-    for (int j0 = 0; j0 < count; j0 += per_round) {
-      const int j = j0 + slot;
-      if (j < count)
-        setup_interval<NX, T, TS>(c, base_row + p0 + j, lane, mask, slots + (size_t)slot * Gm::SLOT,
-                                  j == 0 ? prevb : nullptr);
+    if (slot < per_round) {
+      unsigned char* sl = slots + (size_t)slot * Gm::template slot_bytes<T, TS>();
+      TS* sb = (TS*)sl;
+      T* sf = FLOAT_ELEMENTS ? (T*)(sl + align16(Gm::SLOT * sizeof(TS))) : nullptr;
+      for (int j = slot; j < count; j += per_round)
+        setup_interval<NX, T, TS>(c, base_row + p0 + j, lane, mask, sb, sf, j == 0 ? prevb : nullptr, cf);
     }
     __syncthreads();
   }
@@ -729,7 +849,7 @@ struct SmootherOp {
   __device__ static long long total_tiles(const Ctx& c) { return c.ctr->total_tiles_s; }
   __device__ static int tile_elems(const Ctx& c) { return c.tile_s; }
   static constexpr bool HAS_EPILOGUE = false;
-  __host__ __device__ static size_t epilogue_bytes(int) { return 0; }
+  __host__ __device__ static size_t epilogue_bytes(int, int) { return 0; }
   __device__ static void epilogue(const Ctx&, int, long long, int, const T*, unsigned char*) {}
 };
 
@@ -764,14 +884,18 @@ struct ScanSmem {
   __host__ __device__ static size_t scan_part(int NG, int W) {
     return NG * group_bytes() + 2 * align16((size_t)NG * Op::ES * sizeof(T)) + window_bytes(W);
   }
-  __host__ __device__ static size_t bytes(int NG, int W) {
-    const size_t sp = scan_part(NG, W), ep = Op::epilogue_bytes(NG * Op::G);
+  __host__ __device__ static size_t bytes(int NG, int W, int E) {
+    const size_t sp = scan_part(NG, W), ep = Op::epilogue_bytes(NG * Op::G, NG * E);
     return align16(Op::ES * sizeof(T)) + 32 + (sp > ep ? sp : ep);
   }
   __host__ __device__ static size_t payload_bytes() { return align16(Op::ES * sizeof(T)); }
-  __host__ __device__ static size_t tile_state_bytes() { return 16 + 2 * payload_bytes(); }
+  __host__ __device__ static size_t tile_state_bytes() { return 16 + 3 * payload_bytes(); }
 };
 
+// Tile state: [tile flag | group flag | aggregate | inclusive prefix | group
+// aggregate].  Flag words hold (call epoch << 32) | status: tile flag 1 =
+// aggregate published, 2 = inclusive prefix published; group flag 3 = the
+// group aggregate published.
 template <class Op>
 __device__ __forceinline__ void publish(const Grp<Op::G>& g, unsigned char* ts, const typename Op::T* x, int slot,
                                         unsigned status, unsigned long long epoch) {
@@ -780,26 +904,124 @@ __device__ __forceinline__ void publish(const Grp<Op::G>& g, unsigned char* ts, 
   for (int e = g.lane; e < Op::ES; e += Op::G) __stcg(dst + e, x[e]);
   __threadfence();
   g.sync();
-  if (g.lane == 0) st_release_u64((unsigned long long*)ts, ((epoch & 0xffffffffull) << 32) | status);
+  if (g.lane == 0)
+    st_release_u64((unsigned long long*)(ts + (status == 3u ? 8 : 0)), ((epoch & 0xffffffffull) << 32) | status);
 }
 
-// Decoupled look-back of one tile, done by the whole block, a window of up to
-// W predecessor tiles per round.  Lane group 0 polls the flags (tile
-// j_hi - q for q < w); the round needs the tiles down to the nearest one that
-// already holds its inclusive prefix (or the whole window).  All threads fetch
-// those payloads together, and all lane groups fold them pairwise in a tree
-// of log2(W) levels (scan order: the older tile is the left operand) before
-// group 0 folds the result into the running exclusive prefix.  Every wait is
-// bounded: past SPIN_LIMIT polls the block records DEVERR_TIMEOUT and goes on
-// with what it has, so the kernel always terminates.
+// One look-back round over up to W earlier tiles x_q = tile (j_hi - q*step),
+// q < w, done by the whole block.  step = 1: the tile's own group, where a
+// tile is usable when it has published its aggregate (or its inclusive
+// prefix); step = W: the last tiles of earlier groups, usable when they have
+// published their group aggregate (or their inclusive prefix, which then
+// covers everything up to the end of their group).  The round needs the
+// tiles down to the nearest one holding an inclusive prefix (or all w).
+// Lane group 0 polls the flags, all threads fetch the payloads, and all lane
+// groups fold them pairwise in a tree of log2(w) levels (scan order: the
+// older tile is the left operand); group 0 then folds the product into the
+// running exclusive prefix, excl <- product (x) excl.  Returns 1 when an
+// inclusive prefix ended the walk, 0 when it must go on, -1 on a timed-out
+// wait (DEVERR_TIMEOUT latched); `used` receives the number of tiles folded.
+template <class Op>
+__device__ int lookback_round(const Grp<Op::G>& g, int gid, int NG, const Ctx& c, unsigned long long epoch,
+                              long long j_hi, int step, int w, typename Op::T* excl, typename Op::T* tmp,
+                              typename Op::T* win, int* ctl, typename Op::T* sc, typename Op::TS* scs, bool& ok,
+                              int& used) {
+  using T = typename Op::T;
+  constexpr int G = Op::G, ES = Op::ES;
+  const bool groups = step > 1;
+  T* win2 = win + w * ES;
+  if (gid == 0) {
+    unsigned ready = 0, pref = 0;
+    bool timed_out = true;
+    int need = w;
+    unsigned ns = 32;
+    for (long long it = 0; it < SPIN_LIMIT; ++it) {
+      for (int q = g.lane; q < w; q += G) {
+        if (!((ready >> q) & 1u)) {
+          const unsigned long long* fl = (const unsigned long long*)Op::tile_state(c, j_hi - (long long)q * step);
+          const unsigned long long v = ld_acquire_u64(fl);
+          const bool cur = (v >> 32) == (epoch & 0xffffffffull);
+          if (cur && (v & 3ull) == 2ull) {
+            ready |= 1u << q;
+            pref |= 1u << q;
+          } else if (!groups) {
+            if (cur && (v & 3ull) == 1ull) ready |= 1u << q;
+          } else {
+            const unsigned long long v2 = ld_acquire_u64(fl + 1);
+            if ((v2 >> 32) == (epoch & 0xffffffffull) && (v2 & 3ull) == 3ull) ready |= 1u << q;
+          }
+        }
+      }
+      ready = __reduce_or_sync(g.mask, ready);
+      pref = __reduce_or_sync(g.mask, pref);
+      need = pref ? __ffs(pref) : w;  // tiles q < need
+      const unsigned want = (need >= 32) ? 0xffffffffu : ((1u << need) - 1u);
+      if ((ready & want) == want) { timed_out = false; break; }
+      __nanosleep(ns);
+      if (ns < 1024) ns <<= 1;
+    }
+    if (g.lane == 0) {
+      ctl[0] = need;
+      ctl[1] = pref ? 1 : 0;
+      ctl[2] = timed_out ? 1 : 0;
+      if (timed_out) raise_err(c.ctr, DEVERR_TIMEOUT);
+    }
+  }
+  __syncthreads();
+  const int need = ctl[0];
+  const bool found = ctl[1] != 0;
+  if (ctl[2]) return -1;
+  // payloads: aggregates (group aggregates), the last one a prefix when found
+  for (int idx = threadIdx.x; idx < need * ES; idx += blockDim.x) {
+    const int q = idx / ES, e = idx - (idx / ES) * ES;
+    const int slot = (found && q == need - 1) ? 1 : (groups ? 2 : 0);
+    const T* srcp =
+        (const T*)(Op::tile_state(c, j_hi - (long long)q * step) + 16 + slot * ScanSmem<Op>::payload_bytes());
+    win[idx] = __ldcg(srcp + e);
+  }
+  __syncthreads();
+  // tree: product in scan order x_{need-1} (x) ... (x) x_0
+  T* cur = win;
+  T* nxt = win2;
+  int k = need;
+  while (k > 1) {
+    const int pairs = k >> 1;
+    for (int pi = gid; pi < pairs; pi += NG)
+      ok &= Op::combine(g, nxt + pi * ES, cur + (2 * pi + 1) * ES, cur + 2 * pi * ES, sc, scs, false);
+    if ((k & 1) && gid == pairs % NG)
+      for (int e = g.lane; e < ES; e += G) nxt[pairs * ES + e] = cur[(k - 1) * ES + e];
+    __syncthreads();
+    T* x = cur; cur = nxt; nxt = x;
+    k = pairs + (k & 1);
+  }
+  if (gid == 0) {
+    ok &= Op::combine(g, tmp, cur, excl, sc, scs, false);
+    for (int e = g.lane; e < ES; e += G) excl[e] = tmp[e];
+    g.sync();
+  }
+  __syncthreads();
+  used = need;
+  return found ? 1 : 0;
+}
+
+// Two-level decoupled look-back of one tile, done by the whole block.  Tiles
+// of a sequence form groups of W consecutive tiles.  A tile first folds the
+// earlier tiles of its own group (their aggregates, or down to the nearest
+// inclusive prefix).  The last tile of a full group that found no prefix
+// there publishes the group aggregate (the product over its group).  The
+// walk then goes on over the last tiles of the earlier groups, W at a time,
+// taking their group aggregates, down to the nearest inclusive prefix (the
+// sequence's first tile always has one).  A tile at depth t of a sequence
+// thus folds at most W - 1 + t/W payloads instead of t.  Tickets are taken in
+// increasing order, so every tile waited on belongs to a block that is
+// already running: the walk cannot deadlock.  Every wait is bounded
+// (SPIN_LIMIT polls); past the bound the block latches DEVERR_TIMEOUT and
+// finishes with what it has, so the kernel always terminates.
 template <class Op>
 __device__ bool lookback(const Grp<Op::G>& g, int gid, int NG, int W, const Ctx& c, unsigned long long epoch,
                          long long tile_id, long long t_in_seq, const typename Op::T* agg, typename Op::T* excl,
                          typename Op::T* tmp, typename Op::T* win, int* ctl, typename Op::T* sc,
                          typename Op::TS* scs) {
-  using T = typename Op::T;
-  constexpr int G = Op::G, ES = Op::ES;
-  T* win2 = win + W * ES;
   unsigned char* ts = Op::tile_state(c, tile_id);
   bool ok = true;
   if (t_in_seq == 0) {
@@ -818,73 +1040,33 @@ __device__ bool lookback(const Grp<Op::G>& g, int gid, int NG, int W, const Ctx&
   }
   __syncthreads();
   const long long j_lo = tile_id - t_in_seq;  // first tile of this sequence
+  const int in_grp = (int)(t_in_seq % W);
+  const long long g_lo = tile_id - in_grp;    // first tile of this tile's group
+  int rc = 0, used = 0;
+  // 1. earlier tiles of the own group
   long long j_hi = tile_id - 1;
-  for (;;) {
-    const int w = (int)min((long long)W, j_hi - j_lo + 1);
+  while (j_hi >= g_lo) {
+    const int w = (int)min((long long)W, j_hi - g_lo + 1);
+    rc = lookback_round<Op>(g, gid, NG, c, epoch, j_hi, 1, w, excl, tmp, win, ctl, sc, scs, ok, used);
+    if (rc != 0) break;
+    j_hi -= used;
+  }
+  // the last tile of a full group publishes the group aggregate
+  if (rc == 0 && in_grp == W - 1) {
     if (gid == 0) {
-      unsigned ready = 0, pref = 0;
-      bool timed_out = true;
-      int need = w;
-      unsigned ns = 32;
-      for (long long it = 0; it < SPIN_LIMIT; ++it) {
-        for (int q = g.lane; q < w; q += G) {
-          if (!((ready >> q) & 1u)) {
-            const unsigned long long v = ld_acquire_u64((const unsigned long long*)Op::tile_state(c, j_hi - q));
-            if ((v >> 32) == (epoch & 0xffffffffull) && (v & 3ull)) {
-              ready |= 1u << q;
-              if ((v & 3ull) == 2ull) pref |= 1u << q;
-            }
-          }
-        }
-        ready = __reduce_or_sync(g.mask, ready);
-        pref = __reduce_or_sync(g.mask, pref);
-        need = pref ? __ffs(pref) : w;  // tiles q < need
-        const unsigned want = (need >= 32) ? 0xffffffffu : ((1u << need) - 1u);
-        if ((ready & want) == want) { timed_out = false; break; }
-        __nanosleep(ns);
-        if (ns < 1024) ns <<= 1;
-      }
-      if (g.lane == 0) {
-        ctl[0] = need;
-        ctl[1] = pref ? 1 : 0;
-        ctl[2] = timed_out ? 1 : 0;
-        if (timed_out) raise_err(c.ctr, DEVERR_TIMEOUT);
-      }
-    }
-    __syncthreads();
-    const int need = ctl[0];
-    const bool found = ctl[1] != 0;
-    if (ctl[2]) break;
-    // payloads: aggregates, except the last one when it holds a prefix
-    for (int idx = threadIdx.x; idx < need * ES; idx += blockDim.x) {
-      const int q = idx / ES, e = idx - (idx / ES) * ES;
-      const int slot = (found && q == need - 1) ? 1 : 0;
-      const T* srcp = (const T*)(Op::tile_state(c, j_hi - q) + 16 + slot * ScanSmem<Op>::payload_bytes());
-      win[idx] = __ldcg(srcp + e);
-    }
-    __syncthreads();
-    // tree: x_q = tile j_hi - q; product in scan order x_{k-1} (x) ... (x) x_0
-    T* cur = win;
-    T* nxt = win2;
-    int k = need;
-    while (k > 1) {
-      const int pairs = k >> 1;
-      for (int pi = gid; pi < pairs; pi += NG)
-        ok &= Op::combine(g, nxt + pi * ES, cur + (2 * pi + 1) * ES, cur + 2 * pi * ES, sc, scs, false);
-      if ((k & 1) && gid == pairs % NG)
-        for (int e = g.lane; e < ES; e += G) nxt[pairs * ES + e] = cur[(k - 1) * ES + e];
-      __syncthreads();
-      T* x = cur; cur = nxt; nxt = x;
-      k = pairs + (k & 1);
-    }
-    if (gid == 0) {
-      ok &= Op::combine(g, tmp, cur, excl, sc, scs, false);
-      for (int e = g.lane; e < ES; e += G) excl[e] = tmp[e];
+      ok &= Op::combine(g, tmp, excl, agg, sc, scs, false);
+      publish<Op>(g, ts, tmp, 2, 3u, epoch);
       g.sync();
     }
     __syncthreads();
-    if (found || j_hi - need < j_lo) break;
-    j_hi -= need;
+  }
+  // 2. the last tiles of the earlier groups
+  j_hi = g_lo - 1;
+  while (rc == 0 && j_hi >= j_lo) {
+    const int w = (int)min((long long)W, (j_hi - j_lo) / W + 1);
+    rc = lookback_round<Op>(g, gid, NG, c, epoch, j_hi, W, w, excl, tmp, win, ctl, sc, scs, ok, used);
+    if (rc != 0) break;
+    j_hi -= (long long)used * W;
   }
   if (gid == 0) {
     ok &= Op::combine(g, tmp, excl, agg, sc, scs, false);
@@ -1217,8 +1399,8 @@ int query_shapes_t(int scan_groups, int scan_elems, int window, int recover_thre
   sh->scan_groups_f = sh->scan_groups_s = NG;
   sh->scan_elems_f = sh->scan_elems_s = scan_elems;
   sh->window_f = sh->window_s = window;
-  sh->smem_f = ScanSmem<FOp>::bytes(NG, window);
-  sh->smem_s = ScanSmem<SOp>::bytes(NG, window);
+  sh->smem_f = ScanSmem<FOp>::bytes(NG, window, scan_elems);
+  sh->smem_s = ScanSmem<SOp>::bytes(NG, window, scan_elems);
   set_smem_attr<FOp>((const void*)scan_kernel<FOp>, sh->smem_f);
   set_smem_attr<SOp>((const void*)scan_kernel<SOp>, sh->smem_s);
   int nb = 0;

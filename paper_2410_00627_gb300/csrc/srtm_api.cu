@@ -93,8 +93,9 @@ Layout make_layout(int nx, int ny, int max_ratio, int n_seq, long long total_slo
   const long long FE = 3 * nn + 2 * nx, SE = 2 * nn + nx;
   const long long REC = 4 * nn + 2 * nx + 2LL * nx * MY + MY * MY + MY;
   L.ml = make_model_layout(nx, ny, max_ratio);
-  L.ftile_stride = 16 + 2 * (long long)a16(FE * sT);
-  L.stile_stride = 16 + 2 * (long long)a16(SE * sT);
+  // tile state: two flag words, aggregate, inclusive prefix, group aggregate
+  L.ftile_stride = 16 + 3 * (long long)a16(FE * sT);
+  L.stile_stride = 16 + 3 * (long long)a16(SE * sT);
   const long long tiles_f = total_slow / tile_f + n_seq, tiles_s = total_slow / tile_s + n_seq;
   size_t o = 0;
   auto take = [&](size_t bytes) { const size_t at = a256(o); o = at + bytes; return at; };
