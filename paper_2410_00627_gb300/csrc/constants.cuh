@@ -14,83 +14,68 @@
 // (Eq. 9, 12).  The state size NX is a compile-time constant; the
 // measurement size m <= MY is not.
 #pragma once
+#include "grp.cuh"
+#include "small.cuh"
 #include "srtm_internal.cuh"
 
 namespace srtm {
 
-constexpr int PRE_WARPS = 4;
+constexpr int PRE_THREADS = 256;
 constexpr size_t PRE_SMEM_CAP = 200 * 1024;
 
-// out (R x C, row-major, ld C) = alpha op(A) op(B) + ADD over the 32 lanes of
-// a warp; R <= RM, C <= CM, K <= KM.  op(A) is R x K (tA: A stored K x R),
-// op(B) is K x C (tB: B stored C x K).  No barrier.
-template <int RM, int CM, int KM, bool TA, bool TB>
-__device__ __forceinline__ void w_mm(int R, int K, int C, double* out, const double* A, const double* B,
-                                     const double* ADD, double alpha, int lane) {
-#pragma unroll
-  for (int e0 = 0; e0 < RM * CM; e0 += 32) {
-    const int e = e0 + lane;
+// out (R x C, row-major, ld C) = alpha op(A) op(B) + ADD over the G lanes of
+// one product unit; R <= RM, C <= CM, K <= KM.  op(A) is R x K (TA: A stored
+// K x R), op(B) is K x C (TB: B stored C x K).  SYM: only entries r <= c are
+// formed and each is written to both (r,c) and (c,r) (for results that are
+// symmetric in exact arithmetic).  No barrier.
+template <int RM, int CM, int KM, int G, bool TA, bool TB, bool SYM = false>
+__device__ __forceinline__ void u_mm(int lane, int R, int K, int C, double* out, const double* A, const double* B,
+                                     const double* ADD, double alpha) {
+  for (int e = lane; e < RM * CM; e += G) {
     const int r = e / CM, c = e - (e / CM) * CM;
-    if (e < RM * CM && r < R && c < C) {
+    if (r < R && c < C && (!SYM || r <= c)) {
       double s = 0.0;
 #pragma unroll
       for (int k = 0; k < KM; ++k)
         if (k < K) s = fma(TA ? A[k * R + r] : A[r * K + k], TB ? B[c * K + k] : B[k * C + c], s);
-      out[r * C + c] = ADD ? fma(alpha, s, ADD[r * C + c]) : alpha * s;
+      const double v = ADD ? fma(alpha, s, ADD[r * C + c]) : alpha * s;
+      out[r * C + c] = v;
+      if (SYM) out[c * C + r] = v;
     }
   }
 }
 
-// in-place symmetrisation (mean of the two entries), ends with a barrier
-template <int NM>
-__device__ __forceinline__ void w_sym(int n, double* X, int lane) {
-  __syncwarp();
+// inverse of the symmetric m x m matrix a (ld m) by one unit: every lane
+// forms it in registers, lanes write the upper entries, mirrored
+template <int G>
+__device__ __forceinline__ bool u_sym_inverse(int lane, int m, const double* a, double* inv) {
+  double A[MY][MY], Ai[MY][MY];
 #pragma unroll
-  for (int e0 = 0; e0 < NM * NM; e0 += 32) {
-    const int e = e0 + lane;
-    const int r = e / NM, c = e - (e / NM) * NM;
-    if (e < NM * NM && r < c && c < n) {
-      const double v = 0.5 * (X[r * n + c] + X[c * n + r]);
-      X[r * n + c] = v;
-      X[c * n + r] = v;
+  for (int i = 0; i < MY; ++i)
+#pragma unroll
+    for (int j = 0; j < MY; ++j) A[i][j] = (i < m && j < m) ? a[i * m + j] : ((i == j) ? 1.0 : 0.0);
+  const bool ok = small_sym_inverse<double>(A, Ai, m);
+  for (int e = lane; e < MY * MY; e += G) {
+    const int i = e / MY, j = e - (e / MY) * MY;
+    if (i <= j && j < m) {
+      double v = 0.0;
+#pragma unroll
+      for (int ii = 0; ii < MY; ++ii)
+#pragma unroll
+        for (int jj = 0; jj < MY; ++jj)
+          if (ii == i && jj == j) v = Ai[ii][jj];
+      inv[i * m + j] = v;
+      inv[j * m + i] = v;
     }
-  }
-  __syncwarp();
-}
-
-// inverse of a small m x m matrix by Gauss-Jordan with partial pivoting, on
-// one lane.  a is overwritten.  Returns false on a zero pivot.
-__device__ inline bool small_inverse(int n, double* a, double* inv) {
-  bool ok = true;
-  for (int i = 0; i < n * n; ++i) inv[i] = (i / n == i % n) ? 1.0 : 0.0;
-  for (int s = 0; s < n; ++s) {
-    int p = s;
-    for (int r = s + 1; r < n; ++r)
-      if (fabs(a[r * n + s]) > fabs(a[p * n + s])) p = r;
-    if (!(fabs(a[p * n + s]) > 0.0)) { ok = false; continue; }
-    if (p != s)
-      for (int c = 0; c < n; ++c) {
-        double t = a[s * n + c]; a[s * n + c] = a[p * n + c]; a[p * n + c] = t;
-        t = inv[s * n + c]; inv[s * n + c] = inv[p * n + c]; inv[p * n + c] = t;
-      }
-    const double d = 1.0 / a[s * n + s];
-    for (int c = 0; c < n; ++c) { a[s * n + c] *= d; inv[s * n + c] *= d; }
-    for (int r = 0; r < n; ++r)
-      if (r != s) {
-        const double f = a[r * n + s];
-        if (f != 0.0)
-          for (int c = 0; c < n; ++c) {
-            a[r * n + c] = fma(-f, a[s * n + c], a[r * n + c]);
-            inv[r * n + c] = fma(-f, inv[s * n + c], inv[r * n + c]);
-          }
-      }
   }
   return ok;
 }
 
 // shared-memory layout of the constants kernel (doubles)
 template <int NX>
-struct PreSmem {
+struct PreGeom {
+  static constexpr int G = GroupSize<NX>::value;  // lanes per product unit
+  static constexpr int NU = PRE_THREADS / G;      // product units per block
   static constexpr int NN = NX * NX, NM = NX * MY, MM = MY * MY;
   // inputs
   static constexpr int A = 0, Q = A + NN, H = Q + NN, R = H + NM, P0 = R + MM, m0 = P0 + NN, y0 = m0 + NX;
@@ -98,16 +83,28 @@ struct PreSmem {
   static constexpr int T = y0 + MY, Vs = T + NN, HVs = Vs + NN, Rx = HVs + NM, Rxi = Rx + MM, GQM = Rxi + MM,
                        K = GQM + NM, Cr = K + NM, Cb = Cr + NM, Fc = Cb + NM, Dc = Fc + NN, Jc = Dc + NN,
                        AP = Jc + NN, CP = AP + NN, cross = CP + NM, S1 = cross + NM, S1i = S1 + MM, Lg = S1i + MM,
-                       innov = Lg + NM, P1 = innov + MY, P1o = P1 + NN, m1 = P1o + NN, wk = m1 + NX;
-  static constexpr int WARP_SCR = wk + MM;                   // per-warp n x n scratch follows
-  static constexpr int BASE = WARP_SCR + PRE_WARPS * NN;     // tables follow
-  __host__ __device__ static size_t tables(int L) { return (size_t)(4 * L + 1) * NN; }
+                       innov = Lg + NM, P1 = innov + MY, P1o = P1 + NN, m1 = P1o + NN, USCR = m1 + NX;
+  static constexpr int BASE = USCR + NU * NN;  // per-unit n x n scratch, then the tables
+  // tables: A^0..A^L, S_0..S_{L-1}, Cov(e_i) terms / prefixes, two V buffers
+  __host__ __device__ static size_t tables(int L) { return (size_t)(5 * L + 1) * NN; }
 };
 
+// Per-model constants of one sequence (block = sequence), float64.
+//  1. A^i (i <= l) by doubling: round h forms A^{h+t} = A^h A^t, t = 1..h.
+//  2. the terms A^r Q A^{rT} (r < l), one product unit each.
+//  3. per entry, the running sums S_q = sum_{j<=q} A^j and
+//     Qc_i = Cov(e_i) = sum_{r<i} A^r Q A^{rT}.
+//  4. W_i = Q S_{l-i}^T, Cov(e_i, e_l) = Qc_i A^{(l-i)T}, C_bar = H sum A^i.
+//  5. V_i = A V_{i-1} + W_i (V_1 = W_1) solved as V_i = sum_{j<=i} A^{i-j} W_j
+//     by a log-depth scan: after the round with offset d,
+//     X_i <- X_i + A^d X_{i-d} covers the terms j > i - 2d.
+//  6. V_i H^T, G Q~ M^T = V_l H^T, M Q~ M^T = H (sum_i V_i) H^T.
+//  7. R_x, K, C_bar^T R_x^-1, F, D, J and the first element (one IMKF step
+//     from (m0, P0)), independent products on different units.
 template <int NX>
-__global__ void __launch_bounds__(32 * PRE_WARPS) precompute_kernel(Ctx c, int tables_in_smem) {
-  constexpr int NN = NX * NX;
-  using S = PreSmem<NX>;
+__global__ void __launch_bounds__(PRE_THREADS) precompute_kernel(Ctx c, int tables_in_smem) {
+  using S = PreGeom<NX>;
+  constexpr int G = S::G, NU = S::NU, NN = S::NN;
   extern __shared__ __align__(16) double dsm[];
   __shared__ int s_ok;
   if (c.fold_meta) {
@@ -138,20 +135,23 @@ __global__ void __launch_bounds__(32 * PRE_WARPS) precompute_kernel(Ctx c, int t
   const int m = c.ny, l = c.meta.ratio[s];
   const ModelLayout L = c.ml;
   double* md = c.model + (long long)s * L.stride;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x, nt = blockDim.x;
+  const int tid = threadIdx.x, nt = blockDim.x, unit = tid / G, lane = tid - (tid / G) * G;
+  const unsigned umask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << ((tid & 31) & ~(G - 1)));
   double* sm = dsm;
-  double* wb = dsm + S::WARP_SCR + warp * NN;
-  double *Ap, *Sp, *Qp, *Vp;
+  double* ub = dsm + S::USCR + unit * NN;
+  double *Ap, *Sp, *Qp, *X0, *X1;
   if (tables_in_smem) {
     Ap = dsm + S::BASE;
     Sp = Ap + (size_t)(l + 1) * NN;
     Qp = Sp + (size_t)l * NN;
-    Vp = Qp + (size_t)l * NN;
+    X0 = Qp + (size_t)l * NN;
+    X1 = X0 + (size_t)l * NN;
   } else {
     Ap = md + L.Apow;
     Sp = md + L.Ssc;
     Qp = md + L.Qc;
-    Vp = md + L.Vsc;
+    X0 = md + L.Vsc;
+    X1 = md + L.V2sc;
   }
   {
     const double* F = c.F + (long long)s * NN;
@@ -178,24 +178,24 @@ __global__ void __launch_bounds__(32 * PRE_WARPS) precompute_kernel(Ctx c, int t
     if (tid == 0) s_ok = 1;
   }
   __syncthreads();
-  // A^{h+t} = A^h A^t, t = 1..h, per doubling round
+  // 1. powers
   for (int h = 1; h < l; h *= 2) {
     const int cnt = min(h, l - h);
-    for (int t = warp; t < cnt; t += PRE_WARPS)
-      w_mm<NX, NX, NX, false, false>(NX, NX, NX, Ap + (size_t)(h + 1 + t) * NN, Ap + (size_t)h * NN,
-                                     Ap + (size_t)(1 + t) * NN, nullptr, 1.0, lane);
+    for (int t = unit; t < cnt; t += NU)
+      u_mm<NX, NX, NX, G, false, false>(lane, NX, NX, NX, Ap + (size_t)(h + 1 + t) * NN, Ap + (size_t)h * NN,
+                                        Ap + (size_t)(1 + t) * NN, nullptr, 1.0);
     __syncthreads();
   }
-  // terms A^r Q A^rT (r = 0..l-1) into the Qc table
-  for (int r = warp; r < l; r += PRE_WARPS) {
-    w_mm<NX, NX, NX, false, false>(NX, NX, NX, wb, Ap + (size_t)r * NN, sm + S::Q, nullptr, 1.0, lane);
-    __syncwarp();
-    w_mm<NX, NX, NX, false, true>(NX, NX, NX, Qp + (size_t)r * NN, wb, Ap + (size_t)r * NN, nullptr, 1.0, lane);
-    __syncwarp();
+  // 2. terms A^r Q A^{rT}
+  for (int r = unit; r < l; r += NU) {
+    u_mm<NX, NX, NX, G, false, false>(lane, NX, NX, NX, ub, Ap + (size_t)r * NN, sm + S::Q, nullptr, 1.0);
+    __syncwarp(umask);
+    u_mm<NX, NX, NX, G, false, true, true>(lane, NX, NX, NX, Qp + (size_t)r * NN, ub, Ap + (size_t)r * NN, nullptr,
+                                           1.0);
+    __syncwarp(umask);
   }
   __syncthreads();
-  // running sums S_q (q < l), sum_{i=1..l} A^i, and Qc_i = sum_{r<i} terms
-  // (symmetric: one thread per upper-triangle pair)
+  // 3. running sums per entry
   for (int e = tid; e < NN; e += nt) {
     const int r = e / NX, q = e - (e / NX) * NX;
     double acc = (r == q) ? 1.0 : 0.0;
@@ -205,150 +205,137 @@ __global__ void __launch_bounds__(32 * PRE_WARPS) precompute_kernel(Ctx c, int t
       Sp[(size_t)j * NN + e] = acc;
     }
     sm[S::T + e] = acc + Ap[(size_t)l * NN + e] - ((r == q) ? 1.0 : 0.0);
+    double qa = 0.0;
+    for (int j = 0; j < l; ++j) {
+      qa += Qp[(size_t)j * NN + e];
+      Qp[(size_t)j * NN + e] = qa;
+    }
+  }
+  __syncthreads();
+  // 4. W_i = Q S_{l-i}^T (i = 1..l), Cov(e_i, e_l) = Qc_i A^{(l-i)T}, C_bar = H T
+  for (int t = unit; t <= 2 * l; t += NU) {
+    if (t < l) {
+      const int i = t + 1;
+      u_mm<NX, NX, NX, G, false, true>(lane, NX, NX, NX, X0 + (size_t)(i - 1) * NN, sm + S::Q,
+                                       Sp + (size_t)(l - i) * NN, nullptr, 1.0);
+    } else if (t < 2 * l) {
+      const int i = t - l + 1;
+      u_mm<NX, NX, NX, G, false, true>(lane, NX, NX, NX, md + L.Ql + (size_t)(i - 1) * NN, Qp + (size_t)(i - 1) * NN,
+                                       Ap + (size_t)(l - i) * NN, nullptr, 1.0);
+    } else {
+      u_mm<MY, NX, NX, G, false, false>(lane, m, NX, NX, sm + S::Cb, sm + S::H, sm + S::T, nullptr, 1.0);
+    }
+  }
+  __syncthreads();
+  // 5. V_i = sum_{j<=i} A^{i-j} W_j by doubling offsets
+  double* cur = X0;
+  double* nxt = X1;
+  for (int d = 1; d < l; d *= 2) {
+    for (int i = unit + 1; i <= l; i += NU) {
+      if (i > d) {
+        u_mm<NX, NX, NX, G, false, false>(lane, NX, NX, NX, nxt + (size_t)(i - 1) * NN, Ap + (size_t)d * NN,
+                                          cur + (size_t)(i - 1 - d) * NN, cur + (size_t)(i - 1) * NN, 1.0);
+      } else {
+        for (int e = lane; e < NN; e += G) nxt[(size_t)(i - 1) * NN + e] = cur[(size_t)(i - 1) * NN + e];
+      }
+    }
+    __syncthreads();
+    double* x = cur; cur = nxt; nxt = x;
+  }
+  // 6. V_i H^T, G Q~ M^T = V_l H^T; sum_i V_i (symmetrised) per entry
+  for (int t = unit; t <= l; t += NU) {
+    if (t < l)
+      u_mm<NX, MY, NX, G, false, true>(lane, NX, NX, m, md + L.VH + (size_t)t * NX * m, cur + (size_t)t * NN,
+                                       sm + S::H, nullptr, 1.0);
+    else
+      u_mm<NX, MY, NX, G, false, true>(lane, NX, NX, m, sm + S::GQM, cur + (size_t)(l - 1) * NN, sm + S::H,
+                                       nullptr, 1.0);
   }
   for (int e = tid; e < NN; e += nt) {
     const int r = e / NX, q = e - (e / NX) * NX;
-    if (r > q) continue;
-    double acc = 0.0;
-    for (int j = 0; j < l; ++j) {
-      acc += 0.5 * (Qp[(size_t)j * NN + r * NX + q] + Qp[(size_t)j * NN + q * NX + r]);
-      Qp[(size_t)j * NN + r * NX + q] = acc;
-      Qp[(size_t)j * NN + q * NX + r] = acc;
-    }
-  }
-  __syncthreads();
-  // V chain (warp 0), one fused pass per step:  V_i = A V_{i-1} + Q S_{l-i}^T
-  // Cov(e_i, e_l) = Qc_i A^{(l-i)T} (warps 1..3); C_bar = H sum A^i (warp 1)
-  if (warp == 0) {
-    w_mm<NX, NX, NX, false, true>(NX, NX, NX, Vp, sm + S::Q, Sp + (size_t)(l - 1) * NN, nullptr, 1.0, lane);
-    __syncwarp();
-    for (int i = 2; i <= l; ++i) {
-      const double* Vprev = Vp + (size_t)(i - 2) * NN;
-      const double* Sl = Sp + (size_t)(l - i) * NN;
-      double* Vi = Vp + (size_t)(i - 1) * NN;
-#pragma unroll
-      for (int e0 = 0; e0 < NN; e0 += 32) {
-        const int e = e0 + lane;
-        if (e < NN) {
-          const int r = e / NX, q = e - (e / NX) * NX;
-          double acc = 0.0;
-#pragma unroll
-          for (int k = 0; k < NX; ++k) {
-            acc = fma(sm[S::A + r * NX + k], Vprev[k * NX + q], acc);
-            acc = fma(sm[S::Q + r * NX + k], Sl[q * NX + k], acc);
-          }
-          Vi[e] = acc;
-        }
-      }
-      __syncwarp();
-    }
-  } else {
-    if (warp == 1) w_mm<MY, NX, NX, false, false>(m, NX, NX, sm + S::Cb, sm + S::H, sm + S::T, nullptr, 1.0, lane);
-    for (int i = warp; i <= l; i += PRE_WARPS - 1)
-      w_mm<NX, NX, NX, false, true>(NX, NX, NX, md + L.Ql + (size_t)(i - 1) * NN, Qp + (size_t)(i - 1) * NN,
-                                    Ap + (size_t)(l - i) * NN, nullptr, 1.0, lane);
-  }
-  __syncthreads();
-  // V_i H^T (all warps); tables to global when they were in shared memory
-  for (int i = warp + 1; i <= l; i += PRE_WARPS)
-    w_mm<NX, MY, NX, false, true>(NX, NX, m, md + L.VH + (size_t)(i - 1) * NX * m, Vp + (size_t)(i - 1) * NN,
-                                  sm + S::H, nullptr, 1.0, lane);
-  if (warp == 1) {  // V_l H^T = G Q~ M^T, kept in shared memory as well
-    w_mm<NX, MY, NX, false, true>(NX, NX, m, sm + S::GQM, Vp + (size_t)(l - 1) * NN, sm + S::H, nullptr, 1.0, lane);
+    double v = 0.0;
+    for (int i = 0; i < l; ++i) v += cur[(size_t)i * NN + r * NX + q] + cur[(size_t)i * NN + q * NX + r];
+    sm[S::Vs + e] = 0.5 * v;
   }
   if (tables_in_smem) {
     for (size_t e = tid; e < (size_t)(l + 1) * NN; e += nt) md[L.Apow + e] = Ap[e];
     for (size_t e = tid; e < (size_t)l * NN; e += nt) md[L.Qc + e] = Qp[e];
   }
-  for (int e = tid; e < m * NX; e += nt) md[L.Cb + e] = sm[S::Cb + e];
   __syncthreads();
-  // slow-model constants and the first filter element (warp 0, shared memory)
-  if (warp == 0) {
-    const double* Al = Ap + (size_t)l * NN;
-    const double* Qcl = Qp + (size_t)(l - 1) * NN;
-#pragma unroll
-    for (int e0 = 0; e0 < NN; e0 += 32) {
-      const int e = e0 + lane;
-      if (e < NN) {
-        double v = 0.0;
-        for (int i = 0; i < l; ++i) v += Vp[(size_t)i * NN + e];
-        sm[S::Vs + e] = v;
-      }
-    }
-    w_sym<NX>(NX, sm + S::Vs, lane);
-    w_mm<MY, NX, NX, false, false>(m, NX, NX, sm + S::HVs, sm + S::H, sm + S::Vs, nullptr, 1.0, lane);
-    __syncwarp();
-    w_mm<MY, MY, NX, false, true>(m, NX, m, sm + S::Rx, sm + S::HVs, sm + S::H, sm + S::R, 1.0, lane);
-    w_sym<MY>(m, sm + S::Rx, lane);
-    if (lane == 0) {
-      for (int e = 0; e < m * m; ++e) sm[S::wk + e] = sm[S::Rx + e];
-      if (!small_inverse(m, sm + S::wk, sm + S::Rxi)) s_ok = 0;
-    }
-    __syncwarp();
-    w_sym<MY>(m, sm + S::Rxi, lane);
-    // K = G Q~ M^T R_x^-1 ; C_bar^T R_x^-1 ; A^l P0 ; C_bar P0
-    w_mm<NX, MY, MY, false, false>(NX, m, m, sm + S::K, sm + S::GQM, sm + S::Rxi, nullptr, 1.0, lane);
-    w_mm<NX, MY, MY, true, false>(NX, m, m, sm + S::Cr, sm + S::Cb, sm + S::Rxi, nullptr, 1.0, lane);
-    w_mm<NX, NX, NX, false, false>(NX, NX, NX, sm + S::AP, Al, sm + S::P0, nullptr, 1.0, lane);
-    w_mm<MY, NX, NX, false, false>(m, NX, NX, sm + S::CP, sm + S::Cb, sm + S::P0, nullptr, 1.0, lane);
-    __syncwarp();
-    // F = A^l - K C_bar ; D = Q_bar - K GQM^T ; J = C_bar^T R_x^-1 C_bar
-    w_mm<NX, NX, MY, false, false>(NX, m, NX, sm + S::Fc, sm + S::K, sm + S::Cb, Al, -1.0, lane);
-    w_mm<NX, NX, MY, false, true>(NX, m, NX, sm + S::Dc, sm + S::K, sm + S::GQM, Qcl, -1.0, lane);
-    w_mm<NX, NX, MY, false, false>(NX, m, NX, sm + S::Jc, sm + S::Cr, sm + S::Cb, nullptr, 1.0, lane);
-    // first element: cross = A^l P0 C_bar^T + GQM ; S1 = C_bar P0 C_bar^T + R_x
-    w_mm<NX, MY, NX, false, true>(NX, NX, m, sm + S::cross, sm + S::AP, sm + S::Cb, sm + S::GQM, 1.0, lane);
-    w_mm<MY, MY, NX, false, true>(m, NX, m, sm + S::S1, sm + S::CP, sm + S::Cb, sm + S::Rx, 1.0, lane);
-    w_sym<NX>(NX, sm + S::Dc, lane);
-    w_sym<NX>(NX, sm + S::Jc, lane);
-    w_sym<MY>(m, sm + S::S1, lane);
-    if (lane == 0) {
-      for (int e = 0; e < m * m; ++e) sm[S::wk + e] = sm[S::S1 + e];
-      if (!small_inverse(m, sm + S::wk, sm + S::S1i)) s_ok = 0;
-    }
-    for (int j = lane; j < m; j += 32) {
+  for (int e = tid; e < m * NX; e += nt) md[L.Cb + e] = sm[S::Cb + e];
+  // 7. slow-model constants and the first filter element
+  const double* Al = Ap + (size_t)l * NN;
+  const double* Qcl = Qp + (size_t)(l - 1) * NN;
+  if (unit == 0) u_mm<MY, NX, NX, G, false, false>(lane, m, NX, NX, sm + S::HVs, sm + S::H, sm + S::Vs, nullptr, 1.0);
+  if (unit == 1) u_mm<NX, NX, NX, G, false, false>(lane, NX, NX, NX, sm + S::AP, Al, sm + S::P0, nullptr, 1.0);
+  if (unit == 2) u_mm<MY, NX, NX, G, false, false>(lane, m, NX, NX, sm + S::CP, sm + S::Cb, sm + S::P0, nullptr, 1.0);
+  if (unit == 3)
+    for (int j = lane; j < m; j += G) {
       double v = sm[S::y0 + j];
       for (int q = 0; q < NX; ++q) v = fma(-sm[S::Cb + j * NX + q], sm[S::m0 + q], v);
       sm[S::innov + j] = v;
     }
-    w_mm<NX, NX, NX, false, true>(NX, NX, NX, sm + S::P1, sm + S::AP, Al, Qcl, 1.0, lane);
-    __syncwarp();
-    w_mm<NX, MY, MY, false, false>(NX, m, m, sm + S::Lg, sm + S::cross, sm + S::S1i, nullptr, 1.0, lane);
-    __syncwarp();
-    for (int r = lane; r < NX; r += 32) {
+  __syncthreads();
+  if (unit == 0)
+    u_mm<MY, MY, NX, G, false, true, true>(lane, m, NX, m, sm + S::Rx, sm + S::HVs, sm + S::H, sm + S::R, 1.0);
+  if (unit == 1)
+    u_mm<NX, NX, NX, G, false, true, true>(lane, NX, NX, NX, sm + S::P1, sm + S::AP, Al, Qcl, 1.0);
+  if (unit == 2)
+    u_mm<NX, MY, NX, G, false, true>(lane, NX, NX, m, sm + S::cross, sm + S::AP, sm + S::Cb, sm + S::GQM, 1.0);
+  __syncthreads();
+  if (unit == 0 && !u_sym_inverse<G>(lane, m, sm + S::Rx, sm + S::Rxi) && lane == 0) s_ok = 0;
+  if (unit == 1)
+    u_mm<MY, MY, NX, G, false, true, true>(lane, m, NX, m, sm + S::S1, sm + S::CP, sm + S::Cb, sm + S::Rx, 1.0);
+  __syncthreads();
+  if (unit == 0) u_mm<NX, MY, MY, G, false, false>(lane, NX, m, m, sm + S::K, sm + S::GQM, sm + S::Rxi, nullptr, 1.0);
+  if (unit == 1) u_mm<NX, MY, MY, G, true, false>(lane, NX, m, m, sm + S::Cr, sm + S::Cb, sm + S::Rxi, nullptr, 1.0);
+  if (unit == 2 && !u_sym_inverse<G>(lane, m, sm + S::S1, sm + S::S1i) && lane == 0) s_ok = 0;
+  __syncthreads();
+  // F = A^l - K C_bar ; D = Q_bar - K GQM^T ; J = C_bar^T R_x^-1 C_bar ; L = cross S1^-1
+  if (unit == 0) u_mm<NX, NX, MY, G, false, false>(lane, NX, m, NX, sm + S::Fc, sm + S::K, sm + S::Cb, Al, -1.0);
+  if (unit == 1)
+    u_mm<NX, NX, MY, G, false, true, true>(lane, NX, m, NX, sm + S::Dc, sm + S::K, sm + S::GQM, Qcl, -1.0);
+  if (unit == 2)
+    u_mm<NX, NX, MY, G, false, false, true>(lane, NX, m, NX, sm + S::Jc, sm + S::Cr, sm + S::Cb, nullptr, 1.0);
+  if (unit == 3)
+    u_mm<NX, MY, MY, G, false, false>(lane, NX, m, m, sm + S::Lg, sm + S::cross, sm + S::S1i, nullptr, 1.0);
+  __syncthreads();
+  if (unit == 0)
+    for (int r = lane; r < NX; r += G) {
       double v = 0.0;
       for (int q = 0; q < NX; ++q) v = fma(Al[r * NX + q], sm[S::m0 + q], v);
       for (int j = 0; j < m; ++j) v = fma(sm[S::Lg + r * m + j], sm[S::innov + j], v);
       sm[S::m1 + r] = v;
     }
-    w_mm<NX, NX, MY, false, true>(NX, m, NX, sm + S::P1o, sm + S::Lg, sm + S::cross, sm + S::P1, -1.0, lane);
-    w_sym<NX>(NX, sm + S::P1o, lane);
-    // results to the model table
-    for (int e = lane; e < NN; e += 32) {
-      md[L.Fc + e] = sm[S::Fc + e];
-      md[L.Dc + e] = sm[S::Dc + e];
-      md[L.Jc + e] = sm[S::Jc + e];
-      md[L.P1 + e] = sm[S::P1o + e];
-    }
-    for (int e = lane; e < NX * m; e += 32) {
-      md[L.K + e] = sm[S::K + e];
-      md[L.Cr + e] = sm[S::Cr + e];
-    }
-    for (int e = lane; e < m * m; e += 32) md[L.Rx + e] = sm[S::Rx + e];
-    for (int e = lane; e < NX; e += 32) md[L.m1 + e] = sm[S::m1 + e];
-    if (lane == 0 && !s_ok) atomicOr(&c.ctr->err, DEVERR_SINGULAR);
+  if (unit == 1)
+    u_mm<NX, NX, MY, G, false, true, true>(lane, NX, m, NX, sm + S::P1o, sm + S::Lg, sm + S::cross, sm + S::P1,
+                                           -1.0);
+  __syncthreads();
+  // results to the model table
+  for (int e = tid; e < NN; e += nt) {
+    md[L.Fc + e] = sm[S::Fc + e];
+    md[L.Dc + e] = sm[S::Dc + e];
+    md[L.Jc + e] = sm[S::Jc + e];
+    md[L.P1 + e] = sm[S::P1o + e];
   }
+  for (int e = tid; e < NX * m; e += nt) {
+    md[L.K + e] = sm[S::K + e];
+    md[L.Cr + e] = sm[S::Cr + e];
+  }
+  for (int e = tid; e < m * m; e += nt) md[L.Rx + e] = sm[S::Rx + e];
+  for (int e = tid; e < NX; e += nt) md[L.m1 + e] = sm[S::m1 + e];
+  if (tid == 0 && !s_ok) atomicOr(&c.ctr->err, DEVERR_SINGULAR);
 }
 
 template <int NX>
 inline void launch_precompute(const Ctx& c, cudaStream_t st) {
-  using S = PreSmem<NX>;
+  using S = PreGeom<NX>;
   const size_t base = S::BASE * sizeof(double), tab = S::tables(c.max_ratio) * sizeof(double);
   const int in_smem = base + tab <= PRE_SMEM_CAP ? 1 : 0;
   const size_t smem = base + (in_smem ? tab : 0);
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(precompute_kernel<NX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  precompute_kernel<NX><<<c.n_seq, 32 * PRE_WARPS, smem, st>>>(c, in_smem);
+  precompute_kernel<NX><<<c.n_seq, PRE_THREADS, smem, st>>>(c, in_smem);
 }
 
 }  // namespace srtm

@@ -1,0 +1,137 @@
+// small.cuh -- thread-local small-matrix helpers (register arrays): the
+// inverse of a symmetric positive definite matrix, the inverse of the m x m
+// measurement covariance, and a bit-pattern test for zero / non-finite values.
+#pragma once
+#include "grp.cuh"
+#include "srtm_internal.cuh"
+
+namespace srtm {
+
+// inverse of a symmetric positive definite matrix by Cholesky (a = L L^T,
+// a^-1 = L^-T L^-1).  Only the leading nact x nact block is inverted; the
+// rest of inv is set to the identity.  Returns false if a pivot is not
+// positive.
+template <int N, class T>
+__device__ __forceinline__ bool spd_inverse(const T (&a)[N][N], T (&inv)[N][N], int nact = N) {
+  T Lm[N][N];
+  bool ok = true;
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) Lm[i][j] = (i == j) ? T(1) : T(0);
+    if (j < nact) {
+      T d = a[j][j];
+#pragma unroll
+      for (int k = 0; k < j; ++k) d = fma(-Lm[j][k], Lm[j][k], d);
+      if (!(d > T(0)) || !isfinite(d)) { ok = false; d = T(1); }
+      const T ljj = sqrt(d), rinv = T(1) / ljj;
+      Lm[j][j] = ljj;
+#pragma unroll
+      for (int i = j + 1; i < N; ++i) {
+        if (i < nact) {
+          T s2 = a[i][j];
+#pragma unroll
+          for (int k = 0; k < j; ++k) s2 = fma(-Lm[i][k], Lm[j][k], s2);
+          Lm[i][j] = s2 * rinv;
+        }
+      }
+    }
+  }
+  T Li[N][N];  // L^-1, lower triangular
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+#pragma unroll
+    for (int j = 0; j < N; ++j) Li[i][j] = (i == j) ? T(1) : T(0);
+    if (i < nact) {
+      Li[i][i] = T(1) / Lm[i][i];
+#pragma unroll
+      for (int j = 0; j < i; ++j) {
+        T s2 = T(0);
+#pragma unroll
+        for (int k = j; k < i; ++k) s2 = fma(Lm[i][k], Li[k][j], s2);
+        Li[i][j] = -s2 * Li[i][i];
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+#pragma unroll
+    for (int j = i; j < N; ++j) {
+      T s2 = (i == j) ? T(1) : T(0);
+      if (j < nact) {
+        s2 = T(0);
+#pragma unroll
+        for (int k = j; k < N; ++k)
+          if (k < nact) s2 = fma(Li[k][i], Li[k][j], s2);
+      }
+      inv[i][j] = s2;
+      inv[j][i] = s2;
+    }
+  return ok;
+}
+
+// ===========================================================================
+// interval setup: for every slow interval k (paper index k+1), from
+// p(x_{k-1,l}|y_{1:k-1}) and y_k, the fast-filter blocks it needs (Eq. 17 on
+// the blocks of Remark 2) and the parallel IMS element (Eq. 29):
+//   X = P C_bar^T, S_y = C_bar X + R_x, kap = S_y^-1 (y - C_bar m),
+//   U_i = A^i X + V_i H^T   (U_i = sum_j P^-_{ij} H^T),
+//   m^f_i = A^i m + U_i kap,  P^f_{ij} = A^i P A^{jT} + Cov(e_i,e_j) - U_i S_y^-1 U_j^T,
+//   P^-_{k+1,1} = A P^f_{ll} A^T + Q,  Z = A^T (P^-_{k+1,1})^-1,
+//   E_k = P^f_{1l} Z,  g_k = m^f_1 - E_k A m^f_l,  S_k = P^f_{11} - E_k A (P^f_{1l})^T
+// (last interval: E = 0, g = m^f_1, S = P^f_{11}).  The record keeps what the
+// recovery reuses.  Runs in TR (float64 except in the float32 mode).
+//
+// Row split: SG lanes per interval (SG = nx rounded up to a power of two),
+// lane r owns row r of every n x n product; the interval's matrices live in
+// a shared-memory slot.  The small SPD inverses are formed by every lane of
+// the interval from the slot (a warp FP64 instruction costs the same whatever
+// its active lanes, so the repetition is free).
+// ===========================================================================
+// zero, infinite or NaN test on the bit pattern
+__device__ __forceinline__ bool bad_value(double x) { return bad_pivot(x); }
+__device__ __forceinline__ bool bad_value(float x) { return bad_pivot(x); }
+
+// Inverse of a small symmetric m x m matrix (m <= MY, runtime) held in the
+// leading block of a: adjugate for m <= 3 (one division), Cholesky for m = 4.
+// The rest of inv is the identity.  Returns false on a singular matrix.
+template <class TR>
+__device__ __forceinline__ bool small_sym_inverse(const TR (&a)[MY][MY], TR (&inv)[MY][MY], int m) {
+#pragma unroll
+  for (int i = 0; i < MY; ++i)
+#pragma unroll
+    for (int j = 0; j < MY; ++j) inv[i][j] = (i == j) ? TR(1) : TR(0);
+  if (m == 4) return spd_inverse<MY, TR>(a, inv, 4);
+  TR det;
+  if (m == 1) {
+    det = a[0][0];
+  } else if (m == 2) {
+    det = a[0][0] * a[1][1] - a[0][1] * a[1][0];
+  } else {
+    det = a[0][0] * (a[1][1] * a[2][2] - a[1][2] * a[2][1]) - a[0][1] * (a[1][0] * a[2][2] - a[1][2] * a[2][0]) +
+          a[0][2] * (a[1][0] * a[2][1] - a[1][1] * a[2][0]);
+  }
+  bool ok = !bad_value(det);
+  if (!ok) det = TR(1);
+  const TR id = TR(1) / det;
+  if (m == 1) {
+    inv[0][0] = id;
+  } else if (m == 2) {
+    inv[0][0] = a[1][1] * id;
+    inv[1][1] = a[0][0] * id;
+    inv[0][1] = -a[0][1] * id;
+    inv[1][0] = -a[1][0] * id;
+  } else {
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const int i0 = c == 0 ? 1 : 0, i1 = c == 2 ? 1 : 2, j0 = r == 0 ? 1 : 0, j1 = r == 2 ? 1 : 2;
+        TR v = a[i0][j0] * a[i1][j1] - a[i0][j1] * a[i1][j0];
+        inv[r][c] = (((r + c) & 1) ? -v : v) * id;
+      }
+  }
+  return ok;
+}
+
+}  // namespace srtm

@@ -45,6 +45,7 @@ struct ModelLayout {
   long long Ql;    // L n^2       Cov(e_i, e_l) = Qc_i A^{(l-i)T}
   long long Ssc;   // L n^2       scratch: S_q = sum_{j<=q} A^j
   long long Vsc;   // L n^2       scratch: V_i
+  long long V2sc;  // L n^2       scratch: second buffer of the V_i scan
   long long Cb;    // m n         C_bar = H sum_{i=1..l} A^i
   long long Rx;    // m m         M Q~ M^T + R
   long long Fc;    // n^2         A^l - K C_bar
@@ -67,6 +68,7 @@ __host__ __device__ inline ModelLayout make_model_layout(int n, int m, int L) {
   ml.Ql = o;   o += L * nn;
   ml.Ssc = o;  o += L * nn;
   ml.Vsc = o;  o += L * nn;
+  ml.V2sc = o; o += L * nn;
   ml.Cb = o;   o += (long long)m * n;
   ml.Rx = o;   o += (long long)m * m;
   ml.Fc = o;   o += nn;
