@@ -293,20 +293,12 @@ __device__ void setup_interval(const Ctx& c, long long gi, int lane, unsigned ma
       sb[Gm::Pl + r * NX + q] = w;
     }
   }
-  __syncwarp(mask);
-  // P^f_{ll} = A^l Pl + Qc_l - U_l SUl (row r)
+  // P^f_{k,l} = P^f_{k,ll}: the filter scan's result for this interval (written
+  // before the setup runs), the fast block ll of Eq. (17) in exact arithmetic
   if (row) {
-    const double* Qcl = md + c.ml.Qc + (long long)(l - 1) * NN;
+    const TR* fk = (const TR*)c.fout + gi * (NX + NN) + NX;
 #pragma unroll
-    for (int q = 0; q < NX; ++q) {
-      TR v = (TR)Qcl[r * NX + q];
-#pragma unroll
-      for (int t = 0; t < NX; ++t) v = fma((TR)Al[r * NX + t], sb[Gm::Pl + t * NX + q], v);
-#pragma unroll
-      for (int j = 0; j < MY; ++j)
-        if (j < m) v = fma(-Ul[j], sb[Gm::SUl + j * NX + q], v);
-      sb[Gm::Pll + r * NX + q] = v;
-    }
+    for (int q = 0; q < NX; ++q) sb[Gm::Pll + r * NX + q] = fk[r * NX + q];
   }
   __syncwarp(mask);
   // A P^f_{ll} (row r)
@@ -472,9 +464,9 @@ __device__ void setup_interval(const Ctx& c, long long gi, int lane, unsigned ma
       T Sif[MY][MY], kapf[MY];
 #pragma unroll
       for (int i = 0; i < MY; ++i) {
-        kapf[i] = (T)kap[i];
+        kapf[i] = i < m ? (T)kap[i] : T(0);
 #pragma unroll
-        for (int j = 0; j < MY; ++j) Sif[i][j] = (T)Si[i][j];
+        for (int j = 0; j < MY; ++j) Sif[i][j] = (i < m && j < m) ? (T)Si[i][j] : T(0);
       }
       __syncwarp(mask);
       setup_elements<NX, T, T, T>(r, row, mask, m, last, sf + Gm::fP, sf + Gm::fPl, sf + Gm::fX, sf + Gm::fSUl,
