@@ -62,6 +62,9 @@ def parse(argv=None):
     ap.add_argument("--workload", choices=["config2", "config4"], default="config2")
     ap.add_argument("--n-seq", type=int, default=4096, help="config4: sequences in the batch")
     ap.add_argument("--no-autotune", action="store_true", help="keep the built-in launch shapes")
+    ap.add_argument("--tuning", default=None,
+                    help="explicit launch shapes scan_groups,scan_elems,recover_threads,lookback_window "
+                         "(for every precision; replaces the autotuner)")
     ap.add_argument("--tune-reps", type=int, default=2)
     return ap.parse_args(argv)
 
@@ -184,8 +187,12 @@ def run_ours(args, rank, world, dist):
         return ms, rec_ms
 
     tuning = {}
-    if not args.no_autotune:
-        precs = [args.precision] + ([] if args.no_extras else ["fp64" if args.precision != "fp64" else "mixed"])
+    precs = [args.precision] + ([] if args.no_extras else ["fp64" if args.precision != "fp64" else "mixed"])
+    if args.tuning:
+        for p in precs:
+            api.set_tuning(prob.nx, p, *[int(v) for v in args.tuning.split(",")])
+            tuning[p] = api.get_tuning(prob.nx, p)
+    elif not args.no_autotune:
         for p in precs:
             tuning[p], _ = api.autotune(*ins, prob.ratio, precision=p, reps=args.tune_reps, out=outs)
     clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
@@ -275,7 +282,11 @@ def run_batched(args, rank, world, dist):
     outs = batch_outputs(torch, dev, n_fast, n_slow, nx)
     precs = [args.precision] + ([] if args.no_extras else ["fp64" if args.precision != "fp64" else "mixed"])
     tuning = {}
-    if not args.no_autotune:   # on the first 512 sequences (same distribution, ~1/8 of the work)
+    if args.tuning:
+        for p in precs:
+            api.set_tuning(nx, p, *[int(v) for v in args.tuning.split(",")])
+            tuning[p] = api.get_tuning(nx, p)
+    elif not args.no_autotune:   # on the first 512 sequences (same distribution, ~1/8 of the work)
         sub = synth.pack(probs[:min(512, len(probs))])
         sb, sten = upload_batch(sub, api, torch, dev)
         so = batch_outputs(torch, dev, sub["total_fast"], sub["total_slow"], nx)

@@ -333,8 +333,13 @@ inline void launch_precompute(const Ctx& c, cudaStream_t st) {
   const size_t base = S::BASE * sizeof(double), tab = S::tables(c.max_ratio) * sizeof(double);
   const int in_smem = base + tab <= PRE_SMEM_CAP ? 1 : 0;
   const size_t smem = base + (in_smem ? tab : 0);
-  if (smem > 48 * 1024)
+  static size_t granted[64] = {};  // per device: the largest size already allowed
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (smem > 48 * 1024 && (dev < 0 || dev >= 64 || smem > granted[dev])) {
     cudaFuncSetAttribute(precompute_kernel<NX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (dev >= 0 && dev < 64) granted[dev] = smem;
+  }
   precompute_kernel<NX><<<c.n_seq, PRE_THREADS, smem, st>>>(c, in_smem);
 }
 

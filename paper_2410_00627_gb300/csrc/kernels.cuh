@@ -998,7 +998,7 @@ __global__ void __launch_bounds__(256) scan_kernel(Ctx c, int NG, int E, int W) 
 // upper triangle and mirrored (exactly symmetric).
 // ===========================================================================
 template <int NX, class TR>
-__global__ void __launch_bounds__(128) recover_kernel(Ctx c) {
+__global__ void __launch_bounds__(128, 3) recover_kernel(Ctx c) {
   constexpr int NN = NX * NX, NT = NX * (NX + 1) / 2;
   using RL = Rec<NX>;
   if (!c.ctr->call_ok) return;
@@ -1210,9 +1210,11 @@ int query_shapes_t(int scan_groups, int scan_elems, int window, int recover_thre
   int nb = 0;
   const long long tiles = total_slow / ((long long)NG * scan_elems) + n_seq;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, scan_kernel<FOp>, threads, sh->smem_f);
-  sh->grid_f = (int)std::max(1LL, std::min((long long)std::max(nb, 1) * sm_count, tiles));
+  sh->blocks_per_sm_f = std::max(nb, 1);
+  sh->grid_f = (int)std::max(1LL, std::min((long long)sh->blocks_per_sm_f * sm_count, tiles));
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, scan_kernel<SOp>, threads, sh->smem_s);
-  sh->grid_s = (int)std::max(1LL, std::min((long long)std::max(nb, 1) * sm_count, tiles));
+  sh->blocks_per_sm_s = std::max(nb, 1);
+  sh->grid_s = (int)std::max(1LL, std::min((long long)sh->blocks_per_sm_s * sm_count, tiles));
   sh->grid_setup = 0;
   sh->smem_setup = 0;
   sh->recover_threads = recover_threads;

@@ -117,8 +117,49 @@ Layout make_layout(int nx, int ny, int max_ratio, int n_seq, long long total_slo
   return L;
 }
 
+// Launch shapes depend on (nx, precision, tuning) and the GPU; the scan grids
+// also on the tile count.  The occupancy queries and attribute settings are
+// made once per key and device and cached (caller holds g_mu).
+struct ShapeKey {
+  int dev, nx, prec, sg, se, rt, w;
+  bool operator==(const ShapeKey& o) const {
+    return dev == o.dev && nx == o.nx && prec == o.prec && sg == o.sg && se == o.se && rt == o.rt && w == o.w;
+  }
+};
+constexpr int SHAPE_CACHE = 64;
+ShapeKey g_shape_key[SHAPE_CACHE];
+Shapes g_shape_val[SHAPE_CACHE];
+int g_shape_n = 0, g_shape_next = 0;
+
+int query_shapes_for(int nx, srtm_precision prec, const srtm_tuning& t, int sms, long long total_slow, int n_seq,
+                     Shapes* sh);
+
 int shapes_for(int nx, srtm_precision prec, const srtm_tuning& t, int sms, long long total_slow, int n_seq,
                Shapes* sh) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const ShapeKey key{dev, nx, (int)prec, t.scan_groups, t.scan_elems, t.recover_threads, t.lookback_window};
+  int hit = -1;
+  for (int i = 0; i < g_shape_n; ++i)
+    if (g_shape_key[i] == key) { hit = i; break; }
+  if (hit < 0) {
+    const int rc = query_shapes_for(nx, prec, t, sms, total_slow, n_seq, sh);
+    if (rc) return rc;
+    hit = g_shape_next;
+    g_shape_key[hit] = key;
+    g_shape_val[hit] = *sh;
+    g_shape_next = (g_shape_next + 1) % SHAPE_CACHE;
+    if (g_shape_n < SHAPE_CACHE) ++g_shape_n;
+  }
+  *sh = g_shape_val[hit];
+  const long long tiles = total_slow / ((long long)sh->scan_groups_f * sh->scan_elems_f) + n_seq;
+  sh->grid_f = (int)std::max(1LL, std::min((long long)sh->blocks_per_sm_f * sms, tiles));
+  sh->grid_s = (int)std::max(1LL, std::min((long long)sh->blocks_per_sm_s * sms, tiles));
+  return SRTM_OK;
+}
+
+int query_shapes_for(int nx, srtm_precision prec, const srtm_tuning& t, int sms, long long total_slow, int n_seq,
+                     Shapes* sh) {
 #define SRTM_Q(N) \
   case N:                                                                                               \
     return query_shapes<N>(prec, t.scan_groups, t.scan_elems, t.lookback_window, t.recover_threads, sms, total_slow, \

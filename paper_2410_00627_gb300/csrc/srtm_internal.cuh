@@ -176,6 +176,7 @@ struct Shapes {  // resolved launch shapes for one call
   int window_f, window_s;  // look-back window (tiles per round)
   int recover_threads;
   int grid_f, grid_s, grid_setup;
+  int blocks_per_sm_f, blocks_per_sm_s;  // resident scan blocks per SM
   size_t smem_f, smem_s, smem_setup;
 };
 
