@@ -1186,9 +1186,17 @@ __global__ void __launch_bounds__(128, 3) recover_kernel(Ctx c) {
 // ===========================================================================
 // host-side launch of the templated stages
 // ===========================================================================
+// Raises (never lowers) a kernel's dynamic shared-memory limit on the current
+// device: launches with other shapes may still need a larger limit.
 template <class Op>
 inline void set_smem_attr(const void* fn, size_t bytes) {
-  if (bytes > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  static size_t granted[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (bytes > 48 * 1024 && (dev < 0 || dev >= 64 || bytes > granted[dev])) {
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (dev >= 0 && dev < 64) granted[dev] = bytes;
+  }
 }
 
 template <int NX, class T, class TS, class TR>

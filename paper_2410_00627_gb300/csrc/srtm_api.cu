@@ -254,7 +254,8 @@ int run(Ctx c, srtm_precision prec, cudaStream_t st) {
   rc = launch_meta(c, st, ev);
   if (rc) return fail(rc, "launch of the metadata kernel failed: %s", cudaGetErrorString(cudaGetLastError()));
   rc = launch_for(c.nx, c, prec, sh, st, ev ? ev + 2 : nullptr);
-  if (rc) return fail(rc, "launch of the scan/recovery kernels failed: %s", cudaGetErrorString(cudaGetLastError()));
+  if (rc) return fail(rc, "launch of the constants/scan/recovery kernels failed (scan smem %zu/%zu bytes)", sh.smem_f,
+                      sh.smem_s);
   return SRTM_OK;
 }
 
