@@ -180,6 +180,8 @@ int srtm_autotune_batch(const srtm_batch *b, srtm_precision prec, const srtm_out
  * also forms the per-interval smoother elements), smoother scan (smoother
  * calls only) and fast-rate recovery, plus the metadata kernel for batches. */
 int srtm_launches_per_call(int smoothing, int batched);
+/* Kernel launches of the last call issued on the current GPU (0 before any). */
+int srtm_last_call_launches(void);
 
 /* Stage timing.  While enabled, every call records CUDA events on its stream
  * around each of its launches.  srtm_stage_times() waits for the last timed

@@ -22,7 +22,8 @@ OUTPUT_KEYS = ("fast_mean", "fast_cov", "slow_mean", "slow_cov")
 SYMBOLS = ("srtm_filter", "srtm_smoother", "srtm_filter_batch", "srtm_smoother_batch",
            "srtm_smoother_host", "srtm_status", "srtm_last_error_detail", "srtm_release",
            "srtm_set_tuning", "srtm_get_tuning", "srtm_launches_per_call", "srtm_set_stage_timing",
-           "srtm_stage_times", "srtm_smoother_noalloc", "srtm_autotune", "srtm_autotune_batch")
+           "srtm_stage_times", "srtm_smoother_noalloc", "srtm_autotune", "srtm_autotune_batch",
+           "srtm_last_call_launches")
 STAGES = ("metadata", "constants", "filter_scan", "interval_setup", "smoother_scan", "recovery")
 
 
@@ -85,6 +86,7 @@ def load():
         "srtm_set_tuning": [c_int, c_int, T],
         "srtm_get_tuning": [c_int, c_int, T],
         "srtm_launches_per_call": [c_int, c_int],
+        "srtm_last_call_launches": [],
         "srtm_set_stage_timing": [c_int],
         "srtm_stage_times": [ctypes.POINTER(ctypes.c_float), c_int],
         "srtm_smoother_noalloc": [P, c_int, O, c_void_p],
@@ -274,6 +276,11 @@ def autotune_batch(batch: Batch, precision="mixed", reps=2, stream=None, device=
     _check(load().srtm_autotune_batch(ctypes.byref(batch), PRECISION[precision], ctypes.byref(so), int(reps),
                                       ctypes.byref(t), ctypes.byref(ms), _stream_handle(stream)))
     return {k: getattr(t, k) for k, _ in Tuning._fields_}, float(ms.value)
+
+
+def last_call_launches() -> int:
+    """Kernel launches of the last call issued on the current GPU."""
+    return load().srtm_last_call_launches()
 
 
 def launches_per_call(smoothing: bool = True, batched: bool = False) -> int:

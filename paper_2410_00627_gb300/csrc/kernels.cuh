@@ -638,7 +638,7 @@ struct SmootherOp {
     TR* dP = scs;
     TR* ZdP = scs + NN;
     TR* dm = scs + 2 * NN;
-    TR* out = (TR*)c.sfin + row * (NN + NX);
+    TR* out = (TR*)c.sfin + row * SFin<NX>::SIZE;
     for (int e = g.lane; e < NN; e += G) dP[e] = (TR)x[L::S + e] - rc[RL::Pm + e];
     g_mv<NX, G, false, TR>(g, dm, A1, rc + RL::ml, x + L::g, TR(-1));
     g.sync();
@@ -997,27 +997,37 @@ __global__ void __launch_bounds__(256) scan_kernel(Ctx c, int NG, int E, int W) 
 // interval is smoothed = filtered (E_N = 0).  Covariances are formed on the
 // upper triangle and mirrored (exactly symmetric).
 // ===========================================================================
+struct FastIdx {
+  int s, l, N, i;     // sequence, ratio, slow steps, fast index in the interval (1-based)
+  long long k, row;   // interval within the sequence, global slow row
+};
+
+__device__ __forceinline__ FastIdx fast_index(const Ctx& c, long long f) {
+  FastIdx x;
+  x.s = find_segment(c.meta.off_fast, c.n_seq, f);
+  x.l = c.meta.ratio[x.s];
+  x.N = c.meta.nslow[x.s];
+  const long long loc = f - c.meta.off_fast[x.s];
+  x.k = loc / x.l;
+  x.i = (int)(loc - x.k * x.l) + 1;
+  x.row = c.meta.off_slow[x.s] + x.k;
+  return x;
+}
+
+// filtered moments of fast step x: m^f_i, P^f_ii (upper triangle) and, when
+// need_pfl, P^f_il
 template <int NX, class TR>
-__global__ void __launch_bounds__(128, 3) recover_kernel(Ctx c) {
-  constexpr int NN = NX * NX, NT = NX * (NX + 1) / 2;
+__device__ __forceinline__ void recover_filtered(const Ctx& c, const FastIdx& x, bool need_pfl, TR (&mf)[NX],
+                                                 TR (&Pf)[NX * (NX + 1) / 2], TR (&Pfl)[NX][NX]) {
+  constexpr int NN = NX * NX;
   using RL = Rec<NX>;
-  if (!c.ctr->call_ok) return;
-  const long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (f >= c.total_fast) return;
-  const int m = c.ny;
-  const int s = find_segment(c.meta.off_fast, c.n_seq, f);
-  const int l = c.meta.ratio[s], N = c.meta.nslow[s];
-  const long long loc = f - c.meta.off_fast[s];
-  const long long k = loc / l;
-  const int i = (int)(loc - k * l) + 1;
-  const long long row = c.meta.off_slow[s] + k;
-  const double* md = c.model + (long long)s * c.ml.stride;
-  const TR* rc = (const TR*)c.rec + row * RL::SIZE;
+  const int m = c.ny, i = x.i;
+  const double* md = c.model + (long long)x.s * c.ml.stride;
+  const TR* rc = (const TR*)c.rec + x.row * RL::SIZE;
   const double* Ai = md + c.ml.Apow + (long long)i * NN;
   const double* VHi = md + c.ml.VH + (long long)(i - 1) * NX * m;
   const double* Qci = md + c.ml.Qc + (long long)(i - 1) * NN;
   const double* Qli = md + c.ml.Ql + (long long)(i - 1) * NN;
-  const bool smooth = c.smoothing != 0;
   TR a[NX][NX];
 #pragma unroll
   for (int r = 0; r < NX; ++r)
@@ -1038,7 +1048,6 @@ __global__ void __launch_bounds__(128, 3) recover_kernel(Ctx c) {
       U[r][jj] = v;
     }
   // m^f_i = A^i m + U_i kap
-  TR mf[NX];
 #pragma unroll
   for (int r = 0; r < NX; ++r) {
     TR v = TR(0);
@@ -1049,10 +1058,8 @@ __global__ void __launch_bounds__(128, 3) recover_kernel(Ctx c) {
       if (jj < m) v = fma(U[r][jj], rc[RL::kap + jj], v);
     mf[r] = v;
   }
-  const bool smooth_k = smooth && (k < N - 1);
   // P^f_il = A^i Pl + Cov(e_i,e_l) - U_i SUl
-  TR Pfl[NX][NX];
-  if (smooth_k) {
+  if (need_pfl) {
 #pragma unroll
     for (int r = 0; r < NX; ++r)
 #pragma unroll
@@ -1067,7 +1074,6 @@ __global__ void __launch_bounds__(128, 3) recover_kernel(Ctx c) {
       }
   }
   // P^f_ii (upper triangle)
-  TR Pf[NT];
   {
     TR US[NX][MY], AP[NX][NX];
 #pragma unroll
@@ -1105,82 +1111,104 @@ __global__ void __launch_bounds__(128, 3) recover_kernel(Ctx c) {
         Pf[u++] = v;
       }
   }
-  const long long fi = f;
-  const long long si = row;
-  auto store_state = [&](double* mo, double* co, double* smo, double* sco, const TR* mvv, const TR* Pu) {
-    if (mo) {
+}
+
+// smoothing update in place: m += P^f_il om, P += (P^f_il Om) P^f_il^T (upper)
+template <int NX, class TR>
+__device__ __forceinline__ void recover_smooth(const TR* Om, const TR* om, TR (&mf)[NX], TR (&Pf)[NX * (NX + 1) / 2],
+                                               const TR (&Pfl)[NX][NX]) {
+  TR T1[NX][NX];
 #pragma unroll
-      for (int r = 0; r < NX; ++r) mo[fi * NX + r] = (double)mvv[r];
+  for (int r = 0; r < NX; ++r)
+#pragma unroll
+    for (int q = 0; q < NX; ++q) {
+      TR v = TR(0);
+#pragma unroll
+      for (int t = 0; t < NX; ++t) v = fma(Pfl[r][t], Om[t * NX + q], v);
+      T1[r][q] = v;
     }
-    if (co) {
-      double* dst = co + fi * NN;
-      int uu = 0;
+  int u = 0;
 #pragma unroll
-      for (int r = 0; r < NX; ++r)
+  for (int r = 0; r < NX; ++r)
 #pragma unroll
-        for (int q = r; q < NX; ++q) {
-          const double v = (double)Pu[uu++];
-          dst[r * NX + q] = v;
-          dst[q * NX + r] = v;
-        }
+    for (int q = r; q < NX; ++q) {
+      TR v = Pf[u];
+#pragma unroll
+      for (int t = 0; t < NX; ++t) v = fma(T1[r][t], Pfl[q][t], v);
+      Pf[u++] = v;
     }
-    if (i == l) {
-      if (smo) {
 #pragma unroll
-        for (int r = 0; r < NX; ++r) smo[si * NX + r] = (double)mvv[r];
-      }
-      if (sco) {
-        double* dst = sco + si * NN;
-        int uu = 0;
+  for (int r = 0; r < NX; ++r) {
+    TR v = mf[r];
 #pragma unroll
-        for (int r = 0; r < NX; ++r)
-#pragma unroll
-          for (int q = r; q < NX; ++q) {
-            const double v = (double)Pu[uu++];
-            dst[r * NX + q] = v;
-            dst[q * NX + r] = v;
-          }
-      }
-    }
-  };
-  // filtered outputs (the call's outputs for a filter, the optional extras for a smoother)
-  if (!smooth) {
-    store_state(c.fast_mean, c.fast_cov, c.slow_mean, c.slow_cov, mf, Pf);
-    return;
+    for (int t = 0; t < NX; ++t) v = fma(Pfl[r][t], om[t], v);
+    mf[r] = v;
   }
-  store_state(c.ffast_mean, c.ffast_cov, c.fslow_mean, c.fslow_cov, mf, Pf);
-  if (smooth_k) {
-    const TR* Om = (const TR*)c.sfin + row * (NN + NX);
-    const TR* om = Om + NN;
-    TR T1[NX][NX];
+}
+
+// writes fast row f (mean, mirrored covariance) and, for i == l, slow row
+template <int NX, class TR>
+__device__ __forceinline__ void store_state(long long f, long long row, bool last_i, double* mo, double* co,
+                                            double* smo, double* sco, const TR* mv, const TR* Pu) {
+  constexpr int NN = NX * NX;
+  if (mo) {
 #pragma unroll
-    for (int r = 0; r < NX; ++r)
-#pragma unroll
-      for (int q = 0; q < NX; ++q) {
-        TR v = TR(0);
-#pragma unroll
-        for (int t = 0; t < NX; ++t) v = fma(Pfl[r][t], Om[t * NX + q], v);
-        T1[r][q] = v;
-      }
+    for (int r = 0; r < NX; ++r) mo[f * NX + r] = (double)mv[r];
+  }
+  if (co) {
+    double* dst = co + f * NN;
     int u = 0;
 #pragma unroll
     for (int r = 0; r < NX; ++r)
 #pragma unroll
       for (int q = r; q < NX; ++q) {
-        TR v = Pf[u];
-#pragma unroll
-        for (int t = 0; t < NX; ++t) v = fma(T1[r][t], Pfl[q][t], v);
-        Pf[u++] = v;
+        const double v = (double)Pu[u++];
+        dst[r * NX + q] = v;
+        dst[q * NX + r] = v;
       }
+  }
+  if (last_i) {
+    if (smo) {
 #pragma unroll
-    for (int r = 0; r < NX; ++r) {
-      TR v = mf[r];
+      for (int r = 0; r < NX; ++r) smo[row * NX + r] = (double)mv[r];
+    }
+    if (sco) {
+      double* dst = sco + row * NN;
+      int u = 0;
 #pragma unroll
-      for (int t = 0; t < NX; ++t) v = fma(Pfl[r][t], om[t], v);
-      mf[r] = v;
+      for (int r = 0; r < NX; ++r)
+#pragma unroll
+        for (int q = r; q < NX; ++q) {
+          const double v = (double)Pu[u++];
+          dst[r * NX + q] = v;
+          dst[q * NX + r] = v;
+        }
     }
   }
-  store_state(c.fast_mean, c.fast_cov, c.slow_mean, c.slow_cov, mf, Pf);
+}
+
+template <int NX, class TR>
+__global__ void __launch_bounds__(128, 3) recover_kernel(Ctx c) {
+  constexpr int NT = NX * (NX + 1) / 2;
+  if (!c.ctr->call_ok) return;
+  const long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (f >= c.total_fast) return;
+  const FastIdx x = fast_index(c, f);
+  const bool last_i = x.i == x.l;
+  const bool smooth_k = c.smoothing && (x.k < x.N - 1);
+  TR mf[NX], Pf[NT], Pfl[NX][NX];
+  recover_filtered<NX, TR>(c, x, smooth_k, mf, Pf, Pfl);
+  // filtered outputs (the call's outputs for a filter, the optional extras for a smoother)
+  if (!c.smoothing) {
+    store_state<NX, TR>(f, x.row, last_i, c.fast_mean, c.fast_cov, c.slow_mean, c.slow_cov, mf, Pf);
+    return;
+  }
+  store_state<NX, TR>(f, x.row, last_i, c.ffast_mean, c.ffast_cov, c.fslow_mean, c.fslow_cov, mf, Pf);
+  if (smooth_k) {
+    const TR* Om = (const TR*)c.sfin + x.row * SFin<NX>::SIZE;
+    recover_smooth<NX, TR>(Om + SFin<NX>::Om, Om + SFin<NX>::om, mf, Pf, Pfl);
+  }
+  store_state<NX, TR>(f, x.row, last_i, c.fast_mean, c.fast_cov, c.slow_mean, c.slow_cov, mf, Pf);
 }
 
 // ===========================================================================

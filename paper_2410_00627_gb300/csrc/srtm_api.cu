@@ -41,6 +41,7 @@ struct DevState {
   // placement of the scan tile-state regions used by the previous call
   size_t last_ftile = 0, last_ftile_bytes = 0, last_stile = 0, last_stile_bytes = 0;
   long long last_fstride = 0, last_sstride = 0;
+  int last_launches = 0;  // kernel launches of the last call
 };
 constexpr int MAXDEV = 64;
 std::mutex g_mu;
@@ -91,7 +92,9 @@ Layout make_layout(int nx, int ny, int max_ratio, int n_seq, long long total_slo
   const size_t sT = prec == SRTM_FP64 ? 8 : 4, sR = prec == SRTM_FP32 ? 4 : 8;
   const long long nn = (long long)nx * nx;
   const long long FE = 3 * nn + 2 * nx, SE = 2 * nn + nx;
-  const long long REC = 4 * nn + 2 * nx + 2LL * nx * MY + MY * MY + MY;
+  // record and smoothing-term strides, padded to 32 entries (Rec, SFin)
+  const long long REC = (4 * nn + 2 * nx + 2LL * nx * MY + MY * MY + MY + 31) / 32 * 32;
+  const long long SFN = (nn + nx + 31) / 32 * 32;
   L.ml = make_model_layout(nx, ny, max_ratio);
   // tile state: two flag words, aggregate, inclusive prefix, group aggregate
   L.ftile_stride = 16 + 3 * (long long)a16(FE * sT);
@@ -112,7 +115,7 @@ Layout make_layout(int nx, int ny, int max_ratio, int n_seq, long long total_slo
   L.fout = take(sR * (size_t)(nx + nn) * total_slow);
   L.rec = take(sR * (size_t)REC * total_slow);
   L.selem = take(sT * (size_t)SE * total_slow);
-  L.sfin = take(sR * (size_t)(nx + nn) * total_slow);
+  L.sfin = take(sR * (size_t)SFN * total_slow);
   L.total = a256(o);
   return L;
 }
@@ -243,6 +246,7 @@ int run(Ctx c, srtm_precision prec, cudaStream_t st) {
   c.sfin = w + L.sfin;
   c.tile_f = tile_f;
   c.tile_s = tile_s;
+  d.last_launches = (c.fold_meta ? 0 : 1) + 3 + (c.smoothing ? 1 : 0);
   cudaEvent_t* ev = nullptr;
   if (g_timing) {
     if (!d.ev[0])
@@ -614,6 +618,13 @@ int srtm_autotune_batch(const srtm_batch* b, srtm_precision prec, const srtm_out
 }
 
 int srtm_launches_per_call(int smoothing, int batched) { return (smoothing ? 4 : 3) + (batched ? 1 : 0); }
+
+int srtm_last_call_launches(void) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAXDEV) return 0;
+  std::lock_guard<std::mutex> lk(g_mu);
+  return g_dev[dev].last_launches;
+}
 
 int srtm_set_stage_timing(int enable) {
   std::lock_guard<std::mutex> lk(g_mu);

@@ -98,7 +98,15 @@ struct Rec {
   static constexpr int Z = SUl + MY * NX;     // A^T (P^-_{k+1,1})^-1 NN
   static constexpr int ml = Z + NN;           // m^f_{k,l}            NX
   static constexpr int Pm = ml + NX;          // P^-_{k+1,1}          NN
-  static constexpr int SIZE = Pm + NN;
+  // padded to 32 entries (256 B in float64): records start on cache-line
+  // boundaries and no cache sector holds parts of two of them
+  static constexpr int SIZE = (Pm + NN + 31) / 32 * 32;
+};
+
+// Per-interval smoothing terms (Om_k, om_k), padded like the record.
+template <int NX>
+struct SFin {
+  static constexpr int Om = 0, om = NX * NX, SIZE = (NX * NX + NX + 31) / 32 * 32;
 };
 
 // Filter element (F, d, D, eta, J) and smoother element (E, g, S) layouts.

@@ -70,6 +70,8 @@ def test_filter_call_matches_oracle(oracle_mod, precision):
     prob = synth.random_model(21, 4, 2, 6, 131)
     o = oracle_mod.sequential(prob, smooth=False)
     out = run_filter(prob, precision)
+    from paper_2410_00627_gb300 import api
+    assert api.last_call_launches() == 3   # constants, filter scan, recovery
     l = prob.ratio
     ref = {"fast_mean": o["fast_filt_mean"], "fast_cov": o["fast_filt_cov"],
            "slow_mean": o["slow_filt_mean"], "slow_cov": o["slow_filt_cov"]}
