@@ -142,7 +142,7 @@ int srtm_release(void);
 /* Tuning of the launch shapes (lane groups per scan block, elements per lane
  * group, recovery block size, look-back depth) for one (nx, precision).  Zero
  * values keep the built-in choice (128/lanes-per-group groups, 4 elements,
- * 128 threads, window 16).  Returns SRTM_ERR_ARG for out-of-range values.
+ * 128 threads, window 16, setup inside the filter scan).  Returns SRTM_ERR_ARG for out-of-range values.
  * The setting is process-wide and applies to the calls issued after it.     */
 typedef struct {
   int scan_groups;      /* lane groups per scan block: a power of two such that
@@ -152,6 +152,10 @@ typedef struct {
   int recover_threads;  /* recovery block size (32..128, multiple of 32)       */
   int lookback_window;  /* scan look-back depth: preceding tiles examined per
                            round of the decoupled look-back (1..32)            */
+  int setup_mode;       /* interval setup (smoother elements and recovery
+                           records): 1 = inside the filter scan, after each
+                           tile's results; 2 = its own kernel after the filter
+                           scan (one more launch)                            */
 } srtm_tuning;
 int srtm_set_tuning(int nx, srtm_precision prec, const srtm_tuning *t);
 int srtm_get_tuning(int nx, srtm_precision prec, srtm_tuning *t);
@@ -161,7 +165,8 @@ int srtm_get_tuning(int nx, srtm_precision prec, srtm_tuning *t);
  * sequence of candidate tunings and keeps the fastest for (p->nx, prec) as if
  * by srtm_set_tuning: first the grid of scan_groups (every valid power of
  * two) x scan_elems (1, 2, 4, 8, 16, 32), then lookback_window (4, 8, 16, 32)
- * and recover_threads (32, 64, 96, 128) one at a time from the best so far.
+ * recover_threads (32, 64, 96, 128) and setup_mode (1, 2) one at a time from
+ * the best so far.
  * Each candidate is run once untimed and then `reps` times (reps >= 1), timed
  * by CUDA events on `stream` around the call; its score is the fastest of
  * the reps.  Inputs and `smooth` are as for srtm_smoother (device buffers
@@ -180,7 +185,8 @@ int srtm_autotune_batch(const srtm_batch *b, srtm_precision prec, const srtm_out
  * also forms the per-interval smoother elements), smoother scan (smoother
  * calls only) and fast-rate recovery, plus the metadata kernel for batches. */
 int srtm_launches_per_call(int smoothing, int batched);
-/* Kernel launches of the last call issued on the current GPU (0 before any). */
+/* Kernel launches of the last call issued on the current GPU (0 before any);
+ * one more than srtm_launches_per_call when the setup runs as its own kernel. */
 int srtm_last_call_launches(void);
 
 /* Stage timing.  While enabled, every call records CUDA events on its stream

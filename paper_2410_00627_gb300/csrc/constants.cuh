@@ -263,6 +263,15 @@ __global__ void __launch_bounds__(PRE_THREADS) precompute_kernel(Ctx c, int tabl
   }
   __syncthreads();
   for (int e = tid; e < m * NX; e += nt) md[L.Cb + e] = sm[S::Cb + e];
+  {  // float copies of A, Qc_1, Cov(e_1, e_l), V_1 H^T for the float32 smoother elements
+    float* cf = (float*)(md + L.Cf);
+    for (int e = tid; e < NN; e += nt) {
+      cf[e] = (float)Ap[NN + e];
+      cf[NN + e] = (float)Qp[e];
+      cf[2 * NN + e] = (float)md[L.Ql + e];
+    }
+    for (int e = tid; e < NX * m; e += nt) cf[3 * NN + e] = (float)md[L.VH + e];
+  }
   // 7. slow-model constants and the first filter element
   const double* Al = Ap + (size_t)l * NN;
   const double* Qcl = Qp + (size_t)(l - 1) * NN;

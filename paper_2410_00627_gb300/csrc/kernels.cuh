@@ -33,8 +33,8 @@ struct SetupGeom {
   static constexpr int fP = 0, fPl = fP + NN, fX = fPl + NN, fSUl = fX + NM, fZ = fSUl + NM, fml = fZ + NN,
                        fmv = fml + NX, fU1 = fmv + NX, fP1l = fU1 + UA, fP11 = fP1l + NN, fAml = fP11 + NN,
                        SLOTF = fAml + NX;
-  // per-tile constants staged as float: A, Qc_1, Cov(e_1, e_l), V_1 H^T
-  static constexpr int cA = 0, cQc = NN, cQl = 2 * NN, cVH = 3 * NN, CONSTF = 3 * NN + NM;
+  // the model's float copies (model table, ModelLayout::Cf): A, Qc_1, Cov(e_1, e_l), V_1 H^T
+  static constexpr int cA = 0, cQc = NN, cQl = 2 * NN, cVH = 3 * NN;
   template <class T, class TR>
   __host__ __device__ static constexpr size_t slot_bytes() {
     return ((SLOT * sizeof(TR) + 15) / 16) * 16 + (sizeof(T) != sizeof(TR) ? ((SLOTF * sizeof(T) + 15) / 16) * 16 : 0);
@@ -171,11 +171,9 @@ __device__ __forceinline__ void setup_elements(int r, bool row, unsigned mask, i
 // its float region sf when the smoother elements are formed in float32).
 // prev (optional): p(x_{k-1,l}|y_{1:k-1}) as (m, P) when it is not yet in
 // the filter results (the first interval of a scan tile reads it from the
-// tile's exclusive prefix).  cf: the tile's model constants as float (used
-// when T is narrower than TR).
+// tile's exclusive prefix).
 template <int NX, class T, class TR>
-__device__ void setup_interval(const Ctx& c, long long gi, int lane, unsigned mask, TR* sb, T* sf, const TR* prev,
-                               const T* cf) {
+__device__ void setup_interval(const Ctx& c, long long gi, int lane, unsigned mask, TR* sb, T* sf, const TR* prev) {
   using Gm = SetupGeom<NX>;
   constexpr int NN = NX * NX;
   using RL = Rec<NX>;
@@ -469,6 +467,7 @@ __device__ void setup_interval(const Ctx& c, long long gi, int lane, unsigned ma
         for (int j = 0; j < MY; ++j) Sif[i][j] = (i < m && j < m) ? (T)Si[i][j] : T(0);
       }
       __syncwarp(mask);
+      const T* cf = (const T*)(md + c.ml.Cf);
       setup_elements<NX, T, T, T>(r, row, mask, m, last, sf + Gm::fP, sf + Gm::fPl, sf + Gm::fX, sf + Gm::fSUl,
                                   sf + Gm::fZ, sf + Gm::fml, sf + Gm::fmv, cf + Gm::cA, cf + Gm::cQc, cf + Gm::cQl,
                                   cf + Gm::cVH, Sif, kapf, sf + Gm::fU1, sf + Gm::fP1l, sf + Gm::fP11,
@@ -558,27 +557,15 @@ struct FilterOp {
   static constexpr bool FLOAT_ELEMENTS = sizeof(T) != sizeof(TS);
   __host__ __device__ static size_t epilogue_bytes(int threads, int tile) {
     using Gm = SetupGeom<NX>;
-    const size_t head = align16((NX + NX * NX) * sizeof(TS)) + (FLOAT_ELEMENTS ? align16(Gm::CONSTF * sizeof(T)) : 0);
-    return head + (size_t)epilogue_slots(threads, tile) * Gm::template slot_bytes<T, TS>();
+    return align16((NX + NX * NX) * sizeof(TS)) + (size_t)epilogue_slots(threads, tile) * Gm::template slot_bytes<T, TS>();
   }
   __device__ static void epilogue(const Ctx& c, int s, long long p0, int count, const T* excl, unsigned char* esm) {
     using Gm = SetupGeom<NX>;
     constexpr int SG = Gm::SG, NN = NX * NX;
     TS* prevb = (TS*)esm;
-    T* cf = (T*)(esm + align16((NX + NN) * sizeof(TS)));
-    unsigned char* slots =
-        esm + align16((NX + NN) * sizeof(TS)) + (FLOAT_ELEMENTS ? align16(Gm::CONSTF * sizeof(T)) : 0);
+    unsigned char* slots = esm + align16((NX + NN) * sizeof(TS));
     __syncthreads();
     for (int e = threadIdx.x; e < NX + NN; e += blockDim.x) prevb[e] = (TS)excl[L::d + e];
-    if (FLOAT_ELEMENTS) {  // the sequence's A, Qc_1, Cov(e_1,e_l), V_1 H^T as float, once per tile
-      const double* md = c.model + (long long)s * c.ml.stride;
-      for (int e = threadIdx.x; e < NN; e += blockDim.x) {
-        cf[Gm::cA + e] = (T)md[c.ml.Apow + NN + e];
-        cf[Gm::cQc + e] = (T)md[c.ml.Qc + e];
-        cf[Gm::cQl + e] = (T)md[c.ml.Ql + e];
-      }
-      for (int e = threadIdx.x; e < NX * c.ny; e += blockDim.x) cf[Gm::cVH + e] = (T)md[c.ml.VH + e];
-    }
     __syncthreads();
     const int lane = threadIdx.x % SG, slot = threadIdx.x / SG;
     const int per_round = epilogue_slots(blockDim.x, tile_elems(c));
@@ -589,7 +576,7 @@ struct FilterOp {
       TS* sb = (TS*)sl;
       T* sf = FLOAT_ELEMENTS ? (T*)(sl + align16(Gm::SLOT * sizeof(TS))) : nullptr;
       for (int j = slot; j < count; j += per_round)
-        setup_interval<NX, T, TS>(c, base_row + p0 + j, lane, mask, sb, sf, j == 0 ? prevb : nullptr, cf);
+        setup_interval<NX, T, TS>(c, base_row + p0 + j, lane, mask, sb, sf, j == 0 ? prevb : nullptr);
     }
     __syncthreads();
   }
@@ -688,8 +675,8 @@ struct ScanSmem {
   __host__ __device__ static size_t scan_part(int NG, int W) {
     return NG * group_bytes() + 2 * align16((size_t)NG * Op::ES * sizeof(T)) + window_bytes(W);
   }
-  __host__ __device__ static size_t bytes(int NG, int W, int E) {
-    const size_t sp = scan_part(NG, W), ep = Op::epilogue_bytes(NG * Op::G, NG * E);
+  __host__ __device__ static size_t bytes(int NG, int W, int E, bool epilogue = true) {
+    const size_t sp = scan_part(NG, W), ep = epilogue ? Op::epilogue_bytes(NG * Op::G, NG * E) : 0;
     return align16(Op::ES * sizeof(T)) + 32 + (sp > ep ? sp : ep);
   }
   __host__ __device__ static size_t payload_bytes() { return align16(Op::ES * sizeof(T)); }
@@ -975,7 +962,7 @@ __global__ void __launch_bounds__(256) scan_kernel(Ctx c, int NG, int E, int W) 
         g.sync();
       }
     }
-    if (Op::HAS_EPILOGUE) {
+    if (Op::HAS_EPILOGUE && !c.setup_separate) {
       const long long tp0 = t * tile_elems;
       Op::epilogue(c, s, tp0, (int)min((long long)tile_elems, (long long)N - tp0), excl, esm);
     }
@@ -1212,8 +1199,30 @@ __global__ void __launch_bounds__(128, 3) recover_kernel(Ctx c) {
 }
 
 // ===========================================================================
+// interval setup as its own kernel (after the filter scan): blocks of 128
+// threads, SG lanes per interval, one interval per lane group.
+// ===========================================================================
+template <int NX, class T, class TS>
+__global__ void __launch_bounds__(128) setup_kernel(Ctx c) {
+  using Gm = SetupGeom<NX>;
+  constexpr int SG = Gm::SG;
+  extern __shared__ __align__(16) unsigned char ssm[];
+  if (!c.ctr->call_ok) return;
+  const int lane = threadIdx.x % SG, slot = threadIdx.x / SG, per = blockDim.x / SG;
+  const long long gi = (long long)blockIdx.x * per + slot;
+  if (gi >= c.total_slow) return;  // the whole lane group leaves together
+  const unsigned mask = (SG == 32) ? 0xffffffffu : (((1u << SG) - 1u) << ((threadIdx.x & 31) & ~(SG - 1)));
+  unsigned char* sl = ssm + (size_t)slot * Gm::template slot_bytes<T, TS>();
+  T* sf = (sizeof(T) != sizeof(TS)) ? (T*)(sl + align16(Gm::SLOT * sizeof(TS))) : nullptr;
+  setup_interval<NX, T, TS>(c, gi, lane, mask, (TS*)sl, sf, nullptr);
+}
+
+// ===========================================================================
 // host-side launch of the templated stages
 // ===========================================================================
+template <class Op>
+struct SetupTag {};
+
 // Raises (never lowers) a kernel's dynamic shared-memory limit on the current
 // device: launches with other shapes may still need a larger limit.
 template <class Op>
@@ -1228,8 +1237,8 @@ inline void set_smem_attr(const void* fn, size_t bytes) {
 }
 
 template <int NX, class T, class TS, class TR>
-int query_shapes_t(int scan_groups, int scan_elems, int window, int recover_threads, int sm_count,
-                   long long total_slow, int n_seq, Shapes* sh) {
+int query_shapes_t(int scan_groups, int scan_elems, int window, int recover_threads, int setup_separate,
+                   int sm_count, long long total_slow, int n_seq, Shapes* sh) {
   using FOp = FilterOp<NX, T, TS>;
   using SOp = SmootherOp<NX, T, TR>;
   constexpr int G = FOp::G;
@@ -1239,7 +1248,7 @@ int query_shapes_t(int scan_groups, int scan_elems, int window, int recover_thre
   sh->scan_groups_f = sh->scan_groups_s = NG;
   sh->scan_elems_f = sh->scan_elems_s = scan_elems;
   sh->window_f = sh->window_s = window;
-  sh->smem_f = ScanSmem<FOp>::bytes(NG, window, scan_elems);
+  sh->smem_f = ScanSmem<FOp>::bytes(NG, window, scan_elems, !setup_separate);
   sh->smem_s = ScanSmem<SOp>::bytes(NG, window, scan_elems);
   set_smem_attr<FOp>((const void*)scan_kernel<FOp>, sh->smem_f);
   set_smem_attr<SOp>((const void*)scan_kernel<SOp>, sh->smem_s);
@@ -1251,8 +1260,9 @@ int query_shapes_t(int scan_groups, int scan_elems, int window, int recover_thre
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, scan_kernel<SOp>, threads, sh->smem_s);
   sh->blocks_per_sm_s = std::max(nb, 1);
   sh->grid_s = (int)std::max(1LL, std::min((long long)sh->blocks_per_sm_s * sm_count, tiles));
-  sh->grid_setup = 0;
-  sh->smem_setup = 0;
+  sh->grid_setup = (int)((total_slow + 128 / SetupGeom<NX>::SG - 1) / (128 / SetupGeom<NX>::SG));
+  sh->smem_setup = setup_separate ? (size_t)(128 / SetupGeom<NX>::SG) * SetupGeom<NX>::template slot_bytes<T, TS>() : 0;
+  if (setup_separate) set_smem_attr<SetupTag<FOp>>((const void*)setup_kernel<NX, T, TS>, sh->smem_setup);
   sh->recover_threads = recover_threads;
   if (cudaGetLastError() != cudaSuccess) return SRTM_ERR_CUDA;
   return SRTM_OK;
@@ -1260,17 +1270,17 @@ int query_shapes_t(int scan_groups, int scan_elems, int window, int recover_thre
 
 template <int NX>
 int query_shapes(srtm_precision prec, int scan_groups, int scan_elems, int window, int recover_threads,
-                 int sm_count, long long total_slow, int n_seq, Shapes* sh) {
+                 int setup_separate, int sm_count, long long total_slow, int n_seq, Shapes* sh) {
   switch (prec) {
     case SRTM_FP64:
       return query_shapes_t<NX, double, double, double>(scan_groups, scan_elems, window, recover_threads,
-                                                         sm_count, total_slow, n_seq, sh);
+                                                         setup_separate, sm_count, total_slow, n_seq, sh);
     case SRTM_MIXED:
       return query_shapes_t<NX, float, double, double>(scan_groups, scan_elems, window, recover_threads,
-                                                        sm_count, total_slow, n_seq, sh);
+                                                        setup_separate, sm_count, total_slow, n_seq, sh);
     case SRTM_FP32:
       return query_shapes_t<NX, float, float, float>(scan_groups, scan_elems, window, recover_threads,
-                                                      sm_count, total_slow, n_seq, sh);
+                                                      setup_separate, sm_count, total_slow, n_seq, sh);
   }
   return SRTM_ERR_ARG;
 }
@@ -1286,7 +1296,9 @@ int launch_t(const Ctx& c, const Shapes& sh, cudaStream_t st, cudaEvent_t* ev) {
   if (ev) cudaEventRecord(ev[0], st);
   scan_kernel<FOp><<<sh.grid_f, sh.scan_groups_f * G, sh.smem_f, st>>>(c, sh.scan_groups_f, sh.scan_elems_f, sh.window_f);
   if (ev) cudaEventRecord(ev[1], st);
-  if (ev) cudaEventRecord(ev[2], st);  // the interval setup runs inside the filter scan
+  if (c.setup_separate)
+    setup_kernel<NX, T, TS><<<sh.grid_setup, 128, sh.smem_setup, st>>>(c);
+  if (ev) cudaEventRecord(ev[2], st);  // otherwise the interval setup runs inside the filter scan
   if (c.smoothing)
     scan_kernel<SOp><<<sh.grid_s, sh.scan_groups_s * G, sh.smem_s, st>>>(c, sh.scan_groups_s, sh.scan_elems_s, sh.window_s);
   if (ev) cudaEventRecord(ev[3], st);
@@ -1311,4 +1323,4 @@ int launch_device_path(const Ctx& c, srtm_precision prec, const Shapes& sh, cuda
 #define SRTM_INSTANTIATE(NXV)                                                                                \
   template int srtm::launch_device_path<NXV>(const srtm::Ctx&, srtm_precision, const srtm::Shapes&,          \
                                              cudaStream_t, cudaEvent_t*);                                    \
-  template int srtm::query_shapes<NXV>(srtm_precision, int, int, int, int, int, long long, int, srtm::Shapes*);
+  template int srtm::query_shapes<NXV>(srtm_precision, int, int, int, int, int, int, long long, int, srtm::Shapes*);

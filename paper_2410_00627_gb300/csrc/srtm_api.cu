@@ -58,11 +58,13 @@ srtm_tuning effective_tuning(int nx, srtm_precision prec) {
   t.scan_elems = 4;
   t.recover_threads = 128;
   t.lookback_window = 16;
+  t.setup_mode = 1;
   const srtm_tuning& u = g_tune[nx][prec];
   if (u.scan_groups) t.scan_groups = u.scan_groups;
   if (u.scan_elems) t.scan_elems = u.scan_elems;
   if (u.recover_threads) t.recover_threads = u.recover_threads;
   if (u.lookback_window) t.lookback_window = u.lookback_window;
+  if (u.setup_mode) t.setup_mode = u.setup_mode;
   return t;
 }
 
@@ -124,9 +126,10 @@ Layout make_layout(int nx, int ny, int max_ratio, int n_seq, long long total_slo
 // also on the tile count.  The occupancy queries and attribute settings are
 // made once per key and device and cached (caller holds g_mu).
 struct ShapeKey {
-  int dev, nx, prec, sg, se, rt, w;
+  int dev, nx, prec, sg, se, rt, w, sm;
   bool operator==(const ShapeKey& o) const {
-    return dev == o.dev && nx == o.nx && prec == o.prec && sg == o.sg && se == o.se && rt == o.rt && w == o.w;
+    return dev == o.dev && nx == o.nx && prec == o.prec && sg == o.sg && se == o.se && rt == o.rt && w == o.w &&
+           sm == o.sm;
   }
 };
 constexpr int SHAPE_CACHE = 64;
@@ -141,7 +144,8 @@ int shapes_for(int nx, srtm_precision prec, const srtm_tuning& t, int sms, long 
                Shapes* sh) {
   int dev = 0;
   cudaGetDevice(&dev);
-  const ShapeKey key{dev, nx, (int)prec, t.scan_groups, t.scan_elems, t.recover_threads, t.lookback_window};
+  const ShapeKey key{dev, nx, (int)prec, t.scan_groups, t.scan_elems, t.recover_threads, t.lookback_window,
+                     t.setup_mode};
   int hit = -1;
   for (int i = 0; i < g_shape_n; ++i)
     if (g_shape_key[i] == key) { hit = i; break; }
@@ -158,6 +162,8 @@ int shapes_for(int nx, srtm_precision prec, const srtm_tuning& t, int sms, long 
   const long long tiles = total_slow / ((long long)sh->scan_groups_f * sh->scan_elems_f) + n_seq;
   sh->grid_f = (int)std::max(1LL, std::min((long long)sh->blocks_per_sm_f * sms, tiles));
   sh->grid_s = (int)std::max(1LL, std::min((long long)sh->blocks_per_sm_s * sms, tiles));
+  const int sg = nx == 1 ? 1 : (nx == 2 ? 2 : (nx <= 4 ? 4 : 8)), per = 128 / sg;  // lanes per setup interval
+  sh->grid_setup = (int)((total_slow + per - 1) / per);
   return SRTM_OK;
 }
 
@@ -165,8 +171,8 @@ int query_shapes_for(int nx, srtm_precision prec, const srtm_tuning& t, int sms,
                      Shapes* sh) {
 #define SRTM_Q(N) \
   case N:                                                                                               \
-    return query_shapes<N>(prec, t.scan_groups, t.scan_elems, t.lookback_window, t.recover_threads, sms, total_slow, \
-                           n_seq, sh);
+    return query_shapes<N>(prec, t.scan_groups, t.scan_elems, t.lookback_window, t.recover_threads,              \
+                           t.setup_mode == 2 ? 1 : 0, sms, total_slow, n_seq, sh);
   switch (nx) {
     SRTM_Q(1) SRTM_Q(2) SRTM_Q(3) SRTM_Q(4) SRTM_Q(5) SRTM_Q(6) SRTM_Q(7) SRTM_Q(8)
   }
@@ -246,7 +252,8 @@ int run(Ctx c, srtm_precision prec, cudaStream_t st) {
   c.sfin = w + L.sfin;
   c.tile_f = tile_f;
   c.tile_s = tile_s;
-  d.last_launches = (c.fold_meta ? 0 : 1) + 3 + (c.smoothing ? 1 : 0);
+  c.setup_separate = t.setup_mode == 2 ? 1 : 0;
+  d.last_launches = (c.fold_meta ? 0 : 1) + 3 + (c.smoothing ? 1 : 0) + c.setup_separate;
   cudaEvent_t* ev = nullptr;
   if (g_timing) {
     if (!d.ev[0])
@@ -490,6 +497,7 @@ int srtm_set_tuning(int nx, srtm_precision prec, const srtm_tuning* t) {
     return fail(SRTM_ERR_ARG, "recover_threads out of range");
   if (t->lookback_window && (t->lookback_window < 1 || t->lookback_window > 32))
     return fail(SRTM_ERR_ARG, "lookback_window out of range");
+  if (t->setup_mode < 0 || t->setup_mode > 2) return fail(SRTM_ERR_ARG, "setup_mode out of range");
   std::lock_guard<std::mutex> lk(g_mu);
   g_tune[nx][prec] = *t;
   return SRTM_OK;
@@ -579,6 +587,12 @@ int autotune_impl(int nx, srtm_precision prec, int reps, Call call, srtm_tuning*
     if (rc || th == cur.recover_threads) continue;
     srtm_tuning t = cur;
     t.recover_threads = th;
+    consider(t);
+  }
+  for (int md = 1; md <= 2; ++md) {  // interval setup in the filter scan / as its own kernel
+    if (rc || md == cur.setup_mode) continue;
+    srtm_tuning t = cur;
+    t.setup_mode = md;
     consider(t);
   }
   cudaEventDestroy(e0);
@@ -746,6 +760,7 @@ extern "C" int srtm_smoother_noalloc(const srtm_problem* p, srtm_precision prec,
     c.sfin = w + L.sfin;
     c.tile_f = tile_f;
     c.tile_s = tile_s;
+    c.setup_separate = t.setup_mode == 2 ? 1 : 0;
     rc = launch_meta(c, st, nullptr);
     if (rc) return fail(rc, "launch of the metadata kernel failed");
     rc = launch_for(c.nx, c, prec, sh, st, nullptr);

@@ -56,6 +56,7 @@ struct ModelLayout {
   long long m1;    // n           m^f_{1,l}
   long long P1;    // n^2         P^f_{1,l}
   long long Q;     // n^2         copy of Q
+  long long Cf;    // float copies of A, Qc_1, Cov(e_1,e_l) (n^2 each) and V_1 H^T (n x m, ld m)
   long long stride;
 };
 
@@ -79,6 +80,7 @@ __host__ __device__ inline ModelLayout make_model_layout(int n, int m, int L) {
   ml.m1 = o;   o += n;
   ml.P1 = o;   o += nn;
   ml.Q = o;    o += nn;
+  ml.Cf = o;   o += (3 * nn + (long long)n * MY + 1) / 2;
   ml.stride = (o + 31) / 32 * 32;
   return ml;
 }
@@ -150,6 +152,7 @@ struct Ctx {
   void* sfin;   // [total_slow][NN + NX]   per-interval smoothing terms Om_k, om_k (recovery type)
   // launch shapes
   int tile_f, tile_s;    // elements per scan tile
+  int setup_separate;    // 1: the interval setup runs as its own kernel after the filter scan
 };
 
 // ---------------------------------------------------------------------------
@@ -193,6 +196,6 @@ int launch_device_path(const Ctx& c, srtm_precision prec, const Shapes& sh, cuda
 
 template <int NX>
 int query_shapes(srtm_precision prec, int scan_groups, int scan_elems, int window, int recover_threads,
-                 int sm_count, long long total_slow, int n_seq, Shapes* sh);
+                 int setup_separate, int sm_count, long long total_slow, int n_seq, Shapes* sh);
 
 }  // namespace srtm

@@ -38,7 +38,7 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(api.Problem) == 16 + 7 * 8
     assert ctypes.sizeof(api.Output) == 4 * 8
     assert ctypes.sizeof(api.Batch) == 16 + 16 + 9 * 8
-    assert ctypes.sizeof(api.Tuning) == 16
+    assert ctypes.sizeof(api.Tuning) == 20
 
 
 def test_rejects_bad_arguments_without_gpu(lib):
@@ -55,16 +55,17 @@ def test_rejects_bad_arguments_without_gpu(lib):
 
 
 def test_tuning_validation_and_roundtrip(lib):
-    t = api.Tuning(0, 0, 0, 0)
+    t = api.Tuning(0, 0, 0, 0, 0)
     assert lib.srtm_get_tuning(4, 1, ctypes.byref(t)) == 0
     assert t.scan_groups * 16 == 128 and t.scan_elems >= 1 and t.recover_threads % 32 == 0
-    assert t.lookback_window == 16
+    assert t.lookback_window == 16 and t.setup_mode == 1
     assert lib.srtm_set_tuning(4, 1, ctypes.byref(api.Tuning(3, 0, 0))) == -1   # not a power of two
     assert lib.srtm_set_tuning(4, 1, ctypes.byref(api.Tuning(32, 0, 0))) == -1  # 32*16 lanes > 256
     assert lib.srtm_set_tuning(4, 1, ctypes.byref(api.Tuning(0, 0, 48))) == -1  # not a multiple of 32
     assert lib.srtm_set_tuning(4, 1, ctypes.byref(api.Tuning(0, 0, 256))) == -1  # above the block bound
     assert lib.srtm_set_tuning(4, 1, ctypes.byref(api.Tuning(0, 0, 0, 33))) == -1  # window above 32
     assert lib.srtm_set_tuning(4, 1, ctypes.byref(api.Tuning(0, 0, 0, -1))) == -1
+    assert lib.srtm_set_tuning(4, 1, ctypes.byref(api.Tuning(0, 0, 0, 0, 3))) == -1   # setup_mode
     assert lib.srtm_set_tuning(4, 1, ctypes.byref(api.Tuning(4, 8, 64, 8))) == 0
     assert lib.srtm_get_tuning(4, 1, ctypes.byref(t)) == 0
     assert (t.scan_groups, t.scan_elems, t.recover_threads, t.lookback_window) == (4, 8, 64, 8)

@@ -236,15 +236,15 @@ def test_stage_timing_reports_every_stage():
     assert all(v > 0 for v in t.values())
 
 
-SHAPES = [  # (scan_groups, scan_elems, recover_threads, lookback_window) for nx=4 (16 lanes per group)
-    (2, 1, 32, 1),     # smallest tiles, serial look-back
-    (16, 32, 128, 32),  # largest tiles and window
-    (8, 4, 64, 4),
-    (4, 2, 96, 2),
+SHAPES = [  # (scan_groups, scan_elems, recover_threads, lookback_window, setup_mode), nx=4 (16 lanes per group)
+    (2, 1, 32, 1, 1),      # smallest tiles, serial look-back
+    (16, 32, 128, 32, 2),  # largest tiles and window, setup as its own kernel
+    (8, 4, 64, 4, 2),
+    (4, 2, 96, 2, 1),
 ]
 
 
-@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "g{}e{}t{}w{}".format(*s))
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "g{}e{}t{}w{}s{}".format(*s))
 def test_launch_shapes_do_not_change_results(oracle_mod, shape):
     from paper_2410_00627_gb300 import api
     prob = synth.config2(seed=5, n_slow=613, keep_states=False)
@@ -271,6 +271,7 @@ def test_autotune_keeps_a_valid_tuning_and_results_still_match(oracle_mod):
         assert tuned == api.get_tuning(4, "mixed")
         assert tuned["scan_groups"] in (2, 4, 8, 16) and 1 <= tuned["scan_elems"] <= 32
         assert tuned["recover_threads"] in (32, 64, 96, 128) and tuned["lookback_window"] in (4, 8, 16, 32)
+        assert tuned["setup_mode"] in (1, 2)
         ref_sm, ref_fi = oracle_views(oracle_mod.sequential(prob), prob.ratio)
         sm, fi = run_smoother(prob, "mixed")
         tm, tc = TOL["mixed"]
