@@ -66,6 +66,8 @@ def parse(argv=None):
                     help="explicit launch shapes scan_groups,scan_elems,recover_threads,lookback_window "
                          "(for every precision; replaces the autotuner)")
     ap.add_argument("--tune-reps", type=int, default=2)
+    ap.add_argument("--report-errors", action="store_true",
+                    help="max relative errors of every mode against the FP64 oracle, configs 1, 2, 3, 5 at full size")
     return ap.parse_args(argv)
 
 
@@ -547,6 +549,66 @@ def run_cpu_baseline(args, prob):
                       f"{prob.n_slow * prob.ratio} fast steps) in {el:.1f} s, 1 thread, FP64 C (-O2)"}
 
 
+# --------------------------------------------------------------------------- error report
+REPORT_SIZES = {1: 100, 2: 10_000, 3: 100_000, 5: 10_000}
+
+
+def rel_err(a, b):
+    return float(np.max(np.abs(a - b)) / max(float(np.max(np.abs(b))), 1e-300))
+
+
+def report_errors(cfg, precisions=("fp64", "mixed", "fp32"), n_slow=None, seed=0):
+    """Max relative errors (max |x - x_oracle| / max |x_oracle|) of the smoothed
+    and filtered outputs of each precision mode against the FP64 oracle, for
+    config `cfg` at full size: every slow-rate output and the fast-rate
+    outputs of the first and last three intervals."""
+    import torch
+
+    import oracle
+    from paper_2410_00627_gb300 import api, build, synth
+    build.build()
+    api.load()
+    oracle.build()
+    N = REPORT_SIZES[cfg] if n_slow is None else n_slow
+    prob = synth.CONFIGS[cfg](seed=seed, n_slow=N, keep_states=False)
+    l = prob.ratio
+    w = min(3, N)
+    head = oracle.sequential(prob, k_lo=0, k_hi=w)
+    tail = oracle.sequential(prob, k_lo=N - w, k_hi=N, slow=False, smooth=True)
+    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")  # noqa: E731
+    ins = [dev(getattr(prob, k)) for k in ("F", "Q", "H", "R", "m0", "P0", "y")]
+    res = {}
+    for prec in precisions:
+        try:
+            sm, fi = api.smoother(*ins, l, precision=prec, filtered=api.OUTPUT_KEYS)
+            api.status()
+        except api.SRTMError as err:   # reported, e.g. a singular solve in the float32 mode
+            res[prec] = {"error": str(err)}
+            continue
+        sm = {k: v.cpu().numpy() for k, v in sm.items()}
+        fi = {k: v.cpu().numpy() for k, v in fi.items()}
+        e = {}
+        for name, got, ref in (
+                ("smoothed fast mean", np.concatenate([sm["fast_mean"][:w * l], sm["fast_mean"][-w * l:]]),
+                 np.concatenate([head["fast_smooth_mean"], tail["fast_smooth_mean"]])),
+                ("smoothed fast cov", np.concatenate([sm["fast_cov"][:w * l], sm["fast_cov"][-w * l:]]),
+                 np.concatenate([head["fast_smooth_cov"], tail["fast_smooth_cov"]])),
+                ("smoothed first-state mean (all k)", sm["fast_mean"][0::l], head["first_smooth_mean"]),
+                ("smoothed first-state cov (all k)", sm["fast_cov"][0::l], head["first_smooth_cov"]),
+                ("filtered fast mean", np.concatenate([fi["fast_mean"][:w * l], fi["fast_mean"][-w * l:]]),
+                 np.concatenate([head["fast_filt_mean"], tail["fast_filt_mean"]])),
+                ("filtered fast cov", np.concatenate([fi["fast_cov"][:w * l], fi["fast_cov"][-w * l:]]),
+                 np.concatenate([head["fast_filt_cov"], tail["fast_filt_cov"]])),
+                ("filtered slow mean (all k)", fi["slow_mean"], head["slow_filt_mean"]),
+                ("filtered slow cov (all k)", fi["slow_cov"], head["slow_filt_cov"])):
+            e[name] = rel_err(got, ref)
+        res[prec] = e
+        del sm, fi
+        torch.cuda.empty_cache()
+    return {"config": cfg, "nx": prob.nx, "ny": prob.ny, "ratio": l, "n_slow": N, "n_fast": N * l,
+            "errors": res}
+
+
 def run_reference(args):
     """Reference arm: the FP64 CPU oracle on the host cores, same workload
     (config 4: the first sequences of the batch, about --cpu-seconds of work
@@ -597,6 +659,10 @@ def main():
     if args.impl == "reference":
         if rank == 0:
             print(json.dumps(run_reference(args)), flush=True)
+        return
+    if args.report_errors:
+        for cfg in (1, 2, 3, 5):
+            print(json.dumps(report_errors(cfg)), flush=True)
         return
     import torch
     dist = None
