@@ -66,6 +66,8 @@ def parse(argv=None):
                     help="explicit launch shapes scan_groups,scan_elems,recover_threads,lookback_window "
                          "(for every precision; replaces the autotuner)")
     ap.add_argument("--tune-reps", type=int, default=2)
+    ap.add_argument("--sweep", action="store_true",
+                    help="config 2 over T = 10^2 .. 10^4 slow steps (x sqrt 10), FP64 and mixed, one JSON line each")
     ap.add_argument("--report-errors", action="store_true",
                     help="max relative errors of every mode against the FP64 oracle, configs 1, 2, 3, 5 at full size")
     return ap.parse_args(argv)
@@ -157,8 +159,40 @@ def run_ours(args, rank, world, dist):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
-    def step(precision):
-        api.smoother(*ins, prob.ratio, precision=precision, out=outs)
+    def step(precision, st=None):
+        api.smoother(*ins, prob.ratio, precision=precision, out=outs, stream=st)
+
+    def timed_graph(precision, steps, warmup):
+        """The call captured in a CUDA graph and replayed: flush L2, then the
+        replay between two events, every step on one side stream."""
+        side = torch.cuda.Stream()
+        with torch.cuda.stream(side):
+            for _ in range(warmup):
+                step(precision, side)
+            api.status(side)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=side, capture_error_mode="relaxed"):
+            step(precision, side)
+        launches = api.last_call_launches()
+        ms = []
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        with torch.cuda.stream(side):   # replay() launches on the current stream
+            for _ in range(steps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(side)
+                g.replay()
+                e1.record(side)
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        api.status(side)
+        del g
+        return ms, launches
 
     def timed(precision, steps, warmup, stage=False):
         for _ in range(warmup):
@@ -200,8 +234,10 @@ def run_ours(args, rank, world, dist):
     clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
     if clocks:
         clocks.start()
-    ms, stages = timed(args.precision, args.steps, args.warmup, stage=True)
+    ms, launches = timed_graph(args.precision, args.steps, args.warmup)
     clock_info = clocks.stop() if clocks else None
+    parity = check_parity(prob, outs, args.precision) if rank == 0 else None
+    ms_direct, stages = timed(args.precision, max(5, args.steps // 2), 2, stage=True)
     mean_ms, units = reduce_over_ranks(float(np.mean(ms)), n_fast, dist, dev)
     value = units / (mean_ms * 1e-3)
     if rank != 0:
@@ -219,20 +255,26 @@ def run_ours(args, rank, world, dist):
         "vs_baseline": None, "dtype": {"mixed": "f32+f64", "fp64": "f64", "fp32": "f32"}[args.precision],
         "data": "synthetic (seeded generator, config 2 linear kinetics)",
         "config": dict(config_dict(args, prob, args.precision),
-                       tuning=tuning.get(args.precision, api.get_tuning(prob.nx, args.precision))),
+                       tuning=tuning.get(args.precision, api.get_tuning(prob.nx, args.precision)),
+                       timing="CUDA-graph replay of the call, CUDA events on its stream, mean of the steps"),
+        "ms_per_step_median": float(np.median(ms)),
+        "parity": parity,
+        "direct_calls": {"ms_per_step": float(np.mean(ms_direct)),
+                         "note": "the same call issued through the C-ABI each step (host launch cost included)"},
         "stage_ms": stage_mean,
         "roofline": {"bound": "alu", "kernel": "recover_kernel", "achieved": achieved,
                      "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": achieved / FP64_PEAK_GFLOPS,
                      "peak_source": "GB300 FP64 nominal 1.25 TFLOP/s (recipe table)",
                      "flops_per_fast_step": 2 * fma_per_fast, "traffic": traffic},
-        "gpu_launches": args.steps * api.last_call_launches(),
+        "gpu_launches": args.steps * launches,
         "clocks": clock_info,
     }
     if not args.no_extras:
         other = "fp64" if args.precision != "fp64" else "mixed"
-        ms2, _ = timed(other, max(5, args.steps // 2), 3)
+        ms2, _ = timed_graph(other, max(5, args.steps // 2), 3)
         line[other] = {"value": n_fast / (float(np.mean(ms2)) * 1e-3), "ms_per_step": float(np.mean(ms2)),
-                       "tuning": tuning.get(other, api.get_tuning(prob.nx, other))}
+                       "tuning": tuning.get(other, api.get_tuning(prob.nx, other)),
+                       "parity": check_parity(prob, outs, other)}
         line["e2e"] = run_e2e(args, prob, api, torch, flush)
         line["cpu_baseline"] = run_cpu_baseline(args, prob)
     return line
@@ -337,6 +379,7 @@ def run_batched(args, rank, world, dist):
     ms = timed_graph(g, args.steps)
     clock_info = clocks.stop() if clocks else None
     del g
+    parity = check_parity_batch(probs, pk, outs, args.precision) if rank == 0 else None
     mean_ms, units = reduce_over_ranks(float(np.mean(ms)), n_fast, dist, dev)
     value = units / (mean_ms * 1e-3)
     # per-launch durations of one ungraphed call (library stage events)
@@ -360,6 +403,7 @@ def run_batched(args, rank, world, dist):
         "data": "synthetic (seeded generator, config 4 ragged linear-kinetics batch)",
         "config": batched_config(args, pk, args.precision, tuning.get(args.precision,
                                                                        api.get_tuning(nx, args.precision))),
+        "parity": parity,
         "stage_ms": stage,
         "roofline": {"bound": "alu", "kernel": "recover_kernel", "achieved": achieved,
                      "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": achieved / FP64_PEAK_GFLOPS,
@@ -380,6 +424,26 @@ def run_batched(args, rank, world, dist):
         line["e2e"] = run_batched_e2e(args, pk, batch, ten, outs, api, torch, stream)
         line["cpu_baseline"] = run_cpu_baseline_batched(args, probs)
     return line
+
+
+def check_parity_batch(probs, pk, outs, precision):
+    """Sampled sequences of the timed batched call (the shortest, the first,
+    the last) against the FP64 oracle, every output of each."""
+    import oracle
+    oracle.build()
+    tol = {"fp64": (1e-9, 1e-8), "mixed": (1e-4, 1e-3), "fp32": (1e-4, 1e-3)}[precision]
+    n = pk["n_slow"].astype(np.int64)
+    off_f = np.concatenate([[0], np.cumsum(n * pk["ratio"])])
+    pick = sorted({int(np.argmin(n)), 0, len(probs) - 1})
+    e_mean = e_cov = 0.0
+    for s_ in pick:
+        o = oracle.sequential(probs[s_], slow=False)
+        sl = slice(int(off_f[s_]), int(off_f[s_ + 1]))
+        e_mean = max(e_mean, rel_err(outs["fast_mean"][sl].cpu().numpy(), o["fast_smooth_mean"]))
+        e_cov = max(e_cov, rel_err(outs["fast_cov"][sl].cpu().numpy(), o["fast_smooth_cov"]))
+    return {"max_rel_err_mean": e_mean, "max_rel_err_cov": e_cov, "tol": list(tol),
+            "ok": bool(e_mean <= tol[0] and e_cov <= tol[1]),
+            "checked": f"every fast output of sequences {pick}"}
 
 
 def run_single_loop(probs, pk, ten, outs, api, torch, stream):
@@ -549,6 +613,39 @@ def run_cpu_baseline(args, prob):
                       f"{prob.n_slow * prob.ratio} fast steps) in {el:.1f} s, 1 thread, FP64 C (-O2)"}
 
 
+# --------------------------------------------------------------------------- parity of the timed outputs
+def check_parity(prob, outs, precision, w=3):
+    """The timed call's smoothed outputs against the FP64 oracle: every output
+    when the workload has at most 2*10^6 fast steps, else every x_{k,1} and the
+    fast outputs of the first and last w intervals.  The slow outputs must be
+    the i = l fast rows exactly.  The bench line counts only within tolerance."""
+    import oracle
+    oracle.build()
+    tol = {"fp64": (1e-9, 1e-8), "mixed": (1e-4, 1e-3), "fp32": (1e-4, 1e-3)}[precision]
+    N, l = prob.n_slow, prob.ratio
+    fm, fc = outs["fast_mean"].cpu().numpy(), outs["fast_cov"].cpu().numpy()
+    sm, sc = outs["slow_mean"].cpu().numpy(), outs["slow_cov"].cpu().numpy()
+    if N * l <= 2_000_000:
+        o = oracle.sequential(prob, slow=False)
+        e_mean, e_cov = rel_err(fm, o["fast_smooth_mean"]), rel_err(fc, o["fast_smooth_cov"])
+        checked = f"every fast output ({N * l} fast steps)"
+    else:
+        w = min(w, N)
+        head = oracle.sequential(prob, k_lo=0, k_hi=w, slow=False)
+        tail = oracle.sequential(prob, k_lo=N - w, k_hi=N, slow=False)
+        e_mean = max(rel_err(np.concatenate([fm[:w * l], fm[-w * l:]]),
+                             np.concatenate([head["fast_smooth_mean"], tail["fast_smooth_mean"]])),
+                     rel_err(fm[0::l], head["first_smooth_mean"]))
+        e_cov = max(rel_err(np.concatenate([fc[:w * l], fc[-w * l:]]),
+                            np.concatenate([head["fast_smooth_cov"], tail["fast_smooth_cov"]])),
+                    rel_err(fc[0::l], head["first_smooth_cov"]))
+        checked = f"x_(k,1) of all {N} intervals and every fast output of the first and last {w}"
+    slow_views = bool(np.array_equal(sm, fm[l - 1::l]) and np.array_equal(sc, fc[l - 1::l]))
+    return {"max_rel_err_mean": e_mean, "max_rel_err_cov": e_cov, "tol": list(tol),
+            "ok": bool(e_mean <= tol[0] and e_cov <= tol[1] and slow_views), "checked": checked,
+            "slow_outputs_are_the_i_l_rows": slow_views}
+
+
 # --------------------------------------------------------------------------- error report
 REPORT_SIZES = {1: 100, 2: 10_000, 3: 100_000, 5: 10_000}
 
@@ -663,6 +760,18 @@ def main():
     if args.report_errors:
         for cfg in (1, 2, 3, 5):
             print(json.dumps(report_errors(cfg)), flush=True)
+        return
+    if args.sweep:
+        import copy
+        for n_slow in (100, 316, 1000, 3162, 10000):
+            for prec in ("fp64", "mixed"):
+                a = copy.copy(args)
+                a.n_slow, a.precision, a.no_extras = n_slow, prec, True
+                ln = run_ours(a, 0, 1, None)
+                print(json.dumps({"sweep": "config 2", "n_slow": n_slow, "fast_steps": n_slow * 20, "precision": prec,
+                                  "value": ln["value"], "unit": UNIT, "ms_per_step": ln["ms_per_step"],
+                                  "us_per_call": ln["ms_per_step"] * 1e3, "parity_ok": ln["parity"]["ok"],
+                                  "tuning": ln["config"]["tuning"]}), flush=True)
         return
     import torch
     dist = None
