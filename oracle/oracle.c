@@ -215,8 +215,34 @@ static void model_build(model_t *M, int n, int m, int l, const double *A,
 /* ------------------------------------------------------------------------ */
 
 /* One IMKF step from (mp,Pp) = p(x_{k-1,l}|y_{1:k-1}) with measurement yk. */
+/* log|det S| of a symmetric positive definite S (m x m) by the Cholesky
+ * factor S = G G^T: 2 sum_j log G_jj.  Returns -1 if S is not positive definite. */
+static int logdet_spd(int m, const double *S, double *out) {
+  double *G = dalloc((size_t)m * m);
+  int rc = 0;
+  double acc = 0.0;
+  for (int j = 0; j < m && !rc; ++j) {
+    double d = S[j * m + j];
+    for (int k = 0; k < j; ++k) d -= G[j * m + k] * G[j * m + k];
+    if (!(d > 0.0)) { rc = -1; break; }
+    G[j * m + j] = sqrt(d);
+    acc += log(G[j * m + j]);
+    for (int i = j + 1; i < m; ++i) {
+      double v = S[i * m + j];
+      for (int k = 0; k < j; ++k) v -= G[i * m + k] * G[j * m + k];
+      G[i * m + j] = v / G[j * m + j];
+    }
+  }
+  *out = 2.0 * acc;
+  free(G);
+  return rc;
+}
+
+/* One step of the slow-rate IMKF, Eq. (9)-(12).  term (optional): the
+ * measurement's log predictive density log N(y_k; C_bar m_{k-1}, S_k), the
+ * k-th term of the prediction-error decomposition of log p(y_{1:N}). */
 static int imkf_step(const model_t *M, const double *R, const double *mp, const double *Pp,
-                     const double *yk, double *mf, double *Pf) {
+                     const double *yk, double *mf, double *Pf, double *term) {
   int n = M->n, m = M->m, rc = 0;
   double *mminus = dalloc(n), *Pminus = dalloc((size_t)n * n), *AP = dalloc((size_t)n * n);
   double *cross = dalloc((size_t)n * m), *S = dalloc((size_t)m * m), *CP = dalloc((size_t)m * n);
@@ -234,6 +260,14 @@ static int imkf_step(const model_t *M, const double *R, const double *mp, const 
   if (right_solve(m, S, n, cross, L)) rc = -1;                       /* L_k                */
   gemm(m, n, 1, -1.0, M->Cbar, 0, mp, 0, 0.0, innov);
   axpy(m, 1.0, yk, innov);                                           /* y - C_bar m        */
+  if (term) {  /* -1/2 (m log 2 pi + log det S + innov^T S^-1 innov) */
+    double *z = dalloc(m), ld = 0.0, q = 0.0;
+    copy(m, innov, z);
+    if (solve(m, S, 1, z) || logdet_spd(m, S, &ld)) rc = -1;
+    for (int j = 0; j < m; ++j) q += innov[j] * z[j];
+    *term = -0.5 * (m * log(2.0 * 3.14159265358979323846) + ld + q);
+    free(z);
+  }
   copy(n, mminus, mf);
   gemm(n, m, 1, 1.0, L, 0, innov, 0, 1.0, mf);
   copy(n * n, Pminus, Pf);
@@ -375,7 +409,7 @@ int oracle_srtm_sequential(int n, int m, int l, int N, const double *A, const do
   for (int k = 0; k < N; ++k) {
     const double *mp = k ? mfl + (size_t)(k - 1) * n : m0;
     const double *Pp = k ? Pfl + (size_t)(k - 1) * nn : P0;
-    if (imkf_step(&M, R, mp, Pp, y + (size_t)k * m, mfl + (size_t)k * n, Pfl + (size_t)k * nn)) rc = -1;
+    if (imkf_step(&M, R, mp, Pp, y + (size_t)k * m, mfl + (size_t)k * n, Pfl + (size_t)k * nn, NULL)) rc = -1;
   }
   if (slow_filt_mean) copy(N * n, mfl, slow_filt_mean);
   if (slow_filt_cov) copy(N * nn, Pfl, slow_filt_cov);
@@ -559,7 +593,7 @@ int oracle_srtm_parallel(int n, int m, int l, int N, const double *A, const doub
     double *a = fe + (size_t)k * fs;
     const double *yk = y + (size_t)k * m;
     if (k == 0) {   /* F_1 = 0, d_1 = m^f_{1,l}, D_1 = P^f_{1,l}, eta_1 = 0, J_1 = 0 */
-      if (imkf_step(&M, R, m0, P0, yk, a + nn, a + nn + n)) rc = -1;
+      if (imkf_step(&M, R, m0, P0, yk, a + nn, a + nn + n, NULL)) rc = -1;
     } else {
       copy(nn, F, a);
       gemm(n, m, 1, 1.0, K, 0, yk, 0, 0.0, a + nn);
@@ -629,4 +663,32 @@ int oracle_lifted(int n, int m, int l, const double *A, const double *Q, const d
   copy(m * m, M.MQM, MQM); copy(n * m, M.GQM, GQM);
   model_free(&M);
   return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* log p(y_{1:N}) by the prediction-error decomposition of the slow-rate     */
+/* IMKF (Eq. 9-12): sum_k log N(y_k; C_bar m^f_{k-1,l}, S_k), with           */
+/* S_k = C_bar P^f_{k-1,l} C_bar^T + M Q~ M^T + R.  terms (optional, N       */
+/* values) receives the per-interval terms.                                  */
+/* ------------------------------------------------------------------------ */
+int oracle_loglik(int n, int m, int l, int N, const double *A, const double *Q, const double *H,
+                  const double *R, const double *m0, const double *P0, const double *y, double *terms,
+                  double *total) {
+  if (n < 1 || m < 1 || l < 1 || N < 1 || !total) return -2;
+  model_t M;
+  model_build(&M, n, m, l, A, Q, H);
+  int rc = 0, nn = n * n;
+  double *mf = dalloc((size_t)N * n), *Pf = dalloc((size_t)N * nn), acc = 0.0;
+  for (int k = 0; k < N; ++k) {
+    const double *mp = k ? mf + (size_t)(k - 1) * n : m0;
+    const double *Pp = k ? Pf + (size_t)(k - 1) * nn : P0;
+    double t = 0.0;
+    if (imkf_step(&M, R, mp, Pp, y + (size_t)k * m, mf + (size_t)k * n, Pf + (size_t)k * nn, &t)) rc = -1;
+    if (terms) terms[k] = t;
+    acc += t;
+  }
+  *total = acc;
+  model_free(&M);
+  free(mf); free(Pf);
+  return rc;
 }

@@ -44,8 +44,9 @@ def _load():
         lib.oracle_filter_op.argtypes = [i, _dp, _dp, _dp]
         lib.oracle_smoother_op.argtypes = [i, _dp, _dp, _dp]
         lib.oracle_lifted.argtypes = [i, i, i] + [_dp] * 8
+        lib.oracle_loglik.argtypes = [i, i, i, i] + [_dp] * 9
         for f in (lib.oracle_srtm_sequential, lib.oracle_srtm_parallel, lib.oracle_filter_op,
-                  lib.oracle_smoother_op, lib.oracle_lifted):
+                  lib.oracle_smoother_op, lib.oracle_lifted, lib.oracle_loglik):
             f.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -158,3 +159,16 @@ def lifted(F, Q, H, ratio: int) -> dict:
     lib.oracle_lifted(n, m, int(ratio), _p(Fc), _p(Qc), _p(Hc),
                       *[_p(out[k]) for k in ["Abar", "Qbar", "Cbar", "MQM", "GQM"]])
     return out
+
+
+def loglik(prob, terms: bool = False):
+    """log p(y_{1:N}) by the prediction-error decomposition of the slow-rate
+    IMKF (Eq. 9-12); with terms=True also the N per-interval terms."""
+    lib = _load()
+    n, m, l, N = prob.F.shape[0], prob.H.shape[0], int(prob.ratio), prob.y.shape[0]
+    t = np.zeros(N) if terms else None
+    total = np.zeros(1)
+    rc = lib.oracle_loglik(n, m, l, N, *[_p(a) for a in _inputs(prob)], _p(t), _p(total))
+    if rc != 0:
+        raise RuntimeError(f"oracle_loglik failed rc={rc}")
+    return (float(total[0]), t) if terms else float(total[0])

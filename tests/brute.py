@@ -72,3 +72,17 @@ def posteriors(prob):
         fsm[t - 1] = ms[t * n:(t + 1) * n]
         fsc[t - 1] = Ss[t * n:(t + 1) * n, t * n:(t + 1) * n]
     return {"fast_filt_mean": ffm, "fast_filt_cov": ffc, "fast_smooth_mean": fsm, "fast_smooth_cov": fsc}
+
+
+def loglik(prob):
+    """log p(y_{1:N}) of the stacked measurements under the dense joint prior:
+    y = Hz z + v, so y ~ N(Hz mu, Hz S Hz^T + I_N (x) R)."""
+    F, Q, H, R, m0, P0, y, l = prob.F, prob.Q, prob.H, prob.R, prob.m0, prob.P0, prob.y, prob.ratio
+    n, N, m = F.shape[0], y.shape[0], H.shape[0]
+    mu, S = joint_prior(F, Q, m0, P0, N * l)
+    Hz = meas_matrix(H, n, l, N)
+    Sy = Hz @ S @ Hz.T + np.kron(np.eye(N), R)
+    r = y.ravel() - Hz @ mu
+    sign, logdet = np.linalg.slogdet(Sy)
+    assert sign > 0
+    return float(-0.5 * (N * m * np.log(2 * np.pi) + logdet + r @ np.linalg.solve(Sy, r)))

@@ -242,3 +242,42 @@ def test_sampled_fast_range_matches_full(oracle_mod):
     l = prob.ratio
     for k in ["fast_filt_mean", "fast_filt_cov", "fast_smooth_mean", "fast_smooth_cov"]:
         assert np.array_equal(part[k], full[k][10 * l:13 * l]), k
+
+
+# --------------------------------------------------------------------------- log marginal likelihood
+@pytest.mark.parametrize("kw", TINY, ids=lambda k: "n{nx}m{ny}l{ratio}N{n_slow}".format(**k))
+def test_loglik_matches_dense_joint_density(oracle_mod, kw):
+    """log p(y_{1:N}) from the IMKF's prediction-error decomposition equals the
+    log density of the stacked measurements under the dense joint prior."""
+    prob = synth.random_model(kw["seed"], kw["nx"], kw["ny"], kw["ratio"], kw["n_slow"])
+    total, terms = oracle_mod.loglik(prob, terms=True)
+    ref = brute.loglik(prob)
+    assert abs(total - ref) <= 1e-10 * max(1.0, abs(ref))
+    assert np.isclose(terms.sum(), total, rtol=0, atol=1e-12 * max(1.0, abs(total)))
+
+
+def test_loglik_first_term_is_the_prior_predictive(oracle_mod):
+    """The k = 1 term is log N(y_1; C_bar m0, C_bar P0 C_bar^T + M Q~ M^T + R): with
+    n = m = 1 every piece is a scalar written out by hand."""
+    prob = synth.random_model(31, 1, 1, 3, 2)
+    a, q, h, r = prob.F[0, 0], prob.Q[0, 0], prob.H[0, 0], prob.R[0, 0]
+    l = prob.ratio
+    # y_1 = h (x_1 + x_2 + x_3) + v with x_i = a^i x_0 + sum_{s<i} a^{i-1-s} w_s
+    c = h * sum(a ** i for i in range(1, l + 1))
+    var_w = q * h * h * sum(sum(a ** (i - 1 - s) for i in range(s + 1, l + 1)) ** 2 for s in range(l))
+    mean = c * prob.m0[0]
+    var = c * c * prob.P0[0, 0] + var_w + r
+    want = -0.5 * (np.log(2 * np.pi * var) + (prob.y[0, 0] - mean) ** 2 / var)
+    _, terms = oracle_mod.loglik(prob, terms=True)
+    assert abs(terms[0] - want) <= 1e-12 * max(1.0, abs(want))
+
+
+def test_planted_loglik_mistake_fails_the_dense_pin(oracle_mod):
+    """A total that drops the normalising constant -N m log(2 pi) / 2 (a
+    plausible slip) is rejected by the dense pin that the oracle passes."""
+    prob = synth.random_model(3, 3, 2, 4, 5)
+    total, terms = oracle_mod.loglik(prob, terms=True)
+    ref = brute.loglik(prob)
+    assert abs(total - ref) < 1e-10 * abs(ref)
+    N, m = prob.y.shape
+    assert abs((total + 0.5 * N * m * np.log(2 * np.pi)) - ref) > 1e-3 * abs(ref)
