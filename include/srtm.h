@@ -81,9 +81,16 @@ typedef struct {
 
 /* Caller-allocated outputs; any pointer may be NULL (that output is skipped).
  *   fast_mean n_slow*ratio*nx,  fast_cov n_slow*ratio*nx*nx
- *   slow_mean n_slow*nx,        slow_cov n_slow*nx*nx                          */
+ *   slow_mean n_slow*nx,        slow_cov n_slow*nx*nx
+ *   loglik    one value per sequence: log p(y_{1:N}), the sum over the slow
+ *             steps of log N(y_k; C_bar m^f_{k-1,l}, S_k) with the IMKF's
+ *             predicted measurement and innovation covariance (Eq. 9-12; the
+ *             prediction-error decomposition of the marginal likelihood).
+ *             Formed in float64 from the filter results; costs one more
+ *             launch.  In a smoother call it may be given in either struct.  */
 typedef struct {
   double *fast_mean, *fast_cov, *slow_mean, *slow_cov;
+  double *loglik;
 } srtm_output;
 
 /* A ragged batch of independent sequences with common nx and ny.

@@ -16,7 +16,8 @@ from . import build as _build
 PRECISION = {"fp64": 0, "mixed": 1, "fp32": 2}
 ERRORS = {0: "SRTM_OK", -1: "SRTM_ERR_ARG", -3: "SRTM_ERR_SINGULAR", -4: "SRTM_ERR_TIMEOUT",
           -5: "SRTM_ERR_CUDA", -6: "SRTM_ERR_UNSUPPORTED", -7: "SRTM_ERR_META"}
-OUTPUT_KEYS = ("fast_mean", "fast_cov", "slow_mean", "slow_cov")
+OUTPUT_KEYS = ("fast_mean", "fast_cov", "slow_mean", "slow_cov")   # the default outputs
+ALL_OUTPUTS = OUTPUT_KEYS + ("loglik",)                               # + log p(y_1:N) per sequence
 
 # every entry point declared in include/srtm.h
 SYMBOLS = ("srtm_filter", "srtm_smoother", "srtm_filter_batch", "srtm_smoother_batch",
@@ -34,7 +35,7 @@ class Problem(ctypes.Structure):
 
 
 class Output(ctypes.Structure):
-    _fields_ = [(k, c_void_p) for k in OUTPUT_KEYS]
+    _fields_ = [(k, c_void_p) for k in ALL_OUTPUTS]
 
 
 class Batch(ctypes.Structure):
@@ -127,11 +128,11 @@ def _dev_tensor(t, name, shape):
     return c_void_p(t.data_ptr())
 
 
-def _alloc_outputs(keys, device, rows_fast, rows_slow, nx, out=None):
+def _alloc_outputs(keys, device, rows_fast, rows_slow, nx, out=None, n_seq=1):
     import torch
     res = {}
     shapes = {"fast_mean": (rows_fast, nx), "fast_cov": (rows_fast, nx, nx),
-              "slow_mean": (rows_slow, nx), "slow_cov": (rows_slow, nx, nx)}
+              "slow_mean": (rows_slow, nx), "slow_cov": (rows_slow, nx, nx), "loglik": (n_seq,)}
     for k in keys:
         if k not in shapes:
             raise ValueError(f"unknown output {k}")
@@ -140,7 +141,7 @@ def _alloc_outputs(keys, device, rows_fast, rows_slow, nx, out=None):
             t = torch.empty(shapes[k], dtype=torch.float64, device=device)
         _dev_tensor(t, k, shapes[k])
         res[k] = t
-    o = Output(*[c_void_p(res[k].data_ptr()) if k in res else None for k in OUTPUT_KEYS])
+    o = Output(*[c_void_p(res[k].data_ptr()) if k in res else None for k in ALL_OUTPUTS])
     return res, o
 
 
@@ -195,8 +196,8 @@ def smoother_batch(batch: Batch, precision="fp64", outputs=OUTPUT_KEYS, filtered
     """Ragged batch: every sequence of ``batch`` in one set of launches."""
     import torch
     device = device or torch.device("cuda", torch.cuda.current_device())
-    sm, so = _alloc_outputs(outputs, device, batch.total_fast, batch.total_slow, batch.nx, out)
-    fi, fo = _alloc_outputs(filtered, device, batch.total_fast, batch.total_slow, batch.nx, out_filtered)
+    sm, so = _alloc_outputs(outputs, device, batch.total_fast, batch.total_slow, batch.nx, out, batch.n_seq)
+    fi, fo = _alloc_outputs(filtered, device, batch.total_fast, batch.total_slow, batch.nx, out_filtered, batch.n_seq)
     _check(load().srtm_smoother_batch(ctypes.byref(batch), PRECISION[precision], ctypes.byref(so),
                                       ctypes.byref(fo) if filtered else None, _stream_handle(stream)))
     return sm, fi
@@ -205,13 +206,13 @@ def smoother_batch(batch: Batch, precision="fp64", outputs=OUTPUT_KEYS, filtered
 def filter_batch(batch: Batch, precision="fp64", outputs=OUTPUT_KEYS, stream=None, device=None, out=None):
     import torch
     device = device or torch.device("cuda", torch.cuda.current_device())
-    res, o = _alloc_outputs(outputs, device, batch.total_fast, batch.total_slow, batch.nx, out)
+    res, o = _alloc_outputs(outputs, device, batch.total_fast, batch.total_slow, batch.nx, out, batch.n_seq)
     _check(load().srtm_filter_batch(ctypes.byref(batch), PRECISION[precision], ctypes.byref(o),
                                     _stream_handle(stream)))
     return res
 
 
-def smoother_host(F, Q, H, R, m0, P0, y, ratio, precision="fp64", out=None, stream=None):
+def smoother_host(F, Q, H, R, m0, P0, y, ratio, precision="fp64", out=None, stream=None, loglik=False):
     """Host-buffer entry point: numpy float64 inputs/outputs (pinned or pageable
     memory); the library copies to the GPU, runs the smoother, copies back and
     synchronizes.  ``out`` may hold preallocated (e.g. pinned) output arrays."""
@@ -229,12 +230,14 @@ def smoother_host(F, Q, H, R, m0, P0, y, ratio, precision="fp64", out=None, stre
                    host(R, "R", (ny, ny)), host(m0, "m0", (nx,)), host(P0, "P0", (nx, nx)), host(y, "y", (N, ny)))
     shapes = {"fast_mean": (N * ratio, nx), "fast_cov": (N * ratio, nx, nx), "slow_mean": (N, nx),
               "slow_cov": (N, nx, nx)}
+    if loglik:
+        shapes["loglik"] = (1,)
     res = {}
     for k, s in shapes.items():
         a = None if out is None else out.get(k)
         res[k] = np.empty(s) if a is None else a
         host(res[k], k, s)
-    o = Output(*[c_void_p(res[k].ctypes.data) for k in OUTPUT_KEYS])
+    o = Output(*[c_void_p(res[k].ctypes.data) if k in res else None for k in ALL_OUTPUTS])
     s = c_void_p(0) if stream is None else c_void_p(stream.cuda_stream)
     _check(load().srtm_smoother_host(ctypes.byref(prob), PRECISION[precision], ctypes.byref(o), s))
     return res

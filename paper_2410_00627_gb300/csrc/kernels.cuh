@@ -244,7 +244,8 @@ __device__ void setup_interval(const Ctx& c, long long gi, int lane, unsigned ma
     for (int i = 0; i < MY; ++i)
 #pragma unroll
       for (int j = 0; j < MY; ++j) Sy[i][j] = (i < m && j < m) ? sb[Gm::Sy + i * MY + j] : ((i == j) ? TR(1) : TR(0));
-    ok &= small_sym_inverse<TR>(Sy, Si, m);
+    TR logdet = TR(0);
+    ok &= small_sym_inverse<TR>(Sy, Si, m, &logdet);
 #pragma unroll
     for (int i = 0; i < MY; ++i) {
       TR v = TR(0);
@@ -252,6 +253,14 @@ __device__ void setup_interval(const Ctx& c, long long gi, int lane, unsigned ma
       for (int j = 0; j < MY; ++j)
         if (i < m && j < m) v = fma(Si[i][j], sb[Gm::ev + j], v);
       kap[i] = v;
+    }
+    // log N(y_k; C_bar m^f_{k-1,l}, S_y): this interval's term of log p(y_{1:N})
+    if (c.loglik && lane == 0) {
+      TR q = TR(0);
+#pragma unroll
+      for (int j = 0; j < MY; ++j)
+        if (j < m) q = fma(sb[Gm::ev + j], kap[j], q);
+      c.lterm[gi] = -0.5 * ((double)m * 1.8378770664093454836 + (double)logdet + (double)q);
     }
   }
   // row r: U_l, S_y^-1 U_l^T (column r), m^f_l, P A^{lT}
@@ -1298,6 +1307,7 @@ int launch_t(const Ctx& c, const Shapes& sh, cudaStream_t st, cudaEvent_t* ev) {
   if (ev) cudaEventRecord(ev[1], st);
   if (c.setup_separate)
     setup_kernel<NX, T, TS><<<sh.grid_setup, 128, sh.smem_setup, st>>>(c);
+  launch_loglik(c, st);
   if (ev) cudaEventRecord(ev[2], st);  // otherwise the interval setup runs inside the filter scan
   if (c.smoothing)
     scan_kernel<SOp><<<sh.grid_s, sh.scan_groups_s * G, sh.smem_s, st>>>(c, sh.scan_groups_s, sh.scan_elems_s, sh.window_s);

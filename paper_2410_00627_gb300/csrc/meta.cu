@@ -83,4 +83,29 @@ int launch_meta(const Ctx& c, cudaStream_t st, cudaEvent_t* ev) {
   return cudaGetLastError() == cudaSuccess ? SRTM_OK : SRTM_ERR_CUDA;
 }
 
+// log p(y_{1:N}) of each sequence: the sum of its intervals' terms, one block
+// per sequence in a fixed order (strided partial sums, then a tree), so that
+// repeated calls give identical values.
+__global__ void __launch_bounds__(256) loglik_kernel(Ctx c) {
+  __shared__ double part[256];
+  if (!c.ctr->call_ok) return;
+  const int s = blockIdx.x;
+  const long long lo = c.meta.off_slow[s], hi = c.meta.off_slow[s + 1];
+  double acc = 0.0;
+  for (long long k = lo + threadIdx.x; k < hi; k += blockDim.x) acc += c.lterm[k];
+  part[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) c.loglik[s] = part[0];
+}
+
+int launch_loglik(const Ctx& c, cudaStream_t st) {
+  if (!c.loglik) return SRTM_OK;
+  loglik_kernel<<<c.n_seq, 256, 0, st>>>(c);
+  return cudaGetLastError() == cudaSuccess ? SRTM_OK : SRTM_ERR_CUDA;
+}
+
 }  // namespace srtm

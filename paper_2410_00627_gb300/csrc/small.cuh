@@ -10,11 +10,12 @@ namespace srtm {
 // inverse of a symmetric positive definite matrix by Cholesky (a = L L^T,
 // a^-1 = L^-T L^-1).  Only the leading nact x nact block is inverted; the
 // rest of inv is set to the identity.  Returns false if a pivot is not
-// positive.
+// positive.  logdet (optional): log det of the leading block, 2 sum log L_jj.
 template <int N, class T>
-__device__ __forceinline__ bool spd_inverse(const T (&a)[N][N], T (&inv)[N][N], int nact = N) {
+__device__ __forceinline__ bool spd_inverse(const T (&a)[N][N], T (&inv)[N][N], int nact = N, T* logdet = nullptr) {
   T Lm[N][N];
   bool ok = true;
+  T ld = T(0);
 #pragma unroll
   for (int j = 0; j < N; ++j) {
 #pragma unroll
@@ -26,6 +27,7 @@ __device__ __forceinline__ bool spd_inverse(const T (&a)[N][N], T (&inv)[N][N], 
       if (!(d > T(0)) || !isfinite(d)) { ok = false; d = T(1); }
       const T ljj = sqrt(d), rinv = T(1) / ljj;
       Lm[j][j] = ljj;
+      if (logdet) ld += log(d);
 #pragma unroll
       for (int i = j + 1; i < N; ++i) {
         if (i < nact) {
@@ -67,6 +69,7 @@ __device__ __forceinline__ bool spd_inverse(const T (&a)[N][N], T (&inv)[N][N], 
       inv[i][j] = s2;
       inv[j][i] = s2;
     }
+  if (logdet) *logdet = ld;
   return ok;
 }
 
@@ -95,13 +98,15 @@ __device__ __forceinline__ bool bad_value(float x) { return bad_pivot(x); }
 // Inverse of a small symmetric m x m matrix (m <= MY, runtime) held in the
 // leading block of a: adjugate for m <= 3 (one division), Cholesky for m = 4.
 // The rest of inv is the identity.  Returns false on a singular matrix.
+// logdet (optional): log det a, for a positive definite a.
 template <class TR>
-__device__ __forceinline__ bool small_sym_inverse(const TR (&a)[MY][MY], TR (&inv)[MY][MY], int m) {
+__device__ __forceinline__ bool small_sym_inverse(const TR (&a)[MY][MY], TR (&inv)[MY][MY], int m,
+                                                  TR* logdet = nullptr) {
 #pragma unroll
   for (int i = 0; i < MY; ++i)
 #pragma unroll
     for (int j = 0; j < MY; ++j) inv[i][j] = (i == j) ? TR(1) : TR(0);
-  if (m == 4) return spd_inverse<MY, TR>(a, inv, 4);
+  if (m == 4) return spd_inverse<MY, TR>(a, inv, 4, logdet);
   TR det;
   if (m == 1) {
     det = a[0][0];
@@ -111,6 +116,7 @@ __device__ __forceinline__ bool small_sym_inverse(const TR (&a)[MY][MY], TR (&in
     det = a[0][0] * (a[1][1] * a[2][2] - a[1][2] * a[2][1]) - a[0][1] * (a[1][0] * a[2][2] - a[1][2] * a[2][0]) +
           a[0][2] * (a[1][0] * a[2][1] - a[1][1] * a[2][0]);
   }
+  if (logdet) *logdet = log(det);
   bool ok = !bad_value(det);
   if (!ok) det = TR(1);
   const TR id = TR(1) / det;

@@ -82,7 +82,7 @@ size_t a256(size_t x) { return (x + 255) / 256 * 256; }
 size_t a16(size_t x) { return (x + 15) / 16 * 16; }
 
 struct Layout {
-  size_t ctr, ratio, nslow, off_slow, off_fast, tile_f, tile_s, model, ftile, stile, fout, rec, selem, sfin,
+  size_t ctr, ratio, nslow, off_slow, off_fast, tile_f, tile_s, model, ftile, stile, fout, rec, selem, sfin, lterm,
       total;
   long long ftile_stride, stile_stride;
   ModelLayout ml;
@@ -118,6 +118,7 @@ Layout make_layout(int nx, int ny, int max_ratio, int n_seq, long long total_slo
   L.rec = take(sR * (size_t)REC * total_slow);
   L.selem = take(sT * (size_t)SE * total_slow);
   L.sfin = take(sR * (size_t)SFN * total_slow);
+  L.lterm = take(sizeof(double) * (size_t)total_slow);
   L.total = a256(o);
   return L;
 }
@@ -250,10 +251,11 @@ int run(Ctx c, srtm_precision prec, cudaStream_t st) {
   c.rec = w + L.rec;
   c.selem = w + L.selem;
   c.sfin = w + L.sfin;
+  c.lterm = (double*)(w + L.lterm);
   c.tile_f = tile_f;
   c.tile_s = tile_s;
   c.setup_separate = t.setup_mode == 2 ? 1 : 0;
-  d.last_launches = (c.fold_meta ? 0 : 1) + 3 + (c.smoothing ? 1 : 0) + c.setup_separate;
+  d.last_launches = (c.fold_meta ? 0 : 1) + 3 + (c.smoothing ? 1 : 0) + c.setup_separate + (c.loglik ? 1 : 0);
   cudaEvent_t* ev = nullptr;
   if (g_timing) {
     if (!d.ev[0])
@@ -278,9 +280,9 @@ int check_dims(int nx, int ny) {
 
 int check_outputs(const srtm_output* o, const char* what) {
   if (!o) return SRTM_OK;
-  const double* ps[4] = {o->fast_mean, o->fast_cov, o->slow_mean, o->slow_cov};
-  const char* nm[4] = {"fast_mean", "fast_cov", "slow_mean", "slow_cov"};
-  for (int i = 0; i < 4; ++i)
+  const double* ps[5] = {o->fast_mean, o->fast_cov, o->slow_mean, o->slow_cov, o->loglik};
+  const char* nm[5] = {"fast_mean", "fast_cov", "slow_mean", "slow_cov", "loglik"};
+  for (int i = 0; i < 5; ++i)
     if (ps[i] && !is_device_ptr(ps[i])) return fail(SRTM_ERR_ARG, "%s.%s is not a device pointer", what, nm[i]);
   return SRTM_OK;
 }
@@ -305,6 +307,7 @@ void set_outputs(Ctx& c, const srtm_output* main, const srtm_output* extra) {
   c.ffast_cov = extra ? extra->fast_cov : nullptr;
   c.fslow_mean = extra ? extra->slow_mean : nullptr;
   c.fslow_cov = extra ? extra->slow_cov : nullptr;
+  c.loglik = (main && main->loglik) ? main->loglik : (extra ? extra->loglik : nullptr);
 }
 
 int single(const srtm_problem* p, srtm_precision prec, const srtm_output* out, const srtm_output* extra,
@@ -417,11 +420,12 @@ int srtm_smoother_host(const srtm_problem* hp, srtm_precision prec, const srtm_o
   const long long nx = hp->nx, ny = hp->ny, N = hp->n_slow, l = hp->ratio;
   const size_t in_cnt[7] = {(size_t)(nx * nx), (size_t)(nx * nx), (size_t)(ny * nx), (size_t)(ny * ny),
                             (size_t)nx, (size_t)(nx * nx), (size_t)(N * ny)};
-  const size_t out_cnt[4] = {(size_t)(N * l * nx), (size_t)(N * l * nx * nx), (size_t)(N * nx), (size_t)(N * nx * nx)};
-  double* hout_p[4] = {hout->fast_mean, hout->fast_cov, hout->slow_mean, hout->slow_cov};
-  size_t off[11], o = 0;
+  const size_t out_cnt[5] = {(size_t)(N * l * nx), (size_t)(N * l * nx * nx), (size_t)(N * nx), (size_t)(N * nx * nx),
+                             1};
+  double* hout_p[5] = {hout->fast_mean, hout->fast_cov, hout->slow_mean, hout->slow_cov, hout->loglik};
+  size_t off[12], o = 0;
   for (int i = 0; i < 7; ++i) { off[i] = o; o += a256(in_cnt[i] * sizeof(double)); }
-  for (int i = 0; i < 4; ++i) { off[7 + i] = o; o += hout_p[i] ? a256(out_cnt[i] * sizeof(double)) : 0; }
+  for (int i = 0; i < 5; ++i) { off[7 + i] = o; o += hout_p[i] ? a256(out_cnt[i] * sizeof(double)) : 0; }
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAXDEV) return fail(SRTM_ERR_CUDA, "no device");
   unsigned char* stg = nullptr;
@@ -448,11 +452,11 @@ int srtm_smoother_host(const srtm_problem* hp, srtm_precision prec, const srtm_o
   dp.m0 = (const double*)(stg + off[4]); dp.P0 = (const double*)(stg + off[5]);
   dp.y = (const double*)(stg + off[6]);
   srtm_output dout;
-  double** dsl[4] = {&dout.fast_mean, &dout.fast_cov, &dout.slow_mean, &dout.slow_cov};
-  for (int i = 0; i < 4; ++i) *dsl[i] = hout_p[i] ? (double*)(stg + off[7 + i]) : nullptr;
+  double** dsl[5] = {&dout.fast_mean, &dout.fast_cov, &dout.slow_mean, &dout.slow_cov, &dout.loglik};
+  for (int i = 0; i < 5; ++i) *dsl[i] = hout_p[i] ? (double*)(stg + off[7 + i]) : nullptr;
   rc = srtm_smoother(&dp, prec, &dout, nullptr, stream);
   if (rc) return rc;
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < 5; ++i)
     if (hout_p[i] &&
         cudaMemcpyAsync(hout_p[i], *dsl[i], out_cnt[i] * sizeof(double), cudaMemcpyDefault, st) != cudaSuccess)
       return fail(SRTM_ERR_CUDA, "output copy %d failed", i);
@@ -758,6 +762,7 @@ extern "C" int srtm_smoother_noalloc(const srtm_problem* p, srtm_precision prec,
     c.rec = w + L.rec;
     c.selem = w + L.selem;
     c.sfin = w + L.sfin;
+    c.lterm = (double*)(w + L.lterm);
     c.tile_f = tile_f;
     c.tile_s = tile_s;
     c.setup_separate = t.setup_mode == 2 ? 1 : 0;

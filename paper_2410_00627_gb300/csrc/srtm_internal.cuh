@@ -150,6 +150,8 @@ struct Ctx {
   void* rec;    // [total_slow][Rec::SIZE] per-interval records              (recovery type)
   void* selem;  // [total_slow][SL::SIZE]  smoother elements                  (scan type)
   void* sfin;   // [total_slow][NN + NX]   per-interval smoothing terms Om_k, om_k (recovery type)
+  double* lterm;   // [total_slow] per-interval terms of log p(y_{1:N})
+  double* loglik;  // caller's output: log p(y_{1:N}) per sequence (NULL: not computed)
   // launch shapes
   int tile_f, tile_s;    // elements per scan tile
   int setup_separate;    // 1: the interval setup runs as its own kernel after the filter scan
@@ -193,6 +195,9 @@ struct Shapes {  // resolved launch shapes for one call
 
 template <int NX>
 int launch_device_path(const Ctx& c, srtm_precision prec, const Shapes& sh, cudaStream_t st, cudaEvent_t* ev);
+
+// sums the per-interval terms into the caller's log-likelihood output (meta.cu)
+int launch_loglik(const Ctx& c, cudaStream_t st);
 
 template <int NX>
 int query_shapes(srtm_precision prec, int scan_groups, int scan_elems, int window, int recover_threads,

@@ -36,7 +36,7 @@ def test_library_exports_every_declared_symbol(lib):
 def test_struct_layouts_match_header():
     # two 4-int headers then pointers on LP64
     assert ctypes.sizeof(api.Problem) == 16 + 7 * 8
-    assert ctypes.sizeof(api.Output) == 4 * 8
+    assert ctypes.sizeof(api.Output) == 5 * 8
     assert ctypes.sizeof(api.Batch) == 16 + 16 + 9 * 8
     assert ctypes.sizeof(api.Tuning) == 20
 

@@ -279,3 +279,60 @@ def test_autotune_keeps_a_valid_tuning_and_results_still_match(oracle_mod):
         compare(fi, ref_fi, tm, tc, "filtered after autotune")
     finally:
         api.set_tuning(4, "mixed")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("case", CASES[:9], ids=lambda c: "n{1}m{2}l{3}N{4}".format(*c))
+def test_loglik_matches_oracle(oracle_mod, case, precision):
+    """log p(y_1:N) (the loglik output) against the oracle's prediction-error
+    decomposition; the other outputs are unchanged by asking for it."""
+    from paper_2410_00627_gb300 import api
+    seed, nx, ny, l, N = case
+    prob = synth.random_model(seed, nx, ny, l, N)
+    args = [to_dev(getattr(prob, k)) for k in ("F", "Q", "H", "R", "m0", "P0", "y")]
+    sm, _ = api.smoother(*args, l, precision=precision, outputs=api.ALL_OUTPUTS)
+    api.status()
+    assert api.last_call_launches() == 5
+    want = oracle_mod.loglik(prob)
+    got = float(sm["loglik"].cpu().item())
+    tol = 1e-9 if precision == "fp64" else 1e-4
+    assert abs(got - want) <= tol * max(1.0, abs(want)), (got, want)
+    plain, _ = api.smoother(*args, l, precision=precision)
+    assert np.array_equal(plain["fast_cov"].cpu().numpy(), sm["fast_cov"].cpu().numpy())
+
+
+def test_loglik_full_size_config2_and_filter_call(oracle_mod):
+    from paper_2410_00627_gb300 import api
+    prob = synth.config2(seed=0, n_slow=10_000, keep_states=False)
+    args = [to_dev(getattr(prob, k)) for k in ("F", "Q", "H", "R", "m0", "P0", "y")]
+    want = oracle_mod.loglik(prob)
+    for precision, tol in (("fp64", 1e-9), ("mixed", 1e-4)):
+        out = api.filter(*args, prob.ratio, precision=precision, outputs=("slow_mean", "loglik"))
+        api.status()
+        got = float(out["loglik"].cpu().item())
+        assert abs(got - want) <= tol * abs(want), (precision, got, want)
+
+
+def test_loglik_per_sequence_in_a_batch(oracle_mod):
+    import torch
+
+    from paper_2410_00627_gb300 import api
+    probs = synth.config4(seed=9, n_seq=7, n_min=1, n_max=90)
+    pk = synth.pack(probs)
+    t = lambda a: torch.as_tensor(a, device="cuda")  # noqa: E731
+    b = api.make_batch(t(pk["F"]), t(pk["Q"]), t(pk["H"]), t(pk["R"]), t(pk["m0"]), t(pk["P0"]), t(pk["y"]),
+                       t(pk["ratio"]), t(pk["n_slow"]), pk["max_ratio"], pk["total_slow"], pk["total_fast"])
+    sm, _ = api.smoother_batch(b, precision="fp64", outputs=("slow_mean", "loglik"))
+    api.status()
+    got = sm["loglik"].cpu().numpy()
+    want = np.array([oracle_mod.loglik(p) for p in probs])
+    assert np.all(np.abs(got - want) <= 1e-9 * np.maximum(1.0, np.abs(want)))
+
+
+def test_loglik_through_host_entry_point(oracle_mod):
+    from paper_2410_00627_gb300 import api
+    prob = synth.config2(seed=8, n_slow=200, keep_states=False)
+    res = api.smoother_host(*[np.ascontiguousarray(getattr(prob, k)) for k in ("F", "Q", "H", "R", "m0", "P0", "y")],
+                            prob.ratio, precision="fp64", loglik=True)
+    want = oracle_mod.loglik(prob)
+    assert abs(res["loglik"][0] - want) <= 1e-9 * abs(want)
