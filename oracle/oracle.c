@@ -133,11 +133,51 @@ typedef struct {
   double *GQG;    /* script-G Q~ script-G^T            (ln x ln) (Eq. 14,15)     */
   double *AtHt;   /* script-A^T script-H^T                (n x m) (Eq. 14,16)     */
   double *GQGHt;  /* script-G Q~ script-G^T script-H^T   (ln x m) (Eq. 15,16)     */
+  int nu;         /* inputs (0: none)                                               */
+  double *B;      /* B                                    (n x nu)                 */
+  double *Bbar;   /* B_bar = [A^{l-1}B ... AB B]          (n x l nu) (Eq. 7)       */
+  double *Dbar;   /* D_bar = (C/l)[sum_{i<l}A^i B, ..., B] (m x l nu) (Eq. 10)     */
+  double *sB;     /* stacked fast input map, block (i,j) = A^{i-j} B, j <= i
+                     (ln x l nu): the input part of the stacked means (Eq. 13)    */
 } model_t;
 
 static void model_free(model_t *M) {
   free(M->Apow); free(M->Abar); free(M->Qbar); free(M->Cbar); free(M->MQM);
   free(M->GQM); free(M->GQG); free(M->AtHt); free(M->GQGHt);
+  free(M->B); free(M->Bbar); free(M->Dbar); free(M->sB);
+}
+
+/* The input matrices of the lifted and stacked models (nu > 0): the
+ * interval's inputs are u_bar_k = [u_{k-1,l}; u_{k,1}; ...; u_{k,l-1}], the
+ * inputs that drive x_{k,1}, ..., x_{k,l}. */
+static void model_inputs(model_t *M, int nu, const double *B, const double *H) {
+  int n = M->n, m = M->m, l = M->l, ln = l * n, lu = l * nu;
+  M->nu = nu;
+  M->B = M->Bbar = M->Dbar = M->sB = NULL;
+  if (nu <= 0 || !B) { M->nu = 0; return; }
+  M->B = dalloc((size_t)n * nu);
+  copy(n * nu, B, M->B);
+  M->Bbar = dalloc((size_t)n * lu);
+  M->Dbar = dalloc((size_t)m * lu);
+  M->sB = dalloc((size_t)ln * lu);
+  double *AB = dalloc((size_t)(l + 1) * n * nu), *SB = dalloc((size_t)n * nu), *HSB = dalloc((size_t)m * nu);
+  for (int i = 0; i <= l; ++i) gemm(n, n, nu, 1.0, M->Apow + (size_t)i * n * n, 0, B, 0, 0.0, AB + (size_t)i * n * nu);
+  for (int j = 0; j < l; ++j) {
+    /* Bbar block j = A^{l-1-j} B;  Dbar block j = H sum_{i=0}^{l-1-j} A^i B */
+    const double *Ab = AB + (size_t)(l - 1 - j) * n * nu;
+    for (int r = 0; r < n; ++r) for (int c = 0; c < nu; ++c) M->Bbar[r * lu + j * nu + c] = Ab[r * nu + c];
+    memset(SB, 0, sizeof(double) * (size_t)n * nu);
+    for (int i = 0; i <= l - 1 - j; ++i) axpy(n * nu, 1.0, AB + (size_t)i * n * nu, SB);
+    gemm(m, n, nu, 1.0, H, 0, SB, 0, 0.0, HSB);
+    for (int r = 0; r < m; ++r) for (int c = 0; c < nu; ++c) M->Dbar[r * lu + j * nu + c] = HSB[r * nu + c];
+  }
+  /* stacked: block (i,j) = A^{i-j} B for j <= i (x_{k,i+1} gets u_{k,j}) */
+  for (int i = 0; i < l; ++i)
+    for (int j = 0; j <= i; ++j) {
+      const double *Ab = AB + (size_t)(i - j) * n * nu;
+      for (int r = 0; r < n; ++r) for (int c = 0; c < nu; ++c) M->sB[(size_t)(i * n + r) * lu + j * nu + c] = Ab[r * nu + c];
+    }
+  free(AB); free(SB); free(HSB);
 }
 
 /* Forms the lifted matrices literally: G_bar = [A^{l-1} ... A I] (n x ln),
@@ -242,12 +282,13 @@ static int logdet_spd(int m, const double *S, double *out) {
  * measurement's log predictive density log N(y_k; C_bar m_{k-1}, S_k), the
  * k-th term of the prediction-error decomposition of log p(y_{1:N}). */
 static int imkf_step(const model_t *M, const double *R, const double *mp, const double *Pp,
-                     const double *yk, double *mf, double *Pf, double *term) {
+                     const double *yk, double *mf, double *Pf, double *term, const double *uk) {
   int n = M->n, m = M->m, rc = 0;
   double *mminus = dalloc(n), *Pminus = dalloc((size_t)n * n), *AP = dalloc((size_t)n * n);
   double *cross = dalloc((size_t)n * m), *S = dalloc((size_t)m * m), *CP = dalloc((size_t)m * n);
   double *L = dalloc((size_t)n * m), *innov = dalloc(m);
   gemm(n, n, 1, 1.0, M->Abar, 0, mp, 0, 0.0, mminus);                /* m^- = A_bar m      */
+  if (M->nu && uk) gemm(n, M->l * M->nu, 1, 1.0, M->Bbar, 0, uk, 0, 1.0, mminus); /* + B_bar u_bar_k */
   gemm(n, n, n, 1.0, M->Abar, 0, Pp, 0, 0.0, AP);
   gemm(n, n, n, 1.0, AP, 0, M->Abar, 1, 0.0, Pminus);                /* A_bar P A_bar^T    */
   axpy(n * n, 1.0, M->Qbar, Pminus);                                 /*   + Q_bar          */
@@ -260,6 +301,7 @@ static int imkf_step(const model_t *M, const double *R, const double *mp, const 
   if (right_solve(m, S, n, cross, L)) rc = -1;                       /* L_k                */
   gemm(m, n, 1, -1.0, M->Cbar, 0, mp, 0, 0.0, innov);
   axpy(m, 1.0, yk, innov);                                           /* y - C_bar m        */
+  if (M->nu && uk) gemm(m, M->l * M->nu, 1, -1.0, M->Dbar, 0, uk, 0, 1.0, innov);   /* - D_bar u_bar_k */
   if (term) {  /* -1/2 (m log 2 pi + log det S + innov^T S^-1 innov) */
     double *z = dalloc(m), ld = 0.0, q = 0.0;
     copy(m, innov, z);
@@ -312,8 +354,10 @@ static void get_block(int n, int ln, const double *X, int bi, int bj, double *ou
  *   P^f_{ij}     = P^-_{ij} - L_i (P^- H^T)_j^T                                 */
 static int fast_filter_interval(const model_t *M, const double *H, const double *R,
                                 const double *mp, const double *Pp, const double *yk,
-                                double *mf, double *Pii, double *Pil) {
+                                double *mf, double *Pii, double *Pil, const double *uk) {
   int n = M->n, m = M->m, l = M->l, ln = l * n, rc = 0;
+  double *sBu = dalloc((size_t)ln);   /* input part of the stacked means */
+  if (M->nu && uk) gemm(ln, l * M->nu, 1, 1.0, M->sB, 0, uk, 0, 0.0, sBu);
   double *PHt = dalloc((size_t)ln * m), *S = dalloc((size_t)m * m), *L = dalloc((size_t)ln * m);
   double *PAtHt = dalloc((size_t)n * m), *innov = dalloc(m), *Am = dalloc(n);
   double *AP = dalloc((size_t)n * n), *blk = dalloc((size_t)n * n);
@@ -328,12 +372,14 @@ static int fast_filter_interval(const model_t *M, const double *H, const double 
   copy(m, yk, innov);
   for (int i = 0; i < l; ++i) {
     gemm(n, n, 1, 1.0, M->Apow + (size_t)(i + 1) * n * n, 0, mp, 0, 0.0, Am);
+    axpy(n, 1.0, sBu + (size_t)i * n, Am);
     gemm(m, n, 1, -1.0, H, 0, Am, 0, 1.0, innov);
   }
   for (int i = 0; i < l; ++i) {
     const double *Ai = M->Apow + (size_t)(i + 1) * n * n;
     const double *Li = L + (size_t)i * n * m;
     gemm(n, n, 1, 1.0, Ai, 0, mp, 0, 0.0, mf + (size_t)i * n);
+    axpy(n, 1.0, sBu + (size_t)i * n, mf + (size_t)i * n);
     gemm(n, m, 1, 1.0, Li, 0, innov, 0, 1.0, mf + (size_t)i * n);
     gemm(n, n, n, 1.0, Ai, 0, Pp, 0, 0.0, AP);
     /* (i,i) block */
@@ -349,7 +395,7 @@ static int fast_filter_interval(const model_t *M, const double *H, const double 
     axpy(n * n, 1.0, blk, Po);
     gemm(n, m, n, -1.0, Li, 0, PHt + (size_t)(l - 1) * n * m, 1, 1.0, Po);
   }
-  free(PHt); free(S); free(L); free(PAtHt); free(innov); free(Am); free(AP); free(blk);
+  free(PHt); free(S); free(L); free(PAtHt); free(innov); free(Am); free(AP); free(blk); free(sBu);
   return rc;
 }
 
@@ -359,14 +405,14 @@ static int fast_filter_interval(const model_t *M, const double *H, const double 
 
 /* Smoothing step shared by Eq. (21) (all fast states) and Eq. (22) (first
  * state): given the filtered quantities of interval k and p(x_{k+1,1}|y_{1:N}),
- *   P^-_{k+1,1} = A P^f_{k,l,l} A^T + Q,   m^-_{k+1,1} = A m^f_{k,l}
+ *   P^-_{k+1,1} = A P^f_{k,l,l} A^T + Q,   m^-_{k+1,1} = A m^f_{k,l} + B u_{k,l}
  *   G_{k,i}     = P^f_{k,i,l} A^T [P^-_{k+1,1}]^{-1}
  *   m^s_{k,i}   = m^f_{k,i} + G_{k,i} (m^s_{k+1,1} - m^-_{k+1,1})
  *   P^s_{k,i,i} = P^f_{k,i,i} + G_{k,i} (P^s_{k+1,1} - P^-_{k+1,1}) G_{k,i}^T */
 static int smooth_step(int n, const double *A, const double *Q, const double *ml,
                        const double *Pll, const double *mfi, const double *Pfii,
                        const double *Pfil, const double *ms_next, const double *Ps_next,
-                       double *ms, double *Ps) {
+                       double *ms, double *Ps, const double *bnext) {
   double *AP = dalloc((size_t)n * n), *Pm = dalloc((size_t)n * n), *mm = dalloc(n);
   double *PA = dalloc((size_t)n * n), *G = dalloc((size_t)n * n), *dm = dalloc(n);
   double *dP = dalloc((size_t)n * n), *GdP = dalloc((size_t)n * n);
@@ -375,6 +421,7 @@ static int smooth_step(int n, const double *A, const double *Q, const double *ml
   gemm(n, n, n, 1.0, AP, 0, A, 1, 0.0, Pm);
   axpy(n * n, 1.0, Q, Pm);
   gemm(n, n, 1, 1.0, A, 0, ml, 0, 0.0, mm);
+  if (bnext) axpy(n, 1.0, bnext, mm);                        /* + B u_{k+1,0} */
   gemm(n, n, n, 1.0, Pfil, 0, A, 1, 0.0, PA);
   if (right_solve(n, Pm, n, PA, G)) rc = -1;
   copy(n, ms_next, dm); axpy(n, -1.0, mm, dm);
@@ -388,6 +435,12 @@ static int smooth_step(int n, const double *A, const double *Q, const double *ml
   return rc;
 }
 
+/* Inputs of interval k (0-based): u_bar = rows k l .. k l + l - 1 of u (NULL
+ * without inputs); B u_{k+1,0} = B u_{(k+1) l}, the input term of the
+ * prediction m^-_{k+1,1} in the smoother (NULL without inputs). */
+#define UBAR(k) (M.nu ? u + (size_t)(k) * l * M.nu : NULL)
+#define BNEXT(k) (M.nu ? (gemm(n, M.nu, 1, 1.0, M.B, 0, u + (size_t)((k) + 1) * l * M.nu, 0, 0.0, bnext), bnext) : NULL)
+
 /* Sequential reference: IMKF (Eq. 9,12) for x_{k,l}; fast filter (Eq. 15-17);
  * sequential smoother for x_{k,1} (Eq. 22) and for all fast states (Eq. 21).
  * Arrays: y is N x m.  Every output may be NULL.  Fast outputs cover the
@@ -399,17 +452,22 @@ int oracle_srtm_sequential(int n, int m, int l, int N, const double *A, const do
                            double *slow_filt_mean, double *slow_filt_cov,
                            double *first_smooth_mean, double *first_smooth_cov,
                            double *fast_filt_mean, double *fast_filt_cov,
-                           double *fast_smooth_mean, double *fast_smooth_cov) {
+                           double *fast_smooth_mean, double *fast_smooth_cov, int nu, const double *B,
+                           const double *u) {
   if (n < 1 || m < 1 || l < 1 || N < 1 || k_lo < 0 || k_hi > N || k_lo > k_hi) return -2;
   model_t M;
   model_build(&M, n, m, l, A, Q, H);
+  model_inputs(&M, u ? nu : 0, B, H);
   int rc = 0, nn = n * n;
+  double *bnext = dalloc(n);
   double *mfl = dalloc((size_t)N * n), *Pfl = dalloc((size_t)N * nn);
   /* IMKF */
   for (int k = 0; k < N; ++k) {
     const double *mp = k ? mfl + (size_t)(k - 1) * n : m0;
     const double *Pp = k ? Pfl + (size_t)(k - 1) * nn : P0;
-    if (imkf_step(&M, R, mp, Pp, y + (size_t)k * m, mfl + (size_t)k * n, Pfl + (size_t)k * nn, NULL)) rc = -1;
+    if (imkf_step(&M, R, mp, Pp, y + (size_t)k * m, mfl + (size_t)k * n, Pfl + (size_t)k * nn, NULL,
+                  UBAR(k)))
+      rc = -1;
   }
   if (slow_filt_mean) copy(N * n, mfl, slow_filt_mean);
   if (slow_filt_cov) copy(N * nn, Pfl, slow_filt_cov);
@@ -423,7 +481,7 @@ int oracle_srtm_sequential(int n, int m, int l, int N, const double *A, const do
     for (int k = 0; k < N; ++k) {
       const double *mp = k ? mfl + (size_t)(k - 1) * n : m0;
       const double *Pp = k ? Pfl + (size_t)(k - 1) * nn : P0;
-      if (fast_filter_interval(&M, H, R, mp, Pp, y + (size_t)k * m, mf, Pii, Pil)) rc = -1;
+      if (fast_filter_interval(&M, H, R, mp, Pp, y + (size_t)k * m, mf, Pii, Pil, UBAR(k))) rc = -1;
       copy(n, mf, m1 + (size_t)k * n);
       copy(nn, Pii, P11 + (size_t)k * nn);
       copy(nn, Pil, P1l + (size_t)k * nn);
@@ -436,7 +494,8 @@ int oracle_srtm_sequential(int n, int m, int l, int N, const double *A, const do
     for (int k = N - 2; k >= 0; --k)
       if (smooth_step(n, A, Q, ml + (size_t)k * n, Pll + (size_t)k * nn, m1 + (size_t)k * n,
                       P11 + (size_t)k * nn, P1l + (size_t)k * nn, ms1 + (size_t)(k + 1) * n,
-                      Ps1 + (size_t)(k + 1) * nn, ms1 + (size_t)k * n, Ps1 + (size_t)k * nn)) rc = -1;
+                      Ps1 + (size_t)(k + 1) * nn, ms1 + (size_t)k * n, Ps1 + (size_t)k * nn, BNEXT(k)))
+        rc = -1;
     if (first_smooth_mean) copy(N * n, ms1, first_smooth_mean);
     if (first_smooth_cov) copy(N * nn, Ps1, first_smooth_cov);
     free(m1); free(P11); free(P1l); free(ml); free(Pll);
@@ -445,7 +504,7 @@ int oracle_srtm_sequential(int n, int m, int l, int N, const double *A, const do
     for (int k = k_lo; k < k_hi; ++k) {
       const double *mp = k ? mfl + (size_t)(k - 1) * n : m0;
       const double *Pp = k ? Pfl + (size_t)(k - 1) * nn : P0;
-      if (fast_filter_interval(&M, H, R, mp, Pp, y + (size_t)k * m, mf, Pii, Pil)) rc = -1;
+      if (fast_filter_interval(&M, H, R, mp, Pp, y + (size_t)k * m, mf, Pii, Pil, UBAR(k))) rc = -1;
       size_t row = (size_t)(k - k_lo) * l;
       if (fast_filt_mean) copy(l * n, mf, fast_filt_mean + row * n);
       if (fast_filt_cov) copy(l * nn, Pii, fast_filt_cov + row * nn);
@@ -457,7 +516,7 @@ int oracle_srtm_sequential(int n, int m, int l, int N, const double *A, const do
             copy(nn, Pii + (size_t)i * nn, Psi);
           } else if (smooth_step(n, A, Q, mf + (size_t)(l - 1) * n, Pii + (size_t)(l - 1) * nn,
                                  mf + (size_t)i * n, Pii + (size_t)i * nn, Pil + (size_t)i * nn,
-                                 ms1 + (size_t)(k + 1) * n, Ps1 + (size_t)(k + 1) * nn, msi, Psi)) {
+                                 ms1 + (size_t)(k + 1) * n, Ps1 + (size_t)(k + 1) * nn, msi, Psi, BNEXT(k))) {
             rc = -1;
           }
           if (fast_smooth_mean) copy(n, msi, fast_smooth_mean + (row + i) * n);
@@ -467,7 +526,7 @@ int oracle_srtm_sequential(int n, int m, int l, int N, const double *A, const do
       }
     }
   }
-  free(mf); free(Pii); free(Pil); free(ms1); free(Ps1); free(mfl); free(Pfl);
+  free(mf); free(Pii); free(Pil); free(ms1); free(Ps1); free(mfl); free(Pfl); free(bnext);
   model_free(&M);
   return rc;
 }
@@ -572,13 +631,18 @@ int oracle_srtm_parallel(int n, int m, int l, int N, const double *A, const doub
                          const double *H, const double *R, const double *m0,
                          const double *P0, const double *y, int order, int flags,
                          double *slow_filt_mean, double *slow_filt_cov,
-                         double *first_smooth_mean, double *first_smooth_cov) {
+                         double *first_smooth_mean, double *first_smooth_cov, int nu, const double *B,
+                         const double *u) {
   if (n < 1 || m < 1 || l < 1 || N < 1) return -2;
   model_t M;
   model_build(&M, n, m, l, A, Q, H);
+  model_inputs(&M, u ? nu : 0, B, H);
   int nn = n * n, fs = felem_size(n), ss = selem_size(n), rc = 0;
+  double *bnext = dalloc(n), *yc = dalloc(m), *bl = dalloc(n);
   /* Eq. (25),(26): R_x = M Q~ M^T + R, K = G Q~ M^T R_x^{-1}, F = A_bar - K C_bar,
-   * d_k = K y_k, D = Q_bar - K M Q~ G^T, eta_k = C_bar^T R_x^{-1} y_k, J = C_bar^T R_x^{-1} C_bar */
+   * d_k = K y_k, D = Q_bar - K M Q~ G^T, eta_k = C_bar^T R_x^{-1} y_k, J = C_bar^T R_x^{-1} C_bar;
+   * with inputs y_k is replaced by y_k - D_bar u_bar_k and d_k gains B_bar u_bar_k (the
+   * conditional mean of x_{k,l} given x_{k-1,l} and y_k shifts by the known input terms). */
   double *Rx = dalloc((size_t)m * m), *Rxi = dalloc((size_t)m * m), *K = dalloc((size_t)n * m);
   double *F = dalloc(nn), *D = dalloc(nn), *CtRi = dalloc((size_t)n * m), *J = dalloc(nn);
   copy(m * m, M.MQM, Rx); axpy(m * m, 1.0, R, Rx);
@@ -593,12 +657,19 @@ int oracle_srtm_parallel(int n, int m, int l, int N, const double *A, const doub
     double *a = fe + (size_t)k * fs;
     const double *yk = y + (size_t)k * m;
     if (k == 0) {   /* F_1 = 0, d_1 = m^f_{1,l}, D_1 = P^f_{1,l}, eta_1 = 0, J_1 = 0 */
-      if (imkf_step(&M, R, m0, P0, yk, a + nn, a + nn + n, NULL)) rc = -1;
+      if (imkf_step(&M, R, m0, P0, yk, a + nn, a + nn + n, NULL, UBAR(0))) rc = -1;
     } else {
+      copy(m, yk, yc);
+      memset(bl, 0, sizeof(double) * n);
+      if (M.nu) {
+        gemm(m, l * M.nu, 1, -1.0, M.Dbar, 0, UBAR(k), 0, 1.0, yc);
+        gemm(n, l * M.nu, 1, 1.0, M.Bbar, 0, UBAR(k), 0, 0.0, bl);
+      }
       copy(nn, F, a);
-      gemm(n, m, 1, 1.0, K, 0, yk, 0, 0.0, a + nn);
+      copy(n, bl, a + nn);
+      gemm(n, m, 1, 1.0, K, 0, yc, 0, 1.0, a + nn);
       copy(nn, D, a + nn + n);
-      gemm(n, m, 1, 1.0, CtRi, 0, yk, 0, 0.0, a + 2 * nn + n);
+      gemm(n, m, 1, 1.0, CtRi, 0, yc, 0, 0.0, a + 2 * nn + n);
       copy(nn, J, a + 2 * nn + 2 * n);
     }
   }
@@ -622,7 +693,7 @@ int oracle_srtm_parallel(int n, int m, int l, int N, const double *A, const doub
     for (int k = 0; k < N; ++k) {
       const double *mp = k ? mfl + (size_t)(k - 1) * n : m0;
       const double *Pp = k ? Pfl + (size_t)(k - 1) * nn : P0;
-      if (fast_filter_interval(&M, H, R, mp, Pp, y + (size_t)k * m, mf, Pii, Pil)) rc = -1;
+      if (fast_filter_interval(&M, H, R, mp, Pp, y + (size_t)k * m, mf, Pii, Pil, UBAR(k))) rc = -1;
       double *E = se + (size_t)k * ss, *g = E + nn, *S = E + nn + n;
       if (k == N - 1) {
         memset(E, 0, sizeof(double) * nn);
@@ -636,6 +707,7 @@ int oracle_srtm_parallel(int n, int m, int l, int N, const double *A, const doub
       gemm(n, n, n, 1.0, Pil, 0, A, 1, 0.0, PA);                /* P^f_{k,1,l} A^T */
       if (right_solve(n, Pm, n, PA, E)) rc = -1;
       gemm(n, n, 1, 1.0, A, 0, mfl + (size_t)k * n, 0, 0.0, Am);
+      if (M.nu) axpy(n, 1.0, BNEXT(k), Am);                      /* + B u_{k,l} */
       copy(n, mf, g); gemm(n, n, 1, -1.0, E, 0, Am, 0, 1.0, g);
       gemm(n, n, n, 1.0, E, 0, A, 0, 0.0, EA);
       copy(nn, Pii, S);
@@ -649,6 +721,7 @@ int oracle_srtm_parallel(int n, int m, int l, int N, const double *A, const doub
     free(se); free(mf); free(Pii); free(Pil); free(AP); free(Pm); free(PA); free(Am); free(EA);
   }
   free(Rx); free(Rxi); free(K); free(F); free(D); free(CtRi); free(J); free(fe); free(mfl); free(Pfl);
+  free(bnext); free(yc); free(bl);
   model_free(&M);
   return rc;
 }
@@ -659,6 +732,7 @@ int oracle_lifted(int n, int m, int l, const double *A, const double *Q, const d
   if (n < 1 || m < 1 || l < 1) return -2;
   model_t M;
   model_build(&M, n, m, l, A, Q, H);
+  model_inputs(&M, 0, NULL, H);
   copy(n * n, M.Abar, Abar); copy(n * n, M.Qbar, Qbar); copy(m * n, M.Cbar, Cbar);
   copy(m * m, M.MQM, MQM); copy(n * m, M.GQM, GQM);
   model_free(&M);
@@ -673,17 +747,18 @@ int oracle_lifted(int n, int m, int l, const double *A, const double *Q, const d
 /* ------------------------------------------------------------------------ */
 int oracle_loglik(int n, int m, int l, int N, const double *A, const double *Q, const double *H,
                   const double *R, const double *m0, const double *P0, const double *y, double *terms,
-                  double *total) {
+                  double *total, int nu, const double *B, const double *u) {
   if (n < 1 || m < 1 || l < 1 || N < 1 || !total) return -2;
   model_t M;
   model_build(&M, n, m, l, A, Q, H);
+  model_inputs(&M, u ? nu : 0, B, H);
   int rc = 0, nn = n * n;
   double *mf = dalloc((size_t)N * n), *Pf = dalloc((size_t)N * nn), acc = 0.0;
   for (int k = 0; k < N; ++k) {
     const double *mp = k ? mf + (size_t)(k - 1) * n : m0;
     const double *Pp = k ? Pf + (size_t)(k - 1) * nn : P0;
     double t = 0.0;
-    if (imkf_step(&M, R, mp, Pp, y + (size_t)k * m, mf + (size_t)k * n, Pf + (size_t)k * nn, &t)) rc = -1;
+    if (imkf_step(&M, R, mp, Pp, y + (size_t)k * m, mf + (size_t)k * n, Pf + (size_t)k * nn, &t, UBAR(k))) rc = -1;
     if (terms) terms[k] = t;
     acc += t;
   }

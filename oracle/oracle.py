@@ -39,12 +39,12 @@ def _load():
         build()
         lib = ctypes.CDLL(SO)
         i = ctypes.c_int
-        lib.oracle_srtm_sequential.argtypes = [i, i, i, i] + [_dp] * 7 + [i, i] + [_dp] * 8
-        lib.oracle_srtm_parallel.argtypes = [i, i, i, i] + [_dp] * 7 + [i, i] + [_dp] * 4
+        lib.oracle_srtm_sequential.argtypes = [i, i, i, i] + [_dp] * 7 + [i, i] + [_dp] * 8 + [i, _dp, _dp]
+        lib.oracle_srtm_parallel.argtypes = [i, i, i, i] + [_dp] * 7 + [i, i] + [_dp] * 4 + [i, _dp, _dp]
         lib.oracle_filter_op.argtypes = [i, _dp, _dp, _dp]
         lib.oracle_smoother_op.argtypes = [i, _dp, _dp, _dp]
         lib.oracle_lifted.argtypes = [i, i, i] + [_dp] * 8
-        lib.oracle_loglik.argtypes = [i, i, i, i] + [_dp] * 9
+        lib.oracle_loglik.argtypes = [i, i, i, i] + [_dp] * 9 + [i, _dp, _dp]
         for f in (lib.oracle_srtm_sequential, lib.oracle_srtm_parallel, lib.oracle_filter_op,
                   lib.oracle_smoother_op, lib.oracle_lifted, lib.oracle_loglik):
             f.restype = ctypes.c_int
@@ -62,6 +62,16 @@ def _p(a):
 def _inputs(prob):
     c = lambda a: np.ascontiguousarray(a, dtype=np.float64)  # noqa: E731
     return [c(prob.F), c(prob.Q), c(prob.H), c(prob.R), c(prob.m0), c(prob.P0), c(prob.y)]
+
+
+def _controls(prob):
+    """(nu, B, u) of the known inputs, or (0, None, None)."""
+    B, u = getattr(prob, "B", None), getattr(prob, "u", None)
+    if B is None or u is None:
+        return 0, None, None
+    c = lambda a: np.ascontiguousarray(a, dtype=np.float64)  # noqa: E731
+    B, u = c(B), c(u)
+    return B.shape[1], B, u
 
 
 def sequential(prob, k_lo: int = 0, k_hi: int | None = None, fast: bool = True,
@@ -89,8 +99,9 @@ def sequential(prob, k_lo: int = 0, k_hi: int | None = None, fast: bool = True,
     keys = ["slow_filt_mean", "slow_filt_cov", "first_smooth_mean", "first_smooth_cov",
             "fast_filt_mean", "fast_filt_cov", "fast_smooth_mean", "fast_smooth_cov"]
     ins = _inputs(prob)
+    nu, B, u = _controls(prob)
     rc = lib.oracle_srtm_sequential(n, m, l, N, *[_p(a) for a in ins], k_lo, k_hi,
-                                    *[_p(out.get(k)) for k in keys])
+                                    *[_p(out.get(k)) for k in keys], nu, _p(B), _p(u))
     if rc != 0:
         raise RuntimeError(f"oracle_srtm_sequential failed rc={rc}")
     return out
@@ -105,9 +116,11 @@ def parallel(prob, order: int = 0, flags: int = 0) -> dict:
     out = {k: np.zeros(s) for k, s in [("slow_filt_mean", (N, n)), ("slow_filt_cov", (N, n, n)),
                                        ("first_smooth_mean", (N, n)), ("first_smooth_cov", (N, n, n))]}
     ins = _inputs(prob)
+    nu, B, u = _controls(prob)
     rc = lib.oracle_srtm_parallel(n, m, l, N, *[_p(a) for a in ins], order, flags,
                                   *[_p(out[k]) for k in ["slow_filt_mean", "slow_filt_cov",
-                                                         "first_smooth_mean", "first_smooth_cov"]])
+                                                         "first_smooth_mean", "first_smooth_cov"]],
+                                  nu, _p(B), _p(u))
     if rc != 0:
         raise RuntimeError(f"oracle_srtm_parallel failed rc={rc}")
     return out
@@ -168,7 +181,8 @@ def loglik(prob, terms: bool = False):
     n, m, l, N = prob.F.shape[0], prob.H.shape[0], int(prob.ratio), prob.y.shape[0]
     t = np.zeros(N) if terms else None
     total = np.zeros(1)
-    rc = lib.oracle_loglik(n, m, l, N, *[_p(a) for a in _inputs(prob)], _p(t), _p(total))
+    nu, B, u = _controls(prob)
+    rc = lib.oracle_loglik(n, m, l, N, *[_p(a) for a in _inputs(prob)], _p(t), _p(total), nu, _p(B), _p(u))
     if rc != 0:
         raise RuntimeError(f"oracle_loglik failed rc={rc}")
     return (float(total[0]), t) if terms else float(total[0])

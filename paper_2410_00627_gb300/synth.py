@@ -39,6 +39,7 @@ class Problem:
     R: (ny,ny) measurement-noise covariance.  m0, P0: prior of x_0.
     y: (n_slow, ny) measurements; row k is y_{k+1} in the paper's 1-based index.
     x: optional (n_slow*ratio+1, nx) simulated fast states x_0, x_{1,1}, ..., x_{N,l}.
+    B, u: optional known inputs, x_{t+1} = F x_t + B u_t + w_t (Sec. II).
     """
 
     F: np.ndarray
@@ -52,6 +53,8 @@ class Problem:
     x: np.ndarray | None = None
     name: str = ""
     meta: dict = field(default_factory=dict)
+    B: np.ndarray | None = None   # (nx, nu) input matrix, or None
+    u: np.ndarray | None = None   # (n_slow*ratio, nu) inputs; row t drives x_{t+1}
 
     @property
     def nx(self) -> int:
@@ -82,7 +85,7 @@ def log_uniform(rng: np.random.Generator, lo: float, hi: float, size) -> np.ndar
 
 
 def simulate(rng: np.random.Generator, F, Q, H, R, m0, P0, ratio: int, n_slow: int,
-             keep_states: bool = True):
+             keep_states: bool = True, B=None, u=None):
     """Draw x_0 ~ N(m0,P0), run x_{t+1} = F x_t + w_t for n_slow*ratio fast steps
     and form y_k = H sum_{i=1..ratio} x_{k,i} + v_k.
 
@@ -99,6 +102,8 @@ def simulate(rng: np.random.Generator, F, Q, H, R, m0, P0, ratio: int, n_slow: i
     Lr = np.linalg.cholesky(R)
     x0 = m0 + np.linalg.cholesky(P0) @ rng.standard_normal(nx)
     w = (rng.standard_normal((N * l, nx)) @ Lq.T).reshape(N, l, nx)   # w[k, i-1]: noise into x_{k,i}
+    if B is not None:   # known inputs enter like the noise: B u_t + w_t drives x_{t+1}
+        w = w + (u @ B.T).reshape(N, l, nx)
     v = rng.standard_normal((N, ny)) @ Lr.T
     # e[k, i-1] = sum_{r<=i} F^{i-r} w[k, r-1]
     e = np.empty_like(w)
@@ -260,9 +265,10 @@ def config5(seed: int = 0, n_slow: int = 10_000, keep_states: bool = False) -> P
 
 
 def random_model(seed: int, nx: int, ny: int, ratio: int, n_slow: int,
-                 q_scale: float = 0.05, r_scale: float = 0.1) -> Problem:
+                 q_scale: float = 0.05, r_scale: float = 0.1, nu: int = 0) -> Problem:
     """Small generic model with dense (non-diagonal) Q, R and P0, a random
-    stable F and random H; used for pins and edge cases at tiny sizes."""
+    stable F and random H; used for pins and edge cases at tiny sizes.  With
+    nu > 0 also a random input matrix B and inputs u_t (a sinusoid plus noise)."""
     rng = np.random.default_rng(seed)
     A = rng.standard_normal((nx, nx))
     A *= 0.9 / max(1e-12, np.max(np.abs(np.linalg.eigvals(A))))
@@ -274,8 +280,13 @@ def random_model(seed: int, nx: int, ny: int, ratio: int, n_slow: int,
     m0 = rng.standard_normal(nx)
     Gp = rng.standard_normal((nx, nx))
     P0 = 0.2 * (Gp @ Gp.T / nx + 0.3 * np.eye(nx))
-    y, x = simulate(rng, A, Q, H, R, m0, P0, ratio, n_slow, True)
-    return Problem(A, Q, H, R, m0, P0, y, ratio, x, f"rand{nx}x{ny}l{ratio}N{n_slow}")
+    B = u = None
+    if nu > 0:
+        B = rng.standard_normal((nx, nu)) * 0.5
+        t = np.arange(n_slow * ratio)[:, None]
+        u = np.sin(0.07 * t + np.arange(nu)[None, :]) + 0.3 * rng.standard_normal((n_slow * ratio, nu))
+    y, x = simulate(rng, A, Q, H, R, m0, P0, ratio, n_slow, True, B, u)
+    return Problem(A, Q, H, R, m0, P0, y, ratio, x, f"rand{nx}x{ny}l{ratio}N{n_slow}u{nu}", B=B, u=u)
 
 
 CONFIGS = {1: config1, 2: config2, 3: config3, 4: config4, 5: config5}

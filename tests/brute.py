@@ -11,7 +11,7 @@ from __future__ import annotations
 import numpy as np
 
 
-def joint_prior(F, Q, m0, P0, T):
+def joint_prior(F, Q, m0, P0, T, B=None, u=None):
     n = F.shape[0]
     Apow = [np.eye(n)]
     for _ in range(T):
@@ -27,6 +27,9 @@ def joint_prior(F, Q, m0, P0, T):
     for s in range(T):
         Cxi[(1 + s) * n:(2 + s) * n, (1 + s) * n:(2 + s) * n] = Q
     mu = np.concatenate([Apow[t] @ m0 for t in range(T + 1)])
+    if B is not None:   # known inputs: x_t gains sum_{s<t} A^{t-1-s} B u_s
+        for t in range(1, T + 1):
+            mu[t * n:(t + 1) * n] += sum(Apow[t - 1 - s] @ (B @ u[s]) for s in range(t))
     return mu, Phi @ Cxi @ Phi.T
 
 
@@ -57,7 +60,7 @@ def posteriors(prob):
     (x_{k,i}|y_{1:N}) in the library's row order (k*l + i-1)."""
     F, Q, H, R, m0, P0, y, l = prob.F, prob.Q, prob.H, prob.R, prob.m0, prob.P0, prob.y, prob.ratio
     n, N = F.shape[0], y.shape[0]
-    mu, S = joint_prior(F, Q, m0, P0, N * l)
+    mu, S = joint_prior(F, Q, m0, P0, N * l, getattr(prob, "B", None), getattr(prob, "u", None))
     Hz = meas_matrix(H, n, l, N)
     ffm = np.zeros((N * l, n)); ffc = np.zeros((N * l, n, n))
     for k in range(N):
@@ -79,7 +82,7 @@ def loglik(prob):
     y = Hz z + v, so y ~ N(Hz mu, Hz S Hz^T + I_N (x) R)."""
     F, Q, H, R, m0, P0, y, l = prob.F, prob.Q, prob.H, prob.R, prob.m0, prob.P0, prob.y, prob.ratio
     n, N, m = F.shape[0], y.shape[0], H.shape[0]
-    mu, S = joint_prior(F, Q, m0, P0, N * l)
+    mu, S = joint_prior(F, Q, m0, P0, N * l, getattr(prob, "B", None), getattr(prob, "u", None))
     Hz = meas_matrix(H, n, l, N)
     Sy = Hz @ S @ Hz.T + np.kron(np.eye(N), R)
     r = y.ravel() - Hz @ mu

@@ -281,3 +281,43 @@ def test_planted_loglik_mistake_fails_the_dense_pin(oracle_mod):
     assert abs(total - ref) < 1e-10 * abs(ref)
     N, m = prob.y.shape
     assert abs((total + 0.5 * N * m * np.log(2 * np.pi)) - ref) > 1e-3 * abs(ref)
+
+
+# --------------------------------------------------------------------------- known inputs (B u)
+TINY_U = [
+    dict(seed=41, nx=2, ny=1, ratio=3, n_slow=4, nu=1),
+    dict(seed=42, nx=3, ny=2, ratio=4, n_slow=5, nu=2),
+    dict(seed=43, nx=1, ny=1, ratio=1, n_slow=6, nu=1),
+    dict(seed=44, nx=4, ny=3, ratio=2, n_slow=3, nu=3),
+]
+
+
+@pytest.mark.parametrize("kw", TINY_U, ids=lambda k: "n{nx}m{ny}l{ratio}N{n_slow}u{nu}".format(**k))
+def test_inputs_sequential_and_parallel_match_brute_force(oracle_mod, kw):
+    """With x_{t+1} = F x_t + B u_t + w_t the filter, the smoother, their
+    parallel forms and log p(y_1:N) match the dense joint posterior."""
+    prob = synth.random_model(kw["seed"], kw["nx"], kw["ny"], kw["ratio"], kw["n_slow"], nu=kw["nu"])
+    ref = brute.posteriors(prob)
+    out = oracle_mod.sequential(prob)
+    for key in ["fast_filt_mean", "fast_smooth_mean"]:
+        assert rel_mean(out[key], ref[key]) < 1e-11, key
+    for key in ["fast_filt_cov", "fast_smooth_cov"]:
+        assert rel_cov(out[key], ref[key]) < 1e-11, key
+    l = prob.ratio
+    par = oracle_mod.parallel(prob, order=1)
+    assert rel_mean(par["slow_filt_mean"], ref["fast_filt_mean"][l - 1::l]) < 1e-11
+    assert rel_mean(par["first_smooth_mean"], ref["fast_smooth_mean"][0::l]) < 1e-11
+    assert abs(oracle_mod.loglik(prob) - brute.loglik(prob)) < 1e-10 * abs(brute.loglik(prob))
+
+
+def test_zero_inputs_equal_no_inputs(oracle_mod):
+    prob = synth.random_model(45, 3, 2, 4, 6, nu=2)
+    base = synth.random_model(45, 3, 2, 4, 6, nu=2)
+    base.u = np.zeros_like(base.u)
+    plain = synth.Problem(base.F, base.Q, base.H, base.R, base.m0, base.P0, base.y, base.ratio)
+    a, b = oracle_mod.sequential(base), oracle_mod.sequential(plain)
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
+    assert oracle_mod.loglik(base) == oracle_mod.loglik(plain)
+    # and the inputs matter when they are not zero
+    assert rel_mean(oracle_mod.sequential(prob)["fast_smooth_mean"], b["fast_smooth_mean"]) > 1e-3

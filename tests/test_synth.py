@@ -68,3 +68,21 @@ def test_config4_parallel_build_equals_serial_and_packs():
     off = np.concatenate([[0], np.cumsum(pk["n_slow"])])
     for s, p in enumerate(a):
         assert np.array_equal(pk["y"][off[s]:off[s + 1]], p.y)
+
+
+def test_simulation_with_inputs_matches_stepwise_recursion():
+    """x_{t+1} = F x_t + B u_t + w_t: the vectorised simulator equals the step loop."""
+    p = synth.random_model(17, 3, 2, 4, 6, nu=2)
+    n, m, l, N = 3, 2, 4, 6
+    y, x = synth.simulate(np.random.default_rng(5), p.F, p.Q, p.H, p.R, p.m0, p.P0, l, N, True, p.B, p.u)
+    rng = np.random.default_rng(5)
+    x0 = p.m0 + np.linalg.cholesky(p.P0) @ rng.standard_normal(n)
+    w = (rng.standard_normal((N * l, n)) @ np.linalg.cholesky(p.Q).T)
+    v = rng.standard_normal((N, m)) @ np.linalg.cholesky(p.R).T
+    xs, yy = [x0], np.zeros((N, m))
+    for t in range(N * l):
+        xs.append(p.F @ xs[-1] + p.B @ p.u[t] + w[t])
+        if (t + 1) % l == 0:
+            yy[t // l] = p.H @ np.sum(xs[-l:], axis=0) + v[t // l]
+    assert np.allclose(x, np.array(xs), rtol=0, atol=1e-12)
+    assert np.allclose(y, yy, rtol=0, atol=1e-12)
