@@ -72,11 +72,20 @@ enum {
  *   H  ny*nx   integrated-measurement matrix (applies to the sum of l states)
  *   R  ny*ny   measurement-noise covariance
  *   m0 nx, P0 nx*nx   prior of x_0
- *   y  n_slow*ny      y_k in row k-1                                          */
+ *   y  n_slow*ny      y_k in row k-1
+ * Known inputs (Sec. II: x_{t+1} = F x_t + B u_t + w_t), optional:
+ *   nu                number of inputs, 0..SRTM_MAX_NU (0: no inputs, B and u
+ *                     are ignored)
+ *   B  nx*nu          input matrix
+ *   u  n_slow*ratio*nu  u_t in row t (t = 0 .. n_slow*ratio-1); row t drives
+ *                     x_{t+1}, so interval k uses rows (k-1)*ratio .. k*ratio-1 */
+#define SRTM_MAX_NU 4
 typedef struct {
   int nx, ny, ratio, n_slow;
   const double *F, *Q, *H, *R, *m0, *P0;
   const double *y;
+  int nu;
+  const double *B, *u;
 } srtm_problem;
 
 /* Caller-allocated outputs; any pointer may be NULL (that output is skipped).
@@ -100,6 +109,8 @@ typedef struct {
  *   y          rows of all sequences concatenated in order (total_slow rows)
  *   max_ratio  host-side upper bound of ratio[]
  *   total_slow host-side sum of n_slow[]; total_fast = sum of n_slow[s]*ratio[s]
+ *   nu, B, u   optional known inputs: B packed per sequence (B + s*nx*nu), u
+ *              rows of all sequences concatenated in order (total_fast rows)
  * Outputs are concatenated the same way (fast rows in sequence order, then
  * slow rows in sequence order).  Metadata that disagrees with total_slow,
  * total_fast or max_ratio is detected on the device: nothing is computed and
@@ -110,6 +121,8 @@ typedef struct {
   const int *ratio, *n_slow;
   const double *F, *Q, *H, *R, *m0, *P0;
   const double *y;
+  int nu;
+  const double *B, *u;
 } srtm_batch;
 
 /* Filtering p(x_{k,i} | y_{1:k}): slow IMKF by the parallel scan (Eq. 25-27)

@@ -31,7 +31,8 @@ STAGES = ("metadata", "constants", "filter_scan", "interval_setup", "smoother_sc
 class Problem(ctypes.Structure):
     _fields_ = [("nx", c_int), ("ny", c_int), ("ratio", c_int), ("n_slow", c_int),
                 ("F", c_void_p), ("Q", c_void_p), ("H", c_void_p), ("R", c_void_p),
-                ("m0", c_void_p), ("P0", c_void_p), ("y", c_void_p)]
+                ("m0", c_void_p), ("P0", c_void_p), ("y", c_void_p),
+                ("nu", c_int), ("B", c_void_p), ("u", c_void_p)]
 
 
 class Output(ctypes.Structure):
@@ -43,7 +44,8 @@ class Batch(ctypes.Structure):
                 ("total_slow", c_longlong), ("total_fast", c_longlong),
                 ("ratio", c_void_p), ("n_slow", c_void_p),
                 ("F", c_void_p), ("Q", c_void_p), ("H", c_void_p), ("R", c_void_p),
-                ("m0", c_void_p), ("P0", c_void_p), ("y", c_void_p)]
+                ("m0", c_void_p), ("P0", c_void_p), ("y", c_void_p),
+                ("nu", c_int), ("B", c_void_p), ("u", c_void_p)]
 
 
 class Tuning(ctypes.Structure):
@@ -145,19 +147,25 @@ def _alloc_outputs(keys, device, rows_fast, rows_slow, nx, out=None, n_seq=1):
     return res, o
 
 
-def _problem(F, Q, H, R, m0, P0, y, ratio):
+def _problem(F, Q, H, R, m0, P0, y, ratio, B=None, u=None):
     nx, ny = F.shape[0], H.shape[0]
     n_slow = y.shape[0]
+    nu, pB, pu = 0, None, None
+    if B is not None:
+        nu = B.shape[1]
+        pB, pu = _dev_tensor(B, "B", (nx, nu)), _dev_tensor(u, "u", (n_slow * int(ratio), nu))
     return Problem(nx, ny, int(ratio), n_slow, _dev_tensor(F, "F", (nx, nx)), _dev_tensor(Q, "Q", (nx, nx)),
                    _dev_tensor(H, "H", (ny, nx)), _dev_tensor(R, "R", (ny, ny)), _dev_tensor(m0, "m0", (nx,)),
-                   _dev_tensor(P0, "P0", (nx, nx)), _dev_tensor(y, "y", (n_slow, ny)))
+                   _dev_tensor(P0, "P0", (nx, nx)), _dev_tensor(y, "y", (n_slow, ny)), nu, pB, pu)
 
 
 def smoother(F, Q, H, R, m0, P0, y, ratio, precision="fp64", outputs=OUTPUT_KEYS, filtered=(),
-             stream=None, out=None, out_filtered=None):
+             stream=None, out=None, out_filtered=None, B=None, u=None):
     """p(x_{k,i} | y_{1:N}) for one sequence.  Returns (smoothed, filtered) dicts
-    of CUDA tensors keyed by fast_mean / fast_cov / slow_mean / slow_cov."""
-    prob = _problem(F, Q, H, R, m0, P0, y, ratio)
+    of CUDA tensors keyed by fast_mean / fast_cov / slow_mean / slow_cov (and
+    loglik when asked for).  B (nx, nu) and u (n_slow*ratio, nu): optional
+    known inputs, x_{t+1} = F x_t + B u_t + w_t."""
+    prob = _problem(F, Q, H, R, m0, P0, y, ratio, B, u)
     rows_fast, rows_slow = prob.n_slow * prob.ratio, prob.n_slow
     sm, so = _alloc_outputs(outputs, y.device, rows_fast, rows_slow, prob.nx, out)
     fi, fo = _alloc_outputs(filtered, y.device, rows_fast, rows_slow, prob.nx, out_filtered)
@@ -167,28 +175,34 @@ def smoother(F, Q, H, R, m0, P0, y, ratio, precision="fp64", outputs=OUTPUT_KEYS
     return sm, fi
 
 
-def filter(F, Q, H, R, m0, P0, y, ratio, precision="fp64", outputs=OUTPUT_KEYS, stream=None, out=None):  # noqa: A001
+def filter(F, Q, H, R, m0, P0, y, ratio, precision="fp64", outputs=OUTPUT_KEYS, stream=None, out=None,  # noqa: A001
+           B=None, u=None):
     """p(x_{k,i} | y_{1:k}) for one sequence."""
-    prob = _problem(F, Q, H, R, m0, P0, y, ratio)
+    prob = _problem(F, Q, H, R, m0, P0, y, ratio, B, u)
     res, o = _alloc_outputs(outputs, y.device, prob.n_slow * prob.ratio, prob.n_slow, prob.nx, out)
     _check(load().srtm_filter(ctypes.byref(prob), PRECISION[precision], ctypes.byref(o), _stream_handle(stream)))
     return res
 
 
-def make_batch(F, Q, H, R, m0, P0, y, ratio, n_slow, max_ratio, total_slow, total_fast):
+def make_batch(F, Q, H, R, m0, P0, y, ratio, n_slow, max_ratio, total_slow, total_fast, B=None, u=None):
     """Batch descriptor over packed CUDA tensors: F (S,nx,nx), Q, H (S,ny,nx), R, m0 (S,nx),
-    P0, y (total_slow, ny) and CUDA int32 tensors ratio (S,), n_slow (S,)."""
+    P0, y (total_slow, ny) and CUDA int32 tensors ratio (S,), n_slow (S,); optional
+    inputs B (S,nx,nu) and u (total_fast, nu)."""
     import torch
     S, nx, ny = F.shape[0], F.shape[1], H.shape[1]
     for t, nm in ((ratio, "ratio"), (n_slow, "n_slow")):
         if not (t.is_cuda and t.dtype == torch.int32 and t.is_contiguous() and tuple(t.shape) == (S,)):
             raise TypeError(f"{nm} must be a contiguous CUDA int32 tensor of shape ({S},)")
+    nu, pB, pu = 0, None, None
+    if B is not None:
+        nu = B.shape[2]
+        pB, pu = _dev_tensor(B, "B", (S, nx, nu)), _dev_tensor(u, "u", (int(total_fast), nu))
     return Batch(S, nx, ny, int(max_ratio), int(total_slow), int(total_fast),
                  c_void_p(ratio.data_ptr()), c_void_p(n_slow.data_ptr()),
                  _dev_tensor(F, "F", (S, nx, nx)), _dev_tensor(Q, "Q", (S, nx, nx)),
                  _dev_tensor(H, "H", (S, ny, nx)), _dev_tensor(R, "R", (S, ny, ny)),
                  _dev_tensor(m0, "m0", (S, nx)), _dev_tensor(P0, "P0", (S, nx, nx)),
-                 _dev_tensor(y, "y", (int(total_slow), ny)))
+                 _dev_tensor(y, "y", (int(total_slow), ny)), nu, pB, pu)
 
 
 def smoother_batch(batch: Batch, precision="fp64", outputs=OUTPUT_KEYS, filtered=(), stream=None,
@@ -212,10 +226,12 @@ def filter_batch(batch: Batch, precision="fp64", outputs=OUTPUT_KEYS, stream=Non
     return res
 
 
-def smoother_host(F, Q, H, R, m0, P0, y, ratio, precision="fp64", out=None, stream=None, loglik=False):
+def smoother_host(F, Q, H, R, m0, P0, y, ratio, precision="fp64", out=None, stream=None, loglik=False, B=None,
+                  u=None):
     """Host-buffer entry point: numpy float64 inputs/outputs (pinned or pageable
     memory); the library copies to the GPU, runs the smoother, copies back and
-    synchronizes.  ``out`` may hold preallocated (e.g. pinned) output arrays."""
+    synchronizes.  ``out`` may hold preallocated (e.g. pinned) output arrays;
+    B (nx, nu) and u (n_slow*ratio, nu) are optional known inputs."""
     import numpy as np
 
     def host(a, name, shape):
@@ -226,8 +242,13 @@ def smoother_host(F, Q, H, R, m0, P0, y, ratio, precision="fp64", out=None, stre
         return c_void_p(a.ctypes.data)
 
     nx, ny, N = F.shape[0], H.shape[0], y.shape[0]
+    nu, pB, pu = 0, None, None
+    if B is not None:
+        nu = B.shape[1]
+        pB, pu = host(B, "B", (nx, nu)), host(u, "u", (N * int(ratio), nu))
     prob = Problem(nx, ny, int(ratio), N, host(F, "F", (nx, nx)), host(Q, "Q", (nx, nx)), host(H, "H", (ny, nx)),
-                   host(R, "R", (ny, ny)), host(m0, "m0", (nx,)), host(P0, "P0", (nx, nx)), host(y, "y", (N, ny)))
+                   host(R, "R", (ny, ny)), host(m0, "m0", (nx,)), host(P0, "P0", (nx, nx)), host(y, "y", (N, ny)),
+                   nu, pB, pu)
     shapes = {"fast_mean": (N * ratio, nx), "fast_cov": (N * ratio, nx, nx), "slow_mean": (N, nx),
               "slow_cov": (N, nx, nx)}
     if loglik:
@@ -260,10 +281,10 @@ def get_tuning(nx: int, precision: str) -> dict:
     return {k: getattr(t, k) for k, _ in Tuning._fields_}
 
 
-def autotune(F, Q, H, R, m0, P0, y, ratio, precision="mixed", reps=2, stream=None, out=None):
+def autotune(F, Q, H, R, m0, P0, y, ratio, precision="mixed", reps=2, stream=None, out=None, B=None, u=None):
     """Search the launch shapes for this problem (srtm_autotune) and keep the
     fastest for (nx, precision).  Returns (tuning dict, milliseconds per call)."""
-    prob = _problem(F, Q, H, R, m0, P0, y, ratio)
+    prob = _problem(F, Q, H, R, m0, P0, y, ratio, B, u)
     _, so = _alloc_outputs(OUTPUT_KEYS, y.device, prob.n_slow * prob.ratio, prob.n_slow, prob.nx, out)
     t, ms = Tuning(), ctypes.c_float()
     _check(load().srtm_autotune(ctypes.byref(prob), PRECISION[precision], ctypes.byref(so), int(reps),

@@ -83,7 +83,8 @@ struct PreGeom {
   static constexpr int T = y0 + MY, Vs = T + NN, HVs = Vs + NN, Rx = HVs + NM, Rxi = Rx + MM, GQM = Rxi + MM,
                        K = GQM + NM, Cr = K + NM, Cb = Cr + NM, Fc = Cb + NM, Dc = Fc + NN, Jc = Dc + NN,
                        AP = Jc + NN, CP = AP + NN, cross = CP + NM, S1 = cross + NM, S1i = S1 + MM, Lg = S1i + MM,
-                       innov = Lg + NM, P1 = innov + MY, P1o = P1 + NN, m1 = P1o + NN, USCR = m1 + NX;
+                       innov = Lg + NM, P1 = innov + MY, P1o = P1 + NN, m1 = P1o + NN, bu = m1 + NX,
+                       sbu = bu + NX, USCR = sbu + NX;  // bu, sbu: first interval's b_{1,l}, sum_i b_{1,i}
   static constexpr int BASE = USCR + NU * NN;  // per-unit n x n scratch, then the tables
   // tables: A^0..A^L, S_0..S_{L-1}, Cov(e_i) terms / prefixes, two V buffers
   __host__ __device__ static size_t tables(int L) { return (size_t)(5 * L + 1) * NN; }
@@ -213,6 +214,21 @@ __global__ void __launch_bounds__(PRE_THREADS) precompute_kernel(Ctx c, int tabl
   }
   __syncthreads();
   // 4. W_i = Q S_{l-i}^T (i = 1..l), Cov(e_i, e_l) = Qc_i A^{(l-i)T}, C_bar = H T
+  // known inputs: A^j B and S_j B (j < l), n x nu blocks, into the model table
+  if (c.nu > 0) {
+    const int nu = c.nu;
+    const double* B = c.B + (long long)s * NX * nu;
+    for (int e = tid; e < l * NX * nu; e += nt) {
+      const int j = e / (NX * nu), rc = e - j * NX * nu, r = rc / nu, q = rc - (rc / nu) * nu;
+      double a = 0.0, b = 0.0;
+      for (int k = 0; k < NX; ++k) {
+        a = fma(Ap[(size_t)j * NN + r * NX + k], B[k * nu + q], a);
+        b = fma(Sp[(size_t)j * NN + r * NX + k], B[k * nu + q], b);
+      }
+      md[L.AB + e] = a;
+      md[L.SB + e] = b;
+    }
+  }
   for (int t = unit; t <= 2 * l; t += NU) {
     if (t < l) {
       const int i = t + 1;
@@ -261,6 +277,21 @@ __global__ void __launch_bounds__(PRE_THREADS) precompute_kernel(Ctx c, int tabl
     for (size_t e = tid; e < (size_t)(l + 1) * NN; e += nt) md[L.Apow + e] = Ap[e];
     for (size_t e = tid; e < (size_t)l * NN; e += nt) md[L.Qc + e] = Qp[e];
   }
+  // first interval's input terms b_{1,l} = sum_r A^{l-1-r} B u_r and sum_i b_{1,i} = sum_r S_{l-1-r} B u_r
+  for (int r = tid; r < NX; r += nt) {
+    double b = 0.0, sb = 0.0;
+    if (c.nu > 0) {
+      const int nu = c.nu;
+      const double* u0 = c.u + c.meta.off_fast[s] * nu;
+      for (int q = 0; q < l; ++q)
+        for (int j = 0; j < nu; ++j) {
+          b = fma(md[L.AB + ((size_t)(l - 1 - q) * NX + r) * nu + j], u0[q * nu + j], b);
+          sb = fma(md[L.SB + ((size_t)(l - 1 - q) * NX + r) * nu + j], u0[q * nu + j], sb);
+        }
+    }
+    sm[S::bu + r] = b;
+    sm[S::sbu + r] = sb;
+  }
   __syncthreads();
   for (int e = tid; e < m * NX; e += nt) md[L.Cb + e] = sm[S::Cb + e];
   {  // float copies of A, Qc_1, Cov(e_1, e_l), V_1 H^T for the float32 smoother elements
@@ -279,9 +310,10 @@ __global__ void __launch_bounds__(PRE_THREADS) precompute_kernel(Ctx c, int tabl
   if (unit == 1) u_mm<NX, NX, NX, G, false, false>(lane, NX, NX, NX, sm + S::AP, Al, sm + S::P0, nullptr, 1.0);
   if (unit == 2) u_mm<MY, NX, NX, G, false, false>(lane, m, NX, NX, sm + S::CP, sm + S::Cb, sm + S::P0, nullptr, 1.0);
   if (unit == 3)
-    for (int j = lane; j < m; j += G) {
+    for (int j = lane; j < m; j += G) {   // y_1 - C_bar m0 - H sum_i b_{1,i}
       double v = sm[S::y0 + j];
       for (int q = 0; q < NX; ++q) v = fma(-sm[S::Cb + j * NX + q], sm[S::m0 + q], v);
+      for (int q = 0; q < NX; ++q) v = fma(-sm[S::H + j * NX + q], sm[S::sbu + q], v);
       sm[S::innov + j] = v;
     }
   __syncthreads();
@@ -311,7 +343,7 @@ __global__ void __launch_bounds__(PRE_THREADS) precompute_kernel(Ctx c, int tabl
   __syncthreads();
   if (unit == 0)
     for (int r = lane; r < NX; r += G) {
-      double v = 0.0;
+      double v = sm[S::bu + r];
       for (int q = 0; q < NX; ++q) v = fma(Al[r * NX + q], sm[S::m0 + q], v);
       for (int j = 0; j < m; ++j) v = fma(sm[S::Lg + r * m + j], sm[S::innov + j], v);
       sm[S::m1 + r] = v;

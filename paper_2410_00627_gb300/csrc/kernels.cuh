@@ -47,7 +47,9 @@ struct SetupGeom {
 //   P^f_11 = A P A^T + Qc_1 - U_1 S_y^-1 U_1^T,
 //   P^f_1l = A (P A^{lT}) + Cov(e_1,e_l) - U_1 (S_y^-1 U_l^T),
 //   E = P^f_1l Z,  g = m^f_1 - E A m^f_l,  S = P^f_11 - E A (P^f_1l)^T
-// (reading A7 for S).  Inputs: P, Pl, X, SUl, Z, ml, mv (slot arrays) and
+// (reading A7 for S); with known inputs m^f_1 gains b_{k,1} and the
+// prediction A m^f_l gains B u_{k,l} (b1, bnx; NULL without inputs).
+// Inputs: P, Pl, X, SUl, Z, ml, mv (slot arrays) and
 // the model's A, Qc_1, Cov(e_1,e_l), V_1 H^T (cA, cQc, cQl, cVH; row-major,
 // V_1 H^T with row stride m).  Work arrays: U1 (NX x MY), P1l, P11, Aml and
 // AP1 (NX x NX, A P1l^T; may alias U1 when that holds NX x NX entries).
@@ -56,7 +58,8 @@ __device__ __forceinline__ void setup_elements(int r, bool row, unsigned mask, i
                                                const TE* Pl, const TE* X, const TE* SUl, const TE* Z, const TE* ml,
                                                const TE* mv, const TC* cA, const TC* cQc, const TC* cQl,
                                                const TC* cVH, const TE (&Si)[MY][MY], const TE (&kap)[MY], TE* U1,
-                                               TE* P1l, TE* P11, TE* Aml, TE* AP1, T* se) {
+                                               TE* P1l, TE* P11, TE* Aml, TE* AP1, T* se, const double* b1,
+                                               const double* bnx) {
   using SLy = SL<NX>;
   TE U1r[MY], m1 = TE(0);
   if (row) {
@@ -79,6 +82,10 @@ __device__ __forceinline__ void setup_elements(int r, bool row, unsigned mask, i
     TE aml = TE(0);
 #pragma unroll
     for (int t = 0; t < NX; ++t) aml = fma((TE)cA[r * NX + t], ml[t], aml);
+    if (b1) {  // known inputs: b_{k,1} = B u_{k,0} and the prediction's B u_{k,l}
+      m1 += (TE)b1[r];
+      aml += (TE)bnx[r];
+    }
     Aml[r] = aml;
   }
   __syncwarp(mask);
@@ -228,9 +235,10 @@ __device__ void setup_interval(const Ctx& c, long long gi, int lane, unsigned ma
       sb[Gm::Sy + j * MY + i] = v;
     }
   }
+  const double* ui = c.uin ? c.uin + gi * UIn<NX>::SIZE : nullptr;
   if (lane < m) {
     const double* yk = c.y + gi * m;
-    TR v = (TR)yk[lane];
+    TR v = (TR)(ui ? yk[lane] - ui[UIn<NX>::c + lane] : yk[lane]);
 #pragma unroll
     for (int q = 0; q < NX; ++q) v = fma(-(TR)Cb[lane * NX + q], sb[Gm::mv + q], v);
     sb[Gm::ev + lane] = v;
@@ -285,7 +293,7 @@ __device__ void setup_interval(const Ctx& c, long long gi, int lane, unsigned ma
         if (i < m && j < m) v = fma(Si[i][j], Ul[j], v);
       sb[Gm::SUl + i * NX + r] = v;
     }
-    TR v = TR(0);
+    TR v = ui ? (TR)ui[UIn<NX>::bl + r] : TR(0);
 #pragma unroll
     for (int q = 0; q < NX; ++q) v = fma((TR)Al[r * NX + q], sb[Gm::mv + q], v);
 #pragma unroll
@@ -450,7 +458,8 @@ __device__ void setup_interval(const Ctx& c, long long gi, int lane, unsigned ma
       setup_elements<NX, TR, double, T>(r, row, mask, m, last, sb + Gm::P, sb + Gm::Pl, sb + Gm::X, sb + Gm::SUl,
                                         sb + Gm::Z, sb + Gm::ml, sb + Gm::mv, A1, md + c.ml.Qc, md + c.ml.Ql,
                                         md + c.ml.VH, Si, kap, sb + Gm::U1, sb + Gm::P1l, sb + Gm::P11,
-                                        sb + Gm::Aml, sb + Gm::AP1, se);
+                                        sb + Gm::Aml, sb + Gm::AP1, se, ui ? ui + UIn<NX>::b1 : nullptr,
+                                        ui ? ui + UIn<NX>::bn : nullptr);
     } else {
       // float copies of this lane's rows, then the elements in float32
       if (row) {
@@ -480,7 +489,8 @@ __device__ void setup_interval(const Ctx& c, long long gi, int lane, unsigned ma
       setup_elements<NX, T, T, T>(r, row, mask, m, last, sf + Gm::fP, sf + Gm::fPl, sf + Gm::fX, sf + Gm::fSUl,
                                   sf + Gm::fZ, sf + Gm::fml, sf + Gm::fmv, cf + Gm::cA, cf + Gm::cQc, cf + Gm::cQl,
                                   cf + Gm::cVH, Sif, kapf, sf + Gm::fU1, sf + Gm::fP1l, sf + Gm::fP11,
-                                  sf + Gm::fAml, sf + Gm::fU1, se);
+                                  sf + Gm::fAml, sf + Gm::fU1, se, ui ? ui + UIn<NX>::b1 : nullptr,
+                                  ui ? ui + UIn<NX>::bn : nullptr);
     }
   }
   if (!ok && lane == 0) raise_err(c.ctr, DEVERR_SINGULAR);
@@ -529,11 +539,14 @@ struct FilterOp {
       x[L::J + e] = (T)md[c.ml.Jc + e];
     }
     const int m = c.ny;
-    const double* yk = c.y + (c.meta.off_slow[s] + p) * m;
+    const long long row = c.meta.off_slow[s] + p;
+    const double* yk = c.y + row * m;
+    // with inputs: y_k - c_k enters K and C_bar^T R_x^-1, and d_k gains b_{k,l}
+    const double* ui = c.uin ? c.uin + row * UIn<NX>::SIZE : nullptr;
     for (int r = g.lane; r < NX; r += G) {
-      double dv = 0.0, ev = 0.0;
+      double dv = ui ? ui[UIn<NX>::bl + r] : 0.0, ev = 0.0;
       for (int j = 0; j < m; ++j) {
-        const double yj = yk[j];
+        const double yj = ui ? yk[j] - ui[UIn<NX>::c + j] : yk[j];
         dv = fma(md[c.ml.K + r * m + j], yj, dv);
         ev = fma(md[c.ml.Cr + r * m + j], yj, ev);
       }
@@ -637,6 +650,8 @@ struct SmootherOp {
     TR* out = (TR*)c.sfin + row * SFin<NX>::SIZE;
     for (int e = g.lane; e < NN; e += G) dP[e] = (TR)x[L::S + e] - rc[RL::Pm + e];
     g_mv<NX, G, false, TR>(g, dm, A1, rc + RL::ml, x + L::g, TR(-1));
+    if (c.uin)  // the prediction m^-_{k,1} = A m^f_{k-1,l} + B u_{k-1,l}; same lane per entry as g_mv
+      for (int e = g.lane; e < NX; e += G) dm[e] -= (TR)c.uin[row * UIn<NX>::SIZE + UIn<NX>::bn + e];
     g.sync();
     g_mm<NX, G, false, false, TR>(g, ZdP, rc + RL::Z, dP, (const TR*)nullptr);
     g_mv<NX, G, false, TR>(g, out + NN, rc + RL::Z, dm, (const TR*)nullptr);
@@ -1043,7 +1058,7 @@ __device__ __forceinline__ void recover_filtered(const Ctx& c, const FastIdx& x,
       }
       U[r][jj] = v;
     }
-  // m^f_i = A^i m + U_i kap
+  // m^f_i = A^i m + U_i kap (+ b_{k,i} = sum_{q<i} A^{i-1-q} B u_{k,q} with inputs)
 #pragma unroll
   for (int r = 0; r < NX; ++r) {
     TR v = TR(0);
@@ -1053,6 +1068,18 @@ __device__ __forceinline__ void recover_filtered(const Ctx& c, const FastIdx& x,
     for (int jj = 0; jj < MY; ++jj)
       if (jj < m) v = fma(U[r][jj], rc[RL::kap + jj], v);
     mf[r] = v;
+  }
+  if (c.nu > 0) {
+    const int nu = c.nu;
+    const double* uk = c.u + (c.meta.off_fast[x.s] + x.k * x.l) * nu;
+    const double* AB = md + c.ml.AB;
+    for (int q = 0; q < i; ++q)
+      for (int j = 0; j < nu; ++j) {
+        const double uq = __ldg(uk + q * nu + j);
+        const double* ab = AB + ((long long)(i - 1 - q) * NX) * nu + j;
+#pragma unroll
+        for (int r = 0; r < NX; ++r) mf[r] = fma((TR)__ldg(ab + r * nu), (TR)uq, mf[r]);
+      }
   }
   // P^f_il = A^i Pl + Cov(e_i,e_l) - U_i SUl
   if (need_pfl) {
@@ -1208,6 +1235,64 @@ __global__ void __launch_bounds__(128, 3) recover_kernel(Ctx c) {
 }
 
 // ===========================================================================
+// per-interval input terms (known inputs only): one thread per interval,
+// from the model's A^j B and S_j B tables (ld nu, j < l):
+//   b_{k,l} = sum_q A^{l-1-q} B u_{k,q},   b_{k,1} = B u_{k,0},
+//   B u_{k,l} = B u_{k+1,0} (0 for the last interval),
+//   c_k = H sum_i b_{k,i} = H sum_q S_{l-1-q} B u_{k,q}
+// ===========================================================================
+template <int NX>
+__global__ void __launch_bounds__(128) input_kernel(Ctx c) {
+  using UI = UIn<NX>;
+  if (!c.ctr->call_ok) return;
+  const long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (gi >= c.total_slow) return;
+  const int s = find_segment(c.meta.off_slow, c.n_seq, gi);
+  const long long k = gi - c.meta.off_slow[s];
+  const int l = c.meta.ratio[s], N = c.meta.nslow[s], nu = c.nu, m = c.ny;
+  const double* md = c.model + (long long)s * c.ml.stride;
+  const double* B = c.B + (long long)s * NX * nu;
+  const double* H = c.H + (long long)s * m * NX;
+  const double* uk = c.u + (c.meta.off_fast[s] + k * l) * nu;
+  double bl[NX], sb[NX], b1[NX], bn[NX];
+#pragma unroll
+  for (int r = 0; r < NX; ++r) bl[r] = sb[r] = b1[r] = bn[r] = 0.0;
+  for (int q = 0; q < l; ++q)
+    for (int j = 0; j < nu; ++j) {
+      const double uq = uk[q * nu + j];
+      const double* ab = md + c.ml.AB + ((long long)(l - 1 - q) * NX) * nu + j;
+      const double* sbt = md + c.ml.SB + ((long long)(l - 1 - q) * NX) * nu + j;
+#pragma unroll
+      for (int r = 0; r < NX; ++r) {
+        bl[r] = fma(ab[r * nu], uq, bl[r]);
+        sb[r] = fma(sbt[r * nu], uq, sb[r]);
+      }
+    }
+  for (int j = 0; j < nu; ++j) {
+    const double u0 = uk[j], un = (k < N - 1) ? uk[l * nu + j] : 0.0;
+#pragma unroll
+    for (int r = 0; r < NX; ++r) {
+      b1[r] = fma(B[r * nu + j], u0, b1[r]);
+      bn[r] = fma(B[r * nu + j], un, bn[r]);
+    }
+  }
+  double* out = c.uin + gi * UI::SIZE;
+#pragma unroll
+  for (int r = 0; r < NX; ++r) {
+    out[UI::bl + r] = bl[r];
+    out[UI::b1 + r] = b1[r];
+    out[UI::bn + r] = bn[r];
+  }
+  for (int i = 0; i < MY; ++i) {
+    double v = 0.0;
+    if (i < m)
+#pragma unroll
+      for (int r = 0; r < NX; ++r) v = fma(H[i * NX + r], sb[r], v);
+    out[UI::c + i] = v;
+  }
+}
+
+// ===========================================================================
 // interval setup as its own kernel (after the filter scan): blocks of 128
 // threads, SG lanes per interval, one interval per lane group.
 // ===========================================================================
@@ -1302,6 +1387,7 @@ int launch_t(const Ctx& c, const Shapes& sh, cudaStream_t st, cudaEvent_t* ev) {
   using SOp = SmootherOp<NX, T, TR>;
   constexpr int G = FOp::G;
   launch_precompute<NX>(c, st);
+  if (c.uin) input_kernel<NX><<<(unsigned)((c.total_slow + 127) / 128), 128, 0, st>>>(c);
   if (ev) cudaEventRecord(ev[0], st);
   scan_kernel<FOp><<<sh.grid_f, sh.scan_groups_f * G, sh.smem_f, st>>>(c, sh.scan_groups_f, sh.scan_elems_f, sh.window_f);
   if (ev) cudaEventRecord(ev[1], st);

@@ -83,13 +83,13 @@ size_t a16(size_t x) { return (x + 15) / 16 * 16; }
 
 struct Layout {
   size_t ctr, ratio, nslow, off_slow, off_fast, tile_f, tile_s, model, ftile, stile, fout, rec, selem, sfin, lterm,
-      total;
+      uin, total;
   long long ftile_stride, stile_stride;
   ModelLayout ml;
 };
 
 Layout make_layout(int nx, int ny, int max_ratio, int n_seq, long long total_slow, srtm_precision prec, int tile_f,
-                   int tile_s) {
+                   int tile_s, int nu) {
   Layout L;
   const size_t sT = prec == SRTM_FP64 ? 8 : 4, sR = prec == SRTM_FP32 ? 4 : 8;
   const long long nn = (long long)nx * nx;
@@ -119,6 +119,7 @@ Layout make_layout(int nx, int ny, int max_ratio, int n_seq, long long total_slo
   L.selem = take(sT * (size_t)SE * total_slow);
   L.sfin = take(sR * (size_t)SFN * total_slow);
   L.lterm = take(sizeof(double) * (size_t)total_slow);
+  L.uin = take(nu > 0 ? sizeof(double) * (size_t)(3 * nx + MY) * total_slow : 0);
   L.total = a256(o);
   return L;
 }
@@ -205,7 +206,7 @@ int run(Ctx c, srtm_precision prec, cudaStream_t st) {
   int rc = shapes_for(c.nx, prec, t, d.sms, c.total_slow, c.n_seq, &sh);
   if (rc) return fail(rc, "launch shape query failed (%d)", rc);
   const int tile_f = sh.scan_groups_f * sh.scan_elems_f, tile_s = sh.scan_groups_s * sh.scan_elems_s;
-  const Layout L = make_layout(c.nx, c.ny, c.max_ratio, c.n_seq, c.total_slow, prec, tile_f, tile_s);
+  const Layout L = make_layout(c.nx, c.ny, c.max_ratio, c.n_seq, c.total_slow, prec, tile_f, tile_s, c.nu);
   if (d.ws_bytes < L.total) {
     if (d.ws) {
       cudaDeviceSynchronize();
@@ -252,10 +253,12 @@ int run(Ctx c, srtm_precision prec, cudaStream_t st) {
   c.selem = w + L.selem;
   c.sfin = w + L.sfin;
   c.lterm = (double*)(w + L.lterm);
+  c.uin = c.nu > 0 ? (double*)(w + L.uin) : nullptr;
   c.tile_f = tile_f;
   c.tile_s = tile_s;
   c.setup_separate = t.setup_mode == 2 ? 1 : 0;
-  d.last_launches = (c.fold_meta ? 0 : 1) + 3 + (c.smoothing ? 1 : 0) + c.setup_separate + (c.loglik ? 1 : 0);
+  d.last_launches = (c.fold_meta ? 0 : 1) + 3 + (c.smoothing ? 1 : 0) + c.setup_separate + (c.loglik ? 1 : 0) +
+                    (c.nu > 0 ? 1 : 0);
   cudaEvent_t* ev = nullptr;
   if (g_timing) {
     if (!d.ev[0])
@@ -298,6 +301,15 @@ int check_inputs(const double* F, const double* Q, const double* H, const double
   return SRTM_OK;
 }
 
+// Known inputs: nu in 0..SRTM_MAX_NU; with nu > 0, B and u are device arrays.
+int check_controls(int nu, const double* B, const double* u) {
+  if (nu < 0 || nu > SRTM_MAX_NU) return fail(SRTM_ERR_UNSUPPORTED, "nu=%d outside 0..%d", nu, SRTM_MAX_NU);
+  if (nu == 0) return SRTM_OK;
+  if (!B || !u) return fail(SRTM_ERR_ARG, "nu=%d needs B and u", nu);
+  if (!is_device_ptr(B) || !is_device_ptr(u)) return fail(SRTM_ERR_ARG, "B and u must be device pointers");
+  return SRTM_OK;
+}
+
 void set_outputs(Ctx& c, const srtm_output* main, const srtm_output* extra) {
   c.fast_mean = main ? main->fast_mean : nullptr;
   c.fast_cov = main ? main->fast_cov : nullptr;
@@ -319,9 +331,13 @@ int single(const srtm_problem* p, srtm_precision prec, const srtm_output* out, c
   if (p->ratio < 1) return fail(SRTM_ERR_ARG, "ratio=%d < 1", p->ratio);
   if (p->n_slow < 1) return fail(SRTM_ERR_ARG, "n_slow=%d < 1", p->n_slow);
   if ((rc = check_inputs(p->F, p->Q, p->H, p->R, p->m0, p->P0, p->y))) return rc;
+  if ((rc = check_controls(p->nu, p->B, p->u))) return rc;
   if ((rc = check_outputs(out, "output")) || (rc = check_outputs(extra, "filtered output"))) return rc;
   Ctx c;
   memset(&c, 0, sizeof c);
+  c.nu = p->nu;
+  c.B = p->nu ? p->B : nullptr;
+  c.u = p->nu ? p->u : nullptr;
   c.n_seq = 1;
   c.fold_meta = 1;
   c.nx = p->nx;
@@ -351,9 +367,13 @@ int batch(const srtm_batch* b, srtm_precision prec, const srtm_output* out, cons
   if (!is_device_ptr(b->ratio) || !is_device_ptr(b->n_slow))
     return fail(SRTM_ERR_ARG, "ratio and n_slow must be device int arrays");
   if ((rc = check_inputs(b->F, b->Q, b->H, b->R, b->m0, b->P0, b->y))) return rc;
+  if ((rc = check_controls(b->nu, b->B, b->u))) return rc;
   if ((rc = check_outputs(out, "output")) || (rc = check_outputs(extra, "filtered output"))) return rc;
   Ctx c;
   memset(&c, 0, sizeof c);
+  c.nu = b->nu;
+  c.B = b->nu ? b->B : nullptr;
+  c.u = b->nu ? b->u : nullptr;
   c.n_seq = b->n_seq;
   c.nx = b->nx;
   c.ny = b->ny;
@@ -414,18 +434,21 @@ int srtm_smoother_host(const srtm_problem* hp, srtm_precision prec, const srtm_o
   int rc = check_dims(hp->nx, hp->ny);
   if (rc) return rc;
   if (hp->ratio < 1 || hp->n_slow < 1) return fail(SRTM_ERR_ARG, "ratio and n_slow must be >= 1");
-  const double* in[7] = {hp->F, hp->Q, hp->H, hp->R, hp->m0, hp->P0, hp->y};
-  for (int i = 0; i < 7; ++i)
+  if (hp->nu < 0 || hp->nu > SRTM_MAX_NU) return fail(SRTM_ERR_UNSUPPORTED, "nu=%d outside 0..%d", hp->nu, SRTM_MAX_NU);
+  const int n_in = hp->nu > 0 ? 9 : 7;
+  const double* in[9] = {hp->F, hp->Q, hp->H, hp->R, hp->m0, hp->P0, hp->y, hp->B, hp->u};
+  for (int i = 0; i < n_in; ++i)
     if (!in[i]) return fail(SRTM_ERR_ARG, "input %d is NULL", i);
-  const long long nx = hp->nx, ny = hp->ny, N = hp->n_slow, l = hp->ratio;
-  const size_t in_cnt[7] = {(size_t)(nx * nx), (size_t)(nx * nx), (size_t)(ny * nx), (size_t)(ny * ny),
-                            (size_t)nx, (size_t)(nx * nx), (size_t)(N * ny)};
+  const long long nx = hp->nx, ny = hp->ny, N = hp->n_slow, l = hp->ratio, nu = hp->nu;
+  const size_t in_cnt[9] = {(size_t)(nx * nx), (size_t)(nx * nx), (size_t)(ny * nx), (size_t)(ny * ny),
+                            (size_t)nx,        (size_t)(nx * nx), (size_t)(N * ny),  (size_t)(nx * nu),
+                            (size_t)(N * l * nu)};
   const size_t out_cnt[5] = {(size_t)(N * l * nx), (size_t)(N * l * nx * nx), (size_t)(N * nx), (size_t)(N * nx * nx),
                              1};
   double* hout_p[5] = {hout->fast_mean, hout->fast_cov, hout->slow_mean, hout->slow_cov, hout->loglik};
-  size_t off[12], o = 0;
-  for (int i = 0; i < 7; ++i) { off[i] = o; o += a256(in_cnt[i] * sizeof(double)); }
-  for (int i = 0; i < 5; ++i) { off[7 + i] = o; o += hout_p[i] ? a256(out_cnt[i] * sizeof(double)) : 0; }
+  size_t off[14], o = 0;
+  for (int i = 0; i < n_in; ++i) { off[i] = o; o += a256(in_cnt[i] * sizeof(double)); }
+  for (int i = 0; i < 5; ++i) { off[9 + i] = o; o += hout_p[i] ? a256(out_cnt[i] * sizeof(double)) : 0; }
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAXDEV) return fail(SRTM_ERR_CUDA, "no device");
   unsigned char* stg = nullptr;
@@ -443,7 +466,7 @@ int srtm_smoother_host(const srtm_problem* hp, srtm_precision prec, const srtm_o
     stg = (unsigned char*)d.stage;
   }
   cudaStream_t st = (cudaStream_t)stream;
-  for (int i = 0; i < 7; ++i)
+  for (int i = 0; i < n_in; ++i)
     if (cudaMemcpyAsync(stg + off[i], in[i], in_cnt[i] * sizeof(double), cudaMemcpyDefault, st) != cudaSuccess)
       return fail(SRTM_ERR_CUDA, "input copy %d failed", i);
   srtm_problem dp = *hp;
@@ -451,9 +474,11 @@ int srtm_smoother_host(const srtm_problem* hp, srtm_precision prec, const srtm_o
   dp.H = (const double*)(stg + off[2]); dp.R = (const double*)(stg + off[3]);
   dp.m0 = (const double*)(stg + off[4]); dp.P0 = (const double*)(stg + off[5]);
   dp.y = (const double*)(stg + off[6]);
+  dp.B = n_in > 7 ? (const double*)(stg + off[7]) : nullptr;
+  dp.u = n_in > 7 ? (const double*)(stg + off[8]) : nullptr;
   srtm_output dout;
   double** dsl[5] = {&dout.fast_mean, &dout.fast_cov, &dout.slow_mean, &dout.slow_cov, &dout.loglik};
-  for (int i = 0; i < 5; ++i) *dsl[i] = hout_p[i] ? (double*)(stg + off[7 + i]) : nullptr;
+  for (int i = 0; i < 5; ++i) *dsl[i] = hout_p[i] ? (double*)(stg + off[9 + i]) : nullptr;
   rc = srtm_smoother(&dp, prec, &dout, nullptr, stream);
   if (rc) return rc;
   for (int i = 0; i < 5; ++i)
@@ -697,6 +722,7 @@ extern "C" int srtm_smoother_noalloc(const srtm_problem* p, srtm_precision prec,
   if (p->ratio < 1) return fail(SRTM_ERR_ARG, "ratio=%d < 1", p->ratio);
   if (p->n_slow < 1) return fail(SRTM_ERR_ARG, "n_slow=%d < 1", p->n_slow);
   if ((rc = check_inputs(p->F, p->Q, p->H, p->R, p->m0, p->P0, p->y))) return rc;
+  if ((rc = check_controls(p->nu, p->B, p->u))) return rc;
   if ((rc = check_outputs(smooth, "output"))) return rc;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAXDEV)
@@ -704,6 +730,9 @@ extern "C" int srtm_smoother_noalloc(const srtm_problem* p, srtm_precision prec,
   cudaStream_t st = (cudaStream_t)stream;
   Ctx c;
   memset(&c, 0, sizeof c);
+  c.nu = p->nu;
+  c.B = p->nu ? p->B : nullptr;
+  c.u = p->nu ? p->u : nullptr;
   c.n_seq = 1;
   c.fold_meta = 1;
   c.nx = p->nx;
@@ -736,7 +765,7 @@ extern "C" int srtm_smoother_noalloc(const srtm_problem* p, srtm_precision prec,
     rc = shapes_for(c.nx, prec, t, d.sms, c.total_slow, c.n_seq, &sh);
     if (rc) return fail(rc, "launch shape query failed (%d)", rc);
     const int tile_f = sh.scan_groups_f * sh.scan_elems_f, tile_s = sh.scan_groups_s * sh.scan_elems_s;
-    L = make_layout(c.nx, c.ny, c.max_ratio, c.n_seq, c.total_slow, prec, tile_f, tile_s);
+    L = make_layout(c.nx, c.ny, c.max_ratio, c.n_seq, c.total_slow, prec, tile_f, tile_s, c.nu);
     if (L.total > NOALLOC_SCRATCH_BYTES)
       return fail(SRTM_ERR_ARG, "this problem needs %zu bytes of scratch; the static scratch holds %zu bytes",
                   L.total, NOALLOC_SCRATCH_BYTES);
@@ -763,6 +792,7 @@ extern "C" int srtm_smoother_noalloc(const srtm_problem* p, srtm_precision prec,
     c.selem = w + L.selem;
     c.sfin = w + L.sfin;
     c.lterm = (double*)(w + L.lterm);
+    c.uin = c.nu > 0 ? (double*)(w + L.uin) : nullptr;
     c.tile_f = tile_f;
     c.tile_s = tile_s;
     c.setup_separate = t.setup_mode == 2 ? 1 : 0;

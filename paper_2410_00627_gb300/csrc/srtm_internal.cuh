@@ -57,6 +57,8 @@ struct ModelLayout {
   long long P1;    // n^2         P^f_{1,l}
   long long Q;     // n^2         copy of Q
   long long Cf;    // float copies of A, Qc_1, Cov(e_1,e_l) (n^2 each) and V_1 H^T (n x m, ld m)
+  long long AB;    // L n MU      A^j B   (j = 0..L-1), n x nu blocks (ld nu)      [inputs]
+  long long SB;    // L n MU      S_j B = sum_{i<=j} A^i B                         [inputs]
   long long stride;
 };
 
@@ -81,6 +83,8 @@ __host__ __device__ inline ModelLayout make_model_layout(int n, int m, int L) {
   ml.P1 = o;   o += nn;
   ml.Q = o;    o += nn;
   ml.Cf = o;   o += (3 * nn + (long long)n * MY + 1) / 2;
+  ml.AB = o;   o += (long long)L * n * SRTM_MAX_NU;
+  ml.SB = o;   o += (long long)L * n * SRTM_MAX_NU;
   ml.stride = (o + 31) / 32 * 32;
   return ml;
 }
@@ -103,6 +107,15 @@ struct Rec {
   // padded to 32 entries (256 B in float64): records start on cache-line
   // boundaries and no cache sector holds parts of two of them
   static constexpr int SIZE = (Pm + NN + 31) / 32 * 32;
+};
+
+// Per-interval input terms (with x_{k,i} = A^i x_{k-1,l} + b_{k,i} + noise,
+// b_{k,i} = sum_{r<i} A^{i-1-r} B u_{k,r}):  b_{k,l}, b_{k,1} = B u_{k,0},
+// B u_{k+1,0} (the input of the smoother's prediction m^-_{k+1,1}), and
+// c_k = H sum_i b_{k,i} (the input part of the predicted measurement).
+template <int NX>
+struct UIn {
+  static constexpr int bl = 0, b1 = NX, bn = 2 * NX, c = 3 * NX, SIZE = 3 * NX + MY;
 };
 
 // Per-interval smoothing terms (Om_k, om_k), padded like the record.
@@ -135,6 +148,8 @@ struct Ctx {
   const int* in_ratio;
   const int* in_nslow;
   const double *F, *Q, *H, *R, *m0, *P0, *y;
+  int nu;                 // known inputs (0: none)
+  const double *B, *u;    // B per sequence (nx x nu), u per fast step (rows in sequence order)
   // outputs of the call (smoothed, or filtered for a filter-only call)
   double *fast_mean, *fast_cov, *slow_mean, *slow_cov;
   // filtered outputs requested alongside a smoother call
@@ -151,6 +166,7 @@ struct Ctx {
   void* selem;  // [total_slow][SL::SIZE]  smoother elements                  (scan type)
   void* sfin;   // [total_slow][NN + NX]   per-interval smoothing terms Om_k, om_k (recovery type)
   double* lterm;   // [total_slow] per-interval terms of log p(y_{1:N})
+  double* uin;     // [total_slow][UIn::SIZE] per-interval input terms (NULL without inputs)
   double* loglik;  // caller's output: log p(y_{1:N}) per sequence (NULL: not computed)
   // launch shapes
   int tile_f, tile_s;    // elements per scan tile

@@ -236,9 +236,13 @@ def config4(seed: int = 0, n_seq: int = 4096, n_min: int = 100, n_max: int = 20_
 def pack(probs: list[Problem]) -> dict:
     """A list of same-size sequences as the batch layout of the C-ABI: stacked
     F, Q, H, R, m0, P0, the measurements concatenated in sequence order, and
-    per-sequence ratio / n_slow (int32) with the batch totals."""
+    per-sequence ratio / n_slow (int32) with the batch totals; with known
+    inputs also B stacked (S, nx, nu) and u concatenated (total_fast, nu)."""
     out = {k: np.ascontiguousarray(np.stack([getattr(p, k) for p in probs])) for k in ("F", "Q", "H", "R", "m0", "P0")}
     out["y"] = np.ascontiguousarray(np.concatenate([p.y for p in probs]))
+    if probs[0].B is not None:
+        out["B"] = np.ascontiguousarray(np.stack([p.B for p in probs]))
+        out["u"] = np.ascontiguousarray(np.concatenate([p.u for p in probs]))
     out["ratio"] = np.array([p.ratio for p in probs], dtype=np.int32)
     out["n_slow"] = np.array([p.n_slow for p in probs], dtype=np.int32)
     out["max_ratio"] = int(out["ratio"].max())

@@ -15,13 +15,20 @@ def to_dev(a):
     return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device="cuda")
 
 
+def controls(prob):
+    """Known inputs of a problem as keyword arguments of the binding (none without)."""
+    if getattr(prob, "B", None) is None:
+        return {}
+    return {"B": to_dev(prob.B), "u": to_dev(prob.u)}
+
+
 def run_smoother(prob, precision="fp64", filtered=True):
     import torch
 
     from paper_2410_00627_gb300 import api
     args = [to_dev(getattr(prob, k)) for k in ("F", "Q", "H", "R", "m0", "P0", "y")]
     sm, fi = api.smoother(*args, prob.ratio, precision=precision,
-                          filtered=api.OUTPUT_KEYS if filtered else ())
+                          filtered=api.OUTPUT_KEYS if filtered else (), **controls(prob))
     api.status()
     torch.cuda.synchronize()
     return ({k: v.cpu().numpy() for k, v in sm.items()}, {k: v.cpu().numpy() for k, v in fi.items()})
@@ -30,7 +37,7 @@ def run_smoother(prob, precision="fp64", filtered=True):
 def run_filter(prob, precision="fp64"):
     from paper_2410_00627_gb300 import api
     args = [to_dev(getattr(prob, k)) for k in ("F", "Q", "H", "R", "m0", "P0", "y")]
-    out = api.filter(*args, prob.ratio, precision=precision)
+    out = api.filter(*args, prob.ratio, precision=precision, **controls(prob))
     api.status()
     return {k: v.cpu().numpy() for k, v in out.items()}
 

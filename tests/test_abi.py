@@ -35,9 +35,9 @@ def test_library_exports_every_declared_symbol(lib):
 
 def test_struct_layouts_match_header():
     # two 4-int headers then pointers on LP64
-    assert ctypes.sizeof(api.Problem) == 16 + 7 * 8
+    assert ctypes.sizeof(api.Problem) == 16 + 7 * 8 + 8 + 2 * 8   # + nu (padded), B, u
     assert ctypes.sizeof(api.Output) == 5 * 8
-    assert ctypes.sizeof(api.Batch) == 16 + 16 + 9 * 8
+    assert ctypes.sizeof(api.Batch) == 16 + 16 + 9 * 8 + 8 + 2 * 8
     assert ctypes.sizeof(api.Tuning) == 20
 
 
