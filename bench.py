@@ -68,6 +68,9 @@ def parse(argv=None):
     ap.add_argument("--tune-reps", type=int, default=2)
     ap.add_argument("--sweep", action="store_true",
                     help="config 2 over T = 10^2 .. 10^4 slow steps (x sqrt 10), FP64 and mixed, one JSON line each")
+    ap.add_argument("--figure", action="store_true",
+                    help="run time of the scan and the sequential forms (filter and smoother, FP64) over "
+                         "T = 16 .. 6000 slow steps of config 2, one JSON line per T")
     ap.add_argument("--report-errors", action="store_true",
                     help="max relative errors of every mode against the FP64 oracle, configs 1, 2, 3, 5 at full size")
     return ap.parse_args(argv)
@@ -276,8 +279,70 @@ def run_ours(args, rank, world, dist):
                        "tuning": tuning.get(other, api.get_tuning(prob.nx, other)),
                        "parity": check_parity(prob, outs, other)}
         line["e2e"] = run_e2e(args, prob, api, torch, flush)
+        seq_ms = time_calls(lambda st: api.smoother(*ins, prob.ratio, precision=args.precision, out=outs, stream=st,
+                                                    method="sequential"), 2, 1, stream, flush)
+        line["sequential_comparator"] = {
+            "value": n_fast / (float(np.mean(seq_ms)) * 1e-3), "ms_per_step": float(np.mean(seq_ms)),
+            "call": "srtm_smoother_sequential (IMKF and IMS recursions over the slow steps on one thread), "
+                    "direct calls, mean of 2 after 1 warm-up"}
         line["cpu_baseline"] = run_cpu_baseline(args, prob)
     return line
+
+
+def time_calls(call, steps, warmup, stream, flush=None):
+    """Per-call device times (ms) of ``call(stream)`` by CUDA events on ``stream``
+    after ``warmup`` untimed calls; L2 flushed before each call when given."""
+    import torch
+
+    from paper_2410_00627_gb300 import api
+    for _ in range(warmup):
+        call(stream)
+    api.status(stream)
+    ms = []
+    for _ in range(steps):
+        if flush is not None:
+            flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        call(stream)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    api.status(stream)
+    return ms
+
+
+def run_figure(args):
+    """The scan forms against the sequential forms (the paper's figure of
+    parallel vs sequential IMKF / IMS run time over the number of steps), on
+    config 2 (l = 20) in FP64, each call timed on its own."""
+    import torch
+
+    from paper_2410_00627_gb300 import api, build, synth
+    build.build()
+    api.load()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    lines = []
+    for n_slow in (16, 32, 64, 128, 256, 512, 1024, 2048, 4096, 6000):
+        prob = synth.config2(seed=args.seed, n_slow=n_slow, keep_states=False)
+        t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)  # noqa: E731
+        ins = [t(getattr(prob, k)) for k in ("F", "Q", "H", "R", "m0", "P0", "y")]
+        n_fast = n_slow * prob.ratio
+        outs = {"fast_mean": torch.empty(n_fast, prob.nx, dtype=torch.float64, device=dev),
+                "fast_cov": torch.empty(n_fast, prob.nx, prob.nx, dtype=torch.float64, device=dev),
+                "slow_mean": torch.empty(n_slow, prob.nx, dtype=torch.float64, device=dev),
+                "slow_cov": torch.empty(n_slow, prob.nx, prob.nx, dtype=torch.float64, device=dev)}
+        row = {"figure": "config 2 scan vs sequential, fp64", "n_slow": n_slow, "fast_steps": n_fast, "unit": "us"}
+        for method in ("scan", "sequential"):
+            for kind in ("filter", "smoother"):
+                fn = api.filter if kind == "filter" else api.smoother
+                call = lambda st, fn=fn, method=method: fn(*ins, prob.ratio, precision="fp64", out=outs,  # noqa: E731
+                                                            stream=st, method=method)
+                ms = time_calls(call, 20, 3, stream)
+                row[f"{method}_{kind}_us"] = float(np.median(ms)) * 1e3
+        lines.append(row)
+    return lines
 
 
 # --------------------------------------------------------------------------- config 4 (batched)
@@ -421,6 +486,12 @@ def run_batched(args, rank, world, dist):
                                     "ms_per_step": float(np.mean(ms2)),
                                     "tuning": tuning.get(other, api.get_tuning(nx, other))}
         line["fp64_single_sequence_loop"] = run_single_loop(probs, pk, ten, outs, api, torch, stream)
+        seq_ms = time_calls(lambda st: api.smoother_batch(batch, precision=args.precision, out=outs, stream=st,
+                                                          method="sequential"), 2, 1, stream)
+        line["sequential_comparator"] = {
+            "value": n_fast / (float(np.mean(seq_ms)) * 1e-3), "ms_per_step": float(np.mean(seq_ms)),
+            "call": "srtm_smoother_batch_sequential (IMKF and IMS recursions one thread per sequence), "
+                    "direct calls, mean of 2 after 1 warm-up"}
         line["e2e"] = run_batched_e2e(args, pk, batch, ten, outs, api, torch, stream)
         line["cpu_baseline"] = run_cpu_baseline_batched(args, probs)
     return line
@@ -760,6 +831,10 @@ def main():
     if args.report_errors:
         for cfg in (1, 2, 3, 5):
             print(json.dumps(report_errors(cfg)), flush=True)
+        return
+    if args.figure:
+        for ln in run_figure(args):
+            print(json.dumps(ln), flush=True)
         return
     if args.sweep:
         import copy

@@ -141,6 +141,23 @@ int srtm_filter_batch(const srtm_batch *b, srtm_precision prec, const srtm_outpu
 int srtm_smoother_batch(const srtm_batch *b, srtm_precision prec, const srtm_output *smooth,
                         const srtm_output *filt, srtm_stream_t stream);
 
+/* Sequential forms (the O(N)-depth comparator of the scans): the same
+ * arguments, outputs and errors as the four calls above, with the slow-rate
+ * recursions run one step after another, one GPU thread per sequence -- the
+ * IMKF (Eq. 9-12) forward over k and the IMS recursion (Eq. 21-22) backward.
+ * The per-interval work (Eq. 17 blocks, Eq. 29 elements) and the fast-rate
+ * recovery (Remarks 1, 3) run as in the scan path.  Results agree with the
+ * scan path up to rounding.  Tuning: setup_mode is ignored (always its own
+ * kernel); the scan shapes do not apply.                                      */
+int srtm_filter_sequential(const srtm_problem *p, srtm_precision prec, const srtm_output *filt,
+                           srtm_stream_t stream);
+int srtm_smoother_sequential(const srtm_problem *p, srtm_precision prec, const srtm_output *smooth,
+                             const srtm_output *filt, srtm_stream_t stream);
+int srtm_filter_batch_sequential(const srtm_batch *b, srtm_precision prec, const srtm_output *filt,
+                                 srtm_stream_t stream);
+int srtm_smoother_batch_sequential(const srtm_batch *b, srtm_precision prec, const srtm_output *smooth,
+                                   const srtm_output *filt, srtm_stream_t stream);
+
 /* srtm_smoother with HOST buffers (pageable or pinned) for every input and
  * output.  Copies the inputs to a library-owned device staging area, runs the
  * device path, copies the results back and synchronizes the stream; returns

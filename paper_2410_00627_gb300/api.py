@@ -24,7 +24,9 @@ SYMBOLS = ("srtm_filter", "srtm_smoother", "srtm_filter_batch", "srtm_smoother_b
            "srtm_smoother_host", "srtm_status", "srtm_last_error_detail", "srtm_release",
            "srtm_set_tuning", "srtm_get_tuning", "srtm_launches_per_call", "srtm_set_stage_timing",
            "srtm_stage_times", "srtm_smoother_noalloc", "srtm_autotune", "srtm_autotune_batch",
-           "srtm_last_call_launches")
+           "srtm_last_call_launches", "srtm_filter_sequential", "srtm_smoother_sequential",
+           "srtm_filter_batch_sequential", "srtm_smoother_batch_sequential")
+METHODS = {"scan": "", "sequential": "_sequential"}  # entry-point suffix per method
 STAGES = ("metadata", "constants", "filter_scan", "interval_setup", "smoother_scan", "recovery")
 
 
@@ -95,6 +97,10 @@ def load():
         "srtm_smoother_noalloc": [P, c_int, O, c_void_p],
         "srtm_autotune": [P, c_int, O, c_int, T, ctypes.POINTER(ctypes.c_float), c_void_p],
         "srtm_autotune_batch": [B, c_int, O, c_int, T, ctypes.POINTER(ctypes.c_float), c_void_p],
+        "srtm_filter_sequential": [P, c_int, O, c_void_p],
+        "srtm_smoother_sequential": [P, c_int, O, O, c_void_p],
+        "srtm_filter_batch_sequential": [B, c_int, O, c_void_p],
+        "srtm_smoother_batch_sequential": [B, c_int, O, O, c_void_p],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -159,28 +165,36 @@ def _problem(F, Q, H, R, m0, P0, y, ratio, B=None, u=None):
                    _dev_tensor(P0, "P0", (nx, nx)), _dev_tensor(y, "y", (n_slow, ny)), nu, pB, pu)
 
 
+def _entry(name, method):
+    if method not in METHODS:
+        raise ValueError(f"method must be one of {tuple(METHODS)}, got {method!r}")
+    return getattr(load(), name + METHODS[method])
+
+
 def smoother(F, Q, H, R, m0, P0, y, ratio, precision="fp64", outputs=OUTPUT_KEYS, filtered=(),
-             stream=None, out=None, out_filtered=None, B=None, u=None):
+             stream=None, out=None, out_filtered=None, B=None, u=None, method="scan"):
     """p(x_{k,i} | y_{1:N}) for one sequence.  Returns (smoothed, filtered) dicts
     of CUDA tensors keyed by fast_mean / fast_cov / slow_mean / slow_cov (and
     loglik when asked for).  B (nx, nu) and u (n_slow*ratio, nu): optional
-    known inputs, x_{t+1} = F x_t + B u_t + w_t."""
+    known inputs, x_{t+1} = F x_t + B u_t + w_t.  method: "scan" (the
+    parallel scans, srtm_smoother) or "sequential" (srtm_smoother_sequential)."""
     prob = _problem(F, Q, H, R, m0, P0, y, ratio, B, u)
     rows_fast, rows_slow = prob.n_slow * prob.ratio, prob.n_slow
     sm, so = _alloc_outputs(outputs, y.device, rows_fast, rows_slow, prob.nx, out)
     fi, fo = _alloc_outputs(filtered, y.device, rows_fast, rows_slow, prob.nx, out_filtered)
-    rc = load().srtm_smoother(ctypes.byref(prob), PRECISION[precision], ctypes.byref(so),
-                              ctypes.byref(fo) if filtered else None, _stream_handle(stream))
+    rc = _entry("srtm_smoother", method)(ctypes.byref(prob), PRECISION[precision], ctypes.byref(so),
+                                         ctypes.byref(fo) if filtered else None, _stream_handle(stream))
     _check(rc)
     return sm, fi
 
 
 def filter(F, Q, H, R, m0, P0, y, ratio, precision="fp64", outputs=OUTPUT_KEYS, stream=None, out=None,  # noqa: A001
-           B=None, u=None):
-    """p(x_{k,i} | y_{1:k}) for one sequence."""
+           B=None, u=None, method="scan"):
+    """p(x_{k,i} | y_{1:k}) for one sequence (method as for smoother)."""
     prob = _problem(F, Q, H, R, m0, P0, y, ratio, B, u)
     res, o = _alloc_outputs(outputs, y.device, prob.n_slow * prob.ratio, prob.n_slow, prob.nx, out)
-    _check(load().srtm_filter(ctypes.byref(prob), PRECISION[precision], ctypes.byref(o), _stream_handle(stream)))
+    _check(_entry("srtm_filter", method)(ctypes.byref(prob), PRECISION[precision], ctypes.byref(o),
+                                         _stream_handle(stream)))
     return res
 
 
@@ -197,32 +211,36 @@ def make_batch(F, Q, H, R, m0, P0, y, ratio, n_slow, max_ratio, total_slow, tota
     if B is not None:
         nu = B.shape[2]
         pB, pu = _dev_tensor(B, "B", (S, nx, nu)), _dev_tensor(u, "u", (int(total_fast), nu))
-    return Batch(S, nx, ny, int(max_ratio), int(total_slow), int(total_fast),
-                 c_void_p(ratio.data_ptr()), c_void_p(n_slow.data_ptr()),
-                 _dev_tensor(F, "F", (S, nx, nx)), _dev_tensor(Q, "Q", (S, nx, nx)),
-                 _dev_tensor(H, "H", (S, ny, nx)), _dev_tensor(R, "R", (S, ny, ny)),
-                 _dev_tensor(m0, "m0", (S, nx)), _dev_tensor(P0, "P0", (S, nx, nx)),
-                 _dev_tensor(y, "y", (int(total_slow), ny)), nu, pB, pu)
+    b = Batch(S, nx, ny, int(max_ratio), int(total_slow), int(total_fast),
+              c_void_p(ratio.data_ptr()), c_void_p(n_slow.data_ptr()),
+              _dev_tensor(F, "F", (S, nx, nx)), _dev_tensor(Q, "Q", (S, nx, nx)),
+              _dev_tensor(H, "H", (S, ny, nx)), _dev_tensor(R, "R", (S, ny, ny)),
+              _dev_tensor(m0, "m0", (S, nx)), _dev_tensor(P0, "P0", (S, nx, nx)),
+              _dev_tensor(y, "y", (int(total_slow), ny)), nu, pB, pu)
+    # the descriptor holds raw device pointers: keep the tensors alive with it
+    b._tensors = (F, Q, H, R, m0, P0, y, ratio, n_slow, B, u)
+    return b
 
 
 def smoother_batch(batch: Batch, precision="fp64", outputs=OUTPUT_KEYS, filtered=(), stream=None,
-                   device=None, out=None, out_filtered=None):
+                   device=None, out=None, out_filtered=None, method="scan"):
     """Ragged batch: every sequence of ``batch`` in one set of launches."""
     import torch
     device = device or torch.device("cuda", torch.cuda.current_device())
     sm, so = _alloc_outputs(outputs, device, batch.total_fast, batch.total_slow, batch.nx, out, batch.n_seq)
     fi, fo = _alloc_outputs(filtered, device, batch.total_fast, batch.total_slow, batch.nx, out_filtered, batch.n_seq)
-    _check(load().srtm_smoother_batch(ctypes.byref(batch), PRECISION[precision], ctypes.byref(so),
-                                      ctypes.byref(fo) if filtered else None, _stream_handle(stream)))
+    _check(_entry("srtm_smoother_batch", method)(ctypes.byref(batch), PRECISION[precision], ctypes.byref(so),
+                                                 ctypes.byref(fo) if filtered else None, _stream_handle(stream)))
     return sm, fi
 
 
-def filter_batch(batch: Batch, precision="fp64", outputs=OUTPUT_KEYS, stream=None, device=None, out=None):
+def filter_batch(batch: Batch, precision="fp64", outputs=OUTPUT_KEYS, stream=None, device=None, out=None,
+                 method="scan"):
     import torch
     device = device or torch.device("cuda", torch.cuda.current_device())
     res, o = _alloc_outputs(outputs, device, batch.total_fast, batch.total_slow, batch.nx, out, batch.n_seq)
-    _check(load().srtm_filter_batch(ctypes.byref(batch), PRECISION[precision], ctypes.byref(o),
-                                    _stream_handle(stream)))
+    _check(_entry("srtm_filter_batch", method)(ctypes.byref(batch), PRECISION[precision], ctypes.byref(o),
+                                               _stream_handle(stream)))
     return res
 
 

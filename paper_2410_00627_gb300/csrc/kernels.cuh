@@ -10,6 +10,7 @@
 
 #include "constants.cuh"
 #include "grp.cuh"
+#include "seq.cuh"
 #include "small.cuh"
 #include "srtm_internal.cuh"
 
@@ -1389,13 +1390,19 @@ int launch_t(const Ctx& c, const Shapes& sh, cudaStream_t st, cudaEvent_t* ev) {
   launch_precompute<NX>(c, st);
   if (c.uin) input_kernel<NX><<<(unsigned)((c.total_slow + 127) / 128), 128, 0, st>>>(c);
   if (ev) cudaEventRecord(ev[0], st);
-  scan_kernel<FOp><<<sh.grid_f, sh.scan_groups_f * G, sh.smem_f, st>>>(c, sh.scan_groups_f, sh.scan_elems_f, sh.window_f);
+  const unsigned seq_blocks = (unsigned)((c.n_seq + SEQ_THREADS - 1) / SEQ_THREADS);
+  if (c.sequential)
+    seq_filter_kernel<NX, TS><<<seq_blocks, SEQ_THREADS, 0, st>>>(c);
+  else
+    scan_kernel<FOp><<<sh.grid_f, sh.scan_groups_f * G, sh.smem_f, st>>>(c, sh.scan_groups_f, sh.scan_elems_f, sh.window_f);
   if (ev) cudaEventRecord(ev[1], st);
   if (c.setup_separate)
     setup_kernel<NX, T, TS><<<sh.grid_setup, 128, sh.smem_setup, st>>>(c);
   launch_loglik(c, st);
   if (ev) cudaEventRecord(ev[2], st);  // otherwise the interval setup runs inside the filter scan
-  if (c.smoothing)
+  if (c.smoothing && c.sequential)
+    seq_smoother_kernel<NX, T, TR><<<seq_blocks, SEQ_THREADS, 0, st>>>(c);
+  else if (c.smoothing)
     scan_kernel<SOp><<<sh.grid_s, sh.scan_groups_s * G, sh.smem_s, st>>>(c, sh.scan_groups_s, sh.scan_elems_s, sh.window_s);
   if (ev) cudaEventRecord(ev[3], st);
   const long long blocks = (c.total_fast + sh.recover_threads - 1) / sh.recover_threads;

@@ -201,7 +201,8 @@ int run(Ctx c, srtm_precision prec, cudaStream_t st) {
   DevState& d = g_dev[dev];
   if (!d.sms && cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return fail(SRTM_ERR_CUDA, "cudaDeviceGetAttribute failed");
-  const srtm_tuning t = effective_tuning(c.nx, prec);
+  srtm_tuning t = effective_tuning(c.nx, prec);
+  if (c.sequential) t.setup_mode = 2;  // no filter scan to carry the setup
   Shapes sh;
   int rc = shapes_for(c.nx, prec, t, d.sms, c.total_slow, c.n_seq, &sh);
   if (rc) return fail(rc, "launch shape query failed (%d)", rc);
@@ -323,7 +324,7 @@ void set_outputs(Ctx& c, const srtm_output* main, const srtm_output* extra) {
 }
 
 int single(const srtm_problem* p, srtm_precision prec, const srtm_output* out, const srtm_output* extra,
-           int smoothing, srtm_stream_t stream) {
+           int smoothing, srtm_stream_t stream, int sequential = 0) {
   if (!p) return fail(SRTM_ERR_ARG, "problem is NULL");
   if (prec < SRTM_FP64 || prec > SRTM_FP32) return fail(SRTM_ERR_ARG, "unknown precision %d", (int)prec);
   int rc = check_dims(p->nx, p->ny);
@@ -344,6 +345,7 @@ int single(const srtm_problem* p, srtm_precision prec, const srtm_output* out, c
   c.ny = p->ny;
   c.max_ratio = p->ratio;
   c.smoothing = smoothing;
+  c.sequential = sequential;
   c.uniform_ratio = p->ratio;
   c.uniform_nslow = p->n_slow;
   c.total_slow = p->n_slow;
@@ -354,7 +356,7 @@ int single(const srtm_problem* p, srtm_precision prec, const srtm_output* out, c
 }
 
 int batch(const srtm_batch* b, srtm_precision prec, const srtm_output* out, const srtm_output* extra, int smoothing,
-          srtm_stream_t stream) {
+          srtm_stream_t stream, int sequential = 0) {
   if (!b) return fail(SRTM_ERR_ARG, "batch is NULL");
   if (prec < SRTM_FP64 || prec > SRTM_FP32) return fail(SRTM_ERR_ARG, "unknown precision %d", (int)prec);
   int rc = check_dims(b->nx, b->ny);
@@ -381,6 +383,7 @@ int batch(const srtm_batch* b, srtm_precision prec, const srtm_output* out, cons
   c.smoothing = smoothing;
   c.total_slow = b->total_slow;
   c.total_fast = b->total_fast;
+  c.sequential = sequential;
   c.in_ratio = b->ratio;
   c.in_nslow = b->n_slow;
   c.F = b->F; c.Q = b->Q; c.H = b->H; c.R = b->R; c.m0 = b->m0; c.P0 = b->P0; c.y = b->y;
@@ -408,6 +411,26 @@ int srtm_filter_batch(const srtm_batch* b, srtm_precision prec, const srtm_outpu
 int srtm_smoother_batch(const srtm_batch* b, srtm_precision prec, const srtm_output* smooth,
                         const srtm_output* filt, srtm_stream_t stream) {
   return batch(b, prec, smooth, filt, 1, stream);
+}
+
+int srtm_filter_sequential(const srtm_problem* p, srtm_precision prec, const srtm_output* filt,
+                           srtm_stream_t stream) {
+  return single(p, prec, filt, nullptr, 0, stream, 1);
+}
+
+int srtm_smoother_sequential(const srtm_problem* p, srtm_precision prec, const srtm_output* smooth,
+                             const srtm_output* filt, srtm_stream_t stream) {
+  return single(p, prec, smooth, filt, 1, stream, 1);
+}
+
+int srtm_filter_batch_sequential(const srtm_batch* b, srtm_precision prec, const srtm_output* filt,
+                                 srtm_stream_t stream) {
+  return batch(b, prec, filt, nullptr, 0, stream, 1);
+}
+
+int srtm_smoother_batch_sequential(const srtm_batch* b, srtm_precision prec, const srtm_output* smooth,
+                                   const srtm_output* filt, srtm_stream_t stream) {
+  return batch(b, prec, smooth, filt, 1, stream, 1);
 }
 
 int srtm_status(srtm_stream_t stream) {

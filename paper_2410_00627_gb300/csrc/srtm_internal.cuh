@@ -171,6 +171,7 @@ struct Ctx {
   // launch shapes
   int tile_f, tile_s;    // elements per scan tile
   int setup_separate;    // 1: the interval setup runs as its own kernel after the filter scan
+  int sequential;        // 1: the slow-rate recursions run sequentially (one thread per sequence)
 };
 
 // ---------------------------------------------------------------------------

@@ -336,3 +336,30 @@ def test_loglik_through_host_entry_point(oracle_mod):
                             prob.ratio, precision="fp64", loglik=True)
     want = oracle_mod.loglik(prob)
     assert abs(res["loglik"][0] - want) <= 1e-9 * abs(want)
+
+
+def test_batch_descriptor_keeps_its_tensors_alive(oracle_mod):
+    """make_batch over temporaries: the descriptor holds only raw pointers, so
+    it must keep the tensors alive; freed blocks are reused by new tensors."""
+    import gc
+
+    import torch
+
+    from paper_2410_00627_gb300 import api
+    probs = synth.config4(seed=13, n_seq=20, n_min=1, n_max=60)
+    pk = synth.pack(probs)
+    t = lambda a: torch.as_tensor(a, device="cuda")  # noqa: E731
+    b = api.make_batch(t(pk["F"]), t(pk["Q"]), t(pk["H"]), t(pk["R"]), t(pk["m0"]), t(pk["P0"]), t(pk["y"]),
+                       t(pk["ratio"]), t(pk["n_slow"]), pk["max_ratio"], pk["total_slow"], pk["total_fast"])
+    gc.collect()
+    junk = [torch.full((pk[k].size,), 7, dtype=torch.int32 if k in ("ratio", "n_slow") else torch.float64,
+                       device="cuda") for k in ("F", "Q", "H", "R", "m0", "P0", "y", "ratio", "n_slow")]
+    sm, _ = api.smoother_batch(b, precision="fp64", outputs=("slow_mean",))
+    api.status()
+    del junk
+    got = sm["slow_mean"].cpu().numpy()
+    so = 0
+    for p in probs:
+        ref = oracle_mod.sequential(p)["fast_smooth_mean"][p.ratio - 1::p.ratio]
+        compare({"slow_mean": got[so:so + p.n_slow]}, {"slow_mean": ref}, *TOL["fp64"], label=p.name)
+        so += p.n_slow
