@@ -169,6 +169,16 @@ int srtm_smoother_host(const srtm_problem *host_p, srtm_precision prec,
  * the current GPU: SRTM_OK, SRTM_ERR_TIMEOUT, SRTM_ERR_SINGULAR or SRTM_ERR_META. */
 int srtm_status(srtm_stream_t stream);
 
+/* Failure-detection self-test (the paper has no counterpart).  Launches one
+ * GPU thread on `stream` that waits, with the bounded polling every device-side
+ * wait of this library uses (the scans' look-back), on a control-block flag
+ * that nothing sets.  After `polls` polls (1..2000000; back-off 32 ns doubling
+ * to 1 us, so about polls microseconds) the wait gives up, latches the
+ * device error that the next srtm_status() returns as SRTM_ERR_TIMEOUT, and
+ * the kernel returns: the context stays usable.  Returns SRTM_ERR_ARG for
+ * polls out of range, SRTM_ERR_CUDA if the launch fails.                      */
+int srtm_selftest_wait(long long polls, srtm_stream_t stream);
+
 /* Copies a NUL-terminated description of the last host-side error of this
  * thread into buf (at most len bytes).  Returns the length of the message.    */
 int srtm_last_error_detail(char *buf, int len);

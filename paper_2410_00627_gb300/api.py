@@ -25,7 +25,7 @@ SYMBOLS = ("srtm_filter", "srtm_smoother", "srtm_filter_batch", "srtm_smoother_b
            "srtm_set_tuning", "srtm_get_tuning", "srtm_launches_per_call", "srtm_set_stage_timing",
            "srtm_stage_times", "srtm_smoother_noalloc", "srtm_autotune", "srtm_autotune_batch",
            "srtm_last_call_launches", "srtm_filter_sequential", "srtm_smoother_sequential",
-           "srtm_filter_batch_sequential", "srtm_smoother_batch_sequential")
+           "srtm_filter_batch_sequential", "srtm_smoother_batch_sequential", "srtm_selftest_wait")
 METHODS = {"scan": "", "sequential": "_sequential"}  # entry-point suffix per method
 STAGES = ("metadata", "constants", "filter_scan", "interval_setup", "smoother_scan", "recovery")
 
@@ -101,6 +101,7 @@ def load():
         "srtm_smoother_sequential": [P, c_int, O, O, c_void_p],
         "srtm_filter_batch_sequential": [B, c_int, O, c_void_p],
         "srtm_smoother_batch_sequential": [B, c_int, O, O, c_void_p],
+        "srtm_selftest_wait": [c_longlong, c_void_p],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -280,6 +281,12 @@ def smoother_host(F, Q, H, R, m0, P0, y, ratio, precision="fp64", out=None, stre
     s = c_void_p(0) if stream is None else c_void_p(stream.cuda_stream)
     _check(load().srtm_smoother_host(ctypes.byref(prob), PRECISION[precision], ctypes.byref(o), s))
     return res
+
+
+def selftest_wait(polls: int, stream=None) -> None:
+    """Launch the bounded wait on a flag that nothing sets (srtm_selftest_wait);
+    the next status() raises SRTMError SRTM_ERR_TIMEOUT."""
+    _check(load().srtm_selftest_wait(int(polls), _stream_handle(stream)))
 
 
 def status(stream=None) -> None:

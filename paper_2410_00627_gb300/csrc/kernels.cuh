@@ -750,8 +750,8 @@ __device__ int lookback_round(const Grp<Op::G>& g, int gid, int NG, const Ctx& c
     unsigned ready = 0, pref = 0;
     bool timed_out = true;
     int need = w;
-    unsigned ns = 32;
-    for (long long it = 0; it < SPIN_LIMIT; ++it) {
+    BoundedPoll poll(SPIN_LIMIT);
+    while (poll.more()) {
       for (int q = g.lane; q < w; q += G) {
         if (!((ready >> q) & 1u)) {
           const unsigned long long* fl = (const unsigned long long*)Op::tile_state(c, j_hi - (long long)q * step);
@@ -773,8 +773,7 @@ __device__ int lookback_round(const Grp<Op::G>& g, int gid, int NG, const Ctx& c
       need = pref ? __ffs(pref) : w;  // tiles q < need
       const unsigned want = (need >= 32) ? 0xffffffffu : ((1u << need) - 1u);
       if ((ready & want) == want) { timed_out = false; break; }
-      __nanosleep(ns);
-      if (ns < 1024) ns <<= 1;
+      poll.backoff();
     }
     if (g.lane == 0) {
       ctl[0] = need;

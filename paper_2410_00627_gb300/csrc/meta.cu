@@ -73,6 +73,24 @@ __global__ void __launch_bounds__(1024) meta_kernel(Ctx c) {
   }
 }
 
+// Failure-detection self-test: one thread waits, with the bounded polling of
+// the scans' look-back, on a control-block flag that nothing sets; after
+// `polls` polls it latches DEVERR_TIMEOUT and returns.
+__global__ void wait_probe_kernel(Counters* ctr, long long polls) {
+  BoundedPoll poll(polls);
+  bool seen = false;
+  while (poll.more()) {
+    if (ld_acquire_u64(&ctr->never_set) != 0ull) { seen = true; break; }
+    poll.backoff();
+  }
+  if (!seen) raise_err(ctr, DEVERR_TIMEOUT);
+}
+
+int launch_wait_probe(Counters* ctr, long long polls, cudaStream_t st) {
+  wait_probe_kernel<<<1, 1, 0, st>>>(ctr, polls);
+  return cudaGetLastError() == cudaSuccess ? SRTM_OK : SRTM_ERR_CUDA;
+}
+
 // ev (optional): two events recorded before and after the metadata kernel.
 // A single sequence needs no scan over sequences: its metadata is written by
 // the constants kernel instead (c.fold_meta), saving this launch.

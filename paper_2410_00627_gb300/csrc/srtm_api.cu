@@ -433,6 +433,28 @@ int srtm_smoother_batch_sequential(const srtm_batch* b, srtm_precision prec, con
   return batch(b, prec, smooth, filt, 1, stream, 1);
 }
 
+int srtm_selftest_wait(long long polls, srtm_stream_t stream) {
+  if (polls < 1 || polls > SPIN_LIMIT) return fail(SRTM_ERR_ARG, "polls=%lld outside 1..%lld", polls, SPIN_LIMIT);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAXDEV) return fail(SRTM_ERR_CUDA, "no device");
+  std::lock_guard<std::mutex> lk(g_mu);
+  DevState& d = g_dev[dev];
+  if (!d.ws) {  // the control block lives at the start of the workspace
+    const size_t bytes = 4096;
+    if (cudaMalloc(&d.ws, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      d.ws = nullptr;
+      return fail(SRTM_ERR_CUDA, "workspace cudaMalloc failed");
+    }
+    if (cudaMemset(d.ws, 0, bytes) != cudaSuccess) return fail(SRTM_ERR_CUDA, "workspace memset failed");
+    d.ws_bytes = bytes;
+  }
+  d.last_launches = 1;
+  if (launch_wait_probe((Counters*)d.ws, polls, (cudaStream_t)stream))
+    return fail(SRTM_ERR_CUDA, "launch of the wait probe failed");
+  return SRTM_OK;
+}
+
 int srtm_status(srtm_stream_t stream) {
   if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess)
     return fail(SRTM_ERR_CUDA, "stream synchronize failed: %s", cudaGetErrorString(cudaGetLastError()));

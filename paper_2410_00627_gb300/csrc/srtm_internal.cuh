@@ -24,6 +24,7 @@ struct Counters {
   unsigned int err;           // DevErr bits, sticky until srtm_status()
   unsigned int call_ok;       // 1 when this call's metadata passed validation
   long long total_tiles_f, total_tiles_s;
+  unsigned long long never_set;  // stays 0: the flag of the bounded-wait self-test
 };
 
 // Per-sequence metadata (SoA, written by the metadata kernel).
@@ -198,6 +199,22 @@ __device__ __forceinline__ int find_segment(const long long* off, int n, long lo
 
 __device__ __forceinline__ void raise_err(Counters* c, unsigned bits) { atomicOr(&c->err, bits); }
 
+// Bounded polling for every device-side wait: at most `limit` polls, with an
+// exponential __nanosleep back-off (32 ns doubling up to 1 us) between them.
+// A wait that runs out returns with its condition unmet and the caller
+// latches DEVERR_TIMEOUT, so no wait can hang a kernel.
+struct BoundedPoll {
+  long long left;
+  unsigned ns;
+  __device__ explicit BoundedPoll(long long limit) : left(limit), ns(32) {}
+  __device__ bool more() const { return left > 0; }
+  __device__ void backoff() {
+    --left;
+    __nanosleep(ns);
+    if (ns < 1024) ns <<= 1;
+  }
+};
+
 // ---------------------------------------------------------------------------
 // host-side launch entry points (defined per nx in inst_nx*.cu)
 // ---------------------------------------------------------------------------
@@ -215,6 +232,8 @@ int launch_device_path(const Ctx& c, srtm_precision prec, const Shapes& sh, cuda
 
 // sums the per-interval terms into the caller's log-likelihood output (meta.cu)
 int launch_loglik(const Ctx& c, cudaStream_t st);
+// bounded wait on a flag that nothing sets (failure-detection self-test, meta.cu)
+int launch_wait_probe(Counters* ctr, long long polls, cudaStream_t st);
 
 template <int NX>
 int query_shapes(srtm_precision prec, int scan_groups, int scan_elems, int window, int recover_threads,

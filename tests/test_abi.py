@@ -52,6 +52,10 @@ def test_rejects_bad_arguments_without_gpu(lib):
     assert lib.srtm_smoother(ctypes.byref(bad), 0, None, None, None) == -1
     bad = api.Problem(2, 1, 2, 3)
     assert lib.srtm_smoother(ctypes.byref(bad), 7, None, None, None) == -1
+    assert lib.srtm_selftest_wait(0, None) == -1            # polls out of range
+    assert lib.srtm_selftest_wait(2000001, None) == -1
+    bad = api.Problem(9, 1, 2, 3)
+    assert lib.srtm_smoother_sequential(ctypes.byref(bad), 0, None, None, None) == -6
 
 
 def test_tuning_validation_and_roundtrip(lib):
