@@ -19,8 +19,11 @@
  *
  * Conventions for all entry points
  *   - Matrices are row-major IEEE float64.  Device entry points take DEVICE
- *     pointers (cudaMalloc'd or managed); passing a host pointer returns
- *     SRTM_ERR_ARG.  The caller owns every input and output buffer.
+ *     pointers (cudaMalloc'd or managed) for every input; outputs may also be
+ *     mapped pinned host memory (cudaHostAlloc'd or registered, addressed by
+ *     the device at its host address), which the kernels then write directly.
+ *     Any other host pointer returns SRTM_ERR_ARG.  The caller owns every
+ *     input and output buffer.
  *   - Calls are asynchronous on `stream` (NULL = legacy default stream).
  *     Errors found on the device (a look-back wait that exceeded its bound, a
  *     singular solve, inconsistent batch metadata) are latched on the device
@@ -159,9 +162,12 @@ int srtm_smoother_batch_sequential(const srtm_batch *b, srtm_precision prec, con
                                    const srtm_output *filt, srtm_stream_t stream);
 
 /* srtm_smoother with HOST buffers (pageable or pinned) for every input and
- * output.  Copies the inputs to a library-owned device staging area, runs the
- * device path, copies the results back and synchronizes the stream; returns
- * the final status (as srtm_status).                                          */
+ * output.  Copies the inputs to a library-owned device staging area and runs
+ * the device path.  Outputs in pinned host memory that the device can address
+ * (cudaHostAlloc / registered memory with unified addressing) are written by
+ * the kernels directly, over the CPU-GPU link, with no staging copy; other
+ * outputs are staged on the device and copied back.  Synchronizes the stream
+ * and returns the final status (as srtm_status).                              */
 int srtm_smoother_host(const srtm_problem *host_p, srtm_precision prec,
                        const srtm_output *host_smooth, srtm_stream_t stream);
 

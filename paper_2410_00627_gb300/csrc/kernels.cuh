@@ -1169,17 +1169,56 @@ __device__ __forceinline__ void recover_smooth(const TR* Om, const TR* om, TR (&
   }
 }
 
-// writes fast row f (mean, mirrored covariance) and, for i == l, slow row
+// Output stores of the recovery.  The fast rows of a warp (32 consecutive
+// fast steps) are contiguous in the outputs, so each lane first puts its mean
+// and mirrored covariance into the warp's shared-memory slab and the warp then
+// writes the block out with consecutive lanes on consecutive words: every
+// store instruction covers whole cache lines (this matters most when the
+// outputs are pinned host memory written over the CPU-GPU link).  The slow
+// row (i == l, one fast step in l) is written by its own thread.
+template <int NX>
+struct RecSlab {
+  static constexpr int NN = NX * NX, ROW = NX + NN;
+  static constexpr int MEAN = 0, COV = 32 * NX;  // offsets in the warp's slab (doubles)
+  static constexpr int WARP_DOUBLES = 32 * ROW;
+};
+
 template <int NX, class TR>
-__device__ __forceinline__ void store_state(long long f, long long row, bool last_i, double* mo, double* co,
-                                            double* smo, double* sco, const TR* mv, const TR* Pu) {
+__device__ __forceinline__ void warp_store_fast(double* slab, int lane, long long f0, int nvalid, bool active,
+                                                double* mo, double* co, const TR* mv, const TR* Pu) {
+  using SB = RecSlab<NX>;
   constexpr int NN = NX * NX;
-  if (mo) {
+  if (!mo && !co) return;  // uniform over the warp
+  __syncwarp();
+  if (active) {
 #pragma unroll
-    for (int r = 0; r < NX; ++r) mo[f * NX + r] = (double)mv[r];
+    for (int r = 0; r < NX; ++r) slab[SB::MEAN + lane * NX + r] = (double)mv[r];
+    int u = 0;
+#pragma unroll
+    for (int r = 0; r < NX; ++r)
+#pragma unroll
+      for (int q = r; q < NX; ++q) {
+        const double v = (double)Pu[u++];
+        slab[SB::COV + lane * NN + r * NX + q] = v;
+        slab[SB::COV + lane * NN + q * NX + r] = v;
+      }
   }
-  if (co) {
-    double* dst = co + f * NN;
+  __syncwarp();
+  if (mo)
+    for (int e = lane; e < nvalid * NX; e += 32) mo[f0 * NX + e] = slab[SB::MEAN + e];
+  if (co)
+    for (int e = lane; e < nvalid * NN; e += 32) co[f0 * NN + e] = slab[SB::COV + e];
+}
+
+template <int NX, class TR>
+__device__ __forceinline__ void store_slow(long long row, double* smo, double* sco, const TR* mv, const TR* Pu) {
+  constexpr int NN = NX * NX;
+  if (smo) {
+#pragma unroll
+    for (int r = 0; r < NX; ++r) smo[row * NX + r] = (double)mv[r];
+  }
+  if (sco) {
+    double* dst = sco + row * NN;
     int u = 0;
 #pragma unroll
     for (int r = 0; r < NX; ++r)
@@ -1190,48 +1229,50 @@ __device__ __forceinline__ void store_state(long long f, long long row, bool las
         dst[q * NX + r] = v;
       }
   }
-  if (last_i) {
-    if (smo) {
-#pragma unroll
-      for (int r = 0; r < NX; ++r) smo[row * NX + r] = (double)mv[r];
-    }
-    if (sco) {
-      double* dst = sco + row * NN;
-      int u = 0;
-#pragma unroll
-      for (int r = 0; r < NX; ++r)
-#pragma unroll
-        for (int q = r; q < NX; ++q) {
-          const double v = (double)Pu[u++];
-          dst[r * NX + q] = v;
-          dst[q * NX + r] = v;
-        }
-    }
-  }
+}
+
+// dynamic shared memory of the recovery: one slab per warp
+template <int NX>
+__host__ __device__ inline size_t recover_smem_bytes(int threads) {
+  return (size_t)((threads + 31) / 32) * RecSlab<NX>::WARP_DOUBLES * sizeof(double);
 }
 
 template <int NX, class TR>
 __global__ void __launch_bounds__(128, 3) recover_kernel(Ctx c) {
   constexpr int NT = NX * (NX + 1) / 2;
+  extern __shared__ __align__(16) double rslab[];
   if (!c.ctr->call_ok) return;
   const long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (f >= c.total_fast) return;
-  const FastIdx x = fast_index(c, f);
-  const bool last_i = x.i == x.l;
-  const bool smooth_k = c.smoothing && (x.k < x.N - 1);
+  const int lane = threadIdx.x & 31;
+  const long long f0 = f - lane;  // first fast row of this warp
+  const long long left = c.total_fast - f0;
+  if (left <= 0) return;  // the whole warp is past the end
+  const int nvalid = left < 32 ? (int)left : 32;
+  const bool active = lane < nvalid;
+  double* slab = rslab + (size_t)(threadIdx.x >> 5) * RecSlab<NX>::WARP_DOUBLES;
+  FastIdx x;
+  bool last_i = false, smooth_k = false;
   TR mf[NX], Pf[NT], Pfl[NX][NX];
-  recover_filtered<NX, TR>(c, x, smooth_k, mf, Pf, Pfl);
+  if (active) {
+    x = fast_index(c, f);
+    last_i = x.i == x.l;
+    smooth_k = c.smoothing && (x.k < x.N - 1);
+    recover_filtered<NX, TR>(c, x, smooth_k, mf, Pf, Pfl);
+  }
   // filtered outputs (the call's outputs for a filter, the optional extras for a smoother)
   if (!c.smoothing) {
-    store_state<NX, TR>(f, x.row, last_i, c.fast_mean, c.fast_cov, c.slow_mean, c.slow_cov, mf, Pf);
+    warp_store_fast<NX, TR>(slab, lane, f0, nvalid, active, c.fast_mean, c.fast_cov, mf, Pf);
+    if (active && last_i) store_slow<NX, TR>(x.row, c.slow_mean, c.slow_cov, mf, Pf);
     return;
   }
-  store_state<NX, TR>(f, x.row, last_i, c.ffast_mean, c.ffast_cov, c.fslow_mean, c.fslow_cov, mf, Pf);
-  if (smooth_k) {
+  warp_store_fast<NX, TR>(slab, lane, f0, nvalid, active, c.ffast_mean, c.ffast_cov, mf, Pf);
+  if (active && last_i) store_slow<NX, TR>(x.row, c.fslow_mean, c.fslow_cov, mf, Pf);
+  if (active && smooth_k) {
     const TR* Om = (const TR*)c.sfin + x.row * SFin<NX>::SIZE;
     recover_smooth<NX, TR>(Om + SFin<NX>::Om, Om + SFin<NX>::om, mf, Pf, Pfl);
   }
-  store_state<NX, TR>(f, x.row, last_i, c.fast_mean, c.fast_cov, c.slow_mean, c.slow_cov, mf, Pf);
+  warp_store_fast<NX, TR>(slab, lane, f0, nvalid, active, c.fast_mean, c.fast_cov, mf, Pf);
+  if (active && last_i) store_slow<NX, TR>(x.row, c.slow_mean, c.slow_cov, mf, Pf);
 }
 
 // ===========================================================================
@@ -1316,6 +1357,8 @@ __global__ void __launch_bounds__(128) setup_kernel(Ctx c) {
 // ===========================================================================
 template <class Op>
 struct SetupTag {};
+template <int NX, class TR>
+struct RecoverTag {};
 
 // Raises (never lowers) a kernel's dynamic shared-memory limit on the current
 // device: launches with other shapes may still need a larger limit.
@@ -1358,6 +1401,7 @@ int query_shapes_t(int scan_groups, int scan_elems, int window, int recover_thre
   sh->smem_setup = setup_separate ? (size_t)(128 / SetupGeom<NX>::SG) * SetupGeom<NX>::template slot_bytes<T, TS>() : 0;
   if (setup_separate) set_smem_attr<SetupTag<FOp>>((const void*)setup_kernel<NX, T, TS>, sh->smem_setup);
   sh->recover_threads = recover_threads;
+  set_smem_attr<RecoverTag<NX, TR>>((const void*)recover_kernel<NX, TR>, recover_smem_bytes<NX>(recover_threads));
   if (cudaGetLastError() != cudaSuccess) return SRTM_ERR_CUDA;
   return SRTM_OK;
 }
@@ -1405,7 +1449,7 @@ int launch_t(const Ctx& c, const Shapes& sh, cudaStream_t st, cudaEvent_t* ev) {
     scan_kernel<SOp><<<sh.grid_s, sh.scan_groups_s * G, sh.smem_s, st>>>(c, sh.scan_groups_s, sh.scan_elems_s, sh.window_s);
   if (ev) cudaEventRecord(ev[3], st);
   const long long blocks = (c.total_fast + sh.recover_threads - 1) / sh.recover_threads;
-  recover_kernel<NX, TR><<<(unsigned)blocks, sh.recover_threads, 0, st>>>(c);
+  recover_kernel<NX, TR><<<(unsigned)blocks, sh.recover_threads, recover_smem_bytes<NX>(sh.recover_threads), st>>>(c);
   if (ev) cudaEventRecord(ev[4], st);
   return cudaGetLastError() == cudaSuccess ? SRTM_OK : SRTM_ERR_CUDA;
 }

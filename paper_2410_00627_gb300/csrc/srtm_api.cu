@@ -68,6 +68,18 @@ srtm_tuning effective_tuning(int nx, srtm_precision prec) {
   return t;
 }
 
+// Mapped pinned host memory: the address the device uses for it (with unified
+// addressing the host address itself), or NULL for any other pointer.
+void* mapped_host_ptr(const void* p) {
+  if (!p) return nullptr;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 bool is_device_ptr(const void* p) {
   if (!p) return false;
   cudaPointerAttributes a;
@@ -287,7 +299,8 @@ int check_outputs(const srtm_output* o, const char* what) {
   const double* ps[5] = {o->fast_mean, o->fast_cov, o->slow_mean, o->slow_cov, o->loglik};
   const char* nm[5] = {"fast_mean", "fast_cov", "slow_mean", "slow_cov", "loglik"};
   for (int i = 0; i < 5; ++i)
-    if (ps[i] && !is_device_ptr(ps[i])) return fail(SRTM_ERR_ARG, "%s.%s is not a device pointer", what, nm[i]);
+    if (ps[i] && !is_device_ptr(ps[i]) && mapped_host_ptr(ps[i]) != ps[i])
+      return fail(SRTM_ERR_ARG, "%s.%s is neither device memory nor mapped pinned host memory", what, nm[i]);
   return SRTM_OK;
 }
 
@@ -491,9 +504,19 @@ int srtm_smoother_host(const srtm_problem* hp, srtm_precision prec, const srtm_o
   const size_t out_cnt[5] = {(size_t)(N * l * nx), (size_t)(N * l * nx * nx), (size_t)(N * nx), (size_t)(N * nx * nx),
                              1};
   double* hout_p[5] = {hout->fast_mean, hout->fast_cov, hout->slow_mean, hout->slow_cov, hout->loglik};
+  // outputs in mapped pinned host memory are written by the kernels directly
+  // (over the CPU-GPU link); the others are staged and copied back
+  double* direct[5];
+  for (int i = 0; i < 5; ++i) {
+    direct[i] = (double*)mapped_host_ptr(hout_p[i]);
+    if (direct[i] != hout_p[i]) direct[i] = nullptr;  // only where the device uses the host address
+  }
   size_t off[14], o = 0;
   for (int i = 0; i < n_in; ++i) { off[i] = o; o += a256(in_cnt[i] * sizeof(double)); }
-  for (int i = 0; i < 5; ++i) { off[9 + i] = o; o += hout_p[i] ? a256(out_cnt[i] * sizeof(double)) : 0; }
+  for (int i = 0; i < 5; ++i) {
+    off[9 + i] = o;
+    o += (hout_p[i] && !direct[i]) ? a256(out_cnt[i] * sizeof(double)) : 0;
+  }
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAXDEV) return fail(SRTM_ERR_CUDA, "no device");
   unsigned char* stg = nullptr;
@@ -523,11 +546,11 @@ int srtm_smoother_host(const srtm_problem* hp, srtm_precision prec, const srtm_o
   dp.u = n_in > 7 ? (const double*)(stg + off[8]) : nullptr;
   srtm_output dout;
   double** dsl[5] = {&dout.fast_mean, &dout.fast_cov, &dout.slow_mean, &dout.slow_cov, &dout.loglik};
-  for (int i = 0; i < 5; ++i) *dsl[i] = hout_p[i] ? (double*)(stg + off[9 + i]) : nullptr;
+  for (int i = 0; i < 5; ++i) *dsl[i] = direct[i] ? direct[i] : (hout_p[i] ? (double*)(stg + off[9 + i]) : nullptr);
   rc = srtm_smoother(&dp, prec, &dout, nullptr, stream);
   if (rc) return rc;
   for (int i = 0; i < 5; ++i)
-    if (hout_p[i] &&
+    if (hout_p[i] && !direct[i] &&
         cudaMemcpyAsync(hout_p[i], *dsl[i], out_cnt[i] * sizeof(double), cudaMemcpyDefault, st) != cudaSuccess)
       return fail(SRTM_ERR_CUDA, "output copy %d failed", i);
   return srtm_status(stream);

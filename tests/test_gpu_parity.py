@@ -363,3 +363,26 @@ def test_batch_descriptor_keeps_its_tensors_alive(oracle_mod):
         ref = oracle_mod.sequential(p)["fast_smooth_mean"][p.ratio - 1::p.ratio]
         compare({"slow_mean": got[so:so + p.n_slow]}, {"slow_mean": ref}, *TOL["fp64"], label=p.name)
         so += p.n_slow
+
+
+def test_host_entry_point_direct_pinned_outputs_match_staged():
+    """Pinned host outputs are written by the kernels directly; pageable ones
+    are staged and copied: both equal the device path bit for bit."""
+    import torch
+
+    from paper_2410_00627_gb300 import api
+    prob = synth.config2(seed=21, n_slow=300, keep_states=False)
+    host_in = [np.ascontiguousarray(getattr(prob, k)) for k in ("F", "Q", "H", "R", "m0", "P0", "y")]
+    n_fast, nx = prob.n_slow * prob.ratio, prob.nx
+    shapes = {"fast_mean": (n_fast, nx), "fast_cov": (n_fast, nx, nx), "slow_mean": (prob.n_slow, nx),
+              "slow_cov": (prob.n_slow, nx, nx)}
+    pinned = {k: torch.full(s, np.nan, dtype=torch.float64, pin_memory=True).numpy() for k, s in shapes.items()}
+    for precision in ("fp64", "mixed"):
+        direct = api.smoother_host(*host_in, prob.ratio, precision=precision, out=pinned)
+        staged = api.smoother_host(*host_in, prob.ratio, precision=precision)
+        dev, _ = api.smoother(*[to_dev(a) for a in host_in], prob.ratio, precision=precision)
+        api.status()
+        for k in shapes:
+            want = dev[k].cpu().numpy()
+            assert np.array_equal(direct[k], want), (precision, k)
+            assert np.array_equal(staged[k], want), (precision, k)
