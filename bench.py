@@ -656,7 +656,8 @@ def run_e2e(args, prob, api, torch, flush):
     d2h = sum(a.nbytes for a in on.values())
     return {"value": n_fast / (float(np.mean(ms)) * 1e-3), "unit": UNIT, "ms_per_step": float(np.mean(ms)),
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-            "api": "srtm_smoother_host (C-ABI, pinned host buffers)"}
+            "api": "srtm_smoother_host (C-ABI, pinned host buffers: model arrays packed into one H2D copy, "
+                   "y read and outputs written by the kernels directly over the CPU-GPU link)"}
 
 
 def oracle_time(prob, seconds):

@@ -19,11 +19,11 @@
  *
  * Conventions for all entry points
  *   - Matrices are row-major IEEE float64.  Device entry points take DEVICE
- *     pointers (cudaMalloc'd or managed) for every input; outputs may also be
+ *     pointers (cudaMalloc'd or managed); inputs and outputs may also be
  *     mapped pinned host memory (cudaHostAlloc'd or registered, addressed by
- *     the device at its host address), which the kernels then write directly.
- *     Any other host pointer returns SRTM_ERR_ARG.  The caller owns every
- *     input and output buffer.
+ *     the device at its host address), which the kernels then read or write
+ *     directly over the CPU-GPU link.  Any other host pointer returns
+ *     SRTM_ERR_ARG.  The caller owns every input and output buffer.
  *   - Calls are asynchronous on `stream` (NULL = legacy default stream).
  *     Errors found on the device (a look-back wait that exceeded its bound, a
  *     singular solve, inconsistent batch metadata) are latched on the device
@@ -162,12 +162,13 @@ int srtm_smoother_batch_sequential(const srtm_batch *b, srtm_precision prec, con
                                    const srtm_output *filt, srtm_stream_t stream);
 
 /* srtm_smoother with HOST buffers (pageable or pinned) for every input and
- * output.  Copies the inputs to a library-owned device staging area and runs
- * the device path.  Outputs in pinned host memory that the device can address
- * (cudaHostAlloc / registered memory with unified addressing) are written by
- * the kernels directly, over the CPU-GPU link, with no staging copy; other
- * outputs are staged on the device and copied back.  Synchronizes the stream
- * and returns the final status (as srtm_status).                              */
+ * output.  The model arrays (F, Q, H, R, m0, P0, B) are packed into a
+ * library-owned pinned buffer and copied to the device in one transfer.  The
+ * per-step arrays (y, u) and the outputs, where they are pinned host memory
+ * the device can address (cudaHostAlloc'd or registered, unified addressing),
+ * are read and written by the kernels directly over the CPU-GPU link; where
+ * they are not, they are staged on the device and copied.  Synchronizes the
+ * stream and returns the final status (as srtm_status).                       */
 int srtm_smoother_host(const srtm_problem *host_p, srtm_precision prec,
                        const srtm_output *host_smooth, srtm_stream_t stream);
 

@@ -1183,6 +1183,21 @@ struct RecSlab {
   static constexpr int WARP_DOUBLES = 32 * ROW;
 };
 
+// cnt consecutive doubles from shared memory (16-byte aligned) to global
+// memory: as 16-byte stores (the odd last one by lane 0) when dst is 16-byte
+// aligned, else as 8-byte stores
+__device__ __forceinline__ void warp_copy_out(double* dst, const double* src, int cnt, int lane) {
+  if (reinterpret_cast<uintptr_t>(dst) & 15) {
+    for (int e = lane; e < cnt; e += 32) dst[e] = src[e];
+    return;
+  }
+  const int pairs = cnt >> 1;
+  double2* d2 = reinterpret_cast<double2*>(dst);
+  const double2* s2 = reinterpret_cast<const double2*>(src);
+  for (int e = lane; e < pairs; e += 32) d2[e] = s2[e];
+  if ((cnt & 1) && lane == 0) dst[cnt - 1] = src[cnt - 1];
+}
+
 template <int NX, class TR>
 __device__ __forceinline__ void warp_store_fast(double* slab, int lane, long long f0, int nvalid, bool active,
                                                 double* mo, double* co, const TR* mv, const TR* Pu) {
@@ -1204,10 +1219,10 @@ __device__ __forceinline__ void warp_store_fast(double* slab, int lane, long lon
       }
   }
   __syncwarp();
-  if (mo)
-    for (int e = lane; e < nvalid * NX; e += 32) mo[f0 * NX + e] = slab[SB::MEAN + e];
-  if (co)
-    for (int e = lane; e < nvalid * NN; e += 32) co[f0 * NN + e] = slab[SB::COV + e];
+  // the warp's first row is a multiple of 32, so both blocks keep the
+  // alignment of the output base (16-byte stores for aligned outputs)
+  if (mo) warp_copy_out(mo + f0 * NX, slab + SB::MEAN, nvalid * NX, lane);
+  if (co) warp_copy_out(co + f0 * NN, slab + SB::COV, nvalid * NN, lane);
 }
 
 template <int NX, class TR>

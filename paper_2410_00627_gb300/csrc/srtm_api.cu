@@ -34,6 +34,9 @@ struct DevState {
   size_t ws_bytes = 0;
   void* stage = nullptr;
   size_t stage_bytes = 0;
+  void* hstage = nullptr;            // pinned host buffer: the host entry's packed small inputs
+  size_t hstage_bytes = 0;
+  cudaEvent_t hstage_ev = nullptr;   // recorded after the copy out of hstage
   int sms = 0;
   cudaEvent_t ev[NSTAGE + 1] = {};  // stage-timing events (created on first use)
   cudaStream_t ev_stream = nullptr;
@@ -310,7 +313,8 @@ int check_inputs(const double* F, const double* Q, const double* H, const double
   const char* nm[7] = {"F", "Q", "H", "R", "m0", "P0", "y"};
   for (int i = 0; i < 7; ++i) {
     if (!ps[i]) return fail(SRTM_ERR_ARG, "%s is NULL", nm[i]);
-    if (!is_device_ptr(ps[i])) return fail(SRTM_ERR_ARG, "%s is not a device pointer", nm[i]);
+    if (!is_device_ptr(ps[i]) && mapped_host_ptr(ps[i]) != ps[i])
+      return fail(SRTM_ERR_ARG, "%s is not a device pointer (nor mapped pinned host memory)", nm[i]);
   }
   return SRTM_OK;
 }
@@ -320,7 +324,9 @@ int check_controls(int nu, const double* B, const double* u) {
   if (nu < 0 || nu > SRTM_MAX_NU) return fail(SRTM_ERR_UNSUPPORTED, "nu=%d outside 0..%d", nu, SRTM_MAX_NU);
   if (nu == 0) return SRTM_OK;
   if (!B || !u) return fail(SRTM_ERR_ARG, "nu=%d needs B and u", nu);
-  if (!is_device_ptr(B) || !is_device_ptr(u)) return fail(SRTM_ERR_ARG, "B and u must be device pointers");
+  for (const double* q : {B, u})
+    if (!is_device_ptr(q) && mapped_host_ptr(q) != q)
+      return fail(SRTM_ERR_ARG, "B and u must be device pointers (or mapped pinned host memory)");
   return SRTM_OK;
 }
 
@@ -511,8 +517,24 @@ int srtm_smoother_host(const srtm_problem* hp, srtm_precision prec, const srtm_o
     direct[i] = (double*)mapped_host_ptr(hout_p[i]);
     if (direct[i] != hout_p[i]) direct[i] = nullptr;  // only where the device uses the host address
   }
+  // the model arrays (F, Q, H, R, m0, P0, B) are packed on the host into one
+  // pinned buffer and copied in one transfer; the per-step arrays y and u are
+  // read by the kernels directly when they are mapped pinned host memory
+  const bool small[9] = {true, true, true, true, true, true, false, true, false};
+  const double* bulk_direct[9] = {};
   size_t off[14], o = 0;
-  for (int i = 0; i < n_in; ++i) { off[i] = o; o += a256(in_cnt[i] * sizeof(double)); }
+  for (int i = 0; i < n_in; ++i)
+    if (small[i]) { off[i] = o; o += a256(in_cnt[i] * sizeof(double)); }
+  const size_t small_bytes = o;
+  for (int i = 0; i < n_in; ++i) {
+    if (small[i]) continue;
+    if (mapped_host_ptr(in[i]) == (const void*)in[i]) {
+      bulk_direct[i] = in[i];
+    } else {
+      off[i] = o;
+      o += a256(in_cnt[i] * sizeof(double));
+    }
+  }
   for (int i = 0; i < 5; ++i) {
     off[9 + i] = o;
     o += (hout_p[i] && !direct[i]) ? a256(out_cnt[i] * sizeof(double)) : 0;
@@ -520,9 +542,24 @@ int srtm_smoother_host(const srtm_problem* hp, srtm_precision prec, const srtm_o
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAXDEV) return fail(SRTM_ERR_CUDA, "no device");
   unsigned char* stg = nullptr;
+  unsigned char* hst = nullptr;
+  cudaEvent_t hev = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_mu);
     DevState& d = g_dev[dev];
+    if (!d.hstage_ev && cudaEventCreateWithFlags(&d.hstage_ev, cudaEventDisableTiming) != cudaSuccess)
+      return fail(SRTM_ERR_CUDA, "event creation failed");
+    if (d.hstage_bytes < small_bytes) {
+      if (d.hstage) { cudaEventSynchronize(d.hstage_ev); cudaFreeHost(d.hstage); d.hstage = nullptr; d.hstage_bytes = 0; }
+      if (cudaHostAlloc(&d.hstage, small_bytes, cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        d.hstage = nullptr;
+        return fail(SRTM_ERR_CUDA, "pinned staging allocation of %zu bytes failed", small_bytes);
+      }
+      d.hstage_bytes = small_bytes;
+    }
+    hst = (unsigned char*)d.hstage;
+    hev = d.hstage_ev;
     if (d.stage_bytes < o) {
       if (d.stage) { cudaDeviceSynchronize(); cudaFree(d.stage); d.stage = nullptr; d.stage_bytes = 0; }
       if (cudaMalloc(&d.stage, o) != cudaSuccess) {
@@ -534,16 +571,22 @@ int srtm_smoother_host(const srtm_problem* hp, srtm_precision prec, const srtm_o
     stg = (unsigned char*)d.stage;
   }
   cudaStream_t st = (cudaStream_t)stream;
+  // the previous call's copy out of the pinned buffer must be done before it is rewritten
+  if (cudaEventSynchronize(hev) != cudaSuccess) return fail(SRTM_ERR_CUDA, "staging event wait failed");
   for (int i = 0; i < n_in; ++i)
-    if (cudaMemcpyAsync(stg + off[i], in[i], in_cnt[i] * sizeof(double), cudaMemcpyDefault, st) != cudaSuccess)
+    if (small[i]) memcpy(hst + off[i], in[i], in_cnt[i] * sizeof(double));
+  if (cudaMemcpyAsync(stg, hst, small_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaEventRecord(hev, st) != cudaSuccess)
+    return fail(SRTM_ERR_CUDA, "model input copy failed");
+  for (int i = 0; i < n_in; ++i)
+    if (!small[i] && !bulk_direct[i] &&
+        cudaMemcpyAsync(stg + off[i], in[i], in_cnt[i] * sizeof(double), cudaMemcpyDefault, st) != cudaSuccess)
       return fail(SRTM_ERR_CUDA, "input copy %d failed", i);
+  auto at = [&](int i) { return bulk_direct[i] ? bulk_direct[i] : (const double*)(stg + off[i]); };
   srtm_problem dp = *hp;
-  dp.F = (const double*)(stg + off[0]); dp.Q = (const double*)(stg + off[1]);
-  dp.H = (const double*)(stg + off[2]); dp.R = (const double*)(stg + off[3]);
-  dp.m0 = (const double*)(stg + off[4]); dp.P0 = (const double*)(stg + off[5]);
-  dp.y = (const double*)(stg + off[6]);
-  dp.B = n_in > 7 ? (const double*)(stg + off[7]) : nullptr;
-  dp.u = n_in > 7 ? (const double*)(stg + off[8]) : nullptr;
+  dp.F = at(0); dp.Q = at(1); dp.H = at(2); dp.R = at(3); dp.m0 = at(4); dp.P0 = at(5); dp.y = at(6);
+  dp.B = n_in > 7 ? at(7) : nullptr;
+  dp.u = n_in > 7 ? at(8) : nullptr;
   srtm_output dout;
   double** dsl[5] = {&dout.fast_mean, &dout.fast_cov, &dout.slow_mean, &dout.slow_cov, &dout.loglik};
   for (int i = 0; i < 5; ++i) *dsl[i] = direct[i] ? direct[i] : (hout_p[i] ? (double*)(stg + off[9 + i]) : nullptr);
@@ -570,11 +613,13 @@ int srtm_release(void) {
   int cur = 0;
   cudaGetDevice(&cur);
   for (int d = 0; d < MAXDEV; ++d) {
-    if (!g_dev[d].ws && !g_dev[d].stage) continue;
+    if (!g_dev[d].ws && !g_dev[d].stage && !g_dev[d].hstage) continue;
     cudaSetDevice(d);
     cudaDeviceSynchronize();
     if (g_dev[d].ws) cudaFree(g_dev[d].ws);
     if (g_dev[d].stage) cudaFree(g_dev[d].stage);
+    if (g_dev[d].hstage) cudaFreeHost(g_dev[d].hstage);
+    if (g_dev[d].hstage_ev) cudaEventDestroy(g_dev[d].hstage_ev);
     for (int i = 0; i <= NSTAGE; ++i)
       if (g_dev[d].ev[i]) cudaEventDestroy(g_dev[d].ev[i]);
     g_dev[d] = DevState();

@@ -386,3 +386,50 @@ def test_host_entry_point_direct_pinned_outputs_match_staged():
             want = dev[k].cpu().numpy()
             assert np.array_equal(direct[k], want), (precision, k)
             assert np.array_equal(staged[k], want), (precision, k)
+
+
+def test_host_entry_point_reads_pinned_inputs_directly():
+    """Pinned y (and u) are read by the kernels in place; results equal the
+    device path's bit for bit, with and without known inputs."""
+    import torch
+
+    from paper_2410_00627_gb300 import api
+
+    def pin(a):
+        t = torch.empty(a.shape, dtype=torch.float64, pin_memory=True)
+        t.numpy()[...] = a
+        return t.numpy()
+
+    for prob in (synth.config2(seed=22, n_slow=200, keep_states=False), synth.random_model(23, 3, 2, 5, 90, nu=2)):
+        keys = ("F", "Q", "H", "R", "m0", "P0", "y")
+        host_in = [pin(np.ascontiguousarray(getattr(prob, k))) for k in keys]
+        extra = {} if prob.B is None else {"B": pin(prob.B), "u": pin(prob.u)}
+        got = api.smoother_host(*host_in, prob.ratio, precision="fp64", loglik=True, **extra)
+        dev_extra = {} if prob.B is None else {"B": to_dev(prob.B), "u": to_dev(prob.u)}
+        want, _ = api.smoother(*[to_dev(getattr(prob, k)) for k in keys], prob.ratio, precision="fp64",
+                               outputs=api.ALL_OUTPUTS, **dev_extra)
+        api.status()
+        for k in api.ALL_OUTPUTS:
+            assert np.array_equal(got[k], want[k].cpu().numpy()), (prob.name, k)
+
+
+def test_outputs_at_8_byte_offsets():
+    """Output buffers that are only 8-byte aligned (views one double into a
+    larger tensor) take the 8-byte store path and give the same results."""
+    import torch
+
+    from paper_2410_00627_gb300 import api
+    prob = synth.random_model(24, 3, 2, 5, 37)
+    args = [to_dev(getattr(prob, k)) for k in ("F", "Q", "H", "R", "m0", "P0", "y")]
+    n_fast, nx = prob.n_slow * prob.ratio, prob.nx
+    base = {"fast_mean": n_fast * nx, "fast_cov": n_fast * nx * nx, "slow_mean": prob.n_slow * nx,
+            "slow_cov": prob.n_slow * nx * nx}
+    shapes = {"fast_mean": (n_fast, nx), "fast_cov": (n_fast, nx, nx), "slow_mean": (prob.n_slow, nx),
+              "slow_cov": (prob.n_slow, nx, nx)}
+    odd = {k: torch.empty(n + 1, dtype=torch.float64, device="cuda")[1:].view(shapes[k]) for k, n in base.items()}
+    assert all(v.data_ptr() % 16 == 8 for v in odd.values())
+    got, _ = api.smoother(*args, prob.ratio, out=odd)
+    want, _ = api.smoother(*args, prob.ratio)
+    api.status()
+    for k in shapes:
+        assert torch.equal(got[k], want[k]), k
