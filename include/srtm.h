@@ -196,7 +196,7 @@ int srtm_release(void);
 /* Tuning of the launch shapes (lane groups per scan block, elements per lane
  * group, recovery block size, look-back depth) for one (nx, precision).  Zero
  * values keep the built-in choice (128/lanes-per-group groups, 4 elements,
- * 128 threads, window 16, setup inside the filter scan).  Returns SRTM_ERR_ARG for out-of-range values.
+ * 128 threads, window 16, setup inside the filter scan, one recovery kernel).  Returns SRTM_ERR_ARG for out-of-range values.
  * The setting is process-wide and applies to the calls issued after it.     */
 typedef struct {
   int scan_groups;      /* lane groups per scan block: a power of two such that
@@ -210,6 +210,15 @@ typedef struct {
                            records): 1 = inside the filter scan, after each
                            tile's results; 2 = its own kernel after the filter
                            scan (one more launch)                            */
+  int recover_split;    /* fast-rate recovery of smoother calls: 1 = one kernel
+                           after the smoother scan; 2 = split in two: the
+                           filtered half on a library-owned second stream,
+                           concurrently with the smoother scan, the smoothing
+                           half after it (one more launch; needs
+                           total_fast*(nx + nx(nx+1)/2 + nx^2) recovery-type
+                           words of workspace and is used only while that is
+                           at most 4 GiB and every output is device memory,
+                           else 1 applies)                                   */
 } srtm_tuning;
 int srtm_set_tuning(int nx, srtm_precision prec, const srtm_tuning *t);
 int srtm_get_tuning(int nx, srtm_precision prec, srtm_tuning *t);
@@ -219,11 +228,12 @@ int srtm_get_tuning(int nx, srtm_precision prec, srtm_tuning *t);
  * sequence of candidate tunings and keeps the fastest for (p->nx, prec) as if
  * by srtm_set_tuning: first the grid of scan_groups (every valid power of
  * two) x scan_elems (1, 2, 4, 8, 16, 32), then lookback_window (4, 8, 16, 32)
- * recover_threads (32, 64, 96, 128) and setup_mode (1, 2) one at a time from
- * the best so far.
- * Each candidate is run once untimed and then `reps` times (reps >= 1), timed
- * by CUDA events on `stream` around the call; its score is the fastest of
- * the reps.  Inputs and `smooth` are as for srtm_smoother (device buffers
+ * recover_threads (32, 64, 96, 128), setup_mode (1, 2) and recover_split
+ * (1, 2) one at a time from the best so far.
+ * Each candidate is run once untimed on `stream`, then captured into a CUDA
+ * graph on a private stream and the graph replayed `reps` times (reps >= 1),
+ * timed by CUDA events around each replay (device time without host launch
+ * cost); its score is the fastest of the reps.  Inputs and `smooth` are as for srtm_smoother (device buffers
  * owned by the caller); `smooth` is overwritten by every run.  The stream is
  * synchronized after each run.  On success *best (if not NULL) receives the
  * chosen tuning and *best_ms (if not NULL) its time in milliseconds.  Errors:
@@ -247,7 +257,9 @@ int srtm_last_call_launches(void);
  * around each of its launches.  srtm_stage_times() waits for the last timed
  * call of the current GPU and writes up to n durations in milliseconds, in
  * launch order: metadata, model constants, filter scan, interval setup,
- * smoother scan (0 for a filter call), fast-rate recovery.                   */
+ * smoother scan (0 for a filter call), fast-rate recovery (with a split
+ * recovery: its smoothing half; the filtered half runs beside the smoother
+ * scan on the second stream and is in no stage).                            */
 int srtm_set_stage_timing(int enable);
 int srtm_stage_times(float *ms, int n);
 

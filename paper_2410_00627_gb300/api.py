@@ -52,7 +52,7 @@ class Batch(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("scan_groups", c_int), ("scan_elems", c_int), ("recover_threads", c_int),
-                ("lookback_window", c_int), ("setup_mode", c_int)]
+                ("lookback_window", c_int), ("setup_mode", c_int), ("recover_split", c_int)]
 
 
 class SRTMError(RuntimeError):
@@ -295,9 +295,9 @@ def status(stream=None) -> None:
 
 
 def set_tuning(nx: int, precision: str, scan_groups=0, scan_elems=0, recover_threads=0, lookback_window=0,
-               setup_mode=0):
+               setup_mode=0, recover_split=0):
     _check(load().srtm_set_tuning(nx, PRECISION[precision], ctypes.byref(
-        Tuning(scan_groups, scan_elems, recover_threads, lookback_window, setup_mode))))
+        Tuning(scan_groups, scan_elems, recover_threads, lookback_window, setup_mode, recover_split))))
 
 
 def get_tuning(nx: int, precision: str) -> dict:

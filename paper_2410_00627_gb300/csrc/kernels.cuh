@@ -1252,9 +1252,18 @@ __host__ __device__ inline size_t recover_smem_bytes(int threads) {
   return (size_t)((threads + 31) / 32) * RecSlab<NX>::WARP_DOUBLES * sizeof(double);
 }
 
-template <int NX, class TR>
+// PHASE 0: the whole recovery after the smoother scan.  PHASE 1 / 2: the two
+// halves of a split recovery.  PHASE 1 needs only the filter scan and the
+// interval setup, so it runs on a second stream while the smoother scan runs:
+// it forms the filtered moments (and P^f_il), writes the filtered outputs the
+// caller asked for and keeps the moments in c.rscr.  PHASE 2 runs after the
+// smoother scan: it reads them back, applies the smoothing terms and writes
+// the smoothed outputs.  The arithmetic and its order are those of PHASE 0,
+// so the results are identical.
+template <int NX, class TR, int PHASE>
 __global__ void __launch_bounds__(128, 3) recover_kernel(Ctx c) {
-  constexpr int NT = NX * (NX + 1) / 2;
+  constexpr int NT = NX * (NX + 1) / 2, NN = NX * NX;
+  using RS = RecScr<NX>;
   extern __shared__ __align__(16) double rslab[];
   if (!c.ctr->call_ok) return;
   const long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -1272,7 +1281,18 @@ __global__ void __launch_bounds__(128, 3) recover_kernel(Ctx c) {
     x = fast_index(c, f);
     last_i = x.i == x.l;
     smooth_k = c.smoothing && (x.k < x.N - 1);
-    recover_filtered<NX, TR>(c, x, smooth_k, mf, Pf, Pfl);
+    if (PHASE < 2) {
+      recover_filtered<NX, TR>(c, x, smooth_k, mf, Pf, Pfl);
+    } else {
+      const TR* src = (const TR*)c.rscr + f * RS::SIZE;
+#pragma unroll
+      for (int r = 0; r < NX; ++r) mf[r] = src[RS::mf + r];
+#pragma unroll
+      for (int u = 0; u < NT; ++u) Pf[u] = src[RS::Pf + u];
+      if (smooth_k)
+#pragma unroll
+        for (int e = 0; e < NN; ++e) Pfl[e / NX][e % NX] = src[RS::Pfl + e];
+    }
   }
   // filtered outputs (the call's outputs for a filter, the optional extras for a smoother)
   if (!c.smoothing) {
@@ -1280,8 +1300,23 @@ __global__ void __launch_bounds__(128, 3) recover_kernel(Ctx c) {
     if (active && last_i) store_slow<NX, TR>(x.row, c.slow_mean, c.slow_cov, mf, Pf);
     return;
   }
-  warp_store_fast<NX, TR>(slab, lane, f0, nvalid, active, c.ffast_mean, c.ffast_cov, mf, Pf);
-  if (active && last_i) store_slow<NX, TR>(x.row, c.fslow_mean, c.fslow_cov, mf, Pf);
+  if (PHASE < 2) {
+    warp_store_fast<NX, TR>(slab, lane, f0, nvalid, active, c.ffast_mean, c.ffast_cov, mf, Pf);
+    if (active && last_i) store_slow<NX, TR>(x.row, c.fslow_mean, c.fslow_cov, mf, Pf);
+  }
+  if (PHASE == 1) {
+    if (active) {
+      TR* dst = (TR*)c.rscr + f * RS::SIZE;
+#pragma unroll
+      for (int r = 0; r < NX; ++r) dst[RS::mf + r] = mf[r];
+#pragma unroll
+      for (int u = 0; u < NT; ++u) dst[RS::Pf + u] = Pf[u];
+      if (smooth_k)
+#pragma unroll
+        for (int e = 0; e < NN; ++e) dst[RS::Pfl + e] = Pfl[e / NX][e % NX];
+    }
+    return;
+  }
   if (active && smooth_k) {
     const TR* Om = (const TR*)c.sfin + x.row * SFin<NX>::SIZE;
     recover_smooth<NX, TR>(Om + SFin<NX>::Om, Om + SFin<NX>::om, mf, Pf, Pfl);
@@ -1372,7 +1407,7 @@ __global__ void __launch_bounds__(128) setup_kernel(Ctx c) {
 // ===========================================================================
 template <class Op>
 struct SetupTag {};
-template <int NX, class TR>
+template <int NX, class TR, int PHASE>
 struct RecoverTag {};
 
 // Raises (never lowers) a kernel's dynamic shared-memory limit on the current
@@ -1416,7 +1451,9 @@ int query_shapes_t(int scan_groups, int scan_elems, int window, int recover_thre
   sh->smem_setup = setup_separate ? (size_t)(128 / SetupGeom<NX>::SG) * SetupGeom<NX>::template slot_bytes<T, TS>() : 0;
   if (setup_separate) set_smem_attr<SetupTag<FOp>>((const void*)setup_kernel<NX, T, TS>, sh->smem_setup);
   sh->recover_threads = recover_threads;
-  set_smem_attr<RecoverTag<NX, TR>>((const void*)recover_kernel<NX, TR>, recover_smem_bytes<NX>(recover_threads));
+  set_smem_attr<RecoverTag<NX, TR, 0>>((const void*)recover_kernel<NX, TR, 0>, recover_smem_bytes<NX>(recover_threads));
+  set_smem_attr<RecoverTag<NX, TR, 1>>((const void*)recover_kernel<NX, TR, 1>, recover_smem_bytes<NX>(recover_threads));
+  set_smem_attr<RecoverTag<NX, TR, 2>>((const void*)recover_kernel<NX, TR, 2>, recover_smem_bytes<NX>(recover_threads));
   if (cudaGetLastError() != cudaSuccess) return SRTM_ERR_CUDA;
   return SRTM_OK;
 }
@@ -1441,7 +1478,7 @@ int query_shapes(srtm_precision prec, int scan_groups, int scan_elems, int windo
 // ev (optional): five events recorded after the constants, the filter scan,
 // the interval setup, the smoother scan and the recovery.
 template <int NX, class T, class TS, class TR>
-int launch_t(const Ctx& c, const Shapes& sh, cudaStream_t st, cudaEvent_t* ev) {
+int launch_t(const Ctx& c, const Shapes& sh, cudaStream_t st, cudaEvent_t* ev, const SideStream* side) {
   using FOp = FilterOp<NX, T, TS>;
   using SOp = SmootherOp<NX, T, TR>;
   constexpr int G = FOp::G;
@@ -1458,23 +1495,39 @@ int launch_t(const Ctx& c, const Shapes& sh, cudaStream_t st, cudaEvent_t* ev) {
     setup_kernel<NX, T, TS><<<sh.grid_setup, 128, sh.smem_setup, st>>>(c);
   launch_loglik(c, st);
   if (ev) cudaEventRecord(ev[2], st);  // otherwise the interval setup runs inside the filter scan
+  const unsigned rblocks = (unsigned)((c.total_fast + sh.recover_threads - 1) / sh.recover_threads);
+  const size_t rsmem = recover_smem_bytes<NX>(sh.recover_threads);
+  const bool split = c.smoothing && c.recover_split && side;
+  // split recovery: the smoother scan is issued first, so that its blocks are
+  // placed before the filtered half fills the remaining room
+  if (split) cudaEventRecord(side->fork, st);
   if (c.smoothing && c.sequential)
     seq_smoother_kernel<NX, T, TR><<<seq_blocks, SEQ_THREADS, 0, st>>>(c);
   else if (c.smoothing)
     scan_kernel<SOp><<<sh.grid_s, sh.scan_groups_s * G, sh.smem_s, st>>>(c, sh.scan_groups_s, sh.scan_elems_s, sh.window_s);
+  if (split) {
+    cudaStreamWaitEvent(side->st, side->fork, 0);
+    recover_kernel<NX, TR, 1><<<rblocks, sh.recover_threads, rsmem, side->st>>>(c);
+    cudaEventRecord(side->join, side->st);
+  }
   if (ev) cudaEventRecord(ev[3], st);
-  const long long blocks = (c.total_fast + sh.recover_threads - 1) / sh.recover_threads;
-  recover_kernel<NX, TR><<<(unsigned)blocks, sh.recover_threads, recover_smem_bytes<NX>(sh.recover_threads), st>>>(c);
+  if (split) {
+    cudaStreamWaitEvent(st, side->join, 0);
+    recover_kernel<NX, TR, 2><<<rblocks, sh.recover_threads, rsmem, st>>>(c);
+  } else {
+    recover_kernel<NX, TR, 0><<<rblocks, sh.recover_threads, rsmem, st>>>(c);
+  }
   if (ev) cudaEventRecord(ev[4], st);
   return cudaGetLastError() == cudaSuccess ? SRTM_OK : SRTM_ERR_CUDA;
 }
 
 template <int NX>
-int launch_device_path(const Ctx& c, srtm_precision prec, const Shapes& sh, cudaStream_t st, cudaEvent_t* ev) {
+int launch_device_path(const Ctx& c, srtm_precision prec, const Shapes& sh, cudaStream_t st, cudaEvent_t* ev,
+                       const SideStream* side) {
   switch (prec) {
-    case SRTM_FP64: return launch_t<NX, double, double, double>(c, sh, st, ev);
-    case SRTM_MIXED: return launch_t<NX, float, double, double>(c, sh, st, ev);
-    case SRTM_FP32: return launch_t<NX, float, float, float>(c, sh, st, ev);
+    case SRTM_FP64: return launch_t<NX, double, double, double>(c, sh, st, ev, side);
+    case SRTM_MIXED: return launch_t<NX, float, double, double>(c, sh, st, ev, side);
+    case SRTM_FP32: return launch_t<NX, float, float, float>(c, sh, st, ev, side);
   }
   return SRTM_ERR_ARG;
 }
@@ -1483,5 +1536,5 @@ int launch_device_path(const Ctx& c, srtm_precision prec, const Shapes& sh, cuda
 
 #define SRTM_INSTANTIATE(NXV)                                                                                \
   template int srtm::launch_device_path<NXV>(const srtm::Ctx&, srtm_precision, const srtm::Shapes&,          \
-                                             cudaStream_t, cudaEvent_t*);                                    \
+                                             cudaStream_t, cudaEvent_t*, const srtm::SideStream*);           \
   template int srtm::query_shapes<NXV>(srtm_precision, int, int, int, int, int, int, long long, int, srtm::Shapes*);

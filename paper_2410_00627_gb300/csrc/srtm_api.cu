@@ -45,6 +45,7 @@ struct DevState {
   size_t last_ftile = 0, last_ftile_bytes = 0, last_stile = 0, last_stile_bytes = 0;
   long long last_fstride = 0, last_sstride = 0;
   int last_launches = 0;  // kernel launches of the last call
+  SideStream side = {};   // second stream + fork/join events (split recovery), created on first use
 };
 constexpr int MAXDEV = 64;
 std::mutex g_mu;
@@ -62,12 +63,14 @@ srtm_tuning effective_tuning(int nx, srtm_precision prec) {
   t.recover_threads = 128;
   t.lookback_window = 16;
   t.setup_mode = 1;
+  t.recover_split = 1;
   const srtm_tuning& u = g_tune[nx][prec];
   if (u.scan_groups) t.scan_groups = u.scan_groups;
   if (u.scan_elems) t.scan_elems = u.scan_elems;
   if (u.recover_threads) t.recover_threads = u.recover_threads;
   if (u.lookback_window) t.lookback_window = u.lookback_window;
   if (u.setup_mode) t.setup_mode = u.setup_mode;
+  if (u.recover_split) t.recover_split = u.recover_split;
   return t;
 }
 
@@ -98,13 +101,20 @@ size_t a16(size_t x) { return (x + 15) / 16 * 16; }
 
 struct Layout {
   size_t ctr, ratio, nslow, off_slow, off_fast, tile_f, tile_s, model, ftile, stile, fout, rec, selem, sfin, lterm,
-      uin, total;
+      uin, rscr, total;
   long long ftile_stride, stile_stride;
   ModelLayout ml;
 };
 
+// bytes of the split recovery's per-fast-step moments (RecScr)
+size_t split_scratch_bytes(int nx, srtm_precision prec, long long total_fast) {
+  const size_t sR = prec == SRTM_FP32 ? 4 : 8;
+  return sR * (size_t)(nx + nx * (nx + 1) / 2 + nx * nx) * (size_t)total_fast;
+}
+constexpr size_t SPLIT_SCRATCH_MAX = (size_t)4 << 30;
+
 Layout make_layout(int nx, int ny, int max_ratio, int n_seq, long long total_slow, srtm_precision prec, int tile_f,
-                   int tile_s, int nu) {
+                   int tile_s, int nu, size_t rscr_bytes) {
   Layout L;
   const size_t sT = prec == SRTM_FP64 ? 8 : 4, sR = prec == SRTM_FP32 ? 4 : 8;
   const long long nn = (long long)nx * nx;
@@ -135,6 +145,7 @@ Layout make_layout(int nx, int ny, int max_ratio, int n_seq, long long total_slo
   L.sfin = take(sR * (size_t)SFN * total_slow);
   L.lterm = take(sizeof(double) * (size_t)total_slow);
   L.uin = take(nu > 0 ? sizeof(double) * (size_t)(3 * nx + MY) * total_slow : 0);
+  L.rscr = take(rscr_bytes);
   L.total = a256(o);
   return L;
 }
@@ -197,9 +208,10 @@ int query_shapes_for(int nx, srtm_precision prec, const srtm_tuning& t, int sms,
   return SRTM_ERR_UNSUPPORTED;
 }
 
-int launch_for(int nx, const Ctx& c, srtm_precision prec, const Shapes& sh, cudaStream_t st, cudaEvent_t* ev) {
+int launch_for(int nx, const Ctx& c, srtm_precision prec, const Shapes& sh, cudaStream_t st, cudaEvent_t* ev,
+               const SideStream* side) {
 #define SRTM_L(N) \
-  case N: return launch_device_path<N>(c, prec, sh, st, ev);
+  case N: return launch_device_path<N>(c, prec, sh, st, ev, side);
   switch (nx) {
     SRTM_L(1) SRTM_L(2) SRTM_L(3) SRTM_L(4) SRTM_L(5) SRTM_L(6) SRTM_L(7) SRTM_L(8)
   }
@@ -208,7 +220,10 @@ int launch_for(int nx, const Ctx& c, srtm_precision prec, const Shapes& sh, cuda
 }
 
 // Runs the device path for a fully validated context (sizes in `c` set).
-int run(Ctx c, srtm_precision prec, cudaStream_t st) {
+// host_outputs: some output is pinned host memory written over the CPU-GPU
+// link; the recovery then stays one kernel, so that those slower stores
+// overlap all of its arithmetic instead of only the smoothing half.
+int run(Ctx c, srtm_precision prec, cudaStream_t st, bool host_outputs = false) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAXDEV)
     return fail(SRTM_ERR_CUDA, "no usable CUDA device");
@@ -222,7 +237,21 @@ int run(Ctx c, srtm_precision prec, cudaStream_t st) {
   int rc = shapes_for(c.nx, prec, t, d.sms, c.total_slow, c.n_seq, &sh);
   if (rc) return fail(rc, "launch shape query failed (%d)", rc);
   const int tile_f = sh.scan_groups_f * sh.scan_elems_f, tile_s = sh.scan_groups_s * sh.scan_elems_s;
-  const Layout L = make_layout(c.nx, c.ny, c.max_ratio, c.n_seq, c.total_slow, prec, tile_f, tile_s, c.nu);
+  // split recovery: smoother calls of the scan path whose moments fit the bound
+  const size_t rscr_bytes = split_scratch_bytes(c.nx, prec, c.total_fast);
+  c.recover_split =
+      (t.recover_split == 2 && c.smoothing && !c.sequential && !host_outputs && rscr_bytes <= SPLIT_SCRATCH_MAX) ? 1
+                                                                                                                 : 0;
+  if (c.recover_split && !d.side.st) {
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);  // the filtered half at the lowest priority
+    if (cudaStreamCreateWithPriority(&d.side.st, cudaStreamNonBlocking, lo) != cudaSuccess ||
+        cudaEventCreateWithFlags(&d.side.fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&d.side.join, cudaEventDisableTiming) != cudaSuccess)
+      return fail(SRTM_ERR_CUDA, "second stream creation failed");
+  }
+  const Layout L = make_layout(c.nx, c.ny, c.max_ratio, c.n_seq, c.total_slow, prec, tile_f, tile_s, c.nu,
+                               c.recover_split ? rscr_bytes : 0);
   if (d.ws_bytes < L.total) {
     if (d.ws) {
       cudaDeviceSynchronize();
@@ -270,11 +299,12 @@ int run(Ctx c, srtm_precision prec, cudaStream_t st) {
   c.sfin = w + L.sfin;
   c.lterm = (double*)(w + L.lterm);
   c.uin = c.nu > 0 ? (double*)(w + L.uin) : nullptr;
+  c.rscr = c.recover_split ? (void*)(w + L.rscr) : nullptr;
   c.tile_f = tile_f;
   c.tile_s = tile_s;
   c.setup_separate = t.setup_mode == 2 ? 1 : 0;
   d.last_launches = (c.fold_meta ? 0 : 1) + 3 + (c.smoothing ? 1 : 0) + c.setup_separate + (c.loglik ? 1 : 0) +
-                    (c.nu > 0 ? 1 : 0);
+                    (c.nu > 0 ? 1 : 0) + c.recover_split;
   cudaEvent_t* ev = nullptr;
   if (g_timing) {
     if (!d.ev[0])
@@ -285,7 +315,7 @@ int run(Ctx c, srtm_precision prec, cudaStream_t st) {
   }
   rc = launch_meta(c, st, ev);
   if (rc) return fail(rc, "launch of the metadata kernel failed: %s", cudaGetErrorString(cudaGetLastError()));
-  rc = launch_for(c.nx, c, prec, sh, st, ev ? ev + 2 : nullptr);
+  rc = launch_for(c.nx, c, prec, sh, st, ev ? ev + 2 : nullptr, c.recover_split ? &d.side : nullptr);
   if (rc) return fail(rc, "launch of the constants/scan/recovery kernels failed (scan smem %zu/%zu bytes)", sh.smem_f,
                       sh.smem_s);
   return SRTM_OK;
@@ -330,6 +360,15 @@ int check_controls(int nu, const double* B, const double* u) {
   return SRTM_OK;
 }
 
+// true when some fast or slow output is (mapped pinned) host memory
+bool any_host_output(const srtm_output* out, const srtm_output* extra) {
+  for (const srtm_output* o : {out, extra})
+    if (o)
+      for (const double* q : {o->fast_mean, o->fast_cov, o->slow_mean, o->slow_cov})
+        if (q && !is_device_ptr(q)) return true;
+  return false;
+}
+
 void set_outputs(Ctx& c, const srtm_output* main, const srtm_output* extra) {
   c.fast_mean = main ? main->fast_mean : nullptr;
   c.fast_cov = main ? main->fast_cov : nullptr;
@@ -371,7 +410,7 @@ int single(const srtm_problem* p, srtm_precision prec, const srtm_output* out, c
   c.total_fast = (long long)p->n_slow * p->ratio;
   c.F = p->F; c.Q = p->Q; c.H = p->H; c.R = p->R; c.m0 = p->m0; c.P0 = p->P0; c.y = p->y;
   set_outputs(c, out, extra);
-  return run(c, prec, (cudaStream_t)stream);
+  return run(c, prec, (cudaStream_t)stream, any_host_output(out, extra));
 }
 
 int batch(const srtm_batch* b, srtm_precision prec, const srtm_output* out, const srtm_output* extra, int smoothing,
@@ -407,7 +446,7 @@ int batch(const srtm_batch* b, srtm_precision prec, const srtm_output* out, cons
   c.in_nslow = b->n_slow;
   c.F = b->F; c.Q = b->Q; c.H = b->H; c.R = b->R; c.m0 = b->m0; c.P0 = b->P0; c.y = b->y;
   set_outputs(c, out, extra);
-  return run(c, prec, (cudaStream_t)stream);
+  return run(c, prec, (cudaStream_t)stream, any_host_output(out, extra));
 }
 
 }  // namespace
@@ -613,13 +652,16 @@ int srtm_release(void) {
   int cur = 0;
   cudaGetDevice(&cur);
   for (int d = 0; d < MAXDEV; ++d) {
-    if (!g_dev[d].ws && !g_dev[d].stage && !g_dev[d].hstage) continue;
+    if (!g_dev[d].ws && !g_dev[d].stage && !g_dev[d].hstage && !g_dev[d].side.st) continue;
     cudaSetDevice(d);
     cudaDeviceSynchronize();
     if (g_dev[d].ws) cudaFree(g_dev[d].ws);
     if (g_dev[d].stage) cudaFree(g_dev[d].stage);
     if (g_dev[d].hstage) cudaFreeHost(g_dev[d].hstage);
     if (g_dev[d].hstage_ev) cudaEventDestroy(g_dev[d].hstage_ev);
+    if (g_dev[d].side.st) cudaStreamDestroy(g_dev[d].side.st);
+    if (g_dev[d].side.fork) cudaEventDestroy(g_dev[d].side.fork);
+    if (g_dev[d].side.join) cudaEventDestroy(g_dev[d].side.join);
     for (int i = 0; i <= NSTAGE; ++i)
       if (g_dev[d].ev[i]) cudaEventDestroy(g_dev[d].ev[i]);
     g_dev[d] = DevState();
@@ -640,6 +682,7 @@ int srtm_set_tuning(int nx, srtm_precision prec, const srtm_tuning* t) {
   if (t->lookback_window && (t->lookback_window < 1 || t->lookback_window > 32))
     return fail(SRTM_ERR_ARG, "lookback_window out of range");
   if (t->setup_mode < 0 || t->setup_mode > 2) return fail(SRTM_ERR_ARG, "setup_mode out of range");
+  if (t->recover_split < 0 || t->recover_split > 2) return fail(SRTM_ERR_ARG, "recover_split out of range");
   std::lock_guard<std::mutex> lk(g_mu);
   g_tune[nx][prec] = *t;
   return SRTM_OK;
@@ -667,32 +710,58 @@ int autotune_impl(int nx, srtm_precision prec, int reps, Call call, srtm_tuning*
     saved = g_tune[nx][prec];
   }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+  cudaStream_t cs = nullptr;  // the candidates' graphs are captured and replayed here
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
     if (e0) cudaEventDestroy(e0);
-    return fail(SRTM_ERR_CUDA, "event creation failed");
+    if (e1) cudaEventDestroy(e1);
+    return fail(SRTM_ERR_CUDA, "event or stream creation failed");
+  }
+  bool timing;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    timing = g_timing;
+    g_timing = false;  // no stage events inside the captured candidates
   }
   auto restore = [&](int rc) {
     std::lock_guard<std::mutex> lk(g_mu);
     g_tune[nx][prec] = saved;
     return rc;
   };
+  // A candidate runs once directly on the caller's stream (workspace, shapes,
+  // errors), is then captured into a CUDA graph on a private stream and the
+  // graph replayed `reps` times between events: the score is device time
+  // without host launch cost, as for graph-captured production calls.
   auto score = [&](const srtm_tuning& t, float* ms) -> int {
     {
       std::lock_guard<std::mutex> lk(g_mu);
       g_tune[nx][prec] = t;
     }
-    int rc = call();
+    int rc = call(st);
     if (!rc) rc = srtm_status(st);
+    if (rc) return rc;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed) != cudaSuccess)
+      return fail(SRTM_ERR_CUDA, "stream capture failed to start");
+    rc = call(cs);
+    const cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+    if (!rc && ce != cudaSuccess) rc = fail(SRTM_ERR_CUDA, "stream capture failed: %s", cudaGetErrorString(ce));
+    if (!rc && cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) rc = fail(SRTM_ERR_CUDA, "graph instantiation failed");
     float bestr = 0.f;
     for (int r = 0; r < reps && !rc; ++r) {
-      cudaEventRecord(e0, st);
-      rc = call();
-      cudaEventRecord(e1, st);
-      if (!rc) rc = srtm_status(st);
+      cudaEventRecord(e0, cs);
+      if (cudaGraphLaunch(exec, cs) != cudaSuccess) rc = fail(SRTM_ERR_CUDA, "graph launch failed");
+      cudaEventRecord(e1, cs);
+      const int rs = srtm_status(cs);
+      if (!rc) rc = rs;
       float v = 0.f;
       if (!rc && cudaEventElapsedTime(&v, e0, e1) != cudaSuccess) rc = fail(SRTM_ERR_CUDA, "event timing failed");
       if (!rc && (r == 0 || v < bestr)) bestr = v;
     }
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
     *ms = bestr;
     return rc;
   };
@@ -737,8 +806,19 @@ int autotune_impl(int nx, srtm_precision prec, int reps, Call call, srtm_tuning*
     t.setup_mode = md;
     consider(t);
   }
+  for (int sp = 1; sp <= 2; ++sp) {  // one recovery kernel / filtered half beside the smoother scan
+    if (rc || sp == cur.recover_split) continue;
+    srtm_tuning t = cur;
+    t.recover_split = sp;
+    consider(t);
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  cudaStreamDestroy(cs);
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_timing = timing;
+  }
   if (rc) return restore(rc);
   {
     std::lock_guard<std::mutex> lk(g_mu);
@@ -759,8 +839,9 @@ int srtm_autotune(const srtm_problem* p, srtm_precision prec, const srtm_output*
   int rc = check_dims(p->nx, p->ny);
   if (rc) return rc;
   if (prec < SRTM_FP64 || prec > SRTM_FP32) return fail(SRTM_ERR_ARG, "unknown precision %d", (int)prec);
-  return autotune_impl(p->nx, prec, reps, [&]() { return srtm_smoother(p, prec, smooth, nullptr, stream); }, best,
-                       best_ms, (cudaStream_t)stream);
+  return autotune_impl(
+      p->nx, prec, reps, [&](cudaStream_t s) { return srtm_smoother(p, prec, smooth, nullptr, (srtm_stream_t)s); },
+      best, best_ms, (cudaStream_t)stream);
 }
 
 int srtm_autotune_batch(const srtm_batch* b, srtm_precision prec, const srtm_output* smooth, int reps,
@@ -769,8 +850,10 @@ int srtm_autotune_batch(const srtm_batch* b, srtm_precision prec, const srtm_out
   int rc = check_dims(b->nx, b->ny);
   if (rc) return rc;
   if (prec < SRTM_FP64 || prec > SRTM_FP32) return fail(SRTM_ERR_ARG, "unknown precision %d", (int)prec);
-  return autotune_impl(b->nx, prec, reps, [&]() { return srtm_smoother_batch(b, prec, smooth, nullptr, stream); },
-                       best, best_ms, (cudaStream_t)stream);
+  return autotune_impl(
+      b->nx, prec, reps,
+      [&](cudaStream_t s) { return srtm_smoother_batch(b, prec, smooth, nullptr, (srtm_stream_t)s); }, best, best_ms,
+      (cudaStream_t)stream);
 }
 
 int srtm_launches_per_call(int smoothing, int batched) { return (smoothing ? 4 : 3) + (batched ? 1 : 0); }
@@ -878,7 +961,7 @@ extern "C" int srtm_smoother_noalloc(const srtm_problem* p, srtm_precision prec,
     rc = shapes_for(c.nx, prec, t, d.sms, c.total_slow, c.n_seq, &sh);
     if (rc) return fail(rc, "launch shape query failed (%d)", rc);
     const int tile_f = sh.scan_groups_f * sh.scan_elems_f, tile_s = sh.scan_groups_s * sh.scan_elems_s;
-    L = make_layout(c.nx, c.ny, c.max_ratio, c.n_seq, c.total_slow, prec, tile_f, tile_s, c.nu);
+    L = make_layout(c.nx, c.ny, c.max_ratio, c.n_seq, c.total_slow, prec, tile_f, tile_s, c.nu, 0);
     if (L.total > NOALLOC_SCRATCH_BYTES)
       return fail(SRTM_ERR_ARG, "this problem needs %zu bytes of scratch; the static scratch holds %zu bytes",
                   L.total, NOALLOC_SCRATCH_BYTES);
@@ -911,7 +994,7 @@ extern "C" int srtm_smoother_noalloc(const srtm_problem* p, srtm_precision prec,
     c.setup_separate = t.setup_mode == 2 ? 1 : 0;
     rc = launch_meta(c, st, nullptr);
     if (rc) return fail(rc, "launch of the metadata kernel failed");
-    rc = launch_for(c.nx, c, prec, sh, st, nullptr);
+    rc = launch_for(c.nx, c, prec, sh, st, nullptr, nullptr);
     if (rc) return fail(rc, "launch of the scan/recovery kernels failed");
   }
   // Device-side errors of this call live in the static scratch: wait for the

@@ -173,6 +173,23 @@ struct Ctx {
   int tile_f, tile_s;    // elements per scan tile
   int setup_separate;    // 1: the interval setup runs as its own kernel after the filter scan
   int sequential;        // 1: the slow-rate recursions run sequentially (one thread per sequence)
+  int recover_split;     // 1: filtered half of the recovery concurrent with the smoother scan
+  void* rscr;            // [total_fast][RecScr::SIZE] filtered moments between the two halves (recovery type)
+};
+
+// Filtered moments of one fast step kept between the two halves of a split
+// recovery: m^f_i, P^f_ii (upper triangle), P^f_il.
+template <int NX>
+struct RecScr {
+  static constexpr int NT = NX * (NX + 1) / 2;
+  static constexpr int mf = 0, Pf = NX, Pfl = NX + NT, SIZE = NX + NT + NX * NX;
+};
+
+// The library's second stream of the current GPU and the two events that fork
+// work onto it and join it back (split recovery).
+struct SideStream {
+  cudaStream_t st;
+  cudaEvent_t fork, join;
 };
 
 // ---------------------------------------------------------------------------
@@ -228,7 +245,8 @@ struct Shapes {  // resolved launch shapes for one call
 };
 
 template <int NX>
-int launch_device_path(const Ctx& c, srtm_precision prec, const Shapes& sh, cudaStream_t st, cudaEvent_t* ev);
+int launch_device_path(const Ctx& c, srtm_precision prec, const Shapes& sh, cudaStream_t st, cudaEvent_t* ev,
+                       const SideStream* side);
 
 // sums the per-interval terms into the caller's log-likelihood output (meta.cu)
 int launch_loglik(const Ctx& c, cudaStream_t st);

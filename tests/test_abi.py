@@ -38,7 +38,7 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(api.Problem) == 16 + 7 * 8 + 8 + 2 * 8   # + nu (padded), B, u
     assert ctypes.sizeof(api.Output) == 5 * 8
     assert ctypes.sizeof(api.Batch) == 16 + 16 + 9 * 8 + 8 + 2 * 8
-    assert ctypes.sizeof(api.Tuning) == 20
+    assert ctypes.sizeof(api.Tuning) == 24
 
 
 def test_rejects_bad_arguments_without_gpu(lib):
@@ -70,6 +70,7 @@ def test_tuning_validation_and_roundtrip(lib):
     assert lib.srtm_set_tuning(4, 1, ctypes.byref(api.Tuning(0, 0, 0, 33))) == -1  # window above 32
     assert lib.srtm_set_tuning(4, 1, ctypes.byref(api.Tuning(0, 0, 0, -1))) == -1
     assert lib.srtm_set_tuning(4, 1, ctypes.byref(api.Tuning(0, 0, 0, 0, 3))) == -1   # setup_mode
+    assert lib.srtm_set_tuning(4, 1, ctypes.byref(api.Tuning(0, 0, 0, 0, 0, 3))) == -1  # recover_split
     assert lib.srtm_set_tuning(4, 1, ctypes.byref(api.Tuning(4, 8, 64, 8))) == 0
     assert lib.srtm_get_tuning(4, 1, ctypes.byref(t)) == 0
     assert (t.scan_groups, t.scan_elems, t.recover_threads, t.lookback_window) == (4, 8, 64, 8)

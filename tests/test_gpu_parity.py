@@ -236,15 +236,15 @@ def test_stage_timing_reports_every_stage():
     assert all(v > 0 for v in t.values())
 
 
-SHAPES = [  # (scan_groups, scan_elems, recover_threads, lookback_window, setup_mode), nx=4 (16 lanes per group)
-    (2, 1, 32, 1, 1),      # smallest tiles, serial look-back
-    (16, 32, 128, 32, 2),  # largest tiles and window, setup as its own kernel
-    (8, 4, 64, 4, 2),
-    (4, 2, 96, 2, 1),
+SHAPES = [  # (scan_groups, scan_elems, recover_threads, lookback_window, setup_mode, recover_split), nx=4
+    (2, 1, 32, 1, 1, 1),      # smallest tiles, serial look-back
+    (16, 32, 128, 32, 2, 2),  # largest tiles and window, setup as its own kernel, split recovery
+    (8, 4, 64, 4, 2, 1),
+    (4, 2, 96, 2, 1, 2),
 ]
 
 
-@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "g{}e{}t{}w{}s{}".format(*s))
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "g{}e{}t{}w{}s{}r{}".format(*s))
 def test_launch_shapes_do_not_change_results(oracle_mod, shape):
     from paper_2410_00627_gb300 import api
     prob = synth.config2(seed=5, n_slow=613, keep_states=False)
@@ -433,3 +433,40 @@ def test_outputs_at_8_byte_offsets():
     api.status()
     for k in shapes:
         assert torch.equal(got[k], want[k]), k
+
+
+def test_split_recovery_is_bitwise_identical_to_one_kernel():
+    """The two halves of a split recovery do the one-kernel arithmetic in the
+    same order: smoothed, filtered extras and log likelihood are identical;
+    the call makes one more launch.  Also for a ragged batch."""
+    import torch
+
+    from paper_2410_00627_gb300 import api
+    prob = synth.random_model(25, 4, 2, 6, 300, nu=2)
+    args = [to_dev(getattr(prob, k)) for k in ("F", "Q", "H", "R", "m0", "P0", "y")]
+    ctl = {"B": to_dev(prob.B), "u": to_dev(prob.u)}
+    probs = synth.config4(seed=14, n_seq=12, n_min=1, n_max=80)
+    pk = synth.pack(probs)
+    t = lambda a: torch.as_tensor(a, device="cuda")  # noqa: E731
+    b = api.make_batch(t(pk["F"]), t(pk["Q"]), t(pk["H"]), t(pk["R"]), t(pk["m0"]), t(pk["P0"]), t(pk["y"]),
+                       t(pk["ratio"]), t(pk["n_slow"]), pk["max_ratio"], pk["total_slow"], pk["total_fast"])
+    try:
+        for precision in ("fp64", "mixed", "fp32"):
+            res, launches = {}, {}
+            for split in (1, 2):
+                api.set_tuning(4, precision, recover_split=split)
+                sm, fi = api.smoother(*args, prob.ratio, precision=precision, outputs=api.ALL_OUTPUTS,
+                                      filtered=api.OUTPUT_KEYS, **ctl)
+                api.status()
+                launches[split] = api.last_call_launches()
+                bs, _ = api.smoother_batch(b, precision=precision)
+                api.status()
+                res[split] = ({k: v.cpu() for k, v in sm.items()}, {k: v.cpu() for k, v in fi.items()},
+                              {k: v.cpu() for k, v in bs.items()})
+            assert launches[2] == launches[1] + 1
+            for part in range(3):
+                for k in res[1][part]:
+                    assert torch.equal(res[1][part][k], res[2][part][k]), (precision, part, k)
+    finally:
+        for p in ("fp64", "mixed", "fp32"):
+            api.set_tuning(4, p)
