@@ -258,8 +258,8 @@ int srtm_last_call_launches(void);
  * call of the current GPU and writes up to n durations in milliseconds, in
  * launch order: metadata, model constants, filter scan, interval setup,
  * smoother scan (0 for a filter call), fast-rate recovery (with a split
- * recovery: its smoothing half; the filtered half runs beside the smoother
- * scan on the second stream and is in no stage).                            */
+ * recovery: its smoothing half), then the filtered half of a split recovery
+ * (run beside the smoother scan on the second stream; 0 without a split).   */
 int srtm_set_stage_timing(int enable);
 int srtm_stage_times(float *ms, int n);
 

@@ -27,7 +27,8 @@ SYMBOLS = ("srtm_filter", "srtm_smoother", "srtm_filter_batch", "srtm_smoother_b
            "srtm_last_call_launches", "srtm_filter_sequential", "srtm_smoother_sequential",
            "srtm_filter_batch_sequential", "srtm_smoother_batch_sequential", "srtm_selftest_wait")
 METHODS = {"scan": "", "sequential": "_sequential"}  # entry-point suffix per method
-STAGES = ("metadata", "constants", "filter_scan", "interval_setup", "smoother_scan", "recovery")
+STAGES = ("metadata", "constants", "filter_scan", "interval_setup", "smoother_scan", "recovery",
+          "recovery_filtered_half")
 
 
 class Problem(ctypes.Structure):

@@ -1476,7 +1476,9 @@ int query_shapes(srtm_precision prec, int scan_groups, int scan_elems, int windo
 }
 
 // ev (optional): five events recorded after the constants, the filter scan,
-// the interval setup, the smoother scan and the recovery.
+// the interval setup, the smoother scan and the recovery; with a split
+// recovery also ev[5] before its smoothing half and ev[6], ev[7] around its
+// filtered half (second stream).
 template <int NX, class T, class TS, class TR>
 int launch_t(const Ctx& c, const Shapes& sh, cudaStream_t st, cudaEvent_t* ev, const SideStream* side) {
   using FOp = FilterOp<NX, T, TS>;
@@ -1507,12 +1509,15 @@ int launch_t(const Ctx& c, const Shapes& sh, cudaStream_t st, cudaEvent_t* ev, c
     scan_kernel<SOp><<<sh.grid_s, sh.scan_groups_s * G, sh.smem_s, st>>>(c, sh.scan_groups_s, sh.scan_elems_s, sh.window_s);
   if (split) {
     cudaStreamWaitEvent(side->st, side->fork, 0);
+    if (ev) cudaEventRecord(ev[6], side->st);
     recover_kernel<NX, TR, 1><<<rblocks, sh.recover_threads, rsmem, side->st>>>(c);
+    if (ev) cudaEventRecord(ev[7], side->st);
     cudaEventRecord(side->join, side->st);
   }
   if (ev) cudaEventRecord(ev[3], st);
   if (split) {
     cudaStreamWaitEvent(st, side->join, 0);
+    if (ev) cudaEventRecord(ev[5], st);
     recover_kernel<NX, TR, 2><<<rblocks, sh.recover_threads, rsmem, st>>>(c);
   } else {
     recover_kernel<NX, TR, 0><<<rblocks, sh.recover_threads, rsmem, st>>>(c);

@@ -29,6 +29,10 @@ int fail(int code, const char* fmt, ...) {
 }
 
 constexpr int NSTAGE = 6;  // metadata, constants, filter scan, interval setup, smoother scan, recovery
+// stage-timing events: 0..NSTAGE bound the stages in launch order; with a
+// split recovery NSTAGE+1 marks the start of its smoothing half (main stream)
+// and NSTAGE+2, NSTAGE+3 bound its filtered half (second stream)
+constexpr int NEVENT = NSTAGE + 4;
 struct DevState {
   void* ws = nullptr;
   size_t ws_bytes = 0;
@@ -38,7 +42,8 @@ struct DevState {
   size_t hstage_bytes = 0;
   cudaEvent_t hstage_ev = nullptr;   // recorded after the copy out of hstage
   int sms = 0;
-  cudaEvent_t ev[NSTAGE + 1] = {};  // stage-timing events (created on first use)
+  cudaEvent_t ev[NEVENT] = {};  // stage-timing events (created on first use)
+  bool ev_split = false;        // the timed call split its recovery
   cudaStream_t ev_stream = nullptr;
   bool ev_valid = false;
   // placement of the scan tile-state regions used by the previous call
@@ -308,8 +313,9 @@ int run(Ctx c, srtm_precision prec, cudaStream_t st, bool host_outputs = false) 
   cudaEvent_t* ev = nullptr;
   if (g_timing) {
     if (!d.ev[0])
-      for (int i = 0; i <= NSTAGE; ++i) cudaEventCreate(&d.ev[i]);
+      for (int i = 0; i < NEVENT; ++i) cudaEventCreate(&d.ev[i]);
     ev = d.ev;
+    d.ev_split = c.recover_split != 0;
     d.ev_stream = st;
     d.ev_valid = true;
   }
@@ -662,7 +668,7 @@ int srtm_release(void) {
     if (g_dev[d].side.st) cudaStreamDestroy(g_dev[d].side.st);
     if (g_dev[d].side.fork) cudaEventDestroy(g_dev[d].side.fork);
     if (g_dev[d].side.join) cudaEventDestroy(g_dev[d].side.join);
-    for (int i = 0; i <= NSTAGE; ++i)
+    for (int i = 0; i < NEVENT; ++i)
       if (g_dev[d].ev[i]) cudaEventDestroy(g_dev[d].ev[i]);
     g_dev[d] = DevState();
   }
@@ -879,8 +885,16 @@ int srtm_stage_times(float* ms, int n) {
   DevState& d = g_dev[dev];
   if (!d.ev_valid) return fail(SRTM_ERR_ARG, "no call was timed on this device (srtm_set_stage_timing(1) first)");
   if (cudaEventSynchronize(d.ev[NSTAGE]) != cudaSuccess) return fail(SRTM_ERR_CUDA, "event synchronize failed");
-  for (int i = 0; i < n && i < NSTAGE; ++i)
-    if (cudaEventElapsedTime(&ms[i], d.ev[i], d.ev[i + 1]) != cudaSuccess) return fail(SRTM_ERR_CUDA, "event timing failed");
+  for (int i = 0; i < n && i < NSTAGE + 1; ++i) {
+    cudaEvent_t a = d.ev[i], b = d.ev[i + 1];
+    if (i == NSTAGE - 1 && d.ev_split) a = d.ev[NSTAGE + 1];  // smoothing half only
+    if (i == NSTAGE) {  // filtered half of a split recovery
+      if (!d.ev_split) { ms[i] = 0.f; continue; }
+      a = d.ev[NSTAGE + 2];
+      b = d.ev[NSTAGE + 3];
+    }
+    if (cudaEventElapsedTime(&ms[i], a, b) != cudaSuccess) return fail(SRTM_ERR_CUDA, "event timing failed");
+  }
   return SRTM_OK;
 }
 

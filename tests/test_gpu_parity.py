@@ -227,13 +227,20 @@ def test_stage_timing_reports_every_stage():
     from paper_2410_00627_gb300 import api
     prob = synth.config2(seed=9, n_slow=500, keep_states=False)
     api.set_stage_timing(True)
+    times = {}
     try:
-        run_smoother(prob, "fp64", filtered=False)
-        t = api.stage_times()
+        for split in (1, 2):
+            api.set_tuning(4, "fp64", recover_split=split)
+            run_smoother(prob, "fp64", filtered=False)
+            times[split] = api.stage_times()
     finally:
         api.set_stage_timing(False)
-    assert set(t) == set(api.STAGES)
-    assert all(v > 0 for v in t.values())
+        api.set_tuning(4, "fp64")
+    for split, t in times.items():
+        assert set(t) == set(api.STAGES)
+        assert all(v > 0 for k, v in t.items() if k != "recovery_filtered_half"), (split, t)
+    assert times[1]["recovery_filtered_half"] == 0.0
+    assert times[2]["recovery_filtered_half"] > 0.0
 
 
 SHAPES = [  # (scan_groups, scan_elems, recover_threads, lookback_window, setup_mode, recover_split), nx=4
