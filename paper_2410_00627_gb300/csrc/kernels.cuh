@@ -1283,15 +1283,16 @@ __global__ void __launch_bounds__(128, 3) recover_kernel(Ctx c) {
     smooth_k = c.smoothing && (x.k < x.N - 1);
     if (PHASE < 2) {
       recover_filtered<NX, TR>(c, x, smooth_k, mf, Pf, Pfl);
-    } else {
-      const TR* src = (const TR*)c.rscr + f * RS::SIZE;
+    } else {  // component-major: a warp reads 32 consecutive words per component
+      const TR* src = (const TR*)c.rscr + f;
+      const long long T = c.total_fast;
 #pragma unroll
-      for (int r = 0; r < NX; ++r) mf[r] = src[RS::mf + r];
+      for (int r = 0; r < NX; ++r) mf[r] = src[(RS::mf + r) * T];
 #pragma unroll
-      for (int u = 0; u < NT; ++u) Pf[u] = src[RS::Pf + u];
+      for (int u = 0; u < NT; ++u) Pf[u] = src[(RS::Pf + u) * T];
       if (smooth_k)
 #pragma unroll
-        for (int e = 0; e < NN; ++e) Pfl[e / NX][e % NX] = src[RS::Pfl + e];
+        for (int e = 0; e < NN; ++e) Pfl[e / NX][e % NX] = src[(RS::Pfl + e) * T];
     }
   }
   // filtered outputs (the call's outputs for a filter, the optional extras for a smoother)
@@ -1305,15 +1306,16 @@ __global__ void __launch_bounds__(128, 3) recover_kernel(Ctx c) {
     if (active && last_i) store_slow<NX, TR>(x.row, c.fslow_mean, c.fslow_cov, mf, Pf);
   }
   if (PHASE == 1) {
-    if (active) {
-      TR* dst = (TR*)c.rscr + f * RS::SIZE;
+    if (active) {  // component-major, as read back
+      TR* dst = (TR*)c.rscr + f;
+      const long long T = c.total_fast;
 #pragma unroll
-      for (int r = 0; r < NX; ++r) dst[RS::mf + r] = mf[r];
+      for (int r = 0; r < NX; ++r) dst[(RS::mf + r) * T] = mf[r];
 #pragma unroll
-      for (int u = 0; u < NT; ++u) dst[RS::Pf + u] = Pf[u];
+      for (int u = 0; u < NT; ++u) dst[(RS::Pf + u) * T] = Pf[u];
       if (smooth_k)
 #pragma unroll
-        for (int e = 0; e < NN; ++e) dst[RS::Pfl + e] = Pfl[e / NX][e % NX];
+        for (int e = 0; e < NN; ++e) dst[(RS::Pfl + e) * T] = Pfl[e / NX][e % NX];
     }
     return;
   }

@@ -174,11 +174,12 @@ struct Ctx {
   int setup_separate;    // 1: the interval setup runs as its own kernel after the filter scan
   int sequential;        // 1: the slow-rate recursions run sequentially (one thread per sequence)
   int recover_split;     // 1: filtered half of the recovery concurrent with the smoother scan
-  void* rscr;            // [total_fast][RecScr::SIZE] filtered moments between the two halves (recovery type)
+  void* rscr;            // [RecScr::SIZE][total_fast] filtered moments between the two halves (recovery type)
 };
 
 // Filtered moments of one fast step kept between the two halves of a split
-// recovery: m^f_i, P^f_ii (upper triangle), P^f_il.
+// recovery: m^f_i, P^f_ii (upper triangle), P^f_il; stored component-major
+// (component c of fast step f at c * total_fast + f).
 template <int NX>
 struct RecScr {
   static constexpr int NT = NX * (NX + 1) / 2;
