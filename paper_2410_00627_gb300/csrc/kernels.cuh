@@ -1027,12 +1027,14 @@ __device__ __forceinline__ FastIdx fast_index(const Ctx& c, long long f) {
 
 // filtered moments of fast step x: m^f_i, P^f_ii (upper triangle) and, when
 // need_pfl, P^f_il
-template <int NX, class TR>
+// M = ny (compile-time): every loop over the measurement dimension runs
+// exactly M times (the records keep their MY-padded strides).
+template <int NX, int M, class TR>
 __device__ __forceinline__ void recover_filtered(const Ctx& c, const FastIdx& x, bool need_pfl, TR (&mf)[NX],
                                                  TR (&Pf)[NX * (NX + 1) / 2], TR (&Pfl)[NX][NX]) {
-  constexpr int NN = NX * NX;
+  constexpr int NN = NX * NX, m = M;
   using RL = Rec<NX>;
-  const int m = c.ny, i = x.i;
+  const int i = x.i;
   const double* md = c.model + (long long)x.s * c.ml.stride;
   const TR* rc = (const TR*)c.rec + x.row * RL::SIZE;
   const double* Ai = md + c.ml.Apow + (long long)i * NN;
@@ -1045,17 +1047,14 @@ __device__ __forceinline__ void recover_filtered(const Ctx& c, const FastIdx& x,
 #pragma unroll
     for (int q = 0; q < NX; ++q) a[r][q] = (TR)__ldg(Ai + r * NX + q);
   // U_i = A^i X + V_i H^T
-  TR U[NX][MY];
+  TR U[NX][M];
 #pragma unroll
   for (int r = 0; r < NX; ++r)
 #pragma unroll
-    for (int jj = 0; jj < MY; ++jj) {
-      TR v = TR(0);
-      if (jj < m) {
-        v = (TR)__ldg(VHi + r * m + jj);
+    for (int jj = 0; jj < M; ++jj) {
+      TR v = (TR)__ldg(VHi + r * m + jj);
 #pragma unroll
-        for (int q = 0; q < NX; ++q) v = fma(a[r][q], rc[RL::X + q * MY + jj], v);
-      }
+      for (int q = 0; q < NX; ++q) v = fma(a[r][q], rc[RL::X + q * MY + jj], v);
       U[r][jj] = v;
     }
   // m^f_i = A^i m + U_i kap (+ b_{k,i} = sum_{q<i} A^{i-1-q} B u_{k,q} with inputs)
@@ -1065,8 +1064,7 @@ __device__ __forceinline__ void recover_filtered(const Ctx& c, const FastIdx& x,
 #pragma unroll
     for (int q = 0; q < NX; ++q) v = fma(a[r][q], rc[RL::mv + q], v);
 #pragma unroll
-    for (int jj = 0; jj < MY; ++jj)
-      if (jj < m) v = fma(U[r][jj], rc[RL::kap + jj], v);
+    for (int jj = 0; jj < M; ++jj) v = fma(U[r][jj], rc[RL::kap + jj], v);
     mf[r] = v;
   }
   if (c.nu > 0) {
@@ -1091,24 +1089,20 @@ __device__ __forceinline__ void recover_filtered(const Ctx& c, const FastIdx& x,
 #pragma unroll
         for (int t = 0; t < NX; ++t) v = fma(a[r][t], rc[RL::Pl + t * NX + q], v);
 #pragma unroll
-        for (int jj = 0; jj < MY; ++jj)
-          if (jj < m) v = fma(-U[r][jj], rc[RL::SUl + jj * NX + q], v);
+        for (int jj = 0; jj < M; ++jj) v = fma(-U[r][jj], rc[RL::SUl + jj * NX + q], v);
         Pfl[r][q] = v;
       }
   }
   // P^f_ii (upper triangle)
   {
-    TR US[NX][MY], AP[NX][NX];
+    TR US[NX][M], AP[NX][NX];
 #pragma unroll
     for (int r = 0; r < NX; ++r)
 #pragma unroll
-      for (int jj = 0; jj < MY; ++jj) {
+      for (int jj = 0; jj < M; ++jj) {
         TR v = TR(0);
-        if (jj < m) {
 #pragma unroll
-          for (int j2 = 0; j2 < MY; ++j2)
-            if (j2 < m) v = fma(U[r][j2], rc[RL::Si + j2 * MY + jj], v);
-        }
+        for (int j2 = 0; j2 < M; ++j2) v = fma(U[r][j2], rc[RL::Si + j2 * MY + jj], v);
         US[r][jj] = v;
       }
 #pragma unroll
@@ -1129,8 +1123,7 @@ __device__ __forceinline__ void recover_filtered(const Ctx& c, const FastIdx& x,
 #pragma unroll
         for (int t = 0; t < NX; ++t) v = fma(AP[r][t], a[q][t], v);
 #pragma unroll
-        for (int jj = 0; jj < MY; ++jj)
-          if (jj < m) v = fma(-US[r][jj], U[q][jj], v);
+        for (int jj = 0; jj < M; ++jj) v = fma(-US[r][jj], U[q][jj], v);
         Pf[u++] = v;
       }
   }
@@ -1260,7 +1253,7 @@ __host__ __device__ inline size_t recover_smem_bytes(int threads) {
 // smoother scan: it reads them back, applies the smoothing terms and writes
 // the smoothed outputs.  The arithmetic and its order are those of PHASE 0,
 // so the results are identical.
-template <int NX, class TR, int PHASE>
+template <int NX, int M, class TR, int PHASE>
 __global__ void __launch_bounds__(128, 3) recover_kernel(Ctx c) {
   constexpr int NT = NX * (NX + 1) / 2, NN = NX * NX;
   using RS = RecScr<NX>;
@@ -1282,7 +1275,7 @@ __global__ void __launch_bounds__(128, 3) recover_kernel(Ctx c) {
     last_i = x.i == x.l;
     smooth_k = c.smoothing && (x.k < x.N - 1);
     if (PHASE < 2) {
-      recover_filtered<NX, TR>(c, x, smooth_k, mf, Pf, Pfl);
+      recover_filtered<NX, M, TR>(c, x, smooth_k, mf, Pf, Pfl);
     } else {  // component-major: a warp reads 32 consecutive words per component
       const TR* src = (const TR*)c.rscr + f;
       const long long T = c.total_fast;
@@ -1409,7 +1402,7 @@ __global__ void __launch_bounds__(128) setup_kernel(Ctx c) {
 // ===========================================================================
 template <class Op>
 struct SetupTag {};
-template <int NX, class TR, int PHASE>
+template <int NX, int M, class TR, int PHASE>
 struct RecoverTag {};
 
 // Raises (never lowers) a kernel's dynamic shared-memory limit on the current
@@ -1422,6 +1415,32 @@ inline void set_smem_attr(const void* fn, size_t bytes) {
   if (bytes > 48 * 1024 && (dev < 0 || dev >= 64 || bytes > granted[dev])) {
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (dev >= 0 && dev < 64) granted[dev] = bytes;
+  }
+}
+
+// The recovery is compiled per measurement size (M = ny = 1..4); the
+// smoothing half of a split recovery does not depend on it (one variant).
+template <int NX, class TR, int PHASE>
+inline void set_recover_smem(size_t bytes) {
+  set_smem_attr<RecoverTag<NX, 1, TR, PHASE>>((const void*)recover_kernel<NX, 1, TR, PHASE>, bytes);
+  if constexpr (PHASE != 2) {
+    set_smem_attr<RecoverTag<NX, 2, TR, PHASE>>((const void*)recover_kernel<NX, 2, TR, PHASE>, bytes);
+    set_smem_attr<RecoverTag<NX, 3, TR, PHASE>>((const void*)recover_kernel<NX, 3, TR, PHASE>, bytes);
+    set_smem_attr<RecoverTag<NX, 4, TR, PHASE>>((const void*)recover_kernel<NX, 4, TR, PHASE>, bytes);
+  }
+}
+
+template <int NX, class TR, int PHASE>
+inline void launch_recover(const Ctx& c, unsigned blocks, int threads, size_t smem, cudaStream_t st) {
+  if constexpr (PHASE == 2) {
+    recover_kernel<NX, 1, TR, PHASE><<<blocks, threads, smem, st>>>(c);
+  } else {
+    switch (c.ny) {
+      case 1: recover_kernel<NX, 1, TR, PHASE><<<blocks, threads, smem, st>>>(c); break;
+      case 2: recover_kernel<NX, 2, TR, PHASE><<<blocks, threads, smem, st>>>(c); break;
+      case 3: recover_kernel<NX, 3, TR, PHASE><<<blocks, threads, smem, st>>>(c); break;
+      default: recover_kernel<NX, 4, TR, PHASE><<<blocks, threads, smem, st>>>(c); break;
+    }
   }
 }
 
@@ -1453,9 +1472,9 @@ int query_shapes_t(int scan_groups, int scan_elems, int window, int recover_thre
   sh->smem_setup = setup_separate ? (size_t)(128 / SetupGeom<NX>::SG) * SetupGeom<NX>::template slot_bytes<T, TS>() : 0;
   if (setup_separate) set_smem_attr<SetupTag<FOp>>((const void*)setup_kernel<NX, T, TS>, sh->smem_setup);
   sh->recover_threads = recover_threads;
-  set_smem_attr<RecoverTag<NX, TR, 0>>((const void*)recover_kernel<NX, TR, 0>, recover_smem_bytes<NX>(recover_threads));
-  set_smem_attr<RecoverTag<NX, TR, 1>>((const void*)recover_kernel<NX, TR, 1>, recover_smem_bytes<NX>(recover_threads));
-  set_smem_attr<RecoverTag<NX, TR, 2>>((const void*)recover_kernel<NX, TR, 2>, recover_smem_bytes<NX>(recover_threads));
+  set_recover_smem<NX, TR, 0>(recover_smem_bytes<NX>(recover_threads));
+  set_recover_smem<NX, TR, 1>(recover_smem_bytes<NX>(recover_threads));
+  set_recover_smem<NX, TR, 2>(recover_smem_bytes<NX>(recover_threads));
   if (cudaGetLastError() != cudaSuccess) return SRTM_ERR_CUDA;
   return SRTM_OK;
 }
@@ -1512,7 +1531,7 @@ int launch_t(const Ctx& c, const Shapes& sh, cudaStream_t st, cudaEvent_t* ev, c
   if (split) {
     cudaStreamWaitEvent(side->st, side->fork, 0);
     if (ev) cudaEventRecord(ev[6], side->st);
-    recover_kernel<NX, TR, 1><<<rblocks, sh.recover_threads, rsmem, side->st>>>(c);
+    launch_recover<NX, TR, 1>(c, rblocks, sh.recover_threads, rsmem, side->st);
     if (ev) cudaEventRecord(ev[7], side->st);
     cudaEventRecord(side->join, side->st);
   }
@@ -1520,9 +1539,9 @@ int launch_t(const Ctx& c, const Shapes& sh, cudaStream_t st, cudaEvent_t* ev, c
   if (split) {
     cudaStreamWaitEvent(st, side->join, 0);
     if (ev) cudaEventRecord(ev[5], st);
-    recover_kernel<NX, TR, 2><<<rblocks, sh.recover_threads, rsmem, st>>>(c);
+    launch_recover<NX, TR, 2>(c, rblocks, sh.recover_threads, rsmem, st);
   } else {
-    recover_kernel<NX, TR, 0><<<rblocks, sh.recover_threads, rsmem, st>>>(c);
+    launch_recover<NX, TR, 0>(c, rblocks, sh.recover_threads, rsmem, st);
   }
   if (ev) cudaEventRecord(ev[4], st);
   return cudaGetLastError() == cudaSuccess ? SRTM_OK : SRTM_ERR_CUDA;
