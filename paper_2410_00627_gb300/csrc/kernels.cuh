@@ -54,7 +54,7 @@ struct SetupGeom {
 // the model's A, Qc_1, Cov(e_1,e_l), V_1 H^T (cA, cQc, cQl, cVH; row-major,
 // V_1 H^T with row stride m).  Work arrays: U1 (NX x MY), P1l, P11, Aml and
 // AP1 (NX x NX, A P1l^T; may alias U1 when that holds NX x NX entries).
-template <int NX, class TE, class TC, class T>
+template <int NX, int M, class TE, class TC, class T>
 __device__ __forceinline__ void setup_elements(int r, bool row, unsigned mask, int m, bool last, const TE* P,
                                                const TE* Pl, const TE* X, const TE* SUl, const TE* Z, const TE* ml,
                                                const TE* mv, const TC* cA, const TC* cQc, const TC* cQl,
@@ -62,10 +62,12 @@ __device__ __forceinline__ void setup_elements(int r, bool row, unsigned mask, i
                                                TE* P1l, TE* P11, TE* Aml, TE* AP1, T* se, const double* b1,
                                                const double* bnx) {
   using SLy = SL<NX>;
+  constexpr int MM = M > 0 ? M : MY;  // loop bound over the measurement dimension
+  if constexpr (M > 0) m = M;
   TE U1r[MY], m1 = TE(0);
   if (row) {
 #pragma unroll
-    for (int j = 0; j < MY; ++j) {
+    for (int j = 0; j < MM; ++j) {
       TE v = TE(0);
       if (j < m) {
         v = (TE)cVH[r * m + j];
@@ -78,7 +80,7 @@ __device__ __forceinline__ void setup_elements(int r, bool row, unsigned mask, i
 #pragma unroll
     for (int q = 0; q < NX; ++q) m1 = fma((TE)cA[r * NX + q], mv[q], m1);
 #pragma unroll
-    for (int j = 0; j < MY; ++j)
+    for (int j = 0; j < MM; ++j)
       if (j < m) m1 = fma(U1r[j], kap[j], m1);
     TE aml = TE(0);
 #pragma unroll
@@ -93,10 +95,10 @@ __device__ __forceinline__ void setup_elements(int r, bool row, unsigned mask, i
   if (row) {
     TE US[MY], APr[NX];
 #pragma unroll
-    for (int j = 0; j < MY; ++j) {
+    for (int j = 0; j < MM; ++j) {
       TE v = TE(0);
 #pragma unroll
-      for (int jj = 0; jj < MY; ++jj)
+      for (int jj = 0; jj < MM; ++jj)
         if (jj < m && j < m) v = fma(U1r[jj], Si[jj][j], v);
       US[j] = v;
     }
@@ -114,7 +116,7 @@ __device__ __forceinline__ void setup_elements(int r, bool row, unsigned mask, i
 #pragma unroll
         for (int t = 0; t < NX; ++t) v = fma(APr[t], (TE)cA[q * NX + t], v);
 #pragma unroll
-        for (int j = 0; j < MY; ++j)
+        for (int j = 0; j < MM; ++j)
           if (j < m) v = fma(-US[j], U1[q * MY + j], v);
         P11[r * NX + q] = v;
         P11[q * NX + r] = v;
@@ -123,7 +125,7 @@ __device__ __forceinline__ void setup_elements(int r, bool row, unsigned mask, i
 #pragma unroll
       for (int t = 0; t < NX; ++t) w = fma((TE)cA[r * NX + t], Pl[t * NX + q], w);
 #pragma unroll
-      for (int j = 0; j < MY; ++j)
+      for (int j = 0; j < MM; ++j)
         if (j < m) w = fma(-U1r[j], SUl[j * NX + q], w);
       P1l[r * NX + q] = w;
     }
@@ -180,16 +182,19 @@ __device__ __forceinline__ void setup_elements(int r, bool row, unsigned mask, i
 // prev (optional): p(x_{k-1,l}|y_{1:k-1}) as (m, P) when it is not yet in
 // the filter results (the first interval of a scan tile reads it from the
 // tile's exclusive prefix).
-template <int NX, class T, class TR>
+// M = ny when known at compile time (the setup kernel), 0 = read from c.ny
+// (inside the filter scan); loops over the measurement dimension run M times.
+template <int NX, int M, class T, class TR>
 __device__ void setup_interval(const Ctx& c, long long gi, int lane, unsigned mask, TR* sb, T* sf, const TR* prev) {
   using Gm = SetupGeom<NX>;
+  constexpr int MM = M > 0 ? M : MY;
   constexpr int NN = NX * NX;
   using RL = Rec<NX>;
   const int r = lane;
   const bool row = r < NX;
   const int s = find_segment(c.meta.off_slow, c.n_seq, gi);
   const long long k = gi - c.meta.off_slow[s];
-  const int N = c.meta.nslow[s], l = c.meta.ratio[s], m = c.ny;
+  const int N = c.meta.nslow[s], l = c.meta.ratio[s], m = M > 0 ? M : c.ny;
   const double* md = c.model + (long long)s * c.ml.stride;
   const double* Apow = md + c.ml.Apow;
   const double* Al = Apow + (long long)l * NN;
@@ -214,7 +219,7 @@ __device__ void setup_interval(const Ctx& c, long long gi, int lane, unsigned ma
   // X = P C_bar^T (row r; columns >= m are zero)
   if (row) {
 #pragma unroll
-    for (int j = 0; j < MY; ++j) {
+    for (int j = 0; j < MM; ++j) {
       TR v = TR(0);
       if (j < m) {
 #pragma unroll
@@ -226,8 +231,8 @@ __device__ void setup_interval(const Ctx& c, long long gi, int lane, unsigned ma
   __syncwarp(mask);
   // S_y = C_bar X + R_x (upper entries spread over the lanes, mirrored) and
   // the innovation e = y_k - C_bar m (lane j < m)
-  for (int u = lane; u < MY * MY; u += Gm::SG) {
-    const int i = u / MY, j = u - (u / MY) * MY;
+  for (int u = lane; u < MM * MM; u += Gm::SG) {
+    const int i = u / MM, j = u - (u / MM) * MM;
     if (i <= j && j < m) {
       TR v = (TR)Rx[i * m + j];
 #pragma unroll
@@ -256,10 +261,10 @@ __device__ void setup_interval(const Ctx& c, long long gi, int lane, unsigned ma
     TR logdet = TR(0);
     ok &= small_sym_inverse<TR>(Sy, Si, m, &logdet);
 #pragma unroll
-    for (int i = 0; i < MY; ++i) {
+    for (int i = 0; i < MM; ++i) {
       TR v = TR(0);
 #pragma unroll
-      for (int j = 0; j < MY; ++j)
+      for (int j = 0; j < MM; ++j)
         if (i < m && j < m) v = fma(Si[i][j], sb[Gm::ev + j], v);
       kap[i] = v;
     }
@@ -267,7 +272,7 @@ __device__ void setup_interval(const Ctx& c, long long gi, int lane, unsigned ma
     if (c.loglik && lane == 0) {
       TR q = TR(0);
 #pragma unroll
-      for (int j = 0; j < MY; ++j)
+      for (int j = 0; j < MM; ++j)
         if (j < m) q = fma(sb[Gm::ev + j], kap[j], q);
       c.lterm[gi] = -0.5 * ((double)m * 1.8378770664093454836 + (double)logdet + (double)q);
     }
@@ -277,7 +282,7 @@ __device__ void setup_interval(const Ctx& c, long long gi, int lane, unsigned ma
   if (row) {
     const double* VHl = md + c.ml.VH + (long long)(l - 1) * NX * m;
 #pragma unroll
-    for (int j = 0; j < MY; ++j) {
+    for (int j = 0; j < MM; ++j) {
       TR v = TR(0);
       if (j < m) {
         v = (TR)VHl[r * m + j];
@@ -287,10 +292,10 @@ __device__ void setup_interval(const Ctx& c, long long gi, int lane, unsigned ma
       Ul[j] = v;
     }
 #pragma unroll
-    for (int i = 0; i < MY; ++i) {
+    for (int i = 0; i < MM; ++i) {
       TR v = TR(0);
 #pragma unroll
-      for (int j = 0; j < MY; ++j)
+      for (int j = 0; j < MM; ++j)
         if (i < m && j < m) v = fma(Si[i][j], Ul[j], v);
       sb[Gm::SUl + i * NX + r] = v;
     }
@@ -298,7 +303,7 @@ __device__ void setup_interval(const Ctx& c, long long gi, int lane, unsigned ma
 #pragma unroll
     for (int q = 0; q < NX; ++q) v = fma((TR)Al[r * NX + q], sb[Gm::mv + q], v);
 #pragma unroll
-    for (int j = 0; j < MY; ++j)
+    for (int j = 0; j < MM; ++j)
       if (j < m) v = fma(Ul[j], kap[j], v);
     sb[Gm::ml + r] = v;
 #pragma unroll
@@ -437,17 +442,17 @@ __device__ void setup_interval(const Ctx& c, long long gi, int lane, unsigned ma
         rc[RL::Pm + r * NX + q] = sb[Gm::Pm + r * NX + q];
       }
 #pragma unroll
-      for (int j = 0; j < MY; ++j) {
+      for (int j = 0; j < MM; ++j) {
         rc[RL::X + r * MY + j] = sb[Gm::X + r * MY + j];
         rc[RL::SUl + j * NX + r] = sb[Gm::SUl + j * NX + r];
       }
     }
     if (lane == 0) {
 #pragma unroll
-      for (int i = 0; i < MY; ++i) {
+      for (int i = 0; i < MM; ++i) {
         rc[RL::kap + i] = kap[i];
 #pragma unroll
-        for (int j = 0; j < MY; ++j) rc[RL::Si + i * MY + j] = Si[i][j];
+        for (int j = 0; j < MM; ++j) rc[RL::Si + i * MY + j] = Si[i][j];
       }
     }
   }
@@ -456,7 +461,7 @@ __device__ void setup_interval(const Ctx& c, long long gi, int lane, unsigned ma
     const bool last = k >= N - 1;
     if constexpr (sizeof(T) == sizeof(TR)) {
       __syncwarp(mask);  // the record's reads of Pm (P11 reuses it)
-      setup_elements<NX, TR, double, T>(r, row, mask, m, last, sb + Gm::P, sb + Gm::Pl, sb + Gm::X, sb + Gm::SUl,
+      setup_elements<NX, M, TR, double, T>(r, row, mask, m, last, sb + Gm::P, sb + Gm::Pl, sb + Gm::X, sb + Gm::SUl,
                                         sb + Gm::Z, sb + Gm::ml, sb + Gm::mv, A1, md + c.ml.Qc, md + c.ml.Ql,
                                         md + c.ml.VH, Si, kap, sb + Gm::U1, sb + Gm::P1l, sb + Gm::P11,
                                         sb + Gm::Aml, sb + Gm::AP1, se, ui ? ui + UIn<NX>::b1 : nullptr,
@@ -471,7 +476,7 @@ __device__ void setup_interval(const Ctx& c, long long gi, int lane, unsigned ma
           sf[Gm::fZ + r * NX + q] = (T)sb[Gm::Z + r * NX + q];
         }
 #pragma unroll
-        for (int j = 0; j < MY; ++j) {
+        for (int j = 0; j < MM; ++j) {
           sf[Gm::fX + r * MY + j] = (T)sb[Gm::X + r * MY + j];
           sf[Gm::fSUl + j * NX + r] = (T)sb[Gm::SUl + j * NX + r];
         }
@@ -480,14 +485,14 @@ __device__ void setup_interval(const Ctx& c, long long gi, int lane, unsigned ma
       }
       T Sif[MY][MY], kapf[MY];
 #pragma unroll
-      for (int i = 0; i < MY; ++i) {
+      for (int i = 0; i < MM; ++i) {
         kapf[i] = i < m ? (T)kap[i] : T(0);
 #pragma unroll
-        for (int j = 0; j < MY; ++j) Sif[i][j] = (i < m && j < m) ? (T)Si[i][j] : T(0);
+        for (int j = 0; j < MM; ++j) Sif[i][j] = (i < m && j < m) ? (T)Si[i][j] : T(0);
       }
       __syncwarp(mask);
       const T* cf = (const T*)(md + c.ml.Cf);
-      setup_elements<NX, T, T, T>(r, row, mask, m, last, sf + Gm::fP, sf + Gm::fPl, sf + Gm::fX, sf + Gm::fSUl,
+      setup_elements<NX, M, T, T, T>(r, row, mask, m, last, sf + Gm::fP, sf + Gm::fPl, sf + Gm::fX, sf + Gm::fSUl,
                                   sf + Gm::fZ, sf + Gm::fml, sf + Gm::fmv, cf + Gm::cA, cf + Gm::cQc, cf + Gm::cQl,
                                   cf + Gm::cVH, Sif, kapf, sf + Gm::fU1, sf + Gm::fP1l, sf + Gm::fP11,
                                   sf + Gm::fAml, sf + Gm::fU1, se, ui ? ui + UIn<NX>::b1 : nullptr,
@@ -599,7 +604,7 @@ struct FilterOp {
       TS* sb = (TS*)sl;
       T* sf = FLOAT_ELEMENTS ? (T*)(sl + align16(Gm::SLOT * sizeof(TS))) : nullptr;
       for (int j = slot; j < count; j += per_round)
-        setup_interval<NX, T, TS>(c, base_row + p0 + j, lane, mask, sb, sf, j == 0 ? prevb : nullptr);
+        setup_interval<NX, 0, T, TS>(c, base_row + p0 + j, lane, mask, sb, sf, j == 0 ? prevb : nullptr);
     }
     __syncthreads();
   }
@@ -1382,7 +1387,7 @@ __global__ void __launch_bounds__(128) input_kernel(Ctx c) {
 // interval setup as its own kernel (after the filter scan): blocks of 128
 // threads, SG lanes per interval, one interval per lane group.
 // ===========================================================================
-template <int NX, class T, class TS>
+template <int NX, int M, class T, class TS>
 __global__ void __launch_bounds__(128) setup_kernel(Ctx c) {
   using Gm = SetupGeom<NX>;
   constexpr int SG = Gm::SG;
@@ -1394,13 +1399,13 @@ __global__ void __launch_bounds__(128) setup_kernel(Ctx c) {
   const unsigned mask = (SG == 32) ? 0xffffffffu : (((1u << SG) - 1u) << ((threadIdx.x & 31) & ~(SG - 1)));
   unsigned char* sl = ssm + (size_t)slot * Gm::template slot_bytes<T, TS>();
   T* sf = (sizeof(T) != sizeof(TS)) ? (T*)(sl + align16(Gm::SLOT * sizeof(TS))) : nullptr;
-  setup_interval<NX, T, TS>(c, gi, lane, mask, (TS*)sl, sf, nullptr);
+  setup_interval<NX, M, T, TS>(c, gi, lane, mask, (TS*)sl, sf, nullptr);
 }
 
 // ===========================================================================
 // host-side launch of the templated stages
 // ===========================================================================
-template <class Op>
+template <int NX, int M, class T, class TS>
 struct SetupTag {};
 template <int NX, int M, class TR, int PHASE>
 struct RecoverTag {};
@@ -1470,7 +1475,12 @@ int query_shapes_t(int scan_groups, int scan_elems, int window, int recover_thre
   sh->grid_s = (int)std::max(1LL, std::min((long long)sh->blocks_per_sm_s * sm_count, tiles));
   sh->grid_setup = (int)((total_slow + 128 / SetupGeom<NX>::SG - 1) / (128 / SetupGeom<NX>::SG));
   sh->smem_setup = setup_separate ? (size_t)(128 / SetupGeom<NX>::SG) * SetupGeom<NX>::template slot_bytes<T, TS>() : 0;
-  if (setup_separate) set_smem_attr<SetupTag<FOp>>((const void*)setup_kernel<NX, T, TS>, sh->smem_setup);
+  if (setup_separate) {  // the setup kernel is compiled per measurement size
+    set_smem_attr<SetupTag<NX, 1, T, TS>>((const void*)setup_kernel<NX, 1, T, TS>, sh->smem_setup);
+    set_smem_attr<SetupTag<NX, 2, T, TS>>((const void*)setup_kernel<NX, 2, T, TS>, sh->smem_setup);
+    set_smem_attr<SetupTag<NX, 3, T, TS>>((const void*)setup_kernel<NX, 3, T, TS>, sh->smem_setup);
+    set_smem_attr<SetupTag<NX, 4, T, TS>>((const void*)setup_kernel<NX, 4, T, TS>, sh->smem_setup);
+  }
   sh->recover_threads = recover_threads;
   set_recover_smem<NX, TR, 0>(recover_smem_bytes<NX>(recover_threads));
   set_recover_smem<NX, TR, 1>(recover_smem_bytes<NX>(recover_threads));
@@ -1515,7 +1525,12 @@ int launch_t(const Ctx& c, const Shapes& sh, cudaStream_t st, cudaEvent_t* ev, c
     scan_kernel<FOp><<<sh.grid_f, sh.scan_groups_f * G, sh.smem_f, st>>>(c, sh.scan_groups_f, sh.scan_elems_f, sh.window_f);
   if (ev) cudaEventRecord(ev[1], st);
   if (c.setup_separate)
-    setup_kernel<NX, T, TS><<<sh.grid_setup, 128, sh.smem_setup, st>>>(c);
+    switch (c.ny) {
+      case 1: setup_kernel<NX, 1, T, TS><<<sh.grid_setup, 128, sh.smem_setup, st>>>(c); break;
+      case 2: setup_kernel<NX, 2, T, TS><<<sh.grid_setup, 128, sh.smem_setup, st>>>(c); break;
+      case 3: setup_kernel<NX, 3, T, TS><<<sh.grid_setup, 128, sh.smem_setup, st>>>(c); break;
+      default: setup_kernel<NX, 4, T, TS><<<sh.grid_setup, 128, sh.smem_setup, st>>>(c); break;
+    }
   launch_loglik(c, st);
   if (ev) cudaEventRecord(ev[2], st);  // otherwise the interval setup runs inside the filter scan
   const unsigned rblocks = (unsigned)((c.total_fast + sh.recover_threads - 1) / sh.recover_threads);
