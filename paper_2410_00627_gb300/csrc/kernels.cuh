@@ -1519,9 +1519,14 @@ int launch_t(const Ctx& c, const Shapes& sh, cudaStream_t st, cudaEvent_t* ev, c
   if (c.uin) input_kernel<NX><<<(unsigned)((c.total_slow + 127) / 128), 128, 0, st>>>(c);
   if (ev) cudaEventRecord(ev[0], st);
   const unsigned seq_blocks = (unsigned)((c.n_seq + SEQ_THREADS - 1) / SEQ_THREADS);
-  if (c.sequential)
-    seq_filter_kernel<NX, TS><<<seq_blocks, SEQ_THREADS, 0, st>>>(c);
-  else
+  if (c.sequential) {
+    switch (c.ny) {
+      case 1: seq_filter_kernel<NX, 1, TS><<<seq_blocks, SEQ_THREADS, 0, st>>>(c); break;
+      case 2: seq_filter_kernel<NX, 2, TS><<<seq_blocks, SEQ_THREADS, 0, st>>>(c); break;
+      case 3: seq_filter_kernel<NX, 3, TS><<<seq_blocks, SEQ_THREADS, 0, st>>>(c); break;
+      default: seq_filter_kernel<NX, 4, TS><<<seq_blocks, SEQ_THREADS, 0, st>>>(c); break;
+    }
+  } else
     scan_kernel<FOp><<<sh.grid_f, sh.scan_groups_f * G, sh.smem_f, st>>>(c, sh.scan_groups_f, sh.scan_elems_f, sh.window_f);
   if (ev) cudaEventRecord(ev[1], st);
   if (c.setup_separate)

@@ -20,13 +20,15 @@ constexpr int SEQ_THREADS = 64;
 // x_{k,l} = F x + K (y_k - c_k) + b_{k,l} + eps (Cov eps = D, eps and nu
 // independent), F = A^l - K C_bar, D = Q_bar - K (G Q~ M^T)^T.  Conditioning x
 // on y_k and propagating gives the Eq. (9)-(12) filter result exactly.
-template <int NX, class TS>
+// M = ny (compile-time): loops over the measurement entries run M times.
+template <int NX, int M, class TS>
 __global__ void __launch_bounds__(SEQ_THREADS) seq_filter_kernel(Ctx c) {
-  constexpr int NN = NX * NX;
+  constexpr int NN = NX * NX, MM = M;
   if (!c.ctr->call_ok) return;
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= c.n_seq) return;
-  const int m = c.ny, N = c.meta.nslow[s];
+  constexpr int m = M;
+  const int N = c.meta.nslow[s];
   const long long off = c.meta.off_slow[s];
   const double* md = c.model + (long long)s * c.ml.stride;
   const double* Fc = md + c.ml.Fc;
@@ -56,7 +58,7 @@ __global__ void __launch_bounds__(SEQ_THREADS) seq_filter_kernel(Ctx c) {
     const double* ui = c.uin ? c.uin + row * UIn<NX>::SIZE : nullptr;
     TS yc[MY], CP[MY][NX], S[MY][MY], Si[MY][MY], e[MY];
 #pragma unroll
-    for (int j = 0; j < MY; ++j) {
+    for (int j = 0; j < MM; ++j) {
       yc[j] = TS(0);
       e[j] = TS(0);
       if (j < m) {
@@ -69,7 +71,7 @@ __global__ void __launch_bounds__(SEQ_THREADS) seq_filter_kernel(Ctx c) {
     }
     // C_bar P, S = C_bar P C_bar^T + R_x
 #pragma unroll
-    for (int j = 0; j < MY; ++j)
+    for (int j = 0; j < MM; ++j)
 #pragma unroll
       for (int q = 0; q < NX; ++q) {
         TS v = TS(0);
@@ -79,9 +81,9 @@ __global__ void __launch_bounds__(SEQ_THREADS) seq_filter_kernel(Ctx c) {
         CP[j][q] = v;
       }
 #pragma unroll
-    for (int i = 0; i < MY; ++i)
+    for (int i = 0; i < MM; ++i)
 #pragma unroll
-      for (int j = 0; j < MY; ++j) {
+      for (int j = 0; j < MM; ++j) {
         TS v = (i == j) ? TS(1) : TS(0);
         if (i < m && j < m) {
           v = (TS)__ldg(Rx + i * m + j);
@@ -94,12 +96,12 @@ __global__ void __launch_bounds__(SEQ_THREADS) seq_filter_kernel(Ctx c) {
     // LT = S^-1 C_bar P  (the transposed gain P C_bar^T S^-1)
     TS LT[MY][NX];
 #pragma unroll
-    for (int i = 0; i < MY; ++i)
+    for (int i = 0; i < MM; ++i)
 #pragma unroll
       for (int q = 0; q < NX; ++q) {
         TS v = TS(0);
 #pragma unroll
-        for (int j = 0; j < MY; ++j)
+        for (int j = 0; j < MM; ++j)
           if (j < m) v = fma(Si[i][j], CP[j][q], v);
         LT[i][q] = v;
       }
@@ -109,7 +111,7 @@ __global__ void __launch_bounds__(SEQ_THREADS) seq_filter_kernel(Ctx c) {
     for (int r = 0; r < NX; ++r) {
       TS v = mv[r];
 #pragma unroll
-      for (int j = 0; j < MY; ++j)
+      for (int j = 0; j < MM; ++j)
         if (j < m) v = fma(LT[j][r], e[j], v);
       mp[r] = v;
     }
@@ -119,7 +121,7 @@ __global__ void __launch_bounds__(SEQ_THREADS) seq_filter_kernel(Ctx c) {
       for (int q = r; q < NX; ++q) {
         TS v = P[r][q];
 #pragma unroll
-        for (int j = 0; j < MY; ++j)
+        for (int j = 0; j < MM; ++j)
           if (j < m) v = fma(-CP[j][r], LT[j][q], v);
         P[r][q] = v;
         P[q][r] = v;
@@ -132,7 +134,7 @@ __global__ void __launch_bounds__(SEQ_THREADS) seq_filter_kernel(Ctx c) {
 #pragma unroll
       for (int q = 0; q < NX; ++q) v = fma((TS)__ldg(Fc + r * NX + q), mp[q], v);
 #pragma unroll
-      for (int j = 0; j < MY; ++j)
+      for (int j = 0; j < MM; ++j)
         if (j < m) v = fma((TS)__ldg(Kc + r * m + j), yc[j], v);
       mv[r] = v;
 #pragma unroll
