@@ -743,7 +743,9 @@ def report_errors(cfg, precisions=("fp64", "mixed", "fp32"), n_slow=None, seed=0
     """Max relative errors (max |x - x_oracle| / max |x_oracle|) of the smoothed
     and filtered outputs of each precision mode against the FP64 oracle, for
     config `cfg` at full size: every slow-rate output and the fast-rate
-    outputs of the first and last three intervals."""
+    outputs of the first and last three intervals.  Also the time of the
+    smoother call (smoothed outputs only, built-in launch shapes): median of 5
+    direct calls after 2 warm-up calls, CUDA events on the calling stream."""
     import torch
 
     import oracle
@@ -759,7 +761,7 @@ def report_errors(cfg, precisions=("fp64", "mixed", "fp32"), n_slow=None, seed=0
     tail = oracle.sequential(prob, k_lo=N - w, k_hi=N, slow=False, smooth=True)
     dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")  # noqa: E731
     ins = [dev(getattr(prob, k)) for k in ("F", "Q", "H", "R", "m0", "P0", "y")]
-    res = {}
+    res, timing = {}, {}
     for prec in precisions:
         try:
             sm, fi = api.smoother(*ins, l, precision=prec, filtered=api.OUTPUT_KEYS)
@@ -767,6 +769,10 @@ def report_errors(cfg, precisions=("fp64", "mixed", "fp32"), n_slow=None, seed=0
         except api.SRTMError as err:   # reported, e.g. a singular solve in the float32 mode
             res[prec] = {"error": str(err)}
             continue
+        ms = time_calls(lambda st: api.smoother(*ins, l, precision=prec, out=sm, stream=st), 5, 2,
+                        torch.cuda.current_stream())
+        timing[prec] = {"ms_per_call": float(np.median(ms)),
+                        "fast_states_per_s": N * l / (float(np.median(ms)) * 1e-3)}
         sm = {k: v.cpu().numpy() for k, v in sm.items()}
         fi = {k: v.cpu().numpy() for k, v in fi.items()}
         e = {}
@@ -788,7 +794,7 @@ def report_errors(cfg, precisions=("fp64", "mixed", "fp32"), n_slow=None, seed=0
         del sm, fi
         torch.cuda.empty_cache()
     return {"config": cfg, "nx": prob.nx, "ny": prob.ny, "ratio": l, "n_slow": N, "n_fast": N * l,
-            "errors": res}
+            "errors": res, "timing": timing}
 
 
 def run_reference(args):
