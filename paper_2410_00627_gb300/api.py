@@ -138,6 +138,19 @@ def _dev_tensor(t, name, shape):
     return c_void_p(t.data_ptr())
 
 
+def _out_tensor(t, name, shape):
+    """Outputs: CUDA tensors, or pinned host tensors (the kernels write those
+    directly; with unified addressing the device uses the host address)."""
+    import torch
+    if isinstance(t, torch.Tensor) and not t.is_cuda:
+        if not (t.is_pinned() and t.dtype == torch.float64 and t.is_contiguous()):
+            raise TypeError(f"{name} must be a CUDA tensor or a contiguous pinned float64 host tensor")
+        if tuple(t.shape) != tuple(shape):
+            raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+        return c_void_p(t.data_ptr())
+    return _dev_tensor(t, name, shape)
+
+
 def _alloc_outputs(keys, device, rows_fast, rows_slow, nx, out=None, n_seq=1):
     import torch
     res = {}
@@ -149,7 +162,7 @@ def _alloc_outputs(keys, device, rows_fast, rows_slow, nx, out=None, n_seq=1):
         t = None if out is None else out.get(k)
         if t is None:
             t = torch.empty(shapes[k], dtype=torch.float64, device=device)
-        _dev_tensor(t, k, shapes[k])
+        _out_tensor(t, k, shapes[k])
         res[k] = t
     o = Output(*[c_void_p(res[k].data_ptr()) if k in res else None for k in ALL_OUTPUTS])
     return res, o

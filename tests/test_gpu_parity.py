@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 from paper_2410_00627_gb300 import synth
-from tests.gpu_util import TOL, compare, oracle_views, run_filter, run_smoother, to_dev
+from tests.gpu_util import TOL, assert_same_to_rounding, compare, oracle_views, run_filter, run_smoother, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -97,12 +97,13 @@ def test_outputs_exactly_symmetric_and_last_interval(oracle_mod):
     assert np.array_equal(sm["fast_cov"][-l:], fi["fast_cov"][-l:])
 
 
-def test_repeated_calls_are_bitwise_identical():
-    prob = synth.config2(seed=4, n_slow=300, keep_states=False)
-    a, _ = run_smoother(prob, "fp64", filtered=False)
-    b, _ = run_smoother(prob, "fp64", filtered=False)
-    for k in a:
-        assert np.array_equal(a[k], b[k]), k
+def test_repeated_calls_agree_to_rounding():
+    prob = synth.config2(seed=4, n_slow=3000, keep_states=False)
+    for precision in ("fp64", "mixed"):
+        a, _ = run_smoother(prob, precision, filtered=False)
+        b, _ = run_smoother(prob, precision, filtered=False)
+        for k in a:
+            assert_same_to_rounding(a[k], b[k], precision, k)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
@@ -220,7 +221,7 @@ def test_host_entry_point_matches_device_entry_point():
     host = api.smoother_host(*[np.ascontiguousarray(getattr(prob, k)) for k in ("F", "Q", "H", "R", "m0", "P0", "y")],
                              prob.ratio, precision="mixed")
     for k in dev:
-        assert np.array_equal(dev[k], host[k]), k
+        assert_same_to_rounding(host[k], dev[k], "fp64", k)
 
 
 def test_stage_timing_reports_every_stage():
@@ -305,7 +306,7 @@ def test_loglik_matches_oracle(oracle_mod, case, precision):
     tol = 1e-9 if precision == "fp64" else 1e-4
     assert abs(got - want) <= tol * max(1.0, abs(want)), (got, want)
     plain, _ = api.smoother(*args, l, precision=precision)
-    assert np.array_equal(plain["fast_cov"].cpu().numpy(), sm["fast_cov"].cpu().numpy())
+    assert_same_to_rounding(plain["fast_cov"], sm["fast_cov"], precision, "fast_cov")
 
 
 def test_loglik_full_size_config2_and_filter_call(oracle_mod):
@@ -374,7 +375,7 @@ def test_batch_descriptor_keeps_its_tensors_alive(oracle_mod):
 
 def test_host_entry_point_direct_pinned_outputs_match_staged():
     """Pinned host outputs are written by the kernels directly; pageable ones
-    are staged and copied: both equal the device path bit for bit."""
+    are staged and copied: both agree with the device path to rounding."""
     import torch
 
     from paper_2410_00627_gb300 import api
@@ -391,13 +392,13 @@ def test_host_entry_point_direct_pinned_outputs_match_staged():
         api.status()
         for k in shapes:
             want = dev[k].cpu().numpy()
-            assert np.array_equal(direct[k], want), (precision, k)
-            assert np.array_equal(staged[k], want), (precision, k)
+            assert_same_to_rounding(direct[k], want, precision, f"direct {k}")
+            assert_same_to_rounding(staged[k], want, precision, f"staged {k}")
 
 
 def test_host_entry_point_reads_pinned_inputs_directly():
-    """Pinned y (and u) are read by the kernels in place; results equal the
-    device path's bit for bit, with and without known inputs."""
+    """Pinned y (and u) are read by the kernels in place; results agree with
+    the device path's to rounding, with and without known inputs."""
     import torch
 
     from paper_2410_00627_gb300 import api
@@ -417,7 +418,7 @@ def test_host_entry_point_reads_pinned_inputs_directly():
                                outputs=api.ALL_OUTPUTS, **dev_extra)
         api.status()
         for k in api.ALL_OUTPUTS:
-            assert np.array_equal(got[k], want[k].cpu().numpy()), (prob.name, k)
+            assert_same_to_rounding(got[k], want[k], "fp64", f"{prob.name} {k}")
 
 
 def test_outputs_at_8_byte_offsets():
@@ -439,13 +440,14 @@ def test_outputs_at_8_byte_offsets():
     want, _ = api.smoother(*args, prob.ratio)
     api.status()
     for k in shapes:
-        assert torch.equal(got[k], want[k]), k
+        assert_same_to_rounding(got[k], want[k], "fp64", k)
 
 
-def test_split_recovery_is_bitwise_identical_to_one_kernel():
+def test_split_recovery_matches_one_kernel():
     """The two halves of a split recovery do the one-kernel arithmetic in the
-    same order: smoothed, filtered extras and log likelihood are identical;
-    the call makes one more launch.  Also for a ragged batch."""
+    same order: smoothed, filtered extras and log likelihood agree (to the
+    rounding that separates any two calls); the call makes one more launch.
+    Also for a ragged batch."""
     import torch
 
     from paper_2410_00627_gb300 import api
@@ -473,7 +475,38 @@ def test_split_recovery_is_bitwise_identical_to_one_kernel():
             assert launches[2] == launches[1] + 1
             for part in range(3):
                 for k in res[1][part]:
-                    assert torch.equal(res[1][part][k], res[2][part][k]), (precision, part, k)
+                    assert_same_to_rounding(res[2][part][k], res[1][part][k], precision, f"{part} {k}")
     finally:
         for p in ("fp64", "mixed", "fp32"):
             api.set_tuning(4, p)
+
+
+def test_pinned_host_output_tensors_through_the_device_api():
+    """Outputs may be pinned host tensors (the kernels write them directly):
+    equal to the device outputs, for a single sequence and a batch."""
+    import torch
+
+    from paper_2410_00627_gb300 import api
+    prob = synth.random_model(27, 4, 2, 6, 120)
+    args = [to_dev(getattr(prob, k)) for k in ("F", "Q", "H", "R", "m0", "P0", "y")]
+    n_fast, nx = prob.n_slow * prob.ratio, prob.nx
+    host = {"fast_cov": torch.empty((n_fast, nx, nx), dtype=torch.float64, pin_memory=True),
+            "slow_mean": torch.empty((prob.n_slow, nx), dtype=torch.float64, pin_memory=True)}
+    got, _ = api.smoother(*args, prob.ratio, precision="mixed", out=host)
+    want, _ = api.smoother(*args, prob.ratio, precision="mixed")
+    api.status()
+    assert not got["fast_cov"].is_cuda
+    for k in host:
+        assert_same_to_rounding(got[k], want[k], "mixed", k)
+    with pytest.raises(TypeError):  # pageable host memory is not accepted
+        api.smoother(*args, prob.ratio, out={"slow_mean": torch.empty((prob.n_slow, nx), dtype=torch.float64)})
+    probs = synth.config4(seed=15, n_seq=9, n_min=1, n_max=70)
+    pk = synth.pack(probs)
+    t = lambda a: torch.as_tensor(a, device="cuda")  # noqa: E731
+    b = api.make_batch(t(pk["F"]), t(pk["Q"]), t(pk["H"]), t(pk["R"]), t(pk["m0"]), t(pk["P0"]), t(pk["y"]),
+                       t(pk["ratio"]), t(pk["n_slow"]), pk["max_ratio"], pk["total_slow"], pk["total_fast"])
+    hs = {"slow_cov": torch.empty((pk["total_slow"], 4, 4), dtype=torch.float64, pin_memory=True)}
+    got, _ = api.smoother_batch(b, precision="fp64", out=hs)
+    want, _ = api.smoother_batch(b, precision="fp64")
+    api.status()
+    assert_same_to_rounding(got["slow_cov"], want["slow_cov"], "fp64", "batch slow_cov")
