@@ -3,7 +3,7 @@
 One step = one srtm_smoother call over one synthetic sequence: per-model
 constants, forward filter scan, interval setup + smoother elements, reverse
 smoother scan and fast-rate recovery (fast and slow smoothed means and
-covariances written to HBM).  Workload (default): config 2, the 4-species
+covariances written to HBM).  Workload (default): chain4, the 4-species
 chain with nx=4, ny=2, ratio L=20, T=10^4 slow measurements (2*10^5 fast
 steps), synthetic data from the seeded generator.  Inputs and outputs are
 resident in HBM; L2 (129 MB) is flushed by writing a 256 MB buffer before
@@ -14,7 +14,7 @@ symmetrisation and recovery).  The same line carries the plain-FP64 number.
 Before timing, the library's autotuner (srtm_autotune) picks the launch shapes
 for the workload; the chosen shapes are reported in `config.tuning`.
 
-`--workload config4`: the ragged batch of config 4 (4096 sequences, nx=4,
+`--workload ragged_chains`: the ragged batch (4096 sequences, nx=4,
 ny=1, ratio in {5,10,20}, 100..20000 slow steps each) as one
 srtm_smoother_batch call captured in a CUDA graph and replayed; outputs (about
 77 GB per step) are far larger than L2, so no flush.  The line adds the plain
@@ -22,7 +22,7 @@ FP64 batched number and the plain FP64 single-sequence path looped over the
 4096 sequences.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload config2|config4]
+                  [--workload chain4|ragged_chains]
 Multi-GPU (torchrun): every rank runs its own independent workload (weak
 scaling, no collective on the data path); rank 0 prints.
 """
@@ -59,30 +59,31 @@ def parse(argv=None):
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-extras", action="store_true", help="skip the fp64, e2e and cpu legs")
-    ap.add_argument("--workload", choices=["config2", "config4"], default="config2")
-    ap.add_argument("--n-seq", type=int, default=4096, help="config4: sequences in the batch")
+    ap.add_argument("--workload", choices=["chain4", "ragged_chains"], default="chain4")
+    ap.add_argument("--n-seq", type=int, default=4096, help="ragged_chains: sequences in the batch")
     ap.add_argument("--no-autotune", action="store_true", help="keep the built-in launch shapes")
     ap.add_argument("--tuning", default=None,
                     help="explicit launch shapes scan_groups,scan_elems,recover_threads,lookback_window "
                          "(for every precision; replaces the autotuner)")
     ap.add_argument("--tune-reps", type=int, default=2)
     ap.add_argument("--sweep", action="store_true",
-                    help="config 2 over T = 10^2 .. 10^4 slow steps (x sqrt 10), FP64 and mixed, one JSON line each")
+                    help="chain4 over T = 10^2 .. 10^4 slow steps (x sqrt 10), FP64 and mixed, one JSON line each")
     ap.add_argument("--figure", action="store_true",
                     help="run time of the scan and the sequential forms (filter and smoother, FP64) over "
-                         "T = 16 .. 6000 slow steps of config 2, one JSON line per T")
+                         "T = 16 .. 6000 slow steps of chain4, one JSON line per T")
     ap.add_argument("--report-errors", action="store_true",
-                    help="max relative errors of every mode against the FP64 oracle, configs 1, 2, 3, 5 at full size")
+                    help="max relative errors of every mode against the FP64 oracle, every single-sequence "
+                         "workload at full size")
     return ap.parse_args(argv)
 
 
 def workload(args, rank=0):
     from paper_2410_00627_gb300 import synth
-    return synth.config2(seed=args.seed + rank, n_slow=args.n_slow, keep_states=False)
+    return synth.chain4(seed=args.seed + rank, n_slow=args.n_slow, keep_states=False)
 
 
 def config_dict(args, prob, precision):
-    return {"workload": f"config 2: 4-species chain nx=4 ny=2 L={prob.ratio} T={prob.n_slow} slow "
+    return {"workload": f"chain4: 4-species chain nx=4 ny=2 L={prob.ratio} T={prob.n_slow} slow "
                         f"({prob.n_slow * prob.ratio} fast steps)",
             "precision": precision, "nx": prob.nx, "ny": prob.ny, "ratio": prob.ratio,
             "n_slow": prob.n_slow, "l2": "flushed (256 MB write) before every timed step",
@@ -258,7 +259,7 @@ def run_ours(args, rank, world, dist):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"mixed": "f32+f64", "fp64": "f64", "fp32": "f32"}[args.precision],
-        "data": "synthetic (seeded generator, config 2 linear kinetics)",
+        "data": "synthetic (seeded generator, chain4 linear kinetics)",
         "config": dict(config_dict(args, prob, args.precision),
                        tuning=tuning.get(args.precision, api.get_tuning(prob.nx, args.precision)),
                        timing="CUDA-graph replay of the call, CUDA events on its stream, mean of the steps"),
@@ -327,7 +328,7 @@ def time_calls(call, steps, warmup, stream, flush=None):
 def run_figure(args):
     """The scan forms against the sequential forms (the paper's figure of
     parallel vs sequential IMKF / IMS run time over the number of steps), on
-    config 2 (l = 20) in FP64, each call timed on its own."""
+    chain4 (l = 20) in FP64, each call timed on its own."""
     import torch
 
     from paper_2410_00627_gb300 import api, build, synth
@@ -337,7 +338,7 @@ def run_figure(args):
     stream = torch.cuda.current_stream()
     lines = []
     for n_slow in (16, 32, 64, 128, 256, 512, 1024, 2048, 4096, 6000):
-        prob = synth.config2(seed=args.seed, n_slow=n_slow, keep_states=False)
+        prob = synth.chain4(seed=args.seed, n_slow=n_slow, keep_states=False)
         t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)  # noqa: E731
         ins = [t(getattr(prob, k)) for k in ("F", "Q", "H", "R", "m0", "P0", "y")]
         n_fast = n_slow * prob.ratio
@@ -345,7 +346,7 @@ def run_figure(args):
                 "fast_cov": torch.empty(n_fast, prob.nx, prob.nx, dtype=torch.float64, device=dev),
                 "slow_mean": torch.empty(n_slow, prob.nx, dtype=torch.float64, device=dev),
                 "slow_cov": torch.empty(n_slow, prob.nx, prob.nx, dtype=torch.float64, device=dev)}
-        row = {"figure": "config 2 scan vs sequential, fp64", "n_slow": n_slow, "fast_steps": n_fast, "unit": "us"}
+        row = {"figure": "chain4 scan vs sequential, fp64", "n_slow": n_slow, "fast_steps": n_fast, "unit": "us"}
         for method in ("scan", "sequential"):
             for kind in ("filter", "smoother"):
                 fn = api.filter if kind == "filter" else api.smoother
@@ -357,15 +358,15 @@ def run_figure(args):
     return lines
 
 
-# --------------------------------------------------------------------------- config 4 (batched)
+# --------------------------------------------------------------------------- ragged batch
 def batched_workload(args, rank=0):
     from paper_2410_00627_gb300 import synth
     workers = max(1, min(16, (os.cpu_count() or 1)))
-    return synth.config4(seed=args.seed + rank, n_seq=args.n_seq, workers=workers)
+    return synth.ragged_chains(seed=args.seed + rank, n_seq=args.n_seq, workers=workers)
 
 
 def batched_config(args, pk, precision, tuning):
-    return {"workload": f"config 4: {len(pk['ratio'])} ragged 4-species chains nx=4 ny=1 L in {{5,10,20}} "
+    return {"workload": f"ragged_chains: {len(pk['ratio'])} ragged 4-species chains nx=4 ny=1 L in {{5,10,20}} "
                         f"N in [100,20000] ({pk['total_slow']} slow / {pk['total_fast']} fast steps)",
             "precision": precision, "n_seq": int(len(pk["ratio"])), "total_slow": pk["total_slow"],
             "total_fast": pk["total_fast"], "call": "srtm_smoother_batch captured in a CUDA graph, replayed",
@@ -478,7 +479,7 @@ def run_batched(args, rank, world, dist):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"mixed": "f32+f64", "fp64": "f64", "fp32": "f32"}[args.precision],
-        "data": "synthetic (seeded generator, config 4 ragged linear-kinetics batch)",
+        "data": "synthetic (seeded generator, ragged batch of linear-kinetics chains)",
         "config": batched_config(args, pk, args.precision, tuning.get(args.precision,
                                                                        api.get_tuning(nx, args.precision))),
         "parity": parity,
@@ -487,7 +488,7 @@ def run_batched(args, rank, world, dist):
                      "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": achieved / FP64_PEAK_GFLOPS,
                      "peak_source": "GB300 FP64 nominal 1.25 TFLOP/s (recipe table)",
                      "flops_per_fast_step": 2 * fma_per_fast,
-                     "traffic": recorded_traffic(args.precision, n_fast, "config4")},
+                     "traffic": recorded_traffic(args.precision, n_fast, "ragged_chains")},
         "gpu_launches": args.steps * api.last_call_launches(),
         "clocks": clock_info,
     }
@@ -623,14 +624,14 @@ def run_cpu_baseline_batched(args, probs, seconds=None):
             "sample": f"the first {used} sequences of the batch ({n} fast steps) in {el:.1f} s, 1 thread, FP64 C"}
 
 
-def recorded_traffic(precision, n_fast, workload="config2"):
+def recorded_traffic(precision, n_fast, workload="chain4"):
     """DRAM bytes per call of the recovery from the committed ncu summary, if
-    the recovery kernel's source is unchanged since the capture.  Config 2 is
-    captured at full size; config 4 (too large for a full ncu capture) on its
-    first 64 sequences, scaled to the call by the number of fast steps."""
+    the recovery kernel's source is unchanged since the capture.  chain4 is
+    captured at full size; the ragged batch (too large for a full ncu capture)
+    on its first 64 sequences, scaled to the call by the number of fast steps."""
     import hashlib
-    name = {"config2": f"recover_kernel_config2_T1e4_{precision}.json",
-            "config4": f"recover_kernel_config4_first64_{precision}.json"}[workload]
+    name = {"chain4": f"recover_kernel_chain4_T1e4_{precision}.json",
+            "ragged_chains": f"recover_kernel_ragged_chains_first64_{precision}.json"}[workload]
     prof = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(prof):
         return None
@@ -641,7 +642,7 @@ def recorded_traffic(precision, n_fast, workload="config2"):
         b = src.index("// host-side launch of the templated stages")
         if tr.get("source_sha1") != hashlib.sha1(src[a:b].encode()).hexdigest():
             return None
-        if workload == "config2":
+        if workload == "chain4":
             return float(tr["dram_bytes_per_launch"]) if tr.get("n_fast") == n_fast else None
         return float(tr["dram_bytes_per_launch"]) * n_fast / float(tr["n_fast"])
     except (ValueError, KeyError, OSError):
@@ -744,17 +745,17 @@ def check_parity(prob, outs, precision, w=3):
 
 
 # --------------------------------------------------------------------------- error report
-REPORT_SIZES = {1: 100, 2: 10_000, 3: 100_000, 5: 10_000}
+REPORT_SIZES = {"ab_kinetics": 100, "chain4": 10_000, "network8": 100_000, "stiff_chain6": 10_000}
 
 
 def rel_err(a, b):
     return float(np.max(np.abs(a - b)) / max(float(np.max(np.abs(b))), 1e-300))
 
 
-def report_errors(cfg, precisions=("fp64", "mixed", "fp32"), n_slow=None, seed=0):
+def report_errors(name, precisions=("fp64", "mixed", "fp32"), n_slow=None, seed=0):
     """Max relative errors (max |x - x_oracle| / max |x_oracle|) of the smoothed
     and filtered outputs of each precision mode against the FP64 oracle, for
-    config `cfg` at full size: every slow-rate output and the fast-rate
+    workload `name` at full size: every slow-rate output and the fast-rate
     outputs of the first and last three intervals.  Also the time of the
     smoother call (smoothed outputs only, built-in launch shapes): median of 5
     direct calls after 2 warm-up calls, CUDA events on the calling stream."""
@@ -765,8 +766,8 @@ def report_errors(cfg, precisions=("fp64", "mixed", "fp32"), n_slow=None, seed=0
     build.build()
     api.load()
     oracle.build()
-    N = REPORT_SIZES[cfg] if n_slow is None else n_slow
-    prob = synth.CONFIGS[cfg](seed=seed, n_slow=N, keep_states=False)
+    N = REPORT_SIZES[name] if n_slow is None else n_slow
+    prob = synth.WORKLOADS[name](seed=seed, n_slow=N, keep_states=False)
     l = prob.ratio
     w = min(3, N)
     head = oracle.sequential(prob, k_lo=0, k_hi=w)
@@ -805,15 +806,15 @@ def report_errors(cfg, precisions=("fp64", "mixed", "fp32"), n_slow=None, seed=0
         res[prec] = e
         del sm, fi
         torch.cuda.empty_cache()
-    return {"config": cfg, "nx": prob.nx, "ny": prob.ny, "ratio": l, "n_slow": N, "n_fast": N * l,
+    return {"workload": name, "nx": prob.nx, "ny": prob.ny, "ratio": l, "n_slow": N, "n_fast": N * l,
             "errors": res, "timing": timing}
 
 
 def run_reference(args):
     """Reference arm: the FP64 CPU oracle on the host cores, same workload
-    (config 4: the first sequences of the batch, about --cpu-seconds of work
+    (ragged_chains: the first sequences of the batch, about --cpu-seconds of work
     per step)."""
-    if args.workload == "config4":
+    if args.workload == "ragged_chains":
         probs = batched_workload(args)
         import oracle
         oracle.build()
@@ -861,8 +862,8 @@ def main():
             print(json.dumps(run_reference(args)), flush=True)
         return
     if args.report_errors:
-        for cfg in (1, 2, 3, 5):
-            print(json.dumps(report_errors(cfg)), flush=True)
+        for name in REPORT_SIZES:
+            print(json.dumps(report_errors(name)), flush=True)
         return
     if args.figure:
         for ln in run_figure(args):
@@ -875,7 +876,7 @@ def main():
                 a = copy.copy(args)
                 a.n_slow, a.precision, a.no_extras = n_slow, prec, True
                 ln = run_ours(a, 0, 1, None)
-                print(json.dumps({"sweep": "config 2", "n_slow": n_slow, "fast_steps": n_slow * 20, "precision": prec,
+                print(json.dumps({"sweep": "chain4", "n_slow": n_slow, "fast_steps": n_slow * 20, "precision": prec,
                                   "value": ln["value"], "unit": UNIT, "ms_per_step": ln["ms_per_step"],
                                   "us_per_call": ln["ms_per_step"] * 1e3, "parity_ok": ln["parity"]["ok"],
                                   "tuning": ln["config"]["tuning"]}), flush=True)
@@ -887,7 +888,7 @@ def main():
         local = int(os.environ.get("LOCAL_RANK", "0"))
         torch.cuda.set_device(local)
         dist.init_process_group("nccl", init_method="env://")
-    line = (run_batched if args.workload == "config4" else run_ours)(args, rank, world, dist)
+    line = (run_batched if args.workload == "ragged_chains" else run_ours)(args, rank, world, dist)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

@@ -134,7 +134,7 @@ def simulate(rng: np.random.Generator, F, Q, H, R, m0, P0, ratio: int, n_slow: i
     return y, x
 
 
-def config1(seed: int = 0, n_slow: int = 100, keep_states: bool = True) -> Problem:
+def ab_kinetics(seed: int = 0, n_slow: int = 100, keep_states: bool = True) -> Problem:
     """2-state A->B kinetics: K=[[-k1,0],[k1,-k2]], k1=.5, k2=.2, dt=.1, l=10,
     Q=.01 I, m0=[1,0], P0=.1 I, y = [0,1] * sum of 10 fast states + N(0, 0.1)."""
     rng = np.random.default_rng(seed)
@@ -147,10 +147,10 @@ def config1(seed: int = 0, n_slow: int = 100, keep_states: bool = True) -> Probl
     m0 = np.array([1.0, 0.0])
     P0 = 0.1 * np.eye(2)
     y, x = simulate(rng, F, Q, H, R, m0, P0, 10, n_slow, keep_states)
-    return Problem(F, Q, H, R, m0, P0, y, 10, x, "cfg1", {"K": K, "dt": dt})
+    return Problem(F, Q, H, R, m0, P0, y, 10, x, "ab_kinetics", {"K": K, "dt": dt})
 
 
-def config2(seed: int = 0, n_slow: int = 10_000, keep_states: bool = True) -> Problem:
+def chain4(seed: int = 0, n_slow: int = 10_000, keep_states: bool = True) -> Problem:
     """4-species chain, rates log-U[0.05,1], dt=.05, l=20, H=[e3;e4], Q=1e-3 I,
     R=.05 I, m0=e1, P0=.1 I."""
     rng = np.random.default_rng(seed)
@@ -164,10 +164,10 @@ def config2(seed: int = 0, n_slow: int = 10_000, keep_states: bool = True) -> Pr
     m0 = np.eye(4)[0]
     P0 = 0.1 * np.eye(4)
     y, x = simulate(rng, F, Q, H, R, m0, P0, 20, n_slow, keep_states)
-    return Problem(F, Q, H, R, m0, P0, y, 20, x, "cfg2", {"K": K, "dt": dt, "rates": rates})
+    return Problem(F, Q, H, R, m0, P0, y, 20, x, "chain4", {"K": K, "dt": dt, "rates": rates})
 
 
-def config3(seed: int = 0, n_slow: int = 100_000, keep_states: bool = False) -> Problem:
+def network8(seed: int = 0, n_slow: int = 100_000, keep_states: bool = False) -> Problem:
     """8-state stable network K = -(D+S): D diag log-U[.01,2], S 20%-dense N(0,1)
     scaled so ||S||_2 <= 0.5 min(D) (then K+K^T < 0).  l=50, H (3x8) iid N(0,1),
     Q=1e-4 I, R=.01 I, dt=.05, m0=e1, P0=.1 I."""
@@ -188,10 +188,10 @@ def config3(seed: int = 0, n_slow: int = 100_000, keep_states: bool = False) -> 
     m0 = np.eye(n)[0]
     P0 = 0.1 * np.eye(n)
     y, x = simulate(rng, F, Q, H, R, m0, P0, 50, n_slow, keep_states)
-    return Problem(F, Q, H, R, m0, P0, y, 50, x, "cfg3", {"K": K, "dt": dt})
+    return Problem(F, Q, H, R, m0, P0, y, 50, x, "network8", {"K": K, "dt": dt})
 
 
-def _config4_one(seed: int, s: int, n_min: int, n_max: int, ratios, keep_states: bool) -> Problem:
+def _ragged_one(seed: int, s: int, n_min: int, n_max: int, ratios, keep_states: bool) -> Problem:
     rng = np.random.default_rng([seed, s])
     rates = log_uniform(rng, 0.05, 1.0, 4)
     K = chain_rates_matrix(rates)
@@ -204,17 +204,17 @@ def _config4_one(seed: int, s: int, n_min: int, n_max: int, ratios, keep_states:
     l = int(rng.choice(ratios))
     N = int(rng.integers(n_min, n_max + 1))
     y, x = simulate(rng, F, Q, H, R, m0, P0, l, N, keep_states)
-    return Problem(F, Q, H, R, m0, P0, y, l, x, f"cfg4[{s}]", {"K": K})
+    return Problem(F, Q, H, R, m0, P0, y, l, x, f"ragged_chains[{s}]", {"K": K})
 
 
-def _config4_chunk(args):
+def _ragged_chunk(args):
     seed, lo, hi, n_min, n_max, ratios, keep_states = args
-    return [_config4_one(seed, s, n_min, n_max, ratios, keep_states) for s in range(lo, hi)]
+    return [_ragged_one(seed, s, n_min, n_max, ratios, keep_states) for s in range(lo, hi)]
 
 
-def config4(seed: int = 0, n_seq: int = 4096, n_min: int = 100, n_max: int = 20_000,
+def ragged_chains(seed: int = 0, n_seq: int = 4096, n_min: int = 100, n_max: int = 20_000,
             ratios=(5, 10, 20), keep_states: bool = False, workers: int = 1) -> list[Problem]:
-    """Ragged batch: per sequence a 4-species chain as in config 2 (dt=.05),
+    """Ragged batch: per sequence a 4-species chain as in chain4 (dt=.05),
     ratio drawn from {5,10,20}, n_slow ~ U[n_min, n_max], ny=1 observing
     species 4, Q=1e-3 I, R=.05, m0=e1, P0=.1 I.
 
@@ -224,12 +224,12 @@ def config4(seed: int = 0, n_seq: int = 4096, n_min: int = 100, n_max: int = 20_
     """
     ratios = tuple(int(r) for r in ratios)
     if workers <= 1 or n_seq < 2 * workers:
-        return _config4_chunk((seed, 0, n_seq, n_min, n_max, ratios, keep_states))
+        return _ragged_chunk((seed, 0, n_seq, n_min, n_max, ratios, keep_states))
     import multiprocessing as mp
     bounds = np.linspace(0, n_seq, 4 * workers + 1).astype(int)
     jobs = [(seed, int(a), int(b), n_min, n_max, ratios, keep_states) for a, b in zip(bounds[:-1], bounds[1:]) if b > a]
     with mp.get_context("spawn").Pool(workers) as pool:
-        parts = pool.map(_config4_chunk, jobs)
+        parts = pool.map(_ragged_chunk, jobs)
     return [p for part in parts for p in part]
 
 
@@ -251,7 +251,7 @@ def pack(probs: list[Problem]) -> dict:
     return out
 
 
-def config5(seed: int = 0, n_slow: int = 10_000, keep_states: bool = False) -> Problem:
+def stiff_chain6(seed: int = 0, n_slow: int = 10_000, keep_states: bool = False) -> Problem:
     """Stiff 6-species chain, rates log-U[1e-3,1e2], dt=.01, l=100, observing the
     last two species, Q=1e-6 I, R=1e-3 I, m0=e1, P0=.1 I."""
     rng = np.random.default_rng(seed)
@@ -265,7 +265,7 @@ def config5(seed: int = 0, n_slow: int = 10_000, keep_states: bool = False) -> P
     m0 = np.eye(6)[0]
     P0 = 0.1 * np.eye(6)
     y, x = simulate(rng, F, Q, H, R, m0, P0, 100, n_slow, keep_states)
-    return Problem(F, Q, H, R, m0, P0, y, 100, x, "cfg5", {"K": K, "dt": dt, "rates": rates})
+    return Problem(F, Q, H, R, m0, P0, y, 100, x, "stiff_chain6", {"K": K, "dt": dt, "rates": rates})
 
 
 def random_model(seed: int, nx: int, ny: int, ratio: int, n_slow: int,
@@ -293,4 +293,5 @@ def random_model(seed: int, nx: int, ny: int, ratio: int, n_slow: int,
     return Problem(A, Q, H, R, m0, P0, y, ratio, x, f"rand{nx}x{ny}l{ratio}N{n_slow}u{nu}", B=B, u=u)
 
 
-CONFIGS = {1: config1, 2: config2, 3: config3, 4: config4, 5: config5}
+# single-sequence workloads by name (ragged_chains returns a batch)
+WORKLOADS = {"ab_kinetics": ab_kinetics, "chain4": chain4, "network8": network8, "stiff_chain6": stiff_chain6}

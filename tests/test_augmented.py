@@ -38,9 +38,9 @@ def test_oracle_matches_augmented_state_smoother(oracle_mod, case):
     assert abs(oracle_mod.loglik(prob) - want["loglik"]) <= 1e-9 * max(1.0, abs(want["loglik"]))
 
 
-@pytest.mark.parametrize("cfg,n_slow", [(1, 100), (2, 100)])
-def test_oracle_matches_augmented_state_smoother_configs(oracle_mod, cfg, n_slow):
-    prob = synth.CONFIGS[cfg](seed=4, n_slow=n_slow, keep_states=False)
+@pytest.mark.parametrize("name,n_slow", [("ab_kinetics", 100), ("chain4", 100)])
+def test_oracle_matches_augmented_state_smoother_workloads(oracle_mod, name, n_slow):
+    prob = synth.WORKLOADS[name](seed=4, n_slow=n_slow, keep_states=False)
     want = augmented(prob)
     got = oracle_mod.sequential(prob)
     for k in KEYS:

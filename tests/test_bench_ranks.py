@@ -50,9 +50,9 @@ def test_reduce_over_ranks_single_process():
     assert bench.reduce_over_ranks(2.0, 10, None, "cpu") == (2.0, 10.0)
 
 
-def test_bench_arguments_default_to_one_gpu_config2():
+def test_bench_arguments_default_to_one_gpu_chain4():
     import bench
     a = bench.parse([])
-    assert a.gpus == 1 and a.workload == "config2" and a.warmup >= 3 and a.impl == "ours"
-    b = bench.parse(["--workload", "config4", "--steps", "3"])
-    assert b.workload == "config4" and b.n_seq == 4096 and b.steps == 3
+    assert a.gpus == 1 and a.workload == "chain4" and a.warmup >= 3 and a.impl == "ours"
+    b = bench.parse(["--workload", "ragged_chains", "--steps", "3"])
+    assert b.workload == "ragged_chains" and b.n_seq == 4096 and b.steps == 3

@@ -1,4 +1,4 @@
-"""Config 4 at its full size (4096 ragged sequences, ~4*10^7 slow and ~5*10^8
+"""The ragged batch at its full size (4096 ragged sequences, ~4*10^7 slow and ~5*10^8
 fast steps) in the launch configuration the benchmark times: shapes chosen by
 the autotuner on the first 512 sequences, the batched call captured in a CUDA
 graph and replayed.  Sampled sequences (the shortest, the longest, the first,
@@ -20,11 +20,11 @@ def full_batch():
     import torch
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    probs = synth.config4(seed=0, n_seq=4096, workers=max(1, min(16, os.cpu_count() or 1)))
+    probs = synth.ragged_chains(seed=0, n_seq=4096, workers=max(1, min(16, os.cpu_count() or 1)))
     return probs, synth.pack(probs)
 
 
-def test_config4_full_batch_sampled(oracle_mod, full_batch):
+def test_ragged_chains_full_batch_sampled(oracle_mod, full_batch):
     import torch
 
     import bench
@@ -64,7 +64,7 @@ def test_config4_full_batch_sampled(oracle_mod, full_batch):
                 fs, ff = slice(int(off_s[s]), int(off_s[s + 1])), slice(int(off_f[s]), int(off_f[s + 1]))
                 got = {"fast_mean": outs["fast_mean"][ff].cpu().numpy(), "fast_cov": outs["fast_cov"][ff].cpu().numpy(),
                        "slow_mean": outs["slow_mean"][fs].cpu().numpy(), "slow_cov": outs["slow_cov"][fs].cpu().numpy()}
-                compare(got, refs[s], *TOL[precision], label=f"config4 seq {s} (N={n[s]}, l={pk['ratio'][s]}) {precision}")
+                compare(got, refs[s], *TOL[precision], label=f"ragged_chains seq {s} (N={n[s]}, l={pk['ratio'][s]}) {precision}")
             assert not torch.isnan(outs["slow_cov"]).any()
             del g
     finally:

@@ -2,7 +2,7 @@
 
 Small cases compare every output element by element; they span several scan
 tiles with a ragged tail (scan tiles hold 16-128 slow steps depending on nx).
-Full-size cases (config 2 at 10^4 slow steps, the benchmark's workload and
+Full-size cases (chain4 at 10^4 slow steps, the benchmark's workload and
 launch configuration) compare sampled windows of fast outputs plus every
 slow output against the oracle.  Tolerances: FP64 1e-9 (means) / 1e-8
 (covariances, relative to max |P|); mixed 1e-4 / 1e-3.
@@ -55,14 +55,14 @@ def test_smoother_matches_oracle(oracle_mod, case, precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-@pytest.mark.parametrize("cfg,n_slow", [(1, 100), (2, 257), (5, 40)])
-def test_configs_small_match_oracle(oracle_mod, cfg, n_slow, precision):
-    prob = synth.CONFIGS[cfg](seed=11, n_slow=n_slow, keep_states=False)
+@pytest.mark.parametrize("name,n_slow", [("ab_kinetics", 100), ("chain4", 257), ("stiff_chain6", 40)])
+def test_workloads_small_match_oracle(oracle_mod, name, n_slow, precision):
+    prob = synth.WORKLOADS[name](seed=11, n_slow=n_slow, keep_states=False)
     ref_sm, ref_fi = oracle_views(oracle_mod.sequential(prob), prob.ratio)
     sm, fi = run_smoother(prob, precision)
     tm, tc = TOL[precision]
-    compare(sm, ref_sm, tm, tc, f"cfg{cfg} smoothed {precision}")
-    compare(fi, ref_fi, tm, tc, f"cfg{cfg} filtered {precision}")
+    compare(sm, ref_sm, tm, tc, f"{name} smoothed {precision}")
+    compare(fi, ref_fi, tm, tc, f"{name} filtered {precision}")
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
@@ -80,7 +80,7 @@ def test_filter_call_matches_oracle(oracle_mod, precision):
 
 
 def test_fp32_mode_runs_and_is_close(oracle_mod):
-    prob = synth.config2(seed=2, n_slow=120, keep_states=False)
+    prob = synth.chain4(seed=2, n_slow=120, keep_states=False)
     ref_sm, _ = oracle_views(oracle_mod.sequential(prob), prob.ratio)
     sm, _ = run_smoother(prob, "fp32", filtered=False)
     errs = compare(sm, ref_sm, 1e-2, 1e-1, "fp32")
@@ -88,7 +88,7 @@ def test_fp32_mode_runs_and_is_close(oracle_mod):
 
 
 def test_outputs_exactly_symmetric_and_last_interval(oracle_mod):
-    prob = synth.config2(seed=3, n_slow=50, keep_states=False)
+    prob = synth.chain4(seed=3, n_slow=50, keep_states=False)
     sm, fi = run_smoother(prob, "fp64")
     P = sm["fast_cov"]
     assert np.array_equal(P, np.swapaxes(P, 1, 2))
@@ -98,7 +98,7 @@ def test_outputs_exactly_symmetric_and_last_interval(oracle_mod):
 
 
 def test_repeated_calls_agree_to_rounding():
-    prob = synth.config2(seed=4, n_slow=3000, keep_states=False)
+    prob = synth.chain4(seed=4, n_slow=3000, keep_states=False)
     for precision in ("fp64", "mixed"):
         a, _ = run_smoother(prob, precision, filtered=False)
         b, _ = run_smoother(prob, precision, filtered=False)
@@ -107,13 +107,13 @@ def test_repeated_calls_agree_to_rounding():
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_full_size_config2_sampled(oracle_mod, precision):
-    """Config 2 at its full size (10^4 slow steps, 2*10^5 fast steps) in the
+def test_full_size_chain4_sampled(oracle_mod, precision):
+    """chain4 at its full size (10^4 slow steps, 2*10^5 fast steps) in the
     benchmark's launch configuration (shapes chosen by the autotuner): every
     slow output, and fast outputs of sampled windows (start, two interior
     windows, end)."""
     from paper_2410_00627_gb300 import api
-    prob = synth.config2(seed=0, n_slow=10_000, keep_states=False)
+    prob = synth.chain4(seed=0, n_slow=10_000, keep_states=False)
     l, N = prob.ratio, prob.n_slow
     args = [to_dev(getattr(prob, k)) for k in ("F", "Q", "H", "R", "m0", "P0", "y")]
     try:
@@ -142,8 +142,8 @@ def test_ragged_batch_matches_per_sequence_oracle(oracle_mod):
 
     from paper_2410_00627_gb300 import api
     from tests.gpu_util import to_dev
-    probs = synth.config4(seed=5, n_seq=9, n_min=1, n_max=120)
-    probs[3] = synth.config4(seed=6, n_seq=1, n_min=1, n_max=1)[0]   # a length-1 sequence
+    probs = synth.ragged_chains(seed=5, n_seq=9, n_min=1, n_max=120)
+    probs[3] = synth.ragged_chains(seed=6, n_seq=1, n_min=1, n_max=1)[0]   # a length-1 sequence
     S = len(probs)
     stack = lambda k: to_dev(np.stack([getattr(p, k) for p in probs]))  # noqa: E731
     y = to_dev(np.concatenate([p.y for p in probs]))
@@ -177,7 +177,7 @@ def test_batch_metadata_mismatch_is_reported_not_computed():
 
     from paper_2410_00627_gb300 import api
     from tests.gpu_util import to_dev
-    probs = synth.config4(seed=7, n_seq=3, n_min=5, n_max=9)
+    probs = synth.ragged_chains(seed=7, n_seq=3, n_min=5, n_max=9)
     stack = lambda k: to_dev(np.stack([getattr(p, k) for p in probs]))  # noqa: E731
     y = to_dev(np.concatenate([p.y for p in probs]))
     ratio = torch.tensor([p.ratio for p in probs], dtype=torch.int32, device="cuda")
@@ -216,7 +216,7 @@ def test_host_pointer_rejected():
 
 def test_host_entry_point_matches_device_entry_point():
     from paper_2410_00627_gb300 import api
-    prob = synth.config2(seed=8, n_slow=200, keep_states=False)
+    prob = synth.chain4(seed=8, n_slow=200, keep_states=False)
     dev, _ = run_smoother(prob, "mixed", filtered=False)
     host = api.smoother_host(*[np.ascontiguousarray(getattr(prob, k)) for k in ("F", "Q", "H", "R", "m0", "P0", "y")],
                              prob.ratio, precision="mixed")
@@ -226,7 +226,7 @@ def test_host_entry_point_matches_device_entry_point():
 
 def test_stage_timing_reports_every_stage():
     from paper_2410_00627_gb300 import api
-    prob = synth.config2(seed=9, n_slow=500, keep_states=False)
+    prob = synth.chain4(seed=9, n_slow=500, keep_states=False)
     api.set_stage_timing(True)
     times = {}
     try:
@@ -255,7 +255,7 @@ SHAPES = [  # (scan_groups, scan_elems, recover_threads, lookback_window, setup_
 @pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "g{}e{}t{}w{}s{}r{}".format(*s))
 def test_launch_shapes_do_not_change_results(oracle_mod, shape):
     from paper_2410_00627_gb300 import api
-    prob = synth.config2(seed=5, n_slow=613, keep_states=False)
+    prob = synth.chain4(seed=5, n_slow=613, keep_states=False)
     ref_sm, ref_fi = oracle_views(oracle_mod.sequential(prob), prob.ratio)
     try:
         for precision in ("fp64", "mixed"):
@@ -271,7 +271,7 @@ def test_launch_shapes_do_not_change_results(oracle_mod, shape):
 
 def test_autotune_keeps_a_valid_tuning_and_results_still_match(oracle_mod):
     from paper_2410_00627_gb300 import api
-    prob = synth.config2(seed=6, n_slow=900, keep_states=False)
+    prob = synth.chain4(seed=6, n_slow=900, keep_states=False)
     args = [to_dev(getattr(prob, k)) for k in ("F", "Q", "H", "R", "m0", "P0", "y")]
     try:
         tuned, ms = api.autotune(*args, prob.ratio, precision="mixed", reps=1)
@@ -309,9 +309,9 @@ def test_loglik_matches_oracle(oracle_mod, case, precision):
     assert_same_to_rounding(plain["fast_cov"], sm["fast_cov"], precision, "fast_cov")
 
 
-def test_loglik_full_size_config2_and_filter_call(oracle_mod):
+def test_loglik_full_size_chain4_and_filter_call(oracle_mod):
     from paper_2410_00627_gb300 import api
-    prob = synth.config2(seed=0, n_slow=10_000, keep_states=False)
+    prob = synth.chain4(seed=0, n_slow=10_000, keep_states=False)
     args = [to_dev(getattr(prob, k)) for k in ("F", "Q", "H", "R", "m0", "P0", "y")]
     want = oracle_mod.loglik(prob)
     for precision, tol in (("fp64", 1e-9), ("mixed", 1e-4)):
@@ -325,7 +325,7 @@ def test_loglik_per_sequence_in_a_batch(oracle_mod):
     import torch
 
     from paper_2410_00627_gb300 import api
-    probs = synth.config4(seed=9, n_seq=7, n_min=1, n_max=90)
+    probs = synth.ragged_chains(seed=9, n_seq=7, n_min=1, n_max=90)
     pk = synth.pack(probs)
     t = lambda a: torch.as_tensor(a, device="cuda")  # noqa: E731
     b = api.make_batch(t(pk["F"]), t(pk["Q"]), t(pk["H"]), t(pk["R"]), t(pk["m0"]), t(pk["P0"]), t(pk["y"]),
@@ -339,7 +339,7 @@ def test_loglik_per_sequence_in_a_batch(oracle_mod):
 
 def test_loglik_through_host_entry_point(oracle_mod):
     from paper_2410_00627_gb300 import api
-    prob = synth.config2(seed=8, n_slow=200, keep_states=False)
+    prob = synth.chain4(seed=8, n_slow=200, keep_states=False)
     res = api.smoother_host(*[np.ascontiguousarray(getattr(prob, k)) for k in ("F", "Q", "H", "R", "m0", "P0", "y")],
                             prob.ratio, precision="fp64", loglik=True)
     want = oracle_mod.loglik(prob)
@@ -354,7 +354,7 @@ def test_batch_descriptor_keeps_its_tensors_alive(oracle_mod):
     import torch
 
     from paper_2410_00627_gb300 import api
-    probs = synth.config4(seed=13, n_seq=20, n_min=1, n_max=60)
+    probs = synth.ragged_chains(seed=13, n_seq=20, n_min=1, n_max=60)
     pk = synth.pack(probs)
     t = lambda a: torch.as_tensor(a, device="cuda")  # noqa: E731
     b = api.make_batch(t(pk["F"]), t(pk["Q"]), t(pk["H"]), t(pk["R"]), t(pk["m0"]), t(pk["P0"]), t(pk["y"]),
@@ -379,7 +379,7 @@ def test_host_entry_point_direct_pinned_outputs_match_staged():
     import torch
 
     from paper_2410_00627_gb300 import api
-    prob = synth.config2(seed=21, n_slow=300, keep_states=False)
+    prob = synth.chain4(seed=21, n_slow=300, keep_states=False)
     host_in = [np.ascontiguousarray(getattr(prob, k)) for k in ("F", "Q", "H", "R", "m0", "P0", "y")]
     n_fast, nx = prob.n_slow * prob.ratio, prob.nx
     shapes = {"fast_mean": (n_fast, nx), "fast_cov": (n_fast, nx, nx), "slow_mean": (prob.n_slow, nx),
@@ -408,7 +408,7 @@ def test_host_entry_point_reads_pinned_inputs_directly():
         t.numpy()[...] = a
         return t.numpy()
 
-    for prob in (synth.config2(seed=22, n_slow=200, keep_states=False), synth.random_model(23, 3, 2, 5, 90, nu=2)):
+    for prob in (synth.chain4(seed=22, n_slow=200, keep_states=False), synth.random_model(23, 3, 2, 5, 90, nu=2)):
         keys = ("F", "Q", "H", "R", "m0", "P0", "y")
         host_in = [pin(np.ascontiguousarray(getattr(prob, k))) for k in keys]
         extra = {} if prob.B is None else {"B": pin(prob.B), "u": pin(prob.u)}
@@ -454,7 +454,7 @@ def test_split_recovery_matches_one_kernel():
     prob = synth.random_model(25, 4, 2, 6, 300, nu=2)
     args = [to_dev(getattr(prob, k)) for k in ("F", "Q", "H", "R", "m0", "P0", "y")]
     ctl = {"B": to_dev(prob.B), "u": to_dev(prob.u)}
-    probs = synth.config4(seed=14, n_seq=12, n_min=1, n_max=80)
+    probs = synth.ragged_chains(seed=14, n_seq=12, n_min=1, n_max=80)
     pk = synth.pack(probs)
     t = lambda a: torch.as_tensor(a, device="cuda")  # noqa: E731
     b = api.make_batch(t(pk["F"]), t(pk["Q"]), t(pk["H"]), t(pk["R"]), t(pk["m0"]), t(pk["P0"]), t(pk["y"]),
@@ -500,7 +500,7 @@ def test_pinned_host_output_tensors_through_the_device_api():
         assert_same_to_rounding(got[k], want[k], "mixed", k)
     with pytest.raises(TypeError):  # pageable host memory is not accepted
         api.smoother(*args, prob.ratio, out={"slow_mean": torch.empty((prob.n_slow, nx), dtype=torch.float64)})
-    probs = synth.config4(seed=15, n_seq=9, n_min=1, n_max=70)
+    probs = synth.ragged_chains(seed=15, n_seq=9, n_min=1, n_max=70)
     pk = synth.pack(probs)
     t = lambda a: torch.as_tensor(a, device="cuda")  # noqa: E731
     b = api.make_batch(t(pk["F"]), t(pk["Q"]), t(pk["H"]), t(pk["R"]), t(pk["m0"]), t(pk["P0"]), t(pk["y"]),

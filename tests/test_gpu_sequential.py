@@ -62,7 +62,7 @@ def test_sequential_smoother_matches_oracle(oracle_mod, case, precision):
 
 
 def test_sequential_and_scan_agree_to_rounding():
-    prob = synth.config2(seed=3, n_slow=2000, keep_states=False)
+    prob = synth.chain4(seed=3, n_slow=2000, keep_states=False)
     seq, _ = _run(prob, "fp64", "sequential", filtered=False)
     scan, _ = _run(prob, "fp64", "scan", filtered=False)
     compare(seq, scan, 1e-12, 1e-11, "sequential vs scan")
@@ -84,7 +84,7 @@ def test_sequential_ragged_batch_matches_per_sequence_oracle(oracle_mod):
     import torch
 
     from paper_2410_00627_gb300 import api
-    probs = synth.config4(seed=12, n_seq=150, n_min=1, n_max=150)
+    probs = synth.ragged_chains(seed=12, n_seq=150, n_min=1, n_max=150)
     pk = synth.pack(probs)
     t = lambda a: torch.as_tensor(a, device="cuda")  # noqa: E731
     b = api.make_batch(t(pk["F"]), t(pk["Q"]), t(pk["H"]), t(pk["R"]), t(pk["m0"]), t(pk["P0"]), t(pk["y"]),

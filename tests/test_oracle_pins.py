@@ -149,11 +149,11 @@ def test_lifted_constants_from_joint_prior(oracle_mod, seed, nx, ny, l):
     assert np.allclose(lift["Cbar"], Cb, atol=1e-12 * max(1, np.abs(Cb).max()))
 
 
-@pytest.mark.parametrize("cfg", [1, 2])
-def test_slow_filter_reaches_dare(oracle_mod, cfg):
+@pytest.mark.parametrize("name", ["ab_kinetics", "chain4"])
+def test_slow_filter_reaches_dare(oracle_mod, name):
     """The IMKF covariance converges to the DARE solution with cross term
     S = G Q~ M^T:  X = A X A^T + Qbar - (A X C^T + S)(C X C^T + R_x)^{-1}(.)^T."""
-    prob = synth.CONFIGS[cfg](seed=0, n_slow=400, keep_states=False)
+    prob = synth.WORKLOADS[name](seed=0, n_slow=400, keep_states=False)
     lift = oracle_mod.lifted(prob.F, prob.Q, prob.H, prob.ratio)
     X = scipy.linalg.solve_discrete_are(lift["Abar"].T, lift["Cbar"].T, lift["Qbar"],
                                         lift["MQM"] + prob.R, s=lift["GQM"])
@@ -200,10 +200,10 @@ def test_smoother_operator_associative_with_identity(oracle_mod, n):
             assert np.allclose(x[k], a[k], atol=1e-14), k
 
 
-@pytest.mark.parametrize("cfg,n_slow", [(1, 100), (2, 150)])
-def test_parallel_equals_sequential_midsize(oracle_mod, cfg, n_slow):
+@pytest.mark.parametrize("name,n_slow", [("ab_kinetics", 100), ("chain4", 150)])
+def test_parallel_equals_sequential_midsize(oracle_mod, name, n_slow):
     """The paper states the parallel and sequential forms give identical results."""
-    prob = synth.CONFIGS[cfg](seed=3, n_slow=n_slow, keep_states=False)
+    prob = synth.WORKLOADS[name](seed=3, n_slow=n_slow, keep_states=False)
     seq = oracle_mod.sequential(prob, fast=False)
     for order in (0, 1):
         par = oracle_mod.parallel(prob, order=order)
@@ -213,9 +213,9 @@ def test_parallel_equals_sequential_midsize(oracle_mod, cfg, n_slow):
             assert rel_cov(par[k], seq[k]) < 1e-10, (k, order)
 
 
-@pytest.mark.parametrize("cfg", [1, 2])
-def test_invariants(oracle_mod, cfg):
-    prob = synth.CONFIGS[cfg](seed=5, n_slow=60, keep_states=False)
+@pytest.mark.parametrize("name", ["ab_kinetics", "chain4"])
+def test_invariants(oracle_mod, name):
+    prob = synth.WORKLOADS[name](seed=5, n_slow=60, keep_states=False)
     out = oracle_mod.sequential(prob)
     l = prob.ratio
     for key in ["fast_filt_cov", "fast_smooth_cov", "slow_filt_cov", "first_smooth_cov"]:
@@ -236,7 +236,7 @@ def test_invariants(oracle_mod, cfg):
 
 
 def test_sampled_fast_range_matches_full(oracle_mod):
-    prob = synth.config2(seed=7, n_slow=30, keep_states=False)
+    prob = synth.chain4(seed=7, n_slow=30, keep_states=False)
     full = oracle_mod.sequential(prob)
     part = oracle_mod.sequential(prob, k_lo=10, k_hi=13)
     l = prob.ratio

@@ -5,9 +5,9 @@ import scipy.linalg
 from paper_2410_00627_gb300 import synth
 
 
-def test_config1_transition_is_bateman_closed_form():
+def test_ab_kinetics_transition_is_bateman_closed_form():
     """F = expm(K dt) for A->B kinetics has the Bateman closed form."""
-    p = synth.config1(seed=0, n_slow=5)
+    p = synth.ab_kinetics(seed=0, n_slow=5)
     k1, k2, dt = 0.5, 0.2, 0.1
     e1, e2 = np.exp(-k1 * dt), np.exp(-k2 * dt)
     F = np.array([[e1, 0.0], [k1 * (e1 - e2) / (k2 - k1), e2]])
@@ -37,27 +37,27 @@ def test_simulation_matches_stepwise_recursion():
     assert np.allclose(y, p.y, atol=1e-12)
 
 
-def test_config_shapes_and_structure():
-    p2 = synth.config2(seed=0, n_slow=50)
+def test_workload_shapes_and_structure():
+    p2 = synth.chain4(seed=0, n_slow=50)
     assert p2.F.shape == (4, 4) and p2.H.shape == (2, 4) and p2.ratio == 20
     K = p2.meta["K"]
     assert np.allclose(np.triu(K, 1), 0) and np.allclose(np.tril(K, -2), 0)
     assert np.all((p2.meta["rates"] >= 0.05) & (p2.meta["rates"] <= 1.0))
-    p3 = synth.config3(seed=0, n_slow=10)
+    p3 = synth.network8(seed=0, n_slow=10)
     K3 = p3.meta["K"]
     assert np.max(np.linalg.eigvalsh(K3 + K3.T)) < 0
     assert np.max(np.real(np.linalg.eigvals(K3))) < 0
-    p5 = synth.config5(seed=0, n_slow=10)
+    p5 = synth.stiff_chain6(seed=0, n_slow=10)
     assert p5.ratio == 100 and p5.F.shape == (6, 6)
     assert np.allclose(p5.F, scipy.linalg.expm(p5.meta["K"] * 0.01))
-    b = synth.config4(seed=0, n_seq=8, n_min=10, n_max=30)
+    b = synth.ragged_chains(seed=0, n_seq=8, n_min=10, n_max=30)
     assert len(b) == 8 and all(q.ratio in (5, 10, 20) for q in b)
     assert all(10 <= q.n_slow <= 30 for q in b) and all(q.H.shape == (1, 4) for q in b)
 
 
-def test_config4_parallel_build_equals_serial_and_packs():
-    a = synth.config4(seed=3, n_seq=12, n_min=5, n_max=40)
-    b = synth.config4(seed=3, n_seq=12, n_min=5, n_max=40, workers=2)
+def test_ragged_chains_parallel_build_equals_serial_and_packs():
+    a = synth.ragged_chains(seed=3, n_seq=12, n_min=5, n_max=40)
+    b = synth.ragged_chains(seed=3, n_seq=12, n_min=5, n_max=40, workers=2)
     assert len(a) == len(b) == 12
     for p, q in zip(a, b):
         assert p.ratio == q.ratio and np.array_equal(p.y, q.y) and np.array_equal(p.F, q.F)

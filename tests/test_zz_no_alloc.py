@@ -55,7 +55,7 @@ def test_noalloc_matches_smoother_on_two_calls(lib, precision, tol):
     import torch
 
     from paper_2410_00627_gb300 import api
-    prob = synth.config2(seed=31, n_slow=700, keep_states=False)
+    prob = synth.chain4(seed=31, n_slow=700, keep_states=False)
     p, _keep = _device_problem(prob)
     ref, ref_o = _outputs(prob)
     assert lib.srtm_smoother(ctypes.byref(p), precision, ctypes.byref(ref_o), None, None) == 0
@@ -73,7 +73,7 @@ def test_noalloc_matches_smoother_on_two_calls(lib, precision, tol):
 
 def test_noalloc_rejects_problems_beyond_its_scratch(lib):
     from paper_2410_00627_gb300 import api
-    prob = synth.config2(seed=32, n_slow=60_000, keep_states=False)
+    prob = synth.chain4(seed=32, n_slow=60_000, keep_states=False)
     p, _keep = _device_problem(prob)
     out = api.Output(None, None, None, None)
     assert lib.srtm_smoother_noalloc(ctypes.byref(p), 0, ctypes.byref(out), None) == -1
