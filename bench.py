@@ -707,7 +707,7 @@ def oracle_time(prob, seconds):
 def run_cpu_baseline(args, prob):
     v, reps, el = oracle_time(prob, args.cpu_seconds)
     return {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{reps} full passes over the config-2 workload ({prob.n_slow} slow / "
+            "sample": f"{reps} full passes over the chain4 workload ({prob.n_slow} slow / "
                       f"{prob.n_slow * prob.ratio} fast steps) in {el:.1f} s, 1 thread, FP64 C (-O2)"}
 
 
@@ -789,7 +789,7 @@ def report_errors(name, precisions=("fp64", "mixed", "fp32"), n_slow=None, seed=
         sm = {k: v.cpu().numpy() for k, v in sm.items()}
         fi = {k: v.cpu().numpy() for k, v in fi.items()}
         e = {}
-        for name, got, ref in (
+        for key, got, ref in (
                 ("smoothed fast mean", np.concatenate([sm["fast_mean"][:w * l], sm["fast_mean"][-w * l:]]),
                  np.concatenate([head["fast_smooth_mean"], tail["fast_smooth_mean"]])),
                 ("smoothed fast cov", np.concatenate([sm["fast_cov"][:w * l], sm["fast_cov"][-w * l:]]),
@@ -802,7 +802,7 @@ def report_errors(name, precisions=("fp64", "mixed", "fp32"), n_slow=None, seed=
                  np.concatenate([head["fast_filt_cov"], tail["fast_filt_cov"]])),
                 ("filtered slow mean (all k)", fi["slow_mean"], head["slow_filt_mean"]),
                 ("filtered slow cov (all k)", fi["slow_cov"], head["slow_filt_cov"])):
-            e[name] = rel_err(got, ref)
+            e[key] = rel_err(got, ref)
         res[prec] = e
         del sm, fi
         torch.cuda.empty_cache()
