@@ -52,10 +52,11 @@ typedef struct CUstream_st *srtm_stream_t;
 
 typedef enum {
   SRTM_FP64 = 0,  /* everything in float64                                       */
-  SRTM_MIXED = 1, /* scans and filter elements in float32; the (I + D_i J_j)
-                     solves of Eq. 27, the per-interval smoother elements and
-                     solves (Eq. 17, 29), covariance symmetrisation and the
-                     fast-rate recovery in float64                                */
+  SRTM_MIXED = 1, /* both scans and their elements (Eq. 25-26, 29) in float32;
+                     the (I + D_i J_j) solves of Eq. 27, the per-interval
+                     fast-filter blocks and predicted-covariance solve
+                     (Eq. 17, 21), covariance symmetrisation and the fast-rate
+                     recovery in float64                                          */
   SRTM_FP32 = 2   /* everything after the per-model constants in float32          */
 } srtm_precision;
 
@@ -69,7 +70,8 @@ enum {
   SRTM_ERR_META = -7         /* batch metadata inconsistent with declared sizes */
 };
 
-/* One sequence.  All pointers are device pointers to float64.
+/* One sequence.  All pointers are device pointers to float64 (or mapped
+ * pinned host memory, see the conventions above).
  *   F  nx*nx   fast transition (the paper's A)
  *   Q  nx*nx   fast process-noise covariance
  *   H  ny*nx   integrated-measurement matrix (applies to the sum of l states)
@@ -190,14 +192,17 @@ int srtm_selftest_wait(long long polls, srtm_stream_t stream);
  * thread into buf (at most len bytes).  Returns the length of the message.    */
 int srtm_last_error_detail(char *buf, int len);
 
-/* Frees the cached device workspace and staging buffers of every GPU.        */
+/* Frees the cached device workspace, the staging buffers and the library's
+ * second streams and events of every GPU.                                     */
 int srtm_release(void);
 
 /* Tuning of the launch shapes (lane groups per scan block, elements per lane
- * group, recovery block size, look-back depth) for one (nx, precision).  Zero
- * values keep the built-in choice (128/lanes-per-group groups, 4 elements,
- * 128 threads, window 16, setup inside the filter scan, one recovery kernel).  Returns SRTM_ERR_ARG for out-of-range values.
- * The setting is process-wide and applies to the calls issued after it.     */
+ * group, recovery block size, look-back depth, setup placement, recovery
+ * split) for one (nx, precision).  Zero values keep the built-in choice
+ * (128/lanes-per-group groups, 4 elements, 128 threads, window 16, setup
+ * inside the filter scan, one recovery kernel).  Returns SRTM_ERR_ARG for
+ * out-of-range values.  The setting is process-wide and applies to the calls
+ * issued after it.                                                            */
 typedef struct {
   int scan_groups;      /* lane groups per scan block: a power of two such that
                            groups x lanes-per-group (1, 4, 16 or 32 by nx) is
@@ -233,9 +238,9 @@ int srtm_get_tuning(int nx, srtm_precision prec, srtm_tuning *t);
  * Each candidate is run once untimed on `stream`, then captured into a CUDA
  * graph on a private stream and the graph replayed `reps` times (reps >= 1),
  * timed by CUDA events around each replay (device time without host launch
- * cost); its score is the fastest of the reps.  Inputs and `smooth` are as for srtm_smoother (device buffers
- * owned by the caller); `smooth` is overwritten by every run.  The stream is
- * synchronized after each run.  On success *best (if not NULL) receives the
+ * cost); its score is the fastest of the reps.  Inputs and `smooth` are as
+ * for srtm_smoother (device buffers owned by the caller); `smooth` is
+ * overwritten by every run.  The streams are synchronized after each run.  On success *best (if not NULL) receives the
  * chosen tuning and *best_ms (if not NULL) its time in milliseconds.  Errors:
  * those of srtm_smoother and srtm_status (the first failing candidate stops
  * the search and the previous tuning is restored).                          */
@@ -245,12 +250,14 @@ int srtm_autotune(const srtm_problem *p, srtm_precision prec, const srtm_output 
 int srtm_autotune_batch(const srtm_batch *b, srtm_precision prec, const srtm_output *smooth, int reps,
                         srtm_tuning *best, float *best_ms, srtm_stream_t stream);
 
-/* Kernel launches of one call (for reporting): constants, filter scan (which
- * also forms the per-interval smoother elements), smoother scan (smoother
- * calls only) and fast-rate recovery, plus the metadata kernel for batches. */
+/* Kernel launches of a plain call (for reporting): constants, filter scan
+ * (which also forms the per-interval smoother elements), smoother scan
+ * (smoother calls only) and fast-rate recovery, plus the metadata kernel for
+ * batches.                                                                    */
 int srtm_launches_per_call(int smoothing, int batched);
-/* Kernel launches of the last call issued on the current GPU (0 before any);
- * one more than srtm_launches_per_call when the setup runs as its own kernel. */
+/* Kernel launches of the last call issued on the current GPU (0 before any):
+ * srtm_launches_per_call plus one for each of a separate setup kernel, a
+ * split recovery, known inputs and the log likelihood.                        */
 int srtm_last_call_launches(void);
 
 /* Stage timing.  While enabled, every call records CUDA events on its stream
