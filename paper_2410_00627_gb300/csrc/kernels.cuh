@@ -603,8 +603,16 @@ struct FilterOp {
       unsigned char* sl = slots + (size_t)slot * Gm::template slot_bytes<T, TS>();
       TS* sb = (TS*)sl;
       T* sf = FLOAT_ELEMENTS ? (T*)(sl + align16(Gm::SLOT * sizeof(TS))) : nullptr;
-      for (int j = slot; j < count; j += per_round)
-        setup_interval<NX, 0, T, TS>(c, base_row + p0 + j, lane, mask, sb, sf, j == 0 ? prevb : nullptr);
+      // compiled per measurement size, as the separate setup kernel
+      for (int j = slot; j < count; j += per_round) {
+        const TS* pv = j == 0 ? prevb : nullptr;
+        switch (c.ny) {
+          case 1: setup_interval<NX, 1, T, TS>(c, base_row + p0 + j, lane, mask, sb, sf, pv); break;
+          case 2: setup_interval<NX, 2, T, TS>(c, base_row + p0 + j, lane, mask, sb, sf, pv); break;
+          case 3: setup_interval<NX, 3, T, TS>(c, base_row + p0 + j, lane, mask, sb, sf, pv); break;
+          default: setup_interval<NX, 4, T, TS>(c, base_row + p0 + j, lane, mask, sb, sf, pv); break;
+        }
+      }
     }
     __syncthreads();
   }
