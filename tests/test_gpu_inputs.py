@@ -37,6 +37,7 @@ CASES = [  # (seed, nx, ny, ratio, n_slow, nu)
     (28, 7, 1, 3, 33, 2),
     (29, 8, 3, 4, 67, 4),
     (30, 3, 3, 2, 1, 1),
+    (36, 8, 4, 5, 30, 4),   # largest state, measurement and input sizes
 ]
 
 ARGS = ("F", "Q", "H", "R", "m0", "P0", "y")

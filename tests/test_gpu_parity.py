@@ -39,6 +39,8 @@ CASES = [  # (seed, nx, ny, ratio, n_slow)
     (10, 2, 2, 2, 1),
     (11, 4, 1, 5, 2),
     (12, 3, 3, 1, 17),
+    (13, 8, 4, 3, 40),     # largest state and measurement sizes
+    (14, 7, 4, 1, 25),
 ]
 
 

@@ -34,6 +34,7 @@ CASES = [  # (seed, nx, ny, ratio, n_slow, nu)
     (58, 7, 1, 3, 33, 0),
     (59, 8, 3, 4, 67, 4),
     (60, 2, 2, 2, 1, 0),
+    (63, 8, 4, 3, 30, 2),
 ]
 
 
