@@ -1265,7 +1265,7 @@ __host__ __device__ inline size_t recover_smem_bytes(int threads) {
 // caller asked for and keeps the moments in c.rscr.  PHASE 2 runs after the
 // smoother scan: it reads them back, applies the smoothing terms and writes
 // the smoothed outputs.  The arithmetic and its order are those of PHASE 0,
-// so the results are identical.
+// so for the same scan results the outputs are identical.
 template <int NX, int M, class TR, int PHASE>
 __global__ void __launch_bounds__(128, 3) recover_kernel(Ctx c) {
   constexpr int NT = NX * (NX + 1) / 2, NN = NX * NX;
