@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 from paper_2410_00627_gb300 import synth
-from tests.gpu_util import TOL, compare, oracle_views, run_smoother
+from tests.gpu_util import TOL, compare, oracle_views, run_smoother, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -48,3 +48,29 @@ def test_timeout_latch_is_per_read_and_repeatable():
             api.status()
         api.status()
     assert np.isfinite(api.last_call_launches())
+
+
+def test_singular_model_is_reported_and_the_next_call_is_clean(oracle_mod):
+    """No process or measurement noise and an exactly known prior: the
+    measurement covariance R_x = M Q~ M^T + R is zero, the solves meet a zero
+    pivot, the latch reports SRTM_ERR_SINGULAR (the kernels divide by one
+    instead and stay finite), and the next call is unaffected."""
+    from paper_2410_00627_gb300 import api
+    nx, ny, l, N = 2, 1, 3, 20
+    F = np.eye(nx)
+    Q = np.zeros((nx, nx))
+    H = np.array([[1.0, 0.0]])
+    R = np.zeros((ny, ny))
+    m0 = np.zeros(nx)
+    P0 = np.zeros((nx, nx))
+    y = np.zeros((N, ny))
+    args = [to_dev(a) for a in (F, Q, H, R, m0, P0, y)]
+    api.smoother(*args, l, precision="fp64")
+    with pytest.raises(api.SRTMError) as err:
+        api.status()
+    assert err.value.code == -3  # SRTM_ERR_SINGULAR
+    api.status()
+    prob = synth.random_model(72, 2, 1, 3, 30)
+    sm, _ = run_smoother(prob, "fp64")
+    ref_sm, _ = oracle_views(oracle_mod.sequential(prob), prob.ratio)
+    compare(sm, ref_sm, *TOL["fp64"], label="after a singular call")
