@@ -63,6 +63,11 @@ typedef enum {
 enum {
   SRTM_OK = 0,
   SRTM_ERR_ARG = -1,         /* bad size, NULL required pointer, host pointer   */
+  SRTM_ERR_NOT_PSD = -2,     /* Q, R or P0 not a covariance: a non-finite entry,
+                                asymmetric beyond 1e-8 of its largest diagonal
+                                entry, or indefinite beyond a pivot tolerance of
+                                1e-10 * n * that entry (semi-definite Cholesky in
+                                the constants kernel; singular matrices pass)    */
   SRTM_ERR_SINGULAR = -3,    /* a solve met a zero or non-finite pivot          */
   SRTM_ERR_TIMEOUT = -4,     /* a scan look-back wait exceeded its bound        */
   SRTM_ERR_CUDA = -5,        /* a CUDA runtime call failed                      */
@@ -175,7 +180,8 @@ int srtm_smoother_host(const srtm_problem *host_p, srtm_precision prec,
                        const srtm_output *host_smooth, srtm_stream_t stream);
 
 /* Synchronizes `stream`, then returns and clears the device-side error latch of
- * the current GPU: SRTM_OK, SRTM_ERR_TIMEOUT, SRTM_ERR_SINGULAR or SRTM_ERR_META. */
+ * the current GPU: SRTM_OK, SRTM_ERR_META, SRTM_ERR_TIMEOUT, SRTM_ERR_NOT_PSD
+ * or SRTM_ERR_SINGULAR (the first that applies, in that order).               */
 int srtm_status(srtm_stream_t stream);
 
 /* Failure-detection self-test (the paper has no counterpart).  Launches one
@@ -286,7 +292,7 @@ int srtm_stage_times(float *ms, int n);
  * share the array: calls whose work overlaps on the GPU (other streams or
  * threads) race and must be serialized by the caller.  The call waits for its
  * own work and returns the device-side status directly (SRTM_OK,
- * SRTM_ERR_TIMEOUT or SRTM_ERR_SINGULAR).                                       */
+ * SRTM_ERR_TIMEOUT, SRTM_ERR_NOT_PSD or SRTM_ERR_SINGULAR).                      */
 int srtm_smoother_noalloc(const srtm_problem *p, srtm_precision prec, const srtm_output *smooth,
                           srtm_stream_t stream);
 

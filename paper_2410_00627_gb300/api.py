@@ -14,7 +14,7 @@ from ctypes import c_int, c_longlong, c_void_p
 from . import build as _build
 
 PRECISION = {"fp64": 0, "mixed": 1, "fp32": 2}
-ERRORS = {0: "SRTM_OK", -1: "SRTM_ERR_ARG", -3: "SRTM_ERR_SINGULAR", -4: "SRTM_ERR_TIMEOUT",
+ERRORS = {0: "SRTM_OK", -1: "SRTM_ERR_ARG", -2: "SRTM_ERR_NOT_PSD", -3: "SRTM_ERR_SINGULAR", -4: "SRTM_ERR_TIMEOUT",
           -5: "SRTM_ERR_CUDA", -6: "SRTM_ERR_UNSUPPORTED", -7: "SRTM_ERR_META"}
 OUTPUT_KEYS = ("fast_mean", "fast_cov", "slow_mean", "slow_cov")   # the default outputs
 ALL_OUTPUTS = OUTPUT_KEYS + ("loglik",)                               # + log p(y_1:N) per sequence

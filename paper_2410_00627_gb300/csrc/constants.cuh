@@ -102,12 +102,26 @@ struct PreGeom {
 //  6. V_i H^T, G Q~ M^T = V_l H^T, M Q~ M^T = H (sum_i V_i) H^T.
 //  7. R_x, K, C_bar^T R_x^-1, F, D, J and the first element (one IMKF step
 //     from (m0, P0)), independent products on different units.
+// The first blocks of the grid check, one thread per matrix, that every
+// sequence's Q, R and P0 is a covariance (DEVERR_NOT_PSD); they run beside
+// the sequences' blocks and add nothing to their latency.
 template <int NX>
 __global__ void __launch_bounds__(PRE_THREADS) precompute_kernel(Ctx c, int tables_in_smem) {
   using S = PreGeom<NX>;
   constexpr int G = S::G, NU = S::NU, NN = S::NN;
   extern __shared__ __align__(16) double dsm[];
   __shared__ int s_ok;
+  const int check_blocks = (3 * c.n_seq + PRE_THREADS - 1) / PRE_THREADS;
+  if (blockIdx.x < check_blocks) {
+    const long long item = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (item < 3LL * c.n_seq) {
+      const long long q = item / 3;
+      const int which = (int)(item - q * 3), n = which == 1 ? c.ny : NX;
+      const double* a = which == 0 ? c.Q + q * NN : which == 1 ? c.R + q * c.ny * c.ny : c.P0 + q * NN;
+      if (!psd_check<(NX > MY ? NX : MY)>(a, n)) atomicOr(&c.ctr->err, DEVERR_NOT_PSD);
+    }
+    return;
+  }
   if (c.fold_meta) {
     // single sequence (host-validated): this block writes the call metadata
     if (threadIdx.x == 0) {
@@ -132,7 +146,7 @@ __global__ void __launch_bounds__(PRE_THREADS) precompute_kernel(Ctx c, int tabl
   } else if (!c.ctr->call_ok) {
     return;
   }
-  const int s = blockIdx.x;
+  const int s = blockIdx.x - check_blocks;
   const int m = c.ny, l = c.meta.ratio[s];
   const ModelLayout L = c.ml;
   double* md = c.model + (long long)s * L.stride;
@@ -381,7 +395,8 @@ inline void launch_precompute(const Ctx& c, cudaStream_t st) {
     cudaFuncSetAttribute(precompute_kernel<NX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (dev >= 0 && dev < 64) granted[dev] = smem;
   }
-  precompute_kernel<NX><<<c.n_seq, PRE_THREADS, smem, st>>>(c, in_smem);
+  const int check_blocks = (3 * c.n_seq + PRE_THREADS - 1) / PRE_THREADS;
+  precompute_kernel<NX><<<c.n_seq + check_blocks, PRE_THREADS, smem, st>>>(c, in_smem);
 }
 
 }  // namespace srtm

@@ -140,4 +140,47 @@ __device__ __forceinline__ bool small_sym_inverse(const TR (&a)[MY][MY], TR (&in
   return ok;
 }
 
+// Is the n x n row-major matrix a (n <= N) a covariance: every entry finite,
+// symmetric to within 1e-8 of its largest diagonal entry, and positive
+// semi-definite?  The last test is a Cholesky factorisation of the
+// symmetric part with a pivot tolerance (the semi-definite Cholesky of
+// Higham, "Accuracy and Stability of Numerical Algorithms", 2nd ed.,
+// Sec. 10.3): a pivot below -tau fails; a pivot in [-tau, tau] marks a null
+// direction, and since every 2 x 2 principal minor of a PSD matrix is
+// non-negative, the rest of its column must then vanish to within
+// sqrt(tau * s); tau = 1e-10 * n * s, s = max_i a_ii.  One thread.
+template <int N>
+__device__ __noinline__ bool psd_check(const double* a, int n) {
+  double s = 0.0;
+  bool ok = true;
+  for (int i = 0; i < n; ++i) s = fmax(s, fabs(a[i * n + i]));
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      const double v = a[i * n + j];
+      if (!isfinite(v) || fabs(v - a[j * n + i]) > 1e-8 * s) ok = false;
+    }
+  if (!ok) return false;
+  const double tau = 1e-10 * n * s, off = sqrt(tau * s);
+  double L[N][N];
+  for (int j = 0; j < n; ++j) {
+    double d = a[j * n + j];
+    for (int k = 0; k < j; ++k) d = fma(-L[j][k], L[j][k], d);
+    if (d < -tau) return false;
+    const bool null_dir = d <= tau;
+    const double ljj = null_dir ? 0.0 : sqrt(d);
+    L[j][j] = ljj;
+    for (int i = j + 1; i < n; ++i) {
+      double r = 0.5 * (a[i * n + j] + a[j * n + i]);
+      for (int k = 0; k < j; ++k) r = fma(-L[i][k], L[j][k], r);
+      if (null_dir) {
+        if (fabs(r) > off) return false;
+        L[i][j] = 0.0;
+      } else {
+        L[i][j] = r / ljj;
+      }
+    }
+  }
+  return true;
+}
+
 }  // namespace srtm

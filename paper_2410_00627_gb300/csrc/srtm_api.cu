@@ -535,6 +535,7 @@ int srtm_status(srtm_stream_t stream) {
   cudaMemset(perr, 0, sizeof err);
   if (err & DEVERR_META) return fail(SRTM_ERR_META, "batch metadata disagrees with the declared sizes");
   if (err & DEVERR_TIMEOUT) return fail(SRTM_ERR_TIMEOUT, "a scan look-back wait exceeded its bound");
+  if (err & DEVERR_NOT_PSD) return fail(SRTM_ERR_NOT_PSD, "Q, R or P0 is not a covariance matrix");
   return fail(SRTM_ERR_SINGULAR, "a solve met a zero, negative or non-finite pivot");
 }
 
@@ -1019,6 +1020,7 @@ extern "C" int srtm_smoother_noalloc(const srtm_problem* p, srtm_precision prec,
   if (cudaMemcpy(&err, w + L.ctr + offsetof(Counters, err), sizeof err, cudaMemcpyDeviceToHost) != cudaSuccess)
     return fail(SRTM_ERR_CUDA, "reading the device error latch failed");
   if (err & DEVERR_TIMEOUT) return fail(SRTM_ERR_TIMEOUT, "a scan look-back wait exceeded its bound");
+  if (err & DEVERR_NOT_PSD) return fail(SRTM_ERR_NOT_PSD, "Q, R or P0 is not a covariance matrix");
   if (err & DEVERR_SINGULAR) return fail(SRTM_ERR_SINGULAR, "a solve met a zero, negative or non-finite pivot");
   return SRTM_OK;
 }

@@ -11,7 +11,7 @@ namespace srtm {
 constexpr int MAXNX = 8;  // compiled state sizes 1..8
 constexpr int MY = 4;     // measurement sizes 1..4 (padded to 4 in per-interval records)
 
-enum DevErr : unsigned { DEVERR_TIMEOUT = 1u, DEVERR_SINGULAR = 2u, DEVERR_META = 4u };
+enum DevErr : unsigned { DEVERR_TIMEOUT = 1u, DEVERR_SINGULAR = 2u, DEVERR_META = 4u, DEVERR_NOT_PSD = 8u };
 
 // Look-back wait bound: polls with exponential __nanosleep back-off capped at
 // 2 us, so the bound is a few seconds of wall time.

@@ -9,6 +9,8 @@ wrong sign or index, a transposed operand) fails at least one of them:
 * the textbook Kalman filter + RTS smoother when the ratio l is 1 (Sec. III-C
   notes that l=1 is the standard RTS case);
 * the lifted slow-rate constants (Eq. 7-11) read off the joint prior;
+* with no process noise (Q = 0), the filter equals the linear-regression
+  posterior of x_0 on the stacked measurements, pushed through A^t;
 * the discrete algebraic Riccati equation with cross term (scipy) as the
   steady state of the slow filter covariance;
 * associativity and the identity of both operators (Eq. 27, 30);
@@ -321,3 +323,30 @@ def test_zero_inputs_equal_no_inputs(oracle_mod):
     assert oracle_mod.loglik(base) == oracle_mod.loglik(plain)
     # and the inputs matter when they are not zero
     assert rel_mean(oracle_mod.sequential(prob)["fast_smooth_mean"], b["fast_smooth_mean"]) > 1e-3
+
+
+@pytest.mark.parametrize("seed,nx,ny,l,N", [(74, 3, 2, 4, 25), (76, 2, 1, 7, 12)])
+def test_noise_free_dynamics_filter_is_regression_on_x0(oracle_mod, seed, nx, ny, l, N):
+    """With Q = 0 every fast state is A^t x_0, so p(x_{k,i} | y_{1:k}) is the
+    Gaussian linear-regression posterior of x_0 on the stacked y_1..y_k
+    (y_j = H sum_i A^{(j-1)l+i} x_0 + v_j), pushed through A^t.  The fast-rate
+    filter (Eq. 17) and the slow IMKF (Eq. 9-12) must reproduce it."""
+    prob = synth.random_model(seed, nx, ny, l, N)
+    prob.Q = np.zeros((nx, nx))
+    A, H, R = prob.F, prob.H, prob.R
+    o = oracle_mod.sequential(prob)
+    Ap = [np.eye(nx)]
+    for _ in range(N * l):
+        Ap.append(A @ Ap[-1])
+    C = np.vstack([H @ sum(Ap[(j - 1) * l + i] for i in range(1, l + 1)) for j in range(1, N + 1)])
+    for k in range(1, N + 1):
+        Ck, Rk = C[:k * ny], np.kron(np.eye(k), R)
+        S = Ck @ prob.P0 @ Ck.T + Rk
+        G = np.linalg.solve(S, Ck @ prob.P0).T
+        mx = prob.m0 + G @ (prob.y[:k].reshape(-1) - Ck @ prob.m0)
+        Px = prob.P0 - G @ Ck @ prob.P0
+        for i in range(1, l + 1):
+            t = (k - 1) * l + i
+            assert rel_mean(o["fast_filt_mean"][t - 1], Ap[t] @ mx) < 1e-10, (k, i)
+            assert rel_cov(o["fast_filt_cov"][t - 1], Ap[t] @ Px @ Ap[t].T) < 1e-9, (k, i)
+        assert rel_cov(o["slow_filt_cov"][k - 1], Ap[k * l] @ Px @ Ap[k * l].T) < 1e-9, k
