@@ -92,3 +92,11 @@ def test_launch_counts(lib):
     assert lib.srtm_launches_per_call(1, 0) == 4
     assert lib.srtm_launches_per_call(0, 0) == 3
     assert lib.srtm_launches_per_call(1, 1) == 5
+
+
+def test_error_codes_match_header():
+    """Every SRTM_* status the header declares has the same value and name in the binding."""
+    src = open(os.path.join(ROOT, "include", "srtm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    codes = {int(v): k for k, v in re.findall(r"\b(SRTM_(?:OK|ERR_\w+))\s*=\s*(-?\d+)", src)}
+    assert codes == api.ERRORS
