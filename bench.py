@@ -607,21 +607,35 @@ def run_batched_e2e(args, pk, batch, ten, outs, api, torch, stream):
                    "into pinned host memory"}
 
 
-def run_cpu_baseline_batched(args, probs, seconds=None):
-    import oracle
-    oracle.build()
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.machine()
+
+
+def run_cpu_baseline_batched(args, probs, seconds=None, pool=None):
+    """The oracle on every host core: one sequence per task on spawned worker
+    processes (the sequences are independent), the first sequences of the
+    batch in order, about ``seconds`` of wall time."""
+    from oracle.pool import SequencePool
     seconds = args.cpu_seconds if seconds is None else seconds
-    n, t0 = 0, time.perf_counter()
-    used = 0
-    for p in probs:
-        oracle.sequential(p)
-        n += p.n_slow * p.ratio
-        used += 1
-        if time.perf_counter() - t0 >= seconds:
-            break
-    el = time.perf_counter() - t0
-    return {"value": n / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"the first {used} sequences of the batch ({n} fast steps) in {el:.1f} s, 1 thread, FP64 C"}
+    own = pool is None
+    pool = SequencePool() if own else pool
+    try:
+        r = pool.run(probs, seconds)
+    finally:
+        if own:
+            pool.close()
+    return {"value": r["fast_steps"] / r["seconds"], "unit": UNIT, "cores": r["workers"], "kind": "oracle",
+            "sample": f"the first {r['sequences']} sequences of the batch ({r['fast_steps']} fast steps) in "
+                      f"{r['seconds']:.1f} s, one sequence per task on {r['workers']} spawned worker processes "
+                      f"({cpu_model()}), FP64 C"}
 
 
 def recorded_traffic(precision, n_fast, workload="chain4"):
@@ -820,14 +834,16 @@ def run_reference(args):
         oracle.build()
         from paper_2410_00627_gb300 import synth
         pk = synth.pack(probs)
-        vals = [run_cpu_baseline_batched(args, probs, seconds=args.cpu_seconds / 4) for _ in range(args.warmup)]
-        vals = [run_cpu_baseline_batched(args, probs, seconds=args.cpu_seconds / 2) for _ in range(args.steps)]
+        from oracle.pool import SequencePool
+        with SequencePool() as pool:
+            vals = [run_cpu_baseline_batched(args, probs, args.cpu_seconds / 4, pool) for _ in range(args.warmup)]
+            vals = [run_cpu_baseline_batched(args, probs, args.cpu_seconds / 2, pool) for _ in range(args.steps)]
         value = float(np.mean([v["value"] for v in vals]))
         return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded generator)",
                 "config": batched_config(args, pk, "fp64 (CPU oracle)", None),
-                "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "cpu_baseline": {"value": value, "unit": UNIT, "cores": vals[-1]["cores"], "kind": "oracle",
                                  "sample": vals[-1]["sample"]},
                 "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     from paper_2410_00627_gb300 import synth  # noqa: F401
