@@ -148,9 +148,10 @@ __device__ __forceinline__ bool small_sym_inverse(const TR (&a)[MY][MY], TR (&in
 // Sec. 10.3): a pivot below -tau fails; a pivot in [-tau, tau] marks a null
 // direction, and since every 2 x 2 principal minor of a PSD matrix is
 // non-negative, the rest of its column must then vanish to within
-// sqrt(tau * s); tau = 1e-10 * n * s, s = max_i a_ii.  One thread.
+// sqrt(tau * s); tau = 1e-10 * n * s, s = max_i a_ii.  One thread (host-callable
+// too, for the unit test of the classification).
 template <int N>
-__device__ __noinline__ bool psd_check(const double* a, int n) {
+__host__ __device__ __noinline__ bool psd_check(const double* a, int n) {
   double s = 0.0;
   bool ok = true;
   for (int i = 0; i < n; ++i) s = fmax(s, fabs(a[i * n + i]));
