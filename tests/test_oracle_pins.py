@@ -11,6 +11,9 @@ wrong sign or index, a transposed operand) fails at least one of them:
 * the lifted slow-rate constants (Eq. 7-11) read off the joint prior;
 * with no process noise (Q = 0), the filter equals the linear-regression
   posterior of x_0 on the stacked measurements, pushed through A^t;
+* a non-orthogonal change of state and measurement coordinates maps every
+  mean and covariance as it must, and shifts the log likelihood by the
+  Jacobian term -N log |det S|;
 * the discrete algebraic Riccati equation with cross term (scipy) as the
   steady state of the slow filter covariance;
 * associativity and the identity of both operators (Eq. 27, 30);
@@ -350,3 +353,39 @@ def test_noise_free_dynamics_filter_is_regression_on_x0(oracle_mod, seed, nx, ny
             assert rel_mean(o["fast_filt_mean"][t - 1], Ap[t] @ mx) < 1e-10, (k, i)
             assert rel_cov(o["fast_filt_cov"][t - 1], Ap[t] @ Px @ Ap[t].T) < 1e-9, (k, i)
         assert rel_cov(o["slow_filt_cov"][k - 1], Ap[k * l] @ Px @ Ap[k * l].T) < 1e-9, k
+
+
+def _similarity(prob, T, S):
+    """The same model in state coordinates x' = T x and measurement
+    coordinates y' = S y (inputs enter through B' = T B)."""
+    import copy
+    Ti = np.linalg.inv(T)
+    q = copy.copy(prob)
+    q.F, q.Q, q.H = T @ prob.F @ Ti, T @ prob.Q @ T.T, S @ prob.H @ Ti
+    q.R, q.m0, q.P0 = S @ prob.R @ S.T, T @ prob.m0, T @ prob.P0 @ T.T
+    q.y = prob.y @ S.T
+    if getattr(prob, "B", None) is not None:
+        q.B = T @ prob.B
+    return q
+
+
+@pytest.mark.parametrize("seed,nx,ny,l,N,nu", [(81, 4, 2, 5, 60, 0), (82, 3, 3, 7, 40, 2), (83, 6, 1, 3, 50, 1)])
+def test_posterior_transforms_under_a_change_of_coordinates(oracle_mod, seed, nx, ny, l, N, nu):
+    """Filtering and smoothing commute with an invertible, non-orthogonal change
+    of state coordinates T and of measurement coordinates S: every mean maps to
+    T m and every covariance to T P T^T (a misplaced transpose of a
+    non-symmetric factor such as A or H breaks this), and log p(y'_{1:N}) = log p(y_{1:N}) -
+    N log |det S| (the Jacobian of y' = S y)."""
+    prob = synth.random_model(seed, nx, ny, l, N, nu=nu)
+    rng = np.random.default_rng(seed)
+    T = np.eye(nx) + 0.6 * rng.standard_normal((nx, nx))
+    S = np.eye(ny) + 0.6 * rng.standard_normal((ny, ny))
+    assert min(abs(np.linalg.det(T)), abs(np.linalg.det(S))) > 0.05
+    a = oracle_mod.sequential(prob)
+    b = oracle_mod.sequential(_similarity(prob, T, S))
+    for k in ("slow_filt", "first_smooth", "fast_filt", "fast_smooth"):
+        assert rel_mean(b[k + "_mean"], a[k + "_mean"] @ T.T) < 1e-10, k
+        assert rel_cov(b[k + "_cov"], np.einsum("ij,tjk,lk->til", T, a[k + "_cov"], T)) < 1e-10, k
+    la = oracle_mod.loglik(prob)
+    lb = oracle_mod.loglik(_similarity(prob, T, S))
+    assert abs(lb - (la - N * np.log(abs(np.linalg.det(S))))) < 1e-9 * max(1.0, abs(la))
