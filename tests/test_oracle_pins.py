@@ -11,6 +11,8 @@ wrong sign or index, a transposed operand) fails at least one of them:
 * the lifted slow-rate constants (Eq. 7-11) read off the joint prior;
 * with no process noise (Q = 0), the filter equals the linear-regression
   posterior of x_0 on the stacked measurements, pushed through A^t;
+* with uninformative measurements (R = 10^14 I) every filtered and smoothed
+  moment equals the prior marginal of its fast state;
 * a non-orthogonal change of state and measurement coordinates maps every
   mean and covariance as it must, and shifts the log likelihood by the
   Jacobian term -N log |det S|;
@@ -389,3 +391,25 @@ def test_posterior_transforms_under_a_change_of_coordinates(oracle_mod, seed, nx
     la = oracle_mod.loglik(prob)
     lb = oracle_mod.loglik(_similarity(prob, T, S))
     assert abs(lb - (la - N * np.log(abs(np.linalg.det(S))))) < 1e-9 * max(1.0, abs(la))
+
+
+@pytest.mark.parametrize("seed,nx,ny,l,N,nu", [(84, 4, 2, 20, 40, 0), (85, 3, 1, 6, 30, 2)])
+def test_uninformative_measurements_give_the_prior_marginals(oracle_mod, seed, nx, ny, l, N, nu):
+    """With R = 10^14 I the measurements carry no information (relative weight
+    ~1e-13): filtered and smoothed moments of every fast state equal the prior
+    marginals m_t = A m_{t-1} + B u_{t-1}, P_t = A P_{t-1} A^T + Q from (m0, P0)."""
+    prob = synth.random_model(seed, nx, ny, l, N, nu=nu)
+    prob.R = 1e14 * np.eye(ny)
+    o = oracle_mod.sequential(prob)
+    m, P = prob.m0.copy(), prob.P0.copy()
+    pm, pP = [], []
+    for t in range(N * l):
+        m = prob.F @ m + (prob.B @ prob.u[t] if nu else 0.0)
+        P = prob.F @ P @ prob.F.T + prob.Q
+        pm.append(m)
+        pP.append(P)
+    pm, pP = np.array(pm), np.array(pP)
+    for k in ("fast_filt", "fast_smooth"):
+        assert rel_mean(o[k + "_mean"], pm) < 1e-9, k
+        assert rel_cov(o[k + "_cov"], pP) < 1e-9, k
+    assert rel_cov(o["slow_filt_cov"], pP[l - 1::l]) < 1e-9
