@@ -25,9 +25,10 @@
  *     directly over the CPU-GPU link.  Any other host pointer returns
  *     SRTM_ERR_ARG.  The caller owns every input and output buffer.
  *   - Calls are asynchronous on `stream` (NULL = legacy default stream).
- *     Errors found on the device (a look-back wait that exceeded its bound, a
- *     singular solve, inconsistent batch metadata) are latched on the device
- *     and returned by srtm_status(), which synchronizes the stream.
+ *     Errors found on the device (a look-back wait that exceeded its bound,
+ *     Q, R or P0 that is not a covariance, a singular solve, inconsistent
+ *     batch metadata) are latched on the device and returned by
+ *     srtm_status(), which synchronizes the stream.
  *   - The library owns one cached device workspace per GPU.  A call whose
  *     problem needs more workspace than any earlier call allocates it (a
  *     synchronizing cudaMalloc); make one such call before capturing calls

@@ -100,3 +100,17 @@ def test_error_codes_match_header():
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     codes = {int(v): k for k, v in re.findall(r"\b(SRTM_(?:OK|ERR_\w+))\s*=\s*(-?\d+)", src)}
     assert codes == api.ERRORS
+
+
+def test_header_compiles_as_c99_and_links(lib, tmp_path):
+    """A plain C99 program (gcc -pedantic -Werror, no CUDA headers) includes
+    the header, links the library and checks the calls that need no GPU."""
+    import subprocess
+    libdir = os.path.join(ROOT, "paper_2410_00627_gb300")
+    exe = str(tmp_path / "abi_c_check")
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I", os.path.join(ROOT, "include"),
+                    os.path.join(ROOT, "tests", "native", "abi_c_check.c"), "-o", exe, "-L", libdir, "-lsrtm",
+                    "-Wl,-rpath," + libdir], check=True, capture_output=True, text=True)
+    res = subprocess.run([exe], capture_output=True, text=True, timeout=60)
+    assert res.returncode == 0, res.stderr
+    assert res.stdout.strip() == "ok"
