@@ -722,7 +722,7 @@ def run_cpu_baseline(args, prob):
     v, reps, el = oracle_time(prob, args.cpu_seconds)
     return {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{reps} full passes over the chain4 workload ({prob.n_slow} slow / "
-                      f"{prob.n_slow * prob.ratio} fast steps) in {el:.1f} s, 1 thread, FP64 C (-O2)"}
+                      f"{prob.n_slow * prob.ratio} fast steps) in {el:.1f} s, 1 thread ({cpu_model()}), FP64 C (-O2)"}
 
 
 # --------------------------------------------------------------------------- parity of the timed outputs
@@ -865,7 +865,7 @@ def run_reference(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded generator)",
             "config": config_dict(args, prob, "fp64 (CPU oracle)"),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"the whole workload per step, {args.steps} steps, 1 thread"},
+                             "sample": f"the whole workload per step, {args.steps} steps, 1 thread ({cpu_model()})"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
