@@ -1,4 +1,5 @@
-// constants.cuh -- per-model constants (float64), one block per sequence.
+// constants.cuh -- per-model constants (float64), one block per sequence,
+// after the blocks that check that every Q, R and P0 is a covariance.
 //
 // The lifted slow-rate model and the fast-rate blocks (Sec. III-A/B,
 // Eq. 7-12, 14-15) and the constant parts of the parallel IMKF elements
@@ -90,7 +91,8 @@ struct PreGeom {
   __host__ __device__ static size_t tables(int L) { return (size_t)(5 * L + 1) * NN; }
 };
 
-// Per-model constants of one sequence (block = sequence), float64.
+// Per-model constants of one sequence (one block per sequence, after the
+// check blocks), float64.
 //  1. A^i (i <= l) by doubling: round h forms A^{h+t} = A^h A^t, t = 1..h.
 //  2. the terms A^r Q A^{rT} (r < l), one product unit each.
 //  3. per entry, the running sums S_q = sum_{j<=q} A^j and
