@@ -20,7 +20,9 @@ wrong sign or index, a transposed operand) fails at least one of them:
   Jacobian term -N log |det S|;
 * the discrete algebraic Riccati equation with cross term (scipy) as the
   steady state of the slow filter covariance;
-* associativity and the identity of both operators (Eq. 27, 30);
+* associativity and the identity of both operators (Eq. 27, 30), and each
+  operator against what its elements mean (Gaussian conditioning and
+  marginalisation written out in information form);
 * invariants: symmetry, PSD, smoothed == filtered on the last interval
   (E_N = 0, Eq. 29), smoothed covariance <= filtered covariance;
 * a planted mistake (the printed S_k without the transpose) must fail the
@@ -438,3 +440,57 @@ def test_posterior_is_calibrated_against_the_simulated_states(oracle_mod, make):
         assert 0.9 < nees.mean() / p.nx < 1.1, (k, nees.mean() / p.nx)
         mse[k] = np.mean(e ** 2)
     assert mse["fast_smooth"] < mse["fast_filt"]
+
+
+@pytest.mark.parametrize("n", [1, 2, 4, 6])
+def test_filter_operator_is_gaussian_conditioning_and_marginalisation(oracle_mod, n):
+    """Eq. (27) from what an element means: a_k = (F, d, D, eta, J) holds
+    p(x_k | x_{k-1}) = N(F x_{k-1} + d, D) and the likelihood of its
+    measurements as a function of x_{k-1}, exp(-x^T J x / 2 + eta^T x).  For
+    a_i (x_{i-1} -> x_i) then a_j (x_i -> x_j), textbook Gaussian algebra gives
+    p(x_j | x_{i-1}): condition x_i ~ N(F_i x + d_i, D_i) on the factor of a_j
+    (precision D_i^-1 + J_j), push it through F_j and add D_j; and the
+    likelihood of x_{i-1}: a_i's factor times the Gaussian integral over x_i.
+    The combined element must reproduce both for any x_{i-1}."""
+    rng = np.random.default_rng(300 + n)
+    ai, aj = _random_filter_element(rng, n), _random_filter_element(rng, n)
+    ai["D"] = ai["D"] + 0.3 * np.eye(n)   # the information form below inverts D_i: keep it well conditioned
+    c = oracle_mod.filter_op(ai, aj)
+    Di_inv = np.linalg.inv(ai["D"])
+    Lam = Di_inv + aj["J"]
+    Sig = np.linalg.inv(Lam)
+
+    def log_lik(x):   # log of a_i's factor times the integral over x_i, up to a constant
+        m = ai["F"] @ x + ai["d"]
+        h = Di_inv @ m + aj["eta"]
+        return (-0.5 * x @ ai["J"] @ x + ai["eta"] @ x
+                + 0.5 * h @ Sig @ h - 0.5 * m @ Di_inv @ m)
+
+    base = log_lik(np.zeros(n))
+    for _ in range(5):
+        x = rng.standard_normal(n)
+        mu = Sig @ (Di_inv @ (ai["F"] @ x + ai["d"]) + aj["eta"])
+        assert np.allclose(c["F"] @ x + c["d"], aj["F"] @ mu + aj["d"], rtol=1e-10, atol=1e-10)
+        want = -0.5 * x @ c["J"] @ x + c["eta"] @ x
+        assert abs((log_lik(x) - base) - want) < 1e-9 * max(1.0, abs(want))
+    assert np.allclose(c["D"], aj["F"] @ Sig @ aj["F"].T + aj["D"], rtol=1e-10, atol=1e-10)
+
+
+@pytest.mark.parametrize("n", [1, 3, 5])
+def test_smoother_operator_is_backward_conditional_composition(oracle_mod, n):
+    """Eq. (30) from what an element means: a_k = (E, g, S) holds
+    p(x_k | x_{k+1}) = N(E x_{k+1} + g, S).  Composing a_i (x_i | x_j) with
+    a_j (x_j | x_k) by marginalising x_j gives N(E_i (E_j x + g_j) + g_i,
+    E_i S_j E_i^T + S_i), which the combined element must be."""
+    rng = np.random.default_rng(400 + n)
+
+    def el():
+        G = rng.standard_normal((n, n))
+        return {"E": rng.standard_normal((n, n)) * 0.5, "g": rng.standard_normal(n), "S": G @ G.T}
+
+    ai, aj = el(), el()
+    c = oracle_mod.smoother_op(ai, aj)
+    for _ in range(3):
+        x = rng.standard_normal(n)
+        assert np.allclose(c["E"] @ x + c["g"], ai["E"] @ (aj["E"] @ x + aj["g"]) + ai["g"], rtol=1e-12, atol=1e-12)
+    assert np.allclose(c["S"], ai["E"] @ aj["S"] @ ai["E"].T + ai["S"], rtol=1e-12, atol=1e-12)
