@@ -114,3 +114,26 @@ def test_header_compiles_as_c99_and_links(lib, tmp_path):
     res = subprocess.run([exe], capture_output=True, text=True, timeout=60)
     assert res.returncode == 0, res.stderr
     assert res.stdout.strip() == "ok"
+
+
+@pytest.mark.parametrize("nx", range(1, 9))
+def test_built_in_tunings_are_in_their_documented_ranges(lib, nx):
+    lanes = {1: 1, 2: 4}.get(nx, 16 if nx <= 4 else 32)
+    for prec in (0, 1, 2):
+        t = api.Tuning(0, 0, 0, 0, 0, 0)
+        assert lib.srtm_get_tuning(nx, prec, ctypes.byref(t)) == 0
+        g = t.scan_groups
+        assert g & (g - 1) == 0 and 32 <= g * lanes <= 256, (nx, prec, g)
+        assert 1 <= t.scan_elems <= 64 and 32 <= t.recover_threads <= 128 and t.recover_threads % 32 == 0
+        assert 1 <= t.lookback_window <= 32 and t.setup_mode in (1, 2) and t.recover_split in (1, 2)
+        # every documented value of every field is accepted, one at a time, and read back
+        for field, values in (("scan_elems", (1, 64)), ("recover_threads", (32, 128)),
+                              ("lookback_window", (1, 32)), ("setup_mode", (1, 2)), ("recover_split", (1, 2))):
+            for v in values:
+                u = api.Tuning(0, 0, 0, 0, 0, 0)
+                setattr(u, field, v)
+                assert lib.srtm_set_tuning(nx, prec, ctypes.byref(u)) == 0, (nx, prec, field, v)
+                back = api.Tuning(0, 0, 0, 0, 0, 0)
+                assert lib.srtm_get_tuning(nx, prec, ctypes.byref(back)) == 0
+                assert getattr(back, field) == v, (nx, prec, field, v)
+        assert lib.srtm_set_tuning(nx, prec, ctypes.byref(api.Tuning(0, 0, 0, 0, 0, 0))) == 0   # built-in again
