@@ -137,3 +137,16 @@ def test_built_in_tunings_are_in_their_documented_ranges(lib, nx):
                 assert lib.srtm_get_tuning(nx, prec, ctypes.byref(back)) == 0
                 assert getattr(back, field) == v, (nx, prec, field, v)
         assert lib.srtm_set_tuning(nx, prec, ctypes.byref(api.Tuning(0, 0, 0, 0, 0, 0))) == 0   # built-in again
+
+
+@pytest.mark.parametrize("nx", range(1, 9))
+def test_scan_groups_bounds_follow_the_lanes_per_group(lib, nx):
+    """scan_groups x lanes-per-group (1, 4, 16 or 32 by nx) must lie in 32..256."""
+    lanes = {1: 1, 2: 4}.get(nx, 16 if nx <= 4 else 32)
+    lo, hi = max(1, 32 // lanes), 256 // lanes
+    assert lib.srtm_set_tuning(nx, 1, ctypes.byref(api.Tuning(lo, 0, 0))) == 0
+    assert lib.srtm_set_tuning(nx, 1, ctypes.byref(api.Tuning(hi, 0, 0))) == 0
+    assert lib.srtm_set_tuning(nx, 1, ctypes.byref(api.Tuning(hi * 2, 0, 0))) == -1
+    if lo > 1:
+        assert lib.srtm_set_tuning(nx, 1, ctypes.byref(api.Tuning(lo // 2, 0, 0))) == -1
+    assert lib.srtm_set_tuning(nx, 1, ctypes.byref(api.Tuning(0, 0, 0))) == 0
