@@ -150,3 +150,21 @@ def test_scan_groups_bounds_follow_the_lanes_per_group(lib, nx):
     if lo > 1:
         assert lib.srtm_set_tuning(nx, 1, ctypes.byref(api.Tuning(lo // 2, 0, 0))) == -1
     assert lib.srtm_set_tuning(nx, 1, ctypes.byref(api.Tuning(0, 0, 0))) == 0
+
+
+def test_binding_rejects_non_cuda_inputs_before_any_call():
+    """The binding marshals only contiguous CUDA float64 tensors (no CPU
+    fallback): host tensors and numpy arrays are refused before the library
+    is called; an unknown method is refused by name."""
+    import numpy as np
+    import torch
+    F = torch.eye(2, dtype=torch.float64)
+    args = [F, F, torch.ones(1, 2, dtype=torch.float64), torch.ones(1, 1, dtype=torch.float64),
+            torch.zeros(2, dtype=torch.float64), F, torch.zeros(5, 1, dtype=torch.float64)]
+    with pytest.raises(TypeError, match="CUDA float64"):
+        api.smoother(*args, 3)
+    with pytest.raises(TypeError, match="CUDA float64"):
+        api.filter(*[a.numpy() for a in args], 3)
+    with pytest.raises(ValueError, match="method"):
+        api._entry("srtm_smoother", "bogus")
+    assert np.isfinite(api.launches_per_call(True, False))
