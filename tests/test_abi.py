@@ -168,3 +168,13 @@ def test_binding_rejects_non_cuda_inputs_before_any_call():
     with pytest.raises(ValueError, match="method"):
         api._entry("srtm_smoother", "bogus")
     assert np.isfinite(api.launches_per_call(True, False))
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """Without libsrtm.so every call raises: there is no CPU fallback."""
+    monkeypatch.setattr(api, "_lib", None)
+    monkeypatch.setattr(api, "lib_path", lambda: str(tmp_path / "libsrtm.so"))
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        api.load()
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        api.get_tuning(4, "mixed")
