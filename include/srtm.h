@@ -169,6 +169,55 @@ int srtm_filter_batch_sequential(const srtm_batch *b, srtm_precision prec, const
 int srtm_smoother_batch_sequential(const srtm_batch *b, srtm_precision prec, const srtm_output *smooth,
                                    const srtm_output *filt, srtm_stream_t stream);
 
+/* One sequence split over several GPUs (Sec. II: the filter operator of
+ * Eq. (27) and the smoother operator of Eq. (30) are associative, so a scan
+ * over the whole sequence is a scan over each range combined with the
+ * product of the ranges before it (filter) or after it (smoother); Sec. IV:
+ * the span stays logarithmic).  Each GPU holds a contiguous range of slow
+ * steps k = s..e (its y rows in p->y, p->n_slow = e-s+1; F, Q, H, R as for
+ * the whole sequence; known inputs are not supported: p->nu must be 0,
+ * else SRTM_ERR_UNSUPPORTED) and makes, in this order:
+ *   1. srtm_split_filter_aggregate: agg_f = a_s (x) ... (x) a_e (Eq. 25-27);
+ *      the first range (starts_sequence = 1) has a_1 from p->m0, p->P0; the
+ *      others have generic elements only (m0, P0 are read but do not enter).
+ *   2. exchange: gather every range's agg_f; with srtm_split_combine(0, ...)
+ *      over the aggregates of the EARLIER ranges, (d, D) of the product is
+ *      the filtered x_{s-1,l} ~ N(m_in, P_in) (the first range keeps m0, P0).
+ *   3. srtm_split_smoother_aggregate with p->m0, p->P0 = m_in, P_in:
+ *      agg_s = b_s (x) ... (x) b_e (Eq. 29-30), where b_e is the generic
+ *      element unless ends_sequence (then E_e = 0, Eq. 29 with k = N).
+ *   4. exchange: gather every range's agg_s; with srtm_split_combine(1, ...)
+ *      over the aggregates of the LATER ranges, (g, S) of the product is the
+ *      smoothed x_{e+1,1} ~ N(next_mean, next_cov) (the last range has none).
+ *   5. srtm_split_smoother with p->m0, p->P0 = m_in, P_in and next_mean,
+ *      next_cov (NULL for the last range): the range's fast- and slow-rate
+ *      smoothed (and optionally filtered) outputs, rows relative to the range,
+ *      equal to those of the whole sequence's srtm_smoother up to rounding.
+ *      Its loglik output is the range's share of log p(y_{1:N}) (the sum over
+ *      the ranges is the sequence's).
+ * Aggregates are float64 device arrays: a filter element (F, d, D, eta, J)
+ * holds 3 nx^2 + 2 nx values in that order (matrices row-major), a smoother
+ * element (E, g, S) 2 nx^2 + nx.  In the mixed and FP32 modes they carry the
+ * float32 scans' rounding.  The calls are asynchronous on `stream`; errors
+ * are those of srtm_smoother (device errors through srtm_status).  The
+ * exchange itself (an all-gather of 3 nx^2 + 2 nx values per range, then of
+ * 2 nx^2 + nx) is the caller's: NCCL between GPUs, or any transport.        */
+int srtm_split_filter_aggregate(const srtm_problem *p, int starts_sequence, srtm_precision prec, double *agg,
+                                srtm_stream_t stream);
+int srtm_split_smoother_aggregate(const srtm_problem *p, int ends_sequence, srtm_precision prec, double *agg,
+                                  srtm_stream_t stream);
+int srtm_split_smoother(const srtm_problem *p, const double *next_mean, const double *next_cov,
+                        srtm_precision prec, const srtm_output *smooth, const srtm_output *filt,
+                        srtm_stream_t stream);
+/* The float64 product elems[0] (x) elems[1] (x) ... (x) elems[n-1] of n >= 1
+ * filter elements (op 0, Eq. 27) or smoother elements (op 1, Eq. 30), each
+ * laid out as above and stored one after another, written to out (one
+ * element; its symmetric blocks D and J, or S, as the mean of the matrix and
+ * its transpose).  Device pointers; asynchronous on `stream`; a singular
+ * solve is latched for srtm_status().  Errors: SRTM_ERR_ARG,
+ * SRTM_ERR_UNSUPPORTED (nx), SRTM_ERR_CUDA.                                   */
+int srtm_split_combine(int op, int nx, const double *elems, int n, double *out, srtm_stream_t stream);
+
 /* srtm_smoother with HOST buffers (pageable or pinned) for every input and
  * output.  The model arrays (F, Q, H, R, m0, P0, B) are packed into a
  * library-owned pinned buffer and copied to the device in one transfer.  The
@@ -205,9 +254,10 @@ int srtm_release(void);
 
 /* Tuning of the launch shapes (lane groups per scan block, elements per lane
  * group, recovery block size, look-back depth, setup placement, recovery
- * split) for one (nx, precision).  Zero values keep the built-in choice
- * (128/lanes-per-group groups, 4 elements, 128 threads, window 16, setup
- * inside the filter scan, one recovery kernel).  Returns SRTM_ERR_ARG for
+ * split, batch pipelining) for one (nx, precision).  Zero values keep the
+ * built-in choice (128/lanes-per-group groups, 4 elements, 128 threads,
+ * window 16, setup inside the filter scan, one recovery kernel, batches in
+ * one chunk).  Returns SRTM_ERR_ARG for
  * out-of-range values.  The setting is process-wide and applies to the calls
  * issued after it.                                                            */
 typedef struct {
@@ -231,6 +281,17 @@ typedef struct {
                            words of workspace and is used only while that is
                            at most 4 GiB and every output is device memory,
                            else 1 applies)                                   */
+  int batch_chunks;     /* batches (scan method) only: 1 = every stage over the
+                           whole batch; 2..16 = the batch is processed in that
+                           many chunks of whole sequences with nearly equal
+                           fast steps, the fast-rate recovery of chunk q on a
+                           library-owned second stream while the scans of
+                           chunk q+1 run (replaces recover_split)             */
+  int chunk_recover_bps;/* recovery grid of a chunked batch: 0 = one thread per
+                           fast step of the chunk; 1..3 = that many resident
+                           blocks per SM, each thread looping over fast steps */
+  int chunk_scan_bps;   /* scan grid of a chunked batch: 0 = as many blocks per
+                           SM as fit; 1..8 = at most that many per SM        */
 } srtm_tuning;
 int srtm_set_tuning(int nx, srtm_precision prec, const srtm_tuning *t);
 int srtm_get_tuning(int nx, srtm_precision prec, srtm_tuning *t);
@@ -253,7 +314,10 @@ int srtm_get_tuning(int nx, srtm_precision prec, srtm_tuning *t);
  * the search and the previous tuning is restored).                          */
 int srtm_autotune(const srtm_problem *p, srtm_precision prec, const srtm_output *smooth, int reps,
                   srtm_tuning *best, float *best_ms, srtm_stream_t stream);
-/* The same for a batch (srtm_smoother_batch; tuning key (b->nx, prec)).      */
+/* The same for a batch (srtm_smoother_batch; tuning key (b->nx, prec)), whose
+ * search then also tries batch_chunks (1, 2, 4, 8, 16) and, for the best
+ * chunk count above 1, chunk_recover_bps (0..3) and chunk_scan_bps (0, 1, 2,
+ * 4) one at a time.                                                          */
 int srtm_autotune_batch(const srtm_batch *b, srtm_precision prec, const srtm_output *smooth, int reps,
                         srtm_tuning *best, float *best_ms, srtm_stream_t stream);
 
@@ -264,7 +328,8 @@ int srtm_autotune_batch(const srtm_batch *b, srtm_precision prec, const srtm_out
 int srtm_launches_per_call(int smoothing, int batched);
 /* Kernel launches of the last call issued on the current GPU (0 before any):
  * srtm_launches_per_call plus one for each of a separate setup kernel, a
- * split recovery, known inputs and the log likelihood.                        */
+ * split recovery, known inputs and the log likelihood; a batch in C chunks
+ * launches its scans, setup and recovery once per chunk.                      */
 int srtm_last_call_launches(void);
 
 /* Stage timing.  While enabled, every call records CUDA events on its stream
@@ -273,9 +338,25 @@ int srtm_last_call_launches(void);
  * launch order: metadata, model constants, filter scan, interval setup,
  * smoother scan (0 for a filter call), fast-rate recovery (with a split
  * recovery: its smoothing half), then the filtered half of a split recovery
- * (run beside the smoother scan on the second stream; 0 without a split).   */
+ * (run beside the smoother scan on the second stream; 0 without a split).
+ * A batch in chunks reports as "filter scan" the time from the end of the
+ * constants to the end of the last chunk's smoother scan (all chunks' scans,
+ * overlapping the recoveries of the earlier chunks), 0 for the setup and the
+ * smoother scan, and as "recovery" the summed durations of the chunks'
+ * recovery launches (each timed on the second stream; they overlap scans).  */
 int srtm_set_stage_timing(int enable);
 int srtm_stage_times(float *ms, int n);
+
+/* Arithmetic-throughput calibration (the paper has no counterpart; used for
+ * the roofline denominators of the benchmark).  Runs a kernel of independent
+ * FMA chains (8 per thread, a <- a*b + c) on every SM of the current GPU at its
+ * occupancy limit, in float64 (kind 0) or float32 (kind 1), sized so that one
+ * launch lasts about target_ms milliseconds (1..5000), and writes the fastest
+ * of three timed launches (CUDA events on `stream`) to *gflops (GFLOP/s, an
+ * FMA counted as 2 flops) and its duration to *ms (may be NULL).  Allocates a
+ * small output buffer with cudaMallocAsync on `stream` and synchronizes it.
+ * Errors: SRTM_ERR_ARG (kind, target_ms or gflops invalid), SRTM_ERR_CUDA.   */
+int srtm_measure_peak(int kind, float target_ms, double *gflops, float *ms, srtm_stream_t stream);
 
 /* srtm_smoother for callers that must not allocate device memory (the paper
  * has no counterpart; this is a deployment variant).  Such callers include a
@@ -289,11 +370,13 @@ int srtm_stage_times(float *ms, int n);
  * offered).  A problem whose scratch would exceed 32 MiB (for nx=4 in float64
  * about 2*10^4 slow steps) returns SRTM_ERR_ARG with the needed size in
  * srtm_last_error_detail().  The first call on a GPU looks up the array's
- * device address on that GPU (make it before any stream capture).  All calls
- * share the array: calls whose work overlaps on the GPU (other streams or
- * threads) race and must be serialized by the caller.  The call waits for its
- * own work and returns the device-side status directly (SRTM_OK,
- * SRTM_ERR_TIMEOUT, SRTM_ERR_NOT_PSD or SRTM_ERR_SINGULAR).                      */
+ * device address on that GPU (make it before any stream capture); the address
+ * is kept until srtm_release(), after which the next call looks it up again
+ * (so release after resetting the device).  All calls share the array: calls
+ * whose work overlaps on the GPU (other streams or threads) race and must be
+ * serialized by the caller.  The call reads its device-side status on
+ * `stream`, synchronizes that stream (only), and returns the status directly
+ * (SRTM_OK, SRTM_ERR_TIMEOUT, SRTM_ERR_NOT_PSD or SRTM_ERR_SINGULAR).         */
 int srtm_smoother_noalloc(const srtm_problem *p, srtm_precision prec, const srtm_output *smooth,
                           srtm_stream_t stream);
 

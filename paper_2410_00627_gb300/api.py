@@ -25,7 +25,9 @@ SYMBOLS = ("srtm_filter", "srtm_smoother", "srtm_filter_batch", "srtm_smoother_b
            "srtm_set_tuning", "srtm_get_tuning", "srtm_launches_per_call", "srtm_set_stage_timing",
            "srtm_stage_times", "srtm_smoother_noalloc", "srtm_autotune", "srtm_autotune_batch",
            "srtm_last_call_launches", "srtm_filter_sequential", "srtm_smoother_sequential",
-           "srtm_filter_batch_sequential", "srtm_smoother_batch_sequential", "srtm_selftest_wait")
+           "srtm_filter_batch_sequential", "srtm_smoother_batch_sequential", "srtm_selftest_wait",
+           "srtm_measure_peak", "srtm_split_filter_aggregate", "srtm_split_smoother_aggregate",
+           "srtm_split_smoother", "srtm_split_combine")
 METHODS = {"scan": "", "sequential": "_sequential"}  # entry-point suffix per method
 STAGES = ("metadata", "constants", "filter_scan", "interval_setup", "smoother_scan", "recovery",
           "recovery_filtered_half")
@@ -53,7 +55,8 @@ class Batch(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("scan_groups", c_int), ("scan_elems", c_int), ("recover_threads", c_int),
-                ("lookback_window", c_int), ("setup_mode", c_int), ("recover_split", c_int)]
+                ("lookback_window", c_int), ("setup_mode", c_int), ("recover_split", c_int),
+                ("batch_chunks", c_int), ("chunk_recover_bps", c_int), ("chunk_scan_bps", c_int)]
 
 
 class SRTMError(RuntimeError):
@@ -103,6 +106,12 @@ def load():
         "srtm_filter_batch_sequential": [B, c_int, O, c_void_p],
         "srtm_smoother_batch_sequential": [B, c_int, O, O, c_void_p],
         "srtm_selftest_wait": [c_longlong, c_void_p],
+        "srtm_measure_peak": [c_int, ctypes.c_float, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_float),
+                              c_void_p],
+        "srtm_split_filter_aggregate": [P, c_int, c_int, c_void_p, c_void_p],
+        "srtm_split_smoother_aggregate": [P, c_int, c_int, c_void_p, c_void_p],
+        "srtm_split_smoother": [P, c_void_p, c_void_p, c_int, O, O, c_void_p],
+        "srtm_split_combine": [c_int, c_int, c_void_p, c_int, c_void_p, c_void_p],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -309,9 +318,10 @@ def status(stream=None) -> None:
 
 
 def set_tuning(nx: int, precision: str, scan_groups=0, scan_elems=0, recover_threads=0, lookback_window=0,
-               setup_mode=0, recover_split=0):
+               setup_mode=0, recover_split=0, batch_chunks=0, chunk_recover_bps=0, chunk_scan_bps=0):
     _check(load().srtm_set_tuning(nx, PRECISION[precision], ctypes.byref(
-        Tuning(scan_groups, scan_elems, recover_threads, lookback_window, setup_mode, recover_split))))
+        Tuning(scan_groups, scan_elems, recover_threads, lookback_window, setup_mode, recover_split, batch_chunks,
+               chunk_recover_bps, chunk_scan_bps))))
 
 
 def get_tuning(nx: int, precision: str) -> dict:
@@ -360,6 +370,82 @@ def stage_times() -> dict:
     buf = (ctypes.c_float * len(STAGES))()
     _check(load().srtm_stage_times(buf, len(STAGES)))
     return dict(zip(STAGES, list(buf)))
+
+
+def filter_element_size(nx: int) -> int:
+    """Values of a filter element (F, d, D, eta, J) of Eq. 27."""
+    return 3 * nx * nx + 2 * nx
+
+
+def smoother_element_size(nx: int) -> int:
+    """Values of a smoother element (E, g, S) of Eq. 30."""
+    return 2 * nx * nx + nx
+
+
+def split_filter_aggregate(F, Q, H, R, m0, P0, y, ratio, starts_sequence: bool, precision="mixed", stream=None):
+    """srtm_split_filter_aggregate: the filter aggregate of this range of a
+    split sequence (a float64 CUDA tensor of filter_element_size(nx))."""
+    import torch
+    prob = _problem(F, Q, H, R, m0, P0, y, ratio)
+    agg = torch.empty(filter_element_size(prob.nx), dtype=torch.float64, device=y.device)
+    _check(load().srtm_split_filter_aggregate(ctypes.byref(prob), 1 if starts_sequence else 0, PRECISION[precision],
+                                              c_void_p(agg.data_ptr()), _stream_handle(stream)))
+    return agg
+
+
+def split_smoother_aggregate(F, Q, H, R, m_in, P_in, y, ratio, ends_sequence: bool, precision="mixed", stream=None):
+    """srtm_split_smoother_aggregate: the smoother aggregate of this range
+    (prior m_in, P_in = the filtered state before the range)."""
+    import torch
+    prob = _problem(F, Q, H, R, m_in, P_in, y, ratio)
+    agg = torch.empty(smoother_element_size(prob.nx), dtype=torch.float64, device=y.device)
+    _check(load().srtm_split_smoother_aggregate(ctypes.byref(prob), 1 if ends_sequence else 0, PRECISION[precision],
+                                                c_void_p(agg.data_ptr()), _stream_handle(stream)))
+    return agg
+
+
+def split_smoother(F, Q, H, R, m_in, P_in, y, ratio, next_mean=None, next_cov=None, precision="mixed",
+                   outputs=OUTPUT_KEYS, filtered=(), stream=None, out=None, out_filtered=None):
+    """srtm_split_smoother: this range's smoothed (and filtered) outputs, given
+    the filtered state before it and the smoothed x_{e+1,1} after it (None for
+    the range that ends the sequence).  Returns (smoothed, filtered) dicts."""
+    prob = _problem(F, Q, H, R, m_in, P_in, y, ratio)
+    nx = prob.nx
+    pm = pc = None
+    if next_mean is not None:
+        pm, pc = _dev_tensor(next_mean, "next_mean", (nx,)), _dev_tensor(next_cov, "next_cov", (nx, nx))
+    rows_fast, rows_slow = prob.n_slow * prob.ratio, prob.n_slow
+    sm, so = _alloc_outputs(outputs, y.device, rows_fast, rows_slow, nx, out)
+    fi, fo = _alloc_outputs(filtered, y.device, rows_fast, rows_slow, nx, out_filtered)
+    _check(load().srtm_split_smoother(ctypes.byref(prob), pm, pc, PRECISION[precision], ctypes.byref(so),
+                                      ctypes.byref(fo) if filtered else None, _stream_handle(stream)))
+    return sm, fi
+
+
+def split_combine(op: str, elems, stream=None):
+    """srtm_split_combine: the float64 product elems[0] (x) ... (x) elems[n-1]
+    of filter (op "filter", Eq. 27) or smoother (op "smoother", Eq. 30)
+    elements, given as a contiguous CUDA float64 tensor of shape (n, size)."""
+    import torch
+    n, size = elems.shape
+    nx = {filter_element_size(k): k for k in range(1, 9)}.get(size) if op == "filter" else \
+        {smoother_element_size(k): k for k in range(1, 9)}.get(size)
+    if nx is None:
+        raise ValueError(f"element size {size} matches no state size for op {op!r}")
+    _dev_tensor(elems, "elems", (n, size))
+    out = torch.empty(size, dtype=torch.float64, device=elems.device)
+    _check(load().srtm_split_combine({"filter": 0, "smoother": 1}[op], nx, c_void_p(elems.data_ptr()), n,
+                                     c_void_p(out.data_ptr()), _stream_handle(stream)))
+    return out
+
+
+def measure_peak(kind: str = "fp64", target_ms: float = 200.0, stream=None) -> tuple[float, float]:
+    """FMA throughput of the current GPU (srtm_measure_peak): kind "fp64" or
+    "fp32"; returns (GFLOP/s, milliseconds of the fastest timed launch)."""
+    g, ms = ctypes.c_double(), ctypes.c_float()
+    _check(load().srtm_measure_peak({"fp64": 0, "fp32": 1}[kind], float(target_ms), ctypes.byref(g), ctypes.byref(ms),
+                                    _stream_handle(stream)))
+    return float(g.value), float(ms.value)
 
 
 def release() -> None:

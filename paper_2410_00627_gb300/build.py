@@ -18,7 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsrtm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + CSRC, "-I" + INCLUDE]
-SOURCES = ["srtm_api.cu", "meta.cu"] + [f"inst_nx{n}.cu" for n in range(1, 9)]
+SOURCES = ["srtm_api.cu", "meta.cu", "peak.cu"] + [f"inst_nx{n}.cu" for n in range(1, 9)]
 
 
 def _nvcc() -> str:

@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(PRE_THREADS) precompute_kernel(Ctx c, int tabl
     if (threadIdx.x == 0) {
       const int r = c.uniform_ratio, n = c.uniform_nslow;
       c.ctr->epoch = c.ctr->epoch + 1;
-      for (int i = 0; i < 4; ++i) c.ctr->ticket[i] = 0;
+      for (int i = 0; i < 2 * MAXCHUNK; ++i) c.ctr->ticket[i] = 0;
       c.meta.ratio[0] = r;
       c.meta.nslow[0] = n;
       c.meta.off_slow[0] = 0;

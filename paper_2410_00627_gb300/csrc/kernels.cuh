@@ -458,7 +458,7 @@ __device__ void setup_interval(const Ctx& c, long long gi, int lane, unsigned ma
   }
   if (c.smoothing) {
     T* se = (T*)c.selem + gi * SL<NX>::SIZE;
-    const bool last = k >= N - 1;
+    const bool last = k >= N - 1 && !c.split_tail_open;
     if constexpr (sizeof(T) == sizeof(TR)) {
       __syncwarp(mask);  // the record's reads of Pm (P11 reuses it)
       setup_elements<NX, M, TR, double, T>(r, row, mask, m, last, sb + Gm::P, sb + Gm::Pl, sb + Gm::X, sb + Gm::SUl,
@@ -527,10 +527,11 @@ struct FilterOp {
     for (int e = g.lane; e < ES; e += G) x[e] = (e < NX * NX && e / NX == e % NX) ? T(1) : T(0);
   }
   // a_1 = (0, m^f_{1,l}, P^f_{1,l}, 0, 0);  a_k = (F, K y_k, D, C_bar^T R_x^-1 y_k, J), k > 1
+  // (a range of a split sequence that does not start it has only generic elements)
   __device__ static void load(const Grp<G>& g, T* x, const Ctx& c, int s, long long p, int /*N*/) {
     constexpr int NN = NX * NX;
     const double* md = c.model + (long long)s * c.ml.stride;
-    if (p == 0) {
+    if (p == 0 && !c.split_head_generic) {
       for (int e = g.lane; e < ES; e += G) {
         double v = 0.0;
         if (e >= L::d && e < L::d + NX) v = md[c.ml.m1 + (e - L::d)];
@@ -577,6 +578,7 @@ struct FilterOp {
   // by the whole block in rounds of blockDim/SG intervals.  The first
   // interval's predecessor result is the tile's exclusive prefix.
   static constexpr bool HAS_EPILOGUE = true;
+  static constexpr bool EPILOGUE_ALWAYS = false;  // only while the setup runs inside the filter scan
   // Slots: one per interval of the tile, at most one per SG threads.
   __host__ __device__ static int epilogue_slots(int threads, int tile) {
     const int per = threads / SetupGeom<NX>::SG;
@@ -614,6 +616,10 @@ struct FilterOp {
         }
       }
     }
+    __syncthreads();
+    // the records' P^f_{k-1,l} as LDL^T factors, one thread per interval
+    for (int j = threadIdx.x; j < count; j += blockDim.x)
+      ldlt_inplace<NX, TS>((TS*)c.rec + (base_row + p0 + j) * Rec<NX>::SIZE + Rec<NX>::P);
     __syncthreads();
   }
 };
@@ -677,9 +683,21 @@ struct SmootherOp {
   __device__ static const long long* tile_off(const Ctx& c) { return c.meta.tile_off_s; }
   __device__ static long long total_tiles(const Ctx& c) { return c.ctr->total_tiles_s; }
   __device__ static int tile_elems(const Ctx& c) { return c.tile_s; }
-  static constexpr bool HAS_EPILOGUE = false;
+  // After a tile's results are written: the smoothing terms Om of the tile's
+  // intervals as LDL^T factors for the recovery, one thread per interval.
+  static constexpr bool HAS_EPILOGUE = true;
+  static constexpr bool EPILOGUE_ALWAYS = true;
   __host__ __device__ static size_t epilogue_bytes(int, int) { return 0; }
-  __device__ static void epilogue(const Ctx&, int, long long, int, const T*, unsigned char*) {}
+  __device__ static void epilogue(const Ctx& c, int s, long long p0, int count, const T*, unsigned char*) {
+    const int N = c.meta.nslow[s];
+    __syncthreads();  // every lane group's stores of the tile
+    for (int j = threadIdx.x; j < count; j += blockDim.x) {
+      const long long k = N - 1 - (p0 + j);
+      if (k >= 1)
+        ldlt_inplace<NX, TR_>((TR_*)c.sfin + (c.meta.off_slow[s] + k - 1) * SFin<NX>::SIZE + SFin<NX>::Om);
+    }
+    __syncthreads();
+  }
 };
 
 // ===========================================================================
@@ -931,13 +949,19 @@ __global__ void __launch_bounds__(256) scan_kernel(Ctx c, int NG, int E, int W) 
   unsigned char* esm = uni;  // the tile epilogue reuses the scan buffers
 
   const unsigned long long epoch = c.ctr->epoch;
-  const long long total = Op::total_tiles(c);
   const long long* toff = Op::tile_off(c);
+  // tiles of this launch: the whole call, or the sequences of one chunk of a
+  // pipelined batch (tickets counted per chunk)
+  long long t_lo = 0, total = Op::total_tiles(c);
+  if (c.n_chunks > 1) {
+    t_lo = toff[c.meta.chunk_seq[c.chunk]];
+    total = toff[c.meta.chunk_seq[c.chunk + 1]];
+  }
   const int tile_elems = Op::tile_elems(c);
   bool ok = true;
   for (;;) {
     __syncthreads();
-    if (threadIdx.x == 0) *s_tile = (long long)atomicAdd(&c.ctr->ticket[Op::TICKET], 1u);
+    if (threadIdx.x == 0) *s_tile = t_lo + (long long)atomicAdd(&c.ctr->ticket[Op::TICKET + 2 * c.chunk], 1u);
     __syncthreads();
     const long long tile_id = *s_tile;
     if (tile_id >= total) break;
@@ -980,6 +1004,13 @@ __global__ void __launch_bounds__(256) scan_kernel(Ctx c, int NG, int E, int W) 
     }
     // 3. tile prefix
     ok &= lookback<Op>(g, gid, NG, W, c, epoch, tile_id, t, src + (NG - 1) * ES, excl, b2, win, ctl, sc, scs);
+    if (c.reduce_only) {  // only the product of the whole range: the tile holding its last position writes it
+      if (t == (long long)(N - 1) / tile_elems && gid == 0) {
+        ok &= Op::combine(g, b0, excl, src + (NG - 1) * ES, sc, scs, false);
+        for (int e = g.lane; e < ES; e += G) c.agg_out[e] = (double)b0[e];
+      }
+      continue;
+    }
     // 4. results from the exclusive prefixes
     if (cnt > 0) {
       T* st = b0;
@@ -999,7 +1030,7 @@ __global__ void __launch_bounds__(256) scan_kernel(Ctx c, int NG, int E, int W) 
         g.sync();
       }
     }
-    if (Op::HAS_EPILOGUE && !c.setup_separate) {
+    if (Op::HAS_EPILOGUE && (Op::EPILOGUE_ALWAYS || !c.setup_separate)) {
       const long long tp0 = t * tile_elems;
       Op::epilogue(c, s, tp0, (int)min((long long)tile_elems, (long long)N - tp0), excl, esm);
     }
@@ -1013,9 +1044,9 @@ __global__ void __launch_bounds__(256) scan_kernel(Ctx c, int NG, int E, int W) 
 // and the smoothing terms (Om_k, om_k) formed by the smoother scan:
 //   U_i    = A^i X + V_i H^T
 //   m^f_i  = A^i m + U_i kap
-//   P^f_ii = A^i P A^{iT} + Qc_i - (U_i S_y^-1) U_i^T
+//   P^f_ii = A^i P A^{iT} + Qc_i - (U_i S_y^-1) U_i^T     (P = L D L^T: (A^i L) D (A^i L)^T)
 //   P^f_il = A^i (P A^{lT}) + Cov(e_i,e_l) - U_i (S_y^-1 U_l^T)
-//   m^s_i  = m^f_i + P^f_il om,   P^s_ii = P^f_ii + (P^f_il Om) P^f_il^T
+//   m^s_i  = m^f_i + P^f_il om,   P^s_ii = P^f_ii + P^f_il Om P^f_il^T  (Om = L D L^T)
 // which is Eq. (17) and Eq. (21) with G_{k,i} = P^f_{k,i,l} A^T (P^-_{k+1,1})^-1,
 // grouped so that no n x n product is repeated per fast step.  The last
 // interval is smoothed = filtered (E_N = 0).  Covariances are formed on the
@@ -1108,7 +1139,7 @@ __device__ __forceinline__ void recover_filtered(const Ctx& c, const FastIdx& x,
   }
   // P^f_ii (upper triangle)
   {
-    TR US[NX][M], AP[NX][NX];
+    TR US[NX][M], B[NX][NX], BD[NX][NX];
 #pragma unroll
     for (int r = 0; r < NX; ++r)
 #pragma unroll
@@ -1118,14 +1149,17 @@ __device__ __forceinline__ void recover_filtered(const Ctx& c, const FastIdx& x,
         for (int j2 = 0; j2 < M; ++j2) v = fma(U[r][j2], rc[RL::Si + j2 * MY + jj], v);
         US[r][jj] = v;
       }
+    // A^i P A^iT with P = L D L^T (the record's factors): B = A^i L, then
+    // (B D) B^T on the upper triangle
 #pragma unroll
     for (int r = 0; r < NX; ++r)
 #pragma unroll
       for (int q = 0; q < NX; ++q) {
-        TR v = TR(0);
+        TR v = a[r][q];
 #pragma unroll
-        for (int t = 0; t < NX; ++t) v = fma(a[r][t], rc[RL::P + t * NX + q], v);
-        AP[r][q] = v;
+        for (int t = q + 1; t < NX; ++t) v = fma(a[r][t], rc[RL::P + t * NX + q], v);
+        B[r][q] = v;
+        BD[r][q] = v * rc[RL::P + q * NX + q];
       }
     int u = 0;
 #pragma unroll
@@ -1134,7 +1168,7 @@ __device__ __forceinline__ void recover_filtered(const Ctx& c, const FastIdx& x,
       for (int q = r; q < NX; ++q) {
         TR v = (TR)__ldg(Qci + r * NX + q);
 #pragma unroll
-        for (int t = 0; t < NX; ++t) v = fma(AP[r][t], a[q][t], v);
+        for (int t = 0; t < NX; ++t) v = fma(BD[r][t], B[q][t], v);
 #pragma unroll
         for (int jj = 0; jj < M; ++jj) v = fma(-US[r][jj], U[q][jj], v);
         Pf[u++] = v;
@@ -1142,19 +1176,22 @@ __device__ __forceinline__ void recover_filtered(const Ctx& c, const FastIdx& x,
   }
 }
 
-// smoothing update in place: m += P^f_il om, P += (P^f_il Om) P^f_il^T (upper)
+// smoothing update in place: m += P^f_il om, P += P^f_il Om P^f_il^T (upper)
+// with Om = L D L^T given by its factors (L below the diagonal, D on it):
+// B = P^f_il L, then (B D) B^T
 template <int NX, class TR>
 __device__ __forceinline__ void recover_smooth(const TR* Om, const TR* om, TR (&mf)[NX], TR (&Pf)[NX * (NX + 1) / 2],
                                                const TR (&Pfl)[NX][NX]) {
-  TR T1[NX][NX];
+  TR B[NX][NX], BD[NX][NX];
 #pragma unroll
   for (int r = 0; r < NX; ++r)
 #pragma unroll
     for (int q = 0; q < NX; ++q) {
-      TR v = TR(0);
+      TR v = Pfl[r][q];
 #pragma unroll
-      for (int t = 0; t < NX; ++t) v = fma(Pfl[r][t], Om[t * NX + q], v);
-      T1[r][q] = v;
+      for (int t = q + 1; t < NX; ++t) v = fma(Pfl[r][t], Om[t * NX + q], v);
+      B[r][q] = v;
+      BD[r][q] = v * Om[q * NX + q];
     }
   int u = 0;
 #pragma unroll
@@ -1163,7 +1200,7 @@ __device__ __forceinline__ void recover_smooth(const TR* Om, const TR* om, TR (&
     for (int q = r; q < NX; ++q) {
       TR v = Pf[u];
 #pragma unroll
-      for (int t = 0; t < NX; ++t) v = fma(T1[r][t], Pfl[q][t], v);
+      for (int t = 0; t < NX; ++t) v = fma(BD[r][t], B[q][t], v);
       Pf[u++] = v;
     }
 #pragma unroll
@@ -1189,11 +1226,11 @@ struct RecSlab {
   static constexpr int WARP_DOUBLES = 32 * ROW;
 };
 
-// cnt consecutive doubles from shared memory (16-byte aligned) to global
-// memory: as 16-byte stores (the odd last one by lane 0) when dst is 16-byte
+// cnt consecutive doubles from shared memory to global memory: as 16-byte
+// stores (the odd last one by lane 0) when both dst and src are 16-byte
 // aligned, else as 8-byte stores
 __device__ __forceinline__ void warp_copy_out(double* dst, const double* src, int cnt, int lane) {
-  if (reinterpret_cast<uintptr_t>(dst) & 15) {
+  if ((reinterpret_cast<uintptr_t>(dst) | reinterpret_cast<uintptr_t>(src)) & 15) {
     for (int e = lane; e < cnt; e += 32) dst[e] = src[e];
     return;
   }
@@ -1204,8 +1241,10 @@ __device__ __forceinline__ void warp_copy_out(double* dst, const double* src, in
   if ((cnt & 1) && lane == 0) dst[cnt - 1] = src[cnt - 1];
 }
 
+// The warp's 32 rows f0 .. f0+31 (f0 a multiple of 32) go through the slab;
+// rows v0 .. v1-1 of them are this launch's and are written.
 template <int NX, class TR>
-__device__ __forceinline__ void warp_store_fast(double* slab, int lane, long long f0, int nvalid, bool active,
+__device__ __forceinline__ void warp_store_fast(double* slab, int lane, long long f0, int v0, int v1, bool active,
                                                 double* mo, double* co, const TR* mv, const TR* Pu) {
   using SB = RecSlab<NX>;
   constexpr int NN = NX * NX;
@@ -1225,10 +1264,10 @@ __device__ __forceinline__ void warp_store_fast(double* slab, int lane, long lon
       }
   }
   __syncwarp();
-  // the warp's first row is a multiple of 32, so both blocks keep the
-  // alignment of the output base (16-byte stores for aligned outputs)
-  if (mo) warp_copy_out(mo + f0 * NX, slab + SB::MEAN, nvalid * NX, lane);
-  if (co) warp_copy_out(co + f0 * NN, slab + SB::COV, nvalid * NN, lane);
+  // f0 is a multiple of 32, so dst and src offsets have the same parity and a
+  // 16-byte aligned output base gives 16-byte stores
+  if (mo) warp_copy_out(mo + (f0 + v0) * NX, slab + SB::MEAN + v0 * NX, (v1 - v0) * NX, lane);
+  if (co) warp_copy_out(co + (f0 + v0) * NN, slab + SB::COV + v0 * NN, (v1 - v0) * NN, lane);
 }
 
 template <int NX, class TR>
@@ -1272,65 +1311,75 @@ __global__ void __launch_bounds__(128, 3) recover_kernel(Ctx c) {
   using RS = RecScr<NX>;
   extern __shared__ __align__(16) double rslab[];
   if (!c.ctr->call_ok) return;
-  const long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  // fast steps of this launch: the whole call, or one chunk of a pipelined batch
+  long long f_lo = 0, f_hi = c.total_fast;
+  if (c.n_chunks > 1) {
+    f_lo = c.meta.off_fast[c.meta.chunk_seq[c.chunk]];
+    f_hi = c.meta.off_fast[c.meta.chunk_seq[c.chunk + 1]];
+  }
   const int lane = threadIdx.x & 31;
-  const long long f0 = f - lane;  // first fast row of this warp
-  const long long left = c.total_fast - f0;
-  if (left <= 0) return;  // the whole warp is past the end
-  const int nvalid = left < 32 ? (int)left : 32;
-  const bool active = lane < nvalid;
   double* slab = rslab + (size_t)(threadIdx.x >> 5) * RecSlab<NX>::WARP_DOUBLES;
-  FastIdx x;
-  bool last_i = false, smooth_k = false;
-  TR mf[NX], Pf[NT], Pfl[NX][NX];
-  if (active) {
-    x = fast_index(c, f);
-    last_i = x.i == x.l;
-    smooth_k = c.smoothing && (x.k < x.N - 1);
+  const long long grid_warps = ((long long)gridDim.x * blockDim.x) >> 5;
+  // warps take aligned blocks of 32 fast rows (f0 = 32 wb) that meet
+  // [f_lo, f_hi); with a grid of one thread per fast step each warp makes one
+  // trip, a smaller grid loops
+  for (long long wb = (f_lo >> 5) + ((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5); wb * 32 < f_hi;
+       wb += grid_warps) {
+    const long long f0 = wb * 32, f = f0 + lane;
+    const int v0 = (int)max(0LL, f_lo - f0), v1 = (int)min(32LL, f_hi - f0);
+    const bool active = lane >= v0 && lane < v1;
+    FastIdx x;
+    bool last_i = false, smooth_k = false;
+    TR mf[NX], Pf[NT], Pfl[NX][NX];
+    if (active) {
+      x = fast_index(c, f);
+      last_i = x.i == x.l;
+      smooth_k = c.smoothing && (x.k < x.N - 1 || c.split_tail_open);
+      if (PHASE < 2) {
+        recover_filtered<NX, M, TR>(c, x, smooth_k, mf, Pf, Pfl);
+      } else {  // component-major: a warp reads 32 consecutive words per component
+        const TR* src = (const TR*)c.rscr + f;
+        const long long T = c.total_fast;
+#pragma unroll
+        for (int r = 0; r < NX; ++r) mf[r] = src[(RS::mf + r) * T];
+#pragma unroll
+        for (int u = 0; u < NT; ++u) Pf[u] = src[(RS::Pf + u) * T];
+        if (smooth_k)
+#pragma unroll
+          for (int e = 0; e < NN; ++e) Pfl[e / NX][e % NX] = src[(RS::Pfl + e) * T];
+      }
+    }
+    // filtered outputs (the call's outputs for a filter, the optional extras for a smoother)
+    if (!c.smoothing) {
+      warp_store_fast<NX, TR>(slab, lane, f0, v0, v1, active, c.fast_mean, c.fast_cov, mf, Pf);
+      if (active && last_i) store_slow<NX, TR>(x.row, c.slow_mean, c.slow_cov, mf, Pf);
+      continue;
+    }
     if (PHASE < 2) {
-      recover_filtered<NX, M, TR>(c, x, smooth_k, mf, Pf, Pfl);
-    } else {  // component-major: a warp reads 32 consecutive words per component
-      const TR* src = (const TR*)c.rscr + f;
-      const long long T = c.total_fast;
-#pragma unroll
-      for (int r = 0; r < NX; ++r) mf[r] = src[(RS::mf + r) * T];
-#pragma unroll
-      for (int u = 0; u < NT; ++u) Pf[u] = src[(RS::Pf + u) * T];
-      if (smooth_k)
-#pragma unroll
-        for (int e = 0; e < NN; ++e) Pfl[e / NX][e % NX] = src[(RS::Pfl + e) * T];
+      warp_store_fast<NX, TR>(slab, lane, f0, v0, v1, active, c.ffast_mean, c.ffast_cov, mf, Pf);
+      if (active && last_i) store_slow<NX, TR>(x.row, c.fslow_mean, c.fslow_cov, mf, Pf);
     }
-  }
-  // filtered outputs (the call's outputs for a filter, the optional extras for a smoother)
-  if (!c.smoothing) {
-    warp_store_fast<NX, TR>(slab, lane, f0, nvalid, active, c.fast_mean, c.fast_cov, mf, Pf);
+    if (PHASE == 1) {
+      if (active) {  // component-major, as read back
+        TR* dst = (TR*)c.rscr + f;
+        const long long T = c.total_fast;
+#pragma unroll
+        for (int r = 0; r < NX; ++r) dst[(RS::mf + r) * T] = mf[r];
+#pragma unroll
+        for (int u = 0; u < NT; ++u) dst[(RS::Pf + u) * T] = Pf[u];
+        if (smooth_k)
+#pragma unroll
+          for (int e = 0; e < NN; ++e) dst[(RS::Pfl + e) * T] = Pfl[e / NX][e % NX];
+      }
+      continue;
+    }
+    if (active && smooth_k) {
+      const TR* Om = (const TR*)c.sfin + x.row * SFin<NX>::SIZE;
+      recover_smooth<NX, TR>(Om + SFin<NX>::Om, Om + SFin<NX>::om, mf, Pf, Pfl);
+    }
+    warp_store_fast<NX, TR>(slab, lane, f0, v0, v1, active, c.fast_mean, c.fast_cov, mf, Pf);
     if (active && last_i) store_slow<NX, TR>(x.row, c.slow_mean, c.slow_cov, mf, Pf);
-    return;
   }
-  if (PHASE < 2) {
-    warp_store_fast<NX, TR>(slab, lane, f0, nvalid, active, c.ffast_mean, c.ffast_cov, mf, Pf);
-    if (active && last_i) store_slow<NX, TR>(x.row, c.fslow_mean, c.fslow_cov, mf, Pf);
-  }
-  if (PHASE == 1) {
-    if (active) {  // component-major, as read back
-      TR* dst = (TR*)c.rscr + f;
-      const long long T = c.total_fast;
-#pragma unroll
-      for (int r = 0; r < NX; ++r) dst[(RS::mf + r) * T] = mf[r];
-#pragma unroll
-      for (int u = 0; u < NT; ++u) dst[(RS::Pf + u) * T] = Pf[u];
-      if (smooth_k)
-#pragma unroll
-        for (int e = 0; e < NN; ++e) dst[(RS::Pfl + e) * T] = Pfl[e / NX][e % NX];
-    }
-    return;
-  }
-  if (active && smooth_k) {
-    const TR* Om = (const TR*)c.sfin + x.row * SFin<NX>::SIZE;
-    recover_smooth<NX, TR>(Om + SFin<NX>::Om, Om + SFin<NX>::om, mf, Pf, Pfl);
-  }
-  warp_store_fast<NX, TR>(slab, lane, f0, nvalid, active, c.fast_mean, c.fast_cov, mf, Pf);
-  if (active && last_i) store_slow<NX, TR>(x.row, c.slow_mean, c.slow_cov, mf, Pf);
 }
 
 // ===========================================================================
@@ -1402,12 +1451,24 @@ __global__ void __launch_bounds__(128) setup_kernel(Ctx c) {
   extern __shared__ __align__(16) unsigned char ssm[];
   if (!c.ctr->call_ok) return;
   const int lane = threadIdx.x % SG, slot = threadIdx.x / SG, per = blockDim.x / SG;
-  const long long gi = (long long)blockIdx.x * per + slot;
-  if (gi >= c.total_slow) return;  // the whole lane group leaves together
+  // intervals of this launch: the whole call, or one chunk of a pipelined batch
+  long long g_lo = 0, g_hi = c.total_slow;
+  if (c.n_chunks > 1) {
+    g_lo = c.meta.off_slow[c.meta.chunk_seq[c.chunk]];
+    g_hi = c.meta.off_slow[c.meta.chunk_seq[c.chunk + 1]];
+  }
   const unsigned mask = (SG == 32) ? 0xffffffffu : (((1u << SG) - 1u) << ((threadIdx.x & 31) & ~(SG - 1)));
   unsigned char* sl = ssm + (size_t)slot * Gm::template slot_bytes<T, TS>();
   T* sf = (sizeof(T) != sizeof(TS)) ? (T*)(sl + align16(Gm::SLOT * sizeof(TS))) : nullptr;
-  setup_interval<NX, M, T, TS>(c, gi, lane, mask, (TS*)sl, sf, nullptr);
+  // rounds of `per` intervals, one per lane group (uniform over the block),
+  // then the round's records' P^f_{k-1,l} as LDL^T factors, one thread each
+  for (long long base = g_lo + (long long)blockIdx.x * per; base < g_hi; base += (long long)gridDim.x * per) {
+    if (base + slot < g_hi) setup_interval<NX, M, T, TS>(c, base + slot, lane, mask, (TS*)sl, sf, nullptr);
+    __syncthreads();
+    if (threadIdx.x < per && base + threadIdx.x < g_hi)
+      ldlt_inplace<NX, TS>((TS*)c.rec + (base + threadIdx.x) * Rec<NX>::SIZE + Rec<NX>::P);
+    __syncthreads();
+  }
 }
 
 // ===========================================================================
@@ -1514,6 +1575,99 @@ int query_shapes(srtm_precision prec, int scan_groups, int scan_elems, int windo
   return SRTM_ERR_ARG;
 }
 
+// The last interval of a range of a split sequence that does not end it (one
+// lane group, after the interval setup, before the smoother scan): with the
+// smoothed x_{N,1} = N(next_mean, next_cov) that follows the range (formed
+// from the later ranges' smoother aggregates, Eq. 30),
+//   its smoothing terms Om, om for the recovery (as the smoother scan's result
+//   pass forms them for every other interval), and
+//   its smoother element b_{N-1} <- b_{N-1} (x) (0, next_mean, next_cov), so
+//   that the range's suffix scan yields the smoothed x_{k,1} of the whole
+//   sequence (Sec. II: the operator is associative).
+template <int NX, class T, class TR>
+__global__ void __launch_bounds__(32) split_tail_kernel(Ctx c) {
+  using SOp = SmootherOp<NX, T, TR>;
+  using L = SL<NX>;
+  constexpr int G = SOp::G, ES = SOp::ES, NN = NX * NX;
+  __shared__ T x[ES], b[ES], o[ES], sc[NN];
+  __shared__ TR scs[SOp::SCRS];
+  if (!c.ctr->call_ok || threadIdx.x >= G) return;
+  const Grp<G> g;
+  const long long N = c.total_slow;
+  for (int e = g.lane; e < NN; e += G) {
+    x[L::E + e] = T(0);
+    x[L::S + e] = (T)c.next_cov[e];
+  }
+  for (int e = g.lane; e < NX; e += G) x[L::g + e] = (T)c.next_mean[e];
+  g.sync();
+  SOp::store(g, x, c, 0, -1, (int)N, sc, scs);  // scan position -1 is slow step N: terms of interval N-1
+  if (g.lane == 0) ldlt_inplace<NX, TR>((TR*)c.sfin + (N - 1) * SFin<NX>::SIZE + SFin<NX>::Om);
+  T* el = (T*)c.selem + (N - 1) * ES;
+  for (int e = g.lane; e < ES; e += G) b[e] = el[e];
+  g.sync();
+  g_smoother_combine<NX, G, T>(g, o, b, x, sc, true);  // x is a suffix with E = 0
+  for (int e = g.lane; e < ES; e += G) el[e] = o[e];
+}
+
+template <int NX, class T, class TS>
+inline void launch_setup(const Ctx& c, unsigned grid, size_t smem, cudaStream_t st) {
+  switch (c.ny) {
+    case 1: setup_kernel<NX, 1, T, TS><<<grid, 128, smem, st>>>(c); break;
+    case 2: setup_kernel<NX, 2, T, TS><<<grid, 128, smem, st>>>(c); break;
+    case 3: setup_kernel<NX, 3, T, TS><<<grid, 128, smem, st>>>(c); break;
+    default: setup_kernel<NX, 4, T, TS><<<grid, 128, smem, st>>>(c); break;
+  }
+}
+
+// A batch in chunks of whole sequences (after the metadata, constants and
+// input kernels): on `st` the filter scan, interval setup and smoother scan of
+// chunk q; on the library's second stream the fast-rate recovery of chunk q,
+// which waits for chunk q's scans and runs while `st` goes on with the scans
+// of chunk q+1 (Remark 1: the recovery of an interval needs only that
+// interval's scan results); with staged host outputs, on a third stream the
+// copy of chunk q's rows to the host while the later chunks compute.  The chunks' rows are disjoint, so the launches
+// share the workspace without conflict.  Stage events (optional): ev[1..3]
+// after the last chunk's scans, ev[4] after the last recovery, ev[8+2q] and
+// ev[9+2q] around the recovery of chunk q (on the second stream).
+template <int NX, class T, class TS, class TR>
+int launch_chunks(const Ctx& c, const Shapes& sh, cudaStream_t st, cudaEvent_t* ev, const SideStream* side) {
+  using FOp = FilterOp<NX, T, TS>;
+  using SOp = SmootherOp<NX, T, TR>;
+  constexpr int G = FOp::G;
+  const size_t rsmem = recover_smem_bytes<NX>(sh.recover_threads);
+  for (int q = 0; q < c.n_chunks; ++q) {
+    Ctx cq = c;
+    cq.chunk = q;
+    scan_kernel<FOp><<<sh.grid_f_chunk, sh.scan_groups_f * G, sh.smem_f, st>>>(cq, sh.scan_groups_f, sh.scan_elems_f,
+                                                                             sh.window_f);
+    if (c.setup_separate) launch_setup<NX, T, TS>(cq, (unsigned)sh.grid_setup_chunk, sh.smem_setup, st);
+    if (c.smoothing)
+      scan_kernel<SOp><<<sh.grid_s_chunk, sh.scan_groups_s * G, sh.smem_s, st>>>(cq, sh.scan_groups_s, sh.scan_elems_s,
+                                                                               sh.window_s);
+    cudaEventRecord(side->fork, st);
+    cudaStreamWaitEvent(side->st, side->fork, 0);
+    if (ev) cudaEventRecord(ev[8 + 2 * q], side->st);
+    launch_recover<NX, TR, 0>(cq, (unsigned)sh.grid_recover_chunk, sh.recover_threads, rsmem, side->st);
+    if (ev) cudaEventRecord(ev[9 + 2 * q], side->st);
+    if (c.copy.n) {  // the chunk's staged host outputs, on a third stream beside the next chunks
+      cudaEventRecord(side->cfork, side->st);
+      cudaStreamWaitEvent(side->cst, side->cfork, 0);
+      launch_copy_out(cq, side->cst);
+    }
+  }
+  if (ev)
+    for (int i = 1; i <= 3; ++i) cudaEventRecord(ev[i], st);
+  cudaEventRecord(side->join, side->st);
+  cudaStreamWaitEvent(st, side->join, 0);
+  if (c.copy.n) {
+    cudaEventRecord(side->cjoin, side->cst);
+    cudaStreamWaitEvent(st, side->cjoin, 0);
+  }
+  launch_loglik(c, st);
+  if (ev) cudaEventRecord(ev[4], st);
+  return cudaGetLastError() == cudaSuccess ? SRTM_OK : SRTM_ERR_CUDA;
+}
+
 // ev (optional): five events recorded after the constants, the filter scan,
 // the interval setup, the smoother scan and the recovery; with a split
 // recovery also ev[5] before its smoothing half and ev[6], ev[7] around its
@@ -1526,6 +1680,16 @@ int launch_t(const Ctx& c, const Shapes& sh, cudaStream_t st, cudaEvent_t* ev, c
   launch_precompute<NX>(c, st);
   if (c.uin) input_kernel<NX><<<(unsigned)((c.total_slow + 127) / 128), 128, 0, st>>>(c);
   if (ev) cudaEventRecord(ev[0], st);
+  if ((c.n_chunks > 1 || c.copy.n) && side) return launch_chunks<NX, T, TS, TR>(c, sh, st, ev, side);
+  if (c.split_mode == 1) {  // the filter aggregate of a range of a split sequence: a reducing scan only
+    Ctx cr = c;
+    cr.reduce_only = 1;
+    scan_kernel<FOp><<<sh.grid_f, sh.scan_groups_f * G, sh.smem_f, st>>>(cr, sh.scan_groups_f, sh.scan_elems_f,
+                                                                        sh.window_f);
+    if (ev)
+      for (int i = 1; i <= 4; ++i) cudaEventRecord(ev[i], st);
+    return cudaGetLastError() == cudaSuccess ? SRTM_OK : SRTM_ERR_CUDA;
+  }
   const unsigned seq_blocks = (unsigned)((c.n_seq + SEQ_THREADS - 1) / SEQ_THREADS);
   if (c.sequential) {
     switch (c.ny) {
@@ -1537,15 +1701,19 @@ int launch_t(const Ctx& c, const Shapes& sh, cudaStream_t st, cudaEvent_t* ev, c
   } else
     scan_kernel<FOp><<<sh.grid_f, sh.scan_groups_f * G, sh.smem_f, st>>>(c, sh.scan_groups_f, sh.scan_elems_f, sh.window_f);
   if (ev) cudaEventRecord(ev[1], st);
-  if (c.setup_separate)
-    switch (c.ny) {
-      case 1: setup_kernel<NX, 1, T, TS><<<sh.grid_setup, 128, sh.smem_setup, st>>>(c); break;
-      case 2: setup_kernel<NX, 2, T, TS><<<sh.grid_setup, 128, sh.smem_setup, st>>>(c); break;
-      case 3: setup_kernel<NX, 3, T, TS><<<sh.grid_setup, 128, sh.smem_setup, st>>>(c); break;
-      default: setup_kernel<NX, 4, T, TS><<<sh.grid_setup, 128, sh.smem_setup, st>>>(c); break;
-    }
+  if (c.setup_separate) launch_setup<NX, T, TS>(c, (unsigned)sh.grid_setup, sh.smem_setup, st);
   launch_loglik(c, st);
   if (ev) cudaEventRecord(ev[2], st);  // otherwise the interval setup runs inside the filter scan
+  if (c.split_mode == 2) {  // the smoother aggregate of a range of a split sequence
+    Ctx cr = c;
+    cr.reduce_only = 1;
+    scan_kernel<SOp><<<sh.grid_s, sh.scan_groups_s * G, sh.smem_s, st>>>(cr, sh.scan_groups_s, sh.scan_elems_s,
+                                                                        sh.window_s);
+    if (ev)
+      for (int i = 3; i <= 4; ++i) cudaEventRecord(ev[i], st);
+    return cudaGetLastError() == cudaSuccess ? SRTM_OK : SRTM_ERR_CUDA;
+  }
+  if (c.split_mode == 3 && c.next_mean) split_tail_kernel<NX, T, TR><<<1, SOp::G, 0, st>>>(c);
   const unsigned rblocks = (unsigned)((c.total_fast + sh.recover_threads - 1) / sh.recover_threads);
   const size_t rsmem = recover_smem_bytes<NX>(sh.recover_threads);
   const bool split = c.smoothing && c.recover_split && side;
@@ -1575,6 +1743,54 @@ int launch_t(const Ctx& c, const Shapes& sh, cudaStream_t st, cudaEvent_t* ev, c
   return cudaGetLastError() == cudaSuccess ? SRTM_OK : SRTM_ERR_CUDA;
 }
 
+// Product in float64 of n filter (op 0, Eq. 27) or smoother (op 1, Eq. 30)
+// elements in the paper's order, in[0] (x) in[1] (x) ... (x) in[n-1], by one
+// lane group; the symmetric blocks of the result (D and J, or S) are written
+// as the mean of the matrix and its transpose.  The exchange step of a
+// sequence split over several GPUs: the prefix of the earlier ranges'
+// filter aggregates, the suffix of the later ranges' smoother aggregates.
+template <int NX>
+__global__ void __launch_bounds__(32) split_combine_kernel(int op, const double* in, int n, double* out,
+                                                           Counters* ctr) {
+  using FOp = FilterOp<NX, double, double>;
+  constexpr int G = FOp::G, ESF = FL<NX>::SIZE, ESS = SL<NX>::SIZE, NN = NX * NX;
+  constexpr int ES = ESF > ESS ? ESF : ESS;
+  __shared__ double acc[ES], nxt[ES], el[ES], sc[FOp::SCR], scs[FOp::SCRS];
+  if (threadIdx.x >= G) return;
+  const Grp<G> g;
+  const int es = op == 0 ? ESF : ESS;
+  bool ok = true;
+  for (int e = g.lane; e < es; e += G) acc[e] = in[e];
+  for (int i = 1; i < n; ++i) {
+    g.sync();
+    for (int e = g.lane; e < es; e += G) el[e] = in[(long long)i * es + e];
+    g.sync();
+    if (op == 0) ok &= g_filter_combine<NX, G, double, double>(g, nxt, acc, el, sc, scs, false);
+    else g_smoother_combine<NX, G, double>(g, nxt, acc, el, sc, false);
+    g.sync();
+    for (int e = g.lane; e < es; e += G) acc[e] = nxt[e];
+  }
+  g.sync();
+  for (int e = g.lane; e < es; e += G) {
+    double v = acc[e];
+    const int blk = op == 0 ? ((e >= FL<NX>::D && e < FL<NX>::D + NN) ? FL<NX>::D
+                                                                        : ((e >= FL<NX>::J) ? FL<NX>::J : -1))
+                            : ((e >= SL<NX>::S) ? SL<NX>::S : -1);
+    if (blk >= 0) {
+      const int r = (e - blk) / NX, q = (e - blk) % NX;
+      v = 0.5 * (acc[blk + r * NX + q] + acc[blk + q * NX + r]);
+    }
+    out[e] = v;
+  }
+  if (!ok && g.lane == 0) raise_err(ctr, DEVERR_SINGULAR);
+}
+
+template <int NX>
+int launch_split_combine(int op, const double* in, int n, double* out, Counters* ctr, cudaStream_t st) {
+  split_combine_kernel<NX><<<1, 32, 0, st>>>(op, in, n, out, ctr);
+  return cudaGetLastError() == cudaSuccess ? SRTM_OK : SRTM_ERR_CUDA;
+}
+
 template <int NX>
 int launch_device_path(const Ctx& c, srtm_precision prec, const Shapes& sh, cudaStream_t st, cudaEvent_t* ev,
                        const SideStream* side) {
@@ -1591,4 +1807,5 @@ int launch_device_path(const Ctx& c, srtm_precision prec, const Shapes& sh, cuda
 #define SRTM_INSTANTIATE(NXV)                                                                                \
   template int srtm::launch_device_path<NXV>(const srtm::Ctx&, srtm_precision, const srtm::Shapes&,          \
                                              cudaStream_t, cudaEvent_t*, const srtm::SideStream*);           \
-  template int srtm::query_shapes<NXV>(srtm_precision, int, int, int, int, int, int, long long, int, srtm::Shapes*);
+  template int srtm::query_shapes<NXV>(srtm_precision, int, int, int, int, int, int, long long, int, srtm::Shapes*); \
+  template int srtm::launch_split_combine<NXV>(int, const double*, int, double*, srtm::Counters*, cudaStream_t);

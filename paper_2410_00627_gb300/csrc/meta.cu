@@ -1,6 +1,7 @@
 // meta.cu -- per-call metadata: meta_kernel (one block) validates the batch
-// metadata, forms the row and tile offsets of every sequence, resets the scan
-// tickets and bumps the call epoch that tags the scans' look-back flags.
+// metadata, forms the row and tile offsets of every sequence and the chunks
+// of a pipelined batch, resets the scan tickets and bumps the call epoch that
+// tags the scans' look-back flags.
 #include <cuda_runtime.h>
 
 #include "srtm_internal.cuh"
@@ -15,7 +16,7 @@ __global__ void __launch_bounds__(1024) meta_kernel(Ctx c) {
   if (tid == 0) {
     s_bad = 0;
     c.ctr->epoch = c.ctr->epoch + 1;
-    for (int i = 0; i < 4; ++i) c.ctr->ticket[i] = 0;
+    for (int i = 0; i < 2 * MAXCHUNK; ++i) c.ctr->ticket[i] = 0;
   }
   __syncthreads();
   const int per = (c.n_seq + nt - 1) / nt;
@@ -71,6 +72,29 @@ __global__ void __launch_bounds__(1024) meta_kernel(Ctx c) {
     c.ctr->call_ok = ok ? 1u : 0u;
     if (!ok) atomicOr(&c.ctr->err, DEVERR_META);
   }
+  // chunks of a pipelined batch: chunk q starts at the first sequence whose
+  // fast rows begin at or after q/n_chunks of the batch's fast steps, so that
+  // the chunks hold nearly equal recovery work (empty chunks are allowed)
+  if (c.n_chunks > 1) {
+    __syncthreads();  // the offsets above are visible to the whole block
+    for (int q = tid; q <= c.n_chunks; q += nt) {
+      int first;
+      if (q == 0) {
+        first = 0;
+      } else if (q == c.n_chunks) {
+        first = c.n_seq;
+      } else {
+        const long long want = (c.total_fast * q) / c.n_chunks;
+        int lo = 0, hi = c.n_seq;  // smallest s with off_fast[s] >= want
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if (c.meta.off_fast[mid] >= want) hi = mid; else lo = mid + 1;
+        }
+        first = lo;
+      }
+      c.meta.chunk_seq[q] = first;
+    }
+  }
 }
 
 // Failure-detection self-test: one thread waits, with the bounded polling of
@@ -118,6 +142,48 @@ __global__ void __launch_bounds__(256) loglik_kernel(Ctx c) {
     __syncthreads();
   }
   if (threadIdx.x == 0) c.loglik[s] = part[0];
+}
+
+// Staged host outputs: the rows of the launch's chunk (the whole batch when it
+// is not chunked) from each staging buffer to the caller's pinned host buffer,
+// as consecutive 16-byte stores over the CPU-GPU link (8-byte ones when the two
+// addresses differ in 16-byte alignment).
+__global__ void __launch_bounds__(256) copy_out_kernel(Ctx c) {
+  if (!c.ctr->call_ok) return;
+  const int s_lo = c.n_chunks > 1 ? c.meta.chunk_seq[c.chunk] : 0;
+  const int s_hi = c.n_chunks > 1 ? c.meta.chunk_seq[c.chunk + 1] : c.n_seq;
+  const long long stride = (long long)gridDim.x * blockDim.x, t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  for (int i = 0; i < c.copy.n; ++i) {
+    const long long* off = c.copy.slow[i] ? c.meta.off_slow : c.meta.off_fast;
+    const long long lo = off[s_lo] * c.copy.width[i], hi = off[s_hi] * c.copy.width[i];
+    if (hi <= lo) continue;
+    double* d = c.copy.dst[i];
+    const double* sr = c.copy.src[i];
+    const bool same = (((reinterpret_cast<uintptr_t>(d + lo) ^ reinterpret_cast<uintptr_t>(sr + lo)) & 15) == 0);
+    if (!same) {
+      for (long long e = lo + t0; e < hi; e += stride) d[e] = sr[e];
+      continue;
+    }
+    long long a = lo;
+    if (reinterpret_cast<uintptr_t>(d + a) & 15) {  // one leading element to reach 16-byte alignment
+      if (t0 == 0) d[a] = sr[a];
+      ++a;
+    }
+    const long long pairs = (hi - a) / 2;
+    double2* d2 = reinterpret_cast<double2*>(d + a);
+    const double2* s2 = reinterpret_cast<const double2*>(sr + a);
+    for (long long e = t0; e < pairs; e += stride) d2[e] = __ldcs(s2 + e);
+    if (t0 == 0 && a + 2 * pairs < hi) d[hi - 1] = sr[hi - 1];
+  }
+}
+
+int launch_copy_out(const Ctx& c, cudaStream_t st) {
+  if (c.copy.n == 0) return SRTM_OK;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  copy_out_kernel<<<2 * (sms > 0 ? sms : 1), 256, 0, st>>>(c);
+  return cudaGetLastError() == cudaSuccess ? SRTM_OK : SRTM_ERR_CUDA;
 }
 
 int launch_loglik(const Ctx& c, cudaStream_t st) {

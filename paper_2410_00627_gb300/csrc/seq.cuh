@@ -264,6 +264,7 @@ __global__ void __launch_bounds__(SEQ_THREADS) seq_smoother_kernel(Ctx c) {
         out[SFin<NX>::Om + q * NX + r] = w;
       }
     }
+    ldlt_inplace<NX, TR>(out + SFin<NX>::Om);  // the recovery takes Om as its LDL^T factors
   }
 }
 

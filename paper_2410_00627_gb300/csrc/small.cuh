@@ -7,6 +7,38 @@
 
 namespace srtm {
 
+// In-place unpivoted LDL^T of a symmetric NX x NX matrix held row-major in
+// memory (only the lower triangle and the diagonal are read): afterwards the
+// strictly lower entries hold the unit lower factor L and the diagonal holds
+// D, a = L D L^T; the upper entries are left as they were.  D may have either
+// sign, so no information of a semidefinite matrix is dropped; a zero pivot
+// gives a zero column of L (for a semidefinite matrix that column of a is
+// zero too).  One thread, NX reciprocals.
+template <int NX, class T>
+__device__ __forceinline__ void ldlt_inplace(T* a) {
+#pragma unroll
+  for (int j = 0; j < NX; ++j) {
+    T v[NX > 1 ? NX - 1 : 1];  // v_t = L_jt D_t
+    T d = a[j * NX + j];
+#pragma unroll
+    for (int t = 0; t < j; ++t) {
+      v[t] = a[j * NX + t] * a[t * NX + t];
+      d = fma(-a[j * NX + t], v[t], d);
+    }
+    a[j * NX + j] = d;
+    if (j + 1 < NX) {
+      const T inv = (d != T(0)) ? T(1) / d : T(0);
+#pragma unroll
+      for (int i = j + 1; i < NX; ++i) {
+        T w = a[i * NX + j];
+#pragma unroll
+        for (int t = 0; t < j; ++t) w = fma(-a[i * NX + t], v[t], w);
+        a[i * NX + j] = w * inv;
+      }
+    }
+  }
+}
+
 // inverse of a symmetric positive definite matrix by Cholesky (a = L L^T,
 // a^-1 = L^-T L^-1).  Only the leading nact x nact block is inverted; the
 // rest of inv is set to the identity.  Returns false if a pivot is not

@@ -32,7 +32,8 @@ constexpr int NSTAGE = 6;  // metadata, constants, filter scan, interval setup, 
 // stage-timing events: 0..NSTAGE bound the stages in launch order; with a
 // split recovery NSTAGE+1 marks the start of its smoothing half (main stream)
 // and NSTAGE+2, NSTAGE+3 bound its filtered half (second stream)
-constexpr int NEVENT = NSTAGE + 4;
+// and NSTAGE+4+2q, NSTAGE+5+2q bound the recovery of chunk q of a chunked batch
+constexpr int NEVENT = NSTAGE + 4 + 2 * MAXCHUNK;
 struct DevState {
   void* ws = nullptr;
   size_t ws_bytes = 0;
@@ -44,6 +45,7 @@ struct DevState {
   int sms = 0;
   cudaEvent_t ev[NEVENT] = {};  // stage-timing events (created on first use)
   bool ev_split = false;        // the timed call split its recovery
+  int ev_chunks = 1;            // chunks of the timed call
   cudaStream_t ev_stream = nullptr;
   bool ev_valid = false;
   // placement of the scan tile-state regions used by the previous call
@@ -69,6 +71,9 @@ srtm_tuning effective_tuning(int nx, srtm_precision prec) {
   t.lookback_window = 16;
   t.setup_mode = 1;
   t.recover_split = 1;
+  t.batch_chunks = 1;
+  t.chunk_recover_bps = 0;
+  t.chunk_scan_bps = 0;
   const srtm_tuning& u = g_tune[nx][prec];
   if (u.scan_groups) t.scan_groups = u.scan_groups;
   if (u.scan_elems) t.scan_elems = u.scan_elems;
@@ -76,6 +81,9 @@ srtm_tuning effective_tuning(int nx, srtm_precision prec) {
   if (u.lookback_window) t.lookback_window = u.lookback_window;
   if (u.setup_mode) t.setup_mode = u.setup_mode;
   if (u.recover_split) t.recover_split = u.recover_split;
+  if (u.batch_chunks) t.batch_chunks = u.batch_chunks;
+  if (u.chunk_recover_bps) t.chunk_recover_bps = u.chunk_recover_bps;
+  if (u.chunk_scan_bps) t.chunk_scan_bps = u.chunk_scan_bps;
   return t;
 }
 
@@ -105,8 +113,8 @@ size_t a256(size_t x) { return (x + 255) / 256 * 256; }
 size_t a16(size_t x) { return (x + 15) / 16 * 16; }
 
 struct Layout {
-  size_t ctr, ratio, nslow, off_slow, off_fast, tile_f, tile_s, model, ftile, stile, fout, rec, selem, sfin, lterm,
-      uin, rscr, total;
+  size_t ctr, ratio, nslow, off_slow, off_fast, tile_f, tile_s, chunks, model, ftile, stile, fout, rec, selem, sfin,
+      lterm, uin, rscr, stage, total;
   long long ftile_stride, stile_stride;
   ModelLayout ml;
 };
@@ -117,9 +125,10 @@ size_t split_scratch_bytes(int nx, srtm_precision prec, long long total_fast) {
   return sR * (size_t)(nx + nx * (nx + 1) / 2 + nx * nx) * (size_t)total_fast;
 }
 constexpr size_t SPLIT_SCRATCH_MAX = (size_t)4 << 30;
+constexpr int HOST_CHUNKS = 8;  // chunks of a batch whose outputs are host memory
 
 Layout make_layout(int nx, int ny, int max_ratio, int n_seq, long long total_slow, srtm_precision prec, int tile_f,
-                   int tile_s, int nu, size_t rscr_bytes) {
+                   int tile_s, int nu, size_t rscr_bytes, size_t stage_bytes = 0) {
   Layout L;
   const size_t sT = prec == SRTM_FP64 ? 8 : 4, sR = prec == SRTM_FP32 ? 4 : 8;
   const long long nn = (long long)nx * nx;
@@ -141,6 +150,7 @@ Layout make_layout(int nx, int ny, int max_ratio, int n_seq, long long total_slo
   L.off_fast = take(sizeof(long long) * (n_seq + 1));
   L.tile_f = take(sizeof(long long) * (n_seq + 1));
   L.tile_s = take(sizeof(long long) * (n_seq + 1));
+  L.chunks = take(sizeof(int) * (MAXCHUNK + 1));
   L.model = take(sizeof(double) * (size_t)L.ml.stride * n_seq);
   L.ftile = take((size_t)L.ftile_stride * tiles_f);
   L.stile = take((size_t)L.stile_stride * tiles_s);
@@ -151,6 +161,7 @@ Layout make_layout(int nx, int ny, int max_ratio, int n_seq, long long total_slo
   L.lterm = take(sizeof(double) * (size_t)total_slow);
   L.uin = take(nu > 0 ? sizeof(double) * (size_t)(3 * nx + MY) * total_slow : 0);
   L.rscr = take(rscr_bytes);
+  L.stage = take(stage_bytes);
   L.total = a256(o);
   return L;
 }
@@ -224,10 +235,28 @@ int launch_for(int nx, const Ctx& c, srtm_precision prec, const Shapes& sh, cuda
   return SRTM_ERR_UNSUPPORTED;
 }
 
+// Launch grids of the per-chunk kernels of a pipelined batch.  The host does
+// not know the chunks' sizes (they are formed on the device), so the grids are
+// sized for an even split and the kernels loop over whatever their chunk holds.
+void chunk_grids(const Ctx& c, const srtm_tuning& t, int sms, Shapes* sh) {
+  const int C = c.n_chunks;
+  const int bf = t.chunk_scan_bps > 0 ? std::min(t.chunk_scan_bps, sh->blocks_per_sm_f) : sh->blocks_per_sm_f;
+  const int bs = t.chunk_scan_bps > 0 ? std::min(t.chunk_scan_bps, sh->blocks_per_sm_s) : sh->blocks_per_sm_s;
+  const long long tiles = c.total_slow / ((long long)sh->scan_groups_f * sh->scan_elems_f) / C + c.n_seq / C + 1;
+  sh->grid_f_chunk = (int)std::max(1LL, std::min((long long)bf * sms, tiles));
+  sh->grid_s_chunk = (int)std::max(1LL, std::min((long long)bs * sms, tiles));
+  const int sg = c.nx == 1 ? 1 : (c.nx == 2 ? 2 : (c.nx <= 4 ? 4 : 8)), per = 128 / sg;
+  sh->grid_setup_chunk = (int)std::max(1LL, (c.total_slow / C + per - 1) / per);
+  const long long even = (c.total_fast / C + sh->recover_threads - 1) / sh->recover_threads;
+  sh->grid_recover_chunk =
+      (int)std::max(1LL, t.chunk_recover_bps > 0 ? std::min((long long)t.chunk_recover_bps * sms, even) : even);
+}
+
 // Runs the device path for a fully validated context (sizes in `c` set).
-// host_outputs: some output is pinned host memory written over the CPU-GPU
-// link; the recovery then stays one kernel, so that those slower stores
-// overlap all of its arithmetic instead of only the smoothing half.
+// host_outputs: some output is pinned host memory.  One sequence: the
+// recovery writes it over the CPU-GPU link and stays one kernel, so that those
+// slower stores overlap all of its arithmetic instead of only the smoothing
+// half.  A batch: it is staged in device memory and copied out per chunk.
 int run(Ctx c, srtm_precision prec, cudaStream_t st, bool host_outputs = false) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAXDEV)
@@ -244,10 +273,35 @@ int run(Ctx c, srtm_precision prec, cudaStream_t st, bool host_outputs = false) 
   const int tile_f = sh.scan_groups_f * sh.scan_elems_f, tile_s = sh.scan_groups_s * sh.scan_elems_s;
   // split recovery: smoother calls of the scan path whose moments fit the bound
   const size_t rscr_bytes = split_scratch_bytes(c.nx, prec, c.total_fast);
-  c.recover_split =
-      (t.recover_split == 2 && c.smoothing && !c.sequential && !host_outputs && rscr_bytes <= SPLIT_SCRATCH_MAX) ? 1
-                                                                                                                 : 0;
-  if (c.recover_split && !d.side.st) {
+  c.recover_split = (t.recover_split == 2 && c.smoothing && !c.sequential && !host_outputs &&
+                     rscr_bytes <= SPLIT_SCRATCH_MAX && (c.split_mode == 0 || c.split_mode == 3))
+                        ? 1
+                        : 0;
+  // a batch in chunks: the scans of one chunk beside the recovery of the one before
+  c.n_chunks = 1;
+  c.chunk = 0;
+  if (!c.fold_meta && !c.sequential && t.batch_chunks > 1) {
+    c.n_chunks = std::min(std::min(t.batch_chunks, MAXCHUNK), c.n_seq);
+    if (c.n_chunks > 1) c.recover_split = 0;
+  }
+  // host outputs of a batch: written to device staging, each chunk's rows
+  // copied to the host while the later chunks compute (kernel stores spread
+  // over a large host buffer reach a fraction of the link's rate; a streaming
+  // copy reaches it)
+  double** outp[8] = {&c.fast_mean, &c.fast_cov, &c.slow_mean, &c.slow_cov,
+                      &c.ffast_mean, &c.ffast_cov, &c.fslow_mean, &c.fslow_cov};
+  const int width[8] = {c.nx, c.nx * c.nx, c.nx, c.nx * c.nx, c.nx, c.nx * c.nx, c.nx, c.nx * c.nx};
+  const int slowrow[8] = {0, 0, 1, 1, 0, 0, 1, 1};
+  size_t stage_bytes = 0;
+  memset(&c.copy, 0, sizeof c.copy);
+  if (host_outputs && !c.fold_meta && !c.sequential) {
+    for (int i = 0; i < 8; ++i)
+      if (*outp[i] && !is_device_ptr(*outp[i]))
+        stage_bytes += a256(sizeof(double) * (size_t)width[i] * (size_t)(slowrow[i] ? c.total_slow : c.total_fast));
+    c.n_chunks = std::max(c.n_chunks, std::min(std::min(HOST_CHUNKS, MAXCHUNK), c.n_seq));
+    c.recover_split = 0;
+  }
+  if ((c.recover_split || c.n_chunks > 1 || stage_bytes) && !d.side.st) {
     int lo = 0, hi = 0;
     cudaDeviceGetStreamPriorityRange(&lo, &hi);  // the filtered half at the lowest priority
     if (cudaStreamCreateWithPriority(&d.side.st, cudaStreamNonBlocking, lo) != cudaSuccess ||
@@ -255,8 +309,14 @@ int run(Ctx c, srtm_precision prec, cudaStream_t st, bool host_outputs = false) 
         cudaEventCreateWithFlags(&d.side.join, cudaEventDisableTiming) != cudaSuccess)
       return fail(SRTM_ERR_CUDA, "second stream creation failed");
   }
+  if (stage_bytes && !d.side.cst) {
+    if (cudaStreamCreateWithFlags(&d.side.cst, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&d.side.cfork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&d.side.cjoin, cudaEventDisableTiming) != cudaSuccess)
+      return fail(SRTM_ERR_CUDA, "copy stream creation failed");
+  }
   const Layout L = make_layout(c.nx, c.ny, c.max_ratio, c.n_seq, c.total_slow, prec, tile_f, tile_s, c.nu,
-                               c.recover_split ? rscr_bytes : 0);
+                               c.recover_split ? rscr_bytes : 0, stage_bytes);
   if (d.ws_bytes < L.total) {
     if (d.ws) {
       cudaDeviceSynchronize();
@@ -292,6 +352,7 @@ int run(Ctx c, srtm_precision prec, cudaStream_t st, bool host_outputs = false) 
   c.meta.off_fast = (long long*)(w + L.off_fast);
   c.meta.tile_off_f = (long long*)(w + L.tile_f);
   c.meta.tile_off_s = (long long*)(w + L.tile_s);
+  c.meta.chunk_seq = (int*)(w + L.chunks);
   c.model = (double*)(w + L.model);
   c.ml = L.ml;
   c.ftile = w + L.ftile;
@@ -308,20 +369,41 @@ int run(Ctx c, srtm_precision prec, cudaStream_t st, bool host_outputs = false) 
   c.tile_f = tile_f;
   c.tile_s = tile_s;
   c.setup_separate = t.setup_mode == 2 ? 1 : 0;
-  d.last_launches = (c.fold_meta ? 0 : 1) + 3 + (c.smoothing ? 1 : 0) + c.setup_separate + (c.loglik ? 1 : 0) +
-                    (c.nu > 0 ? 1 : 0) + c.recover_split;
+  if (stage_bytes) {  // redirect the host outputs to their staging buffers
+    size_t so = L.stage;
+    for (int i = 0; i < 8; ++i) {
+      if (!*outp[i] || is_device_ptr(*outp[i])) continue;
+      const int k = c.copy.n++;
+      c.copy.dst[k] = (double*)mapped_host_ptr(*outp[i]);
+      c.copy.src[k] = (const double*)(w + so);
+      c.copy.width[k] = width[i];
+      c.copy.slow[k] = slowrow[i];
+      *outp[i] = (double*)(w + so);
+      so += a256(sizeof(double) * (size_t)width[i] * (size_t)(slowrow[i] ? c.total_slow : c.total_fast));
+    }
+  }
+  if (c.n_chunks > 1 || c.copy.n) chunk_grids(c, t, d.sms, &sh);
+  const int per_chunk = 2 + (c.smoothing ? 1 : 0) + c.setup_separate + (c.copy.n ? 1 : 0);  // scans, setup,
+                                                                                             // recovery, copy
+  d.last_launches = (c.fold_meta ? 0 : 1) + 1 + per_chunk * c.n_chunks + (c.loglik ? 1 : 0) + (c.nu > 0 ? 1 : 0) +
+                    c.recover_split;
+  if (c.split_mode == 1) d.last_launches = 2;                                    // constants, reducing filter scan
+  if (c.split_mode == 2) d.last_launches -= 1;                                   // no recovery
+  if (c.split_mode == 3 && c.next_mean) d.last_launches += 1;                    // the range's tail
   cudaEvent_t* ev = nullptr;
   if (g_timing) {
     if (!d.ev[0])
       for (int i = 0; i < NEVENT; ++i) cudaEventCreate(&d.ev[i]);
     ev = d.ev;
     d.ev_split = c.recover_split != 0;
+    d.ev_chunks = c.n_chunks;
     d.ev_stream = st;
     d.ev_valid = true;
   }
   rc = launch_meta(c, st, ev);
   if (rc) return fail(rc, "launch of the metadata kernel failed: %s", cudaGetErrorString(cudaGetLastError()));
-  rc = launch_for(c.nx, c, prec, sh, st, ev ? ev + 2 : nullptr, c.recover_split ? &d.side : nullptr);
+  rc = launch_for(c.nx, c, prec, sh, st, ev ? ev + 2 : nullptr,
+                  (c.recover_split || c.n_chunks > 1 || c.copy.n) ? &d.side : nullptr);
   if (rc) return fail(rc, "launch of the constants/scan/recovery kernels failed (scan smem %zu/%zu bytes)", sh.smem_f,
                       sh.smem_s);
   return SRTM_OK;
@@ -497,6 +579,110 @@ int srtm_smoother_batch_sequential(const srtm_batch* b, srtm_precision prec, con
   return batch(b, prec, smooth, filt, 1, stream, 1);
 }
 
+}  // extern "C"
+
+namespace {
+
+// One range of a sequence split over several GPUs (contiguous slow steps),
+// validated as a single-sequence call; known inputs are not supported here.
+int split_range(const srtm_problem* p, srtm_precision prec, int mode, int head_generic, int tail_open, double* agg,
+                const double* next_mean, const double* next_cov, const srtm_output* out, const srtm_output* extra,
+                srtm_stream_t stream) {
+  if (!p) return fail(SRTM_ERR_ARG, "problem is NULL");
+  if (prec < SRTM_FP64 || prec > SRTM_FP32) return fail(SRTM_ERR_ARG, "unknown precision %d", (int)prec);
+  int rc = check_dims(p->nx, p->ny);
+  if (rc) return rc;
+  if (p->ratio < 1) return fail(SRTM_ERR_ARG, "ratio=%d < 1", p->ratio);
+  if (p->n_slow < 1) return fail(SRTM_ERR_ARG, "n_slow=%d < 1", p->n_slow);
+  if (p->nu != 0) return fail(SRTM_ERR_UNSUPPORTED, "a split sequence takes no known inputs (nu=%d)", p->nu);
+  if ((rc = check_inputs(p->F, p->Q, p->H, p->R, p->m0, p->P0, p->y))) return rc;
+  if (mode != 3 && !is_device_ptr(agg)) return fail(SRTM_ERR_ARG, "agg must be device memory");
+  if (mode == 3) {
+    if ((next_mean == nullptr) != (next_cov == nullptr))
+      return fail(SRTM_ERR_ARG, "next_mean and next_cov must both be given or both be NULL");
+    if (next_mean && (!is_device_ptr(next_mean) || !is_device_ptr(next_cov)))
+      return fail(SRTM_ERR_ARG, "next_mean and next_cov must be device memory");
+    if ((rc = check_outputs(out, "output")) || (rc = check_outputs(extra, "filtered output"))) return rc;
+  }
+  Ctx c;
+  memset(&c, 0, sizeof c);
+  c.n_seq = 1;
+  c.fold_meta = 1;
+  c.nx = p->nx;
+  c.ny = p->ny;
+  c.max_ratio = p->ratio;
+  c.smoothing = mode == 1 ? 0 : 1;
+  c.uniform_ratio = p->ratio;
+  c.uniform_nslow = p->n_slow;
+  c.total_slow = p->n_slow;
+  c.total_fast = (long long)p->n_slow * p->ratio;
+  c.F = p->F; c.Q = p->Q; c.H = p->H; c.R = p->R; c.m0 = p->m0; c.P0 = p->P0; c.y = p->y;
+  c.split_mode = mode;
+  c.split_head_generic = head_generic;
+  c.split_tail_open = tail_open;
+  c.agg_out = agg;
+  c.next_mean = next_mean;
+  c.next_cov = next_cov;
+  if (mode == 3) set_outputs(c, out, extra);
+  return run(c, prec, (cudaStream_t)stream, mode == 3 && any_host_output(out, extra));
+}
+
+}  // namespace
+
+extern "C" {
+
+int srtm_split_filter_aggregate(const srtm_problem* p, int starts_sequence, srtm_precision prec, double* agg,
+                                srtm_stream_t stream) {
+  return split_range(p, prec, 1, starts_sequence ? 0 : 1, 0, agg, nullptr, nullptr, nullptr, nullptr, stream);
+}
+
+int srtm_split_smoother_aggregate(const srtm_problem* p, int ends_sequence, srtm_precision prec, double* agg,
+                                  srtm_stream_t stream) {
+  return split_range(p, prec, 2, 0, ends_sequence ? 0 : 1, agg, nullptr, nullptr, nullptr, nullptr, stream);
+}
+
+int srtm_split_smoother(const srtm_problem* p, const double* next_mean, const double* next_cov, srtm_precision prec,
+                        const srtm_output* smooth, const srtm_output* filt, srtm_stream_t stream) {
+  return split_range(p, prec, 3, 0, next_mean ? 1 : 0, nullptr, next_mean, next_cov, smooth, filt, stream);
+}
+
+int srtm_split_combine(int op, int nx, const double* elems, int n, double* out, srtm_stream_t stream) {
+  if (op != 0 && op != 1) return fail(SRTM_ERR_ARG, "op=%d is neither 0 (filter) nor 1 (smoother)", op);
+  if (nx < 1 || nx > MAXNX) return fail(SRTM_ERR_UNSUPPORTED, "nx=%d outside 1..%d", nx, MAXNX);
+  if (n < 1) return fail(SRTM_ERR_ARG, "n=%d < 1", n);
+  if (!is_device_ptr(elems) || !is_device_ptr(out)) return fail(SRTM_ERR_ARG, "elems and out must be device memory");
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAXDEV) return fail(SRTM_ERR_CUDA, "no device");
+  std::lock_guard<std::mutex> lk(g_mu);
+  DevState& d = g_dev[dev];
+  if (!d.ws) {  // the error latch lives in the control block at the start of the workspace
+    const size_t bytes = 4096;
+    if (cudaMalloc(&d.ws, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      d.ws = nullptr;
+      return fail(SRTM_ERR_CUDA, "workspace cudaMalloc failed");
+    }
+    if (cudaMemset(d.ws, 0, bytes) != cudaSuccess) return fail(SRTM_ERR_CUDA, "workspace memset failed");
+    d.ws_bytes = bytes;
+  }
+  d.last_launches = 1;
+  Counters* ctr = (Counters*)d.ws;
+  int rc = SRTM_ERR_UNSUPPORTED;
+  cudaStream_t st = (cudaStream_t)stream;
+  switch (nx) {
+    case 1: rc = launch_split_combine<1>(op, elems, n, out, ctr, st); break;
+    case 2: rc = launch_split_combine<2>(op, elems, n, out, ctr, st); break;
+    case 3: rc = launch_split_combine<3>(op, elems, n, out, ctr, st); break;
+    case 4: rc = launch_split_combine<4>(op, elems, n, out, ctr, st); break;
+    case 5: rc = launch_split_combine<5>(op, elems, n, out, ctr, st); break;
+    case 6: rc = launch_split_combine<6>(op, elems, n, out, ctr, st); break;
+    case 7: rc = launch_split_combine<7>(op, elems, n, out, ctr, st); break;
+    case 8: rc = launch_split_combine<8>(op, elems, n, out, ctr, st); break;
+  }
+  if (rc) return fail(rc, "launch of the combine kernel failed");
+  return SRTM_OK;
+}
+
 int srtm_selftest_wait(long long polls, srtm_stream_t stream) {
   if (polls < 1 || polls > SPIN_LIMIT) return fail(SRTM_ERR_ARG, "polls=%lld outside 1..%lld", polls, SPIN_LIMIT);
   int dev = 0;
@@ -654,11 +840,14 @@ int srtm_last_error_detail(char* buf, int len) {
   return n;
 }
 
+void g_noalloc_forget(int dev);
+
 int srtm_release(void) {
   std::lock_guard<std::mutex> lk(g_mu);
   int cur = 0;
   cudaGetDevice(&cur);
   for (int d = 0; d < MAXDEV; ++d) {
+    g_noalloc_forget(d);  // looked up again by the next call (e.g. after a context reset)
     if (!g_dev[d].ws && !g_dev[d].stage && !g_dev[d].hstage && !g_dev[d].side.st) continue;
     cudaSetDevice(d);
     cudaDeviceSynchronize();
@@ -669,6 +858,9 @@ int srtm_release(void) {
     if (g_dev[d].side.st) cudaStreamDestroy(g_dev[d].side.st);
     if (g_dev[d].side.fork) cudaEventDestroy(g_dev[d].side.fork);
     if (g_dev[d].side.join) cudaEventDestroy(g_dev[d].side.join);
+    if (g_dev[d].side.cst) cudaStreamDestroy(g_dev[d].side.cst);
+    if (g_dev[d].side.cfork) cudaEventDestroy(g_dev[d].side.cfork);
+    if (g_dev[d].side.cjoin) cudaEventDestroy(g_dev[d].side.cjoin);
     for (int i = 0; i < NEVENT; ++i)
       if (g_dev[d].ev[i]) cudaEventDestroy(g_dev[d].ev[i]);
     g_dev[d] = DevState();
@@ -690,6 +882,9 @@ int srtm_set_tuning(int nx, srtm_precision prec, const srtm_tuning* t) {
     return fail(SRTM_ERR_ARG, "lookback_window out of range");
   if (t->setup_mode < 0 || t->setup_mode > 2) return fail(SRTM_ERR_ARG, "setup_mode out of range");
   if (t->recover_split < 0 || t->recover_split > 2) return fail(SRTM_ERR_ARG, "recover_split out of range");
+  if (t->batch_chunks < 0 || t->batch_chunks > MAXCHUNK) return fail(SRTM_ERR_ARG, "batch_chunks out of range");
+  if (t->chunk_recover_bps < 0 || t->chunk_recover_bps > 3) return fail(SRTM_ERR_ARG, "chunk_recover_bps out of range");
+  if (t->chunk_scan_bps < 0 || t->chunk_scan_bps > 8) return fail(SRTM_ERR_ARG, "chunk_scan_bps out of range");
   std::lock_guard<std::mutex> lk(g_mu);
   g_tune[nx][prec] = *t;
   return SRTM_OK;
@@ -709,7 +904,7 @@ namespace {
 // Times `call` under each candidate tuning of (nx, prec); see srtm_autotune.
 template <class Call>
 int autotune_impl(int nx, srtm_precision prec, int reps, Call call, srtm_tuning* best, float* best_ms,
-                  cudaStream_t st) {
+                  cudaStream_t st, bool batched = false) {
   if (reps < 1) return fail(SRTM_ERR_ARG, "reps=%d < 1", reps);
   srtm_tuning saved;
   {
@@ -819,6 +1014,30 @@ int autotune_impl(int nx, srtm_precision prec, int reps, Call call, srtm_tuning*
     t.recover_split = sp;
     consider(t);
   }
+  if (batched) {  // a batch in chunks: the scans of one chunk beside the recovery of the one before
+    const int chunks[] = {2, 4, 8, 16};
+    for (int q : chunks) {
+      if (rc || q == cur.batch_chunks) continue;
+      srtm_tuning t = cur;
+      t.batch_chunks = q;
+      consider(t);
+    }
+    if (cur.batch_chunks > 1) {
+      for (int b = 0; b <= 3; ++b) {
+        if (rc || b == cur.chunk_recover_bps) continue;
+        srtm_tuning t = cur;
+        t.chunk_recover_bps = b;
+        consider(t);
+      }
+      const int sbps[] = {0, 1, 2, 4};
+      for (int b : sbps) {
+        if (rc || b == cur.chunk_scan_bps) continue;
+        srtm_tuning t = cur;
+        t.chunk_scan_bps = b;
+        consider(t);
+      }
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaStreamDestroy(cs);
@@ -860,7 +1079,7 @@ int srtm_autotune_batch(const srtm_batch* b, srtm_precision prec, const srtm_out
   return autotune_impl(
       b->nx, prec, reps,
       [&](cudaStream_t s) { return srtm_smoother_batch(b, prec, smooth, nullptr, (srtm_stream_t)s); }, best, best_ms,
-      (cudaStream_t)stream);
+      (cudaStream_t)stream, true);
 }
 
 int srtm_launches_per_call(int smoothing, int batched) { return (smoothing ? 4 : 3) + (batched ? 1 : 0); }
@@ -887,6 +1106,16 @@ int srtm_stage_times(float* ms, int n) {
   if (!d.ev_valid) return fail(SRTM_ERR_ARG, "no call was timed on this device (srtm_set_stage_timing(1) first)");
   if (cudaEventSynchronize(d.ev[NSTAGE]) != cudaSuccess) return fail(SRTM_ERR_CUDA, "event synchronize failed");
   for (int i = 0; i < n && i < NSTAGE + 1; ++i) {
+    if (i == NSTAGE - 1 && d.ev_chunks > 1) {  // the chunks' recovery launches, summed
+      ms[i] = 0.f;
+      for (int q = 0; q < d.ev_chunks; ++q) {
+        float v = 0.f;
+        if (cudaEventElapsedTime(&v, d.ev[NSTAGE + 4 + 2 * q], d.ev[NSTAGE + 5 + 2 * q]) != cudaSuccess)
+          return fail(SRTM_ERR_CUDA, "event timing failed");
+        ms[i] += v;
+      }
+      continue;
+    }
     cudaEvent_t a = d.ev[i], b = d.ev[i + 1];
     if (i == NSTAGE - 1 && d.ev_split) a = d.ev[NSTAGE + 1];  // smoothing half only
     if (i == NSTAGE) {  // filtered half of a split recovery
@@ -922,6 +1151,10 @@ namespace {
 // Device address of g_noalloc_scratch per GPU.  In host code the symbol is
 // only a host-side stand-in, so the address is fetched once per device.
 void* g_noalloc_addr[MAXDEV] = {};
+}
+// Drops the cached address of GPU dev (srtm_release; the caller holds g_mu).
+void g_noalloc_forget(int dev) {
+  if (dev >= 0 && dev < MAXDEV) g_noalloc_addr[dev] = nullptr;
 }
 
 extern "C" int srtm_smoother_noalloc(const srtm_problem* p, srtm_precision prec, const srtm_output* smooth,
@@ -1012,13 +1245,15 @@ extern "C" int srtm_smoother_noalloc(const srtm_problem* p, srtm_precision prec,
     rc = launch_for(c.nx, c, prec, sh, st, nullptr, nullptr);
     if (rc) return fail(rc, "launch of the scan/recovery kernels failed");
   }
-  // Device-side errors of this call live in the static scratch: wait for the
-  // call and read them here.
-  if (cudaStreamSynchronize(st) != cudaSuccess)
-    return fail(SRTM_ERR_CUDA, "stream synchronize failed: %s", cudaGetErrorString(cudaGetLastError()));
+  // Device-side errors of this call live in the static scratch: read them on
+  // the caller's stream and wait for that stream only.
   unsigned err = 0;
-  if (cudaMemcpy(&err, w + L.ctr + offsetof(Counters, err), sizeof err, cudaMemcpyDeviceToHost) != cudaSuccess)
-    return fail(SRTM_ERR_CUDA, "reading the device error latch failed");
+  const cudaError_t ce = cudaMemcpyAsync(&err, w + L.ctr + offsetof(Counters, err), sizeof err,
+                                         cudaMemcpyDeviceToHost, st);
+  const cudaError_t se = cudaStreamSynchronize(st);
+  if (ce != cudaSuccess || se != cudaSuccess)
+    return fail(SRTM_ERR_CUDA, "reading the device error latch failed: %s",
+                cudaGetErrorString(ce != cudaSuccess ? ce : se));
   if (err & DEVERR_TIMEOUT) return fail(SRTM_ERR_TIMEOUT, "a scan look-back wait exceeded its bound");
   if (err & DEVERR_NOT_PSD) return fail(SRTM_ERR_NOT_PSD, "Q, R or P0 is not a covariance matrix");
   if (err & DEVERR_SINGULAR) return fail(SRTM_ERR_SINGULAR, "a solve met a zero, negative or non-finite pivot");

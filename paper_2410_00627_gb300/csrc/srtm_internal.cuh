@@ -10,6 +10,9 @@ namespace srtm {
 
 constexpr int MAXNX = 8;  // compiled state sizes 1..8
 constexpr int MY = 4;     // measurement sizes 1..4 (padded to 4 in per-interval records)
+// A batch may be processed in up to MAXCHUNK chunks of whole sequences: the
+// scans of chunk c+1 run while the fast-rate recovery of chunk c runs.
+constexpr int MAXCHUNK = 16;
 
 enum DevErr : unsigned { DEVERR_TIMEOUT = 1u, DEVERR_SINGULAR = 2u, DEVERR_META = 4u, DEVERR_NOT_PSD = 8u };
 
@@ -20,7 +23,7 @@ constexpr long long SPIN_LIMIT = 2000000;
 // Device-side control block at offset 0 of the workspace.
 struct Counters {
   unsigned long long epoch;   // bumped once per call by the metadata kernel
-  unsigned int ticket[4];     // tile tickets: 0 filter scan, 1 smoother scan
+  unsigned int ticket[2 * MAXCHUNK];  // tile tickets of chunk q: 2q filter scan, 2q+1 smoother scan
   unsigned int err;           // DevErr bits, sticky until srtm_status()
   unsigned int call_ok;       // 1 when this call's metadata passed validation
   long long total_tiles_f, total_tiles_s;
@@ -35,6 +38,7 @@ struct SeqMeta {
   long long* off_fast;        // [n_seq+1] row offsets of fast outputs
   long long* tile_off_f;      // [n_seq+1] filter-scan tile offsets
   long long* tile_off_s;      // [n_seq+1] smoother-scan tile offsets
+  int* chunk_seq;             // [n_chunks+1] first sequence of each chunk (batches)
 };
 
 // Per-model constant table (float64), offsets in doubles.  L is the largest
@@ -95,7 +99,7 @@ __host__ __device__ inline ModelLayout make_model_layout(int n, int m, int L) {
 template <int NX>
 struct Rec {
   static constexpr int NN = NX * NX;
-  static constexpr int P = 0;                 // P^f_{k-1,l}          NN
+  static constexpr int P = 0;                 // P^f_{k-1,l} as LDL^T NN (L below the diagonal, D on it)
   static constexpr int mv = P + NN;           // m^f_{k-1,l}          NX
   static constexpr int X = mv + NX;           // P C_bar^T            NX*MY
   static constexpr int Si = X + NX * MY;      // S_y^-1               MY*MY
@@ -119,7 +123,8 @@ struct UIn {
   static constexpr int bl = 0, b1 = NX, bn = 2 * NX, c = 3 * NX, SIZE = 3 * NX + MY;
 };
 
-// Per-interval smoothing terms (Om_k, om_k), padded like the record.
+// Per-interval smoothing terms (Om_k as its LDL^T factors: L below the
+// diagonal, D on it; om_k), padded like the record.
 template <int NX>
 struct SFin {
   static constexpr int Om = 0, om = NX * NX, SIZE = (NX * NX + NX + 31) / 32 * 32;
@@ -137,6 +142,18 @@ struct SL {
   static constexpr int NN = NX * NX;
   static constexpr int E = 0, g = NN, S = NN + NX;
   static constexpr int SIZE = 2 * NN + NX;
+};
+
+// Host outputs of a batch: the kernels write device staging buffers of the
+// same layout, and each chunk's rows are copied to the host buffers by a
+// streaming copy kernel once the chunk's recovery is done.
+constexpr int MAXCOPY = 8;
+struct CopyOut {
+  int n;                        // staged outputs (0: none)
+  double* dst[MAXCOPY];         // the device's address of the caller's pinned host buffer
+  const double* src[MAXCOPY];   // its staging buffer in the workspace
+  int width[MAXCOPY];           // doubles per row
+  int slow[MAXCOPY];            // 1: one row per slow step, 0: one row per fast step
 };
 
 // Everything a kernel needs; passed by value.
@@ -174,6 +191,18 @@ struct Ctx {
   int setup_separate;    // 1: the interval setup runs as its own kernel after the filter scan
   int sequential;        // 1: the slow-rate recursions run sequentially (one thread per sequence)
   int recover_split;     // 1: filtered half of the recovery concurrent with the smoother scan
+  int n_chunks;          // > 1: a batch processed in chunks of whole sequences, pipelined
+  int chunk;             // the chunk a launch works on (0 when n_chunks == 1)
+  // one sequence split over several GPUs in contiguous slow-step ranges (the
+  // call works on one range): 1 filter aggregate, 2 smoother aggregate,
+  // 3 range smoother; 0 otherwise
+  int split_mode;
+  int split_head_generic;  // the range does not start the sequence: its first filter element is generic
+  int split_tail_open;     // the range does not end the sequence: its last interval is not terminal
+  int reduce_only;         // this scan launch forms only the range's aggregate (written to agg_out)
+  double* agg_out;         // float64 aggregate of the range (filter: FL layout, smoother: SL layout)
+  const double *next_mean, *next_cov;  // smoothed x_{k+1,1} after the range's last interval (mode 3)
+  CopyOut copy;            // staged host outputs of a batch
   void* rscr;            // [RecScr::SIZE][total_fast] filtered moments between the two halves (recovery type)
 };
 
@@ -191,6 +220,8 @@ struct RecScr {
 struct SideStream {
   cudaStream_t st;
   cudaEvent_t fork, join;
+  cudaStream_t cst;           // third stream: copies of staged host outputs
+  cudaEvent_t cfork, cjoin;
 };
 
 // ---------------------------------------------------------------------------
@@ -243,6 +274,8 @@ struct Shapes {  // resolved launch shapes for one call
   int grid_f, grid_s, grid_setup;
   int blocks_per_sm_f, blocks_per_sm_s;  // resident scan blocks per SM
   size_t smem_f, smem_s, smem_setup;
+  // per-chunk launches of a pipelined batch (set by the caller of the launch)
+  int grid_f_chunk, grid_s_chunk, grid_setup_chunk, grid_recover_chunk;
 };
 
 template <int NX>
@@ -251,8 +284,14 @@ int launch_device_path(const Ctx& c, srtm_precision prec, const Shapes& sh, cuda
 
 // sums the per-interval terms into the caller's log-likelihood output (meta.cu)
 int launch_loglik(const Ctx& c, cudaStream_t st);
+// copies the current chunk's rows of every staged host output (meta.cu)
+int launch_copy_out(const Ctx& c, cudaStream_t st);
 // bounded wait on a flag that nothing sets (failure-detection self-test, meta.cu)
 int launch_wait_probe(Counters* ctr, long long polls, cudaStream_t st);
+
+// float64 product of n filter (op 0) or smoother (op 1) elements (kernels.cuh)
+template <int NX>
+int launch_split_combine(int op, const double* in, int n, double* out, Counters* ctr, cudaStream_t st);
 
 template <int NX>
 int query_shapes(srtm_precision prec, int scan_groups, int scan_elems, int window, int recover_threads,

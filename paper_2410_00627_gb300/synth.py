@@ -212,8 +212,35 @@ def _ragged_chunk(args):
     return [_ragged_one(seed, s, n_min, n_max, ratios, keep_states) for s in range(lo, hi)]
 
 
+def ragged_shapes(seed: int = 0, n_seq: int = 4096, n_min: int = 100, n_max: int = 20_000,
+                  ratios=(5, 10, 20)) -> tuple[np.ndarray, np.ndarray]:
+    """(ratio, n_slow) of every sequence of ``ragged_chains`` without building
+    them: the same draws from each sequence's generator, up to its length."""
+    ratios = tuple(int(r) for r in ratios)
+    rs, ns = np.empty(n_seq, dtype=np.int64), np.empty(n_seq, dtype=np.int64)
+    for s in range(n_seq):
+        rng = np.random.default_rng([seed, s])
+        log_uniform(rng, 0.05, 1.0, 4)
+        rs[s] = int(rng.choice(ratios))
+        ns[s] = int(rng.integers(n_min, n_max + 1))
+    return rs, ns
+
+
+def balanced_ranges(fast_steps: np.ndarray, parts: int) -> list[tuple[int, int]]:
+    """Contiguous index ranges [lo, hi) of nearly equal total ``fast_steps``
+    (range r starts at the first index whose preceding sum reaches r/parts of
+    the total); ranges may be empty when one entry outweighs a share."""
+    cum = np.concatenate([[0], np.cumsum(fast_steps, dtype=np.int64)])
+    cuts = [0] + [int(np.searchsorted(cum, cum[-1] * r / parts, side="left")) for r in range(1, parts)] + [len(fast_steps)]
+    cuts = [min(max(c, 0), len(fast_steps)) for c in cuts]
+    for i in range(1, len(cuts)):
+        cuts[i] = max(cuts[i], cuts[i - 1])
+    return [(cuts[i], cuts[i + 1]) for i in range(parts)]
+
+
 def ragged_chains(seed: int = 0, n_seq: int = 4096, n_min: int = 100, n_max: int = 20_000,
-            ratios=(5, 10, 20), keep_states: bool = False, workers: int = 1) -> list[Problem]:
+            ratios=(5, 10, 20), keep_states: bool = False, workers: int = 1,
+            seq_range: tuple[int, int] | None = None) -> list[Problem]:
     """Ragged batch: per sequence a 4-species chain as in chain4 (dt=.05),
     ratio drawn from {5,10,20}, n_slow ~ U[n_min, n_max], ny=1 observing
     species 4, Q=1e-3 I, R=.05, m0=e1, P0=.1 I.
@@ -221,15 +248,29 @@ def ragged_chains(seed: int = 0, n_seq: int = 4096, n_min: int = 100, n_max: int
     Sequence s draws from its own generator seeded with (seed, s), so the
     batch is the same whether it is built serially or by ``workers`` processes
     (a pool started with the ``spawn`` method, safe after CUDA has been used).
+    ``seq_range`` = (lo, hi) builds only sequences lo .. hi-1 of the batch.
     """
     ratios = tuple(int(r) for r in ratios)
-    if workers <= 1 or n_seq < 2 * workers:
-        return _ragged_chunk((seed, 0, n_seq, n_min, n_max, ratios, keep_states))
+    lo, hi = (0, n_seq) if seq_range is None else (int(seq_range[0]), int(seq_range[1]))
+    if workers <= 1 or hi - lo < 2 * workers:
+        return _ragged_chunk((seed, lo, hi, n_min, n_max, ratios, keep_states))
     import multiprocessing as mp
-    bounds = np.linspace(0, n_seq, 4 * workers + 1).astype(int)
+    import os
+    bounds = np.linspace(lo, hi, 4 * workers + 1).astype(int)
     jobs = [(seed, int(a), int(b), n_min, n_max, ratios, keep_states) for a, b in zip(bounds[:-1], bounds[1:]) if b > a]
-    with mp.get_context("spawn").Pool(workers) as pool:
-        parts = pool.map(_ragged_chunk, jobs)
+    # one BLAS thread per worker process (the workers already fill the cores)
+    keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    saved = {k: os.environ.get(k) for k in keys}
+    os.environ.update({k: "1" for k in keys})
+    try:
+        with mp.get_context("spawn").Pool(workers) as pool:
+            parts = pool.map(_ragged_chunk, jobs)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
     return [p for part in parts for p in part]
 
 

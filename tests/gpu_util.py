@@ -62,14 +62,16 @@ def rel_err(a, b):
 
 
 def compare(gpu, ref, tol_m, tol_c, label=""):
-    """gpu / ref: dicts of arrays with *_mean / *_cov keys; returns the errors."""
+    """gpu / ref: dicts of arrays with *_mean / *_cov keys; every key of ref
+    must be in gpu (an output the GPU path did not write fails); returns the
+    errors."""
     errs = {}
     for k in ref:
-        if k not in gpu:
-            continue
+        assert k in gpu, f"{label}: output {k} missing from the GPU results"
+        assert k.endswith("mean") or k.endswith("cov") or k == "loglik", f"{label}: unknown output {k}"
         e = rel_err(gpu[k], ref[k])
         errs[k] = e
-        tol = tol_m if k.endswith("mean") else tol_c
+        tol = tol_c if k.endswith("cov") else tol_m   # means and the log likelihood at the mean tolerance
         assert e <= tol, f"{label} {k}: rel err {e:.3e} > {tol:.1e}"
     return errs
 

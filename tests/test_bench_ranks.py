@@ -1,7 +1,7 @@
-"""The benchmark's host logic: the multi-rank aggregation (weak scaling: every rank runs its
-own workload, no collective on the data path) on two gloo ranks on the CPU:
-the whole-job step time is the slowest rank's, and the units are summed; and
-the reference arm's JSON line (the oracle on the host cores)."""
+"""The benchmark's host logic: the multi-rank aggregation (no collective on the
+data path) on two gloo ranks on the CPU: the whole-job step time is the
+slowest rank's, and the units are summed; the split of the batch over ranks;
+and the reference arm's JSON line (the oracle on the host cores)."""
 import os
 import socket
 
@@ -51,12 +51,32 @@ def test_reduce_over_ranks_single_process():
     assert bench.reduce_over_ranks(2.0, 10, None, "cpu") == (2.0, 10.0)
 
 
-def test_bench_arguments_default_to_one_gpu_chain4():
+def test_bench_arguments_default_to_one_gpu_ragged_batch():
     import bench
     a = bench.parse([])
-    assert a.gpus == 1 and a.workload == "chain4" and a.warmup >= 3 and a.impl == "ours"
-    b = bench.parse(["--workload", "ragged_chains", "--steps", "3"])
-    assert b.workload == "ragged_chains" and b.n_seq == 4096 and b.steps == 3
+    assert a.gpus == 1 and a.workload == "ragged_chains" and a.n_seq == 4096 and a.warmup >= 3 and a.impl == "ours"
+    b = bench.parse(["--workload", "chain4", "--steps", "3"])
+    assert b.workload == "chain4" and b.n_slow == 10_000 and b.steps == 3
+
+
+def test_batch_partition_over_ranks_balances_fast_steps():
+    """Under torchrun the batch is split into contiguous sequence ranges of
+    nearly equal fast steps; the ranges tile the batch and the shapes used to
+    split it are those of the generated sequences."""
+    import numpy as np
+
+    from paper_2410_00627_gb300 import synth
+    r, n = synth.ragged_shapes(0, 4096)
+    f = r * n
+    for world in (2, 4, 8):
+        rng = synth.balanced_ranges(f, world)
+        assert rng[0][0] == 0 and rng[-1][1] == 4096
+        assert all(a[1] == b[0] for a, b in zip(rng[:-1], rng[1:]))
+        share = np.array([f[lo:hi].sum() for lo, hi in rng]) / f.sum()
+        assert np.all(np.abs(share - 1.0 / world) <= f.max() / f.sum() + 1e-12), (world, share)
+    probs = synth.ragged_chains(0, 12, seq_range=(4, 9))
+    r12, n12 = synth.ragged_shapes(0, 12)
+    assert [(p.ratio, p.n_slow) for p in probs] == list(zip(r12[4:9], n12[4:9]))
 
 
 def test_reference_arm_line_on_the_cpu():
@@ -66,8 +86,9 @@ def test_reference_arm_line_on_the_cpu():
     import subprocess
     import sys
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--n-slow", "100",
-                          "--steps", "2", "--warmup", "1"], capture_output=True, text=True, timeout=300, check=True)
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--workload", "chain4",
+                          "--n-slow", "100", "--steps", "2", "--warmup", "1"], capture_output=True, text=True,
+                         timeout=300, check=True)
     lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
     assert len(lines) == 1
     d = json.loads(lines[0])

@@ -135,8 +135,8 @@ def test_full_size_chain4_sampled(oracle_mod, precision):
                 {"fast_mean": o["fast_filt_mean"], "fast_cov": o["fast_filt_cov"]}, tm, tc, f"window {k0}")
     compare({"slow_mean": fi["slow_mean"], "slow_cov": fi["slow_cov"]},
             {"slow_mean": seq["slow_filt_mean"], "slow_cov": seq["slow_filt_cov"]}, tm, tc, "slow filtered")
-    compare({"m": sm["fast_mean"][0::l], "P": sm["fast_cov"][0::l]},
-            {"m": seq["first_smooth_mean"], "P": seq["first_smooth_cov"]}, tm, tc, "first smoothed")
+    compare({"first_mean": sm["fast_mean"][0::l], "first_cov": sm["fast_cov"][0::l]},
+            {"first_mean": seq["first_smooth_mean"], "first_cov": seq["first_smooth_cov"]}, tm, tc, "first smoothed")
 
 
 def test_ragged_batch_matches_per_sequence_oracle(oracle_mod):

@@ -3,11 +3,19 @@
 It serves callers that must not allocate GPU memory (their memory is owned by
 another allocator, or they cannot afford the device-wide synchronisation of
 cudaMalloc/cudaFree): the same device path runs with its scratch in a static
-device array.  This file is collected last so that a run stopping at the
-first failure has already run every other test; it also passes on its own in
-a fresh process.
+device array.  Its outputs are compared with the FP64 oracle on two calls in
+a row (the array keeps the previous call's contents), in a fresh process
+that never calls an allocating entry point of the library (the device's free
+memory must not change between the calls), after a rejected call, and for a
+non-covariance Q whose status is returned by the call itself.  This file is
+collected last so that a run stopping at the first failure has already run
+every other test; it also passes on its own in a fresh process.
 """
 import ctypes
+import json
+import os
+import subprocess
+import sys
 
 import numpy as np
 import pytest
@@ -15,6 +23,9 @@ import pytest
 from paper_2410_00627_gb300 import synth
 
 pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+TOLS = {0: (1e-9, 1e-8), 1: (1e-4, 1e-3), 2: (1e-4, 1e-3)}   # FP64, mixed, FP32 (FP32 within the mixed bound here)
 
 
 @pytest.fixture(scope="module")
@@ -50,25 +61,30 @@ def _outputs(prob):
     return o, api.Output(*[ctypes.c_void_p(o[k].data_ptr()) for k in api.OUTPUT_KEYS])
 
 
-@pytest.mark.parametrize("precision,tol", [(0, (1e-9, 1e-8)), (1, (1e-4, 1e-3))])
-def test_noalloc_matches_smoother_on_two_calls(lib, precision, tol):
+def _oracle_errors(oracle_mod, prob, got):
+    o = oracle_mod.sequential(prob)
+    l = prob.ratio
+    want = {"fast_mean": o["fast_smooth_mean"], "fast_cov": o["fast_smooth_cov"],
+            "slow_mean": o["fast_smooth_mean"][l - 1::l], "slow_cov": o["fast_smooth_cov"][l - 1::l]}
+    return {k: float(np.max(np.abs(got[k] - want[k])) / np.max(np.abs(want[k]))) for k in want}
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_noalloc_matches_oracle_on_two_calls(lib, oracle_mod, precision):
     import torch
 
     from paper_2410_00627_gb300 import api
     prob = synth.chain4(seed=31, n_slow=700, keep_states=False)
     p, _keep = _device_problem(prob)
-    ref, ref_o = _outputs(prob)
-    assert lib.srtm_smoother(ctypes.byref(p), precision, ctypes.byref(ref_o), None, None) == 0
-    assert lib.srtm_status(None) == 0
     for _ in range(2):  # the static scratch keeps the previous call's contents
         got, got_o = _outputs(prob)
         rc = lib.srtm_smoother_noalloc(ctypes.byref(p), precision, ctypes.byref(got_o), None)
         assert rc == 0, api.last_error_detail()
         torch.cuda.synchronize()
-        for k in api.OUTPUT_KEYS:
-            a, b = got[k].cpu().numpy(), ref[k].cpu().numpy()
-            err = np.max(np.abs(a - b)) / np.max(np.abs(b))
-            assert err <= (tol[0] if k.endswith("mean") else tol[1]), (k, err)
+        errs = _oracle_errors(oracle_mod, prob, {k: v.cpu().numpy() for k, v in got.items()})
+        tm, tc = TOLS[precision]
+        for k, e in errs.items():
+            assert e <= (tm if k.endswith("mean") else tc), (precision, k, e)
 
 
 def test_noalloc_rejects_problems_beyond_its_scratch(lib):
@@ -78,3 +94,73 @@ def test_noalloc_rejects_problems_beyond_its_scratch(lib):
     out = api.Output(None, None, None, None)
     assert lib.srtm_smoother_noalloc(ctypes.byref(p), 0, ctypes.byref(out), None) == -1
     assert "static scratch holds" in api.last_error_detail()
+
+
+def test_noalloc_reports_a_bad_covariance_then_runs_clean(lib, oracle_mod):
+    """An indefinite Q comes back as SRTM_ERR_NOT_PSD from the call itself;
+    the next call on good inputs matches the oracle."""
+    import torch
+    prob = synth.chain4(seed=33, n_slow=200, keep_states=False)
+    good_Q = prob.Q.copy()
+    prob.Q = good_Q.copy()
+    prob.Q[0, 0] = -1.0
+    p, _keep = _device_problem(prob)
+    _, o = _outputs(prob)
+    assert lib.srtm_smoother_noalloc(ctypes.byref(p), 0, ctypes.byref(o), None) == -2
+    prob.Q = good_Q
+    p, _keep = _device_problem(prob)
+    got, o = _outputs(prob)
+    assert lib.srtm_smoother_noalloc(ctypes.byref(p), 0, ctypes.byref(o), None) == 0
+    torch.cuda.synchronize()
+    for k, e in _oracle_errors(oracle_mod, prob, {k: v.cpu().numpy() for k, v in got.items()}).items():
+        assert e <= (1e-9 if k.endswith("mean") else 1e-8), (k, e)
+
+
+_FRESH = r"""
+import ctypes, json, sys
+import numpy as np
+import torch
+sys.path.insert(0, {root!r})
+from paper_2410_00627_gb300 import api, synth
+lib = api.load()
+prob = synth.chain4(seed=34, n_slow=500, keep_states=False)
+ts = {{k: torch.as_tensor(np.ascontiguousarray(getattr(prob, k)), dtype=torch.float64, device="cuda")
+      for k in ("F", "Q", "H", "R", "m0", "P0", "y")}}
+p = api.Problem(prob.nx, prob.ny, prob.ratio, prob.n_slow,
+                *[ctypes.c_void_p(ts[k].data_ptr()) for k in ("F", "Q", "H", "R", "m0", "P0", "y")])
+nf, ns, n = prob.n_slow * prob.ratio, prob.n_slow, prob.nx
+outs = [{{"fast_mean": torch.empty((nf, n), dtype=torch.float64, device="cuda"),
+         "fast_cov": torch.empty((nf, n, n), dtype=torch.float64, device="cuda"),
+         "slow_mean": torch.empty((ns, n), dtype=torch.float64, device="cuda"),
+         "slow_cov": torch.empty((ns, n, n), dtype=torch.float64, device="cuda")}} for _ in range(2)]
+torch.cuda.synchronize()
+rcs, free = [], []
+for o in outs:
+    oo = api.Output(*[ctypes.c_void_p(o[k].data_ptr()) for k in api.OUTPUT_KEYS])
+    rcs.append(lib.srtm_smoother_noalloc(ctypes.byref(p), 0, ctypes.byref(oo), None))
+    free.append(torch.cuda.mem_get_info()[0])
+np.save(sys.argv[1], np.concatenate([outs[1][k].cpu().numpy().ravel() for k in api.OUTPUT_KEYS]))
+print(json.dumps({{"rcs": rcs, "free": free, "launches": lib.srtm_last_call_launches()}}))
+"""
+
+
+def test_noalloc_in_a_fresh_process_allocates_nothing(lib, oracle_mod, tmp_path):
+    """In a process that never calls an allocating entry point, two calls in a
+    row leave the device's free memory unchanged and match the oracle."""
+    out = tmp_path / "out.npy"
+    res = subprocess.run([sys.executable, "-c", _FRESH.format(root=ROOT), str(out)], capture_output=True, text=True,
+                         timeout=600)
+    assert res.returncode == 0, res.stderr[-2000:]
+    d = json.loads(res.stdout.strip().splitlines()[-1])
+    assert d["rcs"] == [0, 0], d
+    assert d["free"][0] == d["free"][1], d
+    prob = synth.chain4(seed=34, n_slow=500, keep_states=False)
+    flat = np.load(out)
+    nf, ns, n = prob.n_slow * prob.ratio, prob.n_slow, prob.nx
+    sizes = [nf * n, nf * n * n, ns * n, ns * n * n]
+    parts = np.split(flat, np.cumsum(sizes)[:-1])
+    got = {k: v for k, v in zip(("fast_mean", "fast_cov", "slow_mean", "slow_cov"), parts)}
+    shapes = {"fast_mean": (nf, n), "fast_cov": (nf, n, n), "slow_mean": (ns, n), "slow_cov": (ns, n, n)}
+    got = {k: v.reshape(shapes[k]) for k, v in got.items()}
+    for k, e in _oracle_errors(oracle_mod, prob, got).items():
+        assert e <= (1e-9 if k.endswith("mean") else 1e-8), (k, e)
