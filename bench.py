@@ -644,6 +644,8 @@ def run_batched(args, rank, world, dist):
         seq_ms = time_calls(lambda st: api.smoother_batch(batch, precision=args.precision, out=outs, stream=st,
                                                           method="sequential"), 2, 1, stream)
         seq_max, seq_units = reduce_over_ranks(float(np.mean(seq_ms)), n_fast, dist, dev)
+        outs.clear()                 # the device outputs are not needed any more: room for the
+        torch.cuda.empty_cache()     # library's staging buffers of the host outputs
         e2e = run_batched_e2e(args, probs, pk, batch, ten, api, torch, stream, rank)
         e2e_ms, e2e_units = reduce_over_ranks(e2e["ms_per_step"], n_fast, dist, dev)
         if rank == 0:
@@ -711,15 +713,20 @@ def run_single_loop(probs, pk, ten, outs, api, torch, stream):
 
 
 def pinned_empty(shape):
-    """A page-locked host float64 array as a torch tensor: numpy memory
-    registered with cudaHostRegister (mapped: the device writes it at its host
-    address), so that its size is not rounded up as torch's pinned allocator
-    rounds it.  Returns (tensor, registered)."""
+    """A page-locked host float64 tensor from torch's pinned allocator
+    (cudaHostAlloc: mapped, the device writes it at its host address).  Host
+    memory merely registered with cudaHostRegister was measured much slower to
+    write from the GPU at this size (~42 GB/s against ~193 GB/s)."""
     import torch
-    t = torch.from_numpy(np.empty(shape, dtype=np.float64))
-    if int(torch.cuda.cudart().cudaHostRegister(t.data_ptr(), t.numel() * 8, 0)) == 0:
-        return t, True
-    return torch.empty(shape, dtype=torch.float64, pin_memory=True), False
+    return torch.empty(shape, dtype=torch.float64, pin_memory=True)
+
+
+def release_pinned():
+    """Hand torch's cached pinned host blocks back to the system."""
+    import torch
+    fn = getattr(torch._C, "_host_emptyCache", None)
+    if fn is not None:
+        fn()
 
 
 def run_batched_e2e(args, probs, pk, batch, ten, api, torch, stream, rank=0):
@@ -739,9 +746,7 @@ def run_batched_e2e(args, probs, pk, batch, ten, api, torch, stream, rank=0):
     shapes = {"fast_mean": (n_fast, nx), "fast_cov": (n_fast, nx, nx), "slow_mean": (n_slow, nx),
               "slow_cov": (n_slow, nx, nx)}
     t0 = time.perf_counter()
-    host_out, reg = {}, {}
-    for k, shp in shapes.items():
-        host_out[k], reg[k] = pinned_empty(shp)
+    host_out = {k: pinned_empty(shp) for k, shp in shapes.items()}
     pin_s = time.perf_counter() - t0
     try:
         with torch.cuda.stream(stream):
@@ -767,18 +772,16 @@ def run_batched_e2e(args, probs, pk, batch, ten, api, torch, stream, rank=0):
         ms = ms[1:]
         parity = check_parity_batch(probs, pk, host_out, args.precision) if rank == 0 else None
     finally:
-        for k, t in host_out.items():
-            if reg[k]:
-                torch.cuda.cudart().cudaHostUnregister(t.data_ptr())
         host_out.clear()
+        release_pinned()
     h2d = sum(h.numel() * h.element_size() for h in host_in.values())
     d2h = sum(int(np.prod(shp)) * 8 for shp in shapes.values())
     return {"value": n_fast / (float(np.mean(ms)) * 1e-3), "unit": UNIT, "ms_per_step": float(np.mean(ms)),
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "parity": parity,
             "pin_seconds": pin_s,
             "api": "pinned host inputs copied into the batch's device buffers, then srtm_smoother_batch (CUDA graph) "
-                   "writing every smoothed output (fast and slow means and covariances) into page-locked host "
-                   "memory over the CPU-GPU link"}
+                   "with every smoothed output (fast and slow means and covariances) in pinned host memory: staged "
+                   "in HBM and copied to the host over the CPU-GPU link chunk by chunk while later chunks compute"}
 
 
 def cpu_model() -> str:

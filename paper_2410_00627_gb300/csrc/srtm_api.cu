@@ -861,6 +861,7 @@ int srtm_release(void) {
     if (g_dev[d].side.cst) cudaStreamDestroy(g_dev[d].side.cst);
     if (g_dev[d].side.cfork) cudaEventDestroy(g_dev[d].side.cfork);
     if (g_dev[d].side.cjoin) cudaEventDestroy(g_dev[d].side.cjoin);
+
     for (int i = 0; i < NEVENT; ++i)
       if (g_dev[d].ev[i]) cudaEventDestroy(g_dev[d].ev[i]);
     g_dev[d] = DevState();
