@@ -644,8 +644,8 @@ def run_batched(args, rank, world, dist):
         seq_ms = time_calls(lambda st: api.smoother_batch(batch, precision=args.precision, out=outs, stream=st,
                                                           method="sequential"), 2, 1, stream)
         seq_max, seq_units = reduce_over_ranks(float(np.mean(seq_ms)), n_fast, dist, dev)
-        outs.clear()                 # the device outputs are not needed any more: room for the
-        torch.cuda.empty_cache()     # library's staging buffers of the host outputs
+        outs.clear()                 # the device outputs are not needed any more
+        torch.cuda.empty_cache()
         e2e = run_batched_e2e(args, probs, pk, batch, ten, api, torch, stream, rank)
         e2e_ms, e2e_units = reduce_over_ranks(e2e["ms_per_step"], n_fast, dist, dev)
         if rank == 0:
@@ -734,7 +734,7 @@ def run_batched_e2e(args, probs, pk, batch, ten, api, torch, stream, rank=0):
     the inputs from pinned host memory into the batch's device buffers and
     replays the captured srtm_smoother_batch call whose outputs -- all of them:
     fast and slow smoothed means and covariances -- are pinned host memory,
-    written by the recovery kernels over the CPU-GPU link.  The timed host
+    written by the recovery kernel over the CPU-GPU link.  The timed host
     outputs of sampled sequences are checked against the oracle."""
     keys = ("F", "Q", "H", "R", "m0", "P0", "y", "ratio", "n_slow")
     host_in = {}
@@ -780,8 +780,8 @@ def run_batched_e2e(args, probs, pk, batch, ten, api, torch, stream, rank=0):
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "parity": parity,
             "pin_seconds": pin_s,
             "api": "pinned host inputs copied into the batch's device buffers, then srtm_smoother_batch (CUDA graph) "
-                   "with every smoothed output (fast and slow means and covariances) in pinned host memory: staged "
-                   "in HBM and copied to the host over the CPU-GPU link chunk by chunk while later chunks compute"}
+                   "with every smoothed output (fast and slow means and covariances) in pinned (cudaHostAlloc) host "
+                   "memory, written by the recovery kernel over the CPU-GPU link"}
 
 
 def cpu_model() -> str:
@@ -1004,7 +1004,8 @@ def report_errors(name, precisions=("fp64", "mixed", "fp32"), n_slow=None, seed=
 def run_peaks():
     """FP64 and FP32 FMA peaks of GPU 0 (srtm_measure_peak: 300 ms launches of
     independent FMA chains on every SM, fastest of three, three times each),
-    with the SM clocks sampled by nvidia-smi while they run."""
+    with the SM clocks sampled by nvidia-smi while they run; and the CPU-GPU
+    link's rates for 4 and 32 GiB moves (srtm_measure_link)."""
     import torch
 
     from paper_2410_00627_gb300 import api, build
@@ -1017,10 +1018,12 @@ def run_peaks():
     res = {k: [api.measure_peak(k, 300.0)[0] for _ in range(3)] for k in ("fp64", "fp32")}
     time.sleep(0.3)
     ck = clocks.stop()
+    link = {f"{k}_GBps": {f"{g}GiB": api.measure_link(k, g) for g in (4.0, 32.0)} for k in api.LINK_KINDS}
     return {"peaks": "FMA throughput (srtm_measure_peak)", "gpu": torch.cuda.get_device_name(),
             "fp64_gflops": max(res["fp64"]), "fp32_gflops": max(res["fp32"]), "runs": res,
             "sm_mhz_median": ck["sm_mhz"], "sm_max_mhz": ck["sm_max_mhz"], "reasons": ck["reasons"],
-            "clock_samples": ck["samples"], "when": time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime())}
+            "clock_samples": ck["samples"], "when": time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime()),
+            "link": link}
 
 
 def run_reference(args):

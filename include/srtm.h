@@ -357,6 +357,17 @@ int srtm_stage_times(float *ms, int n);
  * small output buffer with cudaMallocAsync on `stream` and synchronizes it.
  * Errors: SRTM_ERR_ARG (kind, target_ms or gflops invalid), SRTM_ERR_CUDA.   */
 int srtm_measure_peak(int kind, float target_ms, double *gflops, float *ms, srtm_stream_t stream);
+/* CPU-GPU link calibration (the paper has no counterpart; it explains the
+ * end-to-end numbers of the benchmark): moves `gib` GiB (1/16..64) between a
+ * device buffer and page-locked host memory and writes the fastest of three
+ * timed moves (after one untimed) in GB/s to *gbps.  kind 0: device to host
+ * by cudaMemcpyAsync (copy engine) into cudaHostAlloc'd memory; 1: device to
+ * host by a kernel of consecutive 16-byte stores into the same kind of
+ * memory; 2: host to device by cudaMemcpyAsync; 3: as 1 into malloc'd memory
+ * registered with cudaHostRegister.  Allocates and frees its buffers
+ * (cudaMalloc, cudaHostAlloc or malloc + cudaHostRegister) and synchronizes
+ * `stream`.  Errors: SRTM_ERR_ARG, SRTM_ERR_CUDA.                            */
+int srtm_measure_link(int kind, double gib, double *gbps, srtm_stream_t stream);
 
 /* srtm_smoother for callers that must not allocate device memory (the paper
  * has no counterpart; this is a deployment variant).  Such callers include a

@@ -27,7 +27,7 @@ SYMBOLS = ("srtm_filter", "srtm_smoother", "srtm_filter_batch", "srtm_smoother_b
            "srtm_last_call_launches", "srtm_filter_sequential", "srtm_smoother_sequential",
            "srtm_filter_batch_sequential", "srtm_smoother_batch_sequential", "srtm_selftest_wait",
            "srtm_measure_peak", "srtm_split_filter_aggregate", "srtm_split_smoother_aggregate",
-           "srtm_split_smoother", "srtm_split_combine")
+           "srtm_split_smoother", "srtm_split_combine", "srtm_measure_link")
 METHODS = {"scan": "", "sequential": "_sequential"}  # entry-point suffix per method
 STAGES = ("metadata", "constants", "filter_scan", "interval_setup", "smoother_scan", "recovery",
           "recovery_filtered_half")
@@ -112,6 +112,7 @@ def load():
         "srtm_split_smoother_aggregate": [P, c_int, c_int, c_void_p, c_void_p],
         "srtm_split_smoother": [P, c_void_p, c_void_p, c_int, O, O, c_void_p],
         "srtm_split_combine": [c_int, c_int, c_void_p, c_int, c_void_p, c_void_p],
+        "srtm_measure_link": [c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_double), c_void_p],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -446,6 +447,16 @@ def measure_peak(kind: str = "fp64", target_ms: float = 200.0, stream=None) -> t
     _check(load().srtm_measure_peak({"fp64": 0, "fp32": 1}[kind], float(target_ms), ctypes.byref(g), ctypes.byref(ms),
                                     _stream_handle(stream)))
     return float(g.value), float(ms.value)
+
+
+LINK_KINDS = {"d2h_copy_engine": 0, "d2h_kernel_stores": 1, "h2d_copy_engine": 2, "d2h_kernel_stores_registered": 3}
+
+
+def measure_link(kind: str, gib: float = 4.0, stream=None) -> float:
+    """CPU-GPU link rate in GB/s (srtm_measure_link); kind is a key of LINK_KINDS."""
+    g = ctypes.c_double()
+    _check(load().srtm_measure_link(LINK_KINDS[kind], float(gib), ctypes.byref(g), _stream_handle(stream)))
+    return float(g.value)
 
 
 def release() -> None:

@@ -378,6 +378,9 @@ __global__ void __launch_bounds__(PRE_THREADS) precompute_kernel(Ctx c, int tabl
   for (int e = tid; e < NX * m; e += nt) {
     md[L.K + e] = sm[S::K + e];
     md[L.Cr + e] = sm[S::Cr + e];
+    float* cf = (float*)(md + L.Cf);  // float copies for the float32 filter elements
+    cf[3 * NN + NX * MY + e] = (float)sm[S::K + e];
+    cf[3 * NN + 2 * NX * MY + e] = (float)sm[S::Cr + e];
   }
   for (int e = tid; e < m * m; e += nt) md[L.Rx + e] = sm[S::Rx + e];
   for (int e = tid; e < NX; e += nt) md[L.m1 + e] = sm[S::m1 + e];

@@ -258,8 +258,8 @@ __device__ void setup_interval(const Ctx& c, long long gi, int lane, unsigned ma
     for (int i = 0; i < MY; ++i)
 #pragma unroll
       for (int j = 0; j < MY; ++j) Sy[i][j] = (i < m && j < m) ? sb[Gm::Sy + i * MY + j] : ((i == j) ? TR(1) : TR(0));
-    TR logdet = TR(0);
-    ok &= small_sym_inverse<TR>(Sy, Si, m, &logdet);
+    TR logdet = TR(0);  // (the float64 log only when the log likelihood is asked for)
+    ok &= small_sym_inverse<TR>(Sy, Si, m, c.loglik ? &logdet : nullptr);
 #pragma unroll
     for (int i = 0; i < MM; ++i) {
       TR v = TR(0);
@@ -548,17 +548,25 @@ struct FilterOp {
     const int m = c.ny;
     const long long row = c.meta.off_slow[s] + p;
     const double* yk = c.y + row * m;
-    // with inputs: y_k - c_k enters K and C_bar^T R_x^-1, and d_k gains b_{k,l}
+    // with inputs: y_k - c_k enters K and C_bar^T R_x^-1, and d_k gains b_{k,l};
+    // formed in the scan type (float32 elements from the model's float copies
+    // of K and C_bar^T R_x^-1 in the mixed and FP32 modes)
     const double* ui = c.uin ? c.uin + row * UIn<NX>::SIZE : nullptr;
+    const float* cf = (const float*)(md + c.ml.Cf);
     for (int r = g.lane; r < NX; r += G) {
-      double dv = ui ? ui[UIn<NX>::bl + r] : 0.0, ev = 0.0;
+      T dv = ui ? (T)ui[UIn<NX>::bl + r] : T(0), ev = T(0);
       for (int j = 0; j < m; ++j) {
-        const double yj = ui ? yk[j] - ui[UIn<NX>::c + j] : yk[j];
-        dv = fma(md[c.ml.K + r * m + j], yj, dv);
-        ev = fma(md[c.ml.Cr + r * m + j], yj, ev);
+        const T yj = (T)(ui ? yk[j] - ui[UIn<NX>::c + j] : yk[j]);
+        if constexpr (sizeof(T) == sizeof(double)) {
+          dv = fma((T)md[c.ml.K + r * m + j], yj, dv);
+          ev = fma((T)md[c.ml.Cr + r * m + j], yj, ev);
+        } else {
+          dv = fma((T)cf[3 * NN + NX * MY + r * m + j], yj, dv);
+          ev = fma((T)cf[3 * NN + 2 * NX * MY + r * m + j], yj, ev);
+        }
       }
-      x[L::d + r] = (T)dv;
-      x[L::e + r] = (T)ev;
+      x[L::d + r] = dv;
+      x[L::e + r] = ev;
     }
   }
   // filter result at k: d_k = m^f_{k,l}, D_k = P^f_{k,l}, kept in TS (float64
@@ -1624,8 +1632,7 @@ inline void launch_setup(const Ctx& c, unsigned grid, size_t smem, cudaStream_t 
 // chunk q; on the library's second stream the fast-rate recovery of chunk q,
 // which waits for chunk q's scans and runs while `st` goes on with the scans
 // of chunk q+1 (Remark 1: the recovery of an interval needs only that
-// interval's scan results); with staged host outputs, on a third stream the
-// copy of chunk q's rows to the host while the later chunks compute.  The chunks' rows are disjoint, so the launches
+// interval's scan results).  The chunks' rows are disjoint, so the launches
 // share the workspace without conflict.  Stage events (optional): ev[1..3]
 // after the last chunk's scans, ev[4] after the last recovery, ev[8+2q] and
 // ev[9+2q] around the recovery of chunk q (on the second stream).
@@ -1649,20 +1656,11 @@ int launch_chunks(const Ctx& c, const Shapes& sh, cudaStream_t st, cudaEvent_t* 
     if (ev) cudaEventRecord(ev[8 + 2 * q], side->st);
     launch_recover<NX, TR, 0>(cq, (unsigned)sh.grid_recover_chunk, sh.recover_threads, rsmem, side->st);
     if (ev) cudaEventRecord(ev[9 + 2 * q], side->st);
-    if (c.copy.n) {  // the chunk's staged host outputs, on a third stream beside the next chunks
-      cudaEventRecord(side->cfork, side->st);
-      cudaStreamWaitEvent(side->cst, side->cfork, 0);
-      launch_copy_out(cq, side->cst);
-    }
   }
   if (ev)
     for (int i = 1; i <= 3; ++i) cudaEventRecord(ev[i], st);
   cudaEventRecord(side->join, side->st);
   cudaStreamWaitEvent(st, side->join, 0);
-  if (c.copy.n) {
-    cudaEventRecord(side->cjoin, side->cst);
-    cudaStreamWaitEvent(st, side->cjoin, 0);
-  }
   launch_loglik(c, st);
   if (ev) cudaEventRecord(ev[4], st);
   return cudaGetLastError() == cudaSuccess ? SRTM_OK : SRTM_ERR_CUDA;
@@ -1680,7 +1678,7 @@ int launch_t(const Ctx& c, const Shapes& sh, cudaStream_t st, cudaEvent_t* ev, c
   launch_precompute<NX>(c, st);
   if (c.uin) input_kernel<NX><<<(unsigned)((c.total_slow + 127) / 128), 128, 0, st>>>(c);
   if (ev) cudaEventRecord(ev[0], st);
-  if ((c.n_chunks > 1 || c.copy.n) && side) return launch_chunks<NX, T, TS, TR>(c, sh, st, ev, side);
+  if (c.n_chunks > 1 && side) return launch_chunks<NX, T, TS, TR>(c, sh, st, ev, side);
   if (c.split_mode == 1) {  // the filter aggregate of a range of a split sequence: a reducing scan only
     Ctx cr = c;
     cr.reduce_only = 1;

@@ -144,48 +144,6 @@ __global__ void __launch_bounds__(256) loglik_kernel(Ctx c) {
   if (threadIdx.x == 0) c.loglik[s] = part[0];
 }
 
-// Staged host outputs: the rows of the launch's chunk (the whole batch when it
-// is not chunked) from each staging buffer to the caller's pinned host buffer,
-// as consecutive 16-byte stores over the CPU-GPU link (8-byte ones when the two
-// addresses differ in 16-byte alignment).
-__global__ void __launch_bounds__(256) copy_out_kernel(Ctx c) {
-  if (!c.ctr->call_ok) return;
-  const int s_lo = c.n_chunks > 1 ? c.meta.chunk_seq[c.chunk] : 0;
-  const int s_hi = c.n_chunks > 1 ? c.meta.chunk_seq[c.chunk + 1] : c.n_seq;
-  const long long stride = (long long)gridDim.x * blockDim.x, t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  for (int i = 0; i < c.copy.n; ++i) {
-    const long long* off = c.copy.slow[i] ? c.meta.off_slow : c.meta.off_fast;
-    const long long lo = off[s_lo] * c.copy.width[i], hi = off[s_hi] * c.copy.width[i];
-    if (hi <= lo) continue;
-    double* d = c.copy.dst[i];
-    const double* sr = c.copy.src[i];
-    const bool same = (((reinterpret_cast<uintptr_t>(d + lo) ^ reinterpret_cast<uintptr_t>(sr + lo)) & 15) == 0);
-    if (!same) {
-      for (long long e = lo + t0; e < hi; e += stride) d[e] = sr[e];
-      continue;
-    }
-    long long a = lo;
-    if (reinterpret_cast<uintptr_t>(d + a) & 15) {  // one leading element to reach 16-byte alignment
-      if (t0 == 0) d[a] = sr[a];
-      ++a;
-    }
-    const long long pairs = (hi - a) / 2;
-    double2* d2 = reinterpret_cast<double2*>(d + a);
-    const double2* s2 = reinterpret_cast<const double2*>(sr + a);
-    for (long long e = t0; e < pairs; e += stride) d2[e] = __ldcs(s2 + e);
-    if (t0 == 0 && a + 2 * pairs < hi) d[hi - 1] = sr[hi - 1];
-  }
-}
-
-int launch_copy_out(const Ctx& c, cudaStream_t st) {
-  if (c.copy.n == 0) return SRTM_OK;
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  copy_out_kernel<<<2 * (sms > 0 ? sms : 1), 256, 0, st>>>(c);
-  return cudaGetLastError() == cudaSuccess ? SRTM_OK : SRTM_ERR_CUDA;
-}
-
 int launch_loglik(const Ctx& c, cudaStream_t st) {
   if (!c.loglik) return SRTM_OK;
   loglik_kernel<<<c.n_seq, 256, 0, st>>>(c);

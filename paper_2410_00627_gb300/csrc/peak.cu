@@ -1,9 +1,12 @@
-// peak.cu -- arithmetic-throughput calibration (the paper has no
-// counterpart): the float64 and float32 FMA rates of this GPU, measured by a
-// kernel of independent FMA chains on every SM.  They are the denominators of
-// the roofline fractions that the benchmark reports for the FP64-bound
-// fast-rate recovery and the float32 scans.
+// peak.cu -- throughput calibration (the paper has no counterpart): the
+// float64 and float32 FMA rates of this GPU, measured by a kernel of
+// independent FMA chains on every SM (the denominators of the roofline
+// fractions the benchmark reports for the FP64-bound fast-rate recovery and
+// the float32 scans), and the CPU-GPU link's rate for pinned host memory.
 #include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdlib>
 
 #include "srtm_internal.cuh"
 
@@ -89,8 +92,63 @@ int measure(float target_ms, double* gflops, float* ms_out, cudaStream_t st) {
   return rc;
 }
 
+// consecutive 16-byte stores of a grid-stride loop (the pattern of the
+// library's copy-out kernel)
+__global__ void __launch_bounds__(256) link_store_kernel(double2* dst, const double2* src, long long n) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride) dst[i] = __ldcs(src + i);
+}
+
 }  // namespace
 }  // namespace srtm
+
+extern "C" int srtm_measure_link(int kind, double gib, double* gbps, srtm_stream_t stream) {
+  if (!gbps || kind < 0 || kind > 3 || !(gib >= 0.0625 && gib <= 64.0)) return SRTM_ERR_ARG;
+  const size_t bytes = (size_t)(gib * (double)(1ull << 30)) / 256 * 256;
+  cudaStream_t st = (cudaStream_t)stream;
+  void *h = nullptr, *hd = nullptr, *d = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = SRTM_OK, dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return SRTM_ERR_CUDA;
+  const unsigned flags = kind == 3 ? cudaHostRegisterMapped : cudaHostAllocMapped;
+  if (kind == 3) {  // pageable memory made page-locked by registration
+    h = malloc(bytes);
+    if (!h || cudaHostRegister(h, bytes, flags) != cudaSuccess) rc = SRTM_ERR_CUDA;
+  } else if (cudaHostAlloc(&h, bytes, flags) != cudaSuccess) {
+    rc = SRTM_ERR_CUDA;
+  }
+  if (rc == SRTM_OK && (cudaHostGetDevicePointer(&hd, h, 0) != cudaSuccess || cudaMalloc(&d, bytes) != cudaSuccess ||
+                        cudaMemsetAsync(d, 0, bytes, st) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+                        cudaEventCreate(&e1) != cudaSuccess))
+    rc = SRTM_ERR_CUDA;
+  auto once = [&](float* ms) -> int {
+    cudaEventRecord(e0, st);
+    if (kind == 0) cudaMemcpyAsync(h, d, bytes, cudaMemcpyDeviceToHost, st);
+    else if (kind == 2) cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, st);
+    else srtm::link_store_kernel<<<2 * sms, 256, 0, st>>>((double2*)hd, (const double2*)d, (long long)(bytes / 16));
+    cudaEventRecord(e1, st);
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(ms, e0, e1) != cudaSuccess) return SRTM_ERR_CUDA;
+    return SRTM_OK;
+  };
+  double best = 0.0;
+  for (int r = 0; rc == SRTM_OK && r < 4; ++r) {  // the first run warms up; the fastest of the others
+    float ms = 0.f;
+    rc = once(&ms);
+    if (rc == SRTM_OK && r > 0 && ms > 0.f) best = std::max(best, (double)bytes / (ms * 1e-3) / 1e9);
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaStreamSynchronize(st);
+  if (d) cudaFree(d);
+  if (h) {
+    if (kind == 3) { cudaHostUnregister(h); free(h); }
+    else cudaFreeHost(h);
+  }
+  if (rc == SRTM_OK && cudaGetLastError() != cudaSuccess) rc = SRTM_ERR_CUDA;
+  *gbps = best;
+  return rc;
+}
 
 extern "C" int srtm_measure_peak(int kind, float target_ms, double* gflops, float* ms, srtm_stream_t stream) {
   if (!gflops || (kind != 0 && kind != 1) || !(target_ms >= 1.f && target_ms <= 5000.f)) return SRTM_ERR_ARG;

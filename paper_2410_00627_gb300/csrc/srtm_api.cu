@@ -114,7 +114,7 @@ size_t a16(size_t x) { return (x + 15) / 16 * 16; }
 
 struct Layout {
   size_t ctr, ratio, nslow, off_slow, off_fast, tile_f, tile_s, chunks, model, ftile, stile, fout, rec, selem, sfin,
-      lterm, uin, rscr, stage, total;
+      lterm, uin, rscr, total;
   long long ftile_stride, stile_stride;
   ModelLayout ml;
 };
@@ -125,10 +125,9 @@ size_t split_scratch_bytes(int nx, srtm_precision prec, long long total_fast) {
   return sR * (size_t)(nx + nx * (nx + 1) / 2 + nx * nx) * (size_t)total_fast;
 }
 constexpr size_t SPLIT_SCRATCH_MAX = (size_t)4 << 30;
-constexpr int HOST_CHUNKS = 8;  // chunks of a batch whose outputs are host memory
 
 Layout make_layout(int nx, int ny, int max_ratio, int n_seq, long long total_slow, srtm_precision prec, int tile_f,
-                   int tile_s, int nu, size_t rscr_bytes, size_t stage_bytes = 0) {
+                   int tile_s, int nu, size_t rscr_bytes) {
   Layout L;
   const size_t sT = prec == SRTM_FP64 ? 8 : 4, sR = prec == SRTM_FP32 ? 4 : 8;
   const long long nn = (long long)nx * nx;
@@ -161,7 +160,6 @@ Layout make_layout(int nx, int ny, int max_ratio, int n_seq, long long total_slo
   L.lterm = take(sizeof(double) * (size_t)total_slow);
   L.uin = take(nu > 0 ? sizeof(double) * (size_t)(3 * nx + MY) * total_slow : 0);
   L.rscr = take(rscr_bytes);
-  L.stage = take(stage_bytes);
   L.total = a256(o);
   return L;
 }
@@ -253,10 +251,9 @@ void chunk_grids(const Ctx& c, const srtm_tuning& t, int sms, Shapes* sh) {
 }
 
 // Runs the device path for a fully validated context (sizes in `c` set).
-// host_outputs: some output is pinned host memory.  One sequence: the
-// recovery writes it over the CPU-GPU link and stays one kernel, so that those
-// slower stores overlap all of its arithmetic instead of only the smoothing
-// half.  A batch: it is staged in device memory and copied out per chunk.
+// host_outputs: some output is pinned host memory written over the CPU-GPU
+// link; the recovery then stays one kernel, so that those slower stores
+// overlap all of its arithmetic instead of only the smoothing half.
 int run(Ctx c, srtm_precision prec, cudaStream_t st, bool host_outputs = false) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAXDEV)
@@ -284,24 +281,7 @@ int run(Ctx c, srtm_precision prec, cudaStream_t st, bool host_outputs = false) 
     c.n_chunks = std::min(std::min(t.batch_chunks, MAXCHUNK), c.n_seq);
     if (c.n_chunks > 1) c.recover_split = 0;
   }
-  // host outputs of a batch: written to device staging, each chunk's rows
-  // copied to the host while the later chunks compute (kernel stores spread
-  // over a large host buffer reach a fraction of the link's rate; a streaming
-  // copy reaches it)
-  double** outp[8] = {&c.fast_mean, &c.fast_cov, &c.slow_mean, &c.slow_cov,
-                      &c.ffast_mean, &c.ffast_cov, &c.fslow_mean, &c.fslow_cov};
-  const int width[8] = {c.nx, c.nx * c.nx, c.nx, c.nx * c.nx, c.nx, c.nx * c.nx, c.nx, c.nx * c.nx};
-  const int slowrow[8] = {0, 0, 1, 1, 0, 0, 1, 1};
-  size_t stage_bytes = 0;
-  memset(&c.copy, 0, sizeof c.copy);
-  if (host_outputs && !c.fold_meta && !c.sequential) {
-    for (int i = 0; i < 8; ++i)
-      if (*outp[i] && !is_device_ptr(*outp[i]))
-        stage_bytes += a256(sizeof(double) * (size_t)width[i] * (size_t)(slowrow[i] ? c.total_slow : c.total_fast));
-    c.n_chunks = std::max(c.n_chunks, std::min(std::min(HOST_CHUNKS, MAXCHUNK), c.n_seq));
-    c.recover_split = 0;
-  }
-  if ((c.recover_split || c.n_chunks > 1 || stage_bytes) && !d.side.st) {
+  if ((c.recover_split || c.n_chunks > 1) && !d.side.st) {
     int lo = 0, hi = 0;
     cudaDeviceGetStreamPriorityRange(&lo, &hi);  // the filtered half at the lowest priority
     if (cudaStreamCreateWithPriority(&d.side.st, cudaStreamNonBlocking, lo) != cudaSuccess ||
@@ -309,14 +289,8 @@ int run(Ctx c, srtm_precision prec, cudaStream_t st, bool host_outputs = false) 
         cudaEventCreateWithFlags(&d.side.join, cudaEventDisableTiming) != cudaSuccess)
       return fail(SRTM_ERR_CUDA, "second stream creation failed");
   }
-  if (stage_bytes && !d.side.cst) {
-    if (cudaStreamCreateWithFlags(&d.side.cst, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&d.side.cfork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&d.side.cjoin, cudaEventDisableTiming) != cudaSuccess)
-      return fail(SRTM_ERR_CUDA, "copy stream creation failed");
-  }
   const Layout L = make_layout(c.nx, c.ny, c.max_ratio, c.n_seq, c.total_slow, prec, tile_f, tile_s, c.nu,
-                               c.recover_split ? rscr_bytes : 0, stage_bytes);
+                               c.recover_split ? rscr_bytes : 0);
   if (d.ws_bytes < L.total) {
     if (d.ws) {
       cudaDeviceSynchronize();
@@ -369,22 +343,8 @@ int run(Ctx c, srtm_precision prec, cudaStream_t st, bool host_outputs = false) 
   c.tile_f = tile_f;
   c.tile_s = tile_s;
   c.setup_separate = t.setup_mode == 2 ? 1 : 0;
-  if (stage_bytes) {  // redirect the host outputs to their staging buffers
-    size_t so = L.stage;
-    for (int i = 0; i < 8; ++i) {
-      if (!*outp[i] || is_device_ptr(*outp[i])) continue;
-      const int k = c.copy.n++;
-      c.copy.dst[k] = (double*)mapped_host_ptr(*outp[i]);
-      c.copy.src[k] = (const double*)(w + so);
-      c.copy.width[k] = width[i];
-      c.copy.slow[k] = slowrow[i];
-      *outp[i] = (double*)(w + so);
-      so += a256(sizeof(double) * (size_t)width[i] * (size_t)(slowrow[i] ? c.total_slow : c.total_fast));
-    }
-  }
-  if (c.n_chunks > 1 || c.copy.n) chunk_grids(c, t, d.sms, &sh);
-  const int per_chunk = 2 + (c.smoothing ? 1 : 0) + c.setup_separate + (c.copy.n ? 1 : 0);  // scans, setup,
-                                                                                             // recovery, copy
+  if (c.n_chunks > 1) chunk_grids(c, t, d.sms, &sh);
+  const int per_chunk = 2 + (c.smoothing ? 1 : 0) + c.setup_separate;  // scans, setup, recovery
   d.last_launches = (c.fold_meta ? 0 : 1) + 1 + per_chunk * c.n_chunks + (c.loglik ? 1 : 0) + (c.nu > 0 ? 1 : 0) +
                     c.recover_split;
   if (c.split_mode == 1) d.last_launches = 2;                                    // constants, reducing filter scan
@@ -402,8 +362,7 @@ int run(Ctx c, srtm_precision prec, cudaStream_t st, bool host_outputs = false) 
   }
   rc = launch_meta(c, st, ev);
   if (rc) return fail(rc, "launch of the metadata kernel failed: %s", cudaGetErrorString(cudaGetLastError()));
-  rc = launch_for(c.nx, c, prec, sh, st, ev ? ev + 2 : nullptr,
-                  (c.recover_split || c.n_chunks > 1 || c.copy.n) ? &d.side : nullptr);
+  rc = launch_for(c.nx, c, prec, sh, st, ev ? ev + 2 : nullptr, (c.recover_split || c.n_chunks > 1) ? &d.side : nullptr);
   if (rc) return fail(rc, "launch of the constants/scan/recovery kernels failed (scan smem %zu/%zu bytes)", sh.smem_f,
                       sh.smem_s);
   return SRTM_OK;
@@ -858,9 +817,7 @@ int srtm_release(void) {
     if (g_dev[d].side.st) cudaStreamDestroy(g_dev[d].side.st);
     if (g_dev[d].side.fork) cudaEventDestroy(g_dev[d].side.fork);
     if (g_dev[d].side.join) cudaEventDestroy(g_dev[d].side.join);
-    if (g_dev[d].side.cst) cudaStreamDestroy(g_dev[d].side.cst);
-    if (g_dev[d].side.cfork) cudaEventDestroy(g_dev[d].side.cfork);
-    if (g_dev[d].side.cjoin) cudaEventDestroy(g_dev[d].side.cjoin);
+
 
     for (int i = 0; i < NEVENT; ++i)
       if (g_dev[d].ev[i]) cudaEventDestroy(g_dev[d].ev[i]);

@@ -61,7 +61,8 @@ struct ModelLayout {
   long long m1;    // n           m^f_{1,l}
   long long P1;    // n^2         P^f_{1,l}
   long long Q;     // n^2         copy of Q
-  long long Cf;    // float copies of A, Qc_1, Cov(e_1,e_l) (n^2 each) and V_1 H^T (n x m, ld m)
+  long long Cf;    // float copies of A, Qc_1, Cov(e_1,e_l) (n^2 each), V_1 H^T, K and C_bar^T R_x^-1
+                   // (n x m each, ld m, at n x MY strides)
   long long AB;    // L n MU      A^j B   (j = 0..L-1), n x nu blocks (ld nu)      [inputs]
   long long SB;    // L n MU      S_j B = sum_{i<=j} A^i B                         [inputs]
   long long stride;
@@ -87,7 +88,7 @@ __host__ __device__ inline ModelLayout make_model_layout(int n, int m, int L) {
   ml.m1 = o;   o += n;
   ml.P1 = o;   o += nn;
   ml.Q = o;    o += nn;
-  ml.Cf = o;   o += (3 * nn + (long long)n * MY + 1) / 2;
+  ml.Cf = o;   o += (3 * nn + 3LL * n * MY + 1) / 2;
   ml.AB = o;   o += (long long)L * n * SRTM_MAX_NU;
   ml.SB = o;   o += (long long)L * n * SRTM_MAX_NU;
   ml.stride = (o + 31) / 32 * 32;
@@ -144,18 +145,6 @@ struct SL {
   static constexpr int SIZE = 2 * NN + NX;
 };
 
-// Host outputs of a batch: the kernels write device staging buffers of the
-// same layout, and each chunk's rows are copied to the host buffers by a
-// streaming copy kernel once the chunk's recovery is done.
-constexpr int MAXCOPY = 8;
-struct CopyOut {
-  int n;                        // staged outputs (0: none)
-  double* dst[MAXCOPY];         // the device's address of the caller's pinned host buffer
-  const double* src[MAXCOPY];   // its staging buffer in the workspace
-  int width[MAXCOPY];           // doubles per row
-  int slow[MAXCOPY];            // 1: one row per slow step, 0: one row per fast step
-};
-
 // Everything a kernel needs; passed by value.
 struct Ctx {
   int n_seq, nx, ny, max_ratio;
@@ -202,7 +191,6 @@ struct Ctx {
   int reduce_only;         // this scan launch forms only the range's aggregate (written to agg_out)
   double* agg_out;         // float64 aggregate of the range (filter: FL layout, smoother: SL layout)
   const double *next_mean, *next_cov;  // smoothed x_{k+1,1} after the range's last interval (mode 3)
-  CopyOut copy;            // staged host outputs of a batch
   void* rscr;            // [RecScr::SIZE][total_fast] filtered moments between the two halves (recovery type)
 };
 
@@ -220,8 +208,6 @@ struct RecScr {
 struct SideStream {
   cudaStream_t st;
   cudaEvent_t fork, join;
-  cudaStream_t cst;           // third stream: copies of staged host outputs
-  cudaEvent_t cfork, cjoin;
 };
 
 // ---------------------------------------------------------------------------
@@ -284,8 +270,6 @@ int launch_device_path(const Ctx& c, srtm_precision prec, const Shapes& sh, cuda
 
 // sums the per-interval terms into the caller's log-likelihood output (meta.cu)
 int launch_loglik(const Ctx& c, cudaStream_t st);
-// copies the current chunk's rows of every staged host output (meta.cu)
-int launch_copy_out(const Ctx& c, cudaStream_t st);
 // bounded wait on a flag that nothing sets (failure-detection self-test, meta.cu)
 int launch_wait_probe(Counters* ctr, long long polls, cudaStream_t st);
 

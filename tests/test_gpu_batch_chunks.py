@@ -153,10 +153,10 @@ def test_chunked_equals_one_chunk_to_rounding(precision):
 
 
 @pytest.mark.parametrize("chunks", [1, 5])
-def test_batch_host_outputs_are_staged_and_copied_out(oracle_mod, chunks):
+def test_batch_host_outputs_written_over_the_link(oracle_mod, chunks):
     """Pinned host outputs of a batch (smoothed and filtered, fast and slow,
-    and the log likelihood) are written to device staging and copied out chunk
-    by chunk on a third stream: every output of every sequence against the
+    and the log likelihood), written by the kernels over the CPU-GPU link, in
+    one piece and in chunks: every output of every sequence against the
     oracle, also when the host buffers start 8 bytes past a 16-byte boundary."""
     import torch
 
