@@ -374,6 +374,10 @@ __global__ void __launch_bounds__(PRE_THREADS) precompute_kernel(Ctx c, int tabl
     md[L.Dc + e] = sm[S::Dc + e];
     md[L.Jc + e] = sm[S::Jc + e];
     md[L.P1 + e] = sm[S::P1o + e];
+    float* cf = (float*)(md + L.Cf) + 3 * NN + 3 * NX * MY;  // float copies for the float32 filter elements
+    cf[e] = (float)sm[S::Fc + e];
+    cf[NN + e] = (float)sm[S::Dc + e];
+    cf[2 * NN + e] = (float)sm[S::Jc + e];
   }
   for (int e = tid; e < NX * m; e += nt) {
     md[L.K + e] = sm[S::K + e];

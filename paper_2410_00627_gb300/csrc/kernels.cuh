@@ -540,10 +540,19 @@ struct FilterOp {
       }
       return;
     }
-    for (int e = g.lane; e < NN; e += G) {
-      x[L::F + e] = (T)md[c.ml.Fc + e];
-      x[L::D + e] = (T)md[c.ml.Dc + e];
-      x[L::J + e] = (T)md[c.ml.Jc + e];
+    if constexpr (sizeof(T) == sizeof(double)) {
+      for (int e = g.lane; e < NN; e += G) {
+        x[L::F + e] = (T)md[c.ml.Fc + e];
+        x[L::D + e] = (T)md[c.ml.Dc + e];
+        x[L::J + e] = (T)md[c.ml.Jc + e];
+      }
+    } else {  // the model's float copies (no float64 conversion per element)
+      const float* cfe = (const float*)(md + c.ml.Cf) + 3 * NN + 3 * NX * MY;
+      for (int e = g.lane; e < NN; e += G) {
+        x[L::F + e] = cfe[e];
+        x[L::D + e] = cfe[NN + e];
+        x[L::J + e] = cfe[2 * NN + e];
+      }
     }
     const int m = c.ny;
     const long long row = c.meta.off_slow[s] + p;

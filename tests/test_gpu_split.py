@@ -207,3 +207,35 @@ def test_two_processes_exchange_aggregates_over_gloo(oracle_mod):
             return self.a
     res = [({k: _T(v) for k, v in got[r][0].items()}, {k: _T(v) for k, v in got[r][1].items()}) for r in range(2)]
     _check_ranges(oracle_mod, prob, res, 2, "fp64", "gloo")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_full_size_chain4_split_boundaries(oracle_mod, precision):
+    """chain4 at 10^4 slow steps over 4 ranges (many scan tiles per range): the
+    fast outputs of the two intervals on each side of every range boundary,
+    the sequence's first and last intervals, and every smoothed x_{k,1},
+    against the oracle of the whole sequence."""
+    from paper_2410_00627_gb300 import api, split
+    prob = synth.chain4(seed=9, n_slow=10_000, keep_states=False)
+    l, N = prob.ratio, prob.n_slow
+    parts = 4
+    res = split.smoother_split_serial(*_model(prob), to_dev(prob.y), l, parts, precision,
+                                      filtered=api.OUTPUT_KEYS)
+    api.status()
+    rg = split.ranges(N, parts)
+    sm = {k: np.concatenate([res[r][0][k].cpu().numpy() for r in range(parts)]) for k in api.OUTPUT_KEYS}
+    fi = {k: np.concatenate([res[r][1][k].cpu().numpy() for r in range(parts)]) for k in api.OUTPUT_KEYS}
+    tm, tc = TOL[precision]
+    windows = [(0, 2), (N - 2, N)] + [(hi - 2, hi + 2) for _, hi in rg[:-1]]
+    for k0, k1 in windows:
+        o = oracle_mod.sequential(prob, k_lo=k0, k_hi=k1, slow=False)
+        sl = slice(k0 * l, k1 * l)
+        compare({"fast_mean": sm["fast_mean"][sl], "fast_cov": sm["fast_cov"][sl]},
+                {"fast_mean": o["fast_smooth_mean"], "fast_cov": o["fast_smooth_cov"]}, tm, tc, f"smoothed {k0}")
+        compare({"fast_mean": fi["fast_mean"][sl], "fast_cov": fi["fast_cov"][sl]},
+                {"fast_mean": o["fast_filt_mean"], "fast_cov": o["fast_filt_cov"]}, tm, tc, f"filtered {k0}")
+    seq = oracle_mod.sequential(prob, fast=False)
+    compare({"first_mean": sm["fast_mean"][0::l], "first_cov": sm["fast_cov"][0::l]},
+            {"first_mean": seq["first_smooth_mean"], "first_cov": seq["first_smooth_cov"]}, tm, tc, "x_(k,1)")
+    compare({"slow_mean": fi["slow_mean"], "slow_cov": fi["slow_cov"]},
+            {"slow_mean": seq["slow_filt_mean"], "slow_cov": seq["slow_filt_cov"]}, tm, tc, "filtered slow")
