@@ -155,6 +155,8 @@ def reduce_over_ranks(mean_ms, units, dist, device):
     if dist is None:
         return float(mean_ms), float(units)
     import torch
+    if dist.get_backend() == "gloo":
+        device = "cpu"
     t = torch.tensor([float(mean_ms)], dtype=torch.float64, device=device)
     u = torch.tensor([float(units)], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -1108,8 +1110,10 @@ def main():
     if world > 1:
         import torch.distributed as dist
         local = int(os.environ.get("LOCAL_RANK", "0"))
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", init_method="env://")
+        torch.cuda.set_device(local % torch.cuda.device_count())
+        # NCCL between GPUs; SRTM_DIST_BACKEND=gloo runs the ranks' host-side
+        # reductions over gloo (e.g. several ranks sharing one GPU)
+        dist.init_process_group(os.environ.get("SRTM_DIST_BACKEND", "nccl"), init_method="env://")
     line = (run_batched if args.workload == "ragged_chains" else run_ours)(args, rank, world, dist)
     if args.workload == "ragged_chains" and world == 1 and not args.no_chain4 and not args.no_extras:
         import copy

@@ -386,6 +386,11 @@ __global__ void __launch_bounds__(PRE_THREADS) precompute_kernel(Ctx c, int tabl
     cf[3 * NN + NX * MY + e] = (float)sm[S::K + e];
     cf[3 * NN + 2 * NX * MY + e] = (float)sm[S::Cr + e];
   }
+  {  // float copies of C_bar and R_x for the rank-m filter combine
+    float* cf = (float*)(md + L.Cf) + 6 * NN + 3 * NX * MY;
+    for (int e = tid; e < m * NX; e += nt) cf[e] = (float)sm[S::Cb + e];
+    for (int e = tid; e < m * m; e += nt) cf[MY * NX + e] = (float)sm[S::Rx + e];
+  }
   for (int e = tid; e < m * m; e += nt) md[L.Rx + e] = sm[S::Rx + e];
   for (int e = tid; e < NX; e += nt) md[L.m1 + e] = sm[S::m1 + e];
   if (tid == 0 && !s_ok) atomicOr(&c.ctr->err, DEVERR_SINGULAR);

@@ -23,22 +23,26 @@ struct SetupGeom {
   static constexpr int SG = NX == 1 ? 1 : (NX == 2 ? 2 : (NX <= 4 ? 4 : 8));
   static constexpr int NN = NX * NX, NM = NX * MY, UA = NM > NN ? NM : NN;
   // slot layout in TR; Aml, AP1 and P11 reuse Pll, AP and Pm, whose last
-  // reads precede them, and AP also holds the 2x2 minors of P^- (NX = 4)
-  static constexpr int P = 0, mv = P + NN, X = mv + NX, SUl = X + NM, ml = SUl + NM, Pl = ml + NX, Pll = Pl + NN,
-                       AP = Pll + NN, Pm = AP + NN, Z = Pm + NN, U1 = Z + NN, P1l = U1 + NM, Sy = P1l + NN,
+  // reads precede them, and AP also holds the 2x2 minors of P^- (NX = 4).
+  // Everything from Pll on is dead once the record is written.
+  static constexpr int P = 0, mv = P + NN, X = mv + NX, SUl = X + NM, ml = SUl + NM, Pl = ml + NX, Z = Pl + NN,
+                       Pll = Z + NN, AP = Pll + NN, Pm = AP + NN, U1 = Pm + NN, P1l = U1 + NM, Sy = P1l + NN,
                        ev = Sy + MY * MY, SLOT = ev + MY;
   static constexpr int Aml = Pll, AP1 = AP, P11 = Pm;
-  // float region of a slot (mixed mode: the smoother elements in float32):
-  // float copies of P, Pl, X, SUl, Z, m^f_l, m, then U1 (later A P1l^T, so
-  // max(NM, NN) entries), P1l, P11, A m^f_l
+  // float region of a slot (mixed mode: the smoother elements in float32),
+  // laid over the TR entries from Pll on: float copies of P, Pl, X, SUl, Z,
+  // m^f_l, m, then U1 (later A P1l^T, so max(NM, NN) entries), P1l, P11,
+  // A m^f_l
+  static constexpr int FREG = Pll;
   static constexpr int fP = 0, fPl = fP + NN, fX = fPl + NN, fSUl = fX + NM, fZ = fSUl + NM, fml = fZ + NN,
                        fmv = fml + NX, fU1 = fmv + NX, fP1l = fU1 + UA, fP11 = fP1l + NN, fAml = fP11 + NN,
                        SLOTF = fAml + NX;
+  static_assert(SLOTF * sizeof(float) <= (SLOT - FREG) * sizeof(double), "float region exceeds its TR space");
   // the model's float copies (model table, ModelLayout::Cf): A, Qc_1, Cov(e_1, e_l), V_1 H^T
   static constexpr int cA = 0, cQc = NN, cQl = 2 * NN, cVH = 3 * NN;
   template <class T, class TR>
   __host__ __device__ static constexpr size_t slot_bytes() {
-    return ((SLOT * sizeof(TR) + 15) / 16) * 16 + (sizeof(T) != sizeof(TR) ? ((SLOTF * sizeof(T) + 15) / 16) * 16 : 0);
+    return ((SLOT * sizeof(TR) + 15) / 16) * 16;
   }
 };
 
@@ -467,7 +471,9 @@ __device__ void setup_interval(const Ctx& c, long long gi, int lane, unsigned ma
                                         sb + Gm::Aml, sb + Gm::AP1, se, ui ? ui + UIn<NX>::b1 : nullptr,
                                         ui ? ui + UIn<NX>::bn : nullptr);
     } else {
-      // float copies of this lane's rows, then the elements in float32
+      // float copies of this lane's rows (over the slot's dead TR entries,
+      // after every lane's record reads of Pm), then the elements in float32
+      __syncwarp(mask);
       if (row) {
 #pragma unroll
         for (int q = 0; q < NX; ++q) {
@@ -503,6 +509,215 @@ __device__ void setup_interval(const Ctx& c, long long gi, int lane, unsigned ma
 }
 
 // ===========================================================================
+// Filter operator of Eq. (27) with a generic element of Eq. (26) on the
+// right.  Its J_j = C_bar^T R_x^-1 C_bar has rank m < NX (and eta_j =
+// C_bar^T R_x^-1 (y_k - c_k)), so by the matrix inversion lemma
+//   (I + D_i J_j)^{-1} = I - K C_bar,   S = R_x + C_bar D_i C_bar^T,
+//   K = D_i C_bar^T S^{-1},
+// and the n x n solve of the general combine becomes the m x m one of S:
+//   u = (I - K C_bar)(d_i + D_i eta_j),          d_ij = F_j u + d_j,
+//   D_ij = F_j (D_i - K C_bar D_i) F_j^T + D_j,
+//   V = (I - K C_bar) F_i = F_i - K G,  G = C_bar F_i,   F_ij = F_j V,
+//   eta_ij = V^T (eta_j - J_j d_i) + eta_i,
+//   J_ij = V^T J_j F_i + J_i = G^T S^{-1} G + J_i
+// (the last because (I - K C_bar)^T C_bar^T R_x^-1 = C_bar^T S^{-1}).  This
+// is the measurement update of the left operand by the interval's
+// measurement followed by the element's transition; Eq. (27) is the same map
+// for a general right operand.  S^{-1}: for m = 1 the reciprocal of one value
+// of type T, correctly rounded in T (which equals the float64 reciprocal
+// rounded once to T); for m = 2 the adjugate over det S, with det S (the one
+// step that can cancel) formed in TS (float64 in the mixed mode) from the
+// exact products of the T entries, and its reciprocal rounded once to T; for
+// m > 2 the whole inverse in TS.  Cb (m x NX, ld NX) and Rx (m x m, ld m)
+// hold the model's C_bar and R_x in T.  prefix as in g_filter_combine.
+// Scratch: sc (T) RankScr<NX>::SIZE.
+// ===========================================================================
+template <int NX>
+struct RankScr {
+  static constexpr int NN = NX * NX, NM = NX * MY;
+  static constexpr int CD = 0, Kt = CD + NM, Gm = Kt + NM, SiG = Gm + NM, t = SiG + NM, x = t + NX, Ct = x + NX,
+                       Si = Ct + MY, Pu = Si + MY * MY, FP = Pu + NN, V = FP + NN, SIZE = V + NN;
+};
+
+template <int NX, int G, class T, class TS>
+__device__ __forceinline__ bool g_filter_combine_rank(const Grp<G>& g, T* o, const T* a, const T* b, T* sc,
+                                                      const T* Cb, const T* Rx, int m, bool prefix) {
+  using L = FL<NX>;
+  using R = RankScr<NX>;
+  constexpr int NN = NX * NX, NT = NX * (NX + 1) / 2;
+  T *CD = sc + R::CD, *Kt = sc + R::Kt, *Gm = sc + R::Gm, *SiG = sc + R::SiG, *t = sc + R::t, *x = sc + R::x;
+  T *Ct = sc + R::Ct, *Si = sc + R::Si, *Pu = sc + R::Pu, *FP = sc + R::FP, *V = sc + R::V;
+  const int mn = m * NX;
+  // 1. CD = C_bar D_i, t = d_i + D_i eta_j; without prefix also G = C_bar F_i
+  //    and x = eta_j - J_j d_i
+  const int n1 = prefix ? mn + NX : 2 * mn + 2 * NX;
+  for (int e = g.lane; e < n1; e += G) {
+    if (e < mn) {
+      const int j = e / NX, q = e - (e / NX) * NX;
+      T v = T(0);
+#pragma unroll
+      for (int k = 0; k < NX; ++k) v = fma(Cb[j * NX + k], a[L::D + k * NX + q], v);
+      CD[e] = v;
+    } else if (e < mn + NX) {
+      const int r = e - mn;
+      T v = a[L::d + r];
+#pragma unroll
+      for (int k = 0; k < NX; ++k) v = fma(a[L::D + r * NX + k], b[L::e + k], v);
+      t[r] = v;
+    } else if (e < 2 * mn + NX) {
+      const int f = e - mn - NX, j = f / NX, q = f - (f / NX) * NX;
+      T v = T(0);
+#pragma unroll
+      for (int k = 0; k < NX; ++k) v = fma(Cb[j * NX + k], a[L::F + k * NX + q], v);
+      Gm[f] = v;
+    } else {
+      const int r = e - 2 * mn - NX;
+      T v = b[L::e + r];
+#pragma unroll
+      for (int k = 0; k < NX; ++k) v = fma(-b[L::J + r * NX + k], a[L::d + k], v);
+      x[r] = v;
+    }
+  }
+  g.sync();
+  // 2. S = R_x + CD C_bar^T (exactly symmetric) and S^{-1}, on every lane in
+  //    registers, stored by lane 0 (ld MY); Ct = C_bar t
+  bool ok = true;
+  auto rcp = [](T v) -> T {
+    if constexpr (sizeof(T) == sizeof(float)) return __frcp_rn(v);
+    else return T(1) / v;
+  };
+  if (m == 1) {
+    T s = Rx[0];
+#pragma unroll
+    for (int k = 0; k < NX; ++k) s = fma(CD[k], Cb[k], s);
+    if (bad_value(s)) { ok = false; s = T(1); }
+    if (g.lane == 0) Si[0] = rcp(s);
+  } else if (m == 2) {
+    T s00 = Rx[0], s01 = Rx[1], s11 = Rx[3];
+#pragma unroll
+    for (int k = 0; k < NX; ++k) {
+      s00 = fma(CD[k], Cb[k], s00);
+      s01 = fma(CD[k], Cb[NX + k], s01);
+      s11 = fma(CD[NX + k], Cb[NX + k], s11);
+    }
+    const TS t01 = (TS)s01;
+    T det = (T)fma((TS)s00, (TS)s11, -(t01 * t01));
+    if (bad_value(det)) { ok = false; det = T(1); }
+    const T id = rcp(det);
+    if (g.lane == 0) {
+      Si[0] = s11 * id;
+      Si[1] = -s01 * id;
+      Si[MY] = -s01 * id;
+      Si[MY + 1] = s00 * id;
+    }
+  } else {
+    TS S[MY][MY], Sinv[MY][MY];
+#pragma unroll
+    for (int i = 0; i < MY; ++i)
+#pragma unroll
+      for (int j = i; j < MY; ++j) {
+        T v = T(0);
+        if (j < m) {
+          v = Rx[i * m + j];
+#pragma unroll
+          for (int k = 0; k < NX; ++k) v = fma(CD[i * NX + k], Cb[j * NX + k], v);
+        }
+        S[i][j] = (TS)v;
+        S[j][i] = (TS)v;
+      }
+    ok = small_sym_inverse<TS>(S, Sinv, m);
+    if (g.lane == 0)
+#pragma unroll
+      for (int i = 0; i < MY; ++i)
+#pragma unroll
+        for (int j = 0; j < MY; ++j)
+          if (i < m && j < m) Si[i * MY + j] = (T)Sinv[i][j];
+  }
+  for (int j = g.lane; j < m; j += G) {
+    T v = T(0);
+#pragma unroll
+    for (int k = 0; k < NX; ++k) v = fma(Cb[j * NX + k], t[k], v);
+    Ct[j] = v;
+  }
+  g.sync();
+  // 3. K^T = S^{-1} CD; without prefix also S^{-1} G
+  const int n3 = prefix ? mn : 2 * mn;
+  for (int e = g.lane; e < n3; e += G) {
+    const bool second = e >= mn;
+    const int f = second ? e - mn : e, j = f / NX, q = f - (f / NX) * NX;
+    const T* src = second ? Gm : CD;
+    T v = T(0);
+    for (int i = 0; i < m; ++i) v = fma(Si[j * MY + i], src[i * NX + q], v);
+    (second ? SiG : Kt)[f] = v;
+  }
+  g.sync();
+  // 4. u = t - K Ct (over t); P = D_i - K CD (upper, mirrored); without prefix
+  //    also J_ij = G^T S^{-1} G + J_i (upper, mirrored) and V = F_i - K G
+  const int n4 = prefix ? NX + NT : NX + 2 * NT + NN;
+  for (int e = g.lane; e < n4; e += G) {
+    if (e < NX) {
+      T v = t[e];
+      for (int j = 0; j < m; ++j) v = fma(-Kt[j * NX + e], Ct[j], v);
+      t[e] = v;
+    } else if (e < NX + NT) {
+      int r, q;
+      tri_rc<NX>(e - NX, r, q);
+      T v = a[L::D + r * NX + q];
+      for (int j = 0; j < m; ++j) v = fma(-Kt[j * NX + r], CD[j * NX + q], v);
+      Pu[r * NX + q] = v;
+      Pu[q * NX + r] = v;
+    } else if (e < NX + 2 * NT) {
+      int r, q;
+      tri_rc<NX>(e - NX - NT, r, q);
+      T v = a[L::J + r * NX + q];
+      for (int j = 0; j < m; ++j) v = fma(Gm[j * NX + r], SiG[j * NX + q], v);
+      o[L::J + r * NX + q] = v;
+      o[L::J + q * NX + r] = v;
+    } else {
+      const int f = e - NX - 2 * NT, r = f / NX, q = f - (f / NX) * NX;
+      T v = a[L::F + f];
+      for (int j = 0; j < m; ++j) v = fma(-Kt[j * NX + r], Gm[j * NX + q], v);
+      V[f] = v;
+    }
+  }
+  g.sync();
+  // 5. d_ij = F_j u + d_j, FP = F_j P; without prefix also F_ij = F_j V and
+  //    eta_ij = V^T x + eta_i
+  const int n5 = prefix ? NX + NN : 2 * NX + 2 * NN;
+  for (int e = g.lane; e < n5; e += G) {
+    if (e < NX) {
+      T v = b[L::d + e];
+#pragma unroll
+      for (int k = 0; k < NX; ++k) v = fma(b[L::F + e * NX + k], t[k], v);
+      o[L::d + e] = v;
+    } else if (e < NX + 2 * NN) {
+      const bool second = e >= NX + NN;
+      const int f = e - NX - (second ? NN : 0), r = f / NX, q = f - (f / NX) * NX;
+      const T* src = second ? V : Pu;
+      T v = T(0);
+#pragma unroll
+      for (int k = 0; k < NX; ++k) v = fma(b[L::F + r * NX + k], src[k * NX + q], v);
+      (second ? o + L::F : FP)[f] = v;
+    } else {
+      const int r = e - NX - 2 * NN;
+      T v = a[L::e + r];
+#pragma unroll
+      for (int k = 0; k < NX; ++k) v = fma(V[k * NX + r], x[k], v);
+      o[L::e + r] = v;
+    }
+  }
+  g.sync();
+  // 6. D_ij = FP F_j^T + D_j (upper, mirrored)
+  g_mm_sym<NX, G, false, true, T>(g, o + L::D, FP, b + L::F, b + L::D);
+  if (prefix) {
+    for (int e = g.lane; e < NN; e += G) { o[L::F + e] = T(0); o[L::J + e] = T(0); }
+    for (int e = g.lane; e < NX; e += G) o[L::e + e] = T(0);
+  }
+  g.sync();
+  return ok;
+}
+
+// ===========================================================================
 // scan operators
 // ===========================================================================
 
@@ -515,12 +730,42 @@ struct FilterOp {
   using L = FL<NX>;
   static constexpr int G = GroupSize<NX>::value;
   static constexpr int ES = L::SIZE;
-  static constexpr int SCR = 5 * NX * NX + 2 * NX;
+  // group scratch: the combines' work arrays, then the model's C_bar and R_x
+  // in T for the rank-m combine (loaded once per tile)
+  static constexpr int SCR_GEN = 5 * NX * NX + 2 * NX;
+  static constexpr int SCR_OPS = SCR_GEN > RankScr<NX>::SIZE ? SCR_GEN : RankScr<NX>::SIZE;
+  static constexpr int CB = SCR_OPS, RX = CB + MY * NX;
+  static constexpr int SCR = RX + MY * MY;
   static constexpr int SCRS = NX * NX + 12;
   static constexpr int TICKET = 0;
 
   __device__ static bool combine(const Grp<G>& g, T* o, const T* left, const T* right, T* sc, TS* scs,
                                  bool prefix) {
+    return g_filter_combine<NX, G, T, TS>(g, o, left, right, sc, scs, prefix);
+  }
+  // the measurement sizes below NX take the rank-m combine for a generic right element
+  __device__ static bool rank_form(const Ctx& c) { return c.ny < NX; }
+  // before a tile of sequence s: C_bar and R_x into the group scratch (read
+  // after the group barrier that precedes the tile's first combine)
+  __device__ static void tile_begin(const Grp<G>& g, T* sc, const Ctx& c, int s) {
+    if (!rank_form(c)) return;
+    const int m = c.ny;
+    const double* md = c.model + (long long)s * c.ml.stride;
+    if constexpr (sizeof(T) == sizeof(double)) {
+      for (int e = g.lane; e < m * NX; e += G) sc[CB + e] = (T)md[c.ml.Cb + e];
+      for (int e = g.lane; e < m * m; e += G) sc[RX + e] = (T)md[c.ml.Rx + e];
+    } else {
+      const float* cf = (const float*)(md + c.ml.Cf) + 6 * NX * NX + 3 * NX * MY;
+      for (int e = g.lane; e < m * NX; e += G) sc[CB + e] = cf[e];
+      for (int e = g.lane; e < m * m; e += G) sc[RX + e] = cf[MY * NX + e];
+    }
+  }
+  // left (x) right where right is the element loaded for scan position p:
+  // every element but the sequence's first one is generic
+  __device__ static bool combine_elem(const Grp<G>& g, T* o, const T* left, const T* right, T* sc, TS* scs,
+                                      bool prefix, const Ctx& c, long long p) {
+    if (rank_form(c) && (p > 0 || c.split_head_generic))
+      return g_filter_combine_rank<NX, G, T, TS>(g, o, left, right, sc, sc + CB, sc + RX, c.ny, prefix);
     return g_filter_combine<NX, G, T, TS>(g, o, left, right, sc, scs, prefix);
   }
   __device__ static void identity(const Grp<G>& g, T* x) {  // (I, 0, 0, 0, 0)
@@ -621,7 +866,7 @@ struct FilterOp {
     if (slot < per_round) {
       unsigned char* sl = slots + (size_t)slot * Gm::template slot_bytes<T, TS>();
       TS* sb = (TS*)sl;
-      T* sf = FLOAT_ELEMENTS ? (T*)(sl + align16(Gm::SLOT * sizeof(TS))) : nullptr;
+      T* sf = FLOAT_ELEMENTS ? (T*)(sb + Gm::FREG) : nullptr;
       // compiled per measurement size, as the separate setup kernel
       for (int j = slot; j < count; j += per_round) {
         const TS* pv = j == 0 ? prevb : nullptr;
@@ -664,6 +909,11 @@ struct SmootherOp {
   __device__ static bool combine(const Grp<G>& g, T* o, const T* left, const T* right, T* sc, TS*, bool prefix) {
     g_smoother_combine<NX, G, T>(g, o, right, left, sc, prefix);
     return true;
+  }
+  __device__ static void tile_begin(const Grp<G>&, T*, const Ctx&, int) {}
+  __device__ static bool combine_elem(const Grp<G>& g, T* o, const T* left, const T* right, T* sc, TS* scs,
+                                      bool prefix, const Ctx&, long long) {
+    return combine(g, o, left, right, sc, scs, prefix);
   }
   __device__ static void identity(const Grp<G>& g, T* x) {  // (I, 0, 0)
     for (int e = g.lane; e < ES; e += G) x[e] = (e < NX * NX && e / NX == e % NX) ? T(1) : T(0);
@@ -992,6 +1242,7 @@ __global__ void __launch_bounds__(256) scan_kernel(Ctx c, int NG, int E, int W) 
     T* cur = b0;
     T* el = b1;
     T* tmp = b2;
+    Op::tile_begin(g, sc, c, s);
     if (cnt == 0) {
       Op::identity(g, cur);
     } else {
@@ -1000,7 +1251,7 @@ __global__ void __launch_bounds__(256) scan_kernel(Ctx c, int NG, int E, int W) 
         g.sync();
         Op::load(g, el, c, s, p0 + e, N);
         g.sync();
-        ok &= Op::combine(g, tmp, cur, el, sc, scs, false);
+        ok &= Op::combine_elem(g, tmp, cur, el, sc, scs, false, c, p0 + e);
         T* x = cur; cur = tmp; tmp = x;
       }
     }
@@ -1041,7 +1292,7 @@ __global__ void __launch_bounds__(256) scan_kernel(Ctx c, int NG, int E, int W) 
       for (int e = 0; e < cnt; ++e) {
         Op::load(g, b1, c, s, p0 + e, N);
         g.sync();
-        ok &= Op::combine(g, nx, st, b1, sc, scs, true);
+        ok &= Op::combine_elem(g, nx, st, b1, sc, scs, true, c, p0 + e);
         T* x = st; st = nx; nx = x;
         Op::store(g, st, c, s, p0 + e, N, sc, scs);
         g.sync();
@@ -1476,7 +1727,7 @@ __global__ void __launch_bounds__(128) setup_kernel(Ctx c) {
   }
   const unsigned mask = (SG == 32) ? 0xffffffffu : (((1u << SG) - 1u) << ((threadIdx.x & 31) & ~(SG - 1)));
   unsigned char* sl = ssm + (size_t)slot * Gm::template slot_bytes<T, TS>();
-  T* sf = (sizeof(T) != sizeof(TS)) ? (T*)(sl + align16(Gm::SLOT * sizeof(TS))) : nullptr;
+  T* sf = (sizeof(T) != sizeof(TS)) ? (T*)((TS*)sl + Gm::FREG) : nullptr;
   // rounds of `per` intervals, one per lane group (uniform over the block),
   // then the round's records' P^f_{k-1,l} as LDL^T factors, one thread each
   for (long long base = g_lo + (long long)blockIdx.x * per; base < g_hi; base += (long long)gridDim.x * per) {

@@ -62,7 +62,8 @@ struct ModelLayout {
   long long P1;    // n^2         P^f_{1,l}
   long long Q;     // n^2         copy of Q
   long long Cf;    // float copies of A, Qc_1, Cov(e_1,e_l) (n^2 each), V_1 H^T, K and C_bar^T R_x^-1
-                   // (n x m each, ld m, at n x MY strides), then F, D, J of the generic element (n^2 each)
+                   // (n x m each, ld m, at n x MY strides), then F, D, J of the generic element (n^2 each),
+                   // C_bar (m x n, at an MY x n stride) and R_x (m x m, ld m)
   long long AB;    // L n MU      A^j B   (j = 0..L-1), n x nu blocks (ld nu)      [inputs]
   long long SB;    // L n MU      S_j B = sum_{i<=j} A^i B                         [inputs]
   long long stride;
@@ -88,7 +89,7 @@ __host__ __device__ inline ModelLayout make_model_layout(int n, int m, int L) {
   ml.m1 = o;   o += n;
   ml.P1 = o;   o += nn;
   ml.Q = o;    o += nn;
-  ml.Cf = o;   o += (6 * nn + 3LL * n * MY + 1) / 2;
+  ml.Cf = o;   o += (6 * nn + 4LL * n * MY + MY * MY + 1) / 2;
   ml.AB = o;   o += (long long)L * n * SRTM_MAX_NU;
   ml.SB = o;   o += (long long)L * n * SRTM_MAX_NU;
   ml.stride = (o + 31) / 32 * 32;
