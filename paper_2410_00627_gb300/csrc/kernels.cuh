@@ -24,25 +24,28 @@ struct SetupGeom {
   static constexpr int NN = NX * NX, NM = NX * MY, UA = NM > NN ? NM : NN;
   // slot layout in TR; Aml, AP1 and P11 reuse Pll, AP and Pm, whose last
   // reads precede them, and AP also holds the 2x2 minors of P^- (NX = 4).
-  // Everything from Pll on is dead once the record is written.
+  // Everything from Pll on is dead once the record is written; U1 and P1l
+  // are the work arrays of smoother elements formed in TR.
   static constexpr int P = 0, mv = P + NN, X = mv + NX, SUl = X + NM, ml = SUl + NM, Pl = ml + NX, Z = Pl + NN,
-                       Pll = Z + NN, AP = Pll + NN, Pm = AP + NN, U1 = Pm + NN, P1l = U1 + NM, Sy = P1l + NN,
-                       ev = Sy + MY * MY, SLOT = ev + MY;
+                       Pll = Z + NN, AP = Pll + NN, Pm = AP + NN, Sy = Pm + NN, ev = Sy + MY * MY, U1 = ev + MY,
+                       P1l = U1 + NM, SLOT = P1l + NN;
   static constexpr int Aml = Pll, AP1 = AP, P11 = Pm;
-  // float region of a slot (mixed mode: the smoother elements in float32),
-  // laid over the TR entries from Pll on: float copies of P, Pl, X, SUl, Z,
-  // m^f_l, m, then U1 (later A P1l^T, so max(NM, NN) entries), P1l, P11,
-  // A m^f_l
+  // float region of a slot (mixed mode: the smoother elements in float32,
+  // so U1 and P1l are not needed), laid over the TR entries from Pll on:
+  // float copies of P, Pl, X, SUl, Z, m^f_l, m, then U1 (later A P1l^T, so
+  // max(NM, NN) entries), P1l, P11, A m^f_l
   static constexpr int FREG = Pll;
   static constexpr int fP = 0, fPl = fP + NN, fX = fPl + NN, fSUl = fX + NM, fZ = fSUl + NM, fml = fZ + NN,
                        fmv = fml + NX, fU1 = fmv + NX, fP1l = fU1 + UA, fP11 = fP1l + NN, fAml = fP11 + NN,
                        SLOTF = fAml + NX;
-  static_assert(SLOTF * sizeof(float) <= (SLOT - FREG) * sizeof(double), "float region exceeds its TR space");
+  static constexpr int SLOT_MIXED_CORE = U1;                                // TR entries the mixed mode uses
+  static constexpr int SLOT_MIXED_FLOAT = FREG + (SLOTF * 4 + 7) / 8;       // end of the float region
+  static constexpr int SLOT_MIXED = SLOT_MIXED_CORE > SLOT_MIXED_FLOAT ? SLOT_MIXED_CORE : SLOT_MIXED_FLOAT;
   // the model's float copies (model table, ModelLayout::Cf): A, Qc_1, Cov(e_1, e_l), V_1 H^T
   static constexpr int cA = 0, cQc = NN, cQl = 2 * NN, cVH = 3 * NN;
   template <class T, class TR>
   __host__ __device__ static constexpr size_t slot_bytes() {
-    return ((SLOT * sizeof(TR) + 15) / 16) * 16;
+    return (((sizeof(T) != sizeof(TR) ? SLOT_MIXED : SLOT) * sizeof(TR) + 15) / 16) * 16;
   }
 };
 

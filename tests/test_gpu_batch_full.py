@@ -54,9 +54,12 @@ def test_ragged_chains_full_batch_sampled(oracle_mod, full_batch):
             g = torch.cuda.CUDAGraph()
             with torch.cuda.graph(g, stream=stream, capture_error_mode="relaxed"):
                 api.smoother_batch(batch, precision=precision, out=outs, stream=stream)
-            for v in outs.values():
-                v.fill_(float("nan"))
+            # the poison fill and the replay on one stream: a fill on another
+            # stream may run beside the replay's persistent scans and land
+            # after the recovery's stores
             with torch.cuda.stream(stream):   # replay() launches on the current stream
+                for v in outs.values():
+                    v.fill_(float("nan"))
                 g.replay()
             stream.synchronize()
             api.status(stream)
