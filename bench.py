@@ -81,7 +81,7 @@ def parse(argv=None):
     ap.add_argument("--no-autotune", action="store_true", help="keep the built-in launch shapes")
     ap.add_argument("--tuning", default=None,
                     help="explicit launch shapes scan_groups,scan_elems,recover_threads,lookback_window"
-                         "[,setup_mode,recover_split,batch_chunks,chunk_recover_bps,chunk_scan_bps] "
+                         "[,setup_mode,recover_split,batch_chunks,chunk_recover_bps,chunk_scan_bps,recover_form] "
                          "(for every precision; replaces the autotuner)")
     ap.add_argument("--tune-reps", type=int, default=2)
     ap.add_argument("--sweep", action="store_true",
@@ -274,7 +274,8 @@ def run_ours(args, rank, world, dist):
     roof = recovery_roofline(stage_mean, prob.nx, prob.ny, args.precision, prob.n_slow, n_fast,
                              recorded_traffic(args.precision, n_fast), peaks,
                              "stage events around the recovery launch(es) of direct calls, mean of the steps "
-                             "(a split recovery adds its two halves)")
+                             "(a split recovery adds its two halves)",
+                             api.get_tuning(prob.nx, args.precision)["recover_form"])
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak",
@@ -309,9 +310,18 @@ def run_ours(args, rank, world, dist):
     return line
 
 
-def recovery_fma(n, m):
+def recovery_fma(n, m, form=1):
     """FMAs per fast step of the smoothing recovery as the kernel executes them
-    (Remarks 1 and 3; a multiply counts as one): U_i (n^2 m), m^f_i (n^2 + n m),
+    (a multiply counts as one).
+
+    form 2 (two-point): the mean C1_i mu0 + C2_i mu1 + c3_i y_k (2 n^2 + n m),
+    W = C1_i E_k + C2_i (n^3), and two factored quadratic forms W P^s_{k+1,1}
+    W^T and C1_i S_k C1_i^T, each (W L) (n^2 (n-1)/2), its columns scaled by D
+    (n^2) and the upper triangle (n(n+1)/2 n); per fast step of an interval
+    with a successor (the last interval of a sequence, 1/N of the steps, takes
+    one quadratic form and no W).
+
+    form 1 (record form, Remarks 1 and 3): U_i (n^2 m), m^f_i (n^2 + n m),
     P^f_il (n^3 + n^2 m), U_i S_y^-1 (n m^2), A^i P A^iT with P = L D L^T from
     the record, (A^i L) D (A^i L)^T: A^i L (n^2 (n-1)/2), its columns scaled by
     D (n^2) and the upper triangle (n(n+1)/2 n, the n(n+1)/2 m of the gain term
@@ -319,34 +329,43 @@ def recovery_fma(n, m):
     Om = L D L^T (n^2 (n-1)/2 + n^2 + n(n+1)/2 n) and the smoothed mean (n^2).
     Products whose result is symmetric count their upper triangle only, as
     computed."""
+    if form == 2:
+        return 2 * n * n + n * m + n ** 3 + 2 * (n * n * (n - 1) // 2 + n * n + n * (n + 1) // 2 * n)
     return (n ** 3 + n * n * (n - 1) + n * (n + 1) // 2 * (2 * n + m) + 2 * n * n * m + n * m * m + 4 * n * n
             + n * m)
 
 
-def recovery_roofline(stage_ms, n, m, precision, n_slow, n_fast, traffic, peaks, timing):
+def recovery_roofline(stage_ms, n, m, precision, n_slow, n_fast, traffic, peaks, timing, form=1):
     """The roofline object of the dominant kernel (recover_kernel, bound by the
     float64 FMA pipe): algorithmic FLOPs per call over its event-timed duration,
     against the measured peak, with the per-phase fractions beside it."""
     key = "fp32" if precision == "fp32" else "fp64"
     rec_ms = stage_ms["recovery"] + stage_ms.get("recovery_filtered_half", 0.0)
-    achieved = 2.0 * recovery_fma(n, m) * n_fast / (rec_ms * 1e-3) / 1e9
+    achieved = 2.0 * recovery_fma(n, m, form) * n_fast / (rec_ms * 1e-3) / 1e9
     peak = peaks[f"{key}_gflops"]
     return {"bound": "alu", "kernel": "recover_kernel", "achieved": achieved, "peak": peak, "unit": "GFLOP/s",
             "frac": achieved / peak, "traffic": traffic,
             "peak_source": f"{key.upper()} FMA peak, {peaks['source']}",
-            "flops_per_fast_step": 2 * recovery_fma(n, m), "fast_steps_per_launch": n_fast, "timing": timing,
-            "phases": roofline_phases(stage_ms, n, m, precision, n_slow, n_fast, peaks)}
+            "recover_form": {1: "record", 2: "two-point"}[form],
+            "flops_per_fast_step": 2 * recovery_fma(n, m, form), "fast_steps_per_launch": n_fast, "timing": timing,
+            "phases": roofline_phases(stage_ms, n, m, precision, n_slow, n_fast, peaks, form)}
 
 
-def phase_fma(n, m, precision):
+def phase_fma(n, m, precision, form=1):
     """Algorithmic FMAs per slow step of the three slow-rate phases, split by
     the arithmetic type they run in (float64 or float32 in the mixed mode;
     every FMA in float64 in the FP64 mode, in float32 in the FP32 mode).
 
     filter scan (one Eq. 27 combine per element, the element build of Eq. 25-26
     and the interval setup run as its epilogue):
-      combine (25/3) n^3 + 5 n^2, of which the (I + D_i J_j) inverse (n^3) is
-      float64 in the mixed mode; element build 2 n m;
+      combine with a generic element (m < n, the matrix inversion lemma):
+      C_bar D_i, C_bar F_i (2 m n^2), D_i eta_j, J_j d_i (2 n^2), S (m^2 n),
+      S^-1 C_bar D_i, S^-1 G (2 m^2 n), u (n m), D_i - K C_bar D_i and
+      J_ij (upper, 2 n(n+1)/2 m), V (n^2 m), d_ij, eta_ij (2 n^2), F_j P,
+      F_j V (2 n^3), D_ij upper (n(n+1)/2 n); its m x m solve (m = 1: a
+      float32 reciprocal; m = 2: the float64 determinant, 2; m > 2: m^3) is
+      float64 in the mixed mode.  (m >= n: the general combine,
+      (25/3) n^3 + 5 n^2 with the n^3 inverse in float64.)  Element build 2 n m;
       setup record (float64): X = P C_bar^T (n^2 m), S_y (n m (m+1)/2),
       innovation (n m), kappa (m^2), U_l (n^2 m), S_y^-1 U_l^T (n m^2),
       m^f_l (n^2 + n m), P A^{lT} and A P_ll (2 n^3), P^- upper triangle
@@ -355,19 +374,28 @@ def phase_fma(n, m, precision):
       m^f_1 (n^2 + n m), A m^f_l (n^2), U_1 S_y^-1 (n m^2), A P, P^f_1l, E and
       A P^f_1l^T (4 n^3 + n^2 m), P^f_11 upper (n(n+1)/2 (n + m)), g (n^2),
       S upper (n^2 (n+1)/2).
-    smoother scan: one Eq. 30 combine 3 n^3 + n^2 (scan type) and the
-      smoothing terms of its result pass, Z dP, Om upper, om, dm
-      (n^3 + n^2 (n+1)/2 + 2 n^2, float64 in the mixed mode).
+    smoother scan: one Eq. 30 combine 3 n^3 + n^2 (scan type) and, per result,
+      the record form's smoothing terms Z dP, Om upper, om, dm
+      (n^3 + n^2 (n+1)/2 + 2 n^2, float64 in the mixed mode), or the two-point
+      form's LDL^T factors of P^s_{k+1,1} and S_k (2 x sum_j (j + (n-1-j)(j+1)),
+      float64 in the mixed mode).
     The parallel scan's second combine per element (its re-walk) is overhead,
     not algorithmic work, and is not counted."""
-    solve = n ** 3
-    combine = (25 * n ** 3) // 3 + 5 * n * n
+    if m < n:
+        solve = 0 if m == 1 else (2 if m == 2 else m ** 3)
+        combine = (2 * m * n * n + 2 * n * n + m * m * n + 2 * m * m * n + n * m + n * (n + 1) * m + n * n * m
+                   + 2 * n * n + 2 * n ** 3 + n * (n + 1) // 2 * n)
+    else:
+        solve = n ** 3
+        combine = (25 * n ** 3) // 3 + 5 * n * n
     record = (n * n * m + n * m * (m + 1) // 2 + n * m + m * m + n * n * m + n * m * m + n * n + n * m + 2 * n ** 3
               + n * n * (n + 1) // 2 + 2 * n ** 3)
     element = (n * n * m + n * n + n * m + n * n + n * m * m + 4 * n ** 3 + n * n * m + n * (n + 1) // 2 * (n + m)
                + n * n + n * n * (n + 1) // 2)
     s_combine = 3 * n ** 3 + n * n
     s_terms = n ** 3 + n * n * (n + 1) // 2 + 2 * n * n
+    if form == 2:
+        s_terms = 2 * sum(j + (n - 1 - j) * (j + 1) for j in range(n))
     f32 = {"filter_scan": combine - solve + 2 * n * m + element, "smoother_scan": s_combine}
     f64 = {"filter_scan": solve + record, "smoother_scan": s_terms}
     if precision == "fp64":
@@ -377,12 +405,12 @@ def phase_fma(n, m, precision):
     return {k: (f32[k], f64[k]) for k in f32}
 
 
-def roofline_phases(stage_ms, n, m, precision, n_slow, n_fast, peaks):
+def roofline_phases(stage_ms, n, m, precision, n_slow, n_fast, peaks, form=1):
     """Per-phase achieved FLOP/s (algorithmic counts of phase_fma and
     recovery_fma) over the phase's event time, as fractions of the measured
     float32 and float64 FMA peaks."""
     out = {}
-    pf = phase_fma(n, m, precision)
+    pf = phase_fma(n, m, precision, form)
     times = {"filter_scan": stage_ms["filter_scan"] + stage_ms.get("interval_setup", 0.0),
              "smoother_scan": stage_ms["smoother_scan"]}
     for ph, (f32, f64) in pf.items():
@@ -394,10 +422,10 @@ def roofline_phases(stage_ms, n, m, precision, n_slow, n_fast, peaks):
                    "fp64_gflops": g64, "fp64_frac": g64 / peaks["fp64_gflops"],
                    "fma_per_slow_step": {"fp32": f32, "fp64": f64}}
     rec_ms = stage_ms["recovery"] + stage_ms.get("recovery_filtered_half", 0.0)
-    g = 2.0 * recovery_fma(n, m) * n_fast / (rec_ms * 1e-3) / 1e9
+    g = 2.0 * recovery_fma(n, m, form) * n_fast / (rec_ms * 1e-3) / 1e9
     key = "fp32" if precision == "fp32" else "fp64"
     out["recovery"] = {"ms": rec_ms, f"{key}_gflops": g, f"{key}_frac": g / peaks[f"{key}_gflops"],
-                       "fma_per_fast_step": recovery_fma(n, m)}
+                       "fma_per_fast_step": recovery_fma(n, m, form)}
     return out
 
 
@@ -604,13 +632,14 @@ def run_batched(args, rank, world, dist):
     line = None
     if rank == 0:
         peaks = measured_peaks()
+        form = api.get_tuning(nx, args.precision)["recover_form"]
         roof = recovery_roofline(stage_serial, nx, ny, args.precision, n_slow, n_fast,
                                  recorded_traffic(args.precision, n_fast, "ragged_chains"), peaks,
                                  "stage events of a direct call with every stage over the whole batch "
-                                 "(the recovery launch alone on the GPU)")
+                                 "(the recovery launch alone on the GPU)", form)
         key = "fp32" if args.precision == "fp32" else "fp64"
         rec_pipe = stage["recovery"] * 1e-3
-        roof["achieved_in_timed_configuration"] = 2.0 * recovery_fma(nx, ny) * n_fast / rec_pipe / 1e9
+        roof["achieved_in_timed_configuration"] = 2.0 * recovery_fma(nx, ny, form) * n_fast / rec_pipe / 1e9
         roof["note_in_timed_configuration"] = (
             "summed durations of the per-chunk recovery launches of the timed (chunked) configuration, which share "
             "the GPU with the scans of the next chunk" if api.get_tuning(nx, args.precision)["batch_chunks"] > 1

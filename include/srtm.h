@@ -257,7 +257,7 @@ int srtm_release(void);
  * split, batch pipelining) for one (nx, precision).  Zero values keep the
  * built-in choice (128/lanes-per-group groups, 4 elements, 128 threads,
  * window 16, setup inside the filter scan, one recovery kernel, batches in
- * one chunk).  Returns SRTM_ERR_ARG for
+ * one chunk, two-point recovery form).  Returns SRTM_ERR_ARG for
  * out-of-range values.  The setting is process-wide and applies to the calls
  * issued after it.                                                            */
 typedef struct {
@@ -292,6 +292,25 @@ typedef struct {
                            blocks per SM, each thread looping over fast steps */
   int chunk_scan_bps;   /* scan grid of a chunked batch: 0 = as many blocks per
                            SM as fit; 1..8 = at most that many per SM        */
+  int recover_form;     /* fast-rate recovery of smoother calls: 1 = record
+                           form (filtered fast-rate moments of the interval,
+                           Remarks 1 and 3, then the smoothing terms of Eq.
+                           21); 2 = two-point form for the calls that ask for
+                           smoothed outputs only, without known inputs (not
+                           the range calls of a split sequence nor
+                           srtm_smoother_noalloc): every fast-rate smoothed
+                           moment from the smoothed joint of the interval's
+                           first state and the next interval's first state,
+                           conditioned on the interval's measurement (the
+                           same posterior, about 15% fewer float64
+                           operations per fast step at ny = 1; one record of
+                           3 nx^2 + 2 nx recovery-type words per slow step
+                           more workspace).  A sequence whose covariance of
+                           (next first state, measurement) given the
+                           interval's first state is singular or nearly so (a
+                           pivot below 1e-6 of the variance it came from, e.g.
+                           no process noise) keeps the record form inside a
+                           two-point call.                                  */
 } srtm_tuning;
 int srtm_set_tuning(int nx, srtm_precision prec, const srtm_tuning *t);
 int srtm_get_tuning(int nx, srtm_precision prec, srtm_tuning *t);
@@ -301,8 +320,9 @@ int srtm_get_tuning(int nx, srtm_precision prec, srtm_tuning *t);
  * sequence of candidate tunings and keeps the fastest for (p->nx, prec) as if
  * by srtm_set_tuning: first the grid of scan_groups (every valid power of
  * two) x scan_elems (1, 2, 4, 8, 16, 32), then lookback_window (4, 8, 16, 32)
- * recover_threads (32, 64, 96, 128), setup_mode (1, 2) and recover_split
- * (1, 2) one at a time from the best so far.
+ * recover_threads (32, 64, 96, 128) and setup_mode (1, 2) one at a time
+ * from the best so far, then the recovery as (recover_form, recover_split)
+ * in (1, 1), (1, 2), (2, 1).
  * Each candidate is run once untimed on `stream`, then captured into a CUDA
  * graph on a private stream and the graph replayed `reps` times (reps >= 1),
  * timed by CUDA events around each replay (device time without host launch

@@ -56,7 +56,8 @@ class Batch(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("scan_groups", c_int), ("scan_elems", c_int), ("recover_threads", c_int),
                 ("lookback_window", c_int), ("setup_mode", c_int), ("recover_split", c_int),
-                ("batch_chunks", c_int), ("chunk_recover_bps", c_int), ("chunk_scan_bps", c_int)]
+                ("batch_chunks", c_int), ("chunk_recover_bps", c_int), ("chunk_scan_bps", c_int),
+                ("recover_form", c_int)]
 
 
 class SRTMError(RuntimeError):
@@ -319,10 +320,11 @@ def status(stream=None) -> None:
 
 
 def set_tuning(nx: int, precision: str, scan_groups=0, scan_elems=0, recover_threads=0, lookback_window=0,
-               setup_mode=0, recover_split=0, batch_chunks=0, chunk_recover_bps=0, chunk_scan_bps=0):
+               setup_mode=0, recover_split=0, batch_chunks=0, chunk_recover_bps=0, chunk_scan_bps=0,
+               recover_form=0):
     _check(load().srtm_set_tuning(nx, PRECISION[precision], ctypes.byref(
         Tuning(scan_groups, scan_elems, recover_threads, lookback_window, setup_mode, recover_split, batch_chunks,
-               chunk_recover_bps, chunk_scan_bps))))
+               chunk_recover_bps, chunk_scan_bps, recover_form))))
 
 
 def get_tuning(nx: int, precision: str) -> dict:

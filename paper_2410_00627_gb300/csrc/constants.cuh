@@ -86,10 +86,151 @@ struct PreGeom {
                        AP = Jc + NN, CP = AP + NN, cross = CP + NM, S1 = cross + NM, S1i = S1 + MM, Lg = S1i + MM,
                        innov = Lg + NM, P1 = innov + MY, P1o = P1 + NN, m1 = P1o + NN, bu = m1 + NX,
                        sbu = bu + NX, USCR = sbu + NX;  // bu, sbu: first interval's b_{1,l}, sum_i b_{1,i}
-  static constexpr int BASE = USCR + NU * NN;  // per-unit n x n scratch, then the tables
+  // two-point recovery: Cov([x_{k+1,1}; y_k] | x_{k,1}) and its inverse, the
+  // same for y_k alone, H S_{l-1}
+  static constexpr int DD = (NX + MY) * (NX + MY);
+  static constexpr int Vb = USCR + NU * NN, Vbi = Vb + DD, Vy = Vbi + DD, Vyi = Vy + MM, HS = Vyi + MM;
+  static constexpr int BASE = HS + NM;  // then the tables
   // tables: A^0..A^L, S_0..S_{L-1}, Cov(e_i) terms / prefixes, two V buffers
   __host__ __device__ static size_t tables(int L) { return (size_t)(5 * L + 1) * NN; }
 };
+
+// Constants of the two-point recovery of one sequence (float64, by the
+// block of its constants kernel, after the model table is written).  Given
+// the first state x_{k,1} of an interval, the noise parts of the interval's
+// states, eps_i = x_{k,i} - A^{i-1} x_{k,1} (i = 1..l+1, eps_{l+1} the next
+// interval's first state), are e_{i-1} of the lifted model (Sec. III-A), so
+//   Cov(eps_i) = Qc_{i-1},  Cov(eps_i, eps_{l+1}) = Cov(e_{i-1}, e_l),
+//   Cov(eps_i, H sum_j eps_j) = (V_{i-1} - Cov(e_{i-1}, e_l)) H^T,
+// and v = [x_{k+1,1}; y_k] has E[v | x_{k,1}] = [A^l; H S_{l-1}] x_{k,1}
+// (S_{l-1} = sum_{j<l} A^j) and covariance
+//   Vb = [[Qc_l, (V_l - Qc_l) H^T], [., R_x - H V_l H^T - (H V_l H^T)^T + H Qc_l H^T]].
+// Conditioning x_{k,i} on (x_{k,1}, v) (the states between two first states
+// depend on the rest of the data only through them and y_k):
+//   G_i = K_i Vb^{-1},  K_i = Cov(eps_i, v),
+//   C2_i = G_i[:, :n],  c3_i = G_i[:, n:],  C1_i = A^{i-1} - G_i [A^l; H S_{l-1}],
+//   Sg_i = Qc_{i-1} - G_i K_i^T,
+// so that E[x_{k,i} | x_{k,1}, x_{k+1,1}, y_k] = C1_i x_{k,1} + C2_i x_{k+1,1}
+// + c3_i y_k with covariance Sg_i.  The last interval conditions on
+// (x_{k,1}, y_k) only (C1'_i, c3'_i, Sg'_i from the y block of Vb).  A
+// sequence where a pivot of Vb (or of its y block) is below 1e-6 of the
+// variance it came from keeps the record form (bflag = 0): singular or
+// nearly singular process noise over an interval, where the inverse would
+// not keep float64 accuracy.
+template <int NX>
+__device__ void two_point_constants(const Ctx& c, int s, int l, int m, double* md, double* sm, int tid, int nt) {
+  using S = PreGeom<NX>;
+  constexpr int NN = NX * NX, BT = 3 * NN + NX * MY, BO = 2 * NN + NX * MY;
+  const ModelLayout L = c.ml;
+  const int d = NX + m;
+  __shared__ int s_bok;
+  __syncthreads();  // the model table's tables are complete
+  const double* Qcl = md + L.Qc + (size_t)(l - 1) * NN;
+  const double* Al = md + L.Apow + (size_t)l * NN;
+  const double* H = sm + S::H;
+  const double* GQM = sm + S::GQM;
+  double *Vb = sm + S::Vb, *Vbi = sm + S::Vbi, *Vy = sm + S::Vy, *Vyi = sm + S::Vyi, *HS = sm + S::HS;
+  for (int e = tid; e < d * d; e += nt) {  // upper entries, mirrored
+    const int r = e / d, q = e - (e / d) * d;
+    if (r > q) continue;
+    double v;
+    if (q < NX) {
+      v = 0.5 * (Qcl[r * NX + q] + Qcl[q * NX + r]);
+    } else if (r < NX) {
+      const int j = q - NX;
+      v = GQM[r * m + j];
+      for (int t = 0; t < NX; ++t) v = fma(-Qcl[r * NX + t], H[j * NX + t], v);
+    } else {
+      const int i = r - NX, j = q - NX;
+      v = 0.5 * (sm[S::Rx + i * m + j] + sm[S::Rx + j * m + i]);
+      for (int t = 0; t < NX; ++t) v -= H[i * NX + t] * GQM[t * m + j] + H[j * NX + t] * GQM[t * m + i];
+      for (int t = 0; t < NX; ++t) {
+        double w = 0.0;
+        for (int u = 0; u < NX; ++u) w = fma(Qcl[t * NX + u], H[j * NX + u], w);
+        v = fma(H[i * NX + t], w, v);
+      }
+    }
+    Vb[r * d + q] = v;
+    Vb[q * d + r] = v;
+  }
+  for (int e = tid; e < m * NX; e += nt) {  // H S_{l-1} = H + C_bar - H A^l
+    const int j = e / NX, q = e - (e / NX) * NX;
+    double v = H[e] + sm[S::Cb + e];
+    for (int t = 0; t < NX; ++t) v = fma(-H[j * NX + t], Al[t * NX + q], v);
+    HS[e] = v;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < m; ++j) Vy[i * m + j] = Vb[(NX + i) * d + NX + j];
+    const bool ok = spd_inverse_checked(Vb, d, Vbi, 1e-6) && spd_inverse_checked(Vy, m, Vyi, 1e-6);
+    s_bok = ok ? 1 : 0;
+    md[L.bflag] = ok ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  const bool ok = s_bok != 0;
+  // K_i entry (q, col): col < NX the x block, else the y block
+  auto Kent = [&](int i, int q, int col) -> double {
+    const double* Qlj = md + L.Ql + (size_t)(i - 2) * NN;
+    if (col < NX) return Qlj[q * NX + col];
+    const int j = col - NX;
+    double v = md[L.VH + (size_t)(i - 2) * NX * m + q * m + j];
+    for (int t = 0; t < NX; ++t) v = fma(-Qlj[q * NX + t], H[j * NX + t], v);
+    return v;
+  };
+  for (int pr = tid; pr < l * NX; pr += nt) {
+    const int i = pr / NX + 1, r = pr - (pr / NX) * NX;
+    double* bt = md + L.BrT + (size_t)(i - 1) * BT;
+    double* bo = md + L.BrO + (size_t)(i - 1) * BO;
+    const double* Ai = md + L.Apow + (size_t)(i - 1) * NN;
+    if (i == 1 || !ok) {  // x_{k,1} itself (and placeholders when the record form is kept)
+      for (int q = 0; q < NX; ++q) {
+        const double id = (r == q) ? 1.0 : 0.0;
+        bt[r * NX + q] = id;
+        bt[NN + r * NX + q] = 0.0;
+        bt[2 * NN + r * NX + q] = 0.0;
+        bo[r * NX + q] = id;
+        bo[NN + r * NX + q] = 0.0;
+      }
+      for (int j = 0; j < MY; ++j) {
+        bt[3 * NN + r * MY + j] = 0.0;
+        bo[2 * NN + r * MY + j] = 0.0;
+      }
+      continue;
+    }
+    const double* Qj = md + L.Qc + (size_t)(i - 2) * NN;
+    double G[NX + MY], Gy[MY];
+    for (int col = 0; col < d; ++col) {
+      double v = 0.0;
+      for (int c2 = 0; c2 < d; ++c2) v = fma(Kent(i, r, c2), Vbi[c2 * d + col], v);
+      G[col] = v;
+    }
+    for (int j = 0; j < m; ++j) {
+      double v = 0.0;
+      for (int j2 = 0; j2 < m; ++j2) v = fma(Kent(i, r, NX + j2), Vyi[j2 * m + j], v);
+      Gy[j] = v;
+    }
+    for (int q = 0; q < NX; ++q) {
+      double c1 = Ai[r * NX + q], c1o = Ai[r * NX + q], sg = Qj[r * NX + q], sgo = Qj[r * NX + q];
+      for (int t = 0; t < NX; ++t) c1 = fma(-G[t], Al[t * NX + q], c1);
+      for (int j = 0; j < m; ++j) {
+        c1 = fma(-G[NX + j], HS[j * NX + q], c1);
+        c1o = fma(-Gy[j], HS[j * NX + q], c1o);
+        sgo = fma(-Gy[j], Kent(i, q, NX + j), sgo);
+      }
+      for (int col = 0; col < d; ++col) sg = fma(-G[col], Kent(i, q, col), sg);
+      bt[r * NX + q] = c1;
+      bt[NN + r * NX + q] = G[q];
+      bt[2 * NN + r * NX + q] = sg;
+      bo[r * NX + q] = c1o;
+      bo[NN + r * NX + q] = sgo;
+    }
+    for (int j = 0; j < MY; ++j) {
+      bt[3 * NN + r * MY + j] = j < m ? G[NX + j] : 0.0;
+      bo[2 * NN + r * MY + j] = j < m ? Gy[j] : 0.0;
+    }
+  }
+}
 
 // Per-model constants of one sequence (one block per sequence, after the
 // check blocks), float64.
@@ -393,6 +534,7 @@ __global__ void __launch_bounds__(PRE_THREADS) precompute_kernel(Ctx c, int tabl
   }
   for (int e = tid; e < m * m; e += nt) md[L.Rx + e] = sm[S::Rx + e];
   for (int e = tid; e < NX; e += nt) md[L.m1 + e] = sm[S::m1 + e];
+  if (c.bridge) two_point_constants<NX>(c, s, l, m, md, sm, tid, nt);
   if (tid == 0 && !s_ok) atomicOr(&c.ctr->err, DEVERR_SINGULAR);
 }
 

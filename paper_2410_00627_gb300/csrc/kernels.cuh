@@ -49,6 +49,12 @@ struct SetupGeom {
   }
 };
 
+// The per-interval records of sequence s are read by the recovery unless the
+// call takes the two-point form for it.
+__device__ __forceinline__ bool records_needed(const Ctx& c, int s) {
+  return !(c.bridge && c.model[(long long)s * c.ml.stride + c.ml.bflag] != 0.0);
+}
+
 // Smoother element of one interval (Eq. 29 with the fast-filter blocks of
 // Eq. 17 for i = 1 and i = l), row r by lane r, in the arithmetic type TE:
 //   U_1 = A X + V_1 H^T,  m^f_1 = A m + U_1 kap,
@@ -435,8 +441,9 @@ __device__ void setup_interval(const Ctx& c, long long gi, int lane, unsigned ma
     }
   }
   __syncwarp(mask);
-  // record (row r; lane 0 the m-sized parts)
-  {
+  // record (row r; lane 0 the m-sized parts), which the two-point recovery
+  // does not read
+  if (records_needed(c, s)) {
     TR* rc = (TR*)c.rec + gi * RL::SIZE;
     if (row) {
       rc[RL::mv + r] = sb[Gm::mv + r];
@@ -883,8 +890,9 @@ struct FilterOp {
     }
     __syncthreads();
     // the records' P^f_{k-1,l} as LDL^T factors, one thread per interval
-    for (int j = threadIdx.x; j < count; j += blockDim.x)
-      ldlt_inplace<NX, TS>((TS*)c.rec + (base_row + p0 + j) * Rec<NX>::SIZE + Rec<NX>::P);
+    if (records_needed(c, s))
+      for (int j = threadIdx.x; j < count; j += blockDim.x)
+        ldlt_inplace<NX, TS>((TS*)c.rec + (base_row + p0 + j) * Rec<NX>::SIZE + Rec<NX>::P);
     __syncthreads();
   }
 };
@@ -925,11 +933,44 @@ struct SmootherOp {
     const T* src = (const T*)c.selem + (c.meta.off_slow[s] + (N - 1 - p)) * ES;
     for (int e = g.lane; e < ES; e += G) x[e] = src[e];
   }
+  // two-point recovery terms of a sequence whose bflag is set: the result at
+  // k is mu0 and (before its LDL^T) L1's source for interval k-1 and mu1 of
+  // interval k-1; interval k also takes E_k and S_k of its element (the last
+  // interval: L2 = P^s_{k,1})
+  __device__ static void store_two_point(const Grp<G>& g, const T* x, const Ctx& c, int s, long long k, int N) {
+    constexpr int NN = NX * NX;
+    using B = BRec<NX>;
+    using TR = TS;
+    const long long row = c.meta.off_slow[s] + k;
+    TR* b = (TR*)c.brec + row * B::SIZE;
+    for (int e = g.lane; e < NX; e += G) b[B::mu0 + e] = (TR)x[L::g + e];
+    if (k >= 1) {
+      TR* bp = b - B::SIZE;
+      for (int e = g.lane; e < NX; e += G) bp[B::mu1 + e] = (TR)x[L::g + e];
+      for (int e = g.lane; e < NN; e += G) bp[B::L1 + e] = (TR)x[L::S + e];
+    }
+    if (k < N - 1) {
+      const T* el = (const T*)c.selem + row * ES;
+      for (int e = g.lane; e < NN; e += G) {
+        b[B::E + e] = (TR)el[L::E + e];
+        b[B::L2 + e] = (TR)el[L::S + e];
+      }
+    } else {
+      for (int e = g.lane; e < NN; e += G) b[B::L2 + e] = (TR)x[L::S + e];
+    }
+  }
+  __device__ static bool two_point(const Ctx& c, int s) {
+    return c.bridge && c.model[(long long)s * c.ml.stride + c.ml.bflag] != 0.0;
+  }
   __device__ static void store(const Grp<G>& g, const T* x, const Ctx& c, int s, long long p, int N, T*, TS* scs) {
     constexpr int NN = NX * NX;
     using RL = Rec<NX>;
     using TR = TS;
     const long long k = N - 1 - p;
+    if (two_point(c, s)) {
+      store_two_point(g, x, c, s, k, N);
+      return;
+    }
     if (k == 0) return;
     const long long row = c.meta.off_slow[s] + k - 1;
     const TR* rc = (const TR*)c.rec + row * RL::SIZE;
@@ -961,6 +1002,20 @@ struct SmootherOp {
   __device__ static void epilogue(const Ctx& c, int s, long long p0, int count, const T*, unsigned char*) {
     const int N = c.meta.nslow[s];
     __syncthreads();  // every lane group's stores of the tile
+    if (two_point(c, s)) {  // the factors this tile's stores wrote: L2 of interval k, L1 of interval k-1
+      using B = BRec<NX>;
+      for (int j = threadIdx.x; j < 2 * count; j += blockDim.x) {
+        const long long k = N - 1 - (p0 + j / 2);
+        TR_* b = (TR_*)c.brec + (c.meta.off_slow[s] + k) * B::SIZE;
+        if (j & 1) {
+          if (k >= 1) ldlt_inplace<NX, TR_>(b - B::SIZE + B::L1);
+        } else {
+          ldlt_inplace<NX, TR_>(b + B::L2);
+        }
+      }
+      __syncthreads();
+      return;
+    }
     for (int j = threadIdx.x; j < count; j += blockDim.x) {
       const long long k = N - 1 - (p0 + j);
       if (k >= 1)
@@ -1483,6 +1538,97 @@ __device__ __forceinline__ void recover_smooth(const TR* Om, const TR* om, TR (&
   }
 }
 
+// P += (W Lf) Df (W Lf)^T on the upper triangle, with Lf Df Lf^T given by
+// its factors f (Lf below the diagonal, Df on it)
+template <int NX, class TR>
+__device__ __forceinline__ void add_factored_quad(const TR (&W)[NX][NX], const TR* f, TR (&P)[NX * (NX + 1) / 2]) {
+  TR B[NX][NX], BD[NX][NX];
+#pragma unroll
+  for (int r = 0; r < NX; ++r)
+#pragma unroll
+    for (int q = 0; q < NX; ++q) {
+      TR v = W[r][q];
+#pragma unroll
+      for (int t = q + 1; t < NX; ++t) v = fma(W[r][t], f[t * NX + q], v);
+      B[r][q] = v;
+      BD[r][q] = v * f[q * NX + q];
+    }
+  int u = 0;
+#pragma unroll
+  for (int r = 0; r < NX; ++r)
+#pragma unroll
+    for (int q = r; q < NX; ++q) {
+      TR v = P[u];
+#pragma unroll
+      for (int t = 0; t < NX; ++t) v = fma(BD[r][t], B[q][t], v);
+      P[u++] = v;
+    }
+}
+
+// Two-point recovery of fast step x (a sequence whose bflag is set), from
+// the interval's terms (BRec) and the constants of fast index i:
+//   m^s_{k,i} = C1_i mu0 + C2_i mu1 + c3_i y_k,
+//   P^s_{k,ii} = Sg_i + [C1_i C2_i] J_k [C1_i C2_i]^T,
+// J_k the smoothed joint covariance of (x_{k,1}, x_{k+1,1}).  With
+// x_{k,1} = E_k x_{k+1,1} + (independent part of covariance S_k),
+//   [C1 C2] J [C1 C2]^T = (C1 E_k + C2) P^s_{k+1,1} (C1 E_k + C2)^T + C1 S_k C1^T,
+// each quadratic form from its LDL^T factors.  The last interval conditions
+// on (x_{k,1}, y_k) only: Sg'_i + C1'_i P^s_{k,1} C1'_i^T.
+template <int NX, int M, class TR>
+__device__ __forceinline__ void recover_two_point(const Ctx& c, const FastIdx& x, TR (&mf)[NX],
+                                                  TR (&Pf)[NX * (NX + 1) / 2]) {
+  constexpr int NN = NX * NX, BT = 3 * NN + NX * MY, BO = 2 * NN + NX * MY;
+  using B = BRec<NX>;
+  const double* md = c.model + (long long)x.s * c.ml.stride;
+  const TR* b = (const TR*)c.brec + x.row * B::SIZE;
+  const bool two = x.k < x.N - 1;
+  const double* K = md + (two ? c.ml.BrT + (long long)(x.i - 1) * BT : c.ml.BrO + (long long)(x.i - 1) * BO);
+  const double* Sg = K + (two ? 2 * NN : NN);
+  const double* c3 = K + (two ? 3 * NN : 2 * NN);
+  const double* yk = c.y + x.row * M;
+  TR C1[NX][NX];
+#pragma unroll
+  for (int r = 0; r < NX; ++r)
+#pragma unroll
+    for (int q = 0; q < NX; ++q) C1[r][q] = (TR)__ldg(K + r * NX + q);
+#pragma unroll
+  for (int r = 0; r < NX; ++r) {
+    TR v = TR(0);
+#pragma unroll
+    for (int q = 0; q < NX; ++q) v = fma(C1[r][q], b[B::mu0 + q], v);
+#pragma unroll
+    for (int j = 0; j < M; ++j) v = fma((TR)__ldg(c3 + r * MY + j), (TR)__ldg(yk + j), v);
+    mf[r] = v;
+  }
+  {
+    int u = 0;
+#pragma unroll
+    for (int r = 0; r < NX; ++r)
+#pragma unroll
+      for (int q = r; q < NX; ++q) Pf[u++] = (TR)__ldg(Sg + r * NX + q);
+  }
+  if (two) {
+    const double* C2 = K + NN;
+    TR W[NX][NX];
+#pragma unroll
+    for (int r = 0; r < NX; ++r) {
+      TR v = mf[r];
+#pragma unroll
+      for (int q = 0; q < NX; ++q) {
+        const TR c2 = (TR)__ldg(C2 + r * NX + q);
+        v = fma(c2, b[B::mu1 + q], v);
+        TR w = c2;
+#pragma unroll
+        for (int t = 0; t < NX; ++t) w = fma(C1[r][t], b[B::E + t * NX + q], w);
+        W[r][q] = w;
+      }
+      mf[r] = v;
+    }
+    add_factored_quad<NX, TR>(W, b + B::L1, Pf);
+  }
+  add_factored_quad<NX, TR>(C1, b + B::L2, Pf);
+}
+
 // Output stores of the recovery.  The fast rows of a warp (32 consecutive
 // fast steps) are contiguous in the outputs, so each lane first puts its mean
 // and mirrored covariance into the warp's shared-memory slab and the warp then
@@ -1606,7 +1752,10 @@ __global__ void __launch_bounds__(128, 3) recover_kernel(Ctx c) {
       x = fast_index(c, f);
       last_i = x.i == x.l;
       smooth_k = c.smoothing && (x.k < x.N - 1 || c.split_tail_open);
-      if (PHASE < 2) {
+      if (PHASE == 0 && c.bridge && c.model[(long long)x.s * c.ml.stride + c.ml.bflag] != 0.0) {
+        recover_two_point<NX, M, TR>(c, x, mf, Pf);  // the smoothed moments themselves
+        smooth_k = false;
+      } else if (PHASE < 2) {
         recover_filtered<NX, M, TR>(c, x, smooth_k, mf, Pf, Pfl);
       } else {  // component-major: a warp reads 32 consecutive words per component
         const TR* src = (const TR*)c.rscr + f;
@@ -1736,8 +1885,9 @@ __global__ void __launch_bounds__(128) setup_kernel(Ctx c) {
   for (long long base = g_lo + (long long)blockIdx.x * per; base < g_hi; base += (long long)gridDim.x * per) {
     if (base + slot < g_hi) setup_interval<NX, M, T, TS>(c, base + slot, lane, mask, (TS*)sl, sf, nullptr);
     __syncthreads();
-    if (threadIdx.x < per && base + threadIdx.x < g_hi)
-      ldlt_inplace<NX, TS>((TS*)c.rec + (base + threadIdx.x) * Rec<NX>::SIZE + Rec<NX>::P);
+    const long long gi = base + threadIdx.x;
+    if (threadIdx.x < per && gi < g_hi && (!c.bridge || records_needed(c, find_segment(c.meta.off_slow, c.n_seq, gi))))
+      ldlt_inplace<NX, TS>((TS*)c.rec + gi * Rec<NX>::SIZE + Rec<NX>::P);
     __syncthreads();
   }
 }

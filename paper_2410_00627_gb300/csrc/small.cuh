@@ -172,6 +172,48 @@ __device__ __forceinline__ bool small_sym_inverse(const TR (&a)[MY][MY], TR (&in
   return ok;
 }
 
+// Inverse of the symmetric positive definite d x d matrix a (row-major, ld
+// d), one thread: a is overwritten by its LDL^T factors (L below the
+// diagonal, D on it) and L^{-1} (above the diagonal, transposed), then
+//   a^{-1} = L^{-T} D^{-1} L^{-1}
+// is written to inv.  Returns false (inv unset) when a pivot D_j is not
+// above rtol times the diagonal entry a_jj it came from (the variable j is
+// then determined by the ones before it to within that fraction of its
+// variance: the matrix is singular or too ill-conditioned for the inverse to
+// keep float64 accuracy) or is not finite.
+__device__ inline bool spd_inverse_checked(double* a, int d, double* inv, double rtol) {
+  for (int j = 0; j < d; ++j) {
+    const double ajj = a[j * d + j];
+    double dj = ajj;
+    for (int k = 0; k < j; ++k) dj = fma(-a[j * d + k] * a[j * d + k], a[k * d + k], dj);
+    if (!(dj > rtol * ajj) || bad_value(dj)) return false;
+    a[j * d + j] = dj;
+    for (int i = j + 1; i < d; ++i) {
+      double v = a[i * d + j];
+      for (int k = 0; k < j; ++k) v = fma(-a[i * d + k] * a[j * d + k], a[k * d + k], v);
+      a[i * d + j] = v / dj;
+    }
+  }
+  // X = L^{-1} (unit lower): X_ij = -sum_{k=j}^{i-1} L_ik X_kj, kept at a[j][i]
+  for (int j = 0; j < d; ++j)
+    for (int i = j + 1; i < d; ++i) {
+      double v = -a[i * d + j];
+      for (int k = j + 1; k < i; ++k) v = fma(-a[i * d + k], a[j * d + k], v);
+      a[j * d + i] = v;
+    }
+  for (int i = 0; i < d; ++i)
+    for (int j = i; j < d; ++j) {
+      double v = 0.0;  // sum_{k >= j} X_ki X_kj / D_k, X_kk = 1
+      for (int k = j; k < d; ++k) {
+        const double xi = k == i ? 1.0 : a[i * d + k], xj = k == j ? 1.0 : a[j * d + k];
+        v = fma(xi * xj, 1.0 / a[k * d + k], v);
+      }
+      inv[i * d + j] = v;
+      inv[j * d + i] = v;
+    }
+  return true;
+}
+
 // Is the n x n row-major matrix a (n <= N) a covariance: every entry finite,
 // symmetric to within 1e-8 of its largest diagonal entry, and positive
 // semi-definite?  The last test is a Cholesky factorisation of the

@@ -74,6 +74,7 @@ srtm_tuning effective_tuning(int nx, srtm_precision prec) {
   t.batch_chunks = 1;
   t.chunk_recover_bps = 0;
   t.chunk_scan_bps = 0;
+  t.recover_form = 2;
   const srtm_tuning& u = g_tune[nx][prec];
   if (u.scan_groups) t.scan_groups = u.scan_groups;
   if (u.scan_elems) t.scan_elems = u.scan_elems;
@@ -84,6 +85,7 @@ srtm_tuning effective_tuning(int nx, srtm_precision prec) {
   if (u.batch_chunks) t.batch_chunks = u.batch_chunks;
   if (u.chunk_recover_bps) t.chunk_recover_bps = u.chunk_recover_bps;
   if (u.chunk_scan_bps) t.chunk_scan_bps = u.chunk_scan_bps;
+  if (u.recover_form) t.recover_form = u.recover_form;
   return t;
 }
 
@@ -114,7 +116,7 @@ size_t a16(size_t x) { return (x + 15) / 16 * 16; }
 
 struct Layout {
   size_t ctr, ratio, nslow, off_slow, off_fast, tile_f, tile_s, chunks, model, ftile, stile, fout, rec, selem, sfin,
-      lterm, uin, rscr, total;
+      lterm, uin, rscr, brec, total;
   long long ftile_stride, stile_stride;
   ModelLayout ml;
 };
@@ -127,7 +129,7 @@ size_t split_scratch_bytes(int nx, srtm_precision prec, long long total_fast) {
 constexpr size_t SPLIT_SCRATCH_MAX = (size_t)4 << 30;
 
 Layout make_layout(int nx, int ny, int max_ratio, int n_seq, long long total_slow, srtm_precision prec, int tile_f,
-                   int tile_s, int nu, size_t rscr_bytes) {
+                   int tile_s, int nu, size_t rscr_bytes, bool two_point = false) {
   Layout L;
   const size_t sT = prec == SRTM_FP64 ? 8 : 4, sR = prec == SRTM_FP32 ? 4 : 8;
   const long long nn = (long long)nx * nx;
@@ -160,6 +162,7 @@ Layout make_layout(int nx, int ny, int max_ratio, int n_seq, long long total_slo
   L.lterm = take(sizeof(double) * (size_t)total_slow);
   L.uin = take(nu > 0 ? sizeof(double) * (size_t)(3 * nx + MY) * total_slow : 0);
   L.rscr = take(rscr_bytes);
+  L.brec = take(two_point ? sR * (size_t)((3 * nn + 2 * nx + 31) / 32 * 32) * total_slow : 0);
   L.total = a256(o);
   return L;
 }
@@ -274,6 +277,13 @@ int run(Ctx c, srtm_precision prec, cudaStream_t st, bool host_outputs = false) 
                      rscr_bytes <= SPLIT_SCRATCH_MAX && (c.split_mode == 0 || c.split_mode == 3))
                         ? 1
                         : 0;
+  // two-point recovery: smoothed outputs only, no known inputs, not a range
+  // of a split sequence; the whole recovery then follows the smoother scan
+  c.bridge = (t.recover_form == 2 && c.smoothing && !c.sequential && c.split_mode == 0 && c.nu == 0 &&
+              !c.ffast_mean && !c.ffast_cov && !c.fslow_mean && !c.fslow_cov)
+                 ? 1
+                 : 0;
+  if (c.bridge) c.recover_split = 0;
   // a batch in chunks: the scans of one chunk beside the recovery of the one before
   c.n_chunks = 1;
   c.chunk = 0;
@@ -290,7 +300,7 @@ int run(Ctx c, srtm_precision prec, cudaStream_t st, bool host_outputs = false) 
       return fail(SRTM_ERR_CUDA, "second stream creation failed");
   }
   const Layout L = make_layout(c.nx, c.ny, c.max_ratio, c.n_seq, c.total_slow, prec, tile_f, tile_s, c.nu,
-                               c.recover_split ? rscr_bytes : 0);
+                               c.recover_split ? rscr_bytes : 0, c.bridge != 0);
   if (d.ws_bytes < L.total) {
     if (d.ws) {
       cudaDeviceSynchronize();
@@ -340,6 +350,7 @@ int run(Ctx c, srtm_precision prec, cudaStream_t st, bool host_outputs = false) 
   c.lterm = (double*)(w + L.lterm);
   c.uin = c.nu > 0 ? (double*)(w + L.uin) : nullptr;
   c.rscr = c.recover_split ? (void*)(w + L.rscr) : nullptr;
+  c.brec = c.bridge ? (void*)(w + L.brec) : nullptr;
   c.tile_f = tile_f;
   c.tile_s = tile_s;
   c.setup_separate = t.setup_mode == 2 ? 1 : 0;
@@ -843,6 +854,7 @@ int srtm_set_tuning(int nx, srtm_precision prec, const srtm_tuning* t) {
   if (t->batch_chunks < 0 || t->batch_chunks > MAXCHUNK) return fail(SRTM_ERR_ARG, "batch_chunks out of range");
   if (t->chunk_recover_bps < 0 || t->chunk_recover_bps > 3) return fail(SRTM_ERR_ARG, "chunk_recover_bps out of range");
   if (t->chunk_scan_bps < 0 || t->chunk_scan_bps > 8) return fail(SRTM_ERR_ARG, "chunk_scan_bps out of range");
+  if (t->recover_form < 0 || t->recover_form > 2) return fail(SRTM_ERR_ARG, "recover_form out of range");
   std::lock_guard<std::mutex> lk(g_mu);
   g_tune[nx][prec] = *t;
   return SRTM_OK;
@@ -966,10 +978,14 @@ int autotune_impl(int nx, srtm_precision prec, int reps, Call call, srtm_tuning*
     t.setup_mode = md;
     consider(t);
   }
-  for (int sp = 1; sp <= 2; ++sp) {  // one recovery kernel / filtered half beside the smoother scan
-    if (rc || sp == cur.recover_split) continue;
+  // recovery: record form in one kernel / with its filtered half beside the
+  // smoother scan, two-point form (which has no filtered half)
+  const int forms[3][2] = {{1, 1}, {1, 2}, {2, 1}};
+  for (const auto& fs : forms) {
+    if (rc || (fs[0] == cur.recover_form && (fs[0] == 2 || fs[1] == cur.recover_split))) continue;
     srtm_tuning t = cur;
-    t.recover_split = sp;
+    t.recover_form = fs[0];
+    t.recover_split = fs[1];
     consider(t);
   }
   if (batched) {  // a batch in chunks: the scans of one chunk beside the recovery of the one before
@@ -1195,6 +1211,8 @@ extern "C" int srtm_smoother_noalloc(const srtm_problem* p, srtm_precision prec,
     c.sfin = w + L.sfin;
     c.lterm = (double*)(w + L.lterm);
     c.uin = c.nu > 0 ? (double*)(w + L.uin) : nullptr;
+    c.bridge = 0;  // the record form: the static scratch holds no two-point terms
+    c.brec = nullptr;
     c.tile_f = tile_f;
     c.tile_s = tile_s;
     c.setup_separate = t.setup_mode == 2 ? 1 : 0;

@@ -64,6 +64,10 @@ struct ModelLayout {
   long long Cf;    // float copies of A, Qc_1, Cov(e_1,e_l) (n^2 each), V_1 H^T, K and C_bar^T R_x^-1
                    // (n x m each, ld m, at n x MY strides), then F, D, J of the generic element (n^2 each),
                    // C_bar (m x n, at an MY x n stride) and R_x (m x m, ld m)
+  long long BrT;   // L (3n^2 + n MY)  two-point recovery constants per fast index i: C1_i, C2_i, Sg_i (n^2 each),
+                   //                  c3_i (n x m, ld MY)                      [two-point recovery]
+  long long BrO;   // L (2n^2 + n MY)  the same for the last interval: C1'_i, Sg'_i, c3'_i
+  long long bflag; // 1              1.0: the sequence takes the two-point recovery
   long long AB;    // L n MU      A^j B   (j = 0..L-1), n x nu blocks (ld nu)      [inputs]
   long long SB;    // L n MU      S_j B = sum_{i<=j} A^i B                         [inputs]
   long long stride;
@@ -90,6 +94,9 @@ __host__ __device__ inline ModelLayout make_model_layout(int n, int m, int L) {
   ml.P1 = o;   o += nn;
   ml.Q = o;    o += nn;
   ml.Cf = o;   o += (6 * nn + 4LL * n * MY + MY * MY + 1) / 2;
+  ml.BrT = o;  o += (long long)L * (3 * nn + (long long)n * MY);
+  ml.BrO = o;  o += (long long)L * (2 * nn + (long long)n * MY);
+  ml.bflag = o; o += 1;
   ml.AB = o;   o += (long long)L * n * SRTM_MAX_NU;
   ml.SB = o;   o += (long long)L * n * SRTM_MAX_NU;
   ml.stride = (o + 31) / 32 * 32;
@@ -123,6 +130,18 @@ struct Rec {
 template <int NX>
 struct UIn {
   static constexpr int bl = 0, b1 = NX, bn = 2 * NX, c = 3 * NX, SIZE = 3 * NX + MY;
+};
+
+// Per-interval terms of the two-point recovery (recovery type), written by
+// the smoother scan: E_k (the smoother gain of Eq. 29), the LDL^T factors of
+// P^s_{k+1,1} (L1) and of the element's S_k = Cov(x_{k,1} | x_{k+1,1}, y_{1:k})
+// (L2; for the last interval of P^s_{k,1}), and the smoothed means
+// mu0 = m^s_{k,1}, mu1 = m^s_{k+1,1}; padded to 32 entries.
+template <int NX>
+struct BRec {
+  static constexpr int NN = NX * NX;
+  static constexpr int E = 0, L1 = NN, L2 = 2 * NN, mu0 = 3 * NN, mu1 = 3 * NN + NX;
+  static constexpr int SIZE = (3 * NN + 2 * NX + 31) / 32 * 32;
 };
 
 // Per-interval smoothing terms (Om_k as its LDL^T factors: L below the
@@ -193,6 +212,11 @@ struct Ctx {
   double* agg_out;         // float64 aggregate of the range (filter: FL layout, smoother: SL layout)
   const double *next_mean, *next_cov;  // smoothed x_{k+1,1} after the range's last interval (mode 3)
   void* rscr;            // [RecScr::SIZE][total_fast] filtered moments between the two halves (recovery type)
+  // two-point recovery: the fast-rate smoothed moments of an interval from
+  // the smoothed joint of its first state and the next interval's first state
+  // and its measurement, for the sequences whose bflag is set
+  int bridge;            // 1: the call forms the two-point constants and terms
+  void* brec;            // [total_slow][BRec::SIZE] (recovery type)
 };
 
 // Filtered moments of one fast step kept between the two halves of a split

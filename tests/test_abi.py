@@ -38,7 +38,7 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(api.Problem) == 16 + 7 * 8 + 8 + 2 * 8   # + nu (padded), B, u
     assert ctypes.sizeof(api.Output) == 5 * 8
     assert ctypes.sizeof(api.Batch) == 16 + 16 + 9 * 8 + 8 + 2 * 8
-    assert ctypes.sizeof(api.Tuning) == 36
+    assert ctypes.sizeof(api.Tuning) == 40
 
 
 def test_rejects_bad_arguments_without_gpu(lib):
@@ -74,6 +74,7 @@ def test_tuning_validation_and_roundtrip(lib):
     assert lib.srtm_set_tuning(4, 1, ctypes.byref(api.Tuning(0, 0, 0, 0, 0, 0, 17))) == -1  # batch_chunks
     assert lib.srtm_set_tuning(4, 1, ctypes.byref(api.Tuning(0, 0, 0, 0, 0, 0, 0, 4))) == -1  # chunk_recover_bps
     assert lib.srtm_set_tuning(4, 1, ctypes.byref(api.Tuning(0, 0, 0, 0, 0, 0, 0, 0, 9))) == -1  # chunk_scan_bps
+    assert lib.srtm_set_tuning(4, 1, ctypes.byref(api.Tuning(0, 0, 0, 0, 0, 0, 0, 0, 0, 3))) == -1  # recover_form
     assert lib.srtm_set_tuning(4, 1, ctypes.byref(api.Tuning(0, 0, 0, 0, 0, 0, -1))) == -1
     assert lib.srtm_set_tuning(4, 1, ctypes.byref(api.Tuning(4, 8, 64, 8))) == 0
     assert lib.srtm_get_tuning(4, 1, ctypes.byref(t)) == 0
@@ -131,10 +132,12 @@ def test_built_in_tunings_are_in_their_documented_ranges(lib, nx):
         assert 1 <= t.scan_elems <= 64 and 32 <= t.recover_threads <= 128 and t.recover_threads % 32 == 0
         assert 1 <= t.lookback_window <= 32 and t.setup_mode in (1, 2) and t.recover_split in (1, 2)
         assert 1 <= t.batch_chunks <= 16 and 0 <= t.chunk_recover_bps <= 3 and 0 <= t.chunk_scan_bps <= 8
+        assert t.recover_form in (1, 2)
         # every documented value of every field is accepted, one at a time, and read back
         for field, values in (("scan_elems", (1, 64)), ("recover_threads", (32, 128)),
                               ("lookback_window", (1, 32)), ("setup_mode", (1, 2)), ("recover_split", (1, 2)),
-                              ("batch_chunks", (1, 16)), ("chunk_recover_bps", (1, 3)), ("chunk_scan_bps", (1, 8))):
+                              ("batch_chunks", (1, 16)), ("chunk_recover_bps", (1, 3)), ("chunk_scan_bps", (1, 8)),
+                              ("recover_form", (1, 2))):
             for v in values:
                 u = api.Tuning(0, 0, 0, 0, 0, 0)
                 setattr(u, field, v)

@@ -232,8 +232,8 @@ def test_stage_timing_reports_every_stage():
     api.set_stage_timing(True)
     times = {}
     try:
-        for split in (1, 2):
-            api.set_tuning(4, "fp64", recover_split=split)
+        for split in (1, 2):   # (the record form: the two-point form has no filtered half)
+            api.set_tuning(4, "fp64", recover_split=split, recover_form=1)
             run_smoother(prob, "fp64", filtered=False)
             times[split] = api.stage_times()
     finally:
