@@ -976,7 +976,9 @@ def rel_err(a, b):
 
 def report_errors(name, precisions=("fp64", "mixed", "fp32"), n_slow=None, seed=0):
     """Max relative errors (max |x - x_oracle| / max |x_oracle|) of the smoothed
-    and filtered outputs of each precision mode against the FP64 oracle, for
+    outputs (a smoother call without filtered outputs, and the record form of a
+    call that also asks for them) and the filtered outputs of each precision
+    mode against the FP64 oracle, for
     workload `name` at full size: every slow-rate output and the fast-rate
     outputs of the first and last three intervals.  Also the time of the
     smoother call (smoothed outputs only, built-in launch shapes): median of 5
@@ -999,7 +1001,11 @@ def report_errors(name, precisions=("fp64", "mixed", "fp32"), n_slow=None, seed=
     res, timing = {}, {}
     for prec in precisions:
         try:
-            sm, fi = api.smoother(*ins, l, precision=prec, filtered=api.OUTPUT_KEYS)
+            # smoothed outputs only (the recovery form the tuning selects: two-point
+            # by default), then with the filtered outputs (the record form)
+            sm, _ = api.smoother(*ins, l, precision=prec)
+            api.status()
+            sr, fi = api.smoother(*ins, l, precision=prec, filtered=api.OUTPUT_KEYS)
             api.status()
         except api.SRTMError as err:   # reported, e.g. a singular solve in the float32 mode
             res[prec] = {"error": str(err)}
@@ -1009,6 +1015,7 @@ def report_errors(name, precisions=("fp64", "mixed", "fp32"), n_slow=None, seed=
         timing[prec] = {"ms_per_call": float(np.median(ms)),
                         "fast_states_per_s": N * l / (float(np.median(ms)) * 1e-3)}
         sm = {k: v.cpu().numpy() for k, v in sm.items()}
+        sr = {k: v.cpu().numpy() for k, v in sr.items()}
         fi = {k: v.cpu().numpy() for k, v in fi.items()}
         e = {}
         for key, got, ref in (
@@ -1018,6 +1025,10 @@ def report_errors(name, precisions=("fp64", "mixed", "fp32"), n_slow=None, seed=
                  np.concatenate([head["fast_smooth_cov"], tail["fast_smooth_cov"]])),
                 ("smoothed first-state mean (all k)", sm["fast_mean"][0::l], head["first_smooth_mean"]),
                 ("smoothed first-state cov (all k)", sm["fast_cov"][0::l], head["first_smooth_cov"]),
+                ("smoothed fast mean, record form", np.concatenate([sr["fast_mean"][:w * l], sr["fast_mean"][-w * l:]]),
+                 np.concatenate([head["fast_smooth_mean"], tail["fast_smooth_mean"]])),
+                ("smoothed fast cov, record form", np.concatenate([sr["fast_cov"][:w * l], sr["fast_cov"][-w * l:]]),
+                 np.concatenate([head["fast_smooth_cov"], tail["fast_smooth_cov"]])),
                 ("filtered fast mean", np.concatenate([fi["fast_mean"][:w * l], fi["fast_mean"][-w * l:]]),
                  np.concatenate([head["fast_filt_mean"], tail["fast_filt_mean"]])),
                 ("filtered fast cov", np.concatenate([fi["fast_cov"][:w * l], fi["fast_cov"][-w * l:]]),
@@ -1026,7 +1037,7 @@ def report_errors(name, precisions=("fp64", "mixed", "fp32"), n_slow=None, seed=
                 ("filtered slow cov (all k)", fi["slow_cov"], head["slow_filt_cov"])):
             e[key] = rel_err(got, ref)
         res[prec] = e
-        del sm, fi
+        del sm, sr, fi
         torch.cuda.empty_cache()
     return {"workload": name, "nx": prob.nx, "ny": prob.ny, "ratio": l, "n_slow": N, "n_fast": N * l,
             "errors": res, "timing": timing}
