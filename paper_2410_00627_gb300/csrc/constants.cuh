@@ -160,75 +160,107 @@ __device__ void two_point_constants(const Ctx& c, int s, int l, int m, double* m
     HS[e] = v;
   }
   __syncthreads();
+  // the two inverses on two warps at once
+  __shared__ int s_ok2[2];
+  for (int e = tid; e < m * m; e += nt) Vy[e] = Vb[(NX + e / m) * d + NX + e % m];
+  __syncthreads();  // Vy copied before Vb is factorised in place
+  if (tid == 0) s_ok2[0] = spd_inverse_checked(Vb, d, Vbi, 1e-6) ? 1 : 0;
+  if (tid == 32 % nt) s_ok2[1] = spd_inverse_checked(Vy, m, Vyi, 1e-6) ? 1 : 0;
+  __syncthreads();
   if (tid == 0) {
-    for (int i = 0; i < m; ++i)
-      for (int j = 0; j < m; ++j) Vy[i * m + j] = Vb[(NX + i) * d + NX + j];
-    const bool ok = spd_inverse_checked(Vb, d, Vbi, 1e-6) && spd_inverse_checked(Vy, m, Vyi, 1e-6);
-    s_bok = ok ? 1 : 0;
-    md[L.bflag] = ok ? 1.0 : 0.0;
+    s_bok = s_ok2[0] && s_ok2[1];
+    md[L.bflag] = s_bok ? 1.0 : 0.0;
   }
   __syncthreads();
   const bool ok = s_bok != 0;
-  // K_i entry (q, col): col < NX the x block, else the y block
-  auto Kent = [&](int i, int q, int col) -> double {
+  // K_i row q (col < NX the x block, else the y block) into registers
+  constexpr int DM = NX + MY;
+  auto Krow = [&](int i, int q, double (&K)[DM]) {
     const double* Qlj = md + L.Ql + (size_t)(i - 2) * NN;
-    if (col < NX) return Qlj[q * NX + col];
-    const int j = col - NX;
-    double v = md[L.VH + (size_t)(i - 2) * NX * m + q * m + j];
-    for (int t = 0; t < NX; ++t) v = fma(-Qlj[q * NX + t], H[j * NX + t], v);
-    return v;
+    const double* VHj = md + L.VH + (size_t)(i - 2) * NX * m;
+#pragma unroll
+    for (int col = 0; col < DM; ++col) {
+      double v = 0.0;
+      if (col < NX) {
+        v = Qlj[q * NX + col];
+      } else if (col - NX < m) {
+        const int j = col - NX;
+        v = VHj[q * m + j];
+#pragma unroll
+        for (int t = 0; t < NX; ++t) v = fma(-Qlj[q * NX + t], H[j * NX + t], v);
+      }
+      K[col] = v;
+    }
   };
-  for (int pr = tid; pr < l * NX; pr += nt) {
-    const int i = pr / NX + 1, r = pr - (pr / NX) * NX;
+  // one thread per entry (i, r, q)
+  for (int e = tid; e < l * NN; e += nt) {
+    const int i = e / NN + 1, rq = e - (e / NN) * NN, r = rq / NX, q = rq - (rq / NX) * NX;
     double* bt = md + L.BrT + (size_t)(i - 1) * BT;
     double* bo = md + L.BrO + (size_t)(i - 1) * BO;
     const double* Ai = md + L.Apow + (size_t)(i - 1) * NN;
     if (i == 1 || !ok) {  // x_{k,1} itself (and placeholders when the record form is kept)
-      for (int q = 0; q < NX; ++q) {
-        const double id = (r == q) ? 1.0 : 0.0;
-        bt[r * NX + q] = id;
-        bt[NN + r * NX + q] = 0.0;
-        bt[2 * NN + r * NX + q] = 0.0;
-        bo[r * NX + q] = id;
-        bo[NN + r * NX + q] = 0.0;
-      }
-      for (int j = 0; j < MY; ++j) {
-        bt[3 * NN + r * MY + j] = 0.0;
-        bo[2 * NN + r * MY + j] = 0.0;
-      }
+      const double id = (r == q) ? 1.0 : 0.0;
+      bt[rq] = id;
+      bt[NN + rq] = 0.0;
+      bt[2 * NN + rq] = 0.0;
+      bo[rq] = id;
+      bo[NN + rq] = 0.0;
+      if (q == 0)
+        for (int j = 0; j < MY; ++j) {
+          bt[3 * NN + r * MY + j] = 0.0;
+          bo[2 * NN + r * MY + j] = 0.0;
+        }
       continue;
     }
     const double* Qj = md + L.Qc + (size_t)(i - 2) * NN;
-    double G[NX + MY], Gy[MY];
-    for (int col = 0; col < d; ++col) {
+    double Kr[DM], Kq[DM], G[DM], Gy[MY];
+    Krow(i, r, Kr);
+    Krow(i, q, Kq);
+#pragma unroll
+    for (int col = 0; col < DM; ++col) {
       double v = 0.0;
-      for (int c2 = 0; c2 < d; ++c2) v = fma(Kent(i, r, c2), Vbi[c2 * d + col], v);
+      if (col < d) {
+#pragma unroll
+        for (int c2 = 0; c2 < DM; ++c2)
+          if (c2 < d) v = fma(Kr[c2], Vbi[c2 * d + col], v);
+      }
       G[col] = v;
     }
-    for (int j = 0; j < m; ++j) {
+#pragma unroll
+    for (int j = 0; j < MY; ++j) {
       double v = 0.0;
-      for (int j2 = 0; j2 < m; ++j2) v = fma(Kent(i, r, NX + j2), Vyi[j2 * m + j], v);
+      if (j < m) {
+#pragma unroll
+        for (int j2 = 0; j2 < MY; ++j2)
+          if (j2 < m) v = fma(Kr[NX + j2], Vyi[j2 * m + j], v);
+      }
       Gy[j] = v;
     }
-    for (int q = 0; q < NX; ++q) {
-      double c1 = Ai[r * NX + q], c1o = Ai[r * NX + q], sg = Qj[r * NX + q], sgo = Qj[r * NX + q];
-      for (int t = 0; t < NX; ++t) c1 = fma(-G[t], Al[t * NX + q], c1);
-      for (int j = 0; j < m; ++j) {
+    double c1 = Ai[rq], c1o = Ai[rq], sg = Qj[rq], sgo = Qj[rq];
+#pragma unroll
+    for (int t = 0; t < NX; ++t) {
+      c1 = fma(-G[t], Al[t * NX + q], c1);
+      sg = fma(-G[t], Kq[t], sg);
+    }
+#pragma unroll
+    for (int j = 0; j < MY; ++j)
+      if (j < m) {
         c1 = fma(-G[NX + j], HS[j * NX + q], c1);
+        sg = fma(-G[NX + j], Kq[NX + j], sg);
         c1o = fma(-Gy[j], HS[j * NX + q], c1o);
-        sgo = fma(-Gy[j], Kent(i, q, NX + j), sgo);
+        sgo = fma(-Gy[j], Kq[NX + j], sgo);
       }
-      for (int col = 0; col < d; ++col) sg = fma(-G[col], Kent(i, q, col), sg);
-      bt[r * NX + q] = c1;
-      bt[NN + r * NX + q] = G[q];
-      bt[2 * NN + r * NX + q] = sg;
-      bo[r * NX + q] = c1o;
-      bo[NN + r * NX + q] = sgo;
-    }
-    for (int j = 0; j < MY; ++j) {
-      bt[3 * NN + r * MY + j] = j < m ? G[NX + j] : 0.0;
-      bo[2 * NN + r * MY + j] = j < m ? Gy[j] : 0.0;
-    }
+    bt[rq] = c1;
+    bt[NN + rq] = G[q];
+    bt[2 * NN + rq] = sg;
+    bo[rq] = c1o;
+    bo[NN + rq] = sgo;
+    if (q == 0)
+#pragma unroll
+      for (int j = 0; j < MY; ++j) {
+        bt[3 * NN + r * MY + j] = j < m ? G[NX + j] : 0.0;
+        bo[2 * NN + r * MY + j] = j < m ? Gy[j] : 0.0;
+      }
   }
 }
 

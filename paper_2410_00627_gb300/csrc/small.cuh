@@ -182,16 +182,18 @@ __device__ __forceinline__ bool small_sym_inverse(const TR (&a)[MY][MY], TR (&in
 // variance: the matrix is singular or too ill-conditioned for the inverse to
 // keep float64 accuracy) or is not finite.
 __device__ inline bool spd_inverse_checked(double* a, int d, double* inv, double rtol) {
+  double rd[16];  // 1 / D_k (d <= 16)
   for (int j = 0; j < d; ++j) {
     const double ajj = a[j * d + j];
     double dj = ajj;
     for (int k = 0; k < j; ++k) dj = fma(-a[j * d + k] * a[j * d + k], a[k * d + k], dj);
     if (!(dj > rtol * ajj) || bad_value(dj)) return false;
     a[j * d + j] = dj;
+    rd[j] = 1.0 / dj;
     for (int i = j + 1; i < d; ++i) {
       double v = a[i * d + j];
       for (int k = 0; k < j; ++k) v = fma(-a[i * d + k] * a[j * d + k], a[k * d + k], v);
-      a[i * d + j] = v / dj;
+      a[i * d + j] = v * rd[j];
     }
   }
   // X = L^{-1} (unit lower): X_ij = -sum_{k=j}^{i-1} L_ik X_kj, kept at a[j][i]
@@ -206,7 +208,7 @@ __device__ inline bool spd_inverse_checked(double* a, int d, double* inv, double
       double v = 0.0;  // sum_{k >= j} X_ki X_kj / D_k, X_kk = 1
       for (int k = j; k < d; ++k) {
         const double xi = k == i ? 1.0 : a[i * d + k], xj = k == j ? 1.0 : a[j * d + k];
-        v = fma(xi * xj, 1.0 / a[k * d + k], v);
+        v = fma(xi * xj, rd[k], v);
       }
       inv[i * d + j] = v;
       inv[j * d + i] = v;
