@@ -559,10 +559,13 @@ __global__ void __launch_bounds__(PRE_THREADS) precompute_kernel(Ctx c, int tabl
     cf[3 * NN + NX * MY + e] = (float)sm[S::K + e];
     cf[3 * NN + 2 * NX * MY + e] = (float)sm[S::Cr + e];
   }
-  {  // float copies of C_bar and R_x for the rank-m filter combine
+  {  // float copies of C_bar and R_x (the rank-m filter combine, the float32
+     // interval setup), A^l and V_l H^T (the float32 interval setup)
     float* cf = (float*)(md + L.Cf) + 6 * NN + 3 * NX * MY;
     for (int e = tid; e < m * NX; e += nt) cf[e] = (float)sm[S::Cb + e];
     for (int e = tid; e < m * m; e += nt) cf[MY * NX + e] = (float)sm[S::Rx + e];
+    for (int e = tid; e < NN; e += nt) cf[MY * NX + MY * MY + e] = (float)Al[e];
+    for (int e = tid; e < NX * m; e += nt) cf[MY * NX + MY * MY + NN + e] = (float)md[L.VH + (size_t)(l - 1) * NX * m + e];
   }
   for (int e = tid; e < m * m; e += nt) md[L.Rx + e] = sm[S::Rx + e];
   for (int e = tid; e < NX; e += nt) md[L.m1 + e] = sm[S::m1 + e];

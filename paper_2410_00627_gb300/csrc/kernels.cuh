@@ -41,6 +41,12 @@ struct SetupGeom {
   static constexpr int SLOT_MIXED_CORE = U1;                                // TR entries the mixed mode uses
   static constexpr int SLOT_MIXED_FLOAT = FREG + (SLOTF * 4 + 7) / 8;       // end of the float region
   static constexpr int SLOT_MIXED = SLOT_MIXED_CORE > SLOT_MIXED_FLOAT ? SLOT_MIXED_CORE : SLOT_MIXED_FLOAT;
+  // the float32 setup of two-point sequences (mixed mode): the float region at
+  // the slot's start, followed by float S_y (MY x MY) and innovation (MY), then
+  // the TR arrays of the P^- solve from TP on: Pll, AP, Pm, Z
+  static constexpr int fSy = SLOTF, fev = fSy + MY * MY, TP = (fev + MY + 1) / 2;
+  static constexpr int tPll = TP, tAP = tPll + NN, tPm = tAP + NN, tZ = tPm + NN;
+  static_assert(tZ + NN <= SLOT_MIXED, "the float32 setup does not fit the mixed-mode slot");
   // the model's float copies (model table, ModelLayout::Cf): A, Qc_1, Cov(e_1, e_l), V_1 H^T
   static constexpr int cA = 0, cQc = NN, cQl = 2 * NN, cVH = 3 * NN;
   template <class T, class TR>
@@ -190,6 +196,271 @@ __device__ __forceinline__ void setup_elements(int r, bool row, unsigned mask, i
   }
 }
 
+// P^-_{k+1,1} = A P^f_{k,l} A^T + Q and Z = A^T (P^-_{k+1,1})^{-1} for one
+// interval by its SG lanes (lane = row), in TR, from the filter result fk =
+// P^f_{k,l} (the fast block ll of Eq. 17 in exact arithmetic); Pll, AP, Pm
+// and Z are the slot's work arrays (AP also holds the 2x2 minors of P^- and
+// the rows of its inverse).  ok turns false on a singular P^-.  No barrier
+// after the last stores of Z.
+template <int NX, int SG, class TR>
+__device__ __forceinline__ void pminus_z(int lane, unsigned mask, const TR* fk, const double* A1, const double* Qm,
+                                         TR* Pll, TR* AP, TR* Pm, TR* Z, bool& ok) {
+  const int r = lane;
+  const bool row = r < NX;
+  if (row) {
+#pragma unroll
+    for (int q = 0; q < NX; ++q) Pll[r * NX + q] = fk[r * NX + q];
+  }
+  __syncwarp(mask);
+  // A P^f_{ll} (row r)
+  if (row) {
+#pragma unroll
+    for (int q = 0; q < NX; ++q) {
+      TR v = TR(0);
+#pragma unroll
+      for (int t = 0; t < NX; ++t) v = fma((TR)A1[r * NX + t], Pll[t * NX + q], v);
+      AP[r * NX + q] = v;
+    }
+  }
+  __syncwarp(mask);
+  // P^-_{k+1,1} = (A P^f_{ll}) A^T + Q (row r, upper triangle, mirrored)
+  if (row) {
+#pragma unroll
+    for (int q = 0; q < NX; ++q) {
+      if (q >= r) {
+        TR v = (TR)Qm[r * NX + q];
+#pragma unroll
+        for (int t = 0; t < NX; ++t) v = fma(AP[r * NX + t], (TR)A1[q * NX + t], v);
+        Pm[r * NX + q] = v;
+        Pm[q * NX + r] = v;
+      }
+    }
+  }
+  __syncwarp(mask);
+  // (P^-)^{-1} by the adjugate for NX <= 4: lane r forms row r of the inverse,
+  // the cofactors C_{c,r} of column r, so that det = sum_c P^-_{c,r} C_{c,r}
+  // needs no other lane; for NX = 4 the twelve 2x2 minors are shared (three
+  // per lane, in the AP slot).  Above NX = 4 every lane forms the whole
+  // inverse by Cholesky.  Then Z = A^T (P^-)^{-1} (row r).
+  if constexpr (NX <= 4) {
+    TR* mn = AP;
+    if constexpr (NX == 4) {
+      for (int u = lane; u < 12; u += SG) {
+        const int r0 = u < 6 ? 0 : 2, v = u < 6 ? u : u - 6;
+        const int p = v < 3 ? 0 : (v < 5 ? 1 : 2);
+        const int q = v < 3 ? v + 1 : (v < 5 ? v - 1 : 3);
+        mn[u] = fma(Pm[r0 * 4 + p], Pm[(r0 + 1) * 4 + q], -Pm[(r0 + 1) * 4 + p] * Pm[r0 * 4 + q]);
+      }
+      __syncwarp(mask);
+    }
+    TR cof[NX];
+    TR det = TR(0);
+    if (row) {
+#pragma unroll
+      for (int col = 0; col < NX; ++col) {
+        TR v;
+        if (NX == 1) {
+          v = TR(1);
+        } else if (NX == 2) {
+          v = (r == col) ? Pm[(1 - r) * 3] : -Pm[r * 2 + col];
+        } else if (NX == 3) {
+          const int i0 = col == 0 ? 1 : 0, i1 = col == 2 ? 1 : 2, j0 = r == 0 ? 1 : 0, j1 = r == 2 ? 1 : 2;
+          v = Pm[i0 * 3 + j0] * Pm[i1 * 3 + j1] - Pm[i0 * 3 + j1] * Pm[i1 * 3 + j0];
+          if ((r + col) & 1) v = -v;
+        } else {
+          const int arow = col ^ 1;
+          const TR* mins = col < 2 ? mn + 6 : mn;
+          const int code = r == 0 ? 0x543 : (r == 1 ? 0x521 : (r == 2 ? 0x420 : 0x310));
+          const int k0 = r > 0 ? 0 : 1, k1 = r > 1 ? 1 : 2, k2 = r > 2 ? 2 : 3;
+          v = Pm[arow * 4 + k0] * mins[(code >> 8) & 15];
+          v = fma(-Pm[arow * 4 + k1], mins[(code >> 4) & 15], v);
+          v = fma(Pm[arow * 4 + k2], mins[code & 15], v);
+          if (((col & 1) != 0) != ((r & 1) != 0)) v = -v;
+        }
+        cof[col] = v;
+        det = fma(Pm[col * NX + r], v, det);
+      }
+      if (bad_value(det)) { ok = false; det = TR(1); }
+    }
+    __syncwarp(mask);  // the minors' last reads
+    if (row) {
+      const TR id = TR(1) / det;
+#pragma unroll
+      for (int q = 0; q < NX; ++q) AP[r * NX + q] = cof[q] * id;
+    }
+    __syncwarp(mask);
+    if (row) {
+#pragma unroll
+      for (int q = 0; q < NX; ++q) {
+        TR v = TR(0);
+#pragma unroll
+        for (int t = 0; t < NX; ++t) v = fma((TR)A1[t * NX + r], AP[t * NX + q], v);
+        Z[r * NX + q] = v;
+      }
+    }
+  } else {
+    TR Pmv[NX][NX], Pmi[NX][NX];
+#pragma unroll
+    for (int i = 0; i < NX; ++i)
+#pragma unroll
+      for (int j = 0; j < NX; ++j) Pmv[i][j] = Pm[i * NX + j];
+    ok &= spd_inverse<NX, TR>(Pmv, Pmi);
+    if (row) {
+#pragma unroll
+      for (int q = 0; q < NX; ++q) {
+        TR v = TR(0);
+#pragma unroll
+        for (int t = 0; t < NX; ++t) v = fma((TR)A1[t * NX + r], Pmi[t][q], v);
+        Z[r * NX + q] = v;
+      }
+    }
+  }
+}
+
+// The interval setup of a sequence that takes the two-point recovery, mixed
+// mode (no record is written, and no log likelihood is asked for): the
+// fast-filter quantities that only feed the smoother element of Eq. (29)
+// (X = P C_bar^T, S_y and its inverse, kap, U_l, S_y^-1 U_l^T, m^f_l,
+// P A^{lT}) are formed in float32, as the element itself; P^-_{k+1,1} and its
+// inverse stay in float64.  Slot layout: SetupGeom's float region from the
+// slot's start, then fSy, fev; the float64 arrays from TP on.
+template <int NX, int M, class T, class TR>
+__device__ __noinline__ void setup_interval_tp(const Ctx& c, long long gi, int s, long long k, int lane, unsigned mask, TR* sb,
+                                  const TR* prev) {
+  using Gm = SetupGeom<NX>;
+  constexpr int MM = M > 0 ? M : MY;
+  constexpr int NN = NX * NX;
+  const int r = lane;
+  const bool row = r < NX;
+  const int N = c.meta.nslow[s], m = M > 0 ? M : c.ny;
+  const double* md = c.model + (long long)s * c.ml.stride;
+  const double* A1 = md + c.ml.Apow + NN;
+  const T* cf = (const T*)(md + c.ml.Cf);
+  const T* Cbf = cf + 6 * NN + 3 * NX * MY;  // m x NX
+  const T* Rxf = Cbf + MY * NX;               // m x m
+  const T* Alf = Rxf + MY * MY;               // NN
+  const T* VHlf = Alf + NN;                   // NX x m
+  T* sf = (T*)sb;
+  bool ok = true;
+  // P^f_{k-1,l}, m^f_{k-1,l} in float
+  if (row) {
+    if (k == 0) {
+      sf[Gm::fmv + r] = (T)c.m0[(long long)s * NX + r];
+#pragma unroll
+      for (int q = 0; q < NX; ++q) sf[Gm::fP + r * NX + q] = (T)c.P0[(long long)s * NN + r * NX + q];
+    } else {
+      const TR* f = prev ? prev : (const TR*)c.fout + (gi - 1) * (NX + NN);
+      sf[Gm::fmv + r] = (T)f[r];
+#pragma unroll
+      for (int q = 0; q < NX; ++q) sf[Gm::fP + r * NX + q] = (T)f[NX + r * NX + q];
+    }
+  }
+  __syncwarp(mask);
+  // X = P C_bar^T (row r)
+  if (row) {
+#pragma unroll
+    for (int j = 0; j < MM; ++j) {
+      T v = T(0);
+      if (j < m) {
+#pragma unroll
+        for (int q = 0; q < NX; ++q) v = fma(sf[Gm::fP + r * NX + q], Cbf[j * NX + q], v);
+      }
+      sf[Gm::fX + r * MY + j] = v;
+    }
+  }
+  __syncwarp(mask);
+  // S_y = C_bar X + R_x (upper entries over the lanes, mirrored), innovation
+  for (int u = lane; u < MM * MM; u += Gm::SG) {
+    const int i = u / MM, j = u - (u / MM) * MM;
+    if (i <= j && j < m) {
+      T v = Rxf[i * m + j];
+#pragma unroll
+      for (int q = 0; q < NX; ++q) v = fma(Cbf[i * NX + q], sf[Gm::fX + q * MY + j], v);
+      sf[Gm::fSy + i * MY + j] = v;
+      sf[Gm::fSy + j * MY + i] = v;
+    }
+  }
+  if (lane < m) {
+    T v = (T)c.y[gi * m + lane];
+#pragma unroll
+    for (int q = 0; q < NX; ++q) v = fma(-Cbf[lane * NX + q], sf[Gm::fmv + q], v);
+    sf[Gm::fev + lane] = v;
+  }
+  __syncwarp(mask);
+  T Si[MY][MY], kap[MY];
+  {
+    T Sy[MY][MY];
+#pragma unroll
+    for (int i = 0; i < MY; ++i)
+#pragma unroll
+      for (int j = 0; j < MY; ++j) Sy[i][j] = (i < m && j < m) ? sf[Gm::fSy + i * MY + j] : ((i == j) ? T(1) : T(0));
+    ok &= small_sym_inverse<T>(Sy, Si, m);
+#pragma unroll
+    for (int i = 0; i < MY; ++i) {
+      T v = T(0);
+#pragma unroll
+      for (int j = 0; j < MY; ++j)
+        if (i < m && j < m) v = fma(Si[i][j], sf[Gm::fev + j], v);
+      kap[i] = i < m ? v : T(0);
+#pragma unroll
+      for (int j = 0; j < MY; ++j)
+        if (!(i < m && j < m)) Si[i][j] = T(0);
+    }
+  }
+  // row r: U_l, S_y^-1 U_l^T (column r), m^f_l, P A^{lT}
+  if (row) {
+    T Ul[MY];
+#pragma unroll
+    for (int j = 0; j < MM; ++j) {
+      T v = T(0);
+      if (j < m) {
+        v = VHlf[r * m + j];
+#pragma unroll
+        for (int q = 0; q < NX; ++q) v = fma(Alf[r * NX + q], sf[Gm::fX + q * MY + j], v);
+      }
+      Ul[j] = v;
+    }
+#pragma unroll
+    for (int i = 0; i < MM; ++i) {
+      T v = T(0);
+#pragma unroll
+      for (int j = 0; j < MM; ++j)
+        if (i < m && j < m) v = fma(Si[i][j], Ul[j], v);
+      sf[Gm::fSUl + i * NX + r] = v;
+    }
+    T v = T(0);
+#pragma unroll
+    for (int q = 0; q < NX; ++q) v = fma(Alf[r * NX + q], sf[Gm::fmv + q], v);
+#pragma unroll
+    for (int j = 0; j < MM; ++j)
+      if (j < m) v = fma(Ul[j], kap[j], v);
+    sf[Gm::fml + r] = v;
+#pragma unroll
+    for (int q = 0; q < NX; ++q) {
+      T w = T(0);
+#pragma unroll
+      for (int t = 0; t < NX; ++t) w = fma(sf[Gm::fP + r * NX + t], Alf[q * NX + t], w);
+      sf[Gm::fPl + r * NX + q] = w;
+    }
+  }
+  // P^-_{k+1,1} and Z in float64, Z rounded once to float
+  pminus_z<NX, Gm::SG, TR>(lane, mask, (const TR*)c.fout + gi * (NX + NN) + NX, A1, md + c.ml.Q, sb + Gm::tPll,
+                          sb + Gm::tAP, sb + Gm::tPm, sb + Gm::tZ, ok);
+  __syncwarp(mask);
+  if (row) {
+#pragma unroll
+    for (int q = 0; q < NX; ++q) sf[Gm::fZ + r * NX + q] = (T)sb[Gm::tZ + r * NX + q];
+  }
+  __syncwarp(mask);
+  T* se = (T*)c.selem + gi * SL<NX>::SIZE;
+  const bool last = k >= N - 1 && !c.split_tail_open;
+  setup_elements<NX, M, T, T, T>(r, row, mask, m, last, sf + Gm::fP, sf + Gm::fPl, sf + Gm::fX, sf + Gm::fSUl,
+                                 sf + Gm::fZ, sf + Gm::fml, sf + Gm::fmv, cf + Gm::cA, cf + Gm::cQc, cf + Gm::cQl,
+                                 cf + Gm::cVH, Si, kap, sf + Gm::fU1, sf + Gm::fP1l, sf + Gm::fP11, sf + Gm::fAml,
+                                 sf + Gm::fU1, se, nullptr, nullptr);
+  if (!ok && lane == 0) raise_err(c.ctr, DEVERR_SINGULAR);
+}
+
 // One interval by its SG lanes (lane = row), slot sb in shared memory (with
 // its float region sf when the smoother elements are formed in float32).
 // prev (optional): p(x_{k-1,l}|y_{1:k-1}) as (m, P) when it is not yet in
@@ -207,6 +478,12 @@ __device__ void setup_interval(const Ctx& c, long long gi, int lane, unsigned ma
   const bool row = r < NX;
   const int s = find_segment(c.meta.off_slow, c.n_seq, gi);
   const long long k = gi - c.meta.off_slow[s];
+  if constexpr (sizeof(T) != sizeof(TR)) {  // mixed mode, a two-point sequence: the float32 setup
+    if (c.smoothing && !c.loglik && !records_needed(c, s)) {
+      setup_interval_tp<NX, M, T, TR>(c, gi, s, k, lane, mask, sb, prev);
+      return;
+    }
+  }
   const int N = c.meta.nslow[s], l = c.meta.ratio[s], m = M > 0 ? M : c.ny;
   const double* md = c.model + (long long)s * c.ml.stride;
   const double* Apow = md + c.ml.Apow;
@@ -327,119 +604,8 @@ __device__ void setup_interval(const Ctx& c, long long gi, int lane, unsigned ma
       sb[Gm::Pl + r * NX + q] = w;
     }
   }
-  // P^f_{k,l} = P^f_{k,ll}: the filter scan's result for this interval (written
-  // before the setup runs), the fast block ll of Eq. (17) in exact arithmetic
-  if (row) {
-    const TR* fk = (const TR*)c.fout + gi * (NX + NN) + NX;
-#pragma unroll
-    for (int q = 0; q < NX; ++q) sb[Gm::Pll + r * NX + q] = fk[r * NX + q];
-  }
-  __syncwarp(mask);
-  // A P^f_{ll} (row r)
-  if (row) {
-#pragma unroll
-    for (int q = 0; q < NX; ++q) {
-      TR v = TR(0);
-#pragma unroll
-      for (int t = 0; t < NX; ++t) v = fma((TR)A1[r * NX + t], sb[Gm::Pll + t * NX + q], v);
-      sb[Gm::AP + r * NX + q] = v;
-    }
-  }
-  __syncwarp(mask);
-  // P^-_{k+1,1} = (A P^f_{ll}) A^T + Q (row r, upper triangle, mirrored)
-  if (row) {
-    const double* Qm = md + c.ml.Q;
-#pragma unroll
-    for (int q = 0; q < NX; ++q) {
-      if (q >= r) {
-        TR v = (TR)Qm[r * NX + q];
-#pragma unroll
-        for (int t = 0; t < NX; ++t) v = fma(sb[Gm::AP + r * NX + t], (TR)A1[q * NX + t], v);
-        sb[Gm::Pm + r * NX + q] = v;
-        sb[Gm::Pm + q * NX + r] = v;
-      }
-    }
-  }
-  __syncwarp(mask);
-  // (P^-)^{-1} by the adjugate for NX <= 4: lane r forms row r of the inverse,
-  // the cofactors C_{c,r} of column r, so that det = sum_c P^-_{c,r} C_{c,r}
-  // needs no other lane; for NX = 4 the twelve 2x2 minors are shared (three
-  // per lane, in the AP slot).  Above NX = 4 every lane forms the whole
-  // inverse by Cholesky.  Then Z = A^T (P^-)^{-1} (row r).
-  if constexpr (NX <= 4) {
-    const TR* Pm = sb + Gm::Pm;
-    TR* mn = sb + Gm::AP;
-    if constexpr (NX == 4) {
-      for (int u = lane; u < 12; u += Gm::SG) {
-        const int r0 = u < 6 ? 0 : 2, v = u < 6 ? u : u - 6;
-        const int p = v < 3 ? 0 : (v < 5 ? 1 : 2);
-        const int q = v < 3 ? v + 1 : (v < 5 ? v - 1 : 3);
-        mn[u] = fma(Pm[r0 * 4 + p], Pm[(r0 + 1) * 4 + q], -Pm[(r0 + 1) * 4 + p] * Pm[r0 * 4 + q]);
-      }
-      __syncwarp(mask);
-    }
-    TR cof[NX];
-    TR det = TR(0);
-    if (row) {
-#pragma unroll
-      for (int col = 0; col < NX; ++col) {
-        TR v;
-        if (NX == 1) {
-          v = TR(1);
-        } else if (NX == 2) {
-          v = (r == col) ? Pm[(1 - r) * 3] : -Pm[r * 2 + col];
-        } else if (NX == 3) {
-          const int i0 = col == 0 ? 1 : 0, i1 = col == 2 ? 1 : 2, j0 = r == 0 ? 1 : 0, j1 = r == 2 ? 1 : 2;
-          v = Pm[i0 * 3 + j0] * Pm[i1 * 3 + j1] - Pm[i0 * 3 + j1] * Pm[i1 * 3 + j0];
-          if ((r + col) & 1) v = -v;
-        } else {
-          const int arow = col ^ 1;
-          const TR* mins = col < 2 ? mn + 6 : mn;
-          const int code = r == 0 ? 0x543 : (r == 1 ? 0x521 : (r == 2 ? 0x420 : 0x310));
-          const int k0 = r > 0 ? 0 : 1, k1 = r > 1 ? 1 : 2, k2 = r > 2 ? 2 : 3;
-          v = Pm[arow * 4 + k0] * mins[(code >> 8) & 15];
-          v = fma(-Pm[arow * 4 + k1], mins[(code >> 4) & 15], v);
-          v = fma(Pm[arow * 4 + k2], mins[code & 15], v);
-          if (((col & 1) != 0) != ((r & 1) != 0)) v = -v;
-        }
-        cof[col] = v;
-        det = fma(Pm[col * NX + r], v, det);
-      }
-      if (bad_value(det)) { ok = false; det = TR(1); }
-    }
-    __syncwarp(mask);  // the minors' last reads
-    if (row) {
-      const TR id = TR(1) / det;
-#pragma unroll
-      for (int q = 0; q < NX; ++q) sb[Gm::AP + r * NX + q] = cof[q] * id;
-    }
-    __syncwarp(mask);
-    if (row) {
-#pragma unroll
-      for (int q = 0; q < NX; ++q) {
-        TR v = TR(0);
-#pragma unroll
-        for (int t = 0; t < NX; ++t) v = fma((TR)A1[t * NX + r], sb[Gm::AP + t * NX + q], v);
-        sb[Gm::Z + r * NX + q] = v;
-      }
-    }
-  } else {
-    TR Pmv[NX][NX], Pmi[NX][NX];
-#pragma unroll
-    for (int i = 0; i < NX; ++i)
-#pragma unroll
-      for (int j = 0; j < NX; ++j) Pmv[i][j] = sb[Gm::Pm + i * NX + j];
-    ok &= spd_inverse<NX, TR>(Pmv, Pmi);
-    if (row) {
-#pragma unroll
-      for (int q = 0; q < NX; ++q) {
-        TR v = TR(0);
-#pragma unroll
-        for (int t = 0; t < NX; ++t) v = fma((TR)A1[t * NX + r], Pmi[t][q], v);
-        sb[Gm::Z + r * NX + q] = v;
-      }
-    }
-  }
+  pminus_z<NX, Gm::SG, TR>(lane, mask, (const TR*)c.fout + gi * (NX + NN) + NX, A1, md + c.ml.Q, sb + Gm::Pll,
+                          sb + Gm::AP, sb + Gm::Pm, sb + Gm::Z, ok);
   __syncwarp(mask);
   // record (row r; lane 0 the m-sized parts), which the two-point recovery
   // does not read

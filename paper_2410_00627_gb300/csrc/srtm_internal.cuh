@@ -63,7 +63,8 @@ struct ModelLayout {
   long long Q;     // n^2         copy of Q
   long long Cf;    // float copies of A, Qc_1, Cov(e_1,e_l) (n^2 each), V_1 H^T, K and C_bar^T R_x^-1
                    // (n x m each, ld m, at n x MY strides), then F, D, J of the generic element (n^2 each),
-                   // C_bar (m x n, at an MY x n stride) and R_x (m x m, ld m)
+                   // C_bar (m x n, at an MY x n stride), R_x (m x m, ld m, at an MY x MY stride), A^l (n^2)
+                   // and V_l H^T (n x m, ld m)
   long long BrT;   // L (3n^2 + n MY)  two-point recovery constants per fast index i: C1_i, C2_i, Sg_i (n^2 each),
                    //                  c3_i (n x m, ld MY)                      [two-point recovery]
   long long BrO;   // L (2n^2 + n MY)  the same for the last interval: C1'_i, Sg'_i, c3'_i
@@ -93,7 +94,7 @@ __host__ __device__ inline ModelLayout make_model_layout(int n, int m, int L) {
   ml.m1 = o;   o += n;
   ml.P1 = o;   o += nn;
   ml.Q = o;    o += nn;
-  ml.Cf = o;   o += (6 * nn + 4LL * n * MY + MY * MY + 1) / 2;
+  ml.Cf = o;   o += (7 * nn + 5LL * n * MY + MY * MY + 1) / 2;
   ml.BrT = o;  o += (long long)L * (3 * nn + (long long)n * MY);
   ml.BrO = o;  o += (long long)L * (2 * nn + (long long)n * MY);
   ml.bflag = o; o += 1;
