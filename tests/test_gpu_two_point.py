@@ -57,6 +57,30 @@ def test_two_point_matches_oracle(oracle_mod, nx, ny, l, N, precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("nx,ny,l,N", [(4, 1, 10, 60), (3, 2, 4, 45), (6, 2, 5, 20)])
+def test_two_point_with_the_setup_as_its_own_kernel(oracle_mod, nx, ny, l, N, precision):
+    """setup_mode 2: the interval setup (float32 for two-point sequences in the
+    mixed mode) runs as its own kernel after the filter scan."""
+    from paper_2410_00627_gb300 import api
+    prob = synth.random_model(500 + nx, nx, ny, l, N)
+    ref, _ = oracle_views(oracle_mod.sequential(prob), l)
+    api.set_tuning(nx, precision, setup_mode=2, recover_form=2)
+    sm, _ = run_smoother(prob, precision, filtered=False)
+    api.status()
+    compare({k: np.asarray(v) for k, v in sm.items()}, ref, *TOL[precision], label=f"setup kernel {prob.name}")
+
+
+def test_two_point_fp32_runs_within_the_mixed_bound(oracle_mod):
+    """The FP32 mode (everything after the model constants in float32, not
+    gated elsewhere) takes the two-point form too; on a well-conditioned model
+    it stays within the mixed tolerances."""
+    prob = synth.random_model(611, 4, 2, 8, 40)
+    ref, _ = oracle_views(oracle_mod.sequential(prob), prob.ratio)
+    got, _ = _smoothed(prob, "fp32", 2)
+    compare(got, ref, *TOL["mixed"], label=f"two-point fp32 {prob.name}")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_two_point_ragged_chains_and_chunks(oracle_mod, precision):
     import torch
 
