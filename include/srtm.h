@@ -142,7 +142,10 @@ int srtm_filter(const srtm_problem *p, srtm_precision prec, const srtm_output *f
                 srtm_stream_t stream);
 
 /* Smoothing p(x_{k,i} | y_{1:N}) (Eq. 21, 29-30).  `filt` (may be NULL)
- * additionally receives the filtering results computed on the way.            */
+ * additionally receives the filtering results computed on the way.  A call
+ * with `filt` NULL and no known inputs forms the fast-rate moments in the
+ * two-point form by default (srtm_tuning.recover_form): the same posterior,
+ * from the smoothed joint of each interval's first state and the next one. */
 int srtm_smoother(const srtm_problem *p, srtm_precision prec, const srtm_output *smooth,
                   const srtm_output *filt, srtm_stream_t stream);
 
