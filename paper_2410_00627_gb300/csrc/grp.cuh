@@ -306,8 +306,10 @@ __device__ __forceinline__ bool g_inverse(const Grp<G>& g, TS* a, TS* mn) {
 //   F_ij = W F_i,                 d_ij = W (d_i + D_i eta_j) + d_j,
 //   D_ij = W D_i F_j^T + D_j,     eta_ij = V^T (eta_j - J_j d_i) + eta_i,
 //   J_ij = V^T J_j F_i + J_i.
-// M is inverted in TS (float64 in the mixed mode) by pivoted Gauss-Jordan;
-// everything else is in T.  D_ij and J_ij are written exactly symmetric.
+// M is inverted in TS (float64 in the mixed mode): by the adjugate for
+// NX <= 4, by pivoted Gauss-Jordan above; everything else is in T.  D_ij and
+// J_ij are written exactly symmetric.  (A generic element on the right takes
+// the rank-m form of this operator instead, g_filter_combine_rank.)
 // prefix=true: a is a prefix that contains the first element (F = 0, eta = 0,
 // J = 0 exactly, Eq. 25 with k = 1), so only d_ij, D_ij are formed and F_ij,
 // eta_ij, J_ij are zero.
