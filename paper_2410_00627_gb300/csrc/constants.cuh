@@ -98,8 +98,9 @@ struct PreGeom {
 // Constants of the two-point recovery of one sequence (float64, by the
 // block of its constants kernel, after the model table is written).  Given
 // the first state x_{k,1} of an interval, the noise parts of the interval's
-// states, eps_i = x_{k,i} - A^{i-1} x_{k,1} (i = 1..l+1, eps_{l+1} the next
-// interval's first state), are e_{i-1} of the lifted model (Sec. III-A), so
+// states, eps_i = x_{k,i} - A^{i-1} x_{k,1} (i = 1..l+1, eps_{l+1} for the
+// next interval's first state), are jointly distributed as e_{i-1} of the
+// lifted model (Sec. III-A; the noise of i - 1 fast steps), so
 //   Cov(eps_i) = Qc_{i-1},  Cov(eps_i, eps_{l+1}) = Cov(e_{i-1}, e_l),
 //   Cov(eps_i, H sum_j eps_j) = (V_{i-1} - Cov(e_{i-1}, e_l)) H^T,
 // and v = [x_{k+1,1}; y_k] has E[v | x_{k,1}] = [A^l; H S_{l-1}] x_{k,1}
